@@ -1,0 +1,621 @@
+/*
+ * sk_oracle.c -- plain, slow FP64 CPU oracle for Many-Configuration
+ * Markov-Chain Monte Carlo (MCMCMC) on the Sherrington-Kirkpatrick (SK)
+ * spin glass (Simkovic & Rossi, arXiv:2102.05613).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path links, loads or
+ * calls this file; only the test-suite, the smoke check and the CPU-baseline
+ * leg of the benchmark do.  It shares no code with the CUDA path: the Philox
+ * generator, the weight tables and every step of the chain are written out
+ * here a second time, from their published definitions.
+ *
+ * What it computes (citations are to the paper's sections and equations):
+ *
+ *  - Energy.  The paper's SK energy (Sec. IV.A) is (1/sqrt L) sum_{j<k} J S S
+ *    with J ~ N(0,1).  We use the equivalent E = -scale * sum_{i<j} J_ij s_i s_j
+ *    with J ~ N(0,1/N) (Gaussian) or J = +-1 (the +-J model), which is the same
+ *    ensemble after J -> -J/sqrt(N).  Local fields h_i = sum_j J_ij s_j, so that
+ *    E = -scale/2 sum_i s_i h_i; flipping site i changes E by 2 scale s_i h_i.
+ *
+ *  - Node rule.  Sec. A.2, Eq. (eq_det_balance_graph_solution): a node c of
+ *    the undirected graph T is visited with P_node(c|T) proportional to
+ *    P_eq(c) P_gen(T|c), normalised over V(T) (Eq. eq_normalization_p_c_T).
+ *    The next graph is generated from the node chosen (Eq. eq_gen_graph).
+ *
+ *  - Graph.  App. B.2 (general graph populating process): a K-ary tree of
+ *    depth one (the "star", K+1 slots) whose root slot is drawn uniformly,
+ *    p_r = 1/(K+1), and whose edges are populated with the symmetric
+ *    single-spin-flip proposal P_gen(c'|c) = 1/N.  Then P_gen(T|c) is the
+ *    same for every slot (the "self-thermalizing tree"), so P_node is
+ *    proportional to P_eq = exp(-beta E) alone.
+ *      * root = centre (probability 1/(K+1)): slot 0 is the current state c,
+ *        slot d = 1..K is c with site_d flipped;
+ *      * root = a leaf (probability K/(K+1)): slot 0 is c, slot 1 (the
+ *        centre) is c with a = site_1 flipped, slot d = 2..K is the centre
+ *        with b = site_d flipped (a double flip, or c itself when b = a).
+ *    All slots are labelled, so a configuration present in m slots is
+ *    chosen with m times its weight.
+ *
+ *  - K = 1 of the same rule is the two-node heat-bath chain of Sec. III.A,
+ *    Eq. (eq_node_two_conf).  The "standard local Metropolis" comparator of
+ *    Sec. IV.B uses the acceptance min(1, P_eq(c1)/P_eq(c0)) of Sec. II.
+ *
+ *  Readings where the paper is silent (random numbers, integer weight
+ *  tables, tie-breaks, acceptance of an MCMCMC step) are spelt out at each
+ *  function below.  Random numbers come from Philox4x32-10 (Salmon, Moraes,
+ *  Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11),
+ *  addressed by counter = (block, step, chain, domain<<24 | stream) and
+ *  key = (seed low word, seed high word).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define SKO_PM1 0
+#define SKO_GAUSS 1
+#define SKO_MCMCMC 0
+#define SKO_METROPOLIS 1
+#define SKO_MAX_K 256
+#define SKO_MAXSLOT_GUARD (SKO_MAX_K + 1)
+
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10, SC'11: ten rounds of two 32x32->64 multiplies with   */
+/* the multipliers 0xD2511F53, 0xCD9E8D57; the key is bumped by the    */
+/* Weyl constants 0x9E3779B9, 0xBB67AE85 between rounds.               */
+/* ------------------------------------------------------------------ */
+void sko_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)x0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)x2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t y0 = hi1 ^ x1 ^ k0;
+        uint32_t y1 = lo1;
+        uint32_t y2 = hi0 ^ x3 ^ k1;
+        uint32_t y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* One Philox block of the chain's stream. */
+static void draw_block(uint64_t seed, uint32_t stream, uint32_t domain,
+                       uint32_t chain, uint64_t step, uint32_t block, uint32_t out[4]) {
+    uint32_t ctr[4] = {block, (uint32_t)step, chain, (domain << 24) | (stream & 0xFFFFFFu)};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    sko_philox(ctr, key, out);
+}
+
+/* floor(x * n / 2^32): a 32-bit word mapped onto {0..n-1}. */
+static uint32_t range32(uint32_t x, uint32_t n) {
+    return (uint32_t)(((uint64_t)x * (uint64_t)n) >> 32);
+}
+
+/* floor(x * n / 2^64) for 64-bit x. */
+static uint64_t range64(uint64_t x, uint64_t n) {
+    return (uint64_t)(((unsigned __int128)x * (unsigned __int128)n) >> 64);
+}
+
+/* ------------------------------------------------------------------ */
+/* Model                                                               */
+/* ------------------------------------------------------------------ */
+static double coupling(int kind, const void* J, int N, int i, int j) {
+    if (kind == SKO_PM1) return (double)((const int8_t*)J)[(size_t)i * N + j];
+    return (double)((const float*)J)[(size_t)i * N + j];
+}
+
+/* E = -scale * sum_{i<j} J_ij s_i s_j, written out as the double sum. */
+double sko_energy(int N, int kind, const void* J, double scale, const int8_t* s) {
+    double e = 0.0;
+    for (int i = 0; i < N; ++i)
+        for (int j = i + 1; j < N; ++j)
+            e += coupling(kind, J, N, i, j) * (double)s[i] * (double)s[j];
+    return -scale * e;
+}
+
+/* h_i = sum_j J_ij s_j (unscaled). */
+void sko_fields(int N, int kind, const void* J, const int8_t* s, double* h) {
+    for (int i = 0; i < N; ++i) {
+        double acc = 0.0;
+        for (int j = 0; j < N; ++j) acc += coupling(kind, J, N, i, j) * (double)s[j];
+        h[i] = acc;
+    }
+}
+
+/* Random start: domain 1, 128 spins per Philox block, bit set -> -1. */
+void sko_init_spins(uint64_t seed, uint32_t stream, uint32_t chain, int N, int8_t* s) {
+    for (int i = 0; i < N; i += 128) {
+        uint32_t w[4];
+        draw_block(seed, stream, 1u, chain, 0, (uint32_t)(i / 128), w);
+        for (int k = 0; k < 128 && i + k < N; ++k) {
+            uint32_t bit = (w[k / 32] >> (k % 32)) & 1u;
+            s[i + k] = bit ? (int8_t)-1 : (int8_t)1;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Integer weight tables for the +-J model (reading of the paper's     */
+/* P_eq ratios in exact integer arithmetic, so that two independent    */
+/* implementations take identical decisions).                          */
+/*   MCMCMC:     W[d] = round(2^52 exp(-2 beta_eff d)), d = (dE-min)/2, */
+/*               cut at the first entry that rounds to zero.           */
+/*   Metropolis: M[k] = round(2^53 exp(-2 beta_eff k)), k = dE/2 >= 1.  */
+/* ------------------------------------------------------------------ */
+int sko_weight_table(double beta_eff, int dmax, uint64_t* W) {
+    int len = 0;
+    for (int d = 0; d <= dmax; ++d) {
+        double v = nearbyint(ldexp(exp(-2.0 * beta_eff * (double)d), 52));
+        if (v <= 0.0) break;
+        W[d] = (uint64_t)v;
+        len = d + 1;
+    }
+    return len;
+}
+
+int sko_metropolis_table(double beta_eff, int kmax, uint64_t* M) {
+    for (int k = 0; k <= kmax; ++k) {
+        double v = nearbyint(ldexp(exp(-2.0 * beta_eff * (double)k), 53));
+        M[k] = (uint64_t)v;
+    }
+    return kmax + 1;
+}
+
+/* ------------------------------------------------------------------ */
+/* One chain                                                           */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int N, kind, K, rule;
+    const void* J;
+    double scale, beta;
+    uint64_t seed;
+    uint32_t stream;
+    /* +-J integer tables */
+    uint64_t* W;
+    int wlen;
+    uint64_t* M;
+    int mlen;
+} sko_ctx;
+
+typedef struct {
+    int n_moves;      /* 0, 1 or 2 spins to flip */
+    int site[2];
+    int slot;         /* selected slot, 0..K */
+} sko_move;
+
+/*
+ * Candidate energies of the K+1 slots (Sec. A.2 node rule on the App. B.2
+ * star).  Returns in dE[j] the unscaled energy change of slot j relative to
+ * the current state, and in flips[j] the spins that slot j differs by.
+ */
+static void star_candidates(const sko_ctx* c, const int8_t* s, const double* h,
+                            int leaf_root, const uint32_t* sites,
+                            double* dE, int (*flips)[2], int* nflip) {
+    const int K = c->K;
+    dE[0] = 0.0;
+    nflip[0] = 0;
+    if (!leaf_root) {
+        for (int d = 1; d <= K; ++d) {
+            int i = (int)sites[d];
+            dE[d] = 2.0 * (double)s[i] * h[i];
+            flips[d][0] = i;
+            nflip[d] = 1;
+        }
+        return;
+    }
+    int a = (int)sites[1];
+    double dEa = 2.0 * (double)s[a] * h[a];
+    dE[1] = dEa;
+    flips[1][0] = a;
+    nflip[1] = 1;
+    for (int d = 2; d <= K; ++d) {
+        int b = (int)sites[d];
+        if (b == a) {            /* the centre flipped back: the root itself */
+            dE[d] = 0.0;
+            nflip[d] = 0;
+            continue;
+        }
+        /* E(c^{a,b}) - E(c) = 2 s_a h_a + 2 s_b h_b - 4 J_ab s_a s_b */
+        dE[d] = dEa + 2.0 * (double)s[b] * h[b]
+              - 4.0 * coupling(c->kind, c->J, c->N, a, b) * (double)s[a] * (double)s[b];
+        flips[d][0] = a;
+        flips[d][1] = b;
+        nflip[d] = 2;
+    }
+}
+
+/*
+ * Slot selection with probability proportional to exp(-beta_eff dE_j).
+ *   +-J: integer weights from the table, inclusive prefix P_j in slot order,
+ *        u = floor(U * P_K / 2^64), the first j with P_j > u.
+ *   Gaussian: the same in double precision with u = (U>>40) 2^-24 P_K.
+ */
+static int select_slot(const sko_ctx* c, const double* dE, int nslot, uint64_t U) {
+    double m = dE[0];
+    for (int j = 1; j < nslot; ++j) if (dE[j] < m) m = dE[j];
+    if (c->kind == SKO_PM1) {
+        uint64_t P[SKO_MAXSLOT_GUARD];
+        uint64_t acc = 0;
+        for (int j = 0; j < nslot; ++j) {
+            long long d = (long long)llround((dE[j] - m) * 0.5);
+            uint64_t w = (d < c->wlen) ? c->W[d] : 0u;
+            acc += w;
+            P[j] = acc;
+        }
+        uint64_t u = range64(U, acc);
+        for (int j = 0; j < nslot; ++j)
+            if (P[j] > u) return j;
+        return nslot - 1; /* unreachable: u < P_K */
+    } else {
+        double P[SKO_MAXSLOT_GUARD];
+        double acc = 0.0;
+        const double be = c->beta * c->scale;
+        for (int j = 0; j < nslot; ++j) {
+            acc += exp(-be * (dE[j] - m));
+            P[j] = acc;
+        }
+        double u = (double)(U >> 40) * ldexp(1.0, -24) * acc;
+        for (int j = 0; j < nslot; ++j)
+            if (P[j] > u) return j;
+        for (int j = nslot - 1; j >= 0; --j)
+            if (exp(-be * (dE[j] - m)) > 0.0) return j;
+        return 0;
+    }
+}
+
+/* Flip spin x: h_k -= 2 s_x J_kx for every k, then s_x = -s_x. */
+static void flip_spin(const sko_ctx* c, int8_t* s, double* h, int x) {
+    double sx = (double)s[x];
+    for (int k = 0; k < c->N; ++k) h[k] -= 2.0 * sx * coupling(c->kind, c->J, c->N, k, x);
+    s[x] = (int8_t)(-s[x]);
+}
+
+/*
+ * Step t of one chain.  The MCMCMC step draws Philox block 0 of domain 0
+ * (U0 = w1:w0 picks the root slot, U1 = w3:w2 picks the node) and blocks
+ * 1..ceil(K/4) (site_d = floor(w * N / 2^32), four per block, d = 1..K).
+ * The Metropolis step draws block 0 only: site = floor(w0 N / 2^32),
+ * U1 = w3:w2 decides acceptance.
+ *
+ * forced >= 0 replays a slot chosen elsewhere instead of the oracle's own
+ * choice (used by the decision-replay check); *own returns the oracle's
+ * choice, Pout and uout the prefix sums and the draw it was taken with.
+ * Returns 1 when the configuration changed (the acceptance count).
+ */
+static int chain_step(const sko_ctx* c, uint32_t chain, uint64_t t, int8_t* s, double* h,
+                      int forced, int* own, double* Pout, double* uout) {
+    uint32_t w0[4];
+    draw_block(c->seed, c->stream, 0u, chain, t, 0u, w0);
+    uint64_t U0 = ((uint64_t)w0[1] << 32) | w0[0];
+    uint64_t U1 = ((uint64_t)w0[3] << 32) | w0[2];
+    if (c->rule == SKO_METROPOLIS) {
+        int i = (int)range32(w0[0], (uint32_t)c->N);
+        double dE = 2.0 * (double)s[i] * h[i];
+        int accept;
+        double pacc;
+        if (c->kind == SKO_PM1) {
+            long long k = llround(dE * 0.5);
+            accept = (dE <= 0.0) || ((U1 >> 11) < c->M[k]);
+            pacc = (dE <= 0.0) ? 1.0 : ldexp((double)c->M[k], -53);
+            if (uout) *uout = ldexp((double)(U1 >> 11), -53);
+        } else {
+            pacc = (dE <= 0.0) ? 1.0 : exp(-c->beta * c->scale * dE);
+            double u = (double)(U1 >> 40) * ldexp(1.0, -24);
+            accept = (dE <= 0.0) || (u < pacc);
+            if (uout) *uout = u;
+        }
+        if (Pout) Pout[0] = pacc;
+        if (own) *own = accept;
+        if (forced >= 0) accept = forced;
+        if (accept) flip_spin(c, s, h, i);
+        return accept;
+    }
+
+    const int K = c->K;
+    int leaf_root = range64(U0, (uint64_t)K + 1u) != 0u;
+    uint32_t sites[SKO_MAXSLOT_GUARD] = {0};
+    for (int d = 1; d <= K; ++d) {
+        uint32_t wb[4];
+        draw_block(c->seed, c->stream, 0u, chain, t, (uint32_t)(1 + (d - 1) / 4), wb);
+        sites[d] = range32(wb[(d - 1) % 4], (uint32_t)c->N);
+    }
+    double dE[SKO_MAXSLOT_GUARD];
+    int flips[SKO_MAXSLOT_GUARD][2];
+    int nflip[SKO_MAXSLOT_GUARD];
+    star_candidates(c, s, h, leaf_root, sites, dE, flips, nflip);
+    int j = select_slot(c, dE, K + 1, U1);
+    if (own) *own = j;
+    if (Pout || uout) {
+        /* prefix sums in the same order as select_slot, for the replay check */
+        double m = dE[0];
+        for (int q = 1; q <= K; ++q) if (dE[q] < m) m = dE[q];
+        double acc = 0.0;
+        for (int q = 0; q <= K; ++q) {
+            double w;
+            if (c->kind == SKO_PM1) {
+                long long d = llround((dE[q] - m) * 0.5);
+                w = (d < c->wlen) ? (double)c->W[d] : 0.0;
+            } else {
+                w = exp(-c->beta * c->scale * (dE[q] - m));
+            }
+            acc += w;
+            if (Pout) Pout[q] = acc;
+        }
+        if (uout) *uout = (c->kind == SKO_PM1) ? ldexp((double)U1, -64) * acc
+                                               : (double)(U1 >> 40) * ldexp(1.0, -24) * acc;
+    }
+    if (forced >= 0) j = forced;
+    for (int f = 0; f < nflip[j]; ++f) flip_spin(c, s, h, flips[j][f]);
+    return nflip[j] > 0;
+}
+
+static int ctx_init(sko_ctx* c, int N, int kind, const void* J, double scale, int rule, int K,
+                    double beta, uint64_t seed, uint32_t stream) {
+    if (N < 2 || N > 65536 || !J) return -1;
+    if (kind != SKO_PM1 && kind != SKO_GAUSS) return -1;
+    if (rule != SKO_MCMCMC && rule != SKO_METROPOLIS) return -1;
+    if (rule == SKO_MCMCMC && (K < 1 || K > SKO_MAX_K)) return -1;
+    if (!(beta >= 0.0) || !(scale > 0.0)) return -1;
+    memset(c, 0, sizeof(*c));
+    c->N = N; c->kind = kind; c->J = J; c->scale = scale; c->rule = rule; c->K = K;
+    c->beta = beta; c->seed = seed; c->stream = stream;
+    if (kind == SKO_PM1) {
+        int dmax = 4 * N + 4;
+        c->W = (uint64_t*)calloc((size_t)dmax + 1, sizeof(uint64_t));
+        c->M = (uint64_t*)calloc((size_t)N + 1, sizeof(uint64_t));
+        if (!c->W || !c->M) return -2;
+        c->wlen = sko_weight_table(beta * scale, dmax, c->W);
+        c->mlen = sko_metropolis_table(beta * scale, N, c->M);
+    }
+    return 0;
+}
+
+static void ctx_free(sko_ctx* c) {
+    free(c->W);
+    free(c->M);
+}
+
+/*
+ * Runs chains chain0 .. chain0+nchains-1 for nsteps steps from step 0.
+ *   init_spins: nchains*N spins (+-1), or NULL for the Philox random start.
+ *   Every record_every steps (after step t with (t+1) % record_every == 0)
+ *   record r stores: rec_E[r*nchains+i] = scale * E of chain i,
+ *   rec_acc[r*nchains+i] = steps in the interval whose configuration changed,
+ *   rec_q[r*(nchains/2)+m] = (1/N) sum_k s_k s'_k of the pair (2m, 2m+1)
+ *   (chain0 must be even for q).  Any output may be NULL.
+ *   trace (nchains*nsteps, may be NULL) receives the slot chosen at each step
+ *   (Metropolis: 1 accepted, 0 rejected).
+ *   resync_every > 0 recomputes the fields from scratch at that period and
+ *   checks them against the maintained ones (exact for +-J, 1e-9 Gaussian).
+ * Returns 0, -1 on a bad argument, -2 out of memory, -3 on a field mismatch.
+ */
+int sko_run(int N, int kind, const void* J, double scale, int rule, int K, double beta,
+            uint64_t seed, uint32_t stream, uint32_t chain0, uint32_t nchains,
+            const int8_t* init_spins, uint64_t nsteps, uint32_t record_every,
+            double* rec_E, uint32_t* rec_acc, double* rec_q,
+            int8_t* final_spins, double* final_E, int32_t* trace, uint32_t resync_every) {
+    sko_ctx c;
+    int rc = ctx_init(&c, N, kind, J, scale, rule, K, beta, seed, stream);
+    if (rc) return rc;
+    if (rec_q && (chain0 % 2u) != 0u) { ctx_free(&c); return -1; }
+    uint64_t nrec = record_every ? nsteps / record_every : 0;
+    int8_t* s = (int8_t*)malloc((size_t)N);
+    double* h = (double*)malloc(sizeof(double) * (size_t)N);
+    double* h2 = (double*)malloc(sizeof(double) * (size_t)N);
+    int8_t* partner = (int8_t*)malloc((size_t)N * (nrec ? nrec : 1));
+    if (!s || !h || !h2 || !partner) { rc = -2; goto done; }
+    for (uint32_t ci = 0; ci < nchains; ++ci) {
+        uint32_t chain = chain0 + ci;
+        if (init_spins) memcpy(s, init_spins + (size_t)ci * N, (size_t)N);
+        else sko_init_spins(seed, stream, 0 + chain, N, s);
+        sko_fields(N, kind, J, s, h);
+        uint32_t acc = 0;
+        for (uint64_t t = 0; t < nsteps; ++t) {
+            int own = -1;
+            acc += (uint32_t)chain_step(&c, chain, t, s, h, -1, &own, NULL, NULL);
+            if (trace) trace[(size_t)ci * nsteps + t] = own;
+            if (resync_every && ((t + 1) % resync_every) == 0) {
+                sko_fields(N, kind, J, s, h2);
+                for (int k = 0; k < N; ++k) {
+                    double d = fabs(h2[k] - h[k]);
+                    if ((kind == SKO_PM1 && d != 0.0) || (kind == SKO_GAUSS && d > 1e-9)) {
+                        rc = -3;
+                        goto done;
+                    }
+                }
+            }
+            if (record_every && ((t + 1) % record_every) == 0) {
+                uint64_t r = (t + 1) / record_every - 1;
+                if (rec_E) rec_E[r * nchains + ci] = sko_energy(N, kind, J, scale, s);
+                if (rec_acc) rec_acc[r * nchains + ci] = acc;
+                acc = 0;
+                if (rec_q) {
+                    if ((ci % 2u) == 0u) {
+                        memcpy(partner + (size_t)r * N, s, (size_t)N);
+                    } else {
+                        double q = 0.0;
+                        for (int k = 0; k < N; ++k)
+                            q += (double)s[k] * (double)partner[(size_t)r * N + k];
+                        rec_q[r * (nchains / 2) + ci / 2] = q / (double)N;
+                    }
+                }
+            }
+        }
+        if (final_spins) memcpy(final_spins + (size_t)ci * N, s, (size_t)N);
+        if (final_E) final_E[ci] = sko_energy(N, kind, J, scale, s);
+    }
+done:
+    free(s); free(h); free(h2); free(partner);
+    ctx_free(&c);
+    return rc;
+}
+
+/*
+ * Decision replay for one chain: walks the chain with the oracle's random
+ * numbers but follows the slot sequence `slots` taken elsewhere (the GPU
+ * trace).  A step whose slot differs from the oracle's own choice is
+ * admissible when the oracle's draw u lies within tol * P_K of the chosen
+ * slot's interval [P_{j-1}, P_j) (Metropolis: within tol of the acceptance
+ * threshold), i.e. when it is a near-tie that rounding may decide either way.
+ * Returns the number of inadmissible steps (>= 0) or a negative error;
+ * n_disagree counts all differing steps, first_bad the first inadmissible one.
+ */
+long long sko_replay(int N, int kind, const void* J, double scale, int rule, int K, double beta,
+                     uint64_t seed, uint32_t stream, uint32_t chain, const int8_t* init_spins,
+                     uint64_t nsteps, const int32_t* slots, double tol,
+                     long long* n_disagree, long long* first_bad,
+                     int8_t* final_spins, double* final_E) {
+    sko_ctx c;
+    int rc = ctx_init(&c, N, kind, J, scale, rule, K, beta, seed, stream);
+    if (rc) return rc;
+    int8_t* s = (int8_t*)malloc((size_t)N);
+    double* h = (double*)malloc(sizeof(double) * (size_t)N);
+    double P[SKO_MAXSLOT_GUARD];
+    long long bad = 0, dis = 0, first = -1;
+    if (!s || !h) { free(s); free(h); ctx_free(&c); return -2; }
+    if (init_spins) memcpy(s, init_spins, (size_t)N);
+    else sko_init_spins(seed, stream, chain, N, s);
+    sko_fields(N, kind, J, s, h);
+    for (uint64_t t = 0; t < nsteps; ++t) {
+        int g = slots[t];
+        int nslot = (rule == SKO_METROPOLIS) ? 2 : K + 1;
+        if (g < 0 || g >= nslot) { bad++; if (first < 0) first = (long long)t; break; }
+        int own = -1;
+        double u = 0.0;
+        chain_step(&c, chain, t, s, h, g, &own, P, &u);
+        if (own != g) {
+            dis++;
+            int ok;
+            if (rule == SKO_METROPOLIS) {
+                ok = fabs(u - P[0]) <= tol;
+            } else {
+                double PK = P[K];
+                double lo = (g == 0) ? 0.0 : P[g - 1];
+                double hi = P[g];
+                ok = (u >= lo - tol * PK) && (u < hi + tol * PK);
+            }
+            if (!ok) { bad++; if (first < 0) first = (long long)t; }
+        }
+    }
+    if (final_spins) memcpy(final_spins, s, (size_t)N);
+    if (final_E) *final_E = sko_energy(N, kind, J, scale, s);
+    if (n_disagree) *n_disagree = dis;
+    if (first_bad) *first_bad = first;
+    free(s); free(h);
+    ctx_free(&c);
+    return bad;
+}
+
+/* ------------------------------------------------------------------ */
+/* Exact enumeration (small N)                                         */
+/* ------------------------------------------------------------------ */
+static void spins_of(uint32_t x, int N, int8_t* s) {
+    for (int i = 0; i < N; ++i) s[i] = ((x >> i) & 1u) ? (int8_t)-1 : (int8_t)1;
+}
+
+/* pi(x) = exp(-beta E(x)) / Z over all 2^N states, x bit i set <=> s_i = -1. */
+int sko_boltzmann(int N, int kind, const void* J, double scale, double beta, double* pi) {
+    if (N < 1 || N > 24) return -1;
+    int8_t s[24];
+    uint32_t n = 1u << N;
+    double emin = INFINITY;
+    for (uint32_t x = 0; x < n; ++x) {
+        spins_of(x, N, s);
+        pi[x] = sko_energy(N, kind, J, scale, s);
+        if (pi[x] < emin) emin = pi[x];
+    }
+    double Z = 0.0;
+    for (uint32_t x = 0; x < n; ++x) {
+        pi[x] = exp(-beta * (pi[x] - emin));
+        Z += pi[x];
+    }
+    for (uint32_t x = 0; x < n; ++x) pi[x] /= Z;
+    return 0;
+}
+
+/*
+ * Exact one-step transition matrix P[x*2^N + y] of the chain, by enumerating
+ * the root choice and every K-tuple of sites (N^K tuples, each 1/N^K).
+ *   root_mode 0: uniform root over the K+1 slots (the method);
+ *   root_mode 1: the root always at the centre (an invalid variant, kept as a
+ *                negative control for the detailed-balance test).
+ *   weight_mode 0: weights exp(-beta dE) in double precision;
+ *   weight_mode 1: the +-J integer tables used by the trajectories.
+ */
+int sko_transition_matrix(int N, int kind, const void* J, double scale, int rule, int K,
+                          double beta, int root_mode, int weight_mode, double* P) {
+    if (N < 1 || N > 12) return -1;
+    if (rule == SKO_MCMCMC && (K < 1 || K > 8)) return -1;
+    sko_ctx c;
+    int rc = ctx_init(&c, N, kind, J, scale, rule, K < 1 ? 1 : K, beta, 0, 0);
+    if (rc) return rc;
+    if (weight_mode == 1 && kind != SKO_PM1) { ctx_free(&c); return -1; }
+    uint32_t n = 1u << N;
+    memset(P, 0, sizeof(double) * (size_t)n * n);
+    int8_t s[12];
+    double h[12];
+    const double be = beta * scale;
+    for (uint32_t x = 0; x < n; ++x) {
+        spins_of(x, N, s);
+        sko_fields(N, kind, J, s, h);
+        double* row = P + (size_t)x * n;
+        if (rule == SKO_METROPOLIS) {
+            for (int i = 0; i < N; ++i) {
+                double dE = 2.0 * (double)s[i] * h[i];
+                double a;
+                if (dE <= 0.0) a = 1.0;
+                else if (weight_mode == 1) a = ldexp((double)c.M[llround(dE * 0.5)], -53);
+                else a = exp(-be * dE);
+                row[x ^ (1u << i)] += a / (double)N;
+                row[x] += (1.0 - a) / (double)N;
+            }
+            continue;
+        }
+        long long ntup = 1;
+        for (int d = 0; d < K; ++d) ntup *= N;
+        const double ptup = 1.0 / (double)ntup;
+        for (int leaf = 0; leaf <= 1; ++leaf) {
+            double proot;
+            if (root_mode == 1) proot = leaf ? 0.0 : 1.0;
+            else proot = leaf ? (double)K / (double)(K + 1) : 1.0 / (double)(K + 1);
+            if (proot == 0.0) continue;
+            uint32_t sites[SKO_MAXSLOT_GUARD] = {0};
+            for (long long tup = 0; tup < ntup; ++tup) {
+                double dE[SKO_MAXSLOT_GUARD], w[SKO_MAXSLOT_GUARD];
+                int flips[SKO_MAXSLOT_GUARD][2], nflip[SKO_MAXSLOT_GUARD];
+                star_candidates(&c, s, h, leaf, sites, dE, flips, nflip);
+                double m = dE[0];
+                for (int j = 1; j <= K; ++j) if (dE[j] < m) m = dE[j];
+                double tot = 0.0;
+                for (int j = 0; j <= K; ++j) {
+                    if (weight_mode == 1) {
+                        long long d = llround((dE[j] - m) * 0.5);
+                        w[j] = (d < c.wlen) ? (double)c.W[d] : 0.0;
+                    } else {
+                        w[j] = exp(-be * (dE[j] - m));
+                    }
+                    tot += w[j];
+                }
+                for (int j = 0; j <= K; ++j) {
+                    uint32_t y = x;
+                    for (int f = 0; f < nflip[j]; ++f) y ^= 1u << flips[j][f];
+                    row[y] += proot * ptup * w[j] / tot;
+                }
+                /* odometer over the K-tuple of sites */
+                for (int d = 1; d <= K; ++d) {
+                    if (++sites[d] < (uint32_t)N) break;
+                    sites[d] = 0;
+                }
+            }
+        }
+    }
+    ctx_free(&c);
+    return 0;
+}

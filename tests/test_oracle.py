@@ -1,0 +1,313 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Nothing here calls the CUDA path.  Each test states what would break it:
+ - Philox: published known-answer vectors and cuRAND's host Philox generator;
+ - the node rule: exact detailed balance and stationarity of enumerated
+   one-step transition matrices w.r.t. the brute-force Boltzmann weights
+   (Sec. A.2, Eq. eq_det_balance_graph_solution), which fails for a dropped
+   J_ab term, a wrong sign, a wrong root probability or a wrong slot weight;
+ - K = 1 reduces to the two-node heat-bath chain (Sec. III.A, Eq. eq_node_two_conf);
+ - beta = 0 has closed-form slot probabilities of the uniform-root star
+   (App. B.2);
+ - a star always rooted at the current state is NOT reversible (negative
+   control: the detailed-balance test has teeth);
+ - long runs reproduce the exact Boltzmann histogram and energy.
+"""
+import ctypes
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2102_05613_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_kat():
+    rows = []
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            v = [int(x, 16) for x in line.split()]
+            rows.append((v[:4], v[4:6], v[6:10]))
+    return rows
+
+
+def test_philox_known_answers():
+    rows = _read_kat()
+    assert len(rows) == 3
+    for ctr, key, want in rows:
+        assert list(oracle.philox(ctr, key)) == want
+
+
+def test_philox_matches_curand_host_generator():
+    path = "/usr/local/cuda/lib64/libcurand.so"
+    if not os.path.exists(path):
+        pytest.skip("libcurand not present")
+    cr = ctypes.CDLL(path)
+    gen = ctypes.c_void_p()
+    assert cr.curandCreateGeneratorHost(ctypes.byref(gen), 161) == 0  # PHILOX4_32_10
+    seed = 0x0123456789ABCDEF
+    assert cr.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(seed)) == 0
+    n = 4 * 64
+    out = np.zeros(n, dtype=np.uint32)
+    assert cr.curandGenerate(gen, out.ctypes.data_as(ctypes.c_void_p), ctypes.c_size_t(n)) == 0
+    cr.curandDestroyGenerator(gen)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    # cuRAND's host Philox emits block i from counter (0, 0, i, 0)
+    for i in range(n // 4):
+        assert list(oracle.philox([0, 0, i, 0], key)) == list(out[4 * i:4 * i + 4])
+
+
+def _pm1(N, seed):
+    return inputs.couplings_pm1(N, seed)
+
+
+def _gauss(N, seed):
+    return inputs.couplings_gauss(N, seed)
+
+
+def test_energy_definition_and_fields():
+    # E = -sum_{i<j} J s s; E = -1/2 sum s h; single and double flip differences
+    rng = np.random.default_rng(3)
+    for J in (_pm1(9, 1), _gauss(9, 2)):
+        s = inputs.initial_spins(1, 9, 5)[0]
+        E = oracle.energy(J, s)
+        Jd = J.astype(np.float64)
+        want = -sum(Jd[i, j] * s[i] * s[j] for i in range(9) for j in range(i + 1, 9))
+        assert abs(E - want) < 1e-12
+        h = oracle.fields(J, s)
+        assert np.allclose(h, Jd @ s.astype(np.float64), atol=1e-12)
+        assert abs(E - (-0.5 * float(s @ h))) < 1e-12
+        for _ in range(20):
+            a, b = rng.choice(9, 2, replace=False)
+            t = s.copy(); t[a] = -t[a]
+            assert abs(oracle.energy(J, t) - E - 2 * s[a] * h[a]) < 1e-12
+            t[b] = -t[b]
+            d2 = 2 * s[a] * h[a] + 2 * s[b] * h[b] - 4 * Jd[a, b] * s[a] * s[b]
+            assert abs(oracle.energy(J, t) - E - d2) < 1e-12
+        assert abs(oracle.energy(J, s, scale=0.25) - 0.25 * E) < 1e-12
+
+
+def _check_balance(P, pi, tol):
+    assert np.allclose(P.sum(axis=1), 1.0, atol=1e-12)
+    assert (P >= -1e-15).all()
+    stat = np.abs(pi @ P - pi).max()
+    flow = pi[:, None] * P
+    db = np.abs(flow - flow.T).max()
+    return stat, db
+
+
+@pytest.mark.parametrize("kind", ["pm1", "gauss"])
+@pytest.mark.parametrize("K", [1, 2, 3, 4])
+def test_star_detailed_balance(kind, K):
+    N = 6 if K <= 3 else 5
+    J = _pm1(N, 11) if kind == "pm1" else _gauss(N, 12)
+    beta = 0.7 if kind == "gauss" else 0.3
+    pi = oracle.boltzmann(J, beta)
+    P = oracle.transition_matrix(J, K=K, beta=beta)
+    stat, db = _check_balance(P, pi, 1e-12)
+    assert stat < 1e-13 and db < 1e-14, (stat, db)
+
+
+def test_star_detailed_balance_integer_tables():
+    # the +-J trajectories use integer weights: reversible to within table rounding
+    J = _pm1(6, 21)
+    for beta in (0.2, 1.0, 3.0):
+        pi = oracle.boltzmann(J, beta)
+        P = oracle.transition_matrix(J, K=3, beta=beta, weight_mode=1)
+        stat, db = _check_balance(P, pi, 1e-12)
+        assert stat < 1e-12 and db < 1e-12, (beta, stat, db)
+
+
+def test_metropolis_detailed_balance_and_closed_form():
+    J = _gauss(6, 31)
+    beta = 1.3
+    pi = oracle.boltzmann(J, beta)
+    P = oracle.transition_matrix(J, rule=oracle.METROPOLIS, beta=beta)
+    stat, db = _check_balance(P, pi, 1e-12)
+    assert stat < 1e-13 and db < 1e-14
+    # min(1, P_eq(c1)/P_eq(c0)) / N for each single flip (Sec. II)
+    s = np.ones(6, dtype=np.int8)
+    E0 = oracle.energy(J, s)
+    for i in range(6):
+        t = s.copy(); t[i] = -1
+        want = min(1.0, math.exp(-beta * (oracle.energy(J, t) - E0))) / 6
+        assert abs(P[0, 1 << i] - want) < 1e-14
+    Jp = _pm1(6, 32)
+    pi = oracle.boltzmann(Jp, 0.8)
+    P = oracle.transition_matrix(Jp, rule=oracle.METROPOLIS, beta=0.8, weight_mode=1)
+    stat, db = _check_balance(P, pi, 1e-12)
+    assert stat < 1e-12 and db < 1e-12
+
+
+def test_k1_is_two_node_heat_bath():
+    # Sec. III.A: the two-node graph with P_node ~ P_eq is heat-bath:
+    # P(c -> c^(i)) = (1/N) / (1 + exp(beta dE_i)) for every state and site.
+    N, beta = 6, 0.9
+    for J in (_gauss(N, 41), _pm1(N, 42)):
+        P = oracle.transition_matrix(J, K=1, beta=beta)
+        for x in range(1 << N):
+            s = np.array([(-1 if (x >> i) & 1 else 1) for i in range(N)], dtype=np.int8)
+            E0 = oracle.energy(J, s)
+            for i in range(N):
+                t = s.copy(); t[i] = -t[i]
+                dE = oracle.energy(J, t) - E0
+                assert abs(P[x, x ^ (1 << i)] - (1.0 / N) / (1.0 + math.exp(beta * dE))) < 1e-14
+
+
+@pytest.mark.parametrize("K", [1, 2, 4])
+def test_beta_zero_closed_form(K):
+    # beta = 0: every slot equally likely.  Root = centre w.p. 1/(K+1), else a leaf.
+    N = 5
+    P = oracle.transition_matrix(_gauss(N, 51), K=K, beta=0.0)
+    pc, pl = 1.0 / (K + 1), K / (K + 1)
+    single = pc * (K / (K + 1)) / N + pl * (1.0 / (K + 1)) / N
+    double = pl * ((K - 1) / (K + 1)) * 2.0 / N**2
+    stay = pc / (K + 1) + pl * (1.0 / (K + 1) + ((K - 1) / (K + 1)) / N)
+    for x in range(1 << N):
+        assert abs(P[x, x] - stay) < 1e-14
+        for i in range(N):
+            assert abs(P[x, x ^ (1 << i)] - single) < 1e-14
+            for j in range(i + 1, N):
+                assert abs(P[x, x ^ (1 << i) ^ (1 << j)] - double) < 1e-14
+
+
+def test_centre_rooted_star_is_not_reversible():
+    # negative control: heat-bath over the K+1 nodes of a star always rooted at
+    # the current state violates detailed balance for K >= 2 (App. B.2 needs p_r)
+    J = _gauss(5, 61)
+    beta = 0.7
+    pi = oracle.boltzmann(J, beta)
+    P = oracle.transition_matrix(J, K=3, beta=beta, root_mode=1)
+    stat, db = _check_balance(P, pi, 1e-12)
+    assert stat > 1e-4 and db > 1e-4
+    # ... while K = 1 is the heat-bath chain either way
+    P1 = oracle.transition_matrix(J, K=1, beta=beta, root_mode=1)
+    stat, db = _check_balance(P1, pi, 1e-12)
+    assert stat < 1e-13 and db < 1e-14
+
+
+def test_weight_table_shape():
+    W = oracle.weight_table(1.0, 400)
+    assert int(W[0]) == 1 << 52
+    assert all(int(W[d]) >= int(W[d + 1]) for d in range(len(W) - 1))
+    # the first dropped entry is the first that rounds to zero
+    assert 2.0 ** 52 * math.exp(-2.0 * len(W)) < 0.5
+    W0 = oracle.weight_table(0.0, 40)
+    assert len(W0) == 41 and all(int(w) == 1 << 52 for w in W0)
+
+
+def _chi2_pvalue(obs, exp_counts):
+    from scipy.stats import chi2
+    m = exp_counts > 5
+    x = ((obs[m] - exp_counts[m]) ** 2 / exp_counts[m]).sum()
+    rest_o, rest_e = obs[~m].sum(), exp_counts[~m].sum()
+    dof = int(m.sum()) - 1
+    if rest_e > 0:
+        x += (rest_o - rest_e) ** 2 / max(rest_e, 1e-9)
+        dof += 1
+    return chi2.sf(x, dof)
+
+
+def test_one_step_sampler_matches_exact_row():
+    # the Philox-driven step (draws, root, sites, integer selection) samples the
+    # enumerated transition row: many chains, one step each, from a fixed state
+    N, K, beta = 5, 3, 0.6
+    J = _pm1(N, 71)
+    P = oracle.transition_matrix(J, K=K, beta=beta, weight_mode=1)
+    x0 = 0b01101
+    s0 = np.array([(-1 if (x0 >> i) & 1 else 1) for i in range(N)], dtype=np.int8)
+    C = 40000
+    r = oracle.run(J, K=K, beta=beta, seed=7, chains=C, init=np.tile(s0, (C, 1)), steps=1)
+    ys = ((r["spins"] < 0).astype(np.int64) << np.arange(N)).sum(axis=1)
+    counts = np.bincount(ys, minlength=1 << N).astype(float)
+    assert _chi2_pvalue(counts, P[x0] * C) > 1e-3
+
+
+def test_long_run_histogram_matches_boltzmann_n12():
+    # config-1 companion: +-J N = 12, beta = 1, K = 8, histogram over states
+    N, K, beta = 12, 8, 1.0
+    J = _pm1(N, 0)
+    pi = oracle.boltzmann(J, beta)
+    # many independent chains, the final state of each after 300 steps
+    C = 20000
+    r = oracle.run(J, K=K, beta=beta, seed=2, chains=C, steps=300)
+    ys = ((r["spins"] < 0).astype(np.int64) << np.arange(N)).sum(axis=1)
+    counts = np.bincount(ys, minlength=1 << N).astype(float)
+    # compare the energy-level histogram (coarse-grained by exact energy)
+    Es = np.array([oracle.energy(J, np.array([(-1 if (x >> i) & 1 else 1) for i in range(N)],
+                                                dtype=np.int8)) for x in range(1 << N)])
+    levels = np.unique(Es)
+    obs = np.array([counts[Es == e].sum() for e in levels])
+    exp_ = np.array([pi[Es == e].sum() for e in levels]) * C
+    assert _chi2_pvalue(obs, exp_) > 1e-3
+    mean_E = float((counts * Es).sum() / C)
+    exact = float((pi * Es).sum())
+    sd = math.sqrt(float((pi * (Es - exact) ** 2).sum()) / C)
+    assert abs(mean_E - exact) < 4 * sd
+
+
+def test_metropolis_long_run_energy_matches_exact():
+    N, beta = 10, 0.8
+    J = _gauss(N, 81)
+    pi = oracle.boltzmann(J, beta)
+    Es = np.array([oracle.energy(J, np.array([(-1 if (x >> i) & 1 else 1) for i in range(N)],
+                                                dtype=np.int8)) for x in range(1 << N)])
+    C = 8000
+    r = oracle.run(J, rule=oracle.METROPOLIS, beta=beta, seed=3, chains=C, steps=600)
+    exact = float((pi * Es).sum())
+    sd = math.sqrt(float((pi * (Es - exact) ** 2).sum()) / C)
+    assert abs(r["final_E"].mean() - exact) < 4 * sd
+
+
+def test_fields_stay_consistent_over_a_run():
+    # maintained fields == recomputed fields: exact for +-J, 1e-9 for Gaussian
+    for J in (_pm1(40, 91), _gauss(40, 92)):
+        oracle.run(J, K=16, beta=1.0, seed=5, chains=2, steps=3000, resync_every=7)
+        oracle.run(J, rule=oracle.METROPOLIS, beta=1.0, seed=5, chains=2, steps=3000,
+                   resync_every=7)
+
+
+def test_records_consistent_with_final_state():
+    J = _pm1(32, 101)
+    r = oracle.run(J, K=8, beta=0.5, seed=9, chains=4, steps=500, record_every=100)
+    assert r["E"].shape == (5, 4)
+    assert np.array_equal(r["E"][-1], r["final_E"])
+    for c in range(4):
+        assert r["E"][-1, c] == oracle.energy(J, r["spins"][c])
+    q = (r["spins"][0].astype(float) @ r["spins"][1]) / 32
+    assert r["q"][-1, 0] == q
+    assert (r["acc"] <= 100).all()
+
+
+def test_random_start_is_philox_domain_one():
+    s = oracle.init_spins(seed=77, stream=3, chain=5, N=300)
+    key = [77, 0]
+    bits = []
+    for b in range(3):
+        w = oracle.philox([b, 0, 5, (1 << 24) | 3], key)
+        for k in range(128):
+            bits.append((int(w[k // 32]) >> (k % 32)) & 1)
+    want = np.array([-1 if x else 1 for x in bits[:300]], dtype=np.int8)
+    assert np.array_equal(s, want)
+    # balanced start
+    s = oracle.init_spins(seed=1, stream=0, chain=0, N=100000)
+    assert abs(int(s.astype(np.int64).sum())) < 5 * math.sqrt(100000)
+
+
+def test_high_temperature_energy_gaussian():
+    # textbook high-temperature (annealed) SK result, leading order in beta:
+    # <E> ~ -beta sum_{i<j} J_ij^2 (Sherrington & Kirkpatrick 1975); loose check
+    N, beta = 128, 0.3
+    J = _gauss(N, 111)
+    want = -beta * float(np.triu(J.astype(np.float64) ** 2, 1).sum())
+    r = oracle.run(J, rule=oracle.METROPOLIS, beta=beta, seed=4, chains=32, steps=40000,
+                   record_every=1000)
+    got = r["E"][10:].mean()
+    assert abs(got - want) < 0.08 * abs(want), (got, want)
