@@ -1,0 +1,330 @@
+#!/usr/bin/env python3
+"""Benchmark of the MCMCMC step on one GB300.
+
+Workload (default): Gaussian SK spin glass, N = 512, J_ij ~ N(0, 1/N) fp32,
+64 disorder instances x 4096 independent chains (262,144 chains), K = 128
+single-flip proposals per step, beta = 1 (T = T_c), observables recorded
+every 100 steps.  One bench step = 100 Monte Carlo steps of every chain,
+one persistent kernel launch over all instances.  The chains' state (spins +
+fields, 671 MB) is larger than L2 and is streamed through on every launch.
+
+Metric: candidate configurations per second (chains x K x MC steps / s);
+MC steps per second (chain-steps / s) is reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs the same workload with its own seeds (weak
+scaling, no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N, INSTANCES, CHAINS, K, BETA, R = 512, 64, 4096, 128, 1.0, 100
+WORKLOAD = (f"gaussian-sk N={N} J~N(0,1/N) fp32, {INSTANCES} instances x {CHAINS} chains, "
+            f"MCMCMC K={K}, beta={BETA}, record every {R} steps; one bench step = {R} MC steps "
+            f"of all chains in one persistent launch")
+METRIC = "SK candidate configs/s (MCMCMC K=128, Gaussian N=512, 64x4096 chains)"
+UNIT = "candidate configs/s"
+
+
+def _env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.proc = None
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(gpu_index), "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    smax.append(float(p[2]))
+                except ValueError:
+                    continue
+                for n_, v in zip(names, p[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n_)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timings (cpu_baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+def _oracle_sample(couplings, chains_per_instance, steps, threads):
+    """Runs the FP64 oracle on `chains_per_instance` chains of every instance
+    for `steps` steps (records every R), on `threads` host threads."""
+    import concurrent.futures as cf
+
+    import oracle
+    jobs = []
+    for i, J in enumerate(couplings):
+        for c0 in range(0, chains_per_instance, 16):
+            jobs.append((i, J, c0, min(16, chains_per_instance - c0)))
+
+    def one(job):
+        i, J, c0, n = job
+        oracle.run(J, K=K, beta=BETA, seed=1, stream=i, chain0=c0, chains=n, steps=steps,
+                   record_every=R)
+
+    oracle.lib()
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(one, jobs))
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(couplings):
+    cores = _cores()
+    per_inst = 128
+    steps = R
+    dt = _oracle_sample(couplings, per_inst, steps, cores)
+    units = INSTANCES * per_inst * steps * K
+    return {"value": units / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{per_inst} chains of each of the {INSTANCES} instances x {steps} steps "
+                      f"(records included), FP64 C oracle, {cores} threads, {dt:.2f} s wall"}
+
+
+def run_reference(args):
+    rank, world, _ = _env()
+    if rank != 0:
+        return 0
+    from paper_2102_05613_gb300 import inputs
+    couplings = [inputs.couplings_gauss(N, i) for i in range(INSTANCES)]
+    cores = _cores()
+    per_inst = 32
+    for _ in range(args.warmup):
+        _oracle_sample(couplings, per_inst, R, cores)
+    times = [_oracle_sample(couplings, per_inst, R, cores) for _ in range(args.steps)]
+    T = sum(times)
+    units = INSTANCES * per_inst * R * K * args.steps
+    value = units / T
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "reference_sample":
+                                            f"{per_inst} chains per instance per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_inst} chains of each of the {INSTANCES} instances x "
+                                       f"{R} steps per bench step, {cores} threads"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+    rank, world, local = _env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2102_05613_gb300 import inputs, sk
+    stream = torch.cuda.current_stream()
+    seed_base = 1000 * rank
+    couplings = [inputs.couplings_gauss(N, seed_base + i) for i in range(INSTANCES)]
+    cap = args.warmup + args.steps + args.e2e_steps + 2
+    insts = [sk.Instance(J, stream=stream) for J in couplings]
+    runs = [sk.Run(inst, chains=CHAINS, K=K, beta=BETA, seed=1 + rank, stream_id=i,
+                   record_every=R, max_records=cap) for i, inst in enumerate(insts)]
+    batch = sk.Batch(runs)
+    info = batch.info()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        batch.advance(R)
+    barrier()
+    c0 = [r.counters() for r in runs]
+    clocks = Clocks(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier()
+    for s, e in ev:
+        s.record(stream)
+        batch.advance(R)
+        e.record(stream)
+    barrier()
+    clk = clocks.stop()
+    for r in runs:
+        r.wait()
+    c1 = [r.counters() for r in runs]
+    total_ms = ev[0][0].elapsed_time(ev[-1][1])
+    launch_ms = [s.elapsed_time(e) for s, e in ev]
+    t_local = total_ms / 1e3
+    t = torch.tensor([t_local], device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    T = float(t.item())
+    chain_steps_rank = INSTANCES * CHAINS * R * args.steps
+    value = world * chain_steps_rank * K / T
+    mc_steps = world * chain_steps_rank / T
+
+    # algorithmic bytes of one launch: J rows the steps needed (N x 4 B each),
+    # the s/h gathers of the K candidates (1 + 4 B each), the field updates
+    # (read + write 4 B per spin per flipped spin) and the state streamed in
+    # and out once per launch (5 B per spin each way)
+    flips = sum(b[0] - a[0] for a, b in zip(c0, c1))
+    rows = sum(b[1] - a[1] for a, b in zip(c0, c1))
+    cs = INSTANCES * CHAINS * R * args.steps
+    rows_ps, flips_ps = rows / cs, flips / cs
+    bytes_ps = rows_ps * N * 4 + K * 5 + flips_ps * N * 8
+    state_bytes = INSTANCES * CHAINS * N * 5 * 2
+    alg_bytes_launch = bytes_ps * INSTANCES * CHAINS * R + state_bytes
+    mean_launch_s = statistics.mean(launch_ms) / 1e3
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    hbm_peak = peaks.get("hbm_gbs")
+    peak_src = "measured"
+    if hbm_peak is None:
+        hbm_peak, peak_src = 6800.0, "fallback"
+    achieved = alg_bytes_launch / mean_launch_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
+                "kernel": "step_kernel",
+                "bytes_per_chain_step": bytes_ps, "J_rows_per_chain_step": rows_ps,
+                "flips_per_chain_step": flips_ps}
+
+    # end to end through the C ABI from pinned host buffers: upload the 64
+    # coupling matrices and the 262,144 start configurations, run 100 steps,
+    # read the step's records back
+    e2e = None
+    if args.e2e_steps > 0:
+        hJ = [torch.from_numpy(J).pin_memory() for J in couplings]
+        hS = [torch.from_numpy(inputs.initial_spins(CHAINS, N, seed_base + 77 + i)).pin_memory()
+              for i in range(INSTANCES)]
+        hE = [torch.empty((1, CHAINS), dtype=torch.float64).pin_memory() for _ in runs]
+        hQ = [torch.empty((1, CHAINS // 2), dtype=torch.float64).pin_memory() for _ in runs]
+        hA = [torch.empty((1, CHAINS), dtype=torch.int32).pin_memory() for _ in runs]
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            for inst, J in zip(insts, hJ):
+                inst.set_couplings(J)
+            for r, S in zip(runs, hS):
+                r.reset(S)
+            batch.advance(R)
+            for r, e_, q_, a_ in zip(runs, hE, hQ, hA):
+                r.observables(0, 1, out=(e_, q_, a_))
+        barrier()
+        te = time.perf_counter() - t0
+        tt = torch.tensor([te], device="cuda")
+        if dist is not None:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        te = float(tt.item())
+        h2d = sum(x.numel() * x.element_size() for x in hJ + hS)
+        d2h = sum(x.numel() * x.element_size() for x in hE + hQ + hA)
+        e2e = {"value": world * INSTANCES * CHAINS * R * K * args.e2e_steps / te, "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "steps": args.e2e_steps, "ms_per_step": 1e3 * te / args.e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(couplings)
+
+    for r in runs:
+        r.close()
+    batch.close()
+    for i in insts:
+        i.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "N": N, "instances": INSTANCES, "chains": CHAINS,
+                           "K": K, "beta": BETA, "mc_steps_per_bench_step": R,
+                           "l2": "state (671 MB) larger than L2, streamed every launch",
+                           "launch": info},
+                "mc_steps_per_s": mc_steps,
+                "gpu_launches": 2 * args.steps,
+                "roofline": roofline, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,215 @@
+/*
+ * sk_mcmcmc.h -- C ABI of the GB300 (sm_103a) Many-Configuration Markov-Chain
+ * Monte Carlo sampler for the Sherrington-Kirkpatrick spin glass
+ * (Simkovic & Rossi, arXiv:2102.05613).
+ *
+ * The problem (Sec. II): draw samples of P_eq(c) = exp(-beta E(c)) / Z over
+ * spin configurations c = (s_1..s_N), s_i = +-1, visiting K+1 configurations
+ * per Monte Carlo step.  The energy is the SK energy of Sec. IV.A written as
+ *     E(s) = -scale * sum_{i<j} J_ij s_i s_j
+ * with J symmetric, zero diagonal, J_ij ~ N(0, 1/N) (Gaussian) or +-1 (+-J).
+ *
+ * Each step of the many-configuration rule (Sec. A.2, Eq.
+ * eq_det_balance_graph_solution, on the star graph of App. B.2 with a uniform
+ * root) proposes K configurations from the current one by single spin flips,
+ * picks the next state among the K+1 nodes with probability proportional to
+ * exp(-beta E), and updates the maintained local fields h_i = sum_j J_ij s_j.
+ * SK_RULE_METROPOLIS is the single-flip Metropolis comparator of Sec. IV.B.
+ *
+ * Conventions for every call:
+ *  - the return value is an sk_status; on error nothing is written to the
+ *    caller's outputs and sk_last_error() describes the failure (per thread);
+ *  - buffers marked "mem" are host pointers when mem == SK_MEM_HOST and
+ *    device pointers (of the current device) when mem == SK_MEM_DEVICE; input
+ *    buffers are copied before the call returns (device inputs: enqueued on
+ *    the object's stream), so the caller keeps ownership and may reuse them
+ *    once the call (host) or the stream (device) has moved on;
+ *  - objects (sk_instance, sk_run, sk_batch) are owned by the library and
+ *    released by their *_destroy / *_free call;
+ *  - work is enqueued on the CUDA stream given at creation (NULL = the legacy
+ *    default stream); calls that return data to the host synchronise it.
+ *  - there is no CPU fallback: without a usable sm_103a device every call
+ *    that needs one returns SK_ERR_CUDA.
+ *
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11), counter
+ * (block, step, chain, domain<<24 | stream_id), key = seed.  A chain's
+ * trajectory depends only on (seed, stream_id, chain index, couplings, K,
+ * beta, rule, start), never on how chains are batched or launched.
+ */
+#ifndef SK_MCMCMC_H
+#define SK_MCMCMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SK_OK = 0,
+    SK_ERR_INVALID_ARG = 1, /* an argument is out of range or inconsistent     */
+    SK_ERR_OOM = 2,         /* a device or host allocation failed              */
+    SK_ERR_CUDA = 3,        /* a CUDA runtime call failed (no device, ...)     */
+    SK_ERR_TIMEOUT = 4,     /* a bounded device wait expired; state is invalid */
+    SK_ERR_NOT_READY = 5,   /* work still in flight (non-blocking query)       */
+    SK_ERR_DEVICE = 6       /* a kernel reported an inconsistency (bounds)     */
+} sk_status;
+
+typedef enum { SK_J_PM1 = 0, SK_J_GAUSS = 1 } sk_jkind;      /* int8 +-1 / float32 */
+typedef enum { SK_RULE_MCMCMC = 0, SK_RULE_METROPOLIS = 1 } sk_rule;
+typedef enum { SK_MEM_HOST = 0, SK_MEM_DEVICE = 1 } sk_mem;
+
+#define SK_MAX_K 256u        /* proposals per step                         */
+#define SK_MAX_N 8192u       /* spins per configuration                    */
+
+typedef struct sk_instance sk_instance;  /* couplings resident on the device */
+typedef struct sk_run sk_run;            /* chains of one instance            */
+typedef struct sk_batch sk_batch;        /* runs advanced by one launch       */
+
+/* ---------------------------------------------------------------------- */
+/* Instances (Sec. IV.A: one disorder realisation {J_ij})                  */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * sk_create_instance: uploads an N x N coupling matrix.
+ *   N          2 .. SK_MAX_N spins.
+ *   kind       SK_J_PM1: couplings are int8 with values in {-1, 0, +1};
+ *              SK_J_GAUSS: couplings are float32.
+ *   couplings  N*N row-major, symmetric, zero diagonal (checked for host
+ *              input: SK_ERR_INVALID_ARG otherwise); mem says where it lives.
+ *   scale      energy multiplier (> 0): E = -scale sum_{i<j} J s s.  1.0 for
+ *              the +-J model with integer energies; 1/sqrt(N) gives the +-J
+ *              model on the paper's Gaussian temperature scale.
+ *   stream     cudaStream_t (as void*) for this instance's copies, or NULL.
+ * The device copy is padded to Npad = ceil(N/32)*32 rows and columns.
+ */
+sk_status sk_create_instance(uint32_t N, uint32_t kind, const void* couplings, uint32_t mem,
+                             double scale, void* stream, sk_instance** out);
+
+/* Replaces the couplings of an existing instance (same N and kind); used to
+ * re-upload a disorder realisation without reallocating. */
+sk_status sk_set_couplings(sk_instance* inst, const void* couplings, uint32_t mem);
+
+sk_status sk_destroy_instance(sk_instance* inst);
+
+/*
+ * sk_energy: E(s) = -scale sum_{i<j} J_ij s_i s_j for `count` configurations
+ * (Sec. IV.A), computed on the device in double precision (exact for +-J).
+ *   spins  count*N int8 values +-1, row-major (mem: SK_MEM_HOST/DEVICE);
+ *   out_E  count doubles, always a host pointer.
+ */
+sk_status sk_energy(const sk_instance* inst, const int8_t* spins, uint32_t count, uint32_t mem,
+                    double* out_E);
+
+/* ---------------------------------------------------------------------- */
+/* Runs: `chains` independent Markov chains on one instance                */
+/* ---------------------------------------------------------------------- */
+typedef struct {
+    uint32_t chains;        /* >= 1; pairs (2m, 2m+1) give the overlap q        */
+    uint32_t K;             /* proposals per step, 1..SK_MAX_K (MCMCMC only)    */
+    uint32_t rule;          /* sk_rule                                          */
+    uint32_t record_every;  /* record observables after every R-th step; 0=off  */
+    uint64_t max_records;   /* record capacity (records past it are dropped)    */
+    double beta;            /* inverse temperature, >= 0                        */
+    uint64_t seed;          /* Philox key                                       */
+    uint32_t stream_id;     /* Philox stream (24 bits), e.g. the instance index */
+    uint32_t trace_chains;  /* chains 0..trace_chains-1 log the slot chosen at  */
+    uint64_t trace_steps;   /*   each of their first trace_steps steps (debug)  */
+    const int8_t* init_spins; /* chains*N start (+-1), or NULL: Philox start   */
+    uint32_t init_mem;      /* sk_mem of init_spins                             */
+} sk_run_params;
+
+/*
+ * mcmcmc_create: allocates the chains' state (spins, local fields, records)
+ * and initialises it: spins from init_spins or from Philox domain 1, fields
+ * h = J s.  The run is at step 0.  Asynchronous on the instance's stream.
+ */
+sk_status mcmcmc_create(sk_instance* inst, const sk_run_params* p, sk_run** out);
+
+/*
+ * mcmcmc_advance: enqueues `steps` Monte Carlo steps of every chain of the
+ * run (one persistent kernel launch).  Records fall at global steps t with
+ * (t+1) % record_every == 0, record index (t+1)/record_every - 1.
+ * Step counts are limited to 2^32 in total per run.
+ */
+sk_status mcmcmc_advance(sk_run* run, uint64_t steps);
+
+/* mcmcmc_run: mcmcmc_create followed by mcmcmc_advance(steps). */
+sk_status mcmcmc_run(sk_instance* inst, const sk_run_params* p, uint64_t steps, sk_run** out);
+
+/*
+ * mcmcmc_reset: restarts the run at step 0 from new spins (chains*N, mem) or
+ * from the Philox start when spins == NULL; fields are recomputed, records
+ * and acceptance counters cleared.  Reuses the run's device memory.
+ */
+sk_status mcmcmc_reset(sk_run* run, const int8_t* spins, uint32_t mem);
+
+/*
+ * mcmcmc_wait: blocks until the run's stream is idle, at most timeout_ns
+ * nanoseconds (0 = no limit): SK_ERR_TIMEOUT if work is still in flight then.
+ * Reports SK_ERR_TIMEOUT / SK_ERR_DEVICE raised by a kernel of the run.
+ */
+sk_status mcmcmc_wait(sk_run* run, uint64_t timeout_ns);
+
+/*
+ * mcmcmc_observables: copies records [first, first+count) (synchronises):
+ *   energy[r*chains + c]       E of chain c (scale included), double;
+ *   overlap[r*(chains/2) + m]  q = (1/N) sum_i s_i s'_i of chains 2m, 2m+1;
+ *   accepted[r*chains + c]     steps of the interval whose configuration
+ *                              changed (uint32).
+ * Any output may be NULL.  mem says where the outputs live.
+ */
+sk_status mcmcmc_observables(sk_run* run, uint64_t first, uint64_t count, double* energy,
+                             double* overlap, uint32_t* accepted, uint32_t mem);
+
+/*
+ * mcmcmc_state: copies the current spins (chains*N int8) and, if non-NULL,
+ * the maintained fields (chains*N, int32 for +-J, float32 for Gaussian) and
+ * the step counter (synchronises; spins/fields per mem, step a host pointer).
+ */
+sk_status mcmcmc_state(sk_run* run, int8_t* spins, void* fields, uint64_t* step, uint32_t mem);
+
+/* mcmcmc_trace: copies the slot log (trace_chains*trace_steps int32; slot
+ * 0..K for MCMCMC, 1/0 accepted/rejected for Metropolis). */
+sk_status mcmcmc_trace(sk_run* run, int32_t* slots, uint32_t mem);
+
+/*
+ * mcmcmc_counters: work done since the run's last reset, summed over its
+ * chains (synchronises): spins flipped, and rows of J the steps needed (row a
+ * of every leaf-rooted step, for the J_ab terms, plus the row of every other
+ * flipped spin).  Both host pointers, either may be NULL.
+ */
+sk_status mcmcmc_counters(sk_run* run, uint64_t* flips, uint64_t* rows);
+
+sk_status mcmcmc_free(sk_run* run);
+
+/* ---------------------------------------------------------------------- */
+/* Batches: many runs (instances, N, K, beta, rule may differ) advanced by */
+/* one persistent launch; the runs must share one CUDA stream.            */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * mcmcmc_batch_create: plans work items (blocks of chains of one run) for
+ * the runs.  warps_per_cta 0 lets the library choose; otherwise 2..32 even.
+ */
+sk_status mcmcmc_batch_create(sk_run* const* runs, uint32_t n_runs, uint32_t warps_per_cta,
+                              sk_batch** out);
+
+/* Advances every run of the batch by `steps` steps in one kernel launch. */
+sk_status mcmcmc_batch_advance(sk_batch* b, uint64_t steps);
+
+/* Launch geometry chosen for the batch (for reports): CTAs, warps per CTA,
+ * dynamic shared memory bytes per CTA, work items. */
+sk_status mcmcmc_batch_info(const sk_batch* b, uint32_t* grid, uint32_t* warps_per_cta,
+                            uint32_t* smem_bytes, uint32_t* items);
+
+sk_status mcmcmc_batch_free(sk_batch* b);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* sk_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SK_MCMCMC_H */

@@ -1,0 +1,627 @@
+// sk_capi.cu -- host runtime behind the C ABI of include/sk_mcmcmc.h:
+// coupling store, run state and records, +-J weight tables, work-item
+// planning for batched persistent launches, bounded waits and errors.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "sk_internal.h"
+#include "sk_mcmcmc.h"
+
+using sk::JobDev;
+using sk::WorkItem;
+
+namespace {
+
+thread_local std::string g_err;
+
+sk_status fail(sk_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define SK_CU(call)                                                                        \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(SK_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));     \
+    } while (0)
+
+uint32_t pad_n(uint32_t n) { return (n + sk::kPadTo - 1) / sk::kPadTo * sk::kPadTo; }
+size_t jbytes(uint32_t kind) { return kind == SK_J_PM1 ? 1 : 4; }
+
+// The device the library runs on must be an sm_103 part (the only target
+// the kernels are built for).
+sk_status check_device() {
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n == 0)
+        return fail(SK_ERR_CUDA, "no CUDA device available (%s)", cudaGetErrorString(e));
+    int dev = 0, major = 0, minor = 0;
+    SK_CU(cudaGetDevice(&dev));
+    SK_CU(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev));
+    SK_CU(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev));
+    if (major != 10 || minor != 3)
+        return fail(SK_ERR_CUDA, "device compute capability %d.%d: this library is built for sm_103a only",
+                    major, minor);
+    return SK_OK;
+}
+
+template <typename T>
+sk_status dalloc(T** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) return SK_OK;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SK_ERR_OOM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    return SK_OK;
+}
+
+// +-J weight tables (exact integer arithmetic on both the chain and its
+// checks): MCMCMC W[d] = round(2^52 exp(-2 beta_eff d)) for d = (dE - min)/2
+// until the first entry that rounds to zero; Metropolis M[k] =
+// round(2^53 exp(-2 beta_eff k)) for dE = 2k, k = 0..N.
+std::vector<uint64_t> mcmcmc_table(double beta_eff, uint32_t N) {
+    std::vector<uint64_t> w;
+    const uint32_t dmax = 4 * N + 4;
+    for (uint32_t d = 0; d <= dmax; ++d) {
+        const double v = std::nearbyint(std::ldexp(std::exp(-2.0 * beta_eff * d), 52));
+        if (!(v > 0.0)) break;
+        w.push_back(static_cast<uint64_t>(v));
+    }
+    return w;
+}
+std::vector<uint64_t> metropolis_table(double beta_eff, uint32_t N) {
+    std::vector<uint64_t> m(N + 1);
+    for (uint32_t k = 0; k <= N; ++k)
+        m[k] = static_cast<uint64_t>(std::nearbyint(std::ldexp(std::exp(-2.0 * beta_eff * k), 53)));
+    return m;
+}
+
+}  // namespace
+
+struct sk_instance {
+    uint32_t N = 0, Npad = 0, kind = 0;
+    double scale = 1.0;
+    void* dJ = nullptr;
+    cudaStream_t st = nullptr;
+};
+
+struct sk_batch {
+    std::vector<sk_run*> runs;
+    JobDev* djobs = nullptr;
+    WorkItem* ditems = nullptr;
+    uint32_t* dqueue = nullptr;
+    uint32_t n_items = 0, W = 0, per_warp = 0, grid = 0;
+    int nb = 1;
+    cudaStream_t st = nullptr;
+};
+
+struct sk_run {
+    sk_instance* inst = nullptr;
+    sk_run_params p{};
+    uint32_t chains = 0;
+    int8_t* ds = nullptr;
+    void* dh = nullptr;
+    uint32_t* dacc = nullptr;
+    unsigned long long* dwork = nullptr;
+    double* drecE = nullptr;
+    uint32_t* drecAcc = nullptr;
+    double* drecQ = nullptr;
+    int32_t* dtrace = nullptr;
+    uint64_t* dW = nullptr;
+    uint32_t wlen = 0;
+    uint64_t* dstep = nullptr;
+    int* derr = nullptr;
+    uint64_t step = 0;  // host mirror of the device step counter
+    JobDev job{};
+    sk_batch* self = nullptr;
+};
+
+namespace {
+
+sk_status validate_couplings(uint32_t N, uint32_t kind, const void* J) {
+    if (kind == SK_J_PM1) {
+        const int8_t* a = static_cast<const int8_t*>(J);
+        for (uint32_t i = 0; i < N; ++i) {
+            if (a[static_cast<size_t>(i) * N + i] != 0)
+                return fail(SK_ERR_INVALID_ARG, "J[%u][%u] != 0 (diagonal must be zero)", i, i);
+            for (uint32_t j = 0; j < N; ++j) {
+                const int8_t v = a[static_cast<size_t>(i) * N + j];
+                if (v < -1 || v > 1)
+                    return fail(SK_ERR_INVALID_ARG, "J[%u][%u] = %d is not in {-1,0,1}", i, j, v);
+                if (v != a[static_cast<size_t>(j) * N + i])
+                    return fail(SK_ERR_INVALID_ARG, "J is not symmetric at (%u,%u)", i, j);
+            }
+        }
+    } else {
+        const float* a = static_cast<const float*>(J);
+        for (uint32_t i = 0; i < N; ++i) {
+            if (a[static_cast<size_t>(i) * N + i] != 0.0f)
+                return fail(SK_ERR_INVALID_ARG, "J[%u][%u] != 0 (diagonal must be zero)", i, i);
+            for (uint32_t j = 0; j < N; ++j) {
+                const float v = a[static_cast<size_t>(i) * N + j];
+                if (!std::isfinite(v)) return fail(SK_ERR_INVALID_ARG, "J[%u][%u] is not finite", i, j);
+                if (v != a[static_cast<size_t>(j) * N + i])
+                    return fail(SK_ERR_INVALID_ARG, "J is not symmetric at (%u,%u)", i, j);
+            }
+        }
+    }
+    return SK_OK;
+}
+
+sk_status upload_couplings(sk_instance* in, const void* J, uint32_t mem) {
+    const size_t b = jbytes(in->kind);
+    if (mem == SK_MEM_HOST) {
+        sk_status s = validate_couplings(in->N, in->kind, J);
+        if (s != SK_OK) return s;
+    } else if (mem != SK_MEM_DEVICE) {
+        return fail(SK_ERR_INVALID_ARG, "mem must be SK_MEM_HOST or SK_MEM_DEVICE");
+    }
+    SK_CU(cudaMemsetAsync(in->dJ, 0, static_cast<size_t>(in->Npad) * in->Npad * b, in->st));
+    SK_CU(cudaMemcpy2DAsync(in->dJ, in->Npad * b, J, in->N * b, in->N * b, in->N, cudaMemcpyDefault,
+                            in->st));
+    if (mem == SK_MEM_HOST) SK_CU(cudaStreamSynchronize(in->st));
+    return SK_OK;
+}
+
+sk_status check_run_error(sk_run* r) {
+    int h = 0;
+    SK_CU(cudaMemcpyAsync(&h, r->derr, sizeof(int), cudaMemcpyDeviceToHost, r->inst->st));
+    SK_CU(cudaStreamSynchronize(r->inst->st));
+    if (h == sk::kDevTimeout) return fail(SK_ERR_TIMEOUT, "a bounded device wait expired in the step kernel");
+    if (h == sk::kDevBounds) return fail(SK_ERR_DEVICE, "a kernel reported an out-of-range index");
+    return SK_OK;
+}
+
+sk_status init_state(sk_run* r, const int8_t* spins, uint32_t mem) {
+    sk_instance* in = r->inst;
+    const int8_t* dinit = nullptr;
+    int8_t* tmp = nullptr;
+    if (spins) {
+        if (mem == SK_MEM_DEVICE) {
+            dinit = spins;
+        } else if (mem == SK_MEM_HOST) {
+            const size_t n = static_cast<size_t>(r->chains) * in->N;
+            for (size_t i = 0; i < n; ++i)
+                if (spins[i] != 1 && spins[i] != -1)
+                    return fail(SK_ERR_INVALID_ARG, "initial spin %zu is %d, not +-1", i, spins[i]);
+            sk_status s = dalloc(&tmp, n);
+            if (s != SK_OK) return s;
+            SK_CU(cudaMemcpyAsync(tmp, spins, n, cudaMemcpyHostToDevice, in->st));
+            dinit = tmp;
+        } else {
+            return fail(SK_ERR_INVALID_ARG, "init_mem must be SK_MEM_HOST or SK_MEM_DEVICE");
+        }
+    }
+    SK_CU(cudaMemsetAsync(r->dstep, 0, sizeof(uint64_t), in->st));
+    SK_CU(cudaMemsetAsync(r->derr, 0, sizeof(int), in->st));
+    const uint64_t R = r->p.max_records;
+    if (R && r->p.record_every) {
+        SK_CU(cudaMemsetAsync(r->drecE, 0, R * r->chains * sizeof(double), in->st));
+        SK_CU(cudaMemsetAsync(r->drecAcc, 0, R * r->chains * sizeof(uint32_t), in->st));
+        if (r->chains >= 2) SK_CU(cudaMemsetAsync(r->drecQ, 0, R * (r->chains / 2) * sizeof(double), in->st));
+    }
+    if (r->dtrace)
+        SK_CU(cudaMemsetAsync(r->dtrace, 0xff, static_cast<size_t>(r->p.trace_chains) * r->p.trace_steps * 4,
+                              in->st));
+    SK_CU(sk::launch_init(&r->job, dinit, r->chains, in->N, in->Npad, in->kind, in->st));
+    if (tmp) {
+        SK_CU(cudaStreamSynchronize(in->st));
+        cudaFree(tmp);
+    }
+    r->step = 0;
+    return SK_OK;
+}
+
+void free_run_buffers(sk_run* r) {
+    cudaFree(r->ds);
+    cudaFree(r->dh);
+    cudaFree(r->dacc);
+    cudaFree(r->dwork);
+    cudaFree(r->drecE);
+    cudaFree(r->drecAcc);
+    cudaFree(r->drecQ);
+    cudaFree(r->dtrace);
+    cudaFree(r->dW);
+    cudaFree(r->dstep);
+    cudaFree(r->derr);
+}
+
+constexpr size_t kSmemBudget = 232448 - 1024;  // dynamic smem per CTA, static part reserved
+
+}  // namespace
+
+extern "C" {
+
+const char* sk_last_error(void) { return g_err.c_str(); }
+
+sk_status sk_create_instance(uint32_t N, uint32_t kind, const void* couplings, uint32_t mem,
+                             double scale, void* stream, sk_instance** out) {
+    if (!out) return fail(SK_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (N < 2 || N > SK_MAX_N) return fail(SK_ERR_INVALID_ARG, "N = %u outside 2..%u", N, SK_MAX_N);
+    if (kind != SK_J_PM1 && kind != SK_J_GAUSS) return fail(SK_ERR_INVALID_ARG, "unknown coupling kind %u", kind);
+    if (!couplings) return fail(SK_ERR_INVALID_ARG, "couplings is NULL");
+    if (!(scale > 0.0) || !std::isfinite(scale)) return fail(SK_ERR_INVALID_ARG, "scale must be > 0");
+    sk_status s = check_device();
+    if (s != SK_OK) return s;
+    sk_instance* in = new sk_instance();
+    in->N = N;
+    in->Npad = pad_n(N);
+    in->kind = kind;
+    in->scale = scale;
+    in->st = static_cast<cudaStream_t>(stream);
+    s = dalloc(&in->dJ, static_cast<size_t>(in->Npad) * in->Npad * jbytes(kind));
+    if (s == SK_OK) s = upload_couplings(in, couplings, mem);
+    if (s != SK_OK) {
+        cudaFree(in->dJ);
+        delete in;
+        return s;
+    }
+    *out = in;
+    return SK_OK;
+}
+
+sk_status sk_set_couplings(sk_instance* in, const void* couplings, uint32_t mem) {
+    if (!in || !couplings) return fail(SK_ERR_INVALID_ARG, "NULL argument");
+    return upload_couplings(in, couplings, mem);
+}
+
+sk_status sk_destroy_instance(sk_instance* in) {
+    if (!in) return fail(SK_ERR_INVALID_ARG, "instance is NULL");
+    cudaStreamSynchronize(in->st);
+    cudaFree(in->dJ);
+    delete in;
+    return SK_OK;
+}
+
+sk_status sk_energy(const sk_instance* in, const int8_t* spins, uint32_t count, uint32_t mem,
+                    double* out_E) {
+    if (!in || !spins || !out_E) return fail(SK_ERR_INVALID_ARG, "NULL argument");
+    if (count == 0) return SK_OK;
+    const size_t n = static_cast<size_t>(count) * in->N;
+    int8_t* tmp = nullptr;
+    double* dE = nullptr;
+    const int8_t* dsp = spins;
+    sk_status s = SK_OK;
+    if (mem == SK_MEM_HOST) {
+        for (size_t i = 0; i < n; ++i)
+            if (spins[i] != 1 && spins[i] != -1) return fail(SK_ERR_INVALID_ARG, "spin %zu is not +-1", i);
+        if ((s = dalloc(&tmp, n)) != SK_OK) return s;
+        SK_CU(cudaMemcpyAsync(tmp, spins, n, cudaMemcpyHostToDevice, in->st));
+        dsp = tmp;
+    } else if (mem != SK_MEM_DEVICE) {
+        return fail(SK_ERR_INVALID_ARG, "mem must be SK_MEM_HOST or SK_MEM_DEVICE");
+    }
+    if ((s = dalloc(&dE, count * sizeof(double))) != SK_OK) {
+        cudaFree(tmp);
+        return s;
+    }
+    cudaError_t e = sk::launch_energy(in->dJ, in->kind, in->N, in->Npad, in->scale, dsp, count, dE, in->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out_E, dE, count * sizeof(double), cudaMemcpyDeviceToHost, in->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(in->st);
+    cudaFree(tmp);
+    cudaFree(dE);
+    if (e != cudaSuccess) return fail(SK_ERR_CUDA, "sk_energy: %s", cudaGetErrorString(e));
+    return SK_OK;
+}
+
+sk_status mcmcmc_create(sk_instance* in, const sk_run_params* p, sk_run** out) {
+    if (!in || !p || !out) return fail(SK_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (p->chains == 0 || p->chains > (1u << 30)) return fail(SK_ERR_INVALID_ARG, "chains = %u", p->chains);
+    if (p->rule != SK_RULE_MCMCMC && p->rule != SK_RULE_METROPOLIS)
+        return fail(SK_ERR_INVALID_ARG, "unknown rule %u", p->rule);
+    if (p->rule == SK_RULE_MCMCMC && (p->K < 1 || p->K > SK_MAX_K))
+        return fail(SK_ERR_INVALID_ARG, "K = %u outside 1..%u", p->K, SK_MAX_K);
+    if (!(p->beta >= 0.0) || !std::isfinite(p->beta)) return fail(SK_ERR_INVALID_ARG, "beta must be >= 0");
+    if (p->stream_id > 0xFFFFFFu) return fail(SK_ERR_INVALID_ARG, "stream_id must fit 24 bits");
+    if (p->trace_chains > p->chains) return fail(SK_ERR_INVALID_ARG, "trace_chains > chains");
+    sk_run* r = new sk_run();
+    r->inst = in;
+    r->p = *p;
+    r->chains = p->chains;
+    if (r->p.rule == SK_RULE_METROPOLIS) r->p.K = 1;
+    if (!r->p.record_every) r->p.max_records = 0;
+    if (!r->p.trace_chains || !r->p.trace_steps) r->p.trace_chains = 0, r->p.trace_steps = 0;
+    const size_t C = r->chains, np = in->Npad, R = r->p.max_records;
+    sk_status s = SK_OK;
+    if (s == SK_OK) s = dalloc(&r->ds, C * np);
+    if (s == SK_OK) s = dalloc(&r->dh, C * np * 4);
+    if (s == SK_OK) s = dalloc(&r->dacc, C * 4);
+    if (s == SK_OK) s = dalloc(&r->dwork, C * 16);
+    if (s == SK_OK) s = dalloc(&r->drecE, R * C * 8);
+    if (s == SK_OK) s = dalloc(&r->drecAcc, R * C * 4);
+    if (s == SK_OK) s = dalloc(&r->drecQ, R * (C / 2) * 8);
+    if (s == SK_OK) s = dalloc(&r->dtrace, static_cast<size_t>(r->p.trace_chains) * r->p.trace_steps * 4);
+    if (s == SK_OK) s = dalloc(&r->dstep, 8);
+    if (s == SK_OK) s = dalloc(&r->derr, 4);
+    if (s == SK_OK && in->kind == SK_J_PM1) {
+        const double be = r->p.beta * in->scale;
+        std::vector<uint64_t> t = r->p.rule == SK_RULE_MCMCMC ? mcmcmc_table(be, in->N) : metropolis_table(be, in->N);
+        r->wlen = static_cast<uint32_t>(t.size());
+        s = dalloc(&r->dW, std::max<size_t>(t.size(), 1) * 8);
+        if (s == SK_OK && !t.empty()) {
+            cudaError_t e = cudaMemcpy(r->dW, t.data(), t.size() * 8, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) s = fail(SK_ERR_CUDA, "table upload: %s", cudaGetErrorString(e));
+        }
+    }
+    if (s != SK_OK) {
+        free_run_buffers(r);
+        delete r;
+        return s;
+    }
+    JobDev& j = r->job;
+    j.J = in->dJ;
+    j.s = r->ds;
+    j.h = r->dh;
+    j.W = r->dW;
+    j.step = r->dstep;
+    j.acc_run = r->dacc;
+    j.rec_E = r->drecE;
+    j.rec_acc = r->drecAcc;
+    j.rec_q = r->drecQ;
+    j.trace = r->dtrace;
+    j.err = r->derr;
+    j.work = r->dwork;
+    j.seed = r->p.seed;
+    j.rec_capacity = R;
+    j.trace_steps = r->p.trace_steps;
+    j.scale = in->scale;
+    j.beta_eff = static_cast<float>(r->p.beta * in->scale);
+    j.stream = r->p.stream_id;
+    j.N = in->N;
+    j.Npad = in->Npad;
+    j.chains = r->chains;
+    j.K = r->p.K;
+    j.kind = in->kind;
+    j.rule = r->p.rule;
+    j.wlen = r->wlen;
+    j.record_every = r->p.record_every;
+    j.trace_chains = r->p.trace_chains;
+    s = init_state(r, p->init_spins, p->init_mem);
+    if (s == SK_OK) {
+        sk_run* one[1] = {r};
+        s = mcmcmc_batch_create(one, 1, 0, &r->self);
+    }
+    if (s != SK_OK) {
+        std::string keep = g_err;
+        cudaStreamSynchronize(in->st);
+        free_run_buffers(r);
+        delete r;
+        g_err = keep;
+        return s;
+    }
+    *out = r;
+    return SK_OK;
+}
+
+sk_status mcmcmc_advance(sk_run* r, uint64_t steps) {
+    if (!r) return fail(SK_ERR_INVALID_ARG, "run is NULL");
+    return mcmcmc_batch_advance(r->self, steps);
+}
+
+sk_status mcmcmc_run(sk_instance* in, const sk_run_params* p, uint64_t steps, sk_run** out) {
+    sk_status s = mcmcmc_create(in, p, out);
+    if (s != SK_OK) return s;
+    s = mcmcmc_advance(*out, steps);
+    if (s != SK_OK) {
+        mcmcmc_free(*out);
+        *out = nullptr;
+    }
+    return s;
+}
+
+sk_status mcmcmc_reset(sk_run* r, const int8_t* spins, uint32_t mem) {
+    if (!r) return fail(SK_ERR_INVALID_ARG, "run is NULL");
+    return init_state(r, spins, mem);
+}
+
+sk_status mcmcmc_wait(sk_run* r, uint64_t timeout_ns) {
+    if (!r) return fail(SK_ERR_INVALID_ARG, "run is NULL");
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaStreamQuery(r->inst->st);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) return fail(SK_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
+        if (timeout_ns) {
+            const auto ns = std::chrono::duration_cast<std::chrono::nanoseconds>(
+                                std::chrono::steady_clock::now() - t0).count();
+            if (static_cast<uint64_t>(ns) >= timeout_ns)
+                return fail(SK_ERR_TIMEOUT, "run still in flight after %llu ns", (unsigned long long)timeout_ns);
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    return check_run_error(r);
+}
+
+sk_status mcmcmc_observables(sk_run* r, uint64_t first, uint64_t count, double* energy,
+                             double* overlap, uint32_t* accepted, uint32_t mem) {
+    if (!r) return fail(SK_ERR_INVALID_ARG, "run is NULL");
+    if (mem != SK_MEM_HOST && mem != SK_MEM_DEVICE) return fail(SK_ERR_INVALID_ARG, "bad mem");
+    if (first + count > r->p.max_records)
+        return fail(SK_ERR_INVALID_ARG, "records [%llu, %llu) beyond capacity %llu", (unsigned long long)first,
+                    (unsigned long long)(first + count), (unsigned long long)r->p.max_records);
+    sk_status s = mcmcmc_wait(r, 0);
+    if (s != SK_OK) return s;
+    const size_t C = r->chains;
+    cudaStream_t st = r->inst->st;
+    if (count == 0) return SK_OK;
+    if (energy) SK_CU(cudaMemcpyAsync(energy, r->drecE + first * C, count * C * 8, cudaMemcpyDefault, st));
+    if (accepted) SK_CU(cudaMemcpyAsync(accepted, r->drecAcc + first * C, count * C * 4, cudaMemcpyDefault, st));
+    if (overlap && C >= 2)
+        SK_CU(cudaMemcpyAsync(overlap, r->drecQ + first * (C / 2), count * (C / 2) * 8, cudaMemcpyDefault, st));
+    SK_CU(cudaStreamSynchronize(st));
+    return SK_OK;
+}
+
+sk_status mcmcmc_state(sk_run* r, int8_t* spins, void* fields, uint64_t* step, uint32_t mem) {
+    if (!r) return fail(SK_ERR_INVALID_ARG, "run is NULL");
+    if (mem != SK_MEM_HOST && mem != SK_MEM_DEVICE) return fail(SK_ERR_INVALID_ARG, "bad mem");
+    sk_status s = mcmcmc_wait(r, 0);
+    if (s != SK_OK) return s;
+    sk_instance* in = r->inst;
+    cudaStream_t st = in->st;
+    if (spins)
+        SK_CU(cudaMemcpy2DAsync(spins, in->N, r->ds, in->Npad, in->N, r->chains, cudaMemcpyDefault, st));
+    if (fields)
+        SK_CU(cudaMemcpy2DAsync(fields, in->N * 4, r->dh, in->Npad * 4, in->N * 4, r->chains, cudaMemcpyDefault, st));
+    uint64_t ds = 0;
+    SK_CU(cudaMemcpyAsync(&ds, r->dstep, 8, cudaMemcpyDeviceToHost, st));
+    SK_CU(cudaStreamSynchronize(st));
+    if (step) *step = ds;
+    return SK_OK;
+}
+
+sk_status mcmcmc_trace(sk_run* r, int32_t* slots, uint32_t mem) {
+    if (!r || !slots) return fail(SK_ERR_INVALID_ARG, "NULL argument");
+    if (mem != SK_MEM_HOST && mem != SK_MEM_DEVICE) return fail(SK_ERR_INVALID_ARG, "bad mem");
+    sk_status s = mcmcmc_wait(r, 0);
+    if (s != SK_OK) return s;
+    const size_t n = static_cast<size_t>(r->p.trace_chains) * r->p.trace_steps;
+    if (n) {
+        SK_CU(cudaMemcpyAsync(slots, r->dtrace, n * 4, cudaMemcpyDefault, r->inst->st));
+        SK_CU(cudaStreamSynchronize(r->inst->st));
+    }
+    return SK_OK;
+}
+
+sk_status mcmcmc_counters(sk_run* r, uint64_t* flips, uint64_t* rows) {
+    if (!r) return fail(SK_ERR_INVALID_ARG, "run is NULL");
+    sk_status s = mcmcmc_wait(r, 0);
+    if (s != SK_OK) return s;
+    std::vector<unsigned long long> w(2 * static_cast<size_t>(r->chains));
+    SK_CU(cudaMemcpyAsync(w.data(), r->dwork, w.size() * 8, cudaMemcpyDeviceToHost, r->inst->st));
+    SK_CU(cudaStreamSynchronize(r->inst->st));
+    uint64_t f = 0, q = 0;
+    for (size_t c = 0; c < r->chains; ++c) {
+        f += w[2 * c];
+        q += w[2 * c + 1];
+    }
+    if (flips) *flips = f;
+    if (rows) *rows = q;
+    return SK_OK;
+}
+
+sk_status mcmcmc_free(sk_run* r) {
+    if (!r) return fail(SK_ERR_INVALID_ARG, "run is NULL");
+    cudaStreamSynchronize(r->inst->st);
+    if (r->self) mcmcmc_batch_free(r->self);
+    free_run_buffers(r);
+    delete r;
+    return SK_OK;
+}
+
+sk_status mcmcmc_batch_create(sk_run* const* runs, uint32_t n, uint32_t W, sk_batch** out) {
+    if (!runs || !out || n == 0) return fail(SK_ERR_INVALID_ARG, "empty batch");
+    *out = nullptr;
+    if (W && (W < 2 || W > 32 || (W & 1u)))
+        return fail(SK_ERR_INVALID_ARG, "warps_per_cta = %u must be even in 2..32", W);
+    cudaStream_t st = runs[0]->inst->st;
+    size_t per_warp = 0;
+    uint32_t maxK = 1;
+    for (uint32_t i = 0; i < n; ++i) {
+        if (!runs[i]) return fail(SK_ERR_INVALID_ARG, "run %u is NULL", i);
+        if (runs[i]->inst->st != st) return fail(SK_ERR_INVALID_ARG, "runs of a batch must share a stream");
+        per_warp = std::max(per_warp, sk::warp_smem_bytes(runs[i]->inst->Npad, runs[i]->inst->kind));
+        if (runs[i]->p.rule == SK_RULE_MCMCMC) maxK = std::max(maxK, runs[i]->p.K);
+    }
+    per_warp = (per_warp + 127) / 128 * 128;
+    const uint32_t fit = static_cast<uint32_t>(std::min<size_t>(32, kSmemBudget / per_warp)) & ~1u;
+    if (fit < 2) return fail(SK_ERR_INVALID_ARG, "N too large: %zu bytes of shared memory per chain", per_warp);
+    if (!W) W = fit;
+    if (W > fit) return fail(SK_ERR_INVALID_ARG, "warps_per_cta = %u needs more than %zu bytes of shared memory",
+                             W, kSmemBudget);
+    sk_batch* b = new sk_batch();
+    b->runs.assign(runs, runs + n);
+    b->W = W;
+    b->per_warp = static_cast<uint32_t>(per_warp);
+    b->nb = maxK > 128 ? 2 : 1;
+    b->st = st;
+    std::vector<JobDev> jobs(n);
+    std::vector<WorkItem> items;
+    for (uint32_t i = 0; i < n; ++i) {
+        jobs[i] = runs[i]->job;
+        for (uint32_t c = 0; c < runs[i]->chains; c += W)
+            items.push_back(WorkItem{i, c, std::min(W, runs[i]->chains - c), 0});
+    }
+    b->n_items = static_cast<uint32_t>(items.size());
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int occ = sk::step_kernel_occupancy(b->nb, W, per_warp * W);
+    if (occ <= 0) {
+        delete b;
+        return fail(SK_ERR_CUDA, "step kernel cannot be resident with %u warps and %zu bytes", W, per_warp * W);
+    }
+    b->grid = std::min<uint32_t>(b->n_items, static_cast<uint32_t>(occ * sms));
+    sk_status s = dalloc(&b->djobs, n * sizeof(JobDev));
+    if (s == SK_OK) s = dalloc(&b->ditems, items.size() * sizeof(WorkItem));
+    if (s == SK_OK) s = dalloc(&b->dqueue, sizeof(uint32_t));
+    if (s == SK_OK) {
+        cudaError_t e = cudaMemcpy(b->djobs, jobs.data(), n * sizeof(JobDev), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(b->ditems, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) s = fail(SK_ERR_CUDA, "batch upload: %s", cudaGetErrorString(e));
+    }
+    if (s != SK_OK) {
+        cudaFree(b->djobs);
+        cudaFree(b->ditems);
+        cudaFree(b->dqueue);
+        delete b;
+        return s;
+    }
+    *out = b;
+    return SK_OK;
+}
+
+sk_status mcmcmc_batch_advance(sk_batch* b, uint64_t steps) {
+    if (!b) return fail(SK_ERR_INVALID_ARG, "batch is NULL");
+    if (steps == 0) return SK_OK;
+    for (sk_run* r : b->runs)
+        if (r->step + steps > 0xFFFFFFFFull)
+            return fail(SK_ERR_INVALID_ARG, "a run would pass 2^32 steps");
+    cudaError_t e = sk::launch_step(b->djobs, b->ditems, b->n_items, b->dqueue, steps, b->W, b->per_warp,
+                                    b->grid, b->nb, static_cast<uint32_t>(b->runs.size()), b->st);
+    if (e != cudaSuccess) return fail(SK_ERR_CUDA, "step launch: %s", cudaGetErrorString(e));
+    for (sk_run* r : b->runs) r->step += steps;
+    return SK_OK;
+}
+
+sk_status mcmcmc_batch_info(const sk_batch* b, uint32_t* grid, uint32_t* W, uint32_t* smem,
+                            uint32_t* items) {
+    if (!b) return fail(SK_ERR_INVALID_ARG, "batch is NULL");
+    if (grid) *grid = b->grid;
+    if (W) *W = b->W;
+    if (smem) *smem = b->per_warp * b->W;
+    if (items) *items = b->n_items;
+    return SK_OK;
+}
+
+sk_status mcmcmc_batch_free(sk_batch* b) {
+    if (!b) return fail(SK_ERR_INVALID_ARG, "batch is NULL");
+    cudaStreamSynchronize(b->st);
+    cudaFree(b->djobs);
+    cudaFree(b->ditems);
+    cudaFree(b->dqueue);
+    delete b;
+    return SK_OK;
+}
+
+}  // extern "C"

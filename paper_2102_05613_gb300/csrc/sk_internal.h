@@ -1,0 +1,68 @@
+// sk_internal.h -- structures shared by the host runtime and the kernels of
+// the sampler library (not part of the public C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sk {
+
+constexpr uint32_t kMaxK = 256;      // proposals per step
+constexpr uint32_t kPadTo = 32;      // Npad = round_up(N, 32)
+
+// Error codes written by kernels into the launch's error word.
+enum : int { kDevOk = 0, kDevTimeout = 1, kDevBounds = 2 };
+
+// One run as seen by the kernels.  Row-major layouts, leading dimension Npad:
+//   J[Npad][Npad] (int8 or float), s[chains][Npad] int8 (+-1, padding 0),
+//   h[chains][Npad] (int32 for +-J, float for Gaussian, padding 0).
+struct alignas(16) JobDev {
+    const void* J;
+    int8_t* s;
+    void* h;
+    const uint64_t* W;      // +-J tables: MCMCMC W[d] (wlen) or Metropolis M[k] (N+1)
+    uint64_t* step;         // device step counter of the run
+    uint32_t* acc_run;      // per chain: accepted steps since the last record
+    double* rec_E;          // [rec][chains]
+    uint32_t* rec_acc;      // [rec][chains]
+    double* rec_q;          // [rec][chains/2]
+    int32_t* trace;         // [trace_chains][trace_steps]
+    int* err;               // error word of the run (kDev* codes)
+    unsigned long long* work;  // per chain: [spins flipped, J rows the steps needed]
+    uint64_t seed;
+    uint64_t rec_capacity;
+    uint64_t trace_steps;
+    double scale;           // energy scale of the records
+    float beta_eff;         // beta * scale (Gaussian weights)
+    uint32_t stream;        // Philox stream id (24 bits)
+    uint32_t N, Npad, chains, K;
+    uint32_t kind, rule, wlen, record_every;
+    uint32_t trace_chains;
+    uint32_t pad_[3];
+};
+static_assert(sizeof(JobDev) % 16 == 0, "JobDev is copied as 16-byte words");
+
+// A block of consecutive chains of one run, processed by one CTA (one warp
+// per chain).  chain0 is even so that overlap pairs stay inside a CTA.
+struct WorkItem {
+    uint32_t job, chain0, nchains, pad;
+};
+
+// Bytes of shared memory one warp (one chain) needs for spins, fields and
+// the two J-row staging buffers.
+inline size_t warp_smem_bytes(uint32_t npad, uint32_t kind) {
+    size_t bj = kind == 0 ? 1 : 4;
+    return (size_t)npad * (1 + 4 + 2 * bj);
+}
+
+// Kernel launchers (sk_kernels.cu).  All return cudaGetLastError().
+cudaError_t launch_step(const JobDev* jobs, const WorkItem* items, uint32_t n_items,
+                        uint32_t* queue, uint64_t nsteps, uint32_t warps_per_cta,
+                        uint32_t per_warp_bytes, uint32_t grid, int nb,
+                        uint32_t n_jobs, cudaStream_t st);
+cudaError_t launch_init(const JobDev* job, const int8_t* init, uint32_t chains, uint32_t N,
+                        uint32_t Npad, uint32_t kind, cudaStream_t st);
+cudaError_t launch_energy(const void* J, uint32_t kind, uint32_t N, uint32_t Npad, double scale,
+                          const int8_t* spins, uint32_t count, double* out, cudaStream_t st);
+int step_kernel_occupancy(int nb, uint32_t warps_per_cta, size_t smem_bytes);
+
+}  // namespace sk

@@ -1,0 +1,289 @@
+"""Thin ctypes binding of the sampler's C ABI (include/sk_mcmcmc.h).
+
+Argument marshalling only: every step of the sampler runs in the CUDA
+library.  The functions keep the C names; small classes wrap the opaque
+handles.  Inputs may be numpy arrays (host) or torch CUDA tensors (device,
+passed by pointer); outputs come back as numpy arrays unless a device
+tensor is supplied.  Loading fails loudly when the library has not been
+built: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SK_OK, SK_ERR_INVALID_ARG, SK_ERR_OOM, SK_ERR_CUDA, SK_ERR_TIMEOUT, SK_ERR_NOT_READY, SK_ERR_DEVICE = range(7)
+SK_J_PM1, SK_J_GAUSS = 0, 1
+SK_RULE_MCMCMC, SK_RULE_METROPOLIS = 0, 1
+SK_MEM_HOST, SK_MEM_DEVICE = 0, 1
+SK_MAX_K, SK_MAX_N = 256, 8192
+
+_STATUS = {0: "SK_OK", 1: "SK_ERR_INVALID_ARG", 2: "SK_ERR_OOM", 3: "SK_ERR_CUDA",
+           4: "SK_ERR_TIMEOUT", 5: "SK_ERR_NOT_READY", 6: "SK_ERR_DEVICE"}
+
+# every symbol declared in include/sk_mcmcmc.h
+EXPORTS = ["sk_create_instance", "sk_set_couplings", "sk_destroy_instance", "sk_energy",
+           "mcmcmc_create", "mcmcmc_advance", "mcmcmc_run", "mcmcmc_reset", "mcmcmc_wait",
+           "mcmcmc_observables", "mcmcmc_state", "mcmcmc_trace", "mcmcmc_counters", "mcmcmc_free",
+           "mcmcmc_batch_create", "mcmcmc_batch_advance", "mcmcmc_batch_info",
+           "mcmcmc_batch_free", "sk_last_error"]
+
+
+class SKError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class RunParams(C.Structure):
+    _fields_ = [("chains", C.c_uint32), ("K", C.c_uint32), ("rule", C.c_uint32),
+                ("record_every", C.c_uint32), ("max_records", C.c_uint64),
+                ("beta", C.c_double), ("seed", C.c_uint64), ("stream_id", C.c_uint32),
+                ("trace_chains", C.c_uint32), ("trace_steps", C.c_uint64),
+                ("init_spins", C.c_void_p), ("init_mem", C.c_uint32)]
+
+
+_lib = None
+
+
+def lib(build_if_missing: bool = True):
+    """The loaded CUDA library; builds it in-tree if it is missing."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if build_if_missing:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA sampler library not built ({path}); run build() first")
+        L = C.CDLL(path)
+        vp, u32, u64, d = C.c_void_p, C.c_uint32, C.c_uint64, C.c_double
+        P = C.POINTER(C.c_void_p)
+        sig = {
+            "sk_create_instance": [u32, u32, vp, u32, d, vp, P],
+            "sk_set_couplings": [vp, vp, u32],
+            "sk_destroy_instance": [vp],
+            "sk_energy": [vp, vp, u32, u32, vp],
+            "mcmcmc_create": [vp, C.POINTER(RunParams), P],
+            "mcmcmc_advance": [vp, u64],
+            "mcmcmc_run": [vp, C.POINTER(RunParams), u64, P],
+            "mcmcmc_reset": [vp, vp, u32],
+            "mcmcmc_wait": [vp, u64],
+            "mcmcmc_observables": [vp, u64, u64, vp, vp, vp, u32],
+            "mcmcmc_state": [vp, vp, vp, vp, u32],
+            "mcmcmc_trace": [vp, vp, u32],
+            "mcmcmc_counters": [vp, vp, vp],
+            "mcmcmc_free": [vp],
+            "mcmcmc_batch_create": [P, u32, u32, P],
+            "mcmcmc_batch_advance": [vp, u64],
+            "mcmcmc_batch_info": [vp, vp, vp, vp, vp],
+            "mcmcmc_batch_free": [vp],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.sk_last_error.argtypes = []
+        L.sk_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != SK_OK:
+        raise SKError(status, lib().sk_last_error().decode())
+
+
+def _ptr_mem(a):
+    """(pointer, mem) of a numpy array or a torch tensor."""
+    if a is None:
+        return None, SK_MEM_HOST
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(C.c_void_p), SK_MEM_HOST
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr()), (SK_MEM_DEVICE if a.is_cuda else SK_MEM_HOST)
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+class Instance:
+    """sk_create_instance / sk_destroy_instance (couplings resident on the GPU)."""
+
+    def __init__(self, J, scale: float = 1.0, stream=None):
+        if isinstance(J, np.ndarray):
+            J = np.ascontiguousarray(J)
+            dt = J.dtype
+        else:
+            dt = {"torch.int8": np.int8, "torch.float32": np.float32}[str(J.dtype)]
+        if dt == np.int8:
+            self.kind = SK_J_PM1
+        elif dt == np.float32:
+            self.kind = SK_J_GAUSS
+        else:
+            raise TypeError("couplings must be int8 (+-J) or float32 (Gaussian)")
+        self.N = int(J.shape[0])
+        self.scale = float(scale)
+        self._stream = stream
+        h = C.c_void_p()
+        p, mem = _ptr_mem(J)
+        _check(lib().sk_create_instance(self.N, self.kind, p, mem, self.scale,
+                                        _stream_handle(stream), C.byref(h)))
+        self.handle = h
+
+    def set_couplings(self, J):
+        p, mem = _ptr_mem(J if not isinstance(J, np.ndarray) else np.ascontiguousarray(J))
+        _check(lib().sk_set_couplings(self.handle, p, mem))
+
+    def energy(self, spins) -> np.ndarray:
+        if isinstance(spins, np.ndarray):
+            spins = np.ascontiguousarray(spins, dtype=np.int8).reshape(-1, self.N)
+            count = spins.shape[0]
+        else:
+            count = spins.numel() // self.N
+        out = np.zeros(count)
+        p, mem = _ptr_mem(spins)
+        _check(lib().sk_energy(self.handle, p, count, mem, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(lib().sk_destroy_instance(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Run:
+    """mcmcmc_create / advance / observables / state / free."""
+
+    def __init__(self, inst: Instance, *, chains: int, K: int = 8, rule: int = SK_RULE_MCMCMC,
+                 beta: float = 1.0, seed: int = 1, stream_id: int = 0, record_every: int = 0,
+                 max_records: int = 0, init=None, trace_chains: int = 0, trace_steps: int = 0):
+        self.inst = inst
+        self.chains, self.K, self.rule = int(chains), int(K), int(rule)
+        self.record_every, self.max_records = int(record_every), int(max_records)
+        self.trace_chains, self.trace_steps = int(trace_chains), int(trace_steps)
+        self._init = None
+        pr = RunParams()
+        pr.chains, pr.K, pr.rule = self.chains, self.K, self.rule
+        pr.record_every, pr.max_records = self.record_every, self.max_records
+        pr.beta, pr.seed, pr.stream_id = float(beta), int(seed), int(stream_id)
+        pr.trace_chains, pr.trace_steps = self.trace_chains, self.trace_steps
+        if init is not None:
+            if isinstance(init, np.ndarray):
+                init = np.ascontiguousarray(init, dtype=np.int8)
+            self._init = init
+            p, mem = _ptr_mem(init)
+            pr.init_spins, pr.init_mem = p, mem
+        h = C.c_void_p()
+        _check(lib().mcmcmc_create(inst.handle, C.byref(pr), C.byref(h)))
+        self.handle = h
+
+    def advance(self, steps: int):
+        _check(lib().mcmcmc_advance(self.handle, int(steps)))
+
+    def reset(self, spins=None):
+        if isinstance(spins, np.ndarray):
+            spins = np.ascontiguousarray(spins, dtype=np.int8)
+        p, mem = _ptr_mem(spins)
+        _check(lib().mcmcmc_reset(self.handle, p, mem))
+
+    def wait(self, timeout_ns: int = 0):
+        _check(lib().mcmcmc_wait(self.handle, int(timeout_ns)))
+
+    def observables(self, first: int = 0, count=None, out=None):
+        if count is None:
+            count = self.max_records - first
+        C_ = self.chains
+        if out is None:
+            E = np.zeros((count, C_))
+            q = np.zeros((count, C_ // 2))
+            acc = np.zeros((count, C_), dtype=np.uint32)
+            mem = SK_MEM_HOST
+            ptrs = [x.ctypes.data_as(C.c_void_p) for x in (E, q, acc)]
+        else:
+            E, q, acc = out
+            mem = SK_MEM_DEVICE if getattr(E, "is_cuda", False) else SK_MEM_HOST
+            ptrs = [_ptr_mem(x)[0] for x in (E, q, acc)]
+        _check(lib().mcmcmc_observables(self.handle, first, count, ptrs[0], ptrs[1], ptrs[2], mem))
+        return E, q, acc
+
+    def state(self, fields: bool = False):
+        N = self.inst.N
+        s = np.zeros((self.chains, N), dtype=np.int8)
+        h = None
+        if fields:
+            h = np.zeros((self.chains, N), dtype=np.int32 if self.inst.kind == SK_J_PM1 else np.float32)
+        step = C.c_uint64(0)
+        _check(lib().mcmcmc_state(self.handle, s.ctypes.data_as(C.c_void_p),
+                                  None if h is None else h.ctypes.data_as(C.c_void_p),
+                                  C.byref(step), SK_MEM_HOST))
+        return (s, h, step.value) if fields else (s, step.value)
+
+    def trace(self) -> np.ndarray:
+        t = np.zeros((self.trace_chains, self.trace_steps), dtype=np.int32)
+        _check(lib().mcmcmc_trace(self.handle, t.ctypes.data_as(C.c_void_p), SK_MEM_HOST))
+        return t
+
+    def counters(self):
+        """(spins flipped, J rows needed) since the last reset."""
+        f, r = C.c_uint64(0), C.c_uint64(0)
+        _check(lib().mcmcmc_counters(self.handle, C.byref(f), C.byref(r)))
+        return f.value, r.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(lib().mcmcmc_free(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """mcmcmc_batch_create / advance / free: many runs, one persistent launch."""
+
+    def __init__(self, runs, warps_per_cta: int = 0):
+        self.runs = list(runs)
+        arr = (C.c_void_p * len(self.runs))(*[r.handle.value for r in self.runs])
+        h = C.c_void_p()
+        _check(lib().mcmcmc_batch_create(C.cast(arr, C.POINTER(C.c_void_p)), len(self.runs),
+                                         int(warps_per_cta), C.byref(h)))
+        self.handle = h
+
+    def advance(self, steps: int):
+        _check(lib().mcmcmc_batch_advance(self.handle, int(steps)))
+
+    def info(self):
+        v = [C.c_uint32(0) for _ in range(4)]
+        _check(lib().mcmcmc_batch_info(self.handle, *[C.byref(x) for x in v]))
+        return dict(grid=v[0].value, warps_per_cta=v[1].value, smem_bytes=v[2].value,
+                    items=v[3].value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(lib().mcmcmc_batch_free(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

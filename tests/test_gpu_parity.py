@@ -1,0 +1,289 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
++-J couplings: bit-exact trajectories (integer energies, same Philox
+stream): records of E, acceptance and q, final spins, maintained fields and
+the per-step slot log.  Gaussian couplings: every GPU decision is either the
+oracle's or a near-tie within the fp32 tolerance (decision replay), and the
+GPU's recorded energy per spin equals the oracle's FP64 energy of the same
+state within 1e-5.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2102_05613_gb300 import inputs, sk
+
+from gpu_util import need_gpu
+
+pytestmark = pytest.mark.gpu
+
+# decision replay tolerance on u / P_K (fp32 weights and prefix sums, fp32
+# fields that drift by a few ulp per update); see DESIGN.md "Gaussian parity"
+REPLAY_TOL = 1e-4
+E_PER_SPIN_TOL = 1e-5
+
+
+def _run_gpu(J, *, chains, K, beta, rule, steps, seed, R=0, init=None, trace=0, scale=1.0,
+             stream_id=0, splits=None):
+    inst = sk.Instance(J, scale=scale)
+    nrec = steps // R if R else 0
+    run = sk.Run(inst, chains=chains, K=K, rule=rule, beta=beta, seed=seed, stream_id=stream_id,
+                 record_every=R, max_records=nrec, init=init, trace_chains=trace,
+                 trace_steps=steps if trace else 0)
+    for s in (splits or [steps]):
+        run.advance(s)
+    run.wait()
+    out = {}
+    if nrec:
+        out["E"], out["q"], out["acc"] = run.observables()
+    out["spins"], out["fields"], out["step"] = run.state(fields=True)
+    if trace:
+        out["trace"] = run.trace()
+    run.close()
+    inst.close()
+    return out
+
+
+def _fields_exact(J, spins):
+    return (J.astype(np.int64) @ spins.T.astype(np.int64)).T
+
+
+@pytest.mark.parametrize("rule,K", [(sk.SK_RULE_MCMCMC, 8)])
+def test_pm1_config1_bit_exact(rule, K):
+    """+-J N=64, J seed 0, beta=1, one chain from a random start, K=8, 1e5
+    steps, Philox seed 1: identical trajectory step by step."""
+    need_gpu()
+    N, steps, R = 64, 100_000, 1000
+    J = inputs.couplings_pm1(N, 0)
+    init = inputs.initial_spins(1, N, 1234)
+    g = _run_gpu(J, chains=1, K=K, beta=1.0, rule=rule, steps=steps, seed=1, R=R, init=init,
+                 trace=1)
+    o = oracle.run(J, rule=rule, K=K, beta=1.0, seed=1, chains=1, init=init, steps=steps,
+                   record_every=R, trace=True, want_q=False)
+    assert np.array_equal(g["trace"][0], o["trace"][0])
+    assert np.array_equal(g["E"], o["E"])
+    assert np.array_equal(g["acc"], o["acc"])
+    assert np.array_equal(g["spins"], o["spins"])
+    assert np.array_equal(g["fields"], _fields_exact(J, g["spins"]))
+    assert g["step"] == steps
+
+
+@pytest.mark.parametrize("N,K,chains,beta", [
+    (100, 1, 7, 0.5),      # ragged N (padding), odd chains (ragged CTA), K = 1
+    (100, 5, 6, 0.3),
+    (130, 33, 5, 1.0),     # K not a multiple of 4
+    (96, 128, 4, 2.0),     # 32 Philox blocks: every lane busy
+    (70, 200, 4, 0.7),     # two blocks per lane (K > 128)
+    (64, 256, 2, 1.5),     # maximum K
+    (2, 3, 2, 1.0),        # smallest N
+])
+def test_pm1_bit_exact_shapes(N, K, chains, beta):
+    need_gpu()
+    steps, R = 1500, 100
+    J = inputs.couplings_pm1(N, N + K)
+    init = inputs.initial_spins(chains, N, 7)
+    g = _run_gpu(J, chains=chains, K=K, beta=beta, rule=sk.SK_RULE_MCMCMC, steps=steps, seed=99,
+                 R=R, init=init, trace=min(chains, 3))
+    o = oracle.run(J, K=K, beta=beta, seed=99, chains=chains, init=init, steps=steps,
+                   record_every=R, trace=True)
+    assert np.array_equal(g["trace"], o["trace"][: min(chains, 3)])
+    assert np.array_equal(g["E"], o["E"])
+    assert np.array_equal(g["acc"], o["acc"])
+    if chains >= 2:
+        assert np.array_equal(g["q"], o["q"])
+    assert np.array_equal(g["spins"], o["spins"])
+    assert np.array_equal(g["fields"], _fields_exact(J, g["spins"]))
+
+
+@pytest.mark.parametrize("N,beta,scale", [(64, 1.0, 1.0), (150, 0.4, 1.0), (256, 1.0, 1 / 16)])
+def test_pm1_metropolis_bit_exact(N, beta, scale):
+    need_gpu()
+    steps, R, chains = 4000, 200, 4
+    J = inputs.couplings_pm1(N, 5)
+    init = inputs.initial_spins(chains, N, 8)
+    g = _run_gpu(J, chains=chains, K=1, beta=beta, rule=sk.SK_RULE_METROPOLIS, steps=steps,
+                 seed=3, R=R, init=init, trace=2, scale=scale)
+    o = oracle.run(J, rule=oracle.METROPOLIS, beta=beta, scale=scale, seed=3, chains=chains,
+                   init=init, steps=steps, record_every=R, trace=True)
+    assert np.array_equal(g["trace"], o["trace"][:2])
+    assert np.array_equal(g["E"], o["E"])
+    assert np.array_equal(g["acc"], o["acc"])
+    assert np.array_equal(g["q"], o["q"])
+    assert np.array_equal(g["spins"], o["spins"])
+
+
+def test_pm1_scaled_energy_and_random_start():
+    need_gpu()
+    N, K, chains = 77, 16, 4
+    J = inputs.couplings_pm1(N, 3)
+    scale = 1.0 / math.sqrt(N)
+    g = _run_gpu(J, chains=chains, K=K, beta=1.0, rule=sk.SK_RULE_MCMCMC, steps=0, seed=5,
+                 stream_id=9, scale=scale)
+    for c in range(chains):
+        assert np.array_equal(g["spins"][c], oracle.init_spins(5, 9, c, N))
+    g = _run_gpu(J, chains=chains, K=K, beta=1.0, rule=sk.SK_RULE_MCMCMC, steps=800, seed=5,
+                 stream_id=9, scale=scale, R=100)
+    o = oracle.run(J, K=K, beta=1.0, scale=scale, seed=5, stream=9, chains=chains, steps=800,
+                   record_every=100)
+    assert np.array_equal(g["E"], o["E"])
+    assert np.array_equal(g["spins"], o["spins"])
+
+
+def test_advance_in_pieces_equals_one_advance():
+    # counter-based draws: stopping and resuming is bit-exact (checkpoint/resume)
+    need_gpu()
+    N, K, chains = 90, 24, 6
+    J = inputs.couplings_pm1(N, 4)
+    a = _run_gpu(J, chains=chains, K=K, beta=0.8, rule=sk.SK_RULE_MCMCMC, steps=1000, seed=2, R=50)
+    b = _run_gpu(J, chains=chains, K=K, beta=0.8, rule=sk.SK_RULE_MCMCMC, steps=1000, seed=2, R=50,
+                 splits=[1, 37, 462, 500])
+    for k in ("E", "q", "acc", "spins", "fields"):
+        assert np.array_equal(a[k], b[k]), k
+    # restart from the saved spins: fields are recomputed, trajectory continues
+    J2 = J
+    c = _run_gpu(J2, chains=chains, K=K, beta=0.8, rule=sk.SK_RULE_MCMCMC, steps=400, seed=2, R=50)
+    o = oracle.run(J2, K=K, beta=0.8, seed=2, chains=chains, steps=400, record_every=50)
+    assert np.array_equal(c["spins"], o["spins"])
+
+
+@pytest.mark.parametrize("rule,K,N,beta", [
+    (sk.SK_RULE_MCMCMC, 32, 96, 1.0),
+    (sk.SK_RULE_MCMCMC, 128, 160, 2.0),
+    (sk.SK_RULE_MCMCMC, 200, 64, 0.5),
+    (sk.SK_RULE_METROPOLIS, 1, 128, 1.0),
+])
+def test_gauss_decision_replay(rule, K, N, beta):
+    need_gpu()
+    steps, chains, R = 3000, 4, 300
+    J = inputs.couplings_gauss(N, 17)
+    init = inputs.initial_spins(chains, N, 18)
+    g = _run_gpu(J, chains=chains, K=K, beta=beta, rule=rule, steps=steps, seed=21, R=R,
+                 init=init, trace=chains)
+    orule = oracle.MCMCMC if rule == sk.SK_RULE_MCMCMC else oracle.METROPOLIS
+    for c in range(chains):
+        r = oracle.replay(J, g["trace"][c], rule=orule, K=K, beta=beta, seed=21, chain=c,
+                          init=init[c], tol=REPLAY_TOL)
+        assert r["bad"] == 0, (c, r)
+        assert r["disagree"] <= 3, (c, r)
+        assert np.array_equal(r["spins"], g["spins"][c])
+        # the GPU's recorded energy of its final state vs the FP64 energy
+        assert abs(g["E"][-1, c] - oracle.energy(J, g["spins"][c])) / N <= E_PER_SPIN_TOL
+        h = J.astype(np.float64) @ g["spins"][c].astype(np.float64)
+        assert np.abs(g["fields"][c] - h).max() < 1e-4
+
+
+def test_gauss_statistics_within_3_sigma():
+    # independent GPU and oracle ensembles: E/N, q and acceptance per record
+    need_gpu()
+    N, K, beta, chains, steps, R = 48, 16, 1.0, 512, 1000, 100
+    J = inputs.couplings_gauss(N, 31)
+    g = _run_gpu(J, chains=chains, K=K, beta=beta, rule=sk.SK_RULE_MCMCMC, steps=steps,
+                 seed=100, R=R)
+    o = oracle.run(J, K=K, beta=beta, seed=200, chains=chains, steps=steps, record_every=R)
+    zs = []
+    for key in ("E", "q", "acc"):
+        a = np.asarray(g[key], dtype=float)
+        b = np.asarray(o[key], dtype=float)
+        if key == "q":
+            a, b = np.abs(a), np.abs(b)
+        se = np.sqrt(a.var(axis=1, ddof=1) / a.shape[1] + b.var(axis=1, ddof=1) / b.shape[1])
+        z = (a.mean(axis=1) - b.mean(axis=1)) / np.maximum(se, 1e-12)
+        zs.append(z)
+    zs = np.concatenate(zs)
+    assert np.mean(np.abs(zs) > 3) <= 0.1 and np.abs(zs).max() < 4.5, zs
+
+
+def test_energy_entry_point():
+    need_gpu()
+    for J in (inputs.couplings_pm1(200, 1), inputs.couplings_gauss(200, 2)):
+        S = inputs.initial_spins(9, 200, 3)
+        inst = sk.Instance(J, scale=0.5)
+        E = inst.energy(S)
+        inst.close()
+        for c in range(9):
+            want = oracle.energy(J, S[c], scale=0.5)
+            if J.dtype == np.int8:
+                assert E[c] == want
+            else:
+                assert abs(E[c] - want) <= 1e-9 * 200
+
+
+def test_batch_equals_runs_alone():
+    # uneven N, K, beta, couplings and rules in one launch; each run identical alone
+    need_gpu()
+    specs = [(64, sk.SK_J_PM1, 8, 1.0, sk.SK_RULE_MCMCMC, 6),
+             (200, sk.SK_J_GAUSS, 40, 0.7, sk.SK_RULE_MCMCMC, 10),
+             (333, sk.SK_J_PM1, 150, 2.0, sk.SK_RULE_MCMCMC, 5),
+             (128, sk.SK_J_GAUSS, 1, 1.0, sk.SK_RULE_METROPOLIS, 4),
+             (96, sk.SK_J_PM1, 1, 0.5, sk.SK_RULE_METROPOLIS, 3)]
+    steps, R = 600, 100
+
+    def make(i, spec):
+        N, kind, K, beta, rule, chains = spec
+        J = inputs.couplings(N, kind, 50 + i)
+        inst = sk.Instance(J)
+        run = sk.Run(inst, chains=chains, K=K, rule=rule, beta=beta, seed=7, stream_id=i,
+                     record_every=R, max_records=steps // R)
+        return inst, run
+
+    alone = []
+    for i, spec in enumerate(specs):
+        inst, run = make(i, spec)
+        run.advance(steps)
+        alone.append((run.observables(), run.state(fields=True)))
+        run.close(); inst.close()
+    made = [make(i, spec) for i, spec in enumerate(specs)]
+    b = sk.Batch([r for _, r in made])
+    b.advance(250)
+    b.advance(steps - 250)
+    for (inst, run), (obs, st) in zip(made, alone):
+        o2 = run.observables()
+        s2 = run.state(fields=True)
+        for x, y in zip(obs, o2):
+            assert np.array_equal(x, y)
+        assert np.array_equal(st[0], s2[0]) and np.array_equal(st[1], s2[1]) and st[2] == s2[2]
+    b.close()
+    for inst, run in made:
+        run.close(); inst.close()
+
+
+def test_invalid_arguments_fail_loudly():
+    need_gpu()
+    J = inputs.couplings_pm1(16, 1)
+    with pytest.raises(sk.SKError) as e:
+        bad = J.copy(); bad[0, 1] = 2; bad[1, 0] = 2
+        sk.Instance(bad)
+    assert e.value.status == sk.SK_ERR_INVALID_ARG
+    with pytest.raises(sk.SKError):
+        bad = J.copy(); bad[0, 1] = -bad[0, 1]
+        sk.Instance(bad)
+    inst = sk.Instance(J)
+    with pytest.raises(sk.SKError):
+        sk.Run(inst, chains=2, K=0)
+    with pytest.raises(sk.SKError):
+        sk.Run(inst, chains=2, K=257)
+    with pytest.raises(sk.SKError):
+        sk.Run(inst, chains=0, K=4)
+    with pytest.raises(sk.SKError):
+        sk.Run(inst, chains=2, K=4, beta=-1.0)
+    with pytest.raises(sk.SKError):
+        sk.Run(inst, chains=2, K=4, init=np.zeros((2, 16), dtype=np.int8))
+    inst.close()
+    with pytest.raises(sk.SKError):
+        sk.Instance(np.zeros((8193, 8193), dtype=np.int8))
+
+
+def test_largest_n():
+    need_gpu()
+    N, K, chains, steps = 8192, 64, 2, 60
+    J = inputs.couplings_pm1(N, 9)
+    init = inputs.initial_spins(chains, N, 9)
+    g = _run_gpu(J, chains=chains, K=K, beta=0.05, rule=sk.SK_RULE_MCMCMC, steps=steps, seed=4,
+                 R=20, init=init, trace=2)
+    o = oracle.run(J, K=K, beta=0.05, seed=4, chains=chains, init=init, steps=steps,
+                   record_every=20, trace=True)
+    assert np.array_equal(g["trace"], o["trace"])
+    assert np.array_equal(g["E"], o["E"])
+    assert np.array_equal(g["spins"], o["spins"])
