@@ -131,7 +131,7 @@ def _oracle_sample(couplings, chains_per_instance, steps, threads):
 
 def cpu_baseline(couplings):
     cores = _cores()
-    per_inst = 128
+    per_inst = 512
     steps = R
     dt = _oracle_sample(couplings, per_inst, steps, cores)
     units = INSTANCES * per_inst * steps * K
@@ -171,8 +171,12 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------
 def run_ours(args):
-    import numpy as np
     import torch
+    global INSTANCES, CHAINS, WORKLOAD
+    if (args.instances, args.chains) != (INSTANCES, CHAINS):
+        WORKLOAD = WORKLOAD.replace(f"{INSTANCES} instances x {CHAINS} chains",
+                                    f"{args.instances} instances x {args.chains} chains")
+        INSTANCES, CHAINS = args.instances, args.chains
     rank, world, local = _env()
     dist = None
     if world > 1:
@@ -318,6 +322,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--instances", type=int, default=INSTANCES,
+                    help="smaller cases for profiling only; the bench line uses the default")
+    ap.add_argument("--chains", type=int, default=CHAINS)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

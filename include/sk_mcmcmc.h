@@ -206,6 +206,56 @@ sk_status mcmcmc_batch_info(const sk_batch* b, uint32_t* grid, uint32_t* warps_p
 
 sk_status mcmcmc_batch_free(sk_batch* b);
 
+/* ---------------------------------------------------------------------- */
+/* Allocation-free run.  The paper has no counterpart: this entry point   */
+/* exists for callers of this library that cannot allocate device memory. */
+/* ---------------------------------------------------------------------- */
+
+/* Size of the fixed device array that mcmcmc_run_noalloc works in. */
+#define SK_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/*
+ * mcmcmc_run_noalloc: runs `steps` Monte Carlo steps of `chains` chains, the
+ * same kernels and results as mcmcmc_run with these arguments, without
+ * allocating anything: no cudaMalloc, no cudaFree, no allocating library
+ * routine.  It is for callers that cannot allocate device memory or let a
+ * library do so: applications whose device memory is owned entirely by their
+ * own pool allocator (an extra cudaMalloc would fail or fragment the pool),
+ * latency-critical loops that cannot afford cudaMalloc's implicit device
+ * synchronisation, and plug-in hosts that forbid libraries from allocating.
+ *
+ *   N, kind, scale       as for sk_create_instance;
+ *   couplings            device pointer, N*N row-major (int8 for SK_J_PM1,
+ *                        float32 for SK_J_GAUSS), symmetric, zero diagonal
+ *                        (not checked: the caller vouches for it);
+ *   chains, K, rule, beta, seed, stream_id   as in sk_run_params;
+ *   spins                device pointer, chains*N int8 +-1: the start state
+ *                        on input, the state after `steps` steps on output;
+ *   energy               device pointer, chains doubles: E of the final states;
+ *   stream               cudaStream_t (as void*) or NULL.
+ * No records, traces or counters are kept.
+ *
+ * Working memory: a file-scope device array of SK_NOALLOC_SCRATCH_BYTES
+ * (16 MiB), which every GPU that loads the library holds until the process
+ * exits.  It must hold the padded couplings (Npad^2 bytes for +-J, 4 Npad^2
+ * for Gaussian; Npad = N rounded up to a multiple of 32), 5 bytes per spin of
+ * every chain (chains*Npad*5), 20 bytes per chain, the launch descriptors and
+ * the +-J weight table; a larger problem returns SK_ERR_INVALID_ARG with the
+ * size it would need (e.g. N = 512 Gaussian fits about 6,000 chains).
+ *
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture begins.  Every call reuses the same array, which
+ * keeps the previous call's contents; the call clears what must start at
+ * zero.  Calls that overlap on the GPU (from several host threads or
+ * streams) race on the array: serialise them.  The call returns when its work
+ * on `stream` has finished; a timed-out device wait gives SK_ERR_TIMEOUT.
+ */
+sk_status mcmcmc_run_noalloc(uint32_t N, uint32_t kind, const void* couplings, double scale,
+                             uint32_t chains, uint32_t K, uint32_t rule, double beta,
+                             uint64_t seed, uint32_t stream_id, uint64_t steps, int8_t* spins,
+                             double* energy, void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* sk_last_error(void);
 

@@ -95,6 +95,10 @@ std::vector<uint64_t> metropolis_table(double beta_eff, uint32_t N) {
 
 }  // namespace
 
+namespace sk {
+void set_error_message(const char* msg) { g_err = msg; }
+}  // namespace sk
+
 struct sk_instance {
     uint32_t N = 0, Npad = 0, kind = 0;
     double scale = 1.0;

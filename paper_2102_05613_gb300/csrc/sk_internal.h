@@ -65,4 +65,7 @@ cudaError_t launch_energy(const void* J, uint32_t kind, uint32_t N, uint32_t Npa
                           const int8_t* spins, uint32_t count, double* out, cudaStream_t st);
 int step_kernel_occupancy(int nb, uint32_t warps_per_cta, size_t smem_bytes);
 
+// Sets the message sk_last_error() returns on this thread (sk_capi.cu).
+void set_error_message(const char* msg);
+
 }  // namespace sk

@@ -30,7 +30,7 @@ EXPORTS = ["sk_create_instance", "sk_set_couplings", "sk_destroy_instance", "sk_
            "mcmcmc_create", "mcmcmc_advance", "mcmcmc_run", "mcmcmc_reset", "mcmcmc_wait",
            "mcmcmc_observables", "mcmcmc_state", "mcmcmc_trace", "mcmcmc_counters", "mcmcmc_free",
            "mcmcmc_batch_create", "mcmcmc_batch_advance", "mcmcmc_batch_info",
-           "mcmcmc_batch_free", "sk_last_error"]
+           "mcmcmc_batch_free", "mcmcmc_run_noalloc", "sk_last_error"]
 
 
 class SKError(RuntimeError):
@@ -81,6 +81,7 @@ def lib(build_if_missing: bool = True):
             "mcmcmc_batch_advance": [vp, u64],
             "mcmcmc_batch_info": [vp, vp, vp, vp, vp],
             "mcmcmc_batch_free": [vp],
+            "mcmcmc_run_noalloc": [u32, u32, vp, d, u32, u32, u32, d, u64, u32, u64, vp, vp, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -287,3 +288,17 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def run_noalloc(couplings, spins, energy, *, scale=1.0, K=8, rule=SK_RULE_MCMCMC, beta=1.0,
+                seed=1, stream_id=0, steps=0, stream=None):
+    """mcmcmc_run_noalloc: device couplings (N x N torch tensor, int8 or
+    float32), device spins (chains x N int8, updated in place) and a device
+    float64 energy vector (chains), all owned by the caller."""
+    N = int(couplings.shape[0])
+    kind = SK_J_PM1 if str(couplings.dtype) == "torch.int8" else SK_J_GAUSS
+    chains = int(spins.shape[0])
+    _check(lib().mcmcmc_run_noalloc(N, kind, C.c_void_p(couplings.data_ptr()), float(scale), chains,
+                                    int(K), int(rule), float(beta), int(seed), int(stream_id),
+                                    int(steps), C.c_void_p(spins.data_ptr()),
+                                    C.c_void_p(energy.data_ptr()), _stream_handle(stream)))
