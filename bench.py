@@ -191,7 +191,7 @@ def run_ours(args):
     insts = [sk.Instance(J, stream=stream) for J in couplings]
     runs = [sk.Run(inst, chains=CHAINS, K=K, beta=BETA, seed=1 + rank, stream_id=i,
                    record_every=R, max_records=cap) for i, inst in enumerate(insts)]
-    batch = sk.Batch(runs)
+    batch = sk.Batch(runs, warps_per_cta=args.warps_per_cta)
     info = batch.info()
 
     def barrier():
@@ -227,32 +227,39 @@ def run_ours(args):
     value = world * chain_steps_rank * K / T
     mc_steps = world * chain_steps_rank / T
 
-    # algorithmic bytes of one launch: J rows the steps needed (N x 4 B each),
-    # the s/h gathers of the K candidates (1 + 4 B each), the field updates
-    # (read + write 4 B per spin per flipped spin) and the state streamed in
-    # and out once per launch (5 B per spin each way)
+    # ALU roofline of the step kernel.  Algorithmic lane-operations of one
+    # chain-step (MCMCMC, K proposals, N spins, f = measured spins flipped per
+    # step, r = J rows the steps needed):
+    #   Philox4x32-10 draws  (ceil(K/4) + 1/32) blocks x 84  (10 rounds x 8 ops
+    #                         + 4 range reductions)
+    #   candidate energies    4 K
+    #   min + weights         4 (K + 1)   (compare, subtract, scale, 2^x)
+    #   prefix sum + choice   2 (K + 1)
+    #   field update          f N          (one FMA per spin per flipped spin)
+    # against 152 SMs x 128 lanes x the maximum SM clock.
     flips = sum(b[0] - a[0] for a, b in zip(c0, c1))
     rows = sum(b[1] - a[1] for a, b in zip(c0, c1))
     cs = INSTANCES * CHAINS * R * args.steps
     rows_ps, flips_ps = rows / cs, flips / cs
-    bytes_ps = rows_ps * N * 4 + K * 5 + flips_ps * N * 8
-    state_bytes = INSTANCES * CHAINS * N * 5 * 2
-    alg_bytes_launch = bytes_ps * INSTANCES * CHAINS * R + state_bytes
+    ops_ps = (math.ceil(K / 4) + 1 / 32) * 84 + 4 * K + 6 * (K + 1) + flips_ps * N
+    ops_launch = ops_ps * INSTANCES * CHAINS * R
     mean_launch_s = statistics.mean(launch_ms) / 1e3
     peaks = {}
     pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk_path):
         peaks = json.load(open(pk_path))
-    hbm_peak = peaks.get("hbm_gbs")
-    peak_src = "measured"
-    if hbm_peak is None:
-        hbm_peak, peak_src = 6800.0, "fallback"
-    achieved = alg_bytes_launch / mean_launch_s / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
-                "kernel": "step_kernel",
-                "bytes_per_chain_step": bytes_ps, "J_rows_per_chain_step": rows_ps,
-                "flips_per_chain_step": flips_ps}
+    sm_clock = peaks.get("sm_max_mhz") or 2070.0
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    alu_peak = sms * 128 * sm_clock * 1e6 / 1e12  # T lane-ops/s
+    achieved = ops_launch / mean_launch_s / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
+                "frac": achieved / alu_peak, "traffic": None,
+                "peak_source": f"{sms} SMs x 128 lanes x {sm_clock:.0f} MHz (max SM clock, "
+                               f"MEASURED_PEAKS.json)",
+                "kernel": "step_kernel", "ops_per_chain_step": ops_ps,
+                "J_rows_per_chain_step": rows_ps, "flips_per_chain_step": flips_ps,
+                "J_bytes_per_chain_step": rows_ps * N * 4,
+                "mean_launch_ms": 1e3 * mean_launch_s}
 
     # end to end through the C ABI from pinned host buffers: upload the 64
     # coupling matrices and the 262,144 start configurations, run 100 steps,
@@ -325,6 +332,8 @@ def main():
     ap.add_argument("--instances", type=int, default=INSTANCES,
                     help="smaller cases for profiling only; the bench line uses the default")
     ap.add_argument("--chains", type=int, default=CHAINS)
+    ap.add_argument("--warps-per-cta", type=int, default=0,
+                    help="chains (warps) per CTA; 0 = the library's choice")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -107,12 +107,16 @@ struct sk_instance {
 };
 
 struct sk_batch {
+    struct Class {
+        int cls;
+        uint32_t first_item, n_items, grid;
+    };
     std::vector<sk_run*> runs;
+    std::vector<Class> classes;  // one step-kernel launch per class present
     JobDev* djobs = nullptr;
     WorkItem* ditems = nullptr;
-    uint32_t* dqueue = nullptr;
+    uint32_t* dqueue = nullptr;  // one work counter per class
     uint32_t n_items = 0, W = 0, per_warp = 0, grid = 0;
-    int nb = 1;
     cudaStream_t st = nullptr;
 };
 
@@ -539,12 +543,10 @@ sk_status mcmcmc_batch_create(sk_run* const* runs, uint32_t n, uint32_t W, sk_ba
         return fail(SK_ERR_INVALID_ARG, "warps_per_cta = %u must be even in 2..32", W);
     cudaStream_t st = runs[0]->inst->st;
     size_t per_warp = 0;
-    uint32_t maxK = 1;
     for (uint32_t i = 0; i < n; ++i) {
         if (!runs[i]) return fail(SK_ERR_INVALID_ARG, "run %u is NULL", i);
         if (runs[i]->inst->st != st) return fail(SK_ERR_INVALID_ARG, "runs of a batch must share a stream");
         per_warp = std::max(per_warp, sk::warp_smem_bytes(runs[i]->inst->Npad, runs[i]->inst->kind));
-        if (runs[i]->p.rule == SK_RULE_MCMCMC) maxK = std::max(maxK, runs[i]->p.K);
     }
     per_warp = (per_warp + 127) / 128 * 128;
     const uint32_t fit = static_cast<uint32_t>(std::min<size_t>(32, kSmemBudget / per_warp)) & ~1u;
@@ -556,28 +558,38 @@ sk_status mcmcmc_batch_create(sk_run* const* runs, uint32_t n, uint32_t W, sk_ba
     b->runs.assign(runs, runs + n);
     b->W = W;
     b->per_warp = static_cast<uint32_t>(per_warp);
-    b->nb = maxK > 128 ? 2 : 1;
     b->st = st;
     std::vector<JobDev> jobs(n);
     std::vector<WorkItem> items;
-    for (uint32_t i = 0; i < n; ++i) {
-        jobs[i] = runs[i]->job;
-        for (uint32_t c = 0; c < runs[i]->chains; c += W)
-            items.push_back(WorkItem{i, c, std::min(W, runs[i]->chains - c), 0});
-    }
-    b->n_items = static_cast<uint32_t>(items.size());
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int occ = sk::step_kernel_occupancy(b->nb, W, per_warp * W);
-    if (occ <= 0) {
-        delete b;
-        return fail(SK_ERR_CUDA, "step kernel cannot be resident with %u warps and %zu bytes", W, per_warp * W);
+    for (uint32_t i = 0; i < n; ++i) jobs[i] = runs[i]->job;
+    // items grouped by kernel class, runs in the given order within a class
+    for (int cls = 0; cls < 8; ++cls) {
+        const uint32_t first = static_cast<uint32_t>(items.size());
+        for (uint32_t i = 0; i < n; ++i) {
+            const sk_run* r = runs[i];
+            if (sk::step_class(r->inst->kind, r->p.rule, r->p.K) != cls) continue;
+            for (uint32_t c = 0; c < r->chains; c += W)
+                items.push_back(WorkItem{i, c, std::min(W, r->chains - c), 0});
+        }
+        const uint32_t cnt = static_cast<uint32_t>(items.size()) - first;
+        if (!cnt) continue;
+        const int occ = sk::step_kernel_occupancy(cls, W, per_warp * W);
+        if (occ <= 0) {
+            delete b;
+            return fail(SK_ERR_CUDA, "step kernel cannot be resident with %u warps and %zu bytes", W,
+                        per_warp * W);
+        }
+        const uint32_t grid = std::min<uint32_t>(cnt, static_cast<uint32_t>(occ * sms));
+        b->classes.push_back(sk_batch::Class{cls, first, cnt, grid});
+        b->grid = std::max(b->grid, grid);
     }
-    b->grid = std::min<uint32_t>(b->n_items, static_cast<uint32_t>(occ * sms));
+    b->n_items = static_cast<uint32_t>(items.size());
     sk_status s = dalloc(&b->djobs, n * sizeof(JobDev));
     if (s == SK_OK) s = dalloc(&b->ditems, items.size() * sizeof(WorkItem));
-    if (s == SK_OK) s = dalloc(&b->dqueue, sizeof(uint32_t));
+    if (s == SK_OK) s = dalloc(&b->dqueue, 8 * sizeof(uint32_t));
     if (s == SK_OK) {
         cudaError_t e = cudaMemcpy(b->djobs, jobs.data(), n * sizeof(JobDev), cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
@@ -601,9 +613,14 @@ sk_status mcmcmc_batch_advance(sk_batch* b, uint64_t steps) {
     for (sk_run* r : b->runs)
         if (r->step + steps > 0xFFFFFFFFull)
             return fail(SK_ERR_INVALID_ARG, "a run would pass 2^32 steps");
-    cudaError_t e = sk::launch_step(b->djobs, b->ditems, b->n_items, b->dqueue, steps, b->W, b->per_warp,
-                                    b->grid, b->nb, static_cast<uint32_t>(b->runs.size()), b->st);
-    if (e != cudaSuccess) return fail(SK_ERR_CUDA, "step launch: %s", cudaGetErrorString(e));
+    for (size_t k = 0; k < b->classes.size(); ++k) {
+        const sk_batch::Class& c = b->classes[k];
+        cudaError_t e = sk::launch_step(b->djobs, b->ditems + c.first_item, c.n_items, b->dqueue + k, steps,
+                                        b->W, b->per_warp, c.grid, c.cls,
+                                        static_cast<uint32_t>(b->runs.size()), k + 1 == b->classes.size(),
+                                        b->st);
+        if (e != cudaSuccess) return fail(SK_ERR_CUDA, "step launch: %s", cudaGetErrorString(e));
+    }
     for (sk_run* r : b->runs) r->step += steps;
     return SK_OK;
 }

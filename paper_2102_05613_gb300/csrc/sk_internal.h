@@ -55,15 +55,21 @@ inline size_t warp_smem_bytes(uint32_t npad, uint32_t kind) {
 }
 
 // Kernel launchers (sk_kernels.cu).  All return cudaGetLastError().
+//
+// The step kernel is instantiated per class = step_class(kind, rule, K): the
+// coupling type, the rule, and whether K needs two Philox blocks per lane
+// (K > 128).  launch_step runs the items of one class; `bump` advances every
+// job's step counter by nsteps afterwards (set it on the last class).
+int step_class(uint32_t kind, uint32_t rule, uint32_t K);
 cudaError_t launch_step(const JobDev* jobs, const WorkItem* items, uint32_t n_items,
                         uint32_t* queue, uint64_t nsteps, uint32_t warps_per_cta,
-                        uint32_t per_warp_bytes, uint32_t grid, int nb,
-                        uint32_t n_jobs, cudaStream_t st);
+                        uint32_t per_warp_bytes, uint32_t grid, int cls, uint32_t n_jobs,
+                        bool bump, cudaStream_t st);
+int step_kernel_occupancy(int cls, uint32_t warps_per_cta, size_t smem_bytes);
 cudaError_t launch_init(const JobDev* job, const int8_t* init, uint32_t chains, uint32_t N,
                         uint32_t Npad, uint32_t kind, cudaStream_t st);
 cudaError_t launch_energy(const void* J, uint32_t kind, uint32_t N, uint32_t Npad, double scale,
                           const int8_t* spins, uint32_t count, double* out, cudaStream_t st);
-int step_kernel_occupancy(int nb, uint32_t warps_per_cta, size_t smem_bytes);
 
 // Sets the message sk_last_error() returns on this thread (sk_capi.cu).
 void set_error_message(const char* msg);

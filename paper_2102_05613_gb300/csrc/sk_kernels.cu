@@ -161,18 +161,18 @@ struct WarpMem {
 };
 
 // Block 0 of each step, computed for 32 consecutive steps at once (lane l
-// holds the step base + l) and broadcast by shuffle.
+// holds the step base + l) and broadcast by shuffle.  Steps are 32-bit.
 struct Block0 {
     uint4 v;
-    uint64_t base;
+    uint32_t base;
     bool valid;
 };
-__device__ __forceinline__ uint4 block0(Block0& c, uint64_t t, uint32_t chain, uint32_t c3,
+__device__ __forceinline__ uint4 block0(Block0& c, uint32_t t, uint32_t chain, uint32_t c3,
                                         uint32_t k0, uint32_t k1, int lane) {
     if (!c.valid || t - c.base >= 32u) {
-        c.base = t & ~31ull;
+        c.base = t & ~31u;
         c.valid = true;
-        c.v = philox4x32_10(make_uint4(0u, static_cast<uint32_t>(c.base) + lane, chain, c3), k0, k1);
+        c.v = philox4x32_10(make_uint4(0u, c.base + lane, chain, c3), k0, k1);
     }
     const int src = static_cast<int>(t - c.base);
     return make_uint4(__shfl_sync(kFull, c.v.x, src), __shfl_sync(kFull, c.v.y, src),
@@ -181,14 +181,14 @@ __device__ __forceinline__ uint4 block0(Block0& c, uint64_t t, uint32_t chain, u
 
 // Sites of step t held by this lane: slots d = 128 g + 4 lane + e + 1.
 template <int NB>
-__device__ __forceinline__ void draw_sites(uint32_t (&site)[4 * NB], uint64_t t, uint32_t chain,
+__device__ __forceinline__ void draw_sites(uint32_t (&site)[4 * NB], uint32_t t, uint32_t chain,
                                            uint32_t c3, uint32_t k0, uint32_t k1, uint32_t nblk,
                                            uint32_t N, int lane) {
 #pragma unroll
     for (int g = 0; g < NB; ++g) {
         const uint32_t b = 1u + 32u * g + lane;
         uint4 r = make_uint4(0u, 0u, 0u, 0u);
-        if (b <= nblk) r = philox4x32_10(make_uint4(b, static_cast<uint32_t>(t), chain, c3), k0, k1);
+        if (b <= nblk) r = philox4x32_10(make_uint4(b, t, chain, c3), k0, k1);
         site[4 * g + 0] = __umulhi(r.x, N);
         site[4 * g + 1] = __umulhi(r.y, N);
         site[4 * g + 2] = __umulhi(r.z, N);
@@ -196,21 +196,30 @@ __device__ __forceinline__ void draw_sites(uint32_t (&site)[4 * NB], uint64_t t,
     }
 }
 
+// 2^x on the special-function unit (ex2.approx.ftz: relative error < 2^-22
+// over the range used here, x <= 0).  exp(-beta dE) = 2^(-beta log2(e) dE).
+__device__ __forceinline__ float pow2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // h_k -= c1 J[x1][k] (+ c2 J[x2][k]) for k < Npad; lane l owns elements
-// 4l + 128v.  Row 1 may be in shared memory (staged) or global memory.
-template <typename JT>
+// 4l + 128v.  r1 is the staged row (shared memory) when STAGED, else a row of
+// J in global memory; r2 (the second flip of a double move) is global.
+template <typename JT, bool STAGED, bool TWO>
 __device__ __forceinline__ void update_fields(typename Types<JT>::H* hf, const JT* r1, const JT* r2,
                                               int c1, int c2, uint32_t npad, int lane) {
-    using H = typename Types<JT>::H;
     for (uint32_t k = 4u * lane; k < npad; k += 128u) {
         if constexpr (sizeof(JT) == 1) {
             int4 hv = *reinterpret_cast<int4*>(hf + k);
-            const uint32_t j1 = *reinterpret_cast<const uint32_t*>(r1 + k);
+            const uint32_t j1 = STAGED ? *reinterpret_cast<const uint32_t*>(r1 + k)
+                                       : __ldg(reinterpret_cast<const unsigned int*>(r1 + k));
             hv.x -= c1 * sbyte(j1, 0);
             hv.y -= c1 * sbyte(j1, 1);
             hv.z -= c1 * sbyte(j1, 2);
             hv.w -= c1 * sbyte(j1, 3);
-            if (r2) {
+            if constexpr (TWO) {
                 const uint32_t j2 = __ldg(reinterpret_cast<const unsigned int*>(r2 + k));
                 hv.x -= c2 * sbyte(j2, 0);
                 hv.y -= c2 * sbyte(j2, 1);
@@ -220,13 +229,14 @@ __device__ __forceinline__ void update_fields(typename Types<JT>::H* hf, const J
             *reinterpret_cast<int4*>(hf + k) = hv;
         } else {
             float4 hv = *reinterpret_cast<float4*>(hf + k);
-            const float4 j1 = *reinterpret_cast<const float4*>(r1 + k);
+            const float4 j1 = STAGED ? *reinterpret_cast<const float4*>(r1 + k)
+                                     : __ldg(reinterpret_cast<const float4*>(r1 + k));
             const float f1 = static_cast<float>(c1);
             hv.x = fmaf(-f1, j1.x, hv.x);
             hv.y = fmaf(-f1, j1.y, hv.y);
             hv.z = fmaf(-f1, j1.z, hv.z);
             hv.w = fmaf(-f1, j1.w, hv.w);
-            if (r2) {
+            if constexpr (TWO) {
                 const float4 j2 = __ldg(reinterpret_cast<const float4*>(r2 + k));
                 const float f2 = static_cast<float>(c2);
                 hv.x = fmaf(-f2, j2.x, hv.x);
@@ -236,20 +246,18 @@ __device__ __forceinline__ void update_fields(typename Types<JT>::H* hf, const J
             }
             *reinterpret_cast<float4*>(hf + k) = hv;
         }
-        (void)sizeof(H);
     }
 }
 
 // E = -scale/2 sum_k s_k h_k of the warp's chain.
 template <typename JT>
-__device__ __forceinline__ double chain_energy(const WarpMem& wm, uint32_t npad, double scale,
-                                               int lane) {
-    using H = typename Types<JT>::H;
-    const H* hf = static_cast<const H*>(wm.h);
+__device__ __forceinline__ double chain_energy(const int8_t* S, const void* h, uint32_t npad,
+                                               double scale, int lane) {
     if constexpr (sizeof(JT) == 1) {
+        const int* hf = static_cast<const int*>(h);
         int acc = 0;
         for (uint32_t k = 4u * lane; k < npad; k += 128u) {
-            const uint32_t sw = *reinterpret_cast<const uint32_t*>(wm.s + k);
+            const uint32_t sw = *reinterpret_cast<const uint32_t*>(S + k);
             const int4 hv = *reinterpret_cast<const int4*>(hf + k);
             acc += sbyte(sw, 0) * hv.x + sbyte(sw, 1) * hv.y + sbyte(sw, 2) * hv.z +
                    sbyte(sw, 3) * hv.w;
@@ -257,9 +265,10 @@ __device__ __forceinline__ double chain_energy(const WarpMem& wm, uint32_t npad,
         const int tot = warp_sum(acc);  // = 2 sum_{i<j} J s s, even
         return scale * static_cast<double>(-(tot / 2));
     } else {
+        const float* hf = static_cast<const float*>(h);
         double acc = 0.0;
         for (uint32_t k = 4u * lane; k < npad; k += 128u) {
-            const uint32_t sw = *reinterpret_cast<const uint32_t*>(wm.s + k);
+            const uint32_t sw = *reinterpret_cast<const uint32_t*>(S + k);
             const float4 hv = *reinterpret_cast<const float4*>(hf + k);
             acc += static_cast<double>(sbyte(sw, 0)) * hv.x + static_cast<double>(sbyte(sw, 1)) * hv.y +
                    static_cast<double>(sbyte(sw, 2)) * hv.z + static_cast<double>(sbyte(sw, 3)) * hv.w;
@@ -270,29 +279,30 @@ __device__ __forceinline__ double chain_energy(const WarpMem& wm, uint32_t npad,
 
 // Record point shared by every warp of the CTA (two CTA barriers).
 template <typename JT>
-__device__ void record(const JobDev& jb, bool active, uint32_t chain, uint64_t rec,
-                       const WarpMem& wm, const int8_t* partner_s, uint32_t& acc, int lane) {
+__device__ __noinline__ void record(const JobDev& jb, bool active, uint32_t chain, uint32_t rec,
+                                    const int8_t* S, const void* h, const int8_t* partner_s,
+                                    uint32_t acc) {
+    const int lane = threadIdx.x & 31;
     const bool store = rec < jb.rec_capacity;
     if (active) {
-        const double E = chain_energy<JT>(wm, jb.Npad, jb.scale, lane);
+        const double E = chain_energy<JT>(S, h, jb.Npad, jb.scale, lane);
         if (store && lane == 0) {
-            jb.rec_E[rec * jb.chains + chain] = E;
-            jb.rec_acc[rec * jb.chains + chain] = acc;
+            jb.rec_E[static_cast<size_t>(rec) * jb.chains + chain] = E;
+            jb.rec_acc[static_cast<size_t>(rec) * jb.chains + chain] = acc;
         }
-        acc = 0;
     }
     __syncthreads();
     if (active && store && (chain & 1u) == 0u && chain + 1u < jb.chains) {
         int dot = 0;
         for (uint32_t k = 4u * lane; k < jb.Npad; k += 128u) {
-            const uint32_t a = *reinterpret_cast<const uint32_t*>(wm.s + k);
+            const uint32_t a = *reinterpret_cast<const uint32_t*>(S + k);
             const uint32_t b = *reinterpret_cast<const uint32_t*>(partner_s + k);
             dot += sbyte(a, 0) * sbyte(b, 0) + sbyte(a, 1) * sbyte(b, 1) + sbyte(a, 2) * sbyte(b, 2) +
                    sbyte(a, 3) * sbyte(b, 3);
         }
         dot = warp_sum(dot);
         if (lane == 0)
-            jb.rec_q[rec * (jb.chains / 2) + chain / 2] =
+            jb.rec_q[static_cast<size_t>(rec) * (jb.chains / 2) + chain / 2] =
                 static_cast<double>(dot) / static_cast<double>(jb.N);
     }
     __syncthreads();
@@ -301,29 +311,37 @@ __device__ void record(const JobDev& jb, bool active, uint32_t chain, uint64_t r
 // Steps t0..t1-1 of one chain.  `dead` is set after a timed-out wait: the
 // warp then stops working but still meets the CTA's record barriers.
 template <typename JT, int RULE, int NB>
-__device__ void chain_loop(const JobDev& jb, bool active, uint32_t chain, const WarpMem& wm,
-                           const int8_t* partner_s, uint64_t t0, uint64_t t1, uint32_t& acc,
-                           uint32_t& phase, bool& dead, uint32_t& n_flips, uint32_t& n_rows) {
+__device__ __forceinline__ void chain_loop(const JobDev& jb, bool active, uint32_t chain,
+                                           const WarpMem& wm, const int8_t* partner_s, uint32_t t0,
+                                           uint32_t t1, uint32_t& acc, uint32_t& phase, bool& dead,
+                                           uint32_t& n_flips, uint32_t& n_rows) {
     using H = typename Types<JT>::H;
     using W = typename Types<JT>::W;
     const int lane = threadIdx.x & 31;
     const uint32_t R = jb.record_every;
+    // next record point (step count after which a record falls) and its index
+    uint32_t next_rec = R ? (t0 / R + 1u) * R : 0xFFFFFFFFu;
+    uint32_t rec_idx = R ? t0 / R : 0u;
     if (!active) {
-        if (R) {
-            for (uint64_t p = (t0 / R + 1) * R; p <= t1; p += R)
-                record<JT>(jb, false, chain, p / R - 1, wm, partner_s, acc, lane);
-        }
+        for (; R && next_rec <= t1; next_rec += R, ++rec_idx)
+            record<JT>(jb, false, chain, rec_idx, wm.s, wm.h, partner_s, 0u);
         return;
     }
+    // job parameters held in registers for the whole loop
     const uint32_t N = jb.N, npad = jb.Npad, K = jb.K;
     const uint32_t nblk = (K + 3u) >> 2;
     const uint32_t k0 = static_cast<uint32_t>(jb.seed), k1 = static_cast<uint32_t>(jb.seed >> 32);
     const uint32_t c3 = jb.stream & 0xFFFFFFu;  // domain 0: step draws
-    const JT* Jg = static_cast<const JT*>(jb.J);
+    const JT* __restrict__ Jg = static_cast<const JT*>(jb.J);
+    const uint32_t rowbytes = npad * static_cast<uint32_t>(sizeof(JT));
+    const W* __restrict__ Wt = reinterpret_cast<const W*>(jb.W);
+    const uint32_t wlen = jb.wlen;
+    const float nbl2 = -jb.beta_eff * 1.4426950408889634f;  // -beta log2(e)
+    int32_t* trace = (chain < jb.trace_chains) ? jb.trace + static_cast<size_t>(chain) * jb.trace_steps
+                                               : nullptr;
+    const uint32_t trace_end = trace ? static_cast<uint32_t>(jb.trace_steps) : 0u;
     int8_t* S = wm.s;
     H* hf = static_cast<H*>(wm.h);
-    const uint32_t rowbytes = npad * static_cast<uint32_t>(sizeof(JT));
-    const W* Wt = reinterpret_cast<const W*>(jb.W);
 
     Block0 bc;
     bc.valid = false;
@@ -339,35 +357,35 @@ __device__ void chain_loop(const JobDev& jb, bool active, uint32_t chain, const 
     }
     if (lane == 0 && !dead) {
         fence_proxy_async();
-        bulk_load(wm.row[t0 & 1], Jg + static_cast<size_t>(first) * npad, rowbytes,
-                  &wm.bar[t0 & 1]);
+        bulk_load(wm.row[t0 & 1u], Jg + static_cast<size_t>(first) * npad, rowbytes,
+                  &wm.bar[t0 & 1u]);
     }
 
-    for (uint64_t t = t0; t < t1; ++t) {
-        const int buf = static_cast<int>(t & 1);
+    for (uint32_t t = t0; t < t1; ++t) {
+        const uint32_t buf = t & 1u;
         const uint4 b0 = block0(bc, t, chain, c3, k0, k1, lane);
         const unsigned long long U1 = (static_cast<unsigned long long>(b0.w) << 32) | b0.z;
-        int sel = 0;        // slot chosen (Metropolis: accepted)
+        int sel = 0;  // slot chosen (Metropolis: accepted)
         int nflip = 0;
-        int rows = 0;       // J rows this step needs: row a of a leaf root, flipped spins' rows
+        int rows = 0;  // J rows this step needs: row a of a leaf root, flipped spins' rows
         uint32_t x1 = 0, x2 = 0;
         bool x1_staged = false;
 
         // stage the row the next step needs first
-        uint32_t nsite[4 * NB] = {};
-        if (t + 1 < t1) {
+        uint32_t nsite[4 * NB];
+        if (t + 1u < t1) {
             uint32_t nx;
             if constexpr (RULE == 0) {
-                draw_sites<NB>(nsite, t + 1, chain, c3, k0, k1, nblk, N, lane);
+                draw_sites<NB>(nsite, t + 1u, chain, c3, k0, k1, nblk, N, lane);
                 nx = __shfl_sync(kFull, nsite[0], 0);
             } else {
-                nx = __umulhi(block0(bc, t + 1, chain, c3, k0, k1, lane).x, N);
+                nx = __umulhi(block0(bc, t + 1u, chain, c3, k0, k1, lane).x, N);
             }
             __syncwarp();  // every lane is done with buffer buf^1 (step t-1)
             if (lane == 0 && !dead) {
                 fence_proxy_async();
-                bulk_load(wm.row[buf ^ 1], Jg + static_cast<size_t>(nx) * npad, rowbytes,
-                          &wm.bar[buf ^ 1]);
+                bulk_load(wm.row[buf ^ 1u], Jg + static_cast<size_t>(nx) * npad, rowbytes,
+                          &wm.bar[buf ^ 1u]);
             }
         }
         if (!dead) {
@@ -390,10 +408,9 @@ __device__ void chain_loop(const JobDev& jb, bool active, uint32_t chain, const 
                 bool accept;
                 if constexpr (sizeof(JT) == 1) {
                     const uint32_t k = static_cast<uint32_t>(dE) >> 1;
-                    accept = dE <= 0 || (k < jb.wlen && (U1 >> 11) < __ldg(&jb.W[k]));
+                    accept = dE <= 0 || (k < wlen && (U1 >> 11) < __ldg(&Wt[k]));
                 } else {
-                    accept = dE <= 0.0f ||
-                             static_cast<float>(U1 >> 40) * 0x1p-24f < expf(-jb.beta_eff * dE);
+                    accept = dE <= 0.0f || static_cast<float>(U1 >> 40) * 0x1p-24f < pow2(nbl2 * dE);
                 }
                 sel = accept ? 1 : 0;
                 if (accept) {
@@ -444,9 +461,9 @@ __device__ void chain_loop(const JobDev& jb, bool active, uint32_t chain, const 
                     if (d <= K) {
                         if constexpr (sizeof(JT) == 1) {
                             const uint32_t idx = static_cast<uint32_t>(dE[q] - m) >> 1;
-                            x = idx < jb.wlen ? __ldg(&Wt[idx]) : 0ull;
+                            x = idx < wlen ? __ldg(&Wt[idx]) : 0ull;
                         } else {
-                            x = expf(-jb.beta_eff * (dE[q] - m));
+                            x = pow2(nbl2 * (dE[q] - m));
                         }
                     }
                     w[q] = x;
@@ -455,9 +472,9 @@ __device__ void chain_loop(const JobDev& jb, bool active, uint32_t chain, const 
                 W w0;
                 if constexpr (sizeof(JT) == 1) {
                     const uint32_t idx0 = static_cast<uint32_t>(-m) >> 1;
-                    w0 = idx0 < jb.wlen ? __ldg(&Wt[idx0]) : 0ull;
+                    w0 = idx0 < wlen ? __ldg(&Wt[idx0]) : 0ull;
                 } else {
-                    w0 = expf(jb.beta_eff * m);
+                    w0 = pow2(-nbl2 * m);
                 }
                 W incl[NB], tot[NB];
                 W total = w0;
@@ -535,9 +552,14 @@ __device__ void chain_loop(const JobDev& jb, bool active, uint32_t chain, const 
             if (nflip) {
                 const int c1 = 2 * S[x1];
                 const int c2 = nflip == 2 ? 2 * S[x2] : 0;
-                const JT* r1 = x1_staged ? rowA : Jg + static_cast<size_t>(x1) * npad;
-                const JT* r2 = nflip == 2 ? Jg + static_cast<size_t>(x2) * npad : nullptr;
-                update_fields<JT>(hf, r1, r2, c1, c2, npad, lane);
+                const JT* g1 = Jg + static_cast<size_t>(x1) * npad;
+                const JT* g2 = Jg + static_cast<size_t>(x2) * npad;
+                if (nflip == 2)
+                    update_fields<JT, true, true>(hf, rowA, g2, c1, c2, npad, lane);
+                else if (x1_staged)
+                    update_fields<JT, true, false>(hf, rowA, nullptr, c1, 0, npad, lane);
+                else
+                    update_fields<JT, false, false>(hf, g1, nullptr, c1, 0, npad, lane);
                 __syncwarp();
                 if (lane == 0) {
                     S[x1] = static_cast<int8_t>(-S[x1]);
@@ -547,23 +569,28 @@ __device__ void chain_loop(const JobDev& jb, bool active, uint32_t chain, const 
             }
             n_flips += static_cast<uint32_t>(nflip);
             n_rows += static_cast<uint32_t>(rows);
-            if (chain < jb.trace_chains && t < jb.trace_steps && lane == 0)
-                jb.trace[static_cast<size_t>(chain) * jb.trace_steps + t] = sel;
+            if (t < trace_end && lane == 0) trace[t] = sel;
             __syncwarp();
         }
         if constexpr (RULE == 0) {
 #pragma unroll
             for (int q = 0; q < 4 * NB; ++q) site[q] = nsite[q];
         }
-        if (R && ((t + 1) % R) == 0)
-            record<JT>(jb, !dead, chain, (t + 1) / R - 1, wm, partner_s, acc, lane);
+        if (t + 1u == next_rec) {
+            record<JT>(jb, !dead, chain, rec_idx, S, hf, partner_s, acc);
+            acc = 0;
+            next_rec += R;
+            ++rec_idx;
+        }
     }
 }
 
-template <int NB>
-__global__ void __launch_bounds__(1024, 1)
+// MAXT bounds the CTA size and so sets the register budget per thread
+// (65536 / MAXT): 1024 -> 64, 640 -> 96, 512 -> 128 registers.
+template <typename JT, int RULE, int NB, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1)
     step_kernel(const JobDev* __restrict__ jobs, const WorkItem* __restrict__ items,
-                uint32_t n_items, uint32_t* __restrict__ queue, uint64_t nsteps,
+                uint32_t n_items, uint32_t* __restrict__ queue, uint32_t nsteps,
                 uint32_t per_warp) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(16) JobDev s_job;
@@ -578,6 +605,7 @@ __global__ void __launch_bounds__(1024, 1)
     __syncthreads();
     uint32_t phase = 0;
     bool dead = false;  // a bounded wait of this warp expired: skip all further work
+    constexpr size_t bj = sizeof(JT);
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(queue, 1u);
         __syncthreads();
@@ -592,7 +620,6 @@ __global__ void __launch_bounds__(1024, 1)
         const bool active = static_cast<uint32_t>(warp) < wi.nchains;
         const uint32_t chain = wi.chain0 + warp;
         const uint32_t npad = jb.Npad;
-        const size_t bj = jb.kind == 0 ? 1 : 4;
         WarpMem wm;
         unsigned char* base = smem + static_cast<size_t>(warp) * per_warp;
         wm.s = reinterpret_cast<int8_t*>(base);
@@ -600,9 +627,10 @@ __global__ void __launch_bounds__(1024, 1)
         wm.row[0] = base + 5 * static_cast<size_t>(npad);
         wm.row[1] = base + (5 + bj) * static_cast<size_t>(npad);
         wm.bar = &bars[2 * warp];
-        const int8_t* partner_s = reinterpret_cast<const int8_t*>(smem + static_cast<size_t>(warp ^ 1) * per_warp);
-        const uint64_t t0 = *jb.step;
-        const uint64_t t1 = t0 + nsteps;
+        const int8_t* partner_s =
+            reinterpret_cast<const int8_t*>(smem + static_cast<size_t>(warp ^ 1) * per_warp);
+        const uint32_t t0 = static_cast<uint32_t>(*jb.step);
+        const uint32_t t1 = t0 + nsteps;
         uint32_t acc = 0, n_flips = 0, n_rows = 0;
         if (active) {
             // load the chain's state: spins (npad bytes), fields (4 npad bytes)
@@ -616,15 +644,9 @@ __global__ void __launch_bounds__(1024, 1)
             acc = jb.acc_run[chain];
         }
         __syncwarp();
-        if (nsteps) {
-            const int sel = static_cast<int>(jb.kind) * 2 + static_cast<int>(jb.rule);
-            switch (sel) {
-                case 0: chain_loop<int8_t, 0, NB>(jb, active, chain, wm, partner_s, t0, t1, acc, phase, dead, n_flips, n_rows); break;
-                case 1: chain_loop<int8_t, 1, NB>(jb, active, chain, wm, partner_s, t0, t1, acc, phase, dead, n_flips, n_rows); break;
-                case 2: chain_loop<float, 0, NB>(jb, active, chain, wm, partner_s, t0, t1, acc, phase, dead, n_flips, n_rows); break;
-                default: chain_loop<float, 1, NB>(jb, active, chain, wm, partner_s, t0, t1, acc, phase, dead, n_flips, n_rows); break;
-            }
-        }
+        if (nsteps)
+            chain_loop<JT, RULE, NB>(jb, active, chain, wm, partner_s, t0, t1, acc, phase, dead,
+                                     n_flips, n_rows);
         __syncwarp();
         if (active) {
             uint4* gs = reinterpret_cast<uint4*>(jb.s + static_cast<size_t>(chain) * npad);
@@ -649,44 +671,70 @@ __global__ void bump_steps(const JobDev* __restrict__ jobs, uint32_t n_jobs, uin
 }
 
 // Start state: spins from `init` (chains x N, +-1) or Philox domain 1
-// (128 spins per block, bit set -> -1); fields h_i = sum_j J_ji s_j.
+// (128 spins per block, bit set -> -1); fields h_i = sum_j J_ji s_j for
+// kInitChains chains per CTA (each J element read once for all of them),
+// exact integers for +-J, compensated (Kahan) float sums for Gaussian J.
+constexpr uint32_t kInitChains = 8;
+
 template <typename JT>
-__global__ void init_kernel(JobDev jb, const int8_t* __restrict__ init) {
+__global__ void __launch_bounds__(256) init_kernel(JobDev jb, const int8_t* __restrict__ init) {
     extern __shared__ __align__(16) unsigned char sm[];
-    int8_t* s = reinterpret_cast<int8_t*>(sm);
-    const uint32_t chain = blockIdx.x;
+    int8_t* s = reinterpret_cast<int8_t*>(sm);  // [kInitChains][npad]
     const uint32_t N = jb.N, npad = jb.Npad;
-    if (init) {
-        for (uint32_t i = threadIdx.x; i < npad; i += blockDim.x)
-            s[i] = i < N ? init[static_cast<size_t>(chain) * N + i] : 0;
-    } else {
-        const uint32_t k0 = static_cast<uint32_t>(jb.seed), k1 = static_cast<uint32_t>(jb.seed >> 32);
-        const uint32_t c3 = (1u << 24) | (jb.stream & 0xFFFFFFu);
-        for (uint32_t b = threadIdx.x; b * 128u < npad; b += blockDim.x) {
-            const uint4 r = philox4x32_10(make_uint4(b, 0u, chain, c3), k0, k1);
-            const uint32_t wv[4] = {r.x, r.y, r.z, r.w};
-            for (uint32_t k = 0; k < 128u && b * 128u + k < npad; ++k) {
-                const uint32_t i = b * 128u + k;
-                s[i] = i < N ? (((wv[k >> 5] >> (k & 31)) & 1u) ? -1 : 1) : 0;
+    const uint32_t c0 = blockIdx.x * kInitChains;
+    const uint32_t nc = min(kInitChains, jb.chains - c0);
+    for (uint32_t c = 0; c < nc; ++c) {
+        const uint32_t chain = c0 + c;
+        int8_t* sc = s + static_cast<size_t>(c) * npad;
+        if (init) {
+            for (uint32_t i = threadIdx.x; i < npad; i += blockDim.x)
+                sc[i] = i < N ? init[static_cast<size_t>(chain) * N + i] : 0;
+        } else {
+            const uint32_t k0 = static_cast<uint32_t>(jb.seed), k1 = static_cast<uint32_t>(jb.seed >> 32);
+            const uint32_t c3 = (1u << 24) | (jb.stream & 0xFFFFFFu);
+            for (uint32_t b = threadIdx.x; b * 128u < npad; b += blockDim.x) {
+                const uint4 r = philox4x32_10(make_uint4(b, 0u, chain, c3), k0, k1);
+                const uint32_t wv[4] = {r.x, r.y, r.z, r.w};
+                for (uint32_t k = 0; k < 128u && b * 128u + k < npad; ++k) {
+                    const uint32_t i = b * 128u + k;
+                    sc[i] = i < N ? (((wv[k >> 5] >> (k & 31)) & 1u) ? -1 : 1) : 0;
+                }
             }
         }
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < npad; i += blockDim.x)
-        jb.s[static_cast<size_t>(chain) * npad + i] = s[i];
+    for (uint32_t c = 0; c < nc; ++c)
+        for (uint32_t i = threadIdx.x; i < npad; i += blockDim.x)
+            jb.s[static_cast<size_t>(c0 + c) * npad + i] = s[static_cast<size_t>(c) * npad + i];
     const JT* J = static_cast<const JT*>(jb.J);
     for (uint32_t i = threadIdx.x; i < npad; i += blockDim.x) {
         if constexpr (sizeof(JT) == 1) {
-            int acc = 0;
-            for (uint32_t j = 0; j < N; ++j) acc += static_cast<int>(J[static_cast<size_t>(j) * npad + i]) * s[j];
-            static_cast<int*>(jb.h)[static_cast<size_t>(chain) * npad + i] = acc;
+            int acc[kInitChains] = {};
+            for (uint32_t j = 0; j < N; ++j) {
+                const int v = J[static_cast<size_t>(j) * npad + i];
+#pragma unroll
+                for (uint32_t c = 0; c < kInitChains; ++c) acc[c] += v * s[c * npad + j];
+            }
+            for (uint32_t c = 0; c < nc; ++c)
+                static_cast<int*>(jb.h)[static_cast<size_t>(c0 + c) * npad + i] = acc[c];
         } else {
-            double acc = 0.0;
-            for (uint32_t j = 0; j < N; ++j) acc += static_cast<double>(J[static_cast<size_t>(j) * npad + i]) * s[j];
-            static_cast<float*>(jb.h)[static_cast<size_t>(chain) * npad + i] = static_cast<float>(acc);
+            float sum[kInitChains] = {}, comp[kInitChains] = {};
+            for (uint32_t j = 0; j < N; ++j) {
+                const float v = J[static_cast<size_t>(j) * npad + i];
+#pragma unroll
+                for (uint32_t c = 0; c < kInitChains; ++c) {
+                    const float y = (s[c * npad + j] > 0 ? v : -v) - comp[c];
+                    const float tsum = sum[c] + y;
+                    comp[c] = (tsum - sum[c]) - y;
+                    sum[c] = tsum;
+                }
+            }
+            for (uint32_t c = 0; c < nc; ++c)
+                static_cast<float*>(jb.h)[static_cast<size_t>(c0 + c) * npad + i] = sum[c];
         }
     }
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < nc) {
+        const uint32_t chain = c0 + threadIdx.x;
         jb.acc_run[chain] = 0;
         jb.work[2 * static_cast<size_t>(chain)] = 0;
         jb.work[2 * static_cast<size_t>(chain) + 1] = 0;
@@ -719,49 +767,100 @@ __global__ void energy_kernel(const JT* __restrict__ J, uint32_t N, uint32_t npa
     }
 }
 
+template <typename JT, int RULE, int NB, int MAXT>
+cudaError_t launch_variant(const JobDev* jobs, const WorkItem* items, uint32_t n_items,
+                           uint32_t* queue, uint32_t nsteps, uint32_t W, uint32_t per_warp,
+                           uint32_t grid, cudaStream_t st) {
+    const size_t smem = static_cast<size_t>(per_warp) * W;
+    cudaError_t e = cudaFuncSetAttribute(step_kernel<JT, RULE, NB, MAXT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    step_kernel<JT, RULE, NB, MAXT><<<grid, 32 * W, smem, st>>>(jobs, items, n_items, queue, nsteps, per_warp);
+    return cudaGetLastError();
+}
+
+template <typename JT, int RULE, int NB, int MAXT>
+int occupancy_variant(uint32_t W, size_t smem) {
+    int n = 0;
+    if (cudaFuncSetAttribute(step_kernel<JT, RULE, NB, MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(smem)) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<JT, RULE, NB, MAXT>, 32 * W, smem) !=
+        cudaSuccess)
+        return 0;
+    return n;
+}
+
+// The register budget follows the CTA size: the largest variant that fits W warps.
+template <typename JT, int RULE, int NB>
+cudaError_t launch_class(const JobDev* jobs, const WorkItem* items, uint32_t n_items,
+                         uint32_t* queue, uint32_t nsteps, uint32_t W, uint32_t per_warp,
+                         uint32_t grid, cudaStream_t st) {
+    if (W <= 16) return launch_variant<JT, RULE, NB, 512>(jobs, items, n_items, queue, nsteps, W, per_warp, grid, st);
+    if (W <= 20) return launch_variant<JT, RULE, NB, 640>(jobs, items, n_items, queue, nsteps, W, per_warp, grid, st);
+    return launch_variant<JT, RULE, NB, 1024>(jobs, items, n_items, queue, nsteps, W, per_warp, grid, st);
+}
+
+template <typename JT, int RULE, int NB>
+int occupancy_class(uint32_t W, size_t smem) {
+    if (W <= 16) return occupancy_variant<JT, RULE, NB, 512>(W, smem);
+    if (W <= 20) return occupancy_variant<JT, RULE, NB, 640>(W, smem);
+    return occupancy_variant<JT, RULE, NB, 1024>(W, smem);
+}
+
 }  // namespace
 
 cudaError_t launch_step(const JobDev* jobs, const WorkItem* items, uint32_t n_items,
-                        uint32_t* queue, uint64_t nsteps, uint32_t warps_per_cta,
-                        uint32_t per_warp_bytes, uint32_t grid, int nb, uint32_t n_jobs,
-                        cudaStream_t st) {
-    const size_t smem = static_cast<size_t>(per_warp_bytes) * warps_per_cta;
+                        uint32_t* queue, uint64_t nsteps, uint32_t W, uint32_t per_warp,
+                        uint32_t grid, int cls, uint32_t n_jobs, bool bump, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
-    if (nb == 1) {
-        e = cudaFuncSetAttribute(step_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-        if (e != cudaSuccess) return e;
-        step_kernel<1><<<grid, 32 * warps_per_cta, smem, st>>>(jobs, items, n_items, queue, nsteps, per_warp_bytes);
-    } else {
-        e = cudaFuncSetAttribute(step_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-        if (e != cudaSuccess) return e;
-        step_kernel<2><<<grid, 32 * warps_per_cta, smem, st>>>(jobs, items, n_items, queue, nsteps, per_warp_bytes);
+    const uint32_t ns = static_cast<uint32_t>(nsteps);
+    switch (cls) {
+        case 0: e = launch_class<int8_t, 0, 1>(jobs, items, n_items, queue, ns, W, per_warp, grid, st); break;
+        case 1: e = launch_class<int8_t, 0, 2>(jobs, items, n_items, queue, ns, W, per_warp, grid, st); break;
+        case 2: e = launch_class<int8_t, 1, 1>(jobs, items, n_items, queue, ns, W, per_warp, grid, st); break;
+        case 4: e = launch_class<float, 0, 1>(jobs, items, n_items, queue, ns, W, per_warp, grid, st); break;
+        case 5: e = launch_class<float, 0, 2>(jobs, items, n_items, queue, ns, W, per_warp, grid, st); break;
+        case 6: e = launch_class<float, 1, 1>(jobs, items, n_items, queue, ns, W, per_warp, grid, st); break;
+        default: return cudaErrorInvalidValue;
     }
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess || !bump) return e;
     bump_steps<<<(n_jobs + 127) / 128, 128, 0, st>>>(jobs, n_jobs, nsteps);
     return cudaGetLastError();
 }
 
-int step_kernel_occupancy(int nb, uint32_t warps_per_cta, size_t smem_bytes) {
-    int n = 0;
-    if (nb == 1) {
-        cudaFuncSetAttribute(step_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_bytes));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<1>, 32 * warps_per_cta, smem_bytes);
-    } else {
-        cudaFuncSetAttribute(step_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_bytes));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<2>, 32 * warps_per_cta, smem_bytes);
+int step_kernel_occupancy(int cls, uint32_t W, size_t smem) {
+    switch (cls) {
+        case 0: return occupancy_class<int8_t, 0, 1>(W, smem);
+        case 1: return occupancy_class<int8_t, 0, 2>(W, smem);
+        case 2: return occupancy_class<int8_t, 1, 1>(W, smem);
+        case 4: return occupancy_class<float, 0, 1>(W, smem);
+        case 5: return occupancy_class<float, 0, 2>(W, smem);
+        case 6: return occupancy_class<float, 1, 1>(W, smem);
+        default: return 0;
     }
-    return n;
+}
+
+int step_class(uint32_t kind, uint32_t rule, uint32_t K) {
+    return static_cast<int>(kind) * 4 + (rule == 1 ? 2 : (K > 128 ? 1 : 0));
 }
 
 cudaError_t launch_init(const JobDev* job, const int8_t* init, uint32_t chains, uint32_t N,
                         uint32_t Npad, uint32_t kind, cudaStream_t st) {
     (void)N;
-    if (kind == 0)
-        init_kernel<int8_t><<<chains, 256, Npad, st>>>(*job, init);
-    else
-        init_kernel<float><<<chains, 256, Npad, st>>>(*job, init);
+    const uint32_t blocks = (chains + kInitChains - 1) / kInitChains;
+    const size_t sm = static_cast<size_t>(kInitChains) * Npad;
+    cudaError_t e;
+    if (kind == 0) {
+        e = cudaFuncSetAttribute(init_kernel<int8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
+        if (e != cudaSuccess) return e;
+        init_kernel<int8_t><<<blocks, 256, sm, st>>>(*job, init);
+    } else {
+        e = cudaFuncSetAttribute(init_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
+        if (e != cudaSuccess) return e;
+        init_kernel<float><<<blocks, 256, sm, st>>>(*job, init);
+    }
     return cudaGetLastError();
 }
 

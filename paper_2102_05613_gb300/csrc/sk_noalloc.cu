@@ -210,17 +210,17 @@ extern "C" sk_status mcmcmc_run_noalloc(uint32_t N, uint32_t kind, const void* c
     }
 
     NA_CU(sk::launch_init(&job, spins, chains, N, Npad, kind, st));
-    const int nb = (rule == SK_RULE_MCMCMC && K > 128) ? 2 : 1;
+    const int cls = sk::step_class(kind, rule, K);
     int dev = 0, sms = 0;
     NA_CU(cudaGetDevice(&dev));
     NA_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int occ = sk::step_kernel_occupancy(nb, W, per_warp * W);
+    const int occ = sk::step_kernel_occupancy(cls, W, per_warp * W);
     if (occ <= 0) return nfail(SK_ERR_CUDA, "step kernel cannot be resident");
     const uint32_t grid = std::min<uint32_t>(n_items, static_cast<uint32_t>(occ * sms));
     if (steps)
         NA_CU(sk::launch_step(reinterpret_cast<const sk::JobDev*>(base + o_job),
                               reinterpret_cast<const sk::WorkItem*>(base + o_items), n_items, queue,
-                              steps, W, static_cast<uint32_t>(per_warp), grid, nb, 1, st));
+                              steps, W, static_cast<uint32_t>(per_warp), grid, cls, 1, true, st));
     NA_CU(cudaMemcpy2DAsync(spins, N, base + o_s, Npad, N, chains, cudaMemcpyDeviceToDevice, st));
     NA_CU(sk::launch_energy(base + o_J, kind, N, Npad, scale, spins, chains, energy, st));
     int herr = 0;
