@@ -118,6 +118,10 @@ typedef struct {
     uint64_t trace_steps;   /*   each of their first trace_steps steps (debug)  */
     const int8_t* init_spins; /* chains*N start (+-1), or NULL: Philox start   */
     uint32_t init_mem;      /* sk_mem of init_spins                             */
+    uint32_t recompute_every; /* recompute the fields on the tensor cores after */
+                            /*   every M-th step (0 = never): +-J check, Gaussian */
+                            /*   resync (see mcmcmc_recompute)                  */
+    uint32_t recompute_terms; /* bf16 terms of the Gaussian J split, 1..3 (0=3) */
 } sk_run_params;
 
 /*
@@ -169,6 +173,42 @@ sk_status mcmcmc_observables(sk_run* run, uint64_t first, uint64_t count, double
  * the step counter (synchronises; spins/fields per mem, step a host pointer).
  */
 sk_status mcmcmc_state(sk_run* run, int8_t* spins, void* fields, uint64_t* step, uint32_t mem);
+
+/* ---------------------------------------------------------------------- */
+/* Field recompute on the tensor cores                                     */
+/* ---------------------------------------------------------------------- */
+typedef enum { SK_RECOMPUTE_CHECK = 0, SK_RECOMPUTE_RESYNC = 1, SK_RECOMPUTE_OUTPUT = 2 } sk_recompute_mode;
+
+typedef struct {
+    double max_field_drift;   /* max over chains and spins of |h_maintained - H|   */
+    double max_energy_drift;  /* max over chains of |E(h_maintained) - E(H)|,     */
+                              /*   E = -scale/2 sum_i s_i h_i                     */
+    uint64_t mismatches;      /* fields with h_maintained != H (+-J: must be 0)   */
+    uint64_t recomputes;      /* recomputes these figures cover                   */
+} sk_recompute_stats;
+
+/*
+ * mcmcmc_recompute: recomputes every chain's local fields H = J s (the
+ * definition h_i = sum_j J_ij s_j behind the energy of Sec. IV.A) as one
+ * matrix product on the tensor cores (tcgen05, TMA, tensor memory):
+ *   +-J:      spins and couplings as FP8 e4m3 (+-1, 0 exact), FP32
+ *             accumulation; exact, since every partial sum is an integer
+ *             below 2^24;
+ *   Gaussian: spins as bf16 (exact), J split into `terms` bf16 matrices
+ *             (1..3; three round-to-nearest terms reproduce fp32 J exactly),
+ *             all accumulated in FP32.
+ * mode SK_RECOMPUTE_CHECK compares H with the maintained fields;
+ * SK_RECOMPUTE_RESYNC also replaces the maintained fields by H;
+ * SK_RECOMPUTE_OUTPUT only writes H to fields_out (chains*N float32, mem).
+ * The comparison is done in double precision.  Synchronises; `stats` (host,
+ * may be NULL) receives this call's figures.
+ */
+sk_status mcmcmc_recompute(sk_run* run, uint32_t mode, uint32_t terms, sk_recompute_stats* stats,
+                           float* fields_out, uint32_t mem);
+
+/* Figures accumulated by the periodic recomputes (recompute_every) since
+ * the run's creation or last reset.  Synchronises. */
+sk_status mcmcmc_recompute_stats(sk_run* run, sk_recompute_stats* stats);
 
 /* mcmcmc_trace: copies the slot log (trace_chains*trace_steps int32; slot
  * 0..K for MCMCMC, 1/0 accepted/rejected for Metropolis). */

@@ -103,6 +103,8 @@ struct sk_instance {
     uint32_t N = 0, Npad = 0, kind = 0;
     double scale = 1.0;
     void* dJ = nullptr;
+    void* dJop = nullptr;   // couplings as tensor-core operands (built on first recompute)
+    bool jop_valid = false;
     cudaStream_t st = nullptr;
 };
 
@@ -136,6 +138,10 @@ struct sk_run {
     uint32_t wlen = 0;
     uint64_t* dstep = nullptr;
     int* derr = nullptr;
+    void* dSop = nullptr;                 // spins as tensor-core operands
+    double* ddE = nullptr;                // per chain energy drift accumulator
+    unsigned long long* dstats = nullptr; // [0..2] periodic recomputes, [3..5] last explicit one
+    uint64_t n_recomputes = 0;
     uint64_t step = 0;  // host mirror of the device step counter
     JobDev job{};
     sk_batch* self = nullptr;
@@ -175,6 +181,7 @@ sk_status validate_couplings(uint32_t N, uint32_t kind, const void* J) {
 
 sk_status upload_couplings(sk_instance* in, const void* J, uint32_t mem) {
     const size_t b = jbytes(in->kind);
+    in->jop_valid = false;
     if (mem == SK_MEM_HOST) {
         sk_status s = validate_couplings(in->N, in->kind, J);
         if (s != SK_OK) return s;
@@ -229,6 +236,8 @@ sk_status init_state(sk_run* r, const int8_t* spins, uint32_t mem) {
         SK_CU(cudaMemsetAsync(r->dtrace, 0xff, static_cast<size_t>(r->p.trace_chains) * r->p.trace_steps * 4,
                               in->st));
     SK_CU(sk::launch_init(&r->job, dinit, r->chains, in->N, in->Npad, in->kind, in->st));
+    if (r->dstats) SK_CU(cudaMemsetAsync(r->dstats, 0, 6 * sizeof(unsigned long long), in->st));
+    r->n_recomputes = 0;
     if (tmp) {
         SK_CU(cudaStreamSynchronize(in->st));
         cudaFree(tmp);
@@ -249,6 +258,45 @@ void free_run_buffers(sk_run* r) {
     cudaFree(r->dW);
     cudaFree(r->dstep);
     cudaFree(r->derr);
+    cudaFree(r->dSop);
+    cudaFree(r->ddE);
+    cudaFree(r->dstats);
+}
+
+// Operand buffers of the tensor-core recompute, allocated on first use.
+sk_status ensure_recompute(sk_run* r) {
+    sk_instance* in = r->inst;
+    sk_status s = SK_OK;
+    if (!in->dJop) s = dalloc(&in->dJop, sk::recompute_j_bytes(in->kind, in->Npad));
+    if (s == SK_OK && !r->dSop) s = dalloc(&r->dSop, sk::recompute_s_bytes(in->kind, r->chains, in->Npad));
+    if (s == SK_OK && !r->ddE) {
+        s = dalloc(&r->ddE, static_cast<size_t>(r->chains) * sizeof(double));
+        if (s == SK_OK) SK_CU(cudaMemsetAsync(r->ddE, 0, static_cast<size_t>(r->chains) * sizeof(double), in->st));
+    }
+    if (s == SK_OK && !r->dstats) {
+        s = dalloc(&r->dstats, 6 * sizeof(unsigned long long));
+        if (s == SK_OK) SK_CU(cudaMemsetAsync(r->dstats, 0, 6 * sizeof(unsigned long long), in->st));
+    }
+    if (s != SK_OK) return s;
+    if (!in->jop_valid) {
+        SK_CU(sk::recompute_prepare_j(in->dJ, in->kind, in->Npad, in->dJop, in->st));
+        in->jop_valid = true;
+    }
+    return SK_OK;
+}
+
+uint32_t terms_of(const sk_run* r) { return r->p.recompute_terms ? r->p.recompute_terms : 3u; }
+
+// Periodic recompute after a step segment: +-J check, Gaussian resync.
+sk_status periodic_recompute(sk_run* r) {
+    sk_status s = ensure_recompute(r);
+    if (s != SK_OK) return s;
+    sk_instance* in = r->inst;
+    const uint32_t mode = in->kind == SK_J_PM1 ? 0u : 1u;
+    SK_CU(sk::launch_recompute(in->kind, r->ds, r->dh, nullptr, r->dSop, in->dJop, r->ddE, r->dstats, r->derr,
+                               r->chains, in->Npad, terms_of(r), mode, in->scale, in->st));
+    ++r->n_recomputes;
+    return SK_OK;
 }
 
 constexpr size_t kSmemBudget = 232448 - 1024;  // dynamic smem per CTA, static part reserved
@@ -295,6 +343,7 @@ sk_status sk_destroy_instance(sk_instance* in) {
     if (!in) return fail(SK_ERR_INVALID_ARG, "instance is NULL");
     cudaStreamSynchronize(in->st);
     cudaFree(in->dJ);
+    cudaFree(in->dJop);
     delete in;
     return SK_OK;
 }
@@ -341,6 +390,7 @@ sk_status mcmcmc_create(sk_instance* in, const sk_run_params* p, sk_run** out) {
     if (!(p->beta >= 0.0) || !std::isfinite(p->beta)) return fail(SK_ERR_INVALID_ARG, "beta must be >= 0");
     if (p->stream_id > 0xFFFFFFu) return fail(SK_ERR_INVALID_ARG, "stream_id must fit 24 bits");
     if (p->trace_chains > p->chains) return fail(SK_ERR_INVALID_ARG, "trace_chains > chains");
+    if (p->recompute_terms > 3) return fail(SK_ERR_INVALID_ARG, "recompute_terms must be 0..3");
     sk_run* r = new sk_run();
     r->inst = in;
     r->p = *p;
@@ -527,6 +577,62 @@ sk_status mcmcmc_counters(sk_run* r, uint64_t* flips, uint64_t* rows) {
     return SK_OK;
 }
 
+sk_status mcmcmc_recompute(sk_run* r, uint32_t mode, uint32_t terms, sk_recompute_stats* stats,
+                           float* fields_out, uint32_t mem) {
+    if (!r) return fail(SK_ERR_INVALID_ARG, "run is NULL");
+    if (mode > 2) return fail(SK_ERR_INVALID_ARG, "unknown recompute mode %u", mode);
+    if (terms > 3) return fail(SK_ERR_INVALID_ARG, "terms must be 0..3");
+    if (mode == 2 && !fields_out) return fail(SK_ERR_INVALID_ARG, "fields_out is NULL");
+    if (mem != SK_MEM_HOST && mem != SK_MEM_DEVICE) return fail(SK_ERR_INVALID_ARG, "bad mem");
+    sk_status s = ensure_recompute(r);
+    if (s != SK_OK) return s;
+    sk_instance* in = r->inst;
+    cudaStream_t st = in->st;
+    float* dout = nullptr;
+    if (mode == 2 && (s = dalloc(&dout, static_cast<size_t>(r->chains) * in->Npad * 4)) != SK_OK) return s;
+    SK_CU(cudaMemsetAsync(r->dstats + 3, 0, 3 * sizeof(unsigned long long), st));
+    cudaError_t e = sk::launch_recompute(in->kind, r->ds, r->dh, dout, r->dSop, in->dJop, r->ddE, r->dstats + 3,
+                                         r->derr, r->chains, in->Npad, terms ? terms : 3u, mode, in->scale, st);
+    if (e == cudaSuccess && mode == 2)
+        e = cudaMemcpy2DAsync(fields_out, in->N * 4, dout, in->Npad * 4, in->N * 4, r->chains, cudaMemcpyDefault,
+                              st);
+    unsigned long long h[3] = {0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, r->dstats + 3, sizeof h, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(dout);
+    if (e != cudaSuccess) return fail(SK_ERR_CUDA, "recompute: %s", cudaGetErrorString(e));
+    if ((s = check_run_error(r)) != SK_OK) return s;
+    if (stats) {
+        double d0, d2;
+        std::memcpy(&d0, &h[0], 8);
+        std::memcpy(&d2, &h[2], 8);
+        stats->max_field_drift = d0;
+        stats->max_energy_drift = d2;
+        stats->mismatches = h[1];
+        stats->recomputes = 1;
+    }
+    return SK_OK;
+}
+
+sk_status mcmcmc_recompute_stats(sk_run* r, sk_recompute_stats* stats) {
+    if (!r || !stats) return fail(SK_ERR_INVALID_ARG, "NULL argument");
+    sk_status s = mcmcmc_wait(r, 0);
+    if (s != SK_OK) return s;
+    unsigned long long h[3] = {0, 0, 0};
+    if (r->dstats) {
+        SK_CU(cudaMemcpyAsync(h, r->dstats, sizeof h, cudaMemcpyDeviceToHost, r->inst->st));
+        SK_CU(cudaStreamSynchronize(r->inst->st));
+    }
+    double d0, d2;
+    std::memcpy(&d0, &h[0], 8);
+    std::memcpy(&d2, &h[2], 8);
+    stats->max_field_drift = d0;
+    stats->max_energy_drift = d2;
+    stats->mismatches = h[1];
+    stats->recomputes = r->n_recomputes;
+    return SK_OK;
+}
+
 sk_status mcmcmc_free(sk_run* r) {
     if (!r) return fail(SK_ERR_INVALID_ARG, "run is NULL");
     cudaStreamSynchronize(r->inst->st);
@@ -607,12 +713,8 @@ sk_status mcmcmc_batch_create(sk_run* const* runs, uint32_t n, uint32_t W, sk_ba
     return SK_OK;
 }
 
-sk_status mcmcmc_batch_advance(sk_batch* b, uint64_t steps) {
-    if (!b) return fail(SK_ERR_INVALID_ARG, "batch is NULL");
-    if (steps == 0) return SK_OK;
-    for (sk_run* r : b->runs)
-        if (r->step + steps > 0xFFFFFFFFull)
-            return fail(SK_ERR_INVALID_ARG, "a run would pass 2^32 steps");
+namespace {
+sk_status launch_segment(sk_batch* b, uint64_t steps) {
     for (size_t k = 0; k < b->classes.size(); ++k) {
         const sk_batch::Class& c = b->classes[k];
         cudaError_t e = sk::launch_step(b->djobs, b->ditems + c.first_item, c.n_items, b->dqueue + k, steps,
@@ -622,6 +724,37 @@ sk_status mcmcmc_batch_advance(sk_batch* b, uint64_t steps) {
         if (e != cudaSuccess) return fail(SK_ERR_CUDA, "step launch: %s", cudaGetErrorString(e));
     }
     for (sk_run* r : b->runs) r->step += steps;
+    return SK_OK;
+}
+}  // namespace
+
+sk_status mcmcmc_batch_advance(sk_batch* b, uint64_t steps) {
+    if (!b) return fail(SK_ERR_INVALID_ARG, "batch is NULL");
+    if (steps == 0) return SK_OK;
+    uint32_t M = 0;
+    const sk_run* lead = nullptr;
+    for (sk_run* r : b->runs) {
+        if (r->step + steps > 0xFFFFFFFFull)
+            return fail(SK_ERR_INVALID_ARG, "a run would pass 2^32 steps");
+        if (!r->p.recompute_every) continue;
+        if (!lead) {
+            lead = r;
+            M = r->p.recompute_every;
+        } else if (r->p.recompute_every != M || r->step % M != lead->step % M) {
+            return fail(SK_ERR_INVALID_ARG, "runs of a batch that recompute must share recompute_every and phase");
+        }
+    }
+    if (!M) return launch_segment(b, steps);
+    // segments end on multiples of M; the recomputing runs are recomputed there
+    while (steps) {
+        const uint64_t seg = std::min<uint64_t>(steps, M - lead->step % M);
+        sk_status s = launch_segment(b, seg);
+        if (s != SK_OK) return s;
+        steps -= seg;
+        if (lead->step % M == 0)
+            for (sk_run* r : b->runs)
+                if (r->p.recompute_every && (s = periodic_recompute(r)) != SK_OK) return s;
+    }
     return SK_OK;
 }
 

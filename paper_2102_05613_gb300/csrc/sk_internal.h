@@ -71,6 +71,19 @@ cudaError_t launch_init(const JobDev* job, const int8_t* init, uint32_t chains, 
 cudaError_t launch_energy(const void* J, uint32_t kind, uint32_t N, uint32_t Npad, double scale,
                           const int8_t* spins, uint32_t count, double* out, cudaStream_t st);
 
+// Tensor-core field recompute (sk_recompute.cu).  Operand buffers: J as
+// e4m3 (+-J, npad^2 bytes) or three bf16 terms (Gaussian, 3 npad^2 x 2
+// bytes); spins as e4m3 / bf16 (chains x npad).  mode 0 checks the maintained
+// fields, 1 also replaces them (resync), 2 writes H to `out` only.
+// stats[0] = max |h - H| (double bits), [1] = mismatches, [2] = max |dE|.
+size_t recompute_j_bytes(uint32_t kind, uint32_t npad);
+size_t recompute_s_bytes(uint32_t kind, uint32_t chains, uint32_t npad);
+cudaError_t recompute_prepare_j(const void* J, uint32_t kind, uint32_t npad, void* j_op, cudaStream_t st);
+cudaError_t launch_recompute(uint32_t kind, const int8_t* s, void* h, float* out, void* s_op,
+                             const void* j_op, double* dE, unsigned long long* stats, int* err,
+                             uint32_t chains, uint32_t npad, uint32_t terms, uint32_t mode, double scale,
+                             cudaStream_t st);
+
 // Sets the message sk_last_error() returns on this thread (sk_capi.cu).
 void set_error_message(const char* msg);
 

@@ -1,0 +1,427 @@
+// sk_recompute.cu -- the periodic local-field recompute H = S J^T of all
+// chains of a run on the fifth-generation tensor cores (tcgen05), and the
+// drift check / resynchronisation of the maintained fields against it.
+//
+// H[c][n] = sum_k S[c][k] J[n][k] (J symmetric), M = chains, N = K = Npad.
+//   +-J couplings:     S and J as FP8 e4m3 (+-1 and 0 are exact), kind::f8f6f4,
+//                      FP32 accumulation: every partial sum is an integer below
+//                      2^24, so H is exact and must equal the maintained int32
+//                      fields bit for bit.
+//   Gaussian couplings: S as bf16 (+-1 exact), J split into `terms` bf16
+//                      matrices J = J1 + J2 + J3 (three round-to-nearest terms
+//                      reproduce every fp32 value exactly), kind::f16 with FP32
+//                      accumulation of all terms into one accumulator.
+//
+// One CTA (4 warps) computes a 128 x 256 tile: thread 0 streams A and B
+// tiles with TMA (128-byte swizzle) through a 4-stage mbarrier ring, thread
+// 32 issues the MMAs (K = 32 bytes each) into a 128-lane x 256-column FP32
+// accumulator in tensor memory and commits each stage back to its "empty"
+// barrier, then all 128 threads read their row of the accumulator with
+// tcgen05.ld and compare it with (or replace) the maintained fields.
+// Every wait is bounded; an expired wait sets the run's error word.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <mutex>
+
+#include "sk_internal.h"
+
+namespace sk {
+namespace {
+
+constexpr uint32_t BM = 128, BN = 256, NS = 4;
+constexpr uint32_t TILE_A = BM * 128, TILE_B = BN * 128;  // bytes, 128 B of K per row
+constexpr uint32_t STAGE_BYTES = TILE_A + TILE_B;
+constexpr uint32_t SMEM_BYTES = NS * STAGE_BYTES + 1024;  // + 1 KB alignment slack
+constexpr uint32_t TMEM_COLS = 256;
+constexpr long long kBudget = 4000000000ll;  // ~2 s of clock cycles per wait
+
+__device__ __forceinline__ uint32_t saddr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ bool try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool wait_bounded(uint32_t bar, uint32_t parity) {
+    if (try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!try_wait(bar, parity))
+        if (clock64() - t0 > kBudget) return false;
+    return true;
+}
+__device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+// Shared-memory matrix descriptor: K-major tile, 128-byte rows with the
+// 128-byte swizzle, 8-row groups 1024 bytes apart (tile base 1024-aligned).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((addr & 0x3FFFFu) >> 4);  // start address
+    d |= static_cast<uint64_t>(1) << 16;                 // leading byte offset (unused here)
+    d |= static_cast<uint64_t>(1024 >> 4) << 32;         // stride byte offset
+    d |= static_cast<uint64_t>(1) << 46;                 // descriptor version
+    d |= static_cast<uint64_t>(2) << 61;                 // 128-byte swizzle
+    return d;
+}
+// Instruction descriptor: FP32 accumulator, A/B format code `fmt` (kind::f16:
+// 1 = bf16; kind::f8f6f4: 0 = e4m3), both K-major, N = 256, M = 128.
+__host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((BN >> 3) << 17) | ((BM >> 4) << 24);
+}
+
+template <bool F8>
+__device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if constexpr (F8) {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    } else {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    }
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct Args {
+    void* h;                        // maintained fields [chains][npad]: int32 (+-J) or float
+    const int8_t* s;                // spins [chains][npad]
+    float* out;                     // OUTPUT mode: H [chains][npad]
+    double* dE;                     // per chain: sum_n s_n (h_n - H_n)
+    unsigned long long* stats;      // [0] max |h - H| (double bits), [1] mismatches, [2] max |dE|
+    int* err;
+    uint32_t chains, npad, kblocks, terms, mode;  // mode: 0 check, 1 resync, 2 output
+    uint32_t pm1;
+};
+
+template <bool F8>
+__global__ void __launch_bounds__(128, 1)
+    recompute_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB0,
+                     const __grid_constant__ CUtensorMap tB1, const __grid_constant__ CUtensorMap tB2,
+                     Args args) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full[NS], empty[NS], accum;
+    __shared__ uint32_t tmem_holder;
+    __shared__ int dead;
+    // 128-byte-swizzled tiles must start on a 1024-byte boundary of shared memory
+    unsigned char* smem = smem_raw + ((1024u - (saddr(smem_raw) & 1023u)) & 1023u);
+    const uint32_t tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const uint32_t total = args.terms * args.kblocks;
+    constexpr uint32_t kElems = F8 ? 128u : 64u;  // K elements per 128-byte row
+    constexpr uint32_t idesc = instr_desc(F8 ? 0u : 1u);
+
+    if (tid == 0) {
+        for (uint32_t i = 0; i < NS; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&full[i])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&empty[i])) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&accum)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        dead = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_holder)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_holder;
+
+    if (tid == 0) {
+        // producer: A (spins) and B (couplings, term by term) tiles by TMA
+        const CUtensorMap* tb[3] = {&tB0, &tB1, &tB2};
+        for (uint32_t i = 0; i < total; ++i) {
+            const uint32_t st = i % NS, round = i / NS;
+            if (i >= NS && !wait_bounded(saddr(&empty[st]), (round - 1) & 1u)) {
+                atomicExch(args.err, kDevTimeout);
+                dead = 1;
+                break;
+            }
+            const uint32_t term = i / args.kblocks, kb = i % args.kblocks;
+            unsigned char* a = smem + st * STAGE_BYTES;
+            unsigned char* b = a + TILE_A;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(&full[st])),
+                         "r"(STAGE_BYTES)
+                         : "memory");
+            tma_2d(saddr(a), &tA, static_cast<int>(kb * kElems), static_cast<int>(m0), saddr(&full[st]));
+            tma_2d(saddr(b), tb[term], static_cast<int>(kb * kElems), static_cast<int>(n0), saddr(&full[st]));
+        }
+    } else if (tid == 32) {
+        // MMA issuer: 4 MMAs of K = 32 bytes per stage, accumulate in TMEM
+        for (uint32_t i = 0; i < total; ++i) {
+            const uint32_t st = i % NS, round = i / NS;
+            if (!wait_bounded(saddr(&full[st]), round & 1u)) {
+                atomicExch(args.err, kDevTimeout);
+                dead = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a = saddr(smem + st * STAGE_BYTES);
+            const uint32_t b = a + TILE_A;
+#pragma unroll
+            for (uint32_t kk = 0; kk < 4; ++kk)
+                mma<F8>(tmem, sw128_desc(a + 32 * kk), sw128_desc(b + 32 * kk), idesc, (i | kk) != 0u);
+            mma_commit(saddr(&empty[st]));
+        }
+        mma_commit(saddr(&accum));  // completes when every MMA issued above has
+    }
+    __syncwarp();
+
+    // epilogue: thread t owns accumulator row t (chain m0 + t)
+    const bool ok = wait_bounded(saddr(&accum), 0u);
+    if (!ok && (tid & 31) == 0) atomicExch(args.err, kDevTimeout);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t c = m0 + tid;
+    const bool row_ok = c < args.chains && ok && !dead;
+    const uint32_t taddr = tmem + ((warp * 32u) << 16);
+    double dmax = 0.0, dsum = 0.0;
+    unsigned long long mism = 0;
+    for (uint32_t col = 0; col < BN; col += 16) {
+        uint32_t v[16];
+        tmem_ld16(taddr + col, v);
+        const uint32_t nb = n0 + col;
+        if (!row_ok || nb >= args.npad) continue;  // npad is a multiple of 32: all 16 columns valid
+        const size_t base = static_cast<size_t>(c) * args.npad + nb;
+        if (args.mode == 2) {
+            float4* o = reinterpret_cast<float4*>(args.out + base);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                o[q] = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                                   __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+            continue;
+        }
+        const int4 sw = *reinterpret_cast<const int4*>(args.s + base);
+        const int sv[4] = {sw.x, sw.y, sw.z, sw.w};
+        if (args.pm1) {
+            int4* hp = reinterpret_cast<int4*>(static_cast<int*>(args.h) + base);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int4 hv = hp[q];
+                const int hh[4] = {hv.x, hv.y, hv.z, hv.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float H = __uint_as_float(v[4 * q + e]);
+                    const double d = static_cast<double>(hh[e]) - static_cast<double>(H);
+                    if (d != 0.0) ++mism;
+                    dmax = fmax(dmax, fabs(d));
+                    const int sb = static_cast<int>(static_cast<int32_t>(static_cast<uint32_t>(sv[q]) << (24 - 8 * e)) >> 24);
+                    dsum += sb * d;
+                }
+            }
+        } else {
+            float4* hp = reinterpret_cast<float4*>(static_cast<float*>(args.h) + base);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 hv = hp[q];
+                const float hh[4] = {hv.x, hv.y, hv.z, hv.w};
+                float Hn[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    Hn[e] = __uint_as_float(v[4 * q + e]);
+                    const double d = static_cast<double>(hh[e]) - static_cast<double>(Hn[e]);
+                    dmax = fmax(dmax, fabs(d));
+                    const int sb = static_cast<int>(static_cast<int32_t>(static_cast<uint32_t>(sv[q]) << (24 - 8 * e)) >> 24);
+                    dsum += sb * d;
+                }
+                if (args.mode == 1) hp[q] = make_float4(Hn[0], Hn[1], Hn[2], Hn[3]);
+            }
+        }
+    }
+    if (row_ok && args.mode != 2) {
+        atomicMax(&args.stats[0], static_cast<unsigned long long>(__double_as_longlong(dmax)));
+        if (mism) atomicAdd(&args.stats[1], mism);
+        atomicAdd(&args.dE[c], dsum);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+// max over chains of |dE| = |-scale/2 sum s (h - H)| into stats[2]; clears dE.
+__global__ void finish_energy(double* dE, uint32_t chains, double scale, unsigned long long* stats) {
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= chains) return;
+    const double e = fabs(0.5 * scale * dE[c]);
+    dE[c] = 0.0;
+    atomicMax(&stats[2], static_cast<unsigned long long>(__double_as_longlong(e)));
+}
+
+// Operand conversion: spins +-1 (padding 0) -> e4m3 bytes or bf16 words.
+__global__ void spins_to_e4m3(const int8_t* __restrict__ s, uint8_t* __restrict__ o, size_t n) {
+    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const int v = s[i];
+        o[i] = v == 0 ? 0 : (v > 0 ? 0x38 : 0xB8);  // e4m3: +-1.0
+    }
+}
+__global__ void spins_to_bf16(const int8_t* __restrict__ s, uint16_t* __restrict__ o, size_t n) {
+    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const int v = s[i];
+        o[i] = v == 0 ? 0 : (v > 0 ? 0x3F80 : 0xBF80);  // bf16: +-1.0
+    }
+}
+// J in {-1, 0, +1} -> e4m3 bytes.
+__global__ void pm1_to_e4m3(const int8_t* __restrict__ j, uint8_t* __restrict__ o, size_t n) {
+    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const int v = j[i];
+        o[i] = v == 0 ? 0 : (v > 0 ? 0x38 : 0xB8);
+    }
+}
+// fp32 J -> J1 + J2 + J3, each rounded to nearest bf16 from the remainder of
+// the previous terms; the remainders are exact in fp32.
+__global__ void gauss_to_bf16x3(const float* __restrict__ j, uint16_t* __restrict__ o, size_t n) {
+    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        float r = j[i];
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            const __nv_bfloat16 b = __float2bfloat16_rn(r);
+            o[t * n + i] = __bfloat16_as_ushort(b);
+            r -= __bfloat162float(b);
+        }
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+cudaError_t encoder(PFN_cuTensorMapEncodeTiled_v12000* fn) {
+    std::call_once(g_encode_once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    *fn = g_encode;
+    return g_encode ? cudaSuccess : cudaErrorNotSupported;
+}
+
+// 2-D K-major map: rows x cols elements (cols innermost), box = 128 bytes of
+// K x box_rows rows, 128-byte swizzle, out-of-range elements read as zero.
+cudaError_t make_map(CUtensorMap* m, const void* base, bool bf16, uint64_t rows, uint64_t cols,
+                     uint32_t box_rows) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc;
+    cudaError_t e = encoder(&enc);
+    if (e != cudaSuccess) return e;
+    const uint32_t esz = bf16 ? 2 : 1;
+    const cuuint64_t dims[2] = {cols, rows};
+    const cuuint64_t strides[1] = {cols * esz};
+    const cuuint32_t box[2] = {128u / esz, box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+                           const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+uint32_t grid1d(size_t n) {
+    const size_t b = (n + 255) / 256;
+    return static_cast<uint32_t>(b < 4096 ? (b ? b : 1) : 4096);
+}
+
+}  // namespace
+
+size_t recompute_j_bytes(uint32_t kind, uint32_t npad) {
+    const size_t n = static_cast<size_t>(npad) * npad;
+    return kind == 0 ? n : 3 * n * 2;
+}
+size_t recompute_s_bytes(uint32_t kind, uint32_t chains, uint32_t npad) {
+    return static_cast<size_t>(chains) * npad * (kind == 0 ? 1 : 2);
+}
+
+cudaError_t recompute_prepare_j(const void* J, uint32_t kind, uint32_t npad, void* j_op, cudaStream_t st) {
+    const size_t n = static_cast<size_t>(npad) * npad;
+    if (kind == 0)
+        pm1_to_e4m3<<<grid1d(n), 256, 0, st>>>(static_cast<const int8_t*>(J), static_cast<uint8_t*>(j_op), n);
+    else
+        gauss_to_bf16x3<<<grid1d(n), 256, 0, st>>>(static_cast<const float*>(J), static_cast<uint16_t*>(j_op), n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_recompute(uint32_t kind, const int8_t* s, void* h, float* out, void* s_op,
+                             const void* j_op, double* dE, unsigned long long* stats, int* err,
+                             uint32_t chains, uint32_t npad, uint32_t terms, uint32_t mode, double scale,
+                             cudaStream_t st) {
+    const bool bf = kind != 0;
+    if (!bf) terms = 1;
+    if (terms < 1 || terms > 3) return cudaErrorInvalidValue;
+    const size_t ns = static_cast<size_t>(chains) * npad;
+    if (bf)
+        spins_to_bf16<<<grid1d(ns), 256, 0, st>>>(s, static_cast<uint16_t*>(s_op), ns);
+    else
+        spins_to_e4m3<<<grid1d(ns), 256, 0, st>>>(s, static_cast<uint8_t*>(s_op), ns);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    CUtensorMap tA, tB[3];
+    e = make_map(&tA, s_op, bf, chains, npad, BM);
+    const size_t term_bytes = static_cast<size_t>(npad) * npad * (bf ? 2 : 1);
+    for (uint32_t t = 0; t < 3 && e == cudaSuccess; ++t)
+        e = make_map(&tB[t], static_cast<const unsigned char*>(j_op) + (bf ? t : 0) * term_bytes, bf, npad, npad, BN);
+    if (e != cudaSuccess) return e;
+    Args a;
+    a.h = h;
+    a.s = s;
+    a.out = out;
+    a.dE = dE;
+    a.stats = stats;
+    a.err = err;
+    a.chains = chains;
+    a.npad = npad;
+    a.kblocks = (npad + (bf ? 63u : 127u)) / (bf ? 64u : 128u);
+    a.terms = terms;
+    a.mode = mode;
+    a.pm1 = bf ? 0u : 1u;
+    const dim3 grid((chains + BM - 1) / BM, (npad + BN - 1) / BN);
+    if (bf) {
+        e = cudaFuncSetAttribute(recompute_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        recompute_kernel<false><<<grid, 128, SMEM_BYTES, st>>>(tA, tB[0], tB[1], tB[2], a);
+    } else {
+        e = cudaFuncSetAttribute(recompute_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        recompute_kernel<true><<<grid, 128, SMEM_BYTES, st>>>(tA, tB[0], tB[0], tB[0], a);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess || mode == 2) return e;
+    finish_energy<<<(chains + 255) / 256, 256, 0, st>>>(dE, chains, scale, stats);
+    return cudaGetLastError();
+}
+
+}  // namespace sk

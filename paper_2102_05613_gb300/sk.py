@@ -28,7 +28,8 @@ _STATUS = {0: "SK_OK", 1: "SK_ERR_INVALID_ARG", 2: "SK_ERR_OOM", 3: "SK_ERR_CUDA
 # every symbol declared in include/sk_mcmcmc.h
 EXPORTS = ["sk_create_instance", "sk_set_couplings", "sk_destroy_instance", "sk_energy",
            "mcmcmc_create", "mcmcmc_advance", "mcmcmc_run", "mcmcmc_reset", "mcmcmc_wait",
-           "mcmcmc_observables", "mcmcmc_state", "mcmcmc_trace", "mcmcmc_counters", "mcmcmc_free",
+           "mcmcmc_observables", "mcmcmc_state", "mcmcmc_recompute", "mcmcmc_recompute_stats",
+           "mcmcmc_trace", "mcmcmc_counters", "mcmcmc_free",
            "mcmcmc_batch_create", "mcmcmc_batch_advance", "mcmcmc_batch_info",
            "mcmcmc_batch_free", "mcmcmc_run_noalloc", "sk_last_error"]
 
@@ -44,7 +45,16 @@ class RunParams(C.Structure):
                 ("record_every", C.c_uint32), ("max_records", C.c_uint64),
                 ("beta", C.c_double), ("seed", C.c_uint64), ("stream_id", C.c_uint32),
                 ("trace_chains", C.c_uint32), ("trace_steps", C.c_uint64),
-                ("init_spins", C.c_void_p), ("init_mem", C.c_uint32)]
+                ("init_spins", C.c_void_p), ("init_mem", C.c_uint32),
+                ("recompute_every", C.c_uint32), ("recompute_terms", C.c_uint32)]
+
+
+class RecomputeStats(C.Structure):
+    _fields_ = [("max_field_drift", C.c_double), ("max_energy_drift", C.c_double),
+                ("mismatches", C.c_uint64), ("recomputes", C.c_uint64)]
+
+
+SK_RECOMPUTE_CHECK, SK_RECOMPUTE_RESYNC, SK_RECOMPUTE_OUTPUT = 0, 1, 2
 
 
 _lib = None
@@ -76,6 +86,8 @@ def lib(build_if_missing: bool = True):
             "mcmcmc_state": [vp, vp, vp, vp, u32],
             "mcmcmc_trace": [vp, vp, u32],
             "mcmcmc_counters": [vp, vp, vp],
+            "mcmcmc_recompute": [vp, u32, u32, C.POINTER(RecomputeStats), vp, u32],
+            "mcmcmc_recompute_stats": [vp, C.POINTER(RecomputeStats)],
             "mcmcmc_free": [vp],
             "mcmcmc_batch_create": [P, u32, u32, P],
             "mcmcmc_batch_advance": [vp, u64],
@@ -173,7 +185,8 @@ class Run:
 
     def __init__(self, inst: Instance, *, chains: int, K: int = 8, rule: int = SK_RULE_MCMCMC,
                  beta: float = 1.0, seed: int = 1, stream_id: int = 0, record_every: int = 0,
-                 max_records: int = 0, init=None, trace_chains: int = 0, trace_steps: int = 0):
+                 max_records: int = 0, init=None, trace_chains: int = 0, trace_steps: int = 0,
+                 recompute_every: int = 0, recompute_terms: int = 0):
         self.inst = inst
         self.chains, self.K, self.rule = int(chains), int(K), int(rule)
         self.record_every, self.max_records = int(record_every), int(max_records)
@@ -184,6 +197,7 @@ class Run:
         pr.record_every, pr.max_records = self.record_every, self.max_records
         pr.beta, pr.seed, pr.stream_id = float(beta), int(seed), int(stream_id)
         pr.trace_chains, pr.trace_steps = self.trace_chains, self.trace_steps
+        pr.recompute_every, pr.recompute_terms = int(recompute_every), int(recompute_terms)
         if init is not None:
             if isinstance(init, np.ndarray):
                 init = np.ascontiguousarray(init, dtype=np.int8)
@@ -239,6 +253,23 @@ class Run:
         t = np.zeros((self.trace_chains, self.trace_steps), dtype=np.int32)
         _check(lib().mcmcmc_trace(self.handle, t.ctypes.data_as(C.c_void_p), SK_MEM_HOST))
         return t
+
+    def recompute(self, mode: int = SK_RECOMPUTE_CHECK, terms: int = 3, out: bool = False):
+        """mcmcmc_recompute; returns (stats dict, H or None)."""
+        st = RecomputeStats()
+        H = None
+        ptr = None
+        if out:
+            mode = SK_RECOMPUTE_OUTPUT
+            H = np.zeros((self.chains, self.inst.N), dtype=np.float32)
+            ptr = H.ctypes.data_as(C.c_void_p)
+        _check(lib().mcmcmc_recompute(self.handle, int(mode), int(terms), C.byref(st), ptr, SK_MEM_HOST))
+        return ({k: getattr(st, k) for k, _ in RecomputeStats._fields_}, H)
+
+    def recompute_stats(self):
+        st = RecomputeStats()
+        _check(lib().mcmcmc_recompute_stats(self.handle, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in RecomputeStats._fields_}
 
     def counters(self):
         """(spins flipped, J rows needed) since the last reset."""
