@@ -168,6 +168,63 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# tensor-core field recompute (H = J s for all chains), config-3 sizes
+# ---------------------------------------------------------------------------
+RC_N, RC_CHAINS, RC_ITERS = 2048, 8192, 20
+
+
+def recompute_report(stream, peaks):
+    """Times mcmcmc_recompute on +-J (FP8 e4m3, check) and Gaussian (bf16 x3,
+    resync) couplings with N = 2048 and 8192 chains, and states the error of
+    each recompute format against the FP64 product on 64 chains."""
+    import numpy as np
+    import torch
+    from paper_2102_05613_gb300 import inputs, sk
+    bf16_peak = peaks.get("bf16_tflops") or 1900.0
+    out = {"N": RC_N, "chains": RC_CHAINS,
+           "flops_per_recompute": 2.0 * RC_CHAINS * RC_N * RC_N}
+    for kind, name in ((sk.SK_J_PM1, "pm1_fp8"), (sk.SK_J_GAUSS, "gauss_bf16x3")):
+        J = inputs.couplings(RC_N, kind, 2048 + kind)
+        inst = sk.Instance(J, stream=stream)
+        run = sk.Run(inst, chains=RC_CHAINS, K=64, beta=2.0, seed=5)
+        run.advance(256)
+        mode = sk.SK_RECOMPUTE_CHECK if kind == sk.SK_J_PM1 else sk.SK_RECOMPUTE_RESYNC
+        for _ in range(3):
+            run.recompute(mode, terms=3)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(RC_ITERS)]
+        for a, b in ev:
+            a.record(stream)
+            st, _ = run.recompute(mode, terms=3)
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+        # executed flops: one product for FP8, three (one per bf16 term) for the split
+        exec_flops = out["flops_per_recompute"] * (1 if kind == sk.SK_J_PM1 else 3)
+        peak = bf16_peak * (2.0 if kind == sk.SK_J_PM1 else 1.0)
+        ent = {"ms": ms, "algorithmic_tflops": out["flops_per_recompute"] / ms / 1e9,
+               "executed_tflops": exec_flops / ms / 1e9, "peak_tflops": peak,
+               "peak_source": ("measured bf16 x 2 (nominal fp8/bf16 ratio)" if kind == sk.SK_J_PM1
+                               else "measured bf16"),
+               "frac_executed": exec_flops / ms / 1e9 / peak,
+               "check": st}
+        # error of each format against the FP64 product on the first 64 chains
+        spins, _ = run.state()
+        ex = (J.astype(np.float64) @ spins[:64].T.astype(np.float64)).T
+        errs = {}
+        for terms in ((1,) if kind == sk.SK_J_PM1 else (1, 2, 3)):
+            _, H = run.recompute(terms=terms, out=True)
+            errs[f"terms={terms}" if kind == sk.SK_J_GAUSS else "fp8"] = float(
+                np.abs(H[:64].astype(np.float64) - ex).max())
+        ent["max_abs_error_vs_fp64"] = errs
+        out[name] = ent
+        run.close()
+        inst.close()
+    return out
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def run_ours(args):
@@ -297,6 +354,9 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(couplings)
+    rc = None
+    if rank == 0 and not args.no_recompute:
+        rc = recompute_report(stream, peaks)
 
     for r in runs:
         r.close()
@@ -314,7 +374,8 @@ def run_ours(args):
                            "launch": info},
                 "mc_steps_per_s": mc_steps,
                 "gpu_launches": 2 * args.steps,
-                "roofline": roofline, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
+                "roofline": roofline, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
+                "recompute": rc}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -329,6 +390,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-recompute", action="store_true",
+                    help="skip the tensor-core recompute measurement")
     ap.add_argument("--instances", type=int, default=INSTANCES,
                     help="smaller cases for profiling only; the bench line uses the default")
     ap.add_argument("--chains", type=int, default=CHAINS)

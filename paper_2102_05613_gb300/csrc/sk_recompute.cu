@@ -32,7 +32,7 @@
 namespace sk {
 namespace {
 
-constexpr uint32_t BM = 128, BN = 256, NS = 4;
+constexpr uint32_t BM = 128, BN = 256, NS = 2;  // 2 stages: two CTAs share an SM
 constexpr uint32_t TILE_A = BM * 128, TILE_B = BN * 128;  // bytes, 128 B of K per row
 constexpr uint32_t STAGE_BYTES = TILE_A + TILE_B;
 constexpr uint32_t SMEM_BYTES = NS * STAGE_BYTES + 1024;  // + 1 KB alignment slack
@@ -205,7 +205,10 @@ __global__ void __launch_bounds__(128, 1)
     const uint32_t c = m0 + tid;
     const bool row_ok = c < args.chains && ok && !dead;
     const uint32_t taddr = tmem + ((warp * 32u) << 16);
-    double dmax = 0.0, dsum = 0.0;
+    // per-element differences in exact integer (+-J) or float arithmetic; the
+    // per-chain sums are combined across tiles in double precision
+    int imax = 0, isum = 0;
+    float fmaxd = 0.0f, fsum = 0.0f;
     unsigned long long mism = 0;
     for (uint32_t col = 0; col < BN; col += 16) {
         uint32_t v[16];
@@ -224,19 +227,18 @@ __global__ void __launch_bounds__(128, 1)
         const int4 sw = *reinterpret_cast<const int4*>(args.s + base);
         const int sv[4] = {sw.x, sw.y, sw.z, sw.w};
         if (args.pm1) {
-            int4* hp = reinterpret_cast<int4*>(static_cast<int*>(args.h) + base);
+            const int4* hp = reinterpret_cast<const int4*>(static_cast<const int*>(args.h) + base);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int4 hv = hp[q];
                 const int hh[4] = {hv.x, hv.y, hv.z, hv.w};
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    const float H = __uint_as_float(v[4 * q + e]);
-                    const double d = static_cast<double>(hh[e]) - static_cast<double>(H);
-                    if (d != 0.0) ++mism;
-                    dmax = fmax(dmax, fabs(d));
+                    const int d = hh[e] - __float2int_rn(__uint_as_float(v[4 * q + e]));
+                    mism += d != 0;
+                    imax = max(imax, abs(d));
                     const int sb = static_cast<int>(static_cast<int32_t>(static_cast<uint32_t>(sv[q]) << (24 - 8 * e)) >> 24);
-                    dsum += sb * d;
+                    isum += sb * d;
                 }
             }
         } else {
@@ -249,16 +251,18 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     Hn[e] = __uint_as_float(v[4 * q + e]);
-                    const double d = static_cast<double>(hh[e]) - static_cast<double>(Hn[e]);
-                    dmax = fmax(dmax, fabs(d));
+                    const float d = hh[e] - Hn[e];
+                    fmaxd = fmaxf(fmaxd, fabsf(d));
                     const int sb = static_cast<int>(static_cast<int32_t>(static_cast<uint32_t>(sv[q]) << (24 - 8 * e)) >> 24);
-                    dsum += sb * d;
+                    fsum = fmaf(static_cast<float>(sb), d, fsum);
                 }
                 if (args.mode == 1) hp[q] = make_float4(Hn[0], Hn[1], Hn[2], Hn[3]);
             }
         }
     }
     if (row_ok && args.mode != 2) {
+        const double dmax = args.pm1 ? static_cast<double>(imax) : static_cast<double>(fmaxd);
+        const double dsum = args.pm1 ? static_cast<double>(isum) : static_cast<double>(fsum);
         atomicMax(&args.stats[0], static_cast<unsigned long long>(__double_as_longlong(dmax)));
         if (mism) atomicAdd(&args.stats[1], mism);
         atomicAdd(&args.dE[c], dsum);
