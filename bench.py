@@ -196,9 +196,10 @@ def recompute_report(stream, peaks):
               for _ in range(RC_ITERS)]
         for a, b in ev:
             a.record(stream)
-            st, _ = run.recompute(mode, terms=3)
+            run.recompute(mode, terms=3, sync=False)
             b.record(stream)
         torch.cuda.synchronize()
+        st, _ = run.recompute(mode, terms=3)
         ms = statistics.median(a.elapsed_time(b) for a, b in ev)
         # executed flops: one product for FP8, three (one per bf16 term) for the split
         exec_flops = out["flops_per_recompute"] * (1 if kind == sk.SK_J_PM1 else 3)
@@ -222,6 +223,114 @@ def recompute_report(stream, peaks):
         run.close()
         inst.close()
     return out
+
+
+# ---------------------------------------------------------------------------
+# single-chain latency: +-J N = 64 (J seed 0), K = 8, beta = 1, 1e5 steps
+# ---------------------------------------------------------------------------
+def latency_report(stream):
+    import torch
+    from paper_2102_05613_gb300 import inputs, sk
+    J = inputs.couplings_pm1(64, 0)
+    inst = sk.Instance(J, stream=stream)
+    steps = 100_000
+    run = sk.Run(inst, chains=1, K=8, beta=1.0, seed=1, record_every=1000, max_records=steps // 1000)
+    run.advance(1000)
+    run.reset()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    run.advance(steps)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    run.close()
+    inst.close()
+    return {"workload": "+-J SK N=64, J seed 0, one chain, MCMCMC K=8, beta=1, 1e5 steps, Philox seed 1",
+            "ns_per_step": 1e6 * ms / steps, "candidate_configs_per_s": 8 * steps / (ms / 1e3)}
+
+
+# ---------------------------------------------------------------------------
+# time to thermalise: MCMCMC vs K = 1 Metropolis (Gaussian N = 1024, beta = 1)
+# ---------------------------------------------------------------------------
+TTT_N, TTT_CHAINS, TTT_BETA = 1024, 4096, 1.0
+TTT_METHODS = [("metropolis", 1, 1, 1 << 23), ("mcmcmc_k32", 0, 32, 1 << 21),
+               ("mcmcmc_k128", 0, 128, 1 << 20)]
+TTT_EPS = (1e-2, 3e-3, 1e-3)
+
+
+def run_ttt(args):
+    """e(t) = chain-mean E/N every T/2048 steps from a random start; e_inf and
+    sigma_inf from the last half of the K=128 run; t_therm(eps) = the first
+    record after which |e - e_inf| <= eps + 3 sigma_inf holds for good;
+    wall-clock = t_therm x the method's measured seconds per step."""
+    import numpy as np
+    import torch
+    from paper_2102_05613_gb300 import inputs, sk
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    J = inputs.couplings_gauss(TTT_N, 0)
+    inst = sk.Instance(J, stream=stream)
+    curves = {}
+    for name, rule, Kt, T in TTT_METHODS:
+        R = T // 2048
+        run = sk.Run(inst, chains=TTT_CHAINS, K=Kt, rule=rule, beta=TTT_BETA, seed=7,
+                     record_every=R, max_records=2048)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        chunk = R * 128
+        for _ in range(T // chunk):
+            run.advance(chunk)
+        b.record(stream)
+        torch.cuda.synchronize()
+        E, _, acc = run.observables()
+        s_per_step = a.elapsed_time(b) / 1e3 / T
+        curves[name] = dict(R=R, T=T, e=E.mean(axis=1) / TTT_N, per_chain=E / TTT_N,
+                            s_per_step=s_per_step, acc=float(acc.mean()) / R)
+        run.close()
+    ref = curves["mcmcmc_k128"]
+    tail = ref["per_chain"][1024:]
+    e_inf = float(tail.mean())
+    sig = float(tail.mean(axis=0).std(ddof=1) / math.sqrt(TTT_CHAINS))
+    out = {"workload": f"gaussian-sk N={TTT_N} J seed 0, beta={TTT_BETA}, {TTT_CHAINS} chains from "
+                       f"a random start, records every T/2048 steps",
+           "e_inf": e_inf, "sigma_inf": sig, "methods": {}}
+    for name, c in curves.items():
+        t = (np.arange(len(c["e"])) + 1) * c["R"]
+        dev = np.abs(c["e"] - e_inf)
+        m = {"steps_run": c["T"], "s_per_step": c["s_per_step"],
+             "chain_steps_per_s": TTT_CHAINS / c["s_per_step"], "acceptance": c["acc"],
+             "e_final": float(c["e"][-1]), "t_therm_steps": {}, "t_therm_s": {}}
+        for eps in TTT_EPS:
+            ok = dev <= eps + 3 * sig
+            bad = np.nonzero(~ok)[0]
+            if len(bad) == 0:
+                ts = int(t[0])
+            elif bad[-1] + 1 < len(t):
+                ts = int(t[bad[-1] + 1])
+            else:
+                ts = None  # not thermalised within the run
+            m["t_therm_steps"][str(eps)] = ts
+            m["t_therm_s"][str(eps)] = None if ts is None else ts * c["s_per_step"]
+        out["methods"][name] = m
+    sp = {}
+    met = out["methods"]["metropolis"]
+    for name in ("mcmcmc_k32", "mcmcmc_k128"):
+        mm = out["methods"][name]
+        sp[name] = {}
+        for eps in TTT_EPS:
+            a_, b_ = met["t_therm_s"][str(eps)], mm["t_therm_s"][str(eps)]
+            if b_ is None:
+                sp[name][str(eps)] = None
+            elif a_ is None:
+                sp[name][str(eps)] = f">{met['steps_run'] * met['s_per_step'] / b_:.3g} (Metropolis not thermalised)"
+            else:
+                sp[name][str(eps)] = a_ / b_
+    out["wallclock_speedup_vs_metropolis"] = sp
+    inst.close()
+    print(json.dumps(out), flush=True)
+    return 0
 
 
 # ---------------------------------------------------------------------------
@@ -357,6 +466,7 @@ def run_ours(args):
     rc = None
     if rank == 0 and not args.no_recompute:
         rc = recompute_report(stream, peaks)
+    lat = latency_report(stream) if rank == 0 else None
 
     for r in runs:
         r.close()
@@ -375,7 +485,7 @@ def run_ours(args):
                 "mc_steps_per_s": mc_steps,
                 "gpu_launches": 2 * args.steps,
                 "roofline": roofline, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
-                "recompute": rc}
+                "recompute": rc, "latency_config1": lat}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -390,6 +500,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ttt", action="store_true",
+                    help="time-to-thermalise comparison instead of the throughput line")
     ap.add_argument("--no-recompute", action="store_true",
                     help="skip the tensor-core recompute measurement")
     ap.add_argument("--instances", type=int, default=INSTANCES,
@@ -402,6 +514,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.ttt:
+        return run_ttt(args)
     return run_ours(args)
 
 

@@ -200,8 +200,11 @@ typedef struct {
  * mode SK_RECOMPUTE_CHECK compares H with the maintained fields;
  * SK_RECOMPUTE_RESYNC also replaces the maintained fields by H;
  * SK_RECOMPUTE_OUTPUT only writes H to fields_out (chains*N float32, mem).
- * The comparison is done in double precision.  Synchronises; `stats` (host,
- * may be NULL) receives this call's figures.
+ * Per-element differences are exact integers (+-J) or float32 (Gaussian);
+ * per-chain energy differences are summed in double precision.  With
+ * `stats` non-NULL (host) the call synchronises and returns this call's
+ * figures; with stats NULL (modes CHECK/RESYNC) it only enqueues the work on
+ * the run's stream.
  */
 sk_status mcmcmc_recompute(sk_run* run, uint32_t mode, uint32_t terms, sk_recompute_stats* stats,
                            float* fields_out, uint32_t mem);

@@ -593,6 +593,10 @@ sk_status mcmcmc_recompute(sk_run* r, uint32_t mode, uint32_t terms, sk_recomput
     SK_CU(cudaMemsetAsync(r->dstats + 3, 0, 3 * sizeof(unsigned long long), st));
     cudaError_t e = sk::launch_recompute(in->kind, r->ds, r->dh, dout, r->dSop, in->dJop, r->ddE, r->dstats + 3,
                                          r->derr, r->chains, in->Npad, terms ? terms : 3u, mode, in->scale, st);
+    if (!stats && mode != 2) {  // enqueue only
+        if (e != cudaSuccess) return fail(SK_ERR_CUDA, "recompute: %s", cudaGetErrorString(e));
+        return SK_OK;
+    }
     if (e == cudaSuccess && mode == 2)
         e = cudaMemcpy2DAsync(fields_out, in->N * 4, dout, in->Npad * 4, in->N * 4, r->chains, cudaMemcpyDefault,
                               st);

@@ -254,8 +254,14 @@ class Run:
         _check(lib().mcmcmc_trace(self.handle, t.ctypes.data_as(C.c_void_p), SK_MEM_HOST))
         return t
 
-    def recompute(self, mode: int = SK_RECOMPUTE_CHECK, terms: int = 3, out: bool = False):
-        """mcmcmc_recompute; returns (stats dict, H or None)."""
+    def recompute(self, mode: int = SK_RECOMPUTE_CHECK, terms: int = 3, out: bool = False,
+                  sync: bool = True):
+        """mcmcmc_recompute; returns (stats dict, H or None).  sync=False only
+        enqueues (no stats)."""
+        if not sync and not out:
+            _check(lib().mcmcmc_recompute(self.handle, int(mode), int(terms), None, None,
+                                          SK_MEM_HOST))
+            return None, None
         st = RecomputeStats()
         H = None
         ptr = None
