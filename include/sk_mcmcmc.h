@@ -242,6 +242,31 @@ sk_status mcmcmc_batch_create(sk_run* const* runs, uint32_t n_runs, uint32_t war
 /* Advances every run of the batch by `steps` steps in one kernel launch. */
 sk_status mcmcmc_batch_advance(sk_batch* b, uint64_t steps);
 
+/*
+ * mcmcmc_batch_capture: records the launches that advance every run of the
+ * batch by `steps` steps -- the step kernels of each class, the step-counter
+ * update and, for runs with recompute_every, the tensor-core recomputes --
+ * into a CUDA graph (stream capture on the runs' stream, which must not be
+ * the legacy default stream).  Nothing runs at capture.  With recomputing
+ * runs, `steps` and the runs' current step must be multiples of
+ * recompute_every.  A later mcmcmc_batch_autotune drops the graph.
+ */
+sk_status mcmcmc_batch_capture(sk_batch* b, uint64_t steps);
+
+/* Launches the captured graph `times` times (each advances `steps` steps). */
+sk_status mcmcmc_batch_replay(sk_batch* b, uint32_t times);
+
+/*
+ * mcmcmc_batch_autotune: times a `trial_steps`-step advance of the batch for
+ * each chains-per-CTA value that fits in shared memory (32, 28, ..., 2; the
+ * value also selects the kernel's register budget) and keeps the fastest.
+ * Trials start from a copy of the runs' state, which is restored afterwards,
+ * and run with records and traces off: the runs' trajectories, records and
+ * step counters are unchanged.  *warps_per_cta (may be NULL) receives the
+ * choice.  Synchronises.
+ */
+sk_status mcmcmc_batch_autotune(sk_batch* b, uint32_t trial_steps, uint32_t* warps_per_cta);
+
 /* Launch geometry chosen for the batch (for reports): CTAs, warps per CTA,
  * dynamic shared memory bytes per CTA, work items. */
 sk_status mcmcmc_batch_info(const sk_batch* b, uint32_t* grid, uint32_t* warps_per_cta,

@@ -118,8 +118,10 @@ struct sk_batch {
     JobDev* djobs = nullptr;
     WorkItem* ditems = nullptr;
     uint32_t* dqueue = nullptr;  // one work counter per class
-    uint32_t n_items = 0, W = 0, per_warp = 0, grid = 0;
+    uint32_t n_items = 0, W = 0, per_warp = 0, grid = 0, fit = 0;
     cudaStream_t st = nullptr;
+    cudaGraphExec_t graph = nullptr;  // mcmcmc_batch_capture
+    uint64_t graph_steps = 0;
 };
 
 struct sk_run {
@@ -646,6 +648,61 @@ sk_status mcmcmc_free(sk_run* r) {
     return SK_OK;
 }
 
+namespace {
+
+// Work items of the batch for W chains per CTA, grouped by kernel class;
+// uploads them (replacing the previous plan).
+sk_status plan_batch(sk_batch* b, uint32_t W) {
+    std::vector<WorkItem> items;
+    std::vector<sk_batch::Class> classes;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    uint32_t grid = 0;
+    const uint32_t n = static_cast<uint32_t>(b->runs.size());
+    for (int cls = 0; cls < 8; ++cls) {
+        const uint32_t first = static_cast<uint32_t>(items.size());
+        for (uint32_t i = 0; i < n; ++i) {
+            const sk_run* r = b->runs[i];
+            if (sk::step_class(r->inst->kind, r->p.rule, r->p.K) != cls) continue;
+            for (uint32_t c = 0; c < r->chains; c += W)
+                items.push_back(WorkItem{i, c, std::min(W, r->chains - c), 0});
+        }
+        const uint32_t cnt = static_cast<uint32_t>(items.size()) - first;
+        if (!cnt) continue;
+        const int occ = sk::step_kernel_occupancy(cls, W, static_cast<size_t>(b->per_warp) * W);
+        if (occ <= 0)
+            return fail(SK_ERR_CUDA, "step kernel cannot be resident with %u warps and %u bytes", W,
+                        b->per_warp * W);
+        const uint32_t g = std::min<uint32_t>(cnt, static_cast<uint32_t>(occ * sms));
+        classes.push_back(sk_batch::Class{cls, first, cnt, g});
+        grid = std::max(grid, g);
+    }
+    WorkItem* d = nullptr;
+    sk_status s = dalloc(&d, items.size() * sizeof(WorkItem));
+    if (s != SK_OK) return s;
+    cudaError_t e = cudaMemcpy(d, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return fail(SK_ERR_CUDA, "batch upload: %s", cudaGetErrorString(e));
+    }
+    cudaStreamSynchronize(b->st);  // no launch of the batch may still read the old items
+    cudaFree(b->ditems);
+    b->ditems = d;
+    b->classes = classes;
+    b->n_items = static_cast<uint32_t>(items.size());
+    b->grid = grid;
+    b->W = W;
+    if (b->graph) {  // the captured launches used the old plan
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+        b->graph_steps = 0;
+    }
+    return SK_OK;
+}
+
+}  // namespace
+
 sk_status mcmcmc_batch_create(sk_run* const* runs, uint32_t n, uint32_t W, sk_batch** out) {
     if (!runs || !out || n == 0) return fail(SK_ERR_INVALID_ARG, "empty batch");
     *out = nullptr;
@@ -666,46 +723,18 @@ sk_status mcmcmc_batch_create(sk_run* const* runs, uint32_t n, uint32_t W, sk_ba
                              W, kSmemBudget);
     sk_batch* b = new sk_batch();
     b->runs.assign(runs, runs + n);
-    b->W = W;
     b->per_warp = static_cast<uint32_t>(per_warp);
+    b->fit = fit;
     b->st = st;
     std::vector<JobDev> jobs(n);
-    std::vector<WorkItem> items;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     for (uint32_t i = 0; i < n; ++i) jobs[i] = runs[i]->job;
-    // items grouped by kernel class, runs in the given order within a class
-    for (int cls = 0; cls < 8; ++cls) {
-        const uint32_t first = static_cast<uint32_t>(items.size());
-        for (uint32_t i = 0; i < n; ++i) {
-            const sk_run* r = runs[i];
-            if (sk::step_class(r->inst->kind, r->p.rule, r->p.K) != cls) continue;
-            for (uint32_t c = 0; c < r->chains; c += W)
-                items.push_back(WorkItem{i, c, std::min(W, r->chains - c), 0});
-        }
-        const uint32_t cnt = static_cast<uint32_t>(items.size()) - first;
-        if (!cnt) continue;
-        const int occ = sk::step_kernel_occupancy(cls, W, per_warp * W);
-        if (occ <= 0) {
-            delete b;
-            return fail(SK_ERR_CUDA, "step kernel cannot be resident with %u warps and %zu bytes", W,
-                        per_warp * W);
-        }
-        const uint32_t grid = std::min<uint32_t>(cnt, static_cast<uint32_t>(occ * sms));
-        b->classes.push_back(sk_batch::Class{cls, first, cnt, grid});
-        b->grid = std::max(b->grid, grid);
-    }
-    b->n_items = static_cast<uint32_t>(items.size());
     sk_status s = dalloc(&b->djobs, n * sizeof(JobDev));
-    if (s == SK_OK) s = dalloc(&b->ditems, items.size() * sizeof(WorkItem));
     if (s == SK_OK) s = dalloc(&b->dqueue, 8 * sizeof(uint32_t));
     if (s == SK_OK) {
         cudaError_t e = cudaMemcpy(b->djobs, jobs.data(), n * sizeof(JobDev), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess)
-            e = cudaMemcpy(b->ditems, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) s = fail(SK_ERR_CUDA, "batch upload: %s", cudaGetErrorString(e));
     }
+    if (s == SK_OK) s = plan_batch(b, W);
     if (s != SK_OK) {
         cudaFree(b->djobs);
         cudaFree(b->ditems);
@@ -732,33 +761,207 @@ sk_status launch_segment(sk_batch* b, uint64_t steps) {
 }
 }  // namespace
 
-sk_status mcmcmc_batch_advance(sk_batch* b, uint64_t steps) {
-    if (!b) return fail(SK_ERR_INVALID_ARG, "batch is NULL");
-    if (steps == 0) return SK_OK;
-    uint32_t M = 0;
-    const sk_run* lead = nullptr;
-    for (sk_run* r : b->runs) {
-        if (r->step + steps > 0xFFFFFFFFull)
-            return fail(SK_ERR_INVALID_ARG, "a run would pass 2^32 steps");
+namespace {
+
+// Recompute period shared by the batch's recomputing runs (0 if none) and
+// the run whose phase defines the segments; errors if they disagree.
+sk_status recompute_period(const sk_batch* b, uint32_t* M, const sk_run** lead) {
+    *M = 0;
+    *lead = nullptr;
+    for (const sk_run* r : b->runs) {
         if (!r->p.recompute_every) continue;
-        if (!lead) {
-            lead = r;
-            M = r->p.recompute_every;
-        } else if (r->p.recompute_every != M || r->step % M != lead->step % M) {
+        if (!*lead) {
+            *lead = r;
+            *M = r->p.recompute_every;
+        } else if (r->p.recompute_every != *M || r->step % *M != (*lead)->step % *M) {
             return fail(SK_ERR_INVALID_ARG, "runs of a batch that recompute must share recompute_every and phase");
         }
     }
+    return SK_OK;
+}
+
+// Enqueues `steps` steps of every run (segments ending on recompute points).
+sk_status enqueue_advance(sk_batch* b, uint64_t steps) {
+    uint32_t M;
+    const sk_run* lead;
+    sk_status s = recompute_period(b, &M, &lead);
+    if (s != SK_OK) return s;
     if (!M) return launch_segment(b, steps);
-    // segments end on multiples of M; the recomputing runs are recomputed there
     while (steps) {
         const uint64_t seg = std::min<uint64_t>(steps, M - lead->step % M);
-        sk_status s = launch_segment(b, seg);
-        if (s != SK_OK) return s;
+        if ((s = launch_segment(b, seg)) != SK_OK) return s;
         steps -= seg;
         if (lead->step % M == 0)
             for (sk_run* r : b->runs)
                 if (r->p.recompute_every && (s = periodic_recompute(r)) != SK_OK) return s;
     }
+    return SK_OK;
+}
+
+}  // namespace
+
+sk_status mcmcmc_batch_advance(sk_batch* b, uint64_t steps) {
+    if (!b) return fail(SK_ERR_INVALID_ARG, "batch is NULL");
+    if (steps == 0) return SK_OK;
+    for (sk_run* r : b->runs)
+        if (r->step + steps > 0xFFFFFFFFull) return fail(SK_ERR_INVALID_ARG, "a run would pass 2^32 steps");
+    return enqueue_advance(b, steps);
+}
+
+sk_status mcmcmc_batch_capture(sk_batch* b, uint64_t steps) {
+    if (!b || steps == 0) return fail(SK_ERR_INVALID_ARG, "NULL batch or zero steps");
+    if (!b->st) return fail(SK_ERR_INVALID_ARG, "graph capture needs a stream other than the legacy default stream");
+    uint32_t M;
+    const sk_run* lead;
+    sk_status s = recompute_period(b, &M, &lead);
+    if (s != SK_OK) return s;
+    if (M && (steps % M || lead->step % M))
+        return fail(SK_ERR_INVALID_ARG, "with recompute_every = %u, capture %u-aligned multiples of it", M, M);
+    for (sk_run* r : b->runs)  // allocations happen before the capture
+        if (r->p.recompute_every && (s = ensure_recompute(r)) != SK_OK) return s;
+    SK_CU(cudaStreamSynchronize(b->st));
+    std::vector<uint64_t> mirror;
+    std::vector<uint64_t> nrec;
+    for (sk_run* r : b->runs) {
+        mirror.push_back(r->step);
+        nrec.push_back(r->n_recomputes);
+    }
+    SK_CU(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+    s = enqueue_advance(b, steps);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(b->st, &g);
+    for (size_t i = 0; i < b->runs.size(); ++i) {  // nothing ran yet
+        b->runs[i]->step = mirror[i];
+        b->runs[i]->n_recomputes = nrec[i];
+    }
+    if (s != SK_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+    }
+    if (e != cudaSuccess) return fail(SK_ERR_CUDA, "stream capture: %s", cudaGetErrorString(e));
+    cudaGraphExec_t x = nullptr;
+    const cudaError_t e2 = cudaGraphInstantiate(&x, g, 0);
+    cudaGraphDestroy(g);
+    if (e2 != cudaSuccess) return fail(SK_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e2));
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = x;
+    b->graph_steps = steps;
+    return SK_OK;
+}
+
+sk_status mcmcmc_batch_replay(sk_batch* b, uint32_t times) {
+    if (!b || !b->graph) return fail(SK_ERR_INVALID_ARG, "no captured graph");
+    for (sk_run* r : b->runs)
+        if (r->step + b->graph_steps * times > 0xFFFFFFFFull)
+            return fail(SK_ERR_INVALID_ARG, "a run would pass 2^32 steps");
+    for (uint32_t k = 0; k < times; ++k) {
+        SK_CU(cudaGraphLaunch(b->graph, b->st));
+        for (sk_run* r : b->runs) {
+            if (r->p.recompute_every) r->n_recomputes += b->graph_steps / r->p.recompute_every;
+            r->step += b->graph_steps;
+        }
+    }
+    return SK_OK;
+}
+
+sk_status mcmcmc_batch_autotune(sk_batch* b, uint32_t trial_steps, uint32_t* out_W) {
+    if (!b || trial_steps == 0) return fail(SK_ERR_INVALID_ARG, "NULL batch or zero trial steps");
+    // candidate chains-per-CTA values that fit in shared memory
+    std::vector<uint32_t> cand;
+    for (uint32_t w : {32u, 28u, 24u, 20u, 16u, 12u, 8u, 6u, 4u, 2u})
+        if (w <= b->fit) cand.push_back(w);
+    // back up every run's mutable state; trials run with records and traces off
+    struct Backup {
+        void* s;
+        void* h;
+        void* acc;
+        void* work;
+        void* step;
+    };
+    std::vector<Backup> bk;
+    sk_status s = SK_OK;
+    SK_CU(cudaStreamSynchronize(b->st));
+    for (sk_run* r : b->runs) {
+        Backup x{};
+        const size_t C = r->chains, np = r->inst->Npad;
+        if (s == SK_OK) s = dalloc(&x.s, C * np);
+        if (s == SK_OK) s = dalloc(&x.h, C * np * 4);
+        if (s == SK_OK) s = dalloc(&x.acc, C * 4);
+        if (s == SK_OK) s = dalloc(&x.work, C * 16);
+        if (s == SK_OK) s = dalloc(&x.step, 8);
+        bk.push_back(x);
+        if (s != SK_OK) break;
+        cudaMemcpyAsync(x.s, r->ds, C * np, cudaMemcpyDeviceToDevice, b->st);
+        cudaMemcpyAsync(x.h, r->dh, C * np * 4, cudaMemcpyDeviceToDevice, b->st);
+        cudaMemcpyAsync(x.acc, r->dacc, C * 4, cudaMemcpyDeviceToDevice, b->st);
+        cudaMemcpyAsync(x.work, r->dwork, C * 16, cudaMemcpyDeviceToDevice, b->st);
+        cudaMemcpyAsync(x.step, r->dstep, 8, cudaMemcpyDeviceToDevice, b->st);
+    }
+    auto restore = [&]() {
+        for (size_t i = 0; i < b->runs.size() && i < bk.size(); ++i) {
+            sk_run* r = b->runs[i];
+            const size_t C = r->chains, np = r->inst->Npad;
+            cudaMemcpyAsync(r->ds, bk[i].s, C * np, cudaMemcpyDeviceToDevice, b->st);
+            cudaMemcpyAsync(r->dh, bk[i].h, C * np * 4, cudaMemcpyDeviceToDevice, b->st);
+            cudaMemcpyAsync(r->dacc, bk[i].acc, C * 4, cudaMemcpyDeviceToDevice, b->st);
+            cudaMemcpyAsync(r->dwork, bk[i].work, C * 16, cudaMemcpyDeviceToDevice, b->st);
+            cudaMemcpyAsync(r->dstep, bk[i].step, 8, cudaMemcpyDeviceToDevice, b->st);
+        }
+    };
+    std::vector<JobDev> quiet;
+    for (sk_run* r : b->runs) {
+        JobDev j = r->job;
+        j.rec_capacity = 0;
+        j.trace_chains = 0;
+        quiet.push_back(j);
+    }
+    const uint32_t W0 = b->W;
+    uint32_t best = W0;
+    float best_ms = 1e30f;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (s == SK_OK) {
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaMemcpy(b->djobs, quiet.data(), quiet.size() * sizeof(JobDev), cudaMemcpyHostToDevice);
+        std::vector<uint64_t> mirror;
+        for (sk_run* r : b->runs) mirror.push_back(r->step);
+        for (uint32_t w : cand) {
+            if ((s = plan_batch(b, w)) != SK_OK) break;
+            if ((s = launch_segment(b, trial_steps)) != SK_OK) break;  // warm-up
+            restore();
+            cudaEventRecord(e0, b->st);
+            if ((s = launch_segment(b, trial_steps)) != SK_OK) break;
+            cudaEventRecord(e1, b->st);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            restore();
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = w;
+            }
+        }
+        for (size_t i = 0; i < b->runs.size(); ++i) b->runs[i]->step = mirror[i];
+        std::vector<JobDev> jobs;
+        for (sk_run* r : b->runs) jobs.push_back(r->job);
+        cudaMemcpy(b->djobs, jobs.data(), jobs.size() * sizeof(JobDev), cudaMemcpyHostToDevice);
+        cudaStreamSynchronize(b->st);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    for (Backup& x : bk) {
+        cudaFree(x.s);
+        cudaFree(x.h);
+        cudaFree(x.acc);
+        cudaFree(x.work);
+        cudaFree(x.step);
+    }
+    if (s != SK_OK) {
+        plan_batch(b, W0);
+        return s;
+    }
+    if ((s = plan_batch(b, best)) != SK_OK) return s;
+    if (out_W) *out_W = best;
     return SK_OK;
 }
 
@@ -775,6 +978,7 @@ sk_status mcmcmc_batch_info(const sk_batch* b, uint32_t* grid, uint32_t* W, uint
 sk_status mcmcmc_batch_free(sk_batch* b) {
     if (!b) return fail(SK_ERR_INVALID_ARG, "batch is NULL");
     cudaStreamSynchronize(b->st);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
     cudaFree(b->djobs);
     cudaFree(b->ditems);
     cudaFree(b->dqueue);

@@ -30,7 +30,8 @@ EXPORTS = ["sk_create_instance", "sk_set_couplings", "sk_destroy_instance", "sk_
            "mcmcmc_create", "mcmcmc_advance", "mcmcmc_run", "mcmcmc_reset", "mcmcmc_wait",
            "mcmcmc_observables", "mcmcmc_state", "mcmcmc_recompute", "mcmcmc_recompute_stats",
            "mcmcmc_trace", "mcmcmc_counters", "mcmcmc_free",
-           "mcmcmc_batch_create", "mcmcmc_batch_advance", "mcmcmc_batch_info",
+           "mcmcmc_batch_create", "mcmcmc_batch_advance", "mcmcmc_batch_capture",
+           "mcmcmc_batch_replay", "mcmcmc_batch_autotune", "mcmcmc_batch_info",
            "mcmcmc_batch_free", "mcmcmc_run_noalloc", "sk_last_error"]
 
 
@@ -91,6 +92,9 @@ def lib(build_if_missing: bool = True):
             "mcmcmc_free": [vp],
             "mcmcmc_batch_create": [P, u32, u32, P],
             "mcmcmc_batch_advance": [vp, u64],
+            "mcmcmc_batch_capture": [vp, u64],
+            "mcmcmc_batch_replay": [vp, u32],
+            "mcmcmc_batch_autotune": [vp, u32, vp],
             "mcmcmc_batch_info": [vp, vp, vp, vp, vp],
             "mcmcmc_batch_free": [vp],
             "mcmcmc_run_noalloc": [u32, u32, vp, d, u32, u32, u32, d, u64, u32, u64, vp, vp, vp],
@@ -308,6 +312,17 @@ class Batch:
 
     def advance(self, steps: int):
         _check(lib().mcmcmc_batch_advance(self.handle, int(steps)))
+
+    def capture(self, steps: int):
+        _check(lib().mcmcmc_batch_capture(self.handle, int(steps)))
+
+    def replay(self, times: int = 1):
+        _check(lib().mcmcmc_batch_replay(self.handle, int(times)))
+
+    def autotune(self, trial_steps: int = 20) -> int:
+        w = C.c_uint32(0)
+        _check(lib().mcmcmc_batch_autotune(self.handle, int(trial_steps), C.byref(w)))
+        return w.value
 
     def info(self):
         v = [C.c_uint32(0) for _ in range(4)]
