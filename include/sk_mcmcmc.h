@@ -324,6 +324,82 @@ sk_status mcmcmc_run_noalloc(uint32_t N, uint32_t kind, const void* couplings, d
                              uint64_t seed, uint32_t stream_id, uint64_t steps, int8_t* spins,
                              double* energy, void* stream);
 
+/* ---------------------------------------------------------------------- */
+/* Request server: continuous batching of sampling jobs                    */
+/* ---------------------------------------------------------------------- */
+typedef struct sk_server sk_server;
+
+typedef enum { SK_JOB_QUEUED = 0, SK_JOB_RUNNING = 1, SK_JOB_DONE = 2, SK_JOB_FAILED = 3 } sk_job_state;
+
+typedef struct {
+    uint32_t N, kind;         /* couplings: N spins, sk_jkind                       */
+    const void* couplings;    /* host N*N, copied at submit (couplings_id == 0)      */
+    uint64_t couplings_id;    /* nonzero: couplings registered with                 */
+                              /*   sk_server_add_couplings (couplings may be NULL)  */
+    double scale;             /* energy scale, > 0                                  */
+    uint32_t chains, K, rule; /* as in sk_run_params                                */
+    double beta;
+    uint64_t seed;
+    uint32_t stream_id;
+    uint64_t steps;           /* Monte Carlo steps of every chain, 1 .. 2^32-1      */
+    const int8_t* init_spins; /* host chains*N (+-1) copied at submit, or NULL      */
+} sk_job;
+
+typedef struct {
+    uint32_t state;           /* sk_job_state                                       */
+    sk_status error;          /* SK_ERR_OOM: larger than the server's budget        */
+    double t_submit, t_admit, t_done;  /* seconds since the server's creation       */
+    uint64_t footprint_bytes; /* device bytes charged against the budget            */
+} sk_job_status;
+
+typedef struct {
+    uint64_t chain_steps, candidates, quanta, completed;
+    double busy_seconds, elapsed_seconds;  /* device-busy and wall time              */
+    uint64_t device_bytes_in_use, queued, running;
+} sk_server_stats_t;
+
+/*
+ * sk_server_create: starts a request server with a worker thread and its own
+ * CUDA stream on the current device.  It runs the admitted jobs in quanta of
+ * `quantum_steps` steps: between quanta it retires finished jobs (final spins
+ * and energies copied back, device memory released) and admits queued jobs,
+ * first in first out, while their device footprint (couplings unless already
+ * resident, 5 bytes per spin per chain, per-chain counters) fits
+ * `budget_bytes`; each quantum advances every admitted job in one launch per
+ * kernel class.  A job's result does not depend on the other jobs it shared
+ * launches with (counter-based draws).  The paper's problem statement
+ * (Sec. II) applied to many independent requests.
+ */
+sk_status sk_server_create(uint64_t budget_bytes, uint32_t quantum_steps, sk_server** out);
+
+/* Registers couplings (host copy kept by the server) under a nonzero id for
+ * jobs to share; the device copy is made when a job first needs it and kept
+ * while the budget allows. */
+sk_status sk_server_add_couplings(sk_server* s, uint64_t couplings_id, uint32_t N, uint32_t kind,
+                                  const void* couplings, double scale);
+
+/* Queues a job; *ticket identifies it.  Jobs larger than the budget are
+ * marked failed with SK_ERR_OOM at once. */
+sk_status sk_server_submit(sk_server* s, const sk_job* job, uint64_t* ticket);
+
+/* Current status of a job (host struct). */
+sk_status sk_server_poll(sk_server* s, uint64_t ticket, sk_job_status* status);
+
+/* Result of a finished job: energies (chains doubles), spins (chains*N int8,
+ * may be NULL), spins flipped in total (may be NULL); host pointers.  Returns
+ * SK_ERR_NOT_READY while the job is queued or running, the job's error if it
+ * failed.  The job is forgotten afterwards. */
+sk_status sk_server_result(sk_server* s, uint64_t ticket, double* energies, int8_t* spins,
+                           uint64_t* flips);
+
+/* Blocks until no job is queued or running (timeout_ns 0 = no limit). */
+sk_status sk_server_wait_all(sk_server* s, uint64_t timeout_ns);
+
+sk_status sk_server_stats(sk_server* s, sk_server_stats_t* out);
+
+/* Stops the worker (queued jobs are dropped) and frees everything. */
+sk_status sk_server_destroy(sk_server* s);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* sk_last_error(void);
 

@@ -455,6 +455,7 @@ sk_status mcmcmc_create(sk_instance* in, const sk_run_params* p, sk_run** out) {
     j.wlen = r->wlen;
     j.record_every = r->p.record_every;
     j.trace_chains = r->p.trace_chains;
+    j.step_limit = 0xFFFFFFFFu;
     s = init_state(r, p->init_spins, p->init_mem);
     if (s == SK_OK) {
         sk_run* one[1] = {r};
@@ -756,10 +757,12 @@ sk_status launch_segment(sk_batch* b, uint64_t steps) {
                                         b->st);
         if (e != cudaSuccess) return fail(SK_ERR_CUDA, "step launch: %s", cudaGetErrorString(e));
     }
-    for (sk_run* r : b->runs) r->step += steps;
+    for (sk_run* r : b->runs) r->step = std::min<uint64_t>(r->step + steps, r->job.step_limit);
     return SK_OK;
 }
 }  // namespace
+
+
 
 namespace {
 
@@ -858,7 +861,7 @@ sk_status mcmcmc_batch_replay(sk_batch* b, uint32_t times) {
         SK_CU(cudaGraphLaunch(b->graph, b->st));
         for (sk_run* r : b->runs) {
             if (r->p.recompute_every) r->n_recomputes += b->graph_steps / r->p.recompute_every;
-            r->step += b->graph_steps;
+            r->step = std::min<uint64_t>(r->step + b->graph_steps, r->job.step_limit);
         }
     }
     return SK_OK;
@@ -987,3 +990,19 @@ sk_status mcmcmc_batch_free(sk_batch* b) {
 }
 
 }  // extern "C"
+
+namespace sk {
+// The run stops at `limit` steps in every later advance (used by the server).
+void set_step_limit(sk_run* r, uint32_t limit) { r->job.step_limit = limit; }
+uint64_t host_step(const sk_run* r) { return r->step; }
+size_t run_footprint(uint32_t N, uint32_t kind, uint32_t chains, uint64_t records) {
+    const size_t np = pad_n(N);
+    return static_cast<size_t>(chains) * np * 5 + static_cast<size_t>(chains) * 20 +
+           records * (static_cast<size_t>(chains) * 12 + static_cast<size_t>(chains / 2) * 8) +
+           (kind == SK_J_PM1 ? (4 * static_cast<size_t>(N) + 5) * 8 : 0) + 4096;
+}
+size_t instance_footprint(uint32_t N, uint32_t kind) {
+    const size_t np = pad_n(N);
+    return np * np * jbytes(kind);
+}
+}  // namespace sk

@@ -37,7 +37,8 @@ struct alignas(16) JobDev {
     uint32_t N, Npad, chains, K;
     uint32_t kind, rule, wlen, record_every;
     uint32_t trace_chains;
-    uint32_t pad_[3];
+    uint32_t step_limit;    // the run stops at this step (0xFFFFFFFF: no limit)
+    uint32_t pad_[2];
 };
 static_assert(sizeof(JobDev) % 16 == 0, "JobDev is copied as 16-byte words");
 
@@ -83,6 +84,15 @@ cudaError_t launch_recompute(uint32_t kind, const int8_t* s, void* h, float* out
                              const void* j_op, double* dE, unsigned long long* stats, int* err,
                              uint32_t chains, uint32_t npad, uint32_t terms, uint32_t mode, double scale,
                              cudaStream_t st);
+
+}  // namespace sk
+struct sk_run;
+namespace sk {
+// Host-side helpers for the request server (sk_capi.cu).
+void set_step_limit(sk_run* r, uint32_t limit);
+uint64_t host_step(const sk_run* r);
+size_t run_footprint(uint32_t N, uint32_t kind, uint32_t chains, uint64_t records);
+size_t instance_footprint(uint32_t N, uint32_t kind);
 
 // Sets the message sk_last_error() returns on this thread (sk_capi.cu).
 void set_error_message(const char* msg);

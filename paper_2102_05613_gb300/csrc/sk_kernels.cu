@@ -630,7 +630,8 @@ __global__ void __launch_bounds__(MAXT, 1)
         const int8_t* partner_s =
             reinterpret_cast<const int8_t*>(smem + static_cast<size_t>(warp ^ 1) * per_warp);
         const uint32_t t0 = static_cast<uint32_t>(*jb.step);
-        const uint32_t t1 = t0 + nsteps;
+        const uint32_t t1 = static_cast<uint32_t>(min(static_cast<uint64_t>(t0) + nsteps,
+                                                      static_cast<uint64_t>(jb.step_limit)));
         uint32_t acc = 0, n_flips = 0, n_rows = 0;
         if (active) {
             // load the chain's state: spins (npad bytes), fields (4 npad bytes)
@@ -644,7 +645,7 @@ __global__ void __launch_bounds__(MAXT, 1)
             acc = jb.acc_run[chain];
         }
         __syncwarp();
-        if (nsteps)
+        if (t1 > t0)
             chain_loop<JT, RULE, NB>(jb, active, chain, wm, partner_s, t0, t1, acc, phase, dead,
                                      n_flips, n_rows);
         __syncwarp();
@@ -667,7 +668,11 @@ __global__ void __launch_bounds__(MAXT, 1)
 
 __global__ void bump_steps(const JobDev* __restrict__ jobs, uint32_t n_jobs, uint64_t nsteps) {
     const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < n_jobs) *jobs[j].step += nsteps;
+    if (j < n_jobs) {
+        const uint64_t lim = jobs[j].step_limit;
+        const uint64_t s = *jobs[j].step + nsteps;
+        *jobs[j].step = s < lim ? s : lim;
+    }
 }
 
 // Start state: spins from `init` (chains x N, +-1) or Philox domain 1

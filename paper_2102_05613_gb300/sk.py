@@ -354,3 +354,119 @@ def run_noalloc(couplings, spins, energy, *, scale=1.0, K=8, rule=SK_RULE_MCMCMC
                                     int(K), int(rule), float(beta), int(seed), int(stream_id),
                                     int(steps), C.c_void_p(spins.data_ptr()),
                                     C.c_void_p(energy.data_ptr()), _stream_handle(stream)))
+
+
+# ---------------------------------------------------------------------------
+# request server
+# ---------------------------------------------------------------------------
+class Job(C.Structure):
+    _fields_ = [("N", C.c_uint32), ("kind", C.c_uint32), ("couplings", C.c_void_p),
+                ("couplings_id", C.c_uint64), ("scale", C.c_double), ("chains", C.c_uint32),
+                ("K", C.c_uint32), ("rule", C.c_uint32), ("beta", C.c_double), ("seed", C.c_uint64),
+                ("stream_id", C.c_uint32), ("steps", C.c_uint64), ("init_spins", C.c_void_p)]
+
+
+class JobStatus(C.Structure):
+    _fields_ = [("state", C.c_uint32), ("error", C.c_int), ("t_submit", C.c_double),
+                ("t_admit", C.c_double), ("t_done", C.c_double), ("footprint_bytes", C.c_uint64)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("chain_steps", C.c_uint64), ("candidates", C.c_uint64), ("quanta", C.c_uint64),
+                ("completed", C.c_uint64), ("busy_seconds", C.c_double),
+                ("elapsed_seconds", C.c_double), ("device_bytes_in_use", C.c_uint64),
+                ("queued", C.c_uint64), ("running", C.c_uint64)]
+
+
+SK_JOB_QUEUED, SK_JOB_RUNNING, SK_JOB_DONE, SK_JOB_FAILED = range(4)
+EXPORTS += ["sk_server_create", "sk_server_add_couplings", "sk_server_submit", "sk_server_poll",
+            "sk_server_result", "sk_server_wait_all", "sk_server_stats", "sk_server_destroy"]
+
+
+def _server_sigs(L):
+    vp, u32, u64, d = C.c_void_p, C.c_uint32, C.c_uint64, C.c_double
+    sig = {"sk_server_create": [u64, u32, C.POINTER(C.c_void_p)],
+           "sk_server_add_couplings": [vp, u64, u32, u32, vp, d],
+           "sk_server_submit": [vp, C.POINTER(Job), C.POINTER(C.c_uint64)],
+           "sk_server_poll": [vp, u64, C.POINTER(JobStatus)],
+           "sk_server_result": [vp, u64, vp, vp, C.POINTER(C.c_uint64)],
+           "sk_server_wait_all": [vp, u64],
+           "sk_server_stats": [vp, C.POINTER(ServerStats)],
+           "sk_server_destroy": [vp]}
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = C.c_int
+
+
+def _check_server(status, what):
+    if status != SK_OK:
+        raise SKError(status, what)
+
+
+class Server:
+    """sk_server_*: continuous batching of sampling jobs on one GPU."""
+
+    def __init__(self, budget_bytes: int, quantum_steps: int = 256):
+        _server_sigs(lib())
+        h = C.c_void_p()
+        _check_server(lib().sk_server_create(int(budget_bytes), int(quantum_steps), C.byref(h)),
+                      "sk_server_create")
+        self.handle = h
+        self._keep = {}
+
+    def add_couplings(self, couplings_id: int, J, scale: float = 1.0):
+        J = np.ascontiguousarray(J)
+        kind = SK_J_PM1 if J.dtype == np.int8 else SK_J_GAUSS
+        _check_server(lib().sk_server_add_couplings(self.handle, int(couplings_id), J.shape[0], kind,
+                                                    J.ctypes.data_as(C.c_void_p), float(scale)),
+                      "sk_server_add_couplings")
+
+    def submit(self, *, N, kind, chains, steps, K=8, rule=SK_RULE_MCMCMC, beta=1.0, seed=1,
+               stream_id=0, J=None, couplings_id=0, scale=1.0, init=None) -> int:
+        j = Job()
+        j.N, j.kind, j.chains, j.steps = int(N), int(kind), int(chains), int(steps)
+        j.K, j.rule, j.beta, j.seed, j.stream_id = int(K), int(rule), float(beta), int(seed), int(stream_id)
+        j.couplings_id, j.scale = int(couplings_id), float(scale)
+        if J is not None:
+            J = np.ascontiguousarray(J)
+            j.couplings = J.ctypes.data_as(C.c_void_p).value
+        if init is not None:
+            init = np.ascontiguousarray(init, dtype=np.int8)
+            j.init_spins = init.ctypes.data_as(C.c_void_p).value
+        t = C.c_uint64(0)
+        _check_server(lib().sk_server_submit(self.handle, C.byref(j), C.byref(t)), "sk_server_submit")
+        return t.value
+
+    def poll(self, ticket: int) -> dict:
+        st = JobStatus()
+        _check_server(lib().sk_server_poll(self.handle, int(ticket), C.byref(st)), "sk_server_poll")
+        return {k: getattr(st, k) for k, _ in JobStatus._fields_}
+
+    def result(self, ticket: int, chains: int, N: int):
+        E = np.zeros(chains)
+        S = np.zeros((chains, N), dtype=np.int8)
+        f = C.c_uint64(0)
+        _check_server(lib().sk_server_result(self.handle, int(ticket), E.ctypes.data_as(C.c_void_p),
+                                             S.ctypes.data_as(C.c_void_p), C.byref(f)),
+                      "sk_server_result")
+        return E, S, f.value
+
+    def wait_all(self, timeout_ns: int = 0):
+        _check_server(lib().sk_server_wait_all(self.handle, int(timeout_ns)), "sk_server_wait_all")
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check_server(lib().sk_server_stats(self.handle, C.byref(st)), "sk_server_stats")
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().sk_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
