@@ -338,6 +338,138 @@ def run_ttt(args):
 
 
 # ---------------------------------------------------------------------------
+# uneven batch: 256 instances of N in 128..4096 (half +-J, half Gaussian),
+# 256..2048 chains, K in 16..256, beta in [0.5, 3]; autotuned, CUDA graphs
+# ---------------------------------------------------------------------------
+def run_uneven(args):
+    import torch
+    from paper_2102_05613_gb300 import inputs, sk
+    torch.cuda.set_device(0)
+    st = torch.cuda.Stream()
+    specs = inputs.uneven_batch(256, seed=0)
+    g = torch.Generator(device="cuda")
+    insts, runs = [], []
+    with torch.cuda.stream(st):
+        for i, sp in enumerate(specs):
+            N = sp["N"]
+            g.manual_seed(sp["jseed"])
+            if sp["kind"] == sk.SK_J_PM1:
+                J = (2 * torch.randint(0, 2, (N, N), generator=g, device="cuda") - 1).to(torch.int8)
+            else:
+                J = torch.randn((N, N), generator=g, device="cuda") / math.sqrt(N)
+            J = torch.triu(J, 1)
+            J = (J + J.T).contiguous()
+            insts.append(sk.Instance(J, stream=st))
+            runs.append(sk.Run(insts[-1], chains=sp["chains"], K=sp["K"], beta=sp["beta"], seed=3,
+                               stream_id=i, record_every=R, max_records=args.warmup + args.steps + 2))
+    torch.cuda.synchronize()
+    batch = sk.Batch(runs)
+    t0 = time.perf_counter()
+    batch.autotune(trial_steps=10)
+    tune_s = time.perf_counter() - t0
+    batch.capture(R)
+    batch.replay(args.warmup)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = Clocks(0)
+    for a, b in ev:
+        a.record(st)
+        batch.replay(1)
+        b.record(st)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    T = ev[0][0].elapsed_time(ev[-1][1]) / 1e3
+    cand = sum(sp["chains"] * sp["K"] for sp in specs) * R * args.steps
+    cs = sum(sp["chains"] for sp in specs) * R * args.steps
+    out = {"config": "uneven batch", "workload": "256 SK instances, N uniform in 128..4096 (even: +-J "
+           "int8, odd: Gaussian fp32), 256..2048 chains, K uniform in 16..256, beta uniform in "
+           "[0.5, 3], MCMCMC; one CUDA graph = 100 steps of every chain (one persistent launch per "
+           "launch class)", "metric": UNIT, "value": cand / T, "mc_steps_per_s": cs / T,
+           "ms_per_step": 1e3 * T / args.steps, "steps": args.steps, "warmup": args.warmup,
+           "autotune_s": tune_s, "classes": batch.classes(), "clocks": clk,
+           "chains_total": sum(sp["chains"] for sp in specs)}
+    batch.close()
+    for r in runs:
+        r.close()
+    for x in insts:
+        x.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# serving: Poisson arrivals of sampling jobs into the request server
+# ---------------------------------------------------------------------------
+def _serve_once(rate, duration, pool, budget, quantum, seed):
+    import numpy as np
+    from paper_2102_05613_gb300 import inputs, sk
+    srv = sk.Server(budget_bytes=budget, quantum_steps=quantum)
+    for cid, (N, kind, J) in pool.items():
+        srv.add_couplings(cid, J)
+    jobs = inputs.poisson_jobs(rate, duration, seed=seed)
+    rng = np.random.Generator(np.random.PCG64(seed + 1))
+    ids = list(pool.keys())
+    tickets = []
+    t0 = time.perf_counter()
+    for k, jb in enumerate(jobs):
+        cid = ids[int(rng.integers(0, len(ids)))]
+        N, kind, _ = pool[cid]
+        delay = jb["t_arrive"] - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        rule = sk.SK_RULE_METROPOLIS if jb["K"] == 1 else sk.SK_RULE_MCMCMC
+        tk = srv.submit(N=N, kind=kind, chains=jb["chains"], steps=jb["steps"], K=jb["K"], rule=rule,
+                        beta=jb["beta"], seed=jb["seed"], stream_id=k & 0xFFFFFF, couplings_id=cid)
+        tickets.append((tk, jb, N))
+    submit_s = time.perf_counter() - t0
+    srv.wait_all()
+    st = [srv.poll(t) for t, _, _ in tickets]
+    lat = np.array([x["t_done"] - x["t_submit"] for x in st if x["state"] == sk.SK_JOB_DONE])
+    wait = np.array([x["t_admit"] - x["t_submit"] for x in st if x["state"] == sk.SK_JOB_DONE])
+    done = [x for x in st if x["state"] == sk.SK_JOB_DONE]
+    cand = sum(jb["chains"] * jb["steps"] * jb["K"] for (t, jb, N), x in zip(tickets, st)
+               if x["state"] == sk.SK_JOB_DONE)
+    offered = sum(jb["chains"] * jb["steps"] * jb["K"] for _, jb, _ in tickets)
+    span = max(x["t_done"] for x in done) - min(x["t_submit"] for x in st) if done else float("nan")
+    sstat = srv.stats()
+    srv.close()
+    return {"rate_per_s": rate, "arrival_window_s": duration, "jobs": len(jobs),
+            "completed": len(done), "failed": len(st) - len(done),
+            "latency_p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
+            "latency_p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
+            "queue_wait_p50_s": float(np.percentile(wait, 50)) if len(wait) else None,
+            "throughput_candidates_per_s": cand / span, "span_s": span, "submit_s": submit_s,
+            "offered_candidates_per_s": offered / duration,
+            "saturated": offered / duration > 1.05 * cand / span,
+            "device_busy_s": sstat["busy_seconds"], "quanta": sstat["quanta"]}
+
+
+def run_serve(args):
+    import numpy as np
+    import torch
+    from paper_2102_05613_gb300 import inputs, sk
+    torch.cuda.set_device(0)
+    # 12 disorder instances, N log-uniform in [64, 8192], half +-J / half Gaussian,
+    # registered once; each job samples one of them
+    rng = np.random.Generator(np.random.PCG64(11))
+    pool = {}
+    for i in range(12):
+        N = int(round(math.exp(rng.uniform(math.log(64), math.log(8192)))))
+        kind = i % 2
+        pool[i + 1] = (N, kind, inputs.couplings(N, kind, 7000 + i))
+    budget = 100 << 30
+    res = [_serve_once(args.serve_rate, args.serve_window, pool, budget, 256, seed=1),
+           _serve_once(args.serve_low_rate, args.serve_window, pool, budget, 256, seed=2)]
+    out = {"config": "serving", "workload": "Poisson arrivals of SK sampling jobs; each job: one of 12 "
+           "registered instances (N log-uniform in [64, 8192], +-J or Gaussian), beta U[0.3, 3], K in "
+           "{1 (Metropolis), 16, 64, 256}, steps log-uniform [1e3, 1e5], chains log-uniform [1, 4096]; "
+           "server: 100 GiB budget, 256-step quanta", "runs": res}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def run_ours(args):
@@ -504,6 +636,12 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--config", choices=["default", "uneven"], default="default",
+                    help="uneven: the 256-instance uneven batch in CUDA graphs instead of the bench line")
+    ap.add_argument("--serve", action="store_true", help="the request-server measurement")
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-low-rate", type=float, default=10.0)
+    ap.add_argument("--serve-window", type=float, default=5.0)
     ap.add_argument("--ttt", action="store_true",
                     help="time-to-thermalise comparison instead of the throughput line")
     ap.add_argument("--no-recompute", action="store_true",
@@ -520,6 +658,10 @@ def main():
         return run_reference(args)
     if args.ttt:
         return run_ttt(args)
+    if args.config == "uneven":
+        return run_uneven(args)
+    if args.serve:
+        return run_serve(args)
     return run_ours(args)
 
 

@@ -257,20 +257,31 @@ sk_status mcmcmc_batch_capture(sk_batch* b, uint64_t steps);
 sk_status mcmcmc_batch_replay(sk_batch* b, uint32_t times);
 
 /*
- * mcmcmc_batch_autotune: times a `trial_steps`-step advance of the batch for
- * each chains-per-CTA value that fits in shared memory (32, 28, ..., 2; the
- * value also selects the kernel's register budget) and keeps the fastest.
+ * mcmcmc_batch_autotune: for each launch class of the batch, times a
+ * `trial_steps`-step launch for each chains-per-CTA value that fits in shared
+ * memory (32, 28, ..., 2; the value also selects the kernel's register
+ * budget) and keeps the fastest.
  * Trials start from a copy of the runs' state, which is restored afterwards,
  * and run with records and traces off: the runs' trajectories, records and
  * step counters are unchanged.  *warps_per_cta (may be NULL) receives the
- * choice.  Synchronises.
+ * first class's choice.  Synchronises.
  */
 sk_status mcmcmc_batch_autotune(sk_batch* b, uint32_t trial_steps, uint32_t* warps_per_cta);
 
-/* Launch geometry chosen for the batch (for reports): CTAs, warps per CTA,
- * dynamic shared memory bytes per CTA, work items. */
+/* Launch geometry of the batch (for reports): the largest grid, warps per
+ * CTA and dynamic shared memory of the first launch class, total work items. */
 sk_status mcmcmc_batch_info(const sk_batch* b, uint32_t* grid, uint32_t* warps_per_cta,
                             uint32_t* smem_bytes, uint32_t* items);
+
+/*
+ * mcmcmc_batch_classes: the batch's launch classes.  Work items are grouped
+ * by kernel class (coupling kind, rule, K > 128) and by shared-memory size
+ * bucket (chains of similar N), one persistent launch per class, so small-N
+ * runs keep many chains per CTA next to large-N runs.  *count receives the
+ * number of classes; desc (5 x max uint32, may be NULL) receives per class:
+ * kernel class, shared bytes per chain, chains per CTA, work items, CTAs.
+ */
+sk_status mcmcmc_batch_classes(const sk_batch* b, uint32_t max, uint32_t* count, uint32_t* desc);
 
 sk_status mcmcmc_batch_free(sk_batch* b);
 

@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <thread>
 #include <vector>
@@ -109,16 +110,25 @@ struct sk_instance {
 };
 
 struct sk_batch {
+    // Work items are grouped by launch class: the kernel class (coupling
+    // kind, rule, Philox blocks per lane) and a shared-memory size bucket, so
+    // that runs with small N get many chains per CTA even when the batch
+    // also holds large-N runs.  Each class is one persistent launch.
     struct Class {
+        uint64_t key;            // (kernel class, size bucket)
         int cls;
+        uint32_t per_warp, fit;  // shared memory per chain, most chains per CTA that fit
+        uint32_t W;              // chains (warps) per CTA
         uint32_t first_item, n_items, grid;
     };
     std::vector<sk_run*> runs;
-    std::vector<Class> classes;  // one step-kernel launch per class present
+    std::vector<Class> classes;
+    std::map<uint64_t, uint32_t> tuned;  // key -> W chosen by the autotuner
+    uint32_t W_override = 0;             // warps_per_cta given at creation (0: fit)
     JobDev* djobs = nullptr;
     WorkItem* ditems = nullptr;
-    uint32_t* dqueue = nullptr;  // one work counter per class
-    uint32_t n_items = 0, W = 0, per_warp = 0, grid = 0, fit = 0;
+    uint32_t* dqueue = nullptr;  // one work counter per class (up to kMaxClasses)
+    uint32_t n_items = 0, grid = 0;
     cudaStream_t st = nullptr;
     cudaGraphExec_t graph = nullptr;  // mcmcmc_batch_capture
     uint64_t graph_steps = 0;
@@ -651,33 +661,57 @@ sk_status mcmcmc_free(sk_run* r) {
 
 namespace {
 
-// Work items of the batch for W chains per CTA, grouped by kernel class;
-// uploads them (replacing the previous plan).
-sk_status plan_batch(sk_batch* b, uint32_t W) {
+constexpr uint32_t kMaxClasses = 64;
+
+// Shared memory per chain (rounded to 128 bytes) and its size bucket: the
+// smallest power of two >= it.
+uint32_t run_per_warp(const sk_run* r) {
+    return static_cast<uint32_t>((sk::warp_smem_bytes(r->inst->Npad, r->inst->kind) + 127) / 128 * 128);
+}
+uint64_t class_key(const sk_run* r) {
+    uint32_t b = 128;
+    const uint32_t pw = run_per_warp(r);
+    while (b < pw) b <<= 1;
+    return (static_cast<uint64_t>(sk::step_class(r->inst->kind, r->p.rule, r->p.K)) << 32) | b;
+}
+
+// Work items of the batch, grouped by launch class (kernel class, size
+// bucket), each class with its own chains per CTA: the autotuned value, the
+// creation override, or as many as fit in shared memory.  Uploads them.
+sk_status plan_batch(sk_batch* b) {
+    std::map<uint64_t, std::vector<uint32_t>> groups;  // key -> run indices (in order)
+    const uint32_t n = static_cast<uint32_t>(b->runs.size());
+    for (uint32_t i = 0; i < n; ++i) groups[class_key(b->runs[i])].push_back(i);
+    if (groups.size() > kMaxClasses) return fail(SK_ERR_INVALID_ARG, "too many launch classes in one batch");
     std::vector<WorkItem> items;
     std::vector<sk_batch::Class> classes;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     uint32_t grid = 0;
-    const uint32_t n = static_cast<uint32_t>(b->runs.size());
-    for (int cls = 0; cls < 8; ++cls) {
-        const uint32_t first = static_cast<uint32_t>(items.size());
-        for (uint32_t i = 0; i < n; ++i) {
+    for (auto& g : groups) {
+        sk_batch::Class c{};
+        c.key = g.first;
+        c.cls = static_cast<int>(g.first >> 32);
+        for (uint32_t i : g.second) c.per_warp = std::max(c.per_warp, run_per_warp(b->runs[i]));
+        c.fit = static_cast<uint32_t>(std::min<size_t>(32, kSmemBudget / c.per_warp)) & ~1u;
+        if (c.fit < 2) return fail(SK_ERR_INVALID_ARG, "N too large: %u bytes of shared memory per chain", c.per_warp);
+        auto t = b->tuned.find(c.key);
+        c.W = t != b->tuned.end() ? t->second : (b->W_override ? std::min(b->W_override, c.fit) : c.fit);
+        c.first_item = static_cast<uint32_t>(items.size());
+        for (uint32_t i : g.second) {
             const sk_run* r = b->runs[i];
-            if (sk::step_class(r->inst->kind, r->p.rule, r->p.K) != cls) continue;
-            for (uint32_t c = 0; c < r->chains; c += W)
-                items.push_back(WorkItem{i, c, std::min(W, r->chains - c), 0});
+            for (uint32_t ch = 0; ch < r->chains; ch += c.W)
+                items.push_back(WorkItem{i, ch, std::min(c.W, r->chains - ch), 0});
         }
-        const uint32_t cnt = static_cast<uint32_t>(items.size()) - first;
-        if (!cnt) continue;
-        const int occ = sk::step_kernel_occupancy(cls, W, static_cast<size_t>(b->per_warp) * W);
+        c.n_items = static_cast<uint32_t>(items.size()) - c.first_item;
+        const int occ = sk::step_kernel_occupancy(c.cls, c.W, static_cast<size_t>(c.per_warp) * c.W);
         if (occ <= 0)
-            return fail(SK_ERR_CUDA, "step kernel cannot be resident with %u warps and %u bytes", W,
-                        b->per_warp * W);
-        const uint32_t g = std::min<uint32_t>(cnt, static_cast<uint32_t>(occ * sms));
-        classes.push_back(sk_batch::Class{cls, first, cnt, g});
-        grid = std::max(grid, g);
+            return fail(SK_ERR_CUDA, "step kernel cannot be resident with %u warps and %u bytes", c.W,
+                        c.per_warp * c.W);
+        c.grid = std::min<uint32_t>(c.n_items, static_cast<uint32_t>(occ * sms));
+        grid = std::max(grid, c.grid);
+        classes.push_back(c);
     }
     WorkItem* d = nullptr;
     sk_status s = dalloc(&d, items.size() * sizeof(WorkItem));
@@ -693,7 +727,6 @@ sk_status plan_batch(sk_batch* b, uint32_t W) {
     b->classes = classes;
     b->n_items = static_cast<uint32_t>(items.size());
     b->grid = grid;
-    b->W = W;
     if (b->graph) {  // the captured launches used the old plan
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
@@ -710,32 +743,27 @@ sk_status mcmcmc_batch_create(sk_run* const* runs, uint32_t n, uint32_t W, sk_ba
     if (W && (W < 2 || W > 32 || (W & 1u)))
         return fail(SK_ERR_INVALID_ARG, "warps_per_cta = %u must be even in 2..32", W);
     cudaStream_t st = runs[0]->inst->st;
-    size_t per_warp = 0;
     for (uint32_t i = 0; i < n; ++i) {
         if (!runs[i]) return fail(SK_ERR_INVALID_ARG, "run %u is NULL", i);
         if (runs[i]->inst->st != st) return fail(SK_ERR_INVALID_ARG, "runs of a batch must share a stream");
-        per_warp = std::max(per_warp, sk::warp_smem_bytes(runs[i]->inst->Npad, runs[i]->inst->kind));
+        const size_t pw = (sk::warp_smem_bytes(runs[i]->inst->Npad, runs[i]->inst->kind) + 127) / 128 * 128;
+        if (W && W * pw > kSmemBudget)
+            return fail(SK_ERR_INVALID_ARG, "warps_per_cta = %u needs more than %zu bytes of shared memory", W,
+                        kSmemBudget);
     }
-    per_warp = (per_warp + 127) / 128 * 128;
-    const uint32_t fit = static_cast<uint32_t>(std::min<size_t>(32, kSmemBudget / per_warp)) & ~1u;
-    if (fit < 2) return fail(SK_ERR_INVALID_ARG, "N too large: %zu bytes of shared memory per chain", per_warp);
-    if (!W) W = fit;
-    if (W > fit) return fail(SK_ERR_INVALID_ARG, "warps_per_cta = %u needs more than %zu bytes of shared memory",
-                             W, kSmemBudget);
     sk_batch* b = new sk_batch();
     b->runs.assign(runs, runs + n);
-    b->per_warp = static_cast<uint32_t>(per_warp);
-    b->fit = fit;
+    b->W_override = W;
     b->st = st;
     std::vector<JobDev> jobs(n);
     for (uint32_t i = 0; i < n; ++i) jobs[i] = runs[i]->job;
     sk_status s = dalloc(&b->djobs, n * sizeof(JobDev));
-    if (s == SK_OK) s = dalloc(&b->dqueue, 8 * sizeof(uint32_t));
+    if (s == SK_OK) s = dalloc(&b->dqueue, kMaxClasses * sizeof(uint32_t));
     if (s == SK_OK) {
         cudaError_t e = cudaMemcpy(b->djobs, jobs.data(), n * sizeof(JobDev), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) s = fail(SK_ERR_CUDA, "batch upload: %s", cudaGetErrorString(e));
     }
-    if (s == SK_OK) s = plan_batch(b, W);
+    if (s == SK_OK) s = plan_batch(b);
     if (s != SK_OK) {
         cudaFree(b->djobs);
         cudaFree(b->ditems);
@@ -748,12 +776,16 @@ sk_status mcmcmc_batch_create(sk_run* const* runs, uint32_t n, uint32_t W, sk_ba
 }
 
 namespace {
-sk_status launch_segment(sk_batch* b, uint64_t steps) {
-    for (size_t k = 0; k < b->classes.size(); ++k) {
+// Launches `steps` steps of the batch's classes (only class `only` if >= 0);
+// the step counters are bumped after the last launched class.
+sk_status launch_segment(sk_batch* b, uint64_t steps, int only = -1) {
+    const size_t nc = b->classes.size();
+    for (size_t k = 0; k < nc; ++k) {
+        if (only >= 0 && static_cast<size_t>(only) != k) continue;
         const sk_batch::Class& c = b->classes[k];
-        cudaError_t e = sk::launch_step(b->djobs, b->ditems + c.first_item, c.n_items, b->dqueue + k, steps,
-                                        b->W, b->per_warp, c.grid, c.cls,
-                                        static_cast<uint32_t>(b->runs.size()), k + 1 == b->classes.size(),
+        const bool last = only >= 0 || k + 1 == nc;
+        cudaError_t e = sk::launch_step(b->djobs, b->ditems + c.first_item, c.n_items, b->dqueue + k, steps, c.W,
+                                        c.per_warp, c.grid, c.cls, static_cast<uint32_t>(b->runs.size()), last,
                                         b->st);
         if (e != cudaSuccess) return fail(SK_ERR_CUDA, "step launch: %s", cudaGetErrorString(e));
     }
@@ -761,8 +793,6 @@ sk_status launch_segment(sk_batch* b, uint64_t steps) {
     return SK_OK;
 }
 }  // namespace
-
-
 
 namespace {
 
@@ -869,10 +899,6 @@ sk_status mcmcmc_batch_replay(sk_batch* b, uint32_t times) {
 
 sk_status mcmcmc_batch_autotune(sk_batch* b, uint32_t trial_steps, uint32_t* out_W) {
     if (!b || trial_steps == 0) return fail(SK_ERR_INVALID_ARG, "NULL batch or zero trial steps");
-    // candidate chains-per-CTA values that fit in shared memory
-    std::vector<uint32_t> cand;
-    for (uint32_t w : {32u, 28u, 24u, 20u, 16u, 12u, 8u, 6u, 4u, 2u})
-        if (w <= b->fit) cand.push_back(w);
     // back up every run's mutable state; trials run with records and traces off
     struct Backup {
         void* s;
@@ -918,31 +944,41 @@ sk_status mcmcmc_batch_autotune(sk_batch* b, uint32_t trial_steps, uint32_t* out
         j.trace_chains = 0;
         quiet.push_back(j);
     }
-    const uint32_t W0 = b->W;
-    uint32_t best = W0;
-    float best_ms = 1e30f;
+    const std::map<uint64_t, uint32_t> tuned0 = b->tuned;
+    std::vector<uint64_t> mirror;
+    for (sk_run* r : b->runs) mirror.push_back(r->step);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (s == SK_OK) {
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         cudaMemcpy(b->djobs, quiet.data(), quiet.size() * sizeof(JobDev), cudaMemcpyHostToDevice);
-        std::vector<uint64_t> mirror;
-        for (sk_run* r : b->runs) mirror.push_back(r->step);
-        for (uint32_t w : cand) {
-            if ((s = plan_batch(b, w)) != SK_OK) break;
-            if ((s = launch_segment(b, trial_steps)) != SK_OK) break;  // warm-up
-            restore();
-            cudaEventRecord(e0, b->st);
-            if ((s = launch_segment(b, trial_steps)) != SK_OK) break;
-            cudaEventRecord(e1, b->st);
-            cudaEventSynchronize(e1);
-            float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
-            restore();
-            if (ms < best_ms) {
-                best_ms = ms;
-                best = w;
+        // each launch class is tuned on its own (its launches do not interact)
+        const std::vector<sk_batch::Class> cls0 = b->classes;
+        for (size_t k = 0; k < cls0.size() && s == SK_OK; ++k) {
+            const uint64_t key = cls0[k].key;
+            uint32_t best = cls0[k].W;
+            float best_ms = 1e30f;
+            for (uint32_t w : {32u, 28u, 24u, 20u, 16u, 12u, 8u, 6u, 4u, 2u}) {
+                if (w > cls0[k].fit) continue;
+                b->tuned[key] = w;
+                if ((s = plan_batch(b)) != SK_OK) break;
+                size_t idx = 0;
+                while (idx < b->classes.size() && b->classes[idx].key != key) ++idx;
+                if ((s = launch_segment(b, trial_steps, static_cast<int>(idx))) != SK_OK) break;  // warm-up
+                restore();
+                cudaEventRecord(e0, b->st);
+                if ((s = launch_segment(b, trial_steps, static_cast<int>(idx))) != SK_OK) break;
+                cudaEventRecord(e1, b->st);
+                cudaEventSynchronize(e1);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                restore();
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = w;
+                }
             }
+            b->tuned[key] = best;
         }
         for (size_t i = 0; i < b->runs.size(); ++i) b->runs[i]->step = mirror[i];
         std::vector<JobDev> jobs;
@@ -960,11 +996,12 @@ sk_status mcmcmc_batch_autotune(sk_batch* b, uint32_t trial_steps, uint32_t* out
         cudaFree(x.step);
     }
     if (s != SK_OK) {
-        plan_batch(b, W0);
+        b->tuned = tuned0;
+        plan_batch(b);
         return s;
     }
-    if ((s = plan_batch(b, best)) != SK_OK) return s;
-    if (out_W) *out_W = best;
+    if ((s = plan_batch(b)) != SK_OK) return s;
+    if (out_W) *out_W = b->classes.empty() ? 0 : b->classes[0].W;
     return SK_OK;
 }
 
@@ -972,9 +1009,23 @@ sk_status mcmcmc_batch_info(const sk_batch* b, uint32_t* grid, uint32_t* W, uint
                             uint32_t* items) {
     if (!b) return fail(SK_ERR_INVALID_ARG, "batch is NULL");
     if (grid) *grid = b->grid;
-    if (W) *W = b->W;
-    if (smem) *smem = b->per_warp * b->W;
+    if (W) *W = b->classes.empty() ? 0 : b->classes[0].W;
+    if (smem) *smem = b->classes.empty() ? 0 : b->classes[0].per_warp * b->classes[0].W;
     if (items) *items = b->n_items;
+    return SK_OK;
+}
+
+sk_status mcmcmc_batch_classes(const sk_batch* b, uint32_t max, uint32_t* count, uint32_t* desc) {
+    if (!b || !count) return fail(SK_ERR_INVALID_ARG, "NULL argument");
+    *count = static_cast<uint32_t>(b->classes.size());
+    for (uint32_t k = 0; k < *count && k < max && desc; ++k) {
+        const sk_batch::Class& c = b->classes[k];
+        desc[5 * k + 0] = static_cast<uint32_t>(c.cls);
+        desc[5 * k + 1] = c.per_warp;
+        desc[5 * k + 2] = c.W;
+        desc[5 * k + 3] = c.n_items;
+        desc[5 * k + 4] = c.grid;
+    }
     return SK_OK;
 }
 
