@@ -441,7 +441,8 @@ def _serve_once(rate, duration, pool, budget, quantum, seed):
             "queue_wait_p50_s": float(np.percentile(wait, 50)) if len(wait) else None,
             "throughput_candidates_per_s": cand / span, "span_s": span, "submit_s": submit_s,
             "offered_candidates_per_s": offered / duration,
-            "saturated": offered / duration > 1.05 * cand / span,
+            # saturated: the backlog outlives the arrival window by more than half of it
+            "saturated": span > 1.5 * duration,
             "device_busy_s": sstat["busy_seconds"], "quanta": sstat["quanta"]}
 
 
