@@ -234,7 +234,8 @@ sk_status mcmcmc_free(sk_run* run);
 
 /*
  * mcmcmc_batch_create: plans work items (blocks of chains of one run) for
- * the runs.  warps_per_cta 0 lets the library choose; otherwise 2..32 even.
+ * the runs.  warps_per_cta 0 lets the library choose (as many as fit);
+ * otherwise at most that many warps per CTA (1..32).
  */
 sk_status mcmcmc_batch_create(sk_run* const* runs, uint32_t n_runs, uint32_t warps_per_cta,
                               sk_batch** out);
@@ -258,15 +259,24 @@ sk_status mcmcmc_batch_replay(sk_batch* b, uint32_t times);
 
 /*
  * mcmcmc_batch_autotune: for each launch class of the batch, times a
- * `trial_steps`-step launch for each chains-per-CTA value that fits in shared
- * memory (32, 28, ..., 2; the value also selects the kernel's register
- * budget) and keeps the fastest.
+ * `trial_steps`-step launch for each lanes-per-chain value K allows and each
+ * warps-per-CTA value that fits in shared memory (the CTA size also selects
+ * the kernel's register budget) and keeps the fastest.
  * Trials start from a copy of the runs' state, which is restored afterwards,
  * and run with records and traces off: the runs' trajectories, records and
  * step counters are unchanged.  *warps_per_cta (may be NULL) receives the
  * first class's choice.  Synchronises.
  */
 sk_status mcmcmc_batch_autotune(sk_batch* b, uint32_t trial_steps, uint32_t* warps_per_cta);
+
+/*
+ * mcmcmc_batch_set_lanes: lanes per chain for every launch class (4, 8, 16
+ * or 32; 32/lanes chains share a warp), at least as many as a class's K
+ * needs; 0 restores the default (the fewest lanes K allows, whole warps for
+ * classes of at most 512 chains).  Drops autotuned choices and a captured
+ * graph.  Results do not depend on it.
+ */
+sk_status mcmcmc_batch_set_lanes(sk_batch* b, uint32_t lanes);
 
 /* Launch geometry of the batch (for reports): the largest grid, warps per
  * CTA and dynamic shared memory of the first launch class, total work items. */
@@ -275,11 +285,13 @@ sk_status mcmcmc_batch_info(const sk_batch* b, uint32_t* grid, uint32_t* warps_p
 
 /*
  * mcmcmc_batch_classes: the batch's launch classes.  Work items are grouped
- * by kernel class (coupling kind, rule, K > 128) and by shared-memory size
- * bucket (chains of similar N), one persistent launch per class, so small-N
- * runs keep many chains per CTA next to large-N runs.  *count receives the
- * number of classes; desc (5 x max uint32, may be NULL) receives per class:
- * kernel class, shared bytes per chain, chains per CTA, work items, CTAs.
+ * by kernel class (coupling kind, rule, K > 128), by the fewest lanes per
+ * chain K allows (one Philox block of 4 proposals per lane) and by
+ * shared-memory size bucket (chains of similar N), one persistent launch per
+ * class, so small-N runs keep many chains per CTA next to large-N runs.
+ * *count receives the number of classes; desc (6 x max uint32, may be NULL)
+ * receives per class: kernel class, lanes per chain, shared bytes per chain,
+ * warps per CTA, work items, CTAs.
  */
 sk_status mcmcmc_batch_classes(const sk_batch* b, uint32_t max, uint32_t* count, uint32_t* desc);
 

@@ -111,20 +111,24 @@ struct sk_instance {
 
 struct sk_batch {
     // Work items are grouped by launch class: the kernel class (coupling
-    // kind, rule, Philox blocks per lane) and a shared-memory size bucket, so
-    // that runs with small N get many chains per CTA even when the batch
-    // also holds large-N runs.  Each class is one persistent launch.
+    // kind, rule, Philox blocks per lane), the fewest lanes per chain the
+    // runs' K allows, and a shared-memory size bucket, so that runs with small
+    // N get many chains per CTA even when the batch also holds large-N runs.
+    // Each class is one persistent launch with its own lanes per chain G and
+    // warps per CTA W (W * 32/G chains per CTA).
     struct Class {
-        uint64_t key;            // (kernel class, size bucket)
-        int cls;
-        uint32_t per_warp, fit;  // shared memory per chain, most chains per CTA that fit
-        uint32_t W;              // chains (warps) per CTA
+        uint64_t key;
+        int cls;                 // kernel class incl. G (step_class)
+        uint32_t G, gmin;        // lanes per chain, fewest allowed
+        uint32_t per_chain;      // shared memory per chain
+        uint32_t W;              // warps per CTA
         uint32_t first_item, n_items, grid;
     };
     std::vector<sk_run*> runs;
     std::vector<Class> classes;
-    std::map<uint64_t, uint32_t> tuned;  // key -> W chosen by the autotuner
-    uint32_t W_override = 0;             // warps_per_cta given at creation (0: fit)
+    std::map<uint64_t, uint32_t> tuned;  // key -> (G << 8) | W chosen by the autotuner or forced
+    uint32_t W_override = 0;             // warps_per_cta given at creation (0: as many as fit)
+    uint32_t G_override = 0;             // mcmcmc_batch_set_lanes (0: default)
     JobDev* djobs = nullptr;
     WorkItem* ditems = nullptr;
     uint32_t* dqueue = nullptr;  // one work counter per class (up to kMaxClasses)
@@ -663,21 +667,38 @@ namespace {
 
 constexpr uint32_t kMaxClasses = 64;
 
-// Shared memory per chain (rounded to 128 bytes) and its size bucket: the
-// smallest power of two >= it.
-uint32_t run_per_warp(const sk_run* r) {
+uint32_t run_per_chain(const sk_run* r) {
     return static_cast<uint32_t>((sk::warp_smem_bytes(r->inst->Npad, r->inst->kind) + 127) / 128 * 128);
+}
+// Fewest lanes per chain for a run: one Philox block (4 slots) per lane;
+// K > 128 takes two blocks per lane on a whole warp.
+uint32_t run_gmin(const sk_run* r) {
+    if (r->p.rule != SK_RULE_MCMCMC) return 4;
+    if (r->p.K > 128) return 32;
+    uint32_t g = 4;
+    while (4 * g < r->p.K) g <<= 1;
+    return g;
 }
 uint64_t class_key(const sk_run* r) {
     uint32_t b = 128;
-    const uint32_t pw = run_per_warp(r);
-    while (b < pw) b <<= 1;
-    return (static_cast<uint64_t>(sk::step_class(r->inst->kind, r->p.rule, r->p.K)) << 32) | b;
+    const uint32_t pc = run_per_chain(r);
+    while (b < pc) b <<= 1;
+    const uint64_t kc = static_cast<uint64_t>(sk::step_class(r->inst->kind, r->p.rule, r->p.K, 32)) & ~7ull;
+    return (kc << 40) | (static_cast<uint64_t>(run_gmin(r)) << 32) | b;
+}
+// Most warps per CTA for G lanes per chain: chains of a pair share a CTA,
+// so with whole-warp chains W is even.
+uint32_t fit_warps(uint32_t per_chain, uint32_t G) {
+    const uint32_t spw = 32 / G;
+    uint32_t w = static_cast<uint32_t>(std::min<size_t>(32, kSmemBudget / (static_cast<size_t>(per_chain) * spw)));
+    if (G == 32) w &= ~1u;
+    return w;
 }
 
-// Work items of the batch, grouped by launch class (kernel class, size
-// bucket), each class with its own chains per CTA: the autotuned value, the
-// creation override, or as many as fit in shared memory.  Uploads them.
+// Work items of the batch, grouped by launch class, each class with its own
+// lanes per chain and warps per CTA: the autotuned or forced values, else
+// the fewest lanes K allows (whole-warp chains for runs of few chains, where
+// latency matters) and as many warps as fit.  Uploads them.
 sk_status plan_batch(sk_batch* b) {
     std::map<uint64_t, std::vector<uint32_t>> groups;  // key -> run indices (in order)
     const uint32_t n = static_cast<uint32_t>(b->runs.size());
@@ -692,23 +713,36 @@ sk_status plan_batch(sk_batch* b) {
     for (auto& g : groups) {
         sk_batch::Class c{};
         c.key = g.first;
-        c.cls = static_cast<int>(g.first >> 32);
-        for (uint32_t i : g.second) c.per_warp = std::max(c.per_warp, run_per_warp(b->runs[i]));
-        c.fit = static_cast<uint32_t>(std::min<size_t>(32, kSmemBudget / c.per_warp)) & ~1u;
-        if (c.fit < 2) return fail(SK_ERR_INVALID_ARG, "N too large: %u bytes of shared memory per chain", c.per_warp);
+        const sk_run* r0 = b->runs[g.second[0]];
+        c.gmin = run_gmin(r0);
+        uint64_t total = 0;
+        for (uint32_t i : g.second) {
+            c.per_chain = std::max(c.per_chain, run_per_chain(b->runs[i]));
+            total += b->runs[i]->chains;
+        }
         auto t = b->tuned.find(c.key);
-        c.W = t != b->tuned.end() ? t->second : (b->W_override ? std::min(b->W_override, c.fit) : c.fit);
+        if (t != b->tuned.end()) {
+            c.G = t->second >> 8;
+            c.W = t->second & 0xFFu;
+        } else {
+            c.G = b->G_override ? std::max(b->G_override, c.gmin) : (total <= 512 ? 32u : c.gmin);
+            const uint32_t fit = fit_warps(c.per_chain, c.G);
+            c.W = b->W_override ? std::min(b->W_override, fit) : fit;
+        }
+        if (c.W < 1 || (c.G == 32 && c.W < 2))
+            return fail(SK_ERR_INVALID_ARG, "N too large: %u bytes of shared memory per chain", c.per_chain);
+        c.cls = sk::step_class(r0->inst->kind, r0->p.rule, r0->p.K > 128 ? 256 : 1, c.G);
+        const uint32_t cpc = c.W * (32 / c.G);  // chains per CTA
         c.first_item = static_cast<uint32_t>(items.size());
         for (uint32_t i : g.second) {
             const sk_run* r = b->runs[i];
-            for (uint32_t ch = 0; ch < r->chains; ch += c.W)
-                items.push_back(WorkItem{i, ch, std::min(c.W, r->chains - ch), 0});
+            for (uint32_t ch = 0; ch < r->chains; ch += cpc)
+                items.push_back(WorkItem{i, ch, std::min(cpc, r->chains - ch), 0});
         }
         c.n_items = static_cast<uint32_t>(items.size()) - c.first_item;
-        const int occ = sk::step_kernel_occupancy(c.cls, c.W, static_cast<size_t>(c.per_warp) * c.W);
+        const int occ = sk::step_kernel_occupancy(c.cls, c.W, c.per_chain);
         if (occ <= 0)
-            return fail(SK_ERR_CUDA, "step kernel cannot be resident with %u warps and %u bytes", c.W,
-                        c.per_warp * c.W);
+            return fail(SK_ERR_CUDA, "step kernel cannot be resident with %u warps of %u-lane chains", c.W, c.G);
         c.grid = std::min<uint32_t>(c.n_items, static_cast<uint32_t>(occ * sms));
         grid = std::max(grid, c.grid);
         classes.push_back(c);
@@ -740,16 +774,11 @@ sk_status plan_batch(sk_batch* b) {
 sk_status mcmcmc_batch_create(sk_run* const* runs, uint32_t n, uint32_t W, sk_batch** out) {
     if (!runs || !out || n == 0) return fail(SK_ERR_INVALID_ARG, "empty batch");
     *out = nullptr;
-    if (W && (W < 2 || W > 32 || (W & 1u)))
-        return fail(SK_ERR_INVALID_ARG, "warps_per_cta = %u must be even in 2..32", W);
+    if (W > 32) return fail(SK_ERR_INVALID_ARG, "warps_per_cta = %u must be at most 32", W);
     cudaStream_t st = runs[0]->inst->st;
     for (uint32_t i = 0; i < n; ++i) {
         if (!runs[i]) return fail(SK_ERR_INVALID_ARG, "run %u is NULL", i);
         if (runs[i]->inst->st != st) return fail(SK_ERR_INVALID_ARG, "runs of a batch must share a stream");
-        const size_t pw = (sk::warp_smem_bytes(runs[i]->inst->Npad, runs[i]->inst->kind) + 127) / 128 * 128;
-        if (W && W * pw > kSmemBudget)
-            return fail(SK_ERR_INVALID_ARG, "warps_per_cta = %u needs more than %zu bytes of shared memory", W,
-                        kSmemBudget);
     }
     sk_batch* b = new sk_batch();
     b->runs.assign(runs, runs + n);
@@ -775,6 +804,15 @@ sk_status mcmcmc_batch_create(sk_run* const* runs, uint32_t n, uint32_t W, sk_ba
     return SK_OK;
 }
 
+sk_status mcmcmc_batch_set_lanes(sk_batch* b, uint32_t lanes) {
+    if (!b) return fail(SK_ERR_INVALID_ARG, "batch is NULL");
+    if (lanes && lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32)
+        return fail(SK_ERR_INVALID_ARG, "lanes per chain must be 0, 4, 8, 16 or 32");
+    b->G_override = lanes;
+    b->tuned.clear();
+    return plan_batch(b);
+}
+
 namespace {
 // Launches `steps` steps of the batch's classes (only class `only` if >= 0);
 // the step counters are bumped after the last launched class.
@@ -785,7 +823,7 @@ sk_status launch_segment(sk_batch* b, uint64_t steps, int only = -1) {
         const sk_batch::Class& c = b->classes[k];
         const bool last = only >= 0 || k + 1 == nc;
         cudaError_t e = sk::launch_step(b->djobs, b->ditems + c.first_item, c.n_items, b->dqueue + k, steps, c.W,
-                                        c.per_warp, c.grid, c.cls, static_cast<uint32_t>(b->runs.size()), last,
+                                        c.per_chain, c.grid, c.cls, static_cast<uint32_t>(b->runs.size()), last,
                                         b->st);
         if (e != cudaSuccess) return fail(SK_ERR_CUDA, "step launch: %s", cudaGetErrorString(e));
     }
@@ -956,11 +994,16 @@ sk_status mcmcmc_batch_autotune(sk_batch* b, uint32_t trial_steps, uint32_t* out
         const std::vector<sk_batch::Class> cls0 = b->classes;
         for (size_t k = 0; k < cls0.size() && s == SK_OK; ++k) {
             const uint64_t key = cls0[k].key;
-            uint32_t best = cls0[k].W;
+            uint32_t best = (cls0[k].G << 8) | cls0[k].W;
             float best_ms = 1e30f;
-            for (uint32_t w : {32u, 28u, 24u, 20u, 16u, 12u, 8u, 6u, 4u, 2u}) {
-                if (w > cls0[k].fit) continue;
-                b->tuned[key] = w;
+            std::vector<uint32_t> cand;  // (G << 8) | W
+            for (uint32_t G = cls0[k].gmin; G <= 32; G <<= 1) {
+                const uint32_t fit = fit_warps(cls0[k].per_chain, G);
+                for (uint32_t w : {32u, 24u, 16u, 12u, 8u, 6u, 4u, 2u, 1u})
+                    if (w <= fit && (G < 32 || (w & 1u) == 0)) cand.push_back((G << 8) | w);
+            }
+            for (uint32_t gw : cand) {
+                b->tuned[key] = gw;
                 if ((s = plan_batch(b)) != SK_OK) break;
                 size_t idx = 0;
                 while (idx < b->classes.size() && b->classes[idx].key != key) ++idx;
@@ -975,7 +1018,7 @@ sk_status mcmcmc_batch_autotune(sk_batch* b, uint32_t trial_steps, uint32_t* out
                 restore();
                 if (ms < best_ms) {
                     best_ms = ms;
-                    best = w;
+                    best = gw;
                 }
             }
             b->tuned[key] = best;
@@ -1010,7 +1053,8 @@ sk_status mcmcmc_batch_info(const sk_batch* b, uint32_t* grid, uint32_t* W, uint
     if (!b) return fail(SK_ERR_INVALID_ARG, "batch is NULL");
     if (grid) *grid = b->grid;
     if (W) *W = b->classes.empty() ? 0 : b->classes[0].W;
-    if (smem) *smem = b->classes.empty() ? 0 : b->classes[0].per_warp * b->classes[0].W;
+    if (smem)
+        *smem = b->classes.empty() ? 0 : b->classes[0].per_chain * b->classes[0].W * (32 / b->classes[0].G);
     if (items) *items = b->n_items;
     return SK_OK;
 }
@@ -1020,11 +1064,12 @@ sk_status mcmcmc_batch_classes(const sk_batch* b, uint32_t max, uint32_t* count,
     *count = static_cast<uint32_t>(b->classes.size());
     for (uint32_t k = 0; k < *count && k < max && desc; ++k) {
         const sk_batch::Class& c = b->classes[k];
-        desc[5 * k + 0] = static_cast<uint32_t>(c.cls);
-        desc[5 * k + 1] = c.per_warp;
-        desc[5 * k + 2] = c.W;
-        desc[5 * k + 3] = c.n_items;
-        desc[5 * k + 4] = c.grid;
+        desc[6 * k + 0] = static_cast<uint32_t>(c.cls);
+        desc[6 * k + 1] = c.G;
+        desc[6 * k + 2] = c.per_chain;
+        desc[6 * k + 3] = c.W;
+        desc[6 * k + 4] = c.n_items;
+        desc[6 * k + 5] = c.grid;
     }
     return SK_OK;
 }

@@ -42,14 +42,14 @@ struct alignas(16) JobDev {
 };
 static_assert(sizeof(JobDev) % 16 == 0, "JobDev is copied as 16-byte words");
 
-// A block of consecutive chains of one run, processed by one CTA (one warp
+// A block of consecutive chains of one run, processed by one CTA (G lanes
 // per chain).  chain0 is even so that overlap pairs stay inside a CTA.
 struct WorkItem {
     uint32_t job, chain0, nchains, pad;
 };
 
-// Bytes of shared memory one warp (one chain) needs for spins, fields and
-// the two J-row staging buffers.
+// Bytes of shared memory one chain needs for spins, fields and the two J-row
+// staging buffers.
 inline size_t warp_smem_bytes(uint32_t npad, uint32_t kind) {
     size_t bj = kind == 0 ? 1 : 4;
     return (size_t)npad * (1 + 4 + 2 * bj);
@@ -57,16 +57,20 @@ inline size_t warp_smem_bytes(uint32_t npad, uint32_t kind) {
 
 // Kernel launchers (sk_kernels.cu).  All return cudaGetLastError().
 //
-// The step kernel is instantiated per class = step_class(kind, rule, K): the
-// coupling type, the rule, and whether K needs two Philox blocks per lane
-// (K > 128).  launch_step runs the items of one class; `bump` advances every
-// job's step counter by nsteps afterwards (set it on the last class).
-int step_class(uint32_t kind, uint32_t rule, uint32_t K);
+// The step kernel is instantiated per class = step_class(kind, rule, K, G):
+// the coupling type, the rule, whether K needs two Philox blocks per lane
+// (K > 128, whole-warp chains only) and the lanes per chain G (4, 8, 16, 32;
+// 32/G chains per warp).  A CTA holds W warps, i.e. W * 32/G chains, each
+// with `per_chain` bytes of shared memory.  launch_step runs the items of one
+// class; `bump` advances every job's step counter afterwards (set it on the
+// last class).
+int step_class(uint32_t kind, uint32_t rule, uint32_t K, uint32_t G);
+uint32_t class_lanes(int cls);
 cudaError_t launch_step(const JobDev* jobs, const WorkItem* items, uint32_t n_items,
                         uint32_t* queue, uint64_t nsteps, uint32_t warps_per_cta,
-                        uint32_t per_warp_bytes, uint32_t grid, int cls, uint32_t n_jobs,
+                        uint32_t per_chain_bytes, uint32_t grid, int cls, uint32_t n_jobs,
                         bool bump, cudaStream_t st);
-int step_kernel_occupancy(int cls, uint32_t warps_per_cta, size_t smem_bytes);
+int step_kernel_occupancy(int cls, uint32_t warps_per_cta, size_t per_chain_bytes);
 cudaError_t launch_init(const JobDev* job, const int8_t* init, uint32_t chains, uint32_t N,
                         uint32_t Npad, uint32_t kind, cudaStream_t st);
 cudaError_t launch_energy(const void* J, uint32_t kind, uint32_t N, uint32_t Npad, double scale,

@@ -1,0 +1,668 @@
+// sk_step.cuh -- the persistent MCMCMC / Metropolis step kernel.
+//
+// A chain is owned by a group of G lanes (G = 4, 8, 16 or 32; 32/G chains per
+// warp).  Its spins s[Npad] (int8) and maintained local fields h[Npad] (int32
+// for +-J, float for Gaussian couplings) stay in the chain's slice of shared
+// memory for the whole launch, and the row of J that the next step needs
+// first is bulk-copied (TMA, cp.async.bulk) into a double-buffered
+// shared-memory slot one step ahead: the sites a step proposes do not depend
+// on the chain's state.  Groups only talk to their own lanes (width-G
+// shuffles under the group's lane mask), so the groups of a warp are
+// independent chains.
+//
+// One Monte Carlo step (Sec. A.2, Eq. eq_det_balance_graph_solution, on the
+// star of App. B.2 with a uniform root, p_r = 1/(K+1)):
+//   a1  Philox4x32-10 draws, counter (block, step, chain, stream): block 0
+//       gives U0 (root: leaf iff floor(U0 (K+1) / 2^64) != 0) and U1 (node);
+//       blocks 1..ceil(K/4) give site_d = floor(w N / 2^32), d = 1..K.
+//       Group lane l computes block 1+l (+32 when K > 128), so its slots are
+//       d = 4l+1..4l+4 (+128); block 0 is computed G steps at a time.
+//   a2  the row of J at a = site_1 of the NEXT step is staged by TMA.
+//   a3  candidate energies: centre root dE_d = 2 s_i h_i (i = site_d);
+//       leaf root dE_1 = 2 s_a h_a, dE_d = 2 s_a h_a + 2 s_b h_b - 4 J_ab s_a s_b
+//       (b = site_d != a), 0 when b = a; slot 0 (the current state) is 0.
+//   a4  node choice with probability ~ exp(-beta dE): group min, weights
+//       (+-J: integer table W[(dE-min)/2] ~ 2^52 exp(-2 beta d); Gaussian:
+//       2^x), group inclusive scan in slot order, u = U1 * total, first
+//       slot whose prefix exceeds u.
+//   a5  field update for the 0, 1 or 2 flipped spins x: h_k -= 2 s_x J_kx.
+//   a6  records every R steps: E = -scale/2 sum s h, accepted count, and the
+//       overlap q of chain pairs (2m, 2m+1), which share a CTA.
+// The Metropolis comparator (Sec. II / IV.B) shares the layout: one site per
+// step from block 0, accept iff dE <= 0 or U < exp(-beta dE).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sk_device.cuh"
+#include "sk_internal.h"
+
+namespace sk {
+namespace step {
+
+using dev::kFull;
+using dev::sbyte;
+using dev::Types;
+
+// The G lanes of one chain inside a warp.
+template <int G>
+struct Grp {
+    int gl;         // lane within the group
+    int base;       // first warp lane of the group
+    unsigned mask;  // the group's lanes
+    __device__ __forceinline__ Grp() {
+        const int lane = threadIdx.x & 31;
+        gl = lane & (G - 1);
+        base = lane & ~(G - 1);
+        mask = G == 32 ? kFull : (((1u << G) - 1u) << base);
+    }
+};
+
+template <int G, typename T>
+__device__ __forceinline__ T gshfl(const Grp<G>& g, T v, int src) {
+    return __shfl_sync(g.mask, v, src, G);
+}
+template <int G, typename T>
+__device__ __forceinline__ T gmin(const Grp<G>& g, T v) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+        const T y = __shfl_xor_sync(g.mask, v, o, G);
+        v = y < v ? y : v;
+    }
+    return v;
+}
+template <int G, typename T>
+__device__ __forceinline__ T gsum(const Grp<G>& g, T v) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(g.mask, v, o, G);
+    return v;
+}
+template <int G, typename T>
+__device__ __forceinline__ T gscan(const Grp<G>& g, T v) {  // inclusive, in lane order
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) {
+        const T y = __shfl_up_sync(g.mask, v, o, G);
+        if (g.gl >= o) v += y;
+    }
+    return v;
+}
+template <int G>
+__device__ __forceinline__ unsigned gballot(const Grp<G>& g, bool p) {
+    const unsigned b = __ballot_sync(g.mask, p);
+    return G == 32 ? b : ((b >> g.base) & ((1u << G) - 1u));
+}
+
+// Shared memory of one chain: spins, fields, two staged J rows, two mbarriers.
+struct ChainMem {
+    int8_t* s;
+    void* h;
+    void* row[2];
+    uint64_t* bar;
+};
+
+// Block 0 of each step, computed for G consecutive steps at once (group lane
+// l holds the step base + l) and broadcast in the group.  Steps are 32-bit.
+struct Block0 {
+    uint4 v;
+    uint32_t base;
+    bool valid;
+};
+template <int G>
+__device__ __forceinline__ uint4 block0(Block0& c, uint32_t t, uint32_t chain, uint32_t c3, uint32_t k0,
+                                        uint32_t k1, const Grp<G>& g) {
+    if (!c.valid || t - c.base >= static_cast<uint32_t>(G)) {
+        c.base = t & ~static_cast<uint32_t>(G - 1);
+        c.valid = true;
+        c.v = dev::philox4x32_10(make_uint4(0u, c.base + g.gl, chain, c3), k0, k1);
+    }
+    const int src = static_cast<int>(t - c.base);
+    return make_uint4(gshfl(g, c.v.x, src), gshfl(g, c.v.y, src), gshfl(g, c.v.z, src), gshfl(g, c.v.w, src));
+}
+
+// Sites of step t held by this lane: slots d = 128 q + 4 gl + e + 1.
+template <int NB, int G>
+__device__ __forceinline__ void draw_sites(uint32_t (&site)[4 * NB], uint32_t t, uint32_t chain, uint32_t c3,
+                                           uint32_t k0, uint32_t k1, uint32_t nblk, uint32_t N, const Grp<G>& g) {
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+        const uint32_t b = 1u + 32u * q + g.gl;
+        uint4 r = make_uint4(0u, 0u, 0u, 0u);
+        if (b <= nblk) r = dev::philox4x32_10(make_uint4(b, t, chain, c3), k0, k1);
+        site[4 * q + 0] = __umulhi(r.x, N);
+        site[4 * q + 1] = __umulhi(r.y, N);
+        site[4 * q + 2] = __umulhi(r.z, N);
+        site[4 * q + 3] = __umulhi(r.w, N);
+    }
+}
+
+// h_k -= c1 J[x1][k] + c2 J[x2][k] for k < Npad (c2 = 0: one flip); lane gl
+// owns elements 4 gl + 4 G v.  r1 is the staged row (shared memory) when
+// STAGED, else a row of J in global memory; r2 is global and read only when
+// c2 != 0.
+template <typename JT, bool STAGED, int G>
+__device__ __forceinline__ void update_fields(typename Types<JT>::H* hf, const JT* r1, const JT* r2, int c1,
+                                              int c2, uint32_t npad, int gl) {
+#pragma unroll 2
+    for (uint32_t k = 4u * gl; k < npad; k += 4u * G) {
+        if constexpr (sizeof(JT) == 1) {
+            int4 hv = *reinterpret_cast<int4*>(hf + k);
+            const uint32_t j1 = STAGED ? *reinterpret_cast<const uint32_t*>(r1 + k)
+                                       : __ldg(reinterpret_cast<const unsigned int*>(r1 + k));
+            hv.x -= c1 * sbyte(j1, 0);
+            hv.y -= c1 * sbyte(j1, 1);
+            hv.z -= c1 * sbyte(j1, 2);
+            hv.w -= c1 * sbyte(j1, 3);
+            if (c2) {
+                const uint32_t j2 = __ldg(reinterpret_cast<const unsigned int*>(r2 + k));
+                hv.x -= c2 * sbyte(j2, 0);
+                hv.y -= c2 * sbyte(j2, 1);
+                hv.z -= c2 * sbyte(j2, 2);
+                hv.w -= c2 * sbyte(j2, 3);
+            }
+            *reinterpret_cast<int4*>(hf + k) = hv;
+        } else {
+            float4 hv = *reinterpret_cast<float4*>(hf + k);
+            const float4 j1 = STAGED ? *reinterpret_cast<const float4*>(r1 + k)
+                                     : __ldg(reinterpret_cast<const float4*>(r1 + k));
+            const float f1 = static_cast<float>(c1);
+            hv.x = fmaf(-f1, j1.x, hv.x);
+            hv.y = fmaf(-f1, j1.y, hv.y);
+            hv.z = fmaf(-f1, j1.z, hv.z);
+            hv.w = fmaf(-f1, j1.w, hv.w);
+            if (c2) {
+                const float4 j2 = __ldg(reinterpret_cast<const float4*>(r2 + k));
+                const float f2 = static_cast<float>(c2);
+                hv.x = fmaf(-f2, j2.x, hv.x);
+                hv.y = fmaf(-f2, j2.y, hv.y);
+                hv.z = fmaf(-f2, j2.z, hv.z);
+                hv.w = fmaf(-f2, j2.w, hv.w);
+            }
+            *reinterpret_cast<float4*>(hf + k) = hv;
+        }
+    }
+}
+
+// E = -scale/2 sum_k s_k h_k of the group's chain.
+template <typename JT, int G>
+__device__ __forceinline__ double chain_energy(const int8_t* S, const void* h, uint32_t npad, double scale,
+                                               const Grp<G>& g) {
+    if constexpr (sizeof(JT) == 1) {
+        const int* hf = static_cast<const int*>(h);
+        int acc = 0;
+        for (uint32_t k = 4u * g.gl; k < npad; k += 4u * G) {
+            const uint32_t sw = *reinterpret_cast<const uint32_t*>(S + k);
+            const int4 hv = *reinterpret_cast<const int4*>(hf + k);
+            acc += sbyte(sw, 0) * hv.x + sbyte(sw, 1) * hv.y + sbyte(sw, 2) * hv.z + sbyte(sw, 3) * hv.w;
+        }
+        const int tot = gsum(g, acc);  // = 2 sum_{i<j} J s s, even
+        return scale * static_cast<double>(-(tot / 2));
+    } else {
+        const float* hf = static_cast<const float*>(h);
+        double acc = 0.0;
+        for (uint32_t k = 4u * g.gl; k < npad; k += 4u * G) {
+            const uint32_t sw = *reinterpret_cast<const uint32_t*>(S + k);
+            const float4 hv = *reinterpret_cast<const float4*>(hf + k);
+            acc += static_cast<double>(sbyte(sw, 0)) * hv.x + static_cast<double>(sbyte(sw, 1)) * hv.y +
+                   static_cast<double>(sbyte(sw, 2)) * hv.z + static_cast<double>(sbyte(sw, 3)) * hv.w;
+        }
+        return -0.5 * scale * gsum(g, acc);
+    }
+}
+
+// Record point shared by every thread of the CTA (two CTA barriers).  Only
+// `write` groups (real chains, not shadows) store.
+template <typename JT, int G>
+__device__ __noinline__ void record(const JobDev& jb, bool write, uint32_t chain, uint32_t rec, const int8_t* S,
+                                    const void* h, const int8_t* partner_s, uint32_t acc) {
+    const Grp<G> g;
+    const bool store = write && rec < jb.rec_capacity;
+    const double E = chain_energy<JT, G>(S, h, jb.Npad, jb.scale, g);
+    if (store && g.gl == 0) {
+        jb.rec_E[static_cast<size_t>(rec) * jb.chains + chain] = E;
+        jb.rec_acc[static_cast<size_t>(rec) * jb.chains + chain] = acc;
+    }
+    __syncthreads();
+    if ((chain & 1u) == 0u && chain + 1u < jb.chains) {
+        int dot = 0;
+        for (uint32_t k = 4u * g.gl; k < jb.Npad; k += 4u * G) {
+            const uint32_t a = *reinterpret_cast<const uint32_t*>(S + k);
+            const uint32_t b = *reinterpret_cast<const uint32_t*>(partner_s + k);
+            dot += sbyte(a, 0) * sbyte(b, 0) + sbyte(a, 1) * sbyte(b, 1) + sbyte(a, 2) * sbyte(b, 2) +
+                   sbyte(a, 3) * sbyte(b, 3);
+        }
+        dot = gsum(g, dot);
+        if (store && g.gl == 0)
+            jb.rec_q[static_cast<size_t>(rec) * (jb.chains / 2) + chain / 2] =
+                static_cast<double>(dot) / static_cast<double>(jb.N);
+    }
+    __syncthreads();
+}
+
+// Steps t0..t1-1 of one chain (or of a shadow: a group without a chain of
+// its own in a partly filled warp runs a copy of a real chain and stores
+// nothing, so that every lane reaches the same barriers).  `dead` is set
+// after a timed-out wait: the group then stops working but still meets the
+// CTA's record barriers.
+template <typename JT, int RULE, int NB, int G>
+__device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_t chain, const ChainMem& cm,
+                                           const int8_t* partner_s, uint32_t t0, uint32_t t1, uint32_t& acc,
+                                           uint32_t& phase, bool& dead, uint32_t& n_flips, uint32_t& n_rows) {
+    using H = typename Types<JT>::H;
+    using W = typename Types<JT>::W;
+    const Grp<G> g;
+    const uint32_t R = jb.record_every;
+    uint32_t next_rec = R ? (t0 / R + 1u) * R : 0xFFFFFFFFu;
+    uint32_t rec_idx = R ? t0 / R : 0u;
+    // job parameters held in registers for the whole loop
+    const uint32_t N = jb.N, npad = jb.Npad, K = jb.K;
+    const uint32_t nblk = (K + 3u) >> 2;
+    const uint32_t k0 = static_cast<uint32_t>(jb.seed), k1 = static_cast<uint32_t>(jb.seed >> 32);
+    const uint32_t c3 = jb.stream & 0xFFFFFFu;  // domain 0: step draws
+    const JT* __restrict__ Jg = static_cast<const JT*>(jb.J);
+    const uint32_t rowbytes = npad * static_cast<uint32_t>(sizeof(JT));
+    const W* __restrict__ Wt = reinterpret_cast<const W*>(jb.W);
+    const uint32_t wlen = jb.wlen;
+    const float nbl2 = -jb.beta_eff * 1.4426950408889634f;  // -beta log2(e)
+    int32_t* trace = (write && chain < jb.trace_chains) ? jb.trace + static_cast<size_t>(chain) * jb.trace_steps
+                                                        : nullptr;
+    const uint32_t trace_end = trace ? static_cast<uint32_t>(jb.trace_steps) : 0u;
+    int8_t* S = cm.s;
+    H* hf = static_cast<H*>(cm.h);
+
+    Block0 bc;
+    bc.valid = false;
+    uint32_t site[4 * NB];
+
+    // prologue: the first step's row
+    uint32_t first;
+    if constexpr (RULE == 0) {
+        draw_sites<NB, G>(site, t0, chain, c3, k0, k1, nblk, N, g);
+        first = gshfl(g, site[0], 0);
+    } else {
+        first = __umulhi(block0<G>(bc, t0, chain, c3, k0, k1, g).x, N);
+    }
+    if (g.gl == 0 && !dead) {
+        dev::fence_proxy_async();
+        dev::bulk_load(cm.row[t0 & 1u], Jg + static_cast<size_t>(first) * npad, rowbytes, &cm.bar[t0 & 1u]);
+    }
+
+    for (uint32_t t = t0; t < t1; ++t) {
+        const uint32_t buf = t & 1u;
+        const uint4 b0 = block0<G>(bc, t, chain, c3, k0, k1, g);
+        const unsigned long long U1 = (static_cast<unsigned long long>(b0.w) << 32) | b0.z;
+        int sel = 0;  // slot chosen (Metropolis: accepted)
+        int nflip = 0;
+        int rows = 0;  // J rows this step needs: row a of a leaf root, flipped spins' rows
+        uint32_t x1 = 0, x2 = 0;
+        bool x1_staged = false;
+
+        // stage the row the next step needs first
+        uint32_t nsite[4 * NB];
+        if (t + 1u < t1) {
+            uint32_t nx;
+            if constexpr (RULE == 0) {
+                draw_sites<NB, G>(nsite, t + 1u, chain, c3, k0, k1, nblk, N, g);
+                nx = gshfl(g, nsite[0], 0);
+            } else {
+                nx = __umulhi(block0<G>(bc, t + 1u, chain, c3, k0, k1, g).x, N);
+            }
+            __syncwarp(g.mask);  // every lane of the group is done with buffer buf^1 (step t-1)
+            if (g.gl == 0 && !dead) {
+                dev::fence_proxy_async();
+                dev::bulk_load(cm.row[buf ^ 1u], Jg + static_cast<size_t>(nx) * npad, rowbytes, &cm.bar[buf ^ 1u]);
+            }
+        }
+        if (!dead) {
+            // every lane waits; the outcome is made group-uniform
+            const bool okl = dev::mbar_wait_bounded(&cm.bar[buf], (phase >> buf) & 1u);
+            const bool ok = gballot(g, okl) == (G == 32 ? kFull : ((1u << G) - 1u));
+            phase ^= 1u << buf;
+            if (!ok) {
+                dead = true;
+                if (g.gl == 0) atomicExch(jb.err, kDevTimeout);
+            }
+        }
+        const JT* rowA = static_cast<const JT*>(cm.row[buf]);
+
+        if (!dead) {
+            if constexpr (RULE == 1) {
+                // ---- Metropolis: one single-flip proposal ----
+                const uint32_t i = __umulhi(b0.x, N);
+                const int si = S[i];
+                const H dE = static_cast<H>(2 * si) * hf[i];
+                bool accept;
+                if constexpr (sizeof(JT) == 1) {
+                    const uint32_t k = static_cast<uint32_t>(dE) >> 1;
+                    accept = dE <= 0 || (k < wlen && (U1 >> 11) < __ldg(&Wt[k]));
+                } else {
+                    accept = dE <= 0.0f || static_cast<float>(U1 >> 40) * 0x1p-24f < dev::pow2(nbl2 * dE);
+                }
+                sel = accept ? 1 : 0;
+                if (accept) {
+                    nflip = 1;
+                    x1 = i;
+                    x1_staged = true;
+                }
+                rows = nflip;
+            } else {
+                // ---- MCMCMC: K proposals on the uniform-root star ----
+                const unsigned long long U0 = (static_cast<unsigned long long>(b0.y) << 32) | b0.x;
+                const bool leaf = __umul64hi(U0, static_cast<unsigned long long>(K) + 1ull) != 0ull;
+                const uint32_t a = gshfl(g, site[0], 0);
+                const int sa = S[a];
+                const H dEa = static_cast<H>(2 * sa) * hf[a];
+                H dE[4 * NB];
+                H mloc = 0;
+#pragma unroll
+                for (int q = 0; q < 4 * NB; ++q) {
+                    const uint32_t d = 128u * (q >> 2) + 4u * g.gl + (q & 3) + 1u;
+                    const uint32_t i = site[q];
+                    const int si = S[i];
+                    const H hi = hf[i];
+                    const H single = static_cast<H>(2 * si) * hi;
+                    // leaf root: the centre flipped at b = site_d (0 if b = a)
+                    const H dbl = (i == a) ? H(0)
+                                           : dEa + single - static_cast<H>(4 * sa * si) * static_cast<H>(rowA[i]);
+                    const H v = !leaf ? single : (d == 1u ? dEa : dbl);
+                    dE[q] = v;
+                    if (d <= K) mloc = mloc < v ? mloc : v;
+                }
+                const H m = gmin(g, mloc);
+                // weights in slot order
+                W w[4 * NB];
+                W gsum_[NB];
+#pragma unroll
+                for (int q = 0; q < NB; ++q) gsum_[q] = 0;
+#pragma unroll
+                for (int q = 0; q < 4 * NB; ++q) {
+                    const uint32_t d = 128u * (q >> 2) + 4u * g.gl + (q & 3) + 1u;
+                    W x = 0;
+                    if (d <= K) {
+                        if constexpr (sizeof(JT) == 1) {
+                            const uint32_t idx = static_cast<uint32_t>(dE[q] - m) >> 1;
+                            x = idx < wlen ? __ldg(&Wt[idx]) : 0ull;
+                        } else {
+                            x = dev::pow2(nbl2 * (dE[q] - m));
+                        }
+                    }
+                    w[q] = x;
+                    gsum_[q >> 2] += x;
+                }
+                W w0;
+                if constexpr (sizeof(JT) == 1) {
+                    const uint32_t idx0 = static_cast<uint32_t>(-m) >> 1;
+                    w0 = idx0 < wlen ? __ldg(&Wt[idx0]) : 0ull;
+                } else {
+                    w0 = dev::pow2(-nbl2 * m);
+                }
+                W incl[NB], tot[NB];
+                W total = w0;
+#pragma unroll
+                for (int q = 0; q < NB; ++q) {
+                    incl[q] = gscan(g, gsum_[q]);
+                    tot[q] = gshfl(g, incl[q], G - 1);
+                    total += tot[q];
+                }
+                W u;
+                if constexpr (sizeof(JT) == 1) {
+                    u = __umul64hi(U1, total);
+                } else {
+                    u = static_cast<float>(U1 >> 40) * 0x1p-24f * total;
+                    if (u >= total) u = nextafterf(total, 0.0f);
+                }
+                // first slot whose inclusive prefix exceeds u; the owning
+                // lane finds its entry, one packed shuffle broadcasts it
+                int sel_d = 0;
+                uint32_t sel_site = 0;
+                bool found = u < w0;
+                W base = w0;
+#pragma unroll
+                for (int q = 0; q < NB; ++q) {
+                    const unsigned ball = gballot(g, !found && base + incl[q] > u);
+                    if (!found && ball) {
+                        const int L = __ffs(ball) - 1;
+                        W run = base + (incl[q] - gsum_[q]);
+                        int my_e = -1;
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            if (my_e < 0 && w[4 * q + e] > W(0)) {
+                                run += w[4 * q + e];
+                                if (run > u) my_e = e;
+                            }
+                        }
+                        if (my_e < 0) {  // rounding guard: last positive weight
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                if (w[4 * q + e] > W(0)) my_e = e;
+                        }
+                        uint32_t my_site = 0;
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if (e == my_e) my_site = site[4 * q + e];
+                        const uint32_t packed = gshfl(g, (my_site << 2) | static_cast<uint32_t>(my_e & 3), L);
+                        sel_site = packed >> 2;
+                        sel_d = 128 * q + 4 * L + static_cast<int>(packed & 3u) + 1;
+                        found = true;
+                    }
+                    base += tot[q];
+                }
+                sel = sel_d;
+                if (sel_d != 0) {
+                    if (!leaf) {
+                        nflip = 1;
+                        x1 = sel_site;
+                        x1_staged = (sel_site == a);
+                    } else if (sel_d == 1) {
+                        nflip = 1;
+                        x1 = a;
+                        x1_staged = true;
+                    } else if (sel_site != a) {
+                        nflip = 2;
+                        x1 = a;
+                        x1_staged = true;
+                        x2 = sel_site;
+                    }
+                }
+                rows = leaf ? 1 + (nflip == 2 ? 1 : 0) : nflip;
+            }
+            // ---- field update and flips ----
+            if (nflip) {
+                const int c1 = 2 * S[x1];
+                const int c2 = nflip == 2 ? 2 * S[x2] : 0;
+                if (x1_staged)
+                    update_fields<JT, true, G>(hf, rowA, Jg + static_cast<size_t>(x2) * npad, c1, c2, npad, g.gl);
+                else
+                    update_fields<JT, false, G>(hf, Jg + static_cast<size_t>(x1) * npad, nullptr, c1, 0, npad, g.gl);
+                __syncwarp(g.mask);
+                if (g.gl == 0) {
+                    S[x1] = static_cast<int8_t>(-S[x1]);
+                    if (nflip == 2) S[x2] = static_cast<int8_t>(-S[x2]);
+                }
+                acc += 1u;
+            }
+            n_flips += static_cast<uint32_t>(nflip);
+            n_rows += static_cast<uint32_t>(rows);
+            if (t < trace_end && g.gl == 0) trace[t] = sel;
+            __syncwarp(g.mask);
+        }
+        if constexpr (RULE == 0) {
+#pragma unroll
+            for (int q = 0; q < 4 * NB; ++q) site[q] = nsite[q];
+        }
+        if (t + 1u == next_rec) {
+            record<JT, G>(jb, write && !dead, chain, rec_idx, S, hf, partner_s, acc);
+            acc = 0;
+            next_rec += R;
+            ++rec_idx;
+        }
+    }
+}
+
+// MAXT bounds the CTA size and so the register budget per thread
+// (65536 / MAXT): 1024 -> 64, 640 -> 96, 512 -> 128 registers.
+template <typename JT, int RULE, int NB, int G, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1)
+    step_kernel(const JobDev* __restrict__ jobs, const WorkItem* __restrict__ items, uint32_t n_items,
+                uint32_t* __restrict__ queue, uint32_t nsteps, uint32_t per_chain) {
+    constexpr int SPW = 32 / G;  // chains per warp
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(16) JobDev s_job;
+    __shared__ __align__(8) uint64_t bars[2 * 256];
+    __shared__ uint32_t s_item;
+    const Grp<G> g;
+    const int warp = threadIdx.x >> 5;
+    const int slot = warp * SPW + (threadIdx.x & 31) / G;  // chain slot of this group in the CTA
+    if (g.gl == 0) {
+        dev::mbar_init(&bars[2 * slot], 1);
+        dev::mbar_init(&bars[2 * slot + 1], 1);
+    }
+    dev::fence_mbar_init();
+    __syncthreads();
+    uint32_t phase = 0;
+    bool dead = false;  // a bounded wait of this group expired: skip all further work
+    constexpr size_t bj = sizeof(JT);
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(queue, 1u);
+        __syncthreads();
+        const uint32_t it = s_item;
+        if (it >= n_items) break;
+        const WorkItem wi = items[it];
+        if (threadIdx.x < sizeof(JobDev) / 16)
+            reinterpret_cast<uint4*>(&s_job)[threadIdx.x] = reinterpret_cast<const uint4*>(&jobs[wi.job])[threadIdx.x];
+        __syncthreads();
+        const JobDev& jb = s_job;
+        const bool warp_busy = static_cast<uint32_t>(warp * SPW) < wi.nchains;  // some group has a chain
+        const bool own = static_cast<uint32_t>(slot) < wi.nchains;              // this group has a chain
+        const uint32_t chain = own ? wi.chain0 + slot : wi.chain0;              // shadows copy the first
+        const uint32_t npad = jb.Npad;
+        ChainMem cm;
+        unsigned char* base = smem + static_cast<size_t>(slot) * per_chain;
+        cm.s = reinterpret_cast<int8_t*>(base);
+        cm.h = base + npad;
+        cm.row[0] = base + 5 * static_cast<size_t>(npad);
+        cm.row[1] = base + (5 + bj) * static_cast<size_t>(npad);
+        cm.bar = &bars[2 * slot];
+        const int8_t* partner_s = reinterpret_cast<const int8_t*>(smem + static_cast<size_t>(slot ^ 1) * per_chain);
+        const uint32_t t0 = static_cast<uint32_t>(*jb.step);
+        const uint32_t t1 = static_cast<uint32_t>(
+            min(static_cast<uint64_t>(t0) + nsteps, static_cast<uint64_t>(jb.step_limit)));
+        uint32_t acc = 0, n_flips = 0, n_rows = 0;
+        if (warp_busy) {
+            // load the chain's state: spins (npad bytes), fields (4 npad bytes)
+            const uint4* gs = reinterpret_cast<const uint4*>(jb.s + static_cast<size_t>(chain) * npad);
+            uint4* ss = reinterpret_cast<uint4*>(cm.s);
+            for (uint32_t k = g.gl; k < npad / 16; k += G) ss[k] = gs[k];
+            const uint4* gh = reinterpret_cast<const uint4*>(static_cast<const int*>(jb.h) +
+                                                             static_cast<size_t>(chain) * npad);
+            uint4* sh = reinterpret_cast<uint4*>(cm.h);
+            for (uint32_t k = g.gl; k < npad / 4; k += G) sh[k] = gh[k];
+            acc = jb.acc_run[chain];
+        }
+        __syncwarp();
+        if (t1 > t0) {
+            if (warp_busy) {
+                chain_loop<JT, RULE, NB, G>(jb, own, chain, cm, partner_s, t0, t1, acc, phase, dead, n_flips,
+                                            n_rows);
+            } else {
+                // no chain in this warp: meet the CTA's record barriers only
+                const uint32_t R = jb.record_every;
+                if (R)
+                    for (uint32_t p = (t0 / R + 1u) * R, r = t0 / R; p <= t1; p += R, ++r)
+                        record<JT, G>(jb, false, chain, r, cm.s, cm.h, partner_s, 0u);
+            }
+        }
+        __syncwarp();
+        if (own) {
+            uint4* gs = reinterpret_cast<uint4*>(jb.s + static_cast<size_t>(chain) * npad);
+            const uint4* ss = reinterpret_cast<const uint4*>(cm.s);
+            for (uint32_t k = g.gl; k < npad / 16; k += G) gs[k] = ss[k];
+            uint4* gh = reinterpret_cast<uint4*>(static_cast<int*>(jb.h) + static_cast<size_t>(chain) * npad);
+            const uint4* sh = reinterpret_cast<const uint4*>(cm.h);
+            for (uint32_t k = g.gl; k < npad / 4; k += G) gh[k] = sh[k];
+            if (g.gl == 0) {
+                jb.acc_run[chain] = acc;
+                jb.work[2 * static_cast<size_t>(chain)] += n_flips;
+                jb.work[2 * static_cast<size_t>(chain) + 1] += n_rows;
+            }
+        }
+        __syncthreads();  // s_job and the smem slices are reused by the next item
+    }
+}
+
+template <typename JT, int RULE, int NB, int G, int MAXT>
+cudaError_t launch_variant(const JobDev* jobs, const WorkItem* items, uint32_t n_items, uint32_t* queue,
+                           uint32_t nsteps, uint32_t W, uint32_t per_chain, uint32_t grid, cudaStream_t st) {
+    const size_t smem = static_cast<size_t>(per_chain) * W * (32 / G);
+    cudaError_t e = cudaFuncSetAttribute(step_kernel<JT, RULE, NB, G, MAXT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    step_kernel<JT, RULE, NB, G, MAXT><<<grid, 32 * W, smem, st>>>(jobs, items, n_items, queue, nsteps, per_chain);
+    return cudaGetLastError();
+}
+
+template <typename JT, int RULE, int NB, int G, int MAXT>
+int occupancy_variant(uint32_t W, uint32_t per_chain) {
+    const size_t smem = static_cast<size_t>(per_chain) * W * (32 / G);
+    int n = 0;
+    if (cudaFuncSetAttribute(step_kernel<JT, RULE, NB, G, MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(smem)) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<JT, RULE, NB, G, MAXT>, 32 * W, smem) !=
+        cudaSuccess)
+        return 0;
+    return n;
+}
+
+// The register budget follows the CTA size: the largest variant that fits W warps.
+template <typename JT, int RULE, int NB, int G>
+cudaError_t launch_g(const JobDev* jobs, const WorkItem* items, uint32_t n_items, uint32_t* queue,
+                     uint32_t nsteps, uint32_t W, uint32_t per_chain, uint32_t grid, cudaStream_t st) {
+    if (W <= 16) return launch_variant<JT, RULE, NB, G, 512>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
+    if (W <= 20) return launch_variant<JT, RULE, NB, G, 640>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
+    return launch_variant<JT, RULE, NB, G, 1024>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
+}
+template <typename JT, int RULE, int NB, int G>
+int occupancy_g(uint32_t W, uint32_t per_chain) {
+    if (W <= 16) return occupancy_variant<JT, RULE, NB, G, 512>(W, per_chain);
+    if (W <= 20) return occupancy_variant<JT, RULE, NB, G, 640>(W, per_chain);
+    return occupancy_variant<JT, RULE, NB, G, 1024>(W, per_chain);
+}
+
+// Dispatch over (Philox blocks per lane, lanes per chain) for one coupling
+// type and rule; K > 128 (two blocks per lane) needs whole-warp chains.
+template <typename JT, int RULE>
+cudaError_t launch_rule(int nb, int G, const JobDev* jobs, const WorkItem* items, uint32_t n_items, uint32_t* queue,
+                        uint32_t nsteps, uint32_t W, uint32_t per_chain, uint32_t grid, cudaStream_t st) {
+    if (nb == 2) {
+        if constexpr (RULE == 0) {
+            if (G == 32) return launch_g<JT, RULE, 2, 32>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
+        }
+        return cudaErrorInvalidValue;
+    }
+    switch (G) {
+        case 4: return launch_g<JT, RULE, 1, 4>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
+        case 8: return launch_g<JT, RULE, 1, 8>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
+        case 16: return launch_g<JT, RULE, 1, 16>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
+        case 32: return launch_g<JT, RULE, 1, 32>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+template <typename JT, int RULE>
+int occupancy_rule(int nb, int G, uint32_t W, uint32_t per_chain) {
+    if (nb == 2) {
+        if constexpr (RULE == 0) {
+            if (G == 32) return occupancy_g<JT, RULE, 2, 32>(W, per_chain);
+        }
+        return 0;
+    }
+    switch (G) {
+        case 4: return occupancy_g<JT, RULE, 1, 4>(W, per_chain);
+        case 8: return occupancy_g<JT, RULE, 1, 8>(W, per_chain);
+        case 16: return occupancy_g<JT, RULE, 1, 16>(W, per_chain);
+        case 32: return occupancy_g<JT, RULE, 1, 32>(W, per_chain);
+        default: return 0;
+    }
+}
+
+}  // namespace step
+}  // namespace sk

@@ -100,3 +100,43 @@ def test_capture_rejects_default_stream_and_misaligned_recompute():
     with pytest.raises(sk.SKError):
         bb.capture(150)
     _close(b, bb)
+
+
+@pytest.mark.parametrize("lanes", [4, 8, 16, 32])
+def test_lanes_per_chain_do_not_change_results(lanes):
+    # sub-warp chains (32/lanes chains per warp), ragged chain counts (groups
+    # without a chain run as shadows): bit-exact against the oracle
+    torch = need_gpu()
+    import oracle
+    specs = [(100, 8, 0, 7, 0.8), (130, 13, 0, 13, 1.1), (90, 16, 0, 5, 0.5),
+             (64, 1, 1, 9, 1.0)]   # N, K, rule, chains, beta
+    steps, R = 800, 100
+    st = torch.cuda.Stream()
+    made = []
+    for i, (N, K, rule, chains, beta) in enumerate(specs):
+        J = inputs.couplings_pm1(N, 90 + i)
+        inst = sk.Instance(J, stream=st)
+        init = inputs.initial_spins(chains, N, 40 + i)
+        run = sk.Run(inst, chains=chains, K=K, rule=rule, beta=beta, seed=5, stream_id=i,
+                     record_every=R, max_records=steps // R, init=init, trace_chains=chains,
+                     trace_steps=steps)
+        made.append((J, init, inst, run))
+    b = sk.Batch([m[3] for m in made])
+    b.set_lanes(lanes)
+    assert all(c[1] == lanes for c in b.classes())
+    b.advance(300)
+    b.advance(steps - 300)
+    for i, ((N, K, rule, chains, beta), (J, init, inst, run)) in enumerate(zip(specs, made)):
+        E, q, acc = run.observables()
+        spins, h, _ = run.state(fields=True)
+        tr = run.trace()
+        o = oracle.run(J, rule=rule, K=K, beta=beta, seed=5, stream=i, chains=chains, init=init,
+                       steps=steps, record_every=R, trace=True)
+        assert np.array_equal(tr, o["trace"]), i
+        assert np.array_equal(E, o["E"]) and np.array_equal(acc, o["acc"]), i
+        assert np.array_equal(q, o["q"]), i
+        assert np.array_equal(spins, o["spins"]), i
+        assert np.array_equal(h, (J.astype(np.int64) @ spins.T.astype(np.int64)).T), i
+    b.close()
+    for _, _, inst, run in made:
+        run.close(); inst.close()
