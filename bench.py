@@ -277,18 +277,24 @@ def run_ttt(args):
         R = T // 2048
         run = sk.Run(inst, chains=TTT_CHAINS, K=Kt, rule=rule, beta=TTT_BETA, seed=7,
                      record_every=R, max_records=2048)
+        # each method runs with its own autotuned launch geometry (lanes per
+        # chain, chains per CTA); tuning leaves the chains untouched
+        batch = sk.Batch([run])
+        batch.autotune(trial_steps=64)
+        geometry = batch.classes()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         a.record(stream)
         chunk = R * 128
         for _ in range(T // chunk):
-            run.advance(chunk)
+            batch.advance(chunk)
         b.record(stream)
         torch.cuda.synchronize()
+        batch.close()
         E, _, acc = run.observables()
         s_per_step = a.elapsed_time(b) / 1e3 / T
         curves[name] = dict(R=R, T=T, e=E.mean(axis=1) / TTT_N, per_chain=E / TTT_N,
-                            s_per_step=s_per_step, acc=float(acc.mean()) / R)
+                            s_per_step=s_per_step, acc=float(acc.mean()) / R, geometry=geometry)
         run.close()
     # e_inf: mean of the last half of the K=128 run's records; sigma: the
     # equilibrium fluctuation of one record (its chain mean) over that half,
@@ -303,7 +309,7 @@ def run_ttt(args):
     for name, c in curves.items():
         t = (np.arange(len(c["e"])) + 1) * c["R"]
         dev = np.abs(c["e"] - e_inf)
-        m = {"steps_run": c["T"], "s_per_step": c["s_per_step"],
+        m = {"steps_run": c["T"], "s_per_step": c["s_per_step"], "launch_classes": c["geometry"],
              "chain_steps_per_s": TTT_CHAINS / c["s_per_step"], "acceptance": c["acc"],
              "e_final": float(c["e"][-1]), "t_therm_steps": {}, "t_therm_s": {}}
         for eps in TTT_EPS:
