@@ -315,7 +315,8 @@ sk_status periodic_recompute(sk_run* r) {
     return SK_OK;
 }
 
-constexpr size_t kSmemBudget = 232448 - 1024;  // dynamic smem per CTA, static part reserved
+constexpr size_t kSmemBudget = 232448 - 5120;  // dynamic smem per CTA; the step kernel's static
+                                                // part (mbarriers of 256 chains, job) reserved
 
 }  // namespace
 
@@ -732,6 +733,13 @@ sk_status plan_batch(sk_batch* b) {
         if (c.W < 1 || (c.G == 32 && c.W < 2))
             return fail(SK_ERR_INVALID_ARG, "N too large: %u bytes of shared memory per chain", c.per_chain);
         c.cls = sk::step_class(r0->inst->kind, r0->p.rule, r0->p.K > 128 ? 256 : 1, c.G);
+        int occ = sk::step_kernel_occupancy(c.cls, c.W, c.per_chain);
+        while (occ <= 0 && t == b->tuned.end() && c.W > (c.G == 32 ? 2u : 1u)) {  // default choice: step down
+            c.W -= c.G == 32 ? 2u : 1u;
+            occ = sk::step_kernel_occupancy(c.cls, c.W, c.per_chain);
+        }
+        if (occ <= 0)
+            return fail(SK_ERR_CUDA, "step kernel cannot be resident with %u warps of %u-lane chains", c.W, c.G);
         const uint32_t cpc = c.W * (32 / c.G);  // chains per CTA
         c.first_item = static_cast<uint32_t>(items.size());
         for (uint32_t i : g.second) {
@@ -740,9 +748,6 @@ sk_status plan_batch(sk_batch* b) {
                 items.push_back(WorkItem{i, ch, std::min(cpc, r->chains - ch), 0});
         }
         c.n_items = static_cast<uint32_t>(items.size()) - c.first_item;
-        const int occ = sk::step_kernel_occupancy(c.cls, c.W, c.per_chain);
-        if (occ <= 0)
-            return fail(SK_ERR_CUDA, "step kernel cannot be resident with %u warps of %u-lane chains", c.W, c.G);
         c.grid = std::min<uint32_t>(c.n_items, static_cast<uint32_t>(occ * sms));
         grid = std::max(grid, c.grid);
         classes.push_back(c);
@@ -1004,7 +1009,7 @@ sk_status mcmcmc_batch_autotune(sk_batch* b, uint32_t trial_steps, uint32_t* out
             }
             for (uint32_t gw : cand) {
                 b->tuned[key] = gw;
-                if ((s = plan_batch(b)) != SK_OK) break;
+                if (plan_batch(b) != SK_OK) continue;  // not resident: skip the candidate
                 size_t idx = 0;
                 while (idx < b->classes.size() && b->classes[idx].key != key) ++idx;
                 if ((s = launch_segment(b, trial_steps, static_cast<int>(idx))) != SK_OK) break;  // warm-up

@@ -74,7 +74,7 @@ sk_status scratch_address(void** out) {
 
 size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 
-constexpr size_t kSmemBudget = 232448 - 1024;
+constexpr size_t kSmemBudget = 232448 - 5120;  // the step kernel's static shared memory reserved
 
 }  // namespace
 
