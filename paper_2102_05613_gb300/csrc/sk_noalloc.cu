@@ -215,7 +215,7 @@ extern "C" sk_status mcmcmc_run_noalloc(uint32_t N, uint32_t kind, const void* c
     int dev = 0, sms = 0;
     NA_CU(cudaGetDevice(&dev));
     NA_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int occ = sk::step_kernel_occupancy(cls, W, per_warp * W);
+    const int occ = sk::step_kernel_occupancy(cls, W, per_warp);  // bytes per chain (one chain per warp)
     if (occ <= 0) return nfail(SK_ERR_CUDA, "step kernel cannot be resident");
     const uint32_t grid = std::min<uint32_t>(n_items, static_cast<uint32_t>(occ * sms));
     if (steps)
