@@ -259,9 +259,10 @@ sk_status mcmcmc_batch_replay(sk_batch* b, uint32_t times);
 
 /*
  * mcmcmc_batch_autotune: for each launch class of the batch, times a
- * `trial_steps`-step launch for each lanes-per-chain value K allows and each
- * warps-per-CTA value that fits in shared memory (the CTA size also selects
- * the kernel's register budget) and keeps the fastest.
+ * `trial_steps`-step launch for each staging choice, each lanes-per-chain
+ * value K allows and each warps-per-CTA value that fits in shared memory
+ * (the CTA size also selects the kernel's register budget) and keeps the
+ * fastest.
  * Trials start from a copy of the runs' state, which is restored afterwards,
  * and run with records and traces off: the runs' trajectories, records and
  * step counters are unchanged.  *warps_per_cta (may be NULL) receives the
@@ -270,13 +271,16 @@ sk_status mcmcmc_batch_replay(sk_batch* b, uint32_t times);
 sk_status mcmcmc_batch_autotune(sk_batch* b, uint32_t trial_steps, uint32_t* warps_per_cta);
 
 /*
- * mcmcmc_batch_set_lanes: lanes per chain for every launch class (4, 8, 16
- * or 32; 32/lanes chains share a warp), at least as many as a class's K
- * needs; 0 restores the default (the fewest lanes K allows, whole warps for
- * classes of at most 512 chains).  Drops autotuned choices and a captured
- * graph.  Results do not depend on it.
+ * mcmcmc_batch_set_layout: forces the layout of every launch class.
+ *   lanes    lanes per chain, 4, 8, 16 or 32 (32/lanes chains share a warp),
+ *            at least as many as a class's K needs; 0 = default (the fewest
+ *            lanes K allows, whole warps for classes of at most 512 chains);
+ *   staging  0 = default, 1 = the next step's row of J is staged in shared
+ *            memory by TMA (two row buffers per chain), 2 = rows are read
+ *            through L1 (no buffers, so more chains fit in shared memory).
+ * Drops autotuned choices and a captured graph.  Results do not depend on it.
  */
-sk_status mcmcmc_batch_set_lanes(sk_batch* b, uint32_t lanes);
+sk_status mcmcmc_batch_set_layout(sk_batch* b, uint32_t lanes, uint32_t staging);
 
 /* Launch geometry of the batch (for reports): the largest grid, warps per
  * CTA and dynamic shared memory of the first launch class, total work items. */

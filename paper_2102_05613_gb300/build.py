@@ -17,8 +17,9 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libsk_mcmcmc.so")
-SOURCES = ["sk_kernels.cu", "sk_step_pm1_mcmcmc.cu", "sk_step_pm1_metropolis.cu", "sk_step_gauss_mcmcmc.cu",
-           "sk_step_gauss_metropolis.cu", "sk_capi.cu", "sk_noalloc.cu", "sk_recompute.cu", "sk_server.cu"]
+SOURCES = ["sk_kernels.cu", "sk_capi.cu", "sk_noalloc.cu", "sk_recompute.cu", "sk_server.cu"] + [
+    f"sk_step_{c}_{r}_{s}.cu" for c in ("pm1", "gauss") for r in ("mcmcmc", "metropolis")
+    for s in ("staged", "direct")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

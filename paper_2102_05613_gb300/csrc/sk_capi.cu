@@ -118,17 +118,20 @@ struct sk_batch {
     // warps per CTA W (W * 32/G chains per CTA).
     struct Class {
         uint64_t key;
-        int cls;                 // kernel class incl. G (step_class)
+        int cls;                 // kernel class incl. G and staging (step_class)
         uint32_t G, gmin;        // lanes per chain, fewest allowed
+        uint32_t stage;          // row a staged by TMA (1) or read through L1 (0)
+        uint32_t per_chain_staged, per_chain_direct;
         uint32_t per_chain;      // shared memory per chain
         uint32_t W;              // warps per CTA
         uint32_t first_item, n_items, grid;
     };
     std::vector<sk_run*> runs;
     std::vector<Class> classes;
-    std::map<uint64_t, uint32_t> tuned;  // key -> (G << 8) | W chosen by the autotuner or forced
+    std::map<uint64_t, uint32_t> tuned;  // key -> (stage << 16) | (G << 8) | W chosen by the autotuner
     uint32_t W_override = 0;             // warps_per_cta given at creation (0: as many as fit)
-    uint32_t G_override = 0;             // mcmcmc_batch_set_lanes (0: default)
+    uint32_t G_override = 0;             // mcmcmc_batch_set_layout lanes (0: default)
+    uint32_t S_override = 0;             // mcmcmc_batch_set_layout staging (0: default = staged)
     JobDev* djobs = nullptr;
     WorkItem* ditems = nullptr;
     uint32_t* dqueue = nullptr;  // one work counter per class (up to kMaxClasses)
@@ -668,8 +671,8 @@ namespace {
 
 constexpr uint32_t kMaxClasses = 64;
 
-uint32_t run_per_chain(const sk_run* r) {
-    return static_cast<uint32_t>((sk::warp_smem_bytes(r->inst->Npad, r->inst->kind) + 127) / 128 * 128);
+uint32_t run_per_chain(const sk_run* r, bool staged = true) {
+    return static_cast<uint32_t>((sk::warp_smem_bytes(r->inst->Npad, r->inst->kind, staged) + 127) / 128 * 128);
 }
 // Fewest lanes per chain for a run: one Philox block (4 slots) per lane;
 // K > 128 takes two blocks per lane on a whole warp.
@@ -684,7 +687,7 @@ uint64_t class_key(const sk_run* r) {
     uint32_t b = 128;
     const uint32_t pc = run_per_chain(r);
     while (b < pc) b <<= 1;
-    const uint64_t kc = static_cast<uint64_t>(sk::step_class(r->inst->kind, r->p.rule, r->p.K, 32)) & ~7ull;
+    const uint64_t kc = static_cast<uint64_t>(sk::step_class(r->inst->kind, r->p.rule, r->p.K, 32, 0)) & ~7ull;
     return (kc << 40) | (static_cast<uint64_t>(run_gmin(r)) << 32) | b;
 }
 // Most warps per CTA for G lanes per chain: chains of a pair share a CTA,
@@ -718,21 +721,26 @@ sk_status plan_batch(sk_batch* b) {
         c.gmin = run_gmin(r0);
         uint64_t total = 0;
         for (uint32_t i : g.second) {
-            c.per_chain = std::max(c.per_chain, run_per_chain(b->runs[i]));
+            c.per_chain_staged = std::max(c.per_chain_staged, run_per_chain(b->runs[i], true));
+            c.per_chain_direct = std::max(c.per_chain_direct, run_per_chain(b->runs[i], false));
             total += b->runs[i]->chains;
         }
         auto t = b->tuned.find(c.key);
         if (t != b->tuned.end()) {
-            c.G = t->second >> 8;
+            c.stage = t->second >> 16;
+            c.G = (t->second >> 8) & 0xFFu;
             c.W = t->second & 0xFFu;
+            c.per_chain = c.stage ? c.per_chain_staged : c.per_chain_direct;
         } else {
+            c.stage = b->S_override == 2 ? 0u : 1u;
+            c.per_chain = c.stage ? c.per_chain_staged : c.per_chain_direct;
             c.G = b->G_override ? std::max(b->G_override, c.gmin) : (total <= 512 ? 32u : c.gmin);
             const uint32_t fit = fit_warps(c.per_chain, c.G);
             c.W = b->W_override ? std::min(b->W_override, fit) : fit;
         }
         if (c.W < 1 || (c.G == 32 && c.W < 2))
             return fail(SK_ERR_INVALID_ARG, "N too large: %u bytes of shared memory per chain", c.per_chain);
-        c.cls = sk::step_class(r0->inst->kind, r0->p.rule, r0->p.K > 128 ? 256 : 1, c.G);
+        c.cls = sk::step_class(r0->inst->kind, r0->p.rule, r0->p.K > 128 ? 256 : 1, c.G, c.stage);
         int occ = sk::step_kernel_occupancy(c.cls, c.W, c.per_chain);
         while (occ <= 0 && t == b->tuned.end() && c.W > (c.G == 32 ? 2u : 1u)) {  // default choice: step down
             c.W -= c.G == 32 ? 2u : 1u;
@@ -809,11 +817,13 @@ sk_status mcmcmc_batch_create(sk_run* const* runs, uint32_t n, uint32_t W, sk_ba
     return SK_OK;
 }
 
-sk_status mcmcmc_batch_set_lanes(sk_batch* b, uint32_t lanes) {
+sk_status mcmcmc_batch_set_layout(sk_batch* b, uint32_t lanes, uint32_t staging) {
     if (!b) return fail(SK_ERR_INVALID_ARG, "batch is NULL");
     if (lanes && lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32)
         return fail(SK_ERR_INVALID_ARG, "lanes per chain must be 0, 4, 8, 16 or 32");
+    if (staging > 2) return fail(SK_ERR_INVALID_ARG, "staging must be 0, 1 or 2");
     b->G_override = lanes;
+    b->S_override = staging;
     b->tuned.clear();
     return plan_batch(b);
 }
@@ -999,14 +1009,16 @@ sk_status mcmcmc_batch_autotune(sk_batch* b, uint32_t trial_steps, uint32_t* out
         const std::vector<sk_batch::Class> cls0 = b->classes;
         for (size_t k = 0; k < cls0.size() && s == SK_OK; ++k) {
             const uint64_t key = cls0[k].key;
-            uint32_t best = (cls0[k].G << 8) | cls0[k].W;
+            uint32_t best = (cls0[k].stage << 16) | (cls0[k].G << 8) | cls0[k].W;
             float best_ms = 1e30f;
-            std::vector<uint32_t> cand;  // (G << 8) | W
-            for (uint32_t G = cls0[k].gmin; G <= 32; G <<= 1) {
-                const uint32_t fit = fit_warps(cls0[k].per_chain, G);
-                for (uint32_t w : {32u, 24u, 16u, 12u, 8u, 6u, 4u, 2u, 1u})
-                    if (w <= fit && (G < 32 || (w & 1u) == 0)) cand.push_back((G << 8) | w);
-            }
+            std::vector<uint32_t> cand;  // (stage << 16) | (G << 8) | W
+            for (uint32_t stage = 0; stage <= 1; ++stage)
+                for (uint32_t G = cls0[k].gmin; G <= 32; G <<= 1) {
+                    const uint32_t fit =
+                        fit_warps(stage ? cls0[k].per_chain_staged : cls0[k].per_chain_direct, G);
+                    for (uint32_t w : {32u, 24u, 16u, 12u, 8u, 6u, 4u, 2u, 1u})
+                        if (w <= fit && (G < 32 || (w & 1u) == 0)) cand.push_back((stage << 16) | (G << 8) | w);
+                }
             for (uint32_t gw : cand) {
                 b->tuned[key] = gw;
                 if (plan_batch(b) != SK_OK) continue;  // not resident: skip the candidate

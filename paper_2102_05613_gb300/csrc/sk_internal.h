@@ -48,24 +48,26 @@ struct WorkItem {
     uint32_t job, chain0, nchains, pad;
 };
 
-// Bytes of shared memory one chain needs for spins, fields and the two J-row
-// staging buffers.
-inline size_t warp_smem_bytes(uint32_t npad, uint32_t kind) {
+// Bytes of shared memory one chain needs for spins, fields and (staged) the
+// two J-row buffers.
+inline size_t warp_smem_bytes(uint32_t npad, uint32_t kind, bool staged = true) {
     size_t bj = kind == 0 ? 1 : 4;
-    return (size_t)npad * (1 + 4 + 2 * bj);
+    return (size_t)npad * (1 + 4 + (staged ? 2 * bj : 0));
 }
 
 // Kernel launchers (sk_kernels.cu).  All return cudaGetLastError().
 //
 // The step kernel is instantiated per class = step_class(kind, rule, K, G):
 // the coupling type, the rule, whether K needs two Philox blocks per lane
-// (K > 128, whole-warp chains only) and the lanes per chain G (4, 8, 16, 32;
+// (K > 128, whole-warp chains only), whether row a is staged in shared
+// memory by TMA (stage) or read through L1, and the lanes per chain G (4, 8, 16, 32;
 // 32/G chains per warp).  A CTA holds W warps, i.e. W * 32/G chains, each
 // with `per_chain` bytes of shared memory.  launch_step runs the items of one
 // class; `bump` advances every job's step counter afterwards (set it on the
 // last class).
-int step_class(uint32_t kind, uint32_t rule, uint32_t K, uint32_t G);
+int step_class(uint32_t kind, uint32_t rule, uint32_t K, uint32_t G, uint32_t stage);
 uint32_t class_lanes(int cls);
+bool class_staged(int cls);
 cudaError_t launch_step(const JobDev* jobs, const WorkItem* items, uint32_t n_items,
                         uint32_t* queue, uint64_t nsteps, uint32_t warps_per_cta,
                         uint32_t per_chain_bytes, uint32_t grid, int cls, uint32_t n_jobs,

@@ -9,18 +9,30 @@
 
 namespace sk {
 
-cudaError_t launch_step_pm1_mcmcmc(int, int, const JobDev*, const WorkItem*, uint32_t, uint32_t*, uint32_t,
-                                   uint32_t, uint32_t, uint32_t, cudaStream_t);
-cudaError_t launch_step_pm1_metropolis(int, int, const JobDev*, const WorkItem*, uint32_t, uint32_t*, uint32_t,
-                                       uint32_t, uint32_t, uint32_t, cudaStream_t);
-cudaError_t launch_step_gauss_mcmcmc(int, int, const JobDev*, const WorkItem*, uint32_t, uint32_t*, uint32_t,
-                                     uint32_t, uint32_t, uint32_t, cudaStream_t);
-cudaError_t launch_step_gauss_metropolis(int, int, const JobDev*, const WorkItem*, uint32_t, uint32_t*, uint32_t,
-                                         uint32_t, uint32_t, uint32_t, cudaStream_t);
-int occupancy_pm1_mcmcmc(int, int, uint32_t, uint32_t);
-int occupancy_pm1_metropolis(int, int, uint32_t, uint32_t);
-int occupancy_gauss_mcmcmc(int, int, uint32_t, uint32_t);
-int occupancy_gauss_metropolis(int, int, uint32_t, uint32_t);
+cudaError_t launch_step_pm1_mcmcmc_staged(int, int, const JobDev*, const WorkItem*, uint32_t, uint32_t*,
+                                      uint32_t, uint32_t, uint32_t, uint32_t, cudaStream_t);
+int occupancy_pm1_mcmcmc_staged(int, int, uint32_t, uint32_t);
+cudaError_t launch_step_pm1_mcmcmc_direct(int, int, const JobDev*, const WorkItem*, uint32_t, uint32_t*,
+                                      uint32_t, uint32_t, uint32_t, uint32_t, cudaStream_t);
+int occupancy_pm1_mcmcmc_direct(int, int, uint32_t, uint32_t);
+cudaError_t launch_step_pm1_metropolis_staged(int, int, const JobDev*, const WorkItem*, uint32_t, uint32_t*,
+                                      uint32_t, uint32_t, uint32_t, uint32_t, cudaStream_t);
+int occupancy_pm1_metropolis_staged(int, int, uint32_t, uint32_t);
+cudaError_t launch_step_pm1_metropolis_direct(int, int, const JobDev*, const WorkItem*, uint32_t, uint32_t*,
+                                      uint32_t, uint32_t, uint32_t, uint32_t, cudaStream_t);
+int occupancy_pm1_metropolis_direct(int, int, uint32_t, uint32_t);
+cudaError_t launch_step_gauss_mcmcmc_staged(int, int, const JobDev*, const WorkItem*, uint32_t, uint32_t*,
+                                      uint32_t, uint32_t, uint32_t, uint32_t, cudaStream_t);
+int occupancy_gauss_mcmcmc_staged(int, int, uint32_t, uint32_t);
+cudaError_t launch_step_gauss_mcmcmc_direct(int, int, const JobDev*, const WorkItem*, uint32_t, uint32_t*,
+                                      uint32_t, uint32_t, uint32_t, uint32_t, cudaStream_t);
+int occupancy_gauss_mcmcmc_direct(int, int, uint32_t, uint32_t);
+cudaError_t launch_step_gauss_metropolis_staged(int, int, const JobDev*, const WorkItem*, uint32_t, uint32_t*,
+                                      uint32_t, uint32_t, uint32_t, uint32_t, cudaStream_t);
+int occupancy_gauss_metropolis_staged(int, int, uint32_t, uint32_t);
+cudaError_t launch_step_gauss_metropolis_direct(int, int, const JobDev*, const WorkItem*, uint32_t, uint32_t*,
+                                      uint32_t, uint32_t, uint32_t, uint32_t, cudaStream_t);
+int occupancy_gauss_metropolis_direct(int, int, uint32_t, uint32_t);
 
 namespace {
 
@@ -136,14 +148,35 @@ __global__ void energy_kernel(const JT* __restrict__ J, uint32_t N, uint32_t npa
 
 }  // namespace
 
-// class = kind * 32 + rule * 16 + (nb - 1) * 8 + log2(G)
-int step_class(uint32_t kind, uint32_t rule, uint32_t K, uint32_t G) {
+// class = kind * 64 + rule * 32 + stage * 16 + (nb - 1) * 8 + log2(G)
+int step_class(uint32_t kind, uint32_t rule, uint32_t K, uint32_t G, uint32_t stage) {
     const int nb = (rule == 0 && K > 128) ? 2 : 1;
     int lg = 0;
     while ((1u << lg) < G) ++lg;
-    return static_cast<int>(kind) * 32 + static_cast<int>(rule) * 16 + (nb - 1) * 8 + lg;
+    return static_cast<int>(kind) * 64 + static_cast<int>(rule) * 32 + static_cast<int>(stage != 0) * 16 +
+           (nb - 1) * 8 + lg;
 }
 uint32_t class_lanes(int cls) { return 1u << (cls & 7); }
+bool class_staged(int cls) { return ((cls >> 4) & 1) != 0; }
+
+#define SK_DISPATCH(F, ...)                                                          \
+    do {                                                                             \
+        const int kind_ = cls >> 6, rule_ = (cls >> 5) & 1, stage_ = (cls >> 4) & 1; \
+        if (kind_ == 0 && rule_ == 0) return stage_ ? F##_pm1_mcmcmc_staged(__VA_ARGS__) : F##_pm1_mcmcmc_direct(__VA_ARGS__); \
+        if (kind_ == 0) return stage_ ? F##_pm1_metropolis_staged(__VA_ARGS__) : F##_pm1_metropolis_direct(__VA_ARGS__); \
+        if (rule_ == 0) return stage_ ? F##_gauss_mcmcmc_staged(__VA_ARGS__) : F##_gauss_mcmcmc_direct(__VA_ARGS__); \
+        return stage_ ? F##_gauss_metropolis_staged(__VA_ARGS__) : F##_gauss_metropolis_direct(__VA_ARGS__); \
+    } while (0)
+
+namespace {
+cudaError_t launch_class(int cls, int nb, int G, const JobDev* jobs, const WorkItem* items, uint32_t n_items,
+                         uint32_t* queue, uint32_t ns, uint32_t W, uint32_t per_chain, uint32_t grid, cudaStream_t st) {
+    SK_DISPATCH(launch_step, nb, G, jobs, items, n_items, queue, ns, W, per_chain, grid, st);
+}
+int occupancy_class(int cls, int nb, int G, uint32_t W, uint32_t pc) {
+    SK_DISPATCH(occupancy, nb, G, W, pc);
+}
+}  // namespace
 
 cudaError_t launch_step(const JobDev* jobs, const WorkItem* items, uint32_t n_items, uint32_t* queue,
                         uint64_t nsteps, uint32_t W, uint32_t per_chain, uint32_t grid, int cls, uint32_t n_jobs,
@@ -151,23 +184,16 @@ cudaError_t launch_step(const JobDev* jobs, const WorkItem* items, uint32_t n_it
     cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
     const uint32_t ns = static_cast<uint32_t>(nsteps);
-    const int kind = cls >> 5, rule = (cls >> 4) & 1, nb = ((cls >> 3) & 1) + 1, G = 1 << (cls & 7);
-    if (kind == 0 && rule == 0) e = launch_step_pm1_mcmcmc(nb, G, jobs, items, n_items, queue, ns, W, per_chain, grid, st);
-    else if (kind == 0) e = launch_step_pm1_metropolis(nb, G, jobs, items, n_items, queue, ns, W, per_chain, grid, st);
-    else if (rule == 0) e = launch_step_gauss_mcmcmc(nb, G, jobs, items, n_items, queue, ns, W, per_chain, grid, st);
-    else e = launch_step_gauss_metropolis(nb, G, jobs, items, n_items, queue, ns, W, per_chain, grid, st);
+    const int nb = ((cls >> 3) & 1) + 1, G = 1 << (cls & 7);
+    e = launch_class(cls, nb, G, jobs, items, n_items, queue, ns, W, per_chain, grid, st);
     if (e != cudaSuccess || !bump) return e;
     bump_steps<<<(n_jobs + 127) / 128, 128, 0, st>>>(jobs, n_jobs, nsteps);
     return cudaGetLastError();
 }
 
 int step_kernel_occupancy(int cls, uint32_t W, size_t per_chain) {
-    const int kind = cls >> 5, rule = (cls >> 4) & 1, nb = ((cls >> 3) & 1) + 1, G = 1 << (cls & 7);
-    const uint32_t pc = static_cast<uint32_t>(per_chain);
-    if (kind == 0 && rule == 0) return occupancy_pm1_mcmcmc(nb, G, W, pc);
-    if (kind == 0) return occupancy_pm1_metropolis(nb, G, W, pc);
-    if (rule == 0) return occupancy_gauss_mcmcmc(nb, G, W, pc);
-    return occupancy_gauss_metropolis(nb, G, W, pc);
+    const int nb = ((cls >> 3) & 1) + 1, G = 1 << (cls & 7);
+    return occupancy_class(cls, nb, G, W, static_cast<uint32_t>(per_chain));
 }
 
 cudaError_t launch_init(const JobDev* job, const int8_t* init, uint32_t chains, uint32_t N,

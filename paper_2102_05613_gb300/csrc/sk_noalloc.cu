@@ -211,7 +211,7 @@ extern "C" sk_status mcmcmc_run_noalloc(uint32_t N, uint32_t kind, const void* c
     }
 
     NA_CU(sk::launch_init(&job, spins, chains, N, Npad, kind, st));
-    const int cls = sk::step_class(kind, rule, K, 32);  // whole-warp chains
+    const int cls = sk::step_class(kind, rule, K, 32, 1);  // whole-warp chains, staged rows
     int dev = 0, sms = 0;
     NA_CU(cudaGetDevice(&dev));
     NA_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));

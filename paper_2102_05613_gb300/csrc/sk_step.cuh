@@ -243,7 +243,7 @@ __device__ __noinline__ void record(const JobDev& jb, bool write, uint32_t chain
 // nothing, so that every lane reaches the same barriers).  `dead` is set
 // after a timed-out wait: the group then stops working but still meets the
 // CTA's record barriers.
-template <typename JT, int RULE, int NB, int G>
+template <typename JT, int RULE, int NB, int G, int STAGE>
 __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_t chain, const ChainMem& cm,
                                            const int8_t* partner_s, uint32_t t0, uint32_t t1, uint32_t& acc,
                                            uint32_t& phase, bool& dead, uint32_t& n_flips, uint32_t& n_rows) {
@@ -281,10 +281,12 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
     } else {
         first = __umulhi(block0<G>(bc, t0, chain, c3, k0, k1, g).x, N);
     }
-    if (g.gl == 0 && !dead) {
+    if (STAGE && g.gl == 0 && !dead) {
         dev::fence_proxy_async();
         dev::bulk_load(cm.row[t0 & 1u], Jg + static_cast<size_t>(first) * npad, rowbytes, &cm.bar[t0 & 1u]);
     }
+    (void)first;
+    (void)rowbytes;
 
     for (uint32_t t = t0; t < t1; ++t) {
         const uint32_t buf = t & 1u;
@@ -306,13 +308,16 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
             } else {
                 nx = __umulhi(block0<G>(bc, t + 1u, chain, c3, k0, k1, g).x, N);
             }
-            __syncwarp(g.mask);  // every lane of the group is done with buffer buf^1 (step t-1)
-            if (g.gl == 0 && !dead) {
-                dev::fence_proxy_async();
-                dev::bulk_load(cm.row[buf ^ 1u], Jg + static_cast<size_t>(nx) * npad, rowbytes, &cm.bar[buf ^ 1u]);
+            if constexpr (STAGE) {
+                __syncwarp(g.mask);  // every lane of the group is done with buffer buf^1 (step t-1)
+                if (g.gl == 0 && !dead) {
+                    dev::fence_proxy_async();
+                    dev::bulk_load(cm.row[buf ^ 1u], Jg + static_cast<size_t>(nx) * npad, rowbytes, &cm.bar[buf ^ 1u]);
+                }
             }
+            (void)nx;
         }
-        if (!dead) {
+        if (STAGE && !dead) {
             // every lane waits; the outcome is made group-uniform
             const bool okl = dev::mbar_wait_bounded(&cm.bar[buf], (phase >> buf) & 1u);
             const bool ok = gballot(g, okl) == (G == 32 ? kFull : ((1u << G) - 1u));
@@ -322,7 +327,14 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                 if (g.gl == 0) atomicExch(jb.err, kDevTimeout);
             }
         }
-        const JT* rowA = static_cast<const JT*>(cm.row[buf]);
+        // row a of this step: staged in shared memory, or read through L1 from J
+        const JT* rowA;
+        if constexpr (STAGE) {
+            rowA = static_cast<const JT*>(cm.row[buf]);
+        } else {
+            const uint32_t a0 = RULE == 0 ? gshfl(g, site[0], 0) : __umulhi(b0.x, N);
+            rowA = Jg + static_cast<size_t>(a0) * npad;
+        }
 
         if (!dead) {
             if constexpr (RULE == 1) {
@@ -361,8 +373,8 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                     const H hi = hf[i];
                     const H single = static_cast<H>(2 * si) * hi;
                     // leaf root: the centre flipped at b = site_d (0 if b = a)
-                    const H dbl = (i == a) ? H(0)
-                                           : dEa + single - static_cast<H>(4 * sa * si) * static_cast<H>(rowA[i]);
+                    const JT jab = STAGE ? rowA[i] : __ldg(rowA + i);
+                    const H dbl = (i == a) ? H(0) : dEa + single - static_cast<H>(4 * sa * si) * static_cast<H>(jab);
                     const H v = !leaf ? single : (d == 1u ? dEa : dbl);
                     dE[q] = v;
                     if (d <= K) mloc = mloc < v ? mloc : v;
@@ -470,7 +482,7 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                 const int c1 = 2 * S[x1];
                 const int c2 = nflip == 2 ? 2 * S[x2] : 0;
                 if (x1_staged)
-                    update_fields<JT, true, G>(hf, rowA, Jg + static_cast<size_t>(x2) * npad, c1, c2, npad, g.gl);
+                    update_fields<JT, STAGE != 0, G>(hf, rowA, Jg + static_cast<size_t>(x2) * npad, c1, c2, npad, g.gl);
                 else
                     update_fields<JT, false, G>(hf, Jg + static_cast<size_t>(x1) * npad, nullptr, c1, 0, npad, g.gl);
                 __syncwarp(g.mask);
@@ -500,7 +512,9 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
 
 // MAXT bounds the CTA size and so the register budget per thread
 // (65536 / MAXT): 1024 -> 64, 640 -> 96, 512 -> 128 registers.
-template <typename JT, int RULE, int NB, int G, int MAXT>
+// STAGE: stage row a by TMA (two row buffers per chain in shared memory) or
+// read it through L1 (no buffers: more chains fit in shared memory).
+template <typename JT, int RULE, int NB, int G, int STAGE, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1)
     step_kernel(const JobDev* __restrict__ jobs, const WorkItem* __restrict__ items, uint32_t n_items,
                 uint32_t* __restrict__ queue, uint32_t nsteps, uint32_t per_chain) {
@@ -561,8 +575,8 @@ __global__ void __launch_bounds__(MAXT, 1)
         __syncwarp();
         if (t1 > t0) {
             if (warp_busy) {
-                chain_loop<JT, RULE, NB, G>(jb, own, chain, cm, partner_s, t0, t1, acc, phase, dead, n_flips,
-                                            n_rows);
+                chain_loop<JT, RULE, NB, G, STAGE>(jb, own, chain, cm, partner_s, t0, t1, acc, phase, dead,
+                                                   n_flips, n_rows);
             } else {
                 // no chain in this warp: meet the CTA's record barriers only
                 const uint32_t R = jb.record_every;
@@ -589,77 +603,78 @@ __global__ void __launch_bounds__(MAXT, 1)
     }
 }
 
-template <typename JT, int RULE, int NB, int G, int MAXT>
+template <typename JT, int RULE, int NB, int G, int STAGE, int MAXT>
 cudaError_t launch_variant(const JobDev* jobs, const WorkItem* items, uint32_t n_items, uint32_t* queue,
                            uint32_t nsteps, uint32_t W, uint32_t per_chain, uint32_t grid, cudaStream_t st) {
     const size_t smem = static_cast<size_t>(per_chain) * W * (32 / G);
-    cudaError_t e = cudaFuncSetAttribute(step_kernel<JT, RULE, NB, G, MAXT>,
+    cudaError_t e = cudaFuncSetAttribute(step_kernel<JT, RULE, NB, G, STAGE, MAXT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    step_kernel<JT, RULE, NB, G, MAXT><<<grid, 32 * W, smem, st>>>(jobs, items, n_items, queue, nsteps, per_chain);
+    step_kernel<JT, RULE, NB, G, STAGE, MAXT><<<grid, 32 * W, smem, st>>>(jobs, items, n_items, queue, nsteps, per_chain);
     return cudaGetLastError();
 }
 
-template <typename JT, int RULE, int NB, int G, int MAXT>
+template <typename JT, int RULE, int NB, int G, int STAGE, int MAXT>
 int occupancy_variant(uint32_t W, uint32_t per_chain) {
     const size_t smem = static_cast<size_t>(per_chain) * W * (32 / G);
     int n = 0;
-    if (cudaFuncSetAttribute(step_kernel<JT, RULE, NB, G, MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(step_kernel<JT, RULE, NB, G, STAGE, MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(smem)) != cudaSuccess)
         return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<JT, RULE, NB, G, MAXT>, 32 * W, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<JT, RULE, NB, G, STAGE, MAXT>, 32 * W, smem) !=
         cudaSuccess)
         return 0;
     return n;
 }
 
 // The register budget follows the CTA size: the largest variant that fits W warps.
-template <typename JT, int RULE, int NB, int G>
+template <typename JT, int RULE, int NB, int G, int STAGE>
 cudaError_t launch_g(const JobDev* jobs, const WorkItem* items, uint32_t n_items, uint32_t* queue,
                      uint32_t nsteps, uint32_t W, uint32_t per_chain, uint32_t grid, cudaStream_t st) {
-    if (W <= 16) return launch_variant<JT, RULE, NB, G, 512>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
-    if (W <= 20) return launch_variant<JT, RULE, NB, G, 640>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
-    return launch_variant<JT, RULE, NB, G, 1024>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
+    if (W <= 16) return launch_variant<JT, RULE, NB, G, STAGE, 512>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
+    if (W <= 20) return launch_variant<JT, RULE, NB, G, STAGE, 640>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
+    return launch_variant<JT, RULE, NB, G, STAGE, 1024>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
 }
-template <typename JT, int RULE, int NB, int G>
+template <typename JT, int RULE, int NB, int G, int STAGE>
 int occupancy_g(uint32_t W, uint32_t per_chain) {
-    if (W <= 16) return occupancy_variant<JT, RULE, NB, G, 512>(W, per_chain);
-    if (W <= 20) return occupancy_variant<JT, RULE, NB, G, 640>(W, per_chain);
-    return occupancy_variant<JT, RULE, NB, G, 1024>(W, per_chain);
+    if (W <= 16) return occupancy_variant<JT, RULE, NB, G, STAGE, 512>(W, per_chain);
+    if (W <= 20) return occupancy_variant<JT, RULE, NB, G, STAGE, 640>(W, per_chain);
+    return occupancy_variant<JT, RULE, NB, G, STAGE, 1024>(W, per_chain);
 }
 
 // Dispatch over (Philox blocks per lane, lanes per chain) for one coupling
-// type and rule; K > 128 (two blocks per lane) needs whole-warp chains.
-template <typename JT, int RULE>
+// type, rule and staging choice; K > 128 (two blocks per lane) needs
+// whole-warp chains.
+template <typename JT, int RULE, int STAGE>
 cudaError_t launch_rule(int nb, int G, const JobDev* jobs, const WorkItem* items, uint32_t n_items, uint32_t* queue,
                         uint32_t nsteps, uint32_t W, uint32_t per_chain, uint32_t grid, cudaStream_t st) {
     if (nb == 2) {
         if constexpr (RULE == 0) {
-            if (G == 32) return launch_g<JT, RULE, 2, 32>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
+            if (G == 32) return launch_g<JT, RULE, 2, 32, STAGE>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
         }
         return cudaErrorInvalidValue;
     }
     switch (G) {
-        case 4: return launch_g<JT, RULE, 1, 4>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
-        case 8: return launch_g<JT, RULE, 1, 8>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
-        case 16: return launch_g<JT, RULE, 1, 16>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
-        case 32: return launch_g<JT, RULE, 1, 32>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
+        case 4: return launch_g<JT, RULE, 1, 4, STAGE>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
+        case 8: return launch_g<JT, RULE, 1, 8, STAGE>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
+        case 16: return launch_g<JT, RULE, 1, 16, STAGE>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
+        case 32: return launch_g<JT, RULE, 1, 32, STAGE>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
         default: return cudaErrorInvalidValue;
     }
 }
-template <typename JT, int RULE>
+template <typename JT, int RULE, int STAGE>
 int occupancy_rule(int nb, int G, uint32_t W, uint32_t per_chain) {
     if (nb == 2) {
         if constexpr (RULE == 0) {
-            if (G == 32) return occupancy_g<JT, RULE, 2, 32>(W, per_chain);
+            if (G == 32) return occupancy_g<JT, RULE, 2, 32, STAGE>(W, per_chain);
         }
         return 0;
     }
     switch (G) {
-        case 4: return occupancy_g<JT, RULE, 1, 4>(W, per_chain);
-        case 8: return occupancy_g<JT, RULE, 1, 8>(W, per_chain);
-        case 16: return occupancy_g<JT, RULE, 1, 16>(W, per_chain);
-        case 32: return occupancy_g<JT, RULE, 1, 32>(W, per_chain);
+        case 4: return occupancy_g<JT, RULE, 1, 4, STAGE>(W, per_chain);
+        case 8: return occupancy_g<JT, RULE, 1, 8, STAGE>(W, per_chain);
+        case 16: return occupancy_g<JT, RULE, 1, 16, STAGE>(W, per_chain);
+        case 32: return occupancy_g<JT, RULE, 1, 32, STAGE>(W, per_chain);
         default: return 0;
     }
 }

@@ -32,7 +32,7 @@ EXPORTS = ["sk_create_instance", "sk_set_couplings", "sk_destroy_instance", "sk_
            "mcmcmc_trace", "mcmcmc_counters", "mcmcmc_free",
            "mcmcmc_batch_create", "mcmcmc_batch_advance", "mcmcmc_batch_capture",
            "mcmcmc_batch_replay", "mcmcmc_batch_autotune", "mcmcmc_batch_info",
-           "mcmcmc_batch_classes", "mcmcmc_batch_set_lanes",
+           "mcmcmc_batch_classes", "mcmcmc_batch_set_layout",
            "mcmcmc_batch_free", "mcmcmc_run_noalloc", "sk_last_error"]
 
 
@@ -97,7 +97,7 @@ def lib(build_if_missing: bool = True):
             "mcmcmc_batch_replay": [vp, u32],
             "mcmcmc_batch_autotune": [vp, u32, vp],
             "mcmcmc_batch_classes": [vp, u32, vp, vp],
-            "mcmcmc_batch_set_lanes": [vp, u32],
+            "mcmcmc_batch_set_layout": [vp, u32, u32],
             "mcmcmc_batch_info": [vp, vp, vp, vp, vp],
             "mcmcmc_batch_free": [vp],
             "mcmcmc_run_noalloc": [u32, u32, vp, d, u32, u32, u32, d, u64, u32, u64, vp, vp, vp],
@@ -336,8 +336,10 @@ class Batch:
                                           d.ctypes.data_as(C.c_void_p)))
         return [tuple(int(x) for x in d[6 * k:6 * k + 6]) for k in range(n.value)]
 
-    def set_lanes(self, lanes: int):
-        _check(lib().mcmcmc_batch_set_lanes(self.handle, int(lanes)))
+    def set_layout(self, lanes: int = 0, staging: int = 0):
+        """mcmcmc_batch_set_layout: lanes per chain (0, 4, 8, 16, 32); staging
+        0 default, 1 TMA-staged rows, 2 rows read through L1."""
+        _check(lib().mcmcmc_batch_set_layout(self.handle, int(lanes), int(staging)))
 
     def info(self):
         v = [C.c_uint32(0) for _ in range(4)]

@@ -102,8 +102,9 @@ def test_capture_rejects_default_stream_and_misaligned_recompute():
     _close(b, bb)
 
 
+@pytest.mark.parametrize("staging", [1, 2])
 @pytest.mark.parametrize("lanes", [4, 8, 16, 32])
-def test_lanes_per_chain_do_not_change_results(lanes):
+def test_lanes_per_chain_do_not_change_results(lanes, staging):
     # sub-warp chains (32/lanes chains per warp), ragged chain counts (groups
     # without a chain run as shadows): bit-exact against the oracle
     torch = need_gpu()
@@ -122,7 +123,7 @@ def test_lanes_per_chain_do_not_change_results(lanes):
                      trace_steps=steps)
         made.append((J, init, inst, run))
     b = sk.Batch([m[3] for m in made])
-    b.set_lanes(lanes)
+    b.set_layout(lanes, staging)
     assert all(c[1] == lanes for c in b.classes())
     b.advance(300)
     b.advance(steps - 300)
