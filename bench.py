@@ -501,7 +501,10 @@ def run_ours(args):
     runs = [sk.Run(inst, chains=CHAINS, K=K, beta=BETA, seed=1 + rank, stream_id=i,
                    record_every=R, max_records=cap) for i, inst in enumerate(insts)]
     batch = sk.Batch(runs, warps_per_cta=args.warps_per_cta)
+    if not args.warps_per_cta:
+        batch.autotune(trial_steps=10)  # launch geometry only; the chains are untouched
     info = batch.info()
+    info["classes"] = batch.classes()
 
     def barrier():
         torch.cuda.synchronize()
