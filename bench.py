@@ -492,9 +492,9 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    from paper_2102_05613_gb300 import inputs, sk
+    from paper_2102_05613_gb300 import inputs, replicas, sk
     stream = torch.cuda.current_stream()
-    seed_base = 1000 * rank
+    seed_base = replicas.seed_base(rank)
     couplings = [inputs.couplings_gauss(N, seed_base + i) for i in range(INSTANCES)]
     cap = args.warmup + args.steps + args.e2e_steps + 2
     insts = [sk.Instance(J, stream=stream) for J in couplings]
@@ -530,11 +530,7 @@ def run_ours(args):
     c1 = [r.counters() for r in runs]
     total_ms = ev[0][0].elapsed_time(ev[-1][1])
     launch_ms = [s.elapsed_time(e) for s, e in ev]
-    t_local = total_ms / 1e3
-    t = torch.tensor([t_local], device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    T = float(t.item())
+    T = replicas.max_over_ranks(total_ms / 1e3, dist, device="cuda")
     chain_steps_rank = INSTANCES * CHAINS * R * args.steps
     value = world * chain_steps_rank * K / T
     mc_steps = world * chain_steps_rank / T
@@ -595,11 +591,7 @@ def run_ours(args):
             for r, e_, q_, a_ in zip(runs, hE, hQ, hA):
                 r.observables(0, 1, out=(e_, q_, a_))
         barrier()
-        te = time.perf_counter() - t0
-        tt = torch.tensor([te], device="cuda")
-        if dist is not None:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        te = float(tt.item())
+        te = replicas.max_over_ranks(time.perf_counter() - t0, dist, device="cuda")
         h2d = sum(x.numel() * x.element_size() for x in hJ + hS)
         d2h = sum(x.numel() * x.element_size() for x in hE + hQ + hA)
         e2e = {"value": world * INSTANCES * CHAINS * R * K * args.e2e_steps / te, "unit": UNIT,
