@@ -501,7 +501,9 @@ def run_ours(args):
     runs = [sk.Run(inst, chains=CHAINS, K=K, beta=BETA, seed=1 + rank, stream_id=i,
                    record_every=R, max_records=cap) for i, inst in enumerate(insts)]
     batch = sk.Batch(runs, warps_per_cta=args.warps_per_cta)
-    if not args.warps_per_cta:
+    if args.lanes or args.staging:
+        batch.set_layout(args.lanes, args.staging)
+    elif not args.warps_per_cta:
         batch.autotune(trial_steps=10)  # launch geometry only; the chains are untouched
     info = batch.info()
     info["classes"] = batch.classes()
@@ -652,7 +654,10 @@ def main():
                     help="smaller cases for profiling only; the bench line uses the default")
     ap.add_argument("--chains", type=int, default=CHAINS)
     ap.add_argument("--warps-per-cta", type=int, default=0,
-                    help="chains (warps) per CTA; 0 = the library's choice")
+                    help="warps per CTA (no autotuning); 0 = autotuned")
+    ap.add_argument("--lanes", type=int, default=0, help="lanes per chain (no autotuning)")
+    ap.add_argument("--staging", type=int, default=0,
+                    help="1 TMA-staged rows, 2 rows through L1 (no autotuning)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
