@@ -110,6 +110,18 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 struct Args {
     void* h;                        // maintained fields [chains][npad]: int32 (+-J) or float
     const int8_t* s;                // spins [chains][npad]
@@ -198,74 +210,78 @@ __global__ void __launch_bounds__(128, 1)
     }
     __syncwarp();
 
-    // epilogue: thread t owns accumulator row t (chain m0 + t)
+    // epilogue.  Warp w reads accumulator rows 32w..32w+31 (chains m0 + 32w + r)
+    // 32 columns at a time (thread = row), transposes the 32 x 32 block through
+    // shared memory (the pipeline buffers are free now) and walks it row by row
+    // with lane = column, so that every access to the fields and spins in
+    // global memory is one contiguous 128-byte row segment.  Per-row sums are
+    // kept per lane and reduced once at the end.
     const bool ok = wait_bounded(saddr(&accum), 0u);
     if (!ok && (tid & 31) == 0) atomicExch(args.err, kDevTimeout);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t c = m0 + tid;
-    const bool row_ok = c < args.chains && ok && !dead;
+    const bool tile_ok = ok && !dead;
+    const uint32_t lane = tid & 31;
+    float* T = reinterpret_cast<float*>(smem) + warp * (32 * 33);  // [32 columns][33] per warp
     const uint32_t taddr = tmem + ((warp * 32u) << 16);
-    // per-element differences in exact integer (+-J) or float arithmetic; the
-    // per-chain sums are combined across tiles in double precision
-    int imax = 0, isum = 0;
-    float fmaxd = 0.0f, fsum = 0.0f;
+    const uint32_t row0 = m0 + warp * 32u;
+    float psum[32];   // per row r: this lane's part of sum_n s_n (h_n - H_n)
+    float pmax = 0.0f;
+    int imax = 0, isum[32];
     unsigned long long mism = 0;
-    for (uint32_t col = 0; col < BN; col += 16) {
-        uint32_t v[16];
-        tmem_ld16(taddr + col, v);
-        const uint32_t nb = n0 + col;
-        if (!row_ok || nb >= args.npad) continue;  // npad is a multiple of 32: all 16 columns valid
-        const size_t base = static_cast<size_t>(c) * args.npad + nb;
-        if (args.mode == 2) {
-            float4* o = reinterpret_cast<float4*>(args.out + base);
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                o[q] = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
-                                   __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
-            continue;
-        }
-        const int4 sw = *reinterpret_cast<const int4*>(args.s + base);
-        const int sv[4] = {sw.x, sw.y, sw.z, sw.w};
-        if (args.pm1) {
-            const int4* hp = reinterpret_cast<const int4*>(static_cast<const int*>(args.h) + base);
+    for (int r = 0; r < 32; ++r) {
+        psum[r] = 0.0f;
+        isum[r] = 0;
+    }
+    for (uint32_t col = 0; col < BN; col += 32) {
+        uint32_t v[32];
+        tmem_ld32(taddr + col, v);
+        __syncwarp();
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int4 hv = hp[q];
-                const int hh[4] = {hv.x, hv.y, hv.z, hv.w};
+        for (int j = 0; j < 32; ++j) T[j * 33 + lane] = __uint_as_float(v[j]);  // T[column][row]
+        __syncwarp();
+        const uint32_t n = n0 + col + lane;
+        const bool col_ok = tile_ok && n0 + col < args.npad;  // npad is a multiple of 32
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int d = hh[e] - __float2int_rn(__uint_as_float(v[4 * q + e]));
-                    mism += d != 0;
-                    imax = max(imax, abs(d));
-                    const int sb = static_cast<int>(static_cast<int32_t>(static_cast<uint32_t>(sv[q]) << (24 - 8 * e)) >> 24);
-                    isum += sb * d;
-                }
+        for (int r = 0; r < 32; ++r) {
+            const uint32_t c = row0 + r;
+            if (!col_ok || c >= args.chains) continue;
+            const float H = T[lane * 33 + r];
+            const size_t idx = static_cast<size_t>(c) * args.npad + n;
+            if (args.mode == 2) {
+                args.out[idx] = H;
+                continue;
             }
-        } else {
-            float4* hp = reinterpret_cast<float4*>(static_cast<float*>(args.h) + base);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float4 hv = hp[q];
-                const float hh[4] = {hv.x, hv.y, hv.z, hv.w};
-                float Hn[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    Hn[e] = __uint_as_float(v[4 * q + e]);
-                    const float d = hh[e] - Hn[e];
-                    fmaxd = fmaxf(fmaxd, fabsf(d));
-                    const int sb = static_cast<int>(static_cast<int32_t>(static_cast<uint32_t>(sv[q]) << (24 - 8 * e)) >> 24);
-                    fsum = fmaf(static_cast<float>(sb), d, fsum);
-                }
-                if (args.mode == 1) hp[q] = make_float4(Hn[0], Hn[1], Hn[2], Hn[3]);
+            const int sv = args.s[idx];
+            if (args.pm1) {
+                const int d = static_cast<const int*>(args.h)[idx] - __float2int_rn(H);
+                mism += d != 0;
+                imax = max(imax, abs(d));
+                isum[r] += sv * d;
+            } else {
+                float* hp = static_cast<float*>(args.h) + idx;
+                const float d = *hp - H;
+                pmax = fmaxf(pmax, fabsf(d));
+                psum[r] = fmaf(static_cast<float>(sv), d, psum[r]);
+                if (args.mode == 1) *hp = H;
             }
         }
     }
-    if (row_ok && args.mode != 2) {
-        const double dmax = args.pm1 ? static_cast<double>(imax) : static_cast<double>(fmaxd);
-        const double dsum = args.pm1 ? static_cast<double>(isum) : static_cast<double>(fsum);
+    if (tile_ok && args.mode != 2) {
+        // row sums: lane l holds row r's part for columns l (mod 32); transpose
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < 32; ++r) T[r * 33 + lane] = args.pm1 ? static_cast<float>(isum[r]) : psum[r];
+        __syncwarp();
+        const uint32_t c = row0 + lane;
+        if (c < args.chains) {
+            double rs = 0.0;
+            for (int l = 0; l < 32; ++l) rs += static_cast<double>(T[lane * 33 + l]);
+            atomicAdd(&args.dE[c], rs);
+        }
+        const double dmax = args.pm1 ? static_cast<double>(imax) : static_cast<double>(pmax);
         atomicMax(&args.stats[0], static_cast<unsigned long long>(__double_as_longlong(dmax)));
         if (mism) atomicAdd(&args.stats[1], mism);
-        atomicAdd(&args.dE[c], dsum);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();

@@ -273,19 +273,20 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
     bc.valid = false;
     uint32_t site[4 * NB];
 
-    // prologue: the first step's row
-    uint32_t first;
-    if constexpr (RULE == 0) {
-        draw_sites<NB, G>(site, t0, chain, c3, k0, k1, nblk, N, g);
-        first = gshfl(g, site[0], 0);
-    } else {
-        first = __umulhi(block0<G>(bc, t0, chain, c3, k0, k1, g).x, N);
+    // prologue (staged rows): draw the first step and stage its row
+    if constexpr (STAGE) {
+        uint32_t first;
+        if constexpr (RULE == 0) {
+            draw_sites<NB, G>(site, t0, chain, c3, k0, k1, nblk, N, g);
+            first = gshfl(g, site[0], 0);
+        } else {
+            first = __umulhi(block0<G>(bc, t0, chain, c3, k0, k1, g).x, N);
+        }
+        if (g.gl == 0 && !dead) {
+            dev::fence_proxy_async();
+            dev::bulk_load(cm.row[t0 & 1u], Jg + static_cast<size_t>(first) * npad, rowbytes, &cm.bar[t0 & 1u]);
+        }
     }
-    if (STAGE && g.gl == 0 && !dead) {
-        dev::fence_proxy_async();
-        dev::bulk_load(cm.row[t0 & 1u], Jg + static_cast<size_t>(first) * npad, rowbytes, &cm.bar[t0 & 1u]);
-    }
-    (void)first;
     (void)rowbytes;
 
     for (uint32_t t = t0; t < t1; ++t) {
@@ -298,9 +299,11 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
         uint32_t x1 = 0, x2 = 0;
         bool x1_staged = false;
 
-        // stage the row the next step needs first
+        // direct rows: this step's sites now; staged rows: the next step's
+        // sites and the TMA of its first row, one step ahead
+        if constexpr (!STAGE && RULE == 0) draw_sites<NB, G>(site, t, chain, c3, k0, k1, nblk, N, g);
         uint32_t nsite[4 * NB];
-        if (t + 1u < t1) {
+        if (STAGE && t + 1u < t1) {
             uint32_t nx;
             if constexpr (RULE == 0) {
                 draw_sites<NB, G>(nsite, t + 1u, chain, c3, k0, k1, nblk, N, g);
@@ -497,7 +500,7 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
             if (t < trace_end && g.gl == 0) trace[t] = sel;
             __syncwarp(g.mask);
         }
-        if constexpr (RULE == 0) {
+        if constexpr (RULE == 0 && STAGE) {
 #pragma unroll
             for (int q = 0; q < 4 * NB; ++q) site[q] = nsite[q];
         }
