@@ -242,28 +242,42 @@ __global__ void __launch_bounds__(128, 1)
         __syncwarp();
         const uint32_t n = n0 + col + lane;
         const bool col_ok = tile_ok && n0 + col < args.npad;  // npad is a multiple of 32
+        if (args.mode == 2) {
+#pragma unroll
+            for (int r = 0; r < 32; ++r)
+                if (col_ok && row0 + r < args.chains)
+                    args.out[static_cast<size_t>(row0 + r) * args.npad + n] = T[lane * 33 + r];
+            continue;
+        }
+        // all 32 rows' loads first (each field is read once, then written once
+        // by this thread), then the arithmetic and the stores
+        uint32_t hv[32];
+        int sv[32];
 #pragma unroll
         for (int r = 0; r < 32; ++r) {
-            const uint32_t c = row0 + r;
-            if (!col_ok || c >= args.chains) continue;
-            const float H = T[lane * 33 + r];
-            const size_t idx = static_cast<size_t>(c) * args.npad + n;
-            if (args.mode == 2) {
-                args.out[idx] = H;
-                continue;
+            hv[r] = 0u;
+            sv[r] = 0;
+            if (col_ok && row0 + r < args.chains) {
+                const size_t idx = static_cast<size_t>(row0 + r) * args.npad + n;
+                hv[r] = __ldg(static_cast<const unsigned int*>(args.h) + idx);
+                sv[r] = __ldg(args.s + idx);
             }
-            const int sv = args.s[idx];
+        }
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+            if (!col_ok || row0 + r >= args.chains) continue;
+            const float H = T[lane * 33 + r];
             if (args.pm1) {
-                const int d = static_cast<const int*>(args.h)[idx] - __float2int_rn(H);
+                const int d = static_cast<int>(hv[r]) - __float2int_rn(H);
                 mism += d != 0;
                 imax = max(imax, abs(d));
-                isum[r] += sv * d;
+                isum[r] += sv[r] * d;
             } else {
-                float* hp = static_cast<float*>(args.h) + idx;
-                const float d = *hp - H;
+                const float d = __uint_as_float(hv[r]) - H;
                 pmax = fmaxf(pmax, fabsf(d));
-                psum[r] = fmaf(static_cast<float>(sv), d, psum[r]);
-                if (args.mode == 1) *hp = H;
+                psum[r] = fmaf(static_cast<float>(sv[r]), d, psum[r]);
+                if (args.mode == 1)
+                    static_cast<float*>(args.h)[static_cast<size_t>(row0 + r) * args.npad + n] = H;
             }
         }
     }
