@@ -19,8 +19,9 @@ from gpu_util import need_gpu
 
 pytestmark = pytest.mark.gpu
 
-# decision replay tolerance on u / P_K (fp32 weights and prefix sums, fp32
-# fields that drift by a few ulp per update); see DESIGN.md "Gaussian parity"
+# decision replay tolerance on u / P_K: fp32 fields drift by ~sqrt(f T) 2^-24 |h|
+# after T steps of f flips (~1e-5 at T = 3000), which moves dE by ~4x that and a
+# weight by beta x that (<= 1e-4 at beta = 2); the fp32 prefix sum adds (K+1) 2^-24
 REPLAY_TOL = 1e-4
 E_PER_SPIN_TOL = 1e-5
 
