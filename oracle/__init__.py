@@ -44,13 +44,19 @@ def lib():
         L.sko_run.argtypes = [i, i, vp, d, i, i, d, u64, u32, u32, u32, vp, u64, u32,
                               vp, vp, vp, vp, vp, vp, u32]
         L.sko_run.restype = i
+        L.sko_run_p.argtypes = L.sko_run.argtypes + [d]
+        L.sko_run_p.restype = i
         L.sko_replay.argtypes = [i, i, vp, d, i, i, d, u64, u32, u32, vp, u64, vp, d,
                                  vp, vp, vp, vp]
         L.sko_replay.restype = C.c_longlong
+        L.sko_replay_p.argtypes = L.sko_replay.argtypes + [d]
+        L.sko_replay_p.restype = C.c_longlong
         L.sko_boltzmann.argtypes = [i, i, vp, d, d, vp]
         L.sko_boltzmann.restype = i
         L.sko_transition_matrix.argtypes = [i, i, vp, d, i, i, d, i, i, vp]
         L.sko_transition_matrix.restype = i
+        L.sko_transition_matrix_p.argtypes = [i, i, vp, d, i, i, d, i, i, d, vp]
+        L.sko_transition_matrix_p.restype = i
         _lib = L
     return _lib
 
@@ -105,8 +111,9 @@ def weight_table(beta_eff: float, dmax: int) -> np.ndarray:
 
 def run(J, *, rule=MCMCMC, K=8, beta=1.0, scale=1.0, seed=1, stream=0, chain0=0,
         chains=1, init=None, steps=100, record_every=0, trace=False, resync_every=0,
-        want_q=True):
-    """Runs chains chain0..chain0+chains-1 for `steps` steps (see sko_run)."""
+        want_q=True, p_center=0.0):
+    """Runs chains chain0..chain0+chains-1 for `steps` steps (see sko_run_p;
+    p_center = 0 is the uniform root)."""
     J = np.ascontiguousarray(J)
     N = J.shape[0]
     nrec = steps // record_every if record_every else 0
@@ -117,16 +124,16 @@ def run(J, *, rule=MCMCMC, K=8, beta=1.0, scale=1.0, seed=1, stream=0, chain0=0,
     finE = np.zeros(chains)
     tr = np.zeros((chains, steps), dtype=np.int32) if trace else None
     init_a = None if init is None else np.ascontiguousarray(init, dtype=np.int8).reshape(chains, N)
-    rc = lib().sko_run(N, _kind_of(J), _ptr(J), scale, rule, K, beta, seed, stream, chain0,
-                       chains, _ptr(init_a), steps, record_every, _ptr(E), _ptr(acc), _ptr(q),
-                       _ptr(fin), _ptr(finE), _ptr(tr), resync_every)
+    rc = lib().sko_run_p(N, _kind_of(J), _ptr(J), scale, rule, K, beta, seed, stream, chain0,
+                         chains, _ptr(init_a), steps, record_every, _ptr(E), _ptr(acc), _ptr(q),
+                         _ptr(fin), _ptr(finE), _ptr(tr), resync_every, float(p_center))
     if rc != 0:
         raise RuntimeError(f"sko_run failed with {rc}")
     return dict(E=E, acc=acc, q=q, spins=fin, final_E=finE, trace=tr)
 
 
 def replay(J, slots, *, rule=MCMCMC, K=8, beta=1.0, scale=1.0, seed=1, stream=0, chain=0,
-           init=None, tol=1e-4):
+           init=None, tol=1e-4, p_center=0.0):
     """Follows a slot sequence chosen elsewhere and counts inadmissible steps
     (see sko_replay)."""
     J = np.ascontiguousarray(J)
@@ -137,9 +144,9 @@ def replay(J, slots, *, rule=MCMCMC, K=8, beta=1.0, scale=1.0, seed=1, stream=0,
     fin = np.zeros(N, dtype=np.int8)
     finE = C.c_double(0.0)
     init_a = None if init is None else np.ascontiguousarray(init, dtype=np.int8)
-    bad = lib().sko_replay(N, _kind_of(J), _ptr(J), scale, rule, K, beta, seed, stream, chain,
-                           _ptr(init_a), len(sl), _ptr(sl), tol, C.byref(dis), C.byref(first),
-                           _ptr(fin), C.byref(finE))
+    bad = lib().sko_replay_p(N, _kind_of(J), _ptr(J), scale, rule, K, beta, seed, stream, chain,
+                             _ptr(init_a), len(sl), _ptr(sl), tol, C.byref(dis), C.byref(first),
+                             _ptr(fin), C.byref(finE), float(p_center))
     if bad < 0:
         raise RuntimeError(f"sko_replay failed with {bad}")
     return dict(bad=int(bad), disagree=int(dis.value), first_bad=int(first.value),
@@ -157,13 +164,16 @@ def boltzmann(J, beta, scale=1.0) -> np.ndarray:
 
 
 def transition_matrix(J, *, rule=MCMCMC, K=2, beta=1.0, scale=1.0, root_mode=0,
-                      weight_mode=0) -> np.ndarray:
-    """Exact one-step transition matrix by enumeration (small N, K <= 8)."""
+                      weight_mode=0, p_center=0.0) -> np.ndarray:
+    """Exact one-step transition matrix by enumeration (small N, K <= 8);
+    root_mode 0 the method (uniform root, or the centre with probability
+    p_center and root-weighted slots), 1 always the centre, 2 the centre with
+    probability p_center but no root weights (see sko_transition_matrix_p)."""
     J = np.ascontiguousarray(J)
     N = J.shape[0]
     P = np.zeros((1 << N, 1 << N))
-    rc = lib().sko_transition_matrix(N, _kind_of(J), _ptr(J), scale, rule, K, beta, root_mode,
-                                     weight_mode, _ptr(P))
+    rc = lib().sko_transition_matrix_p(N, _kind_of(J), _ptr(J), scale, rule, K, beta, root_mode,
+                                       weight_mode, float(p_center), _ptr(P))
     if rc != 0:
         raise ValueError(f"transition_matrix failed with {rc}")
     return P

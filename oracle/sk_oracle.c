@@ -36,6 +36,12 @@
  *    All slots are labelled, so a configuration present in m slots is
  *    chosen with m times its weight.
  *
+ *  - Root distribution.  App. B.2 leaves the root probabilities p_r free.
+ *    With the centre drawn as the root with probability p_c and each leaf
+ *    with p_l = (1 - p_c)/K, P_gen(T|c in slot j) = p_{r(j)} N^-K, so the
+ *    node rule weights slot j by P_eq(c_j) p_{r(j)}: the centre slot by p_c,
+ *    every leaf slot by p_l.  p_c = 1/(K+1) is the uniform root above.
+ *
  *  - K = 1 of the same rule is the two-node heat-bath chain of Sec. III.A,
  *    Eq. (eq_node_two_conf).  The "standard local Metropolis" comparator of
  *    Sec. IV.B uses the acceptance min(1, P_eq(c1)/P_eq(c0)) of Sec. II.
@@ -182,6 +188,11 @@ typedef struct {
     int wlen;
     uint64_t* M;
     int mlen;
+    /* root distribution: p_center = 0 is the uniform root 1/(K+1) */
+    double p_center;
+    uint64_t root_thr;    /* non-uniform: the centre is the root iff U0 < root_thr */
+    double f_c, f_l;      /* slot weight factors p_c / max(p_c, p_l), p_l / max(..) */
+    uint64_t F_c, F_l;    /* the same as integers round(f 2^20) for the +-J tables */
 } sko_ctx;
 
 typedef struct {
@@ -232,21 +243,52 @@ static void star_candidates(const sko_ctx* c, const int8_t* s, const double* h,
 }
 
 /*
- * Slot selection with probability proportional to exp(-beta_eff dE_j).
- *   +-J: integer weights from the table, inclusive prefix P_j in slot order,
- *        u = floor(U * P_K / 2^64), the first j with P_j > u.
- *   Gaussian: the same in double precision with u = (U>>40) 2^-24 P_K.
+ * Weight of slot j, proportional to exp(-beta_eff dE_j) times the root
+ * factor of the slot (1 for the uniform root; the centre slot is slot 0 of
+ * a centre root and slot 1 of a leaf root).  m is the minimum of dE over the
+ * slots, a normalisation that cancels in the node probabilities.
+ *   +-J: W[(dE_j - m)/2] from the integer table (0 past its end), then
+ *        floor(W F / 2^20) with the slot's integer factor F when the root is
+ *        not uniform;
+ *   Gaussian: exp(-beta_eff (dE_j - m)) f in double precision.
  */
-static int select_slot(const sko_ctx* c, const double* dE, int nslot, uint64_t U) {
+static double min_dE(const double* dE, int nslot) {
     double m = dE[0];
     for (int j = 1; j < nslot; ++j) if (dE[j] < m) m = dE[j];
+    return m;
+}
+
+static int is_centre_slot(int j, int leaf_root) { return j == (leaf_root ? 1 : 0); }
+
+static uint64_t weight_int(const sko_ctx* c, double dEj, double m, int centre) {
+    long long d = (long long)llround((dEj - m) * 0.5);
+    uint64_t w = (d < c->wlen) ? c->W[d] : 0u;
+    if (c->p_center > 0.0) {
+        uint64_t F = centre ? c->F_c : c->F_l;
+        w = (uint64_t)(((unsigned __int128)w * (unsigned __int128)F) >> 20);
+    }
+    return w;
+}
+
+static double weight_dbl(const sko_ctx* c, double dEj, double m, int centre) {
+    double w = exp(-c->beta * c->scale * (dEj - m));
+    if (c->p_center > 0.0) w *= centre ? c->f_c : c->f_l;
+    return w;
+}
+
+/*
+ * Slot selection with probability proportional to the slot weights above.
+ *   +-J: inclusive integer prefix P_j in slot order, u = floor(U * P_K /
+ *        2^64), the first j with P_j > u.
+ *   Gaussian: the same in double precision with u = (U>>40) 2^-24 P_K.
+ */
+static int select_slot(const sko_ctx* c, const double* dE, int nslot, int leaf_root, uint64_t U) {
+    const double m = min_dE(dE, nslot);
     if (c->kind == SKO_PM1) {
         uint64_t P[SKO_MAXSLOT_GUARD];
         uint64_t acc = 0;
         for (int j = 0; j < nslot; ++j) {
-            long long d = (long long)llround((dE[j] - m) * 0.5);
-            uint64_t w = (d < c->wlen) ? c->W[d] : 0u;
-            acc += w;
+            acc += weight_int(c, dE[j], m, is_centre_slot(j, leaf_root));
             P[j] = acc;
         }
         uint64_t u = range64(U, acc);
@@ -256,16 +298,15 @@ static int select_slot(const sko_ctx* c, const double* dE, int nslot, uint64_t U
     } else {
         double P[SKO_MAXSLOT_GUARD];
         double acc = 0.0;
-        const double be = c->beta * c->scale;
         for (int j = 0; j < nslot; ++j) {
-            acc += exp(-be * (dE[j] - m));
+            acc += weight_dbl(c, dE[j], m, is_centre_slot(j, leaf_root));
             P[j] = acc;
         }
         double u = (double)(U >> 40) * ldexp(1.0, -24) * acc;
         for (int j = 0; j < nslot; ++j)
             if (P[j] > u) return j;
         for (int j = nslot - 1; j >= 0; --j)
-            if (exp(-be * (dE[j] - m)) > 0.0) return j;
+            if (weight_dbl(c, dE[j], m, is_centre_slot(j, leaf_root)) > 0.0) return j;
         return 0;
     }
 }
@@ -319,7 +360,10 @@ static int chain_step(const sko_ctx* c, uint32_t chain, uint64_t t, int8_t* s, d
     }
 
     const int K = c->K;
-    int leaf_root = range64(U0, (uint64_t)K + 1u) != 0u;
+    /* root: slot drawn uniformly from K+1 (leaf iff the draw is not 0), or
+       the centre with probability p_center */
+    int leaf_root = (c->p_center > 0.0) ? (U0 >= c->root_thr)
+                                        : (range64(U0, (uint64_t)K + 1u) != 0u);
     uint32_t sites[SKO_MAXSLOT_GUARD] = {0};
     for (int d = 1; d <= K; ++d) {
         uint32_t wb[4];
@@ -330,22 +374,16 @@ static int chain_step(const sko_ctx* c, uint32_t chain, uint64_t t, int8_t* s, d
     int flips[SKO_MAXSLOT_GUARD][2];
     int nflip[SKO_MAXSLOT_GUARD];
     star_candidates(c, s, h, leaf_root, sites, dE, flips, nflip);
-    int j = select_slot(c, dE, K + 1, U1);
+    int j = select_slot(c, dE, K + 1, leaf_root, U1);
     if (own) *own = j;
     if (Pout || uout) {
         /* prefix sums in the same order as select_slot, for the replay check */
-        double m = dE[0];
-        for (int q = 1; q <= K; ++q) if (dE[q] < m) m = dE[q];
+        const double m = min_dE(dE, K + 1);
         double acc = 0.0;
         for (int q = 0; q <= K; ++q) {
-            double w;
-            if (c->kind == SKO_PM1) {
-                long long d = llround((dE[q] - m) * 0.5);
-                w = (d < c->wlen) ? (double)c->W[d] : 0.0;
-            } else {
-                w = exp(-c->beta * c->scale * (dE[q] - m));
-            }
-            acc += w;
+            const int centre = is_centre_slot(q, leaf_root);
+            acc += (c->kind == SKO_PM1) ? (double)weight_int(c, dE[q], m, centre)
+                                        : weight_dbl(c, dE[q], m, centre);
             if (Pout) Pout[q] = acc;
         }
         if (uout) *uout = (c->kind == SKO_PM1) ? ldexp((double)U1, -64) * acc
@@ -356,8 +394,39 @@ static int chain_step(const sko_ctx* c, uint32_t chain, uint64_t t, int8_t* s, d
     return nflip[j] > 0;
 }
 
+/*
+ * Root distribution (App. B.2, p_r free): p_center = 0 selects the uniform
+ * root; 0 < p_center < 1 asks for the centre as the root with probability
+ * p_center and every leaf with p_l = (1 - p_center)/K.  The slot factors are
+ * the root probabilities over the larger of the two, kept as 20-bit integers
+ * F = round(f 2^20) (one of them 2^20; both must be >= 1, else -1), and the
+ * root probabilities actually used are the ones these integers fix exactly,
+ * p~_c = F_c / (F_c + K F_l) and p~_l = F_l / (F_c + K F_l), so that the
+ * factors stay proportional to the root probabilities (the condition for
+ * detailed balance).  The root is the centre iff U0 < floor(p~_c 2^64).
+ * The Gaussian weights take f = F / 2^20.  Metropolis ignores p_center.
+ */
+static int root_setup(sko_ctx* c, double p_center) {
+    c->p_center = 0.0;
+    c->f_c = c->f_l = 1.0;
+    c->F_c = c->F_l = (uint64_t)1 << 20;
+    c->root_thr = 0;
+    if (c->rule != SKO_MCMCMC || p_center == 0.0) return 0;
+    if (!(p_center > 0.0 && p_center < 1.0)) return -1;
+    const double pl = (1.0 - p_center) / (double)c->K;
+    const double pm = p_center > pl ? p_center : pl;
+    c->F_c = (uint64_t)(p_center / pm * 1048576.0 + 0.5);
+    c->F_l = (uint64_t)(pl / pm * 1048576.0 + 0.5);
+    if (c->F_c < 1u || c->F_l < 1u) return -1;
+    c->f_c = ldexp((double)c->F_c, -20);
+    c->f_l = ldexp((double)c->F_l, -20);
+    c->p_center = (double)c->F_c / ((double)c->F_c + (double)c->K * (double)c->F_l);
+    c->root_thr = (uint64_t)ldexp(c->p_center, 64);
+    return 0;
+}
+
 static int ctx_init(sko_ctx* c, int N, int kind, const void* J, double scale, int rule, int K,
-                    double beta, uint64_t seed, uint32_t stream) {
+                    double beta, uint64_t seed, uint32_t stream, double p_center) {
     if (N < 2 || N > 65536 || !J) return -1;
     if (kind != SKO_PM1 && kind != SKO_GAUSS) return -1;
     if (rule != SKO_MCMCMC && rule != SKO_METROPOLIS) return -1;
@@ -366,6 +435,7 @@ static int ctx_init(sko_ctx* c, int N, int kind, const void* J, double scale, in
     memset(c, 0, sizeof(*c));
     c->N = N; c->kind = kind; c->J = J; c->scale = scale; c->rule = rule; c->K = K;
     c->beta = beta; c->seed = seed; c->stream = stream;
+    if (root_setup(c, p_center)) return -1;
     if (kind == SKO_PM1) {
         int dmax = 4 * N + 4;
         c->W = (uint64_t*)calloc((size_t)dmax + 1, sizeof(uint64_t));
@@ -396,13 +466,14 @@ static void ctx_free(sko_ctx* c) {
  *   checks them against the maintained ones (exact for +-J, 1e-9 Gaussian).
  * Returns 0, -1 on a bad argument, -2 out of memory, -3 on a field mismatch.
  */
-int sko_run(int N, int kind, const void* J, double scale, int rule, int K, double beta,
-            uint64_t seed, uint32_t stream, uint32_t chain0, uint32_t nchains,
-            const int8_t* init_spins, uint64_t nsteps, uint32_t record_every,
-            double* rec_E, uint32_t* rec_acc, double* rec_q,
-            int8_t* final_spins, double* final_E, int32_t* trace, uint32_t resync_every) {
+int sko_run_p(int N, int kind, const void* J, double scale, int rule, int K, double beta,
+              uint64_t seed, uint32_t stream, uint32_t chain0, uint32_t nchains,
+              const int8_t* init_spins, uint64_t nsteps, uint32_t record_every,
+              double* rec_E, uint32_t* rec_acc, double* rec_q,
+              int8_t* final_spins, double* final_E, int32_t* trace, uint32_t resync_every,
+              double p_center) {
     sko_ctx c;
-    int rc = ctx_init(&c, N, kind, J, scale, rule, K, beta, seed, stream);
+    int rc = ctx_init(&c, N, kind, J, scale, rule, K, beta, seed, stream, p_center);
     if (rc) return rc;
     if (rec_q && (chain0 % 2u) != 0u) { ctx_free(&c); return -1; }
     uint64_t nrec = record_every ? nsteps / record_every : 0;
@@ -457,6 +528,17 @@ done:
     return rc;
 }
 
+/* sko_run_p with the uniform root. */
+int sko_run(int N, int kind, const void* J, double scale, int rule, int K, double beta,
+            uint64_t seed, uint32_t stream, uint32_t chain0, uint32_t nchains,
+            const int8_t* init_spins, uint64_t nsteps, uint32_t record_every,
+            double* rec_E, uint32_t* rec_acc, double* rec_q,
+            int8_t* final_spins, double* final_E, int32_t* trace, uint32_t resync_every) {
+    return sko_run_p(N, kind, J, scale, rule, K, beta, seed, stream, chain0, nchains, init_spins,
+                     nsteps, record_every, rec_E, rec_acc, rec_q, final_spins, final_E, trace,
+                     resync_every, 0.0);
+}
+
 /*
  * Decision replay for one chain: walks the chain with the oracle's random
  * numbers but follows the slot sequence `slots` taken elsewhere (the GPU
@@ -467,13 +549,13 @@ done:
  * Returns the number of inadmissible steps (>= 0) or a negative error;
  * n_disagree counts all differing steps, first_bad the first inadmissible one.
  */
-long long sko_replay(int N, int kind, const void* J, double scale, int rule, int K, double beta,
-                     uint64_t seed, uint32_t stream, uint32_t chain, const int8_t* init_spins,
-                     uint64_t nsteps, const int32_t* slots, double tol,
-                     long long* n_disagree, long long* first_bad,
-                     int8_t* final_spins, double* final_E) {
+long long sko_replay_p(int N, int kind, const void* J, double scale, int rule, int K, double beta,
+                       uint64_t seed, uint32_t stream, uint32_t chain, const int8_t* init_spins,
+                       uint64_t nsteps, const int32_t* slots, double tol,
+                       long long* n_disagree, long long* first_bad,
+                       int8_t* final_spins, double* final_E, double p_center) {
     sko_ctx c;
-    int rc = ctx_init(&c, N, kind, J, scale, rule, K, beta, seed, stream);
+    int rc = ctx_init(&c, N, kind, J, scale, rule, K, beta, seed, stream, p_center);
     if (rc) return rc;
     int8_t* s = (int8_t*)malloc((size_t)N);
     double* h = (double*)malloc(sizeof(double) * (size_t)N);
@@ -513,6 +595,16 @@ long long sko_replay(int N, int kind, const void* J, double scale, int rule, int
     return bad;
 }
 
+/* sko_replay_p with the uniform root. */
+long long sko_replay(int N, int kind, const void* J, double scale, int rule, int K, double beta,
+                     uint64_t seed, uint32_t stream, uint32_t chain, const int8_t* init_spins,
+                     uint64_t nsteps, const int32_t* slots, double tol,
+                     long long* n_disagree, long long* first_bad,
+                     int8_t* final_spins, double* final_E) {
+    return sko_replay_p(N, kind, J, scale, rule, K, beta, seed, stream, chain, init_spins, nsteps,
+                        slots, tol, n_disagree, first_bad, final_spins, final_E, 0.0);
+}
+
 /* ------------------------------------------------------------------ */
 /* Exact enumeration (small N)                                         */
 /* ------------------------------------------------------------------ */
@@ -543,19 +635,31 @@ int sko_boltzmann(int N, int kind, const void* J, double scale, double beta, dou
 /*
  * Exact one-step transition matrix P[x*2^N + y] of the chain, by enumerating
  * the root choice and every K-tuple of sites (N^K tuples, each 1/N^K).
- *   root_mode 0: uniform root over the K+1 slots (the method);
+ *   root_mode 0: the method: uniform root over the K+1 slots, or (p_center
+ *                > 0) the centre with probability p_center and the slot
+ *                weights times the root probabilities;
  *   root_mode 1: the root always at the centre (an invalid variant, kept as a
- *                negative control for the detailed-balance test).
+ *                negative control for the detailed-balance test);
+ *   root_mode 2: the centre as root with probability p_center but the slot
+ *                weights left without the root factor (a second invalid
+ *                variant, the negative control for the root factors).
  *   weight_mode 0: weights exp(-beta dE) in double precision;
  *   weight_mode 1: the +-J integer tables used by the trajectories.
  */
-int sko_transition_matrix(int N, int kind, const void* J, double scale, int rule, int K,
-                          double beta, int root_mode, int weight_mode, double* P) {
+int sko_transition_matrix_p(int N, int kind, const void* J, double scale, int rule, int K,
+                            double beta, int root_mode, int weight_mode, double p_center,
+                            double* P) {
     if (N < 1 || N > 12) return -1;
     if (rule == SKO_MCMCMC && (K < 1 || K > 8)) return -1;
+    if (root_mode == 2 && !(p_center > 0.0)) return -1;
     sko_ctx c;
-    int rc = ctx_init(&c, N, kind, J, scale, rule, K < 1 ? 1 : K, beta, 0, 0);
+    int rc = ctx_init(&c, N, kind, J, scale, rule, K < 1 ? 1 : K, beta, 0, 0,
+                      root_mode == 1 ? 0.0 : p_center);
     if (rc) return rc;
+    const double pc = c.p_center > 0.0 ? c.p_center : 1.0 / (double)((K < 1 ? 1 : K) + 1);
+    if (root_mode == 2) {  /* drop the factors, keep the root probabilities */
+        c.p_center = 0.0;
+    }
     if (weight_mode == 1 && kind != SKO_PM1) { ctx_free(&c); return -1; }
     uint32_t n = 1u << N;
     memset(P, 0, sizeof(double) * (size_t)n * n);
@@ -584,23 +688,19 @@ int sko_transition_matrix(int N, int kind, const void* J, double scale, int rule
         for (int leaf = 0; leaf <= 1; ++leaf) {
             double proot;
             if (root_mode == 1) proot = leaf ? 0.0 : 1.0;
-            else proot = leaf ? (double)K / (double)(K + 1) : 1.0 / (double)(K + 1);
+            else proot = leaf ? 1.0 - pc : pc;
             if (proot == 0.0) continue;
             uint32_t sites[SKO_MAXSLOT_GUARD] = {0};
             for (long long tup = 0; tup < ntup; ++tup) {
                 double dE[SKO_MAXSLOT_GUARD], w[SKO_MAXSLOT_GUARD];
                 int flips[SKO_MAXSLOT_GUARD][2], nflip[SKO_MAXSLOT_GUARD];
                 star_candidates(&c, s, h, leaf, sites, dE, flips, nflip);
-                double m = dE[0];
-                for (int j = 1; j <= K; ++j) if (dE[j] < m) m = dE[j];
+                const double m = min_dE(dE, K + 1);
                 double tot = 0.0;
                 for (int j = 0; j <= K; ++j) {
-                    if (weight_mode == 1) {
-                        long long d = llround((dE[j] - m) * 0.5);
-                        w[j] = (d < c.wlen) ? (double)c.W[d] : 0.0;
-                    } else {
-                        w[j] = exp(-be * (dE[j] - m));
-                    }
+                    const int centre = is_centre_slot(j, leaf);
+                    w[j] = (weight_mode == 1) ? (double)weight_int(&c, dE[j], m, centre)
+                                              : weight_dbl(&c, dE[j], m, centre);
                     tot += w[j];
                 }
                 for (int j = 0; j <= K; ++j) {
@@ -618,4 +718,10 @@ int sko_transition_matrix(int N, int kind, const void* J, double scale, int rule
     }
     ctx_free(&c);
     return 0;
+}
+
+/* sko_transition_matrix_p with the uniform root (p_center = 0). */
+int sko_transition_matrix(int N, int kind, const void* J, double scale, int rule, int K,
+                          double beta, int root_mode, int weight_mode, double* P) {
+    return sko_transition_matrix_p(N, kind, J, scale, rule, K, beta, root_mode, weight_mode, 0.0, P);
 }

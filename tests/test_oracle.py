@@ -193,6 +193,86 @@ def test_centre_rooted_star_is_not_reversible():
     assert stat < 1e-13 and db < 1e-14
 
 
+@pytest.mark.parametrize("kind", ["pm1", "gauss"])
+@pytest.mark.parametrize("K,p_center", [(2, 0.05), (2, 0.9), (3, 0.3), (4, 0.5)])
+def test_nonuniform_root_detailed_balance(kind, K, p_center):
+    # App. B.2: any root distribution p_r with the node weights P_eq p_r(node)
+    # leaves P_eq invariant and the chain reversible
+    N = 5
+    J = _pm1(N, 13) if kind == "pm1" else _gauss(N, 14)
+    beta = 0.4 if kind == "pm1" else 0.8
+    pi = oracle.boltzmann(J, beta)
+    P = oracle.transition_matrix(J, K=K, beta=beta, p_center=p_center)
+    stat, db = _check_balance(P, pi, 1e-12)
+    assert stat < 1e-13 and db < 1e-14, (stat, db)
+    if kind == "pm1":  # the integer tables with the integer root factors
+        P = oracle.transition_matrix(J, K=K, beta=beta, weight_mode=1, p_center=p_center)
+        stat, db = _check_balance(P, pi, 1e-12)
+        assert stat < 1e-12 and db < 1e-12, (stat, db)
+    # negative control: the same root probabilities without the p_r factor
+    P = oracle.transition_matrix(J, K=K, beta=beta, root_mode=2, p_center=p_center)
+    stat, db = _check_balance(P, pi, 1e-12)
+    assert db > 1e-5, db
+
+
+@pytest.mark.parametrize("K,p_center", [(2, 0.2), (4, 0.5), (3, 0.25)])
+def test_nonuniform_root_beta_zero_closed_form(K, p_center):
+    # beta = 0: slot j is chosen with probability p_r(j) / sum_slots p_r.  With
+    # the centre as root (probability p_c): stay w.p. p_c, flip one of the K
+    # leaves' sites otherwise.  With a leaf as root (1 - p_c): stay at the root
+    # (p_l) or at a leaf whose site repeats a = site_1, flip a (the centre,
+    # p_c), or flip a and b != a (a leaf).  (These p_center are exact: the
+    # factor ratio p_c / p_l is a power of two.)
+    N = 5
+    P = oracle.transition_matrix(_gauss(N, 52), K=K, beta=0.0, p_center=p_center)
+    pc = p_center
+    pl = (1.0 - pc) / K
+    single = pc * (K * pl) / N + (1 - pc) * pc / N
+    double = (1 - pc) * ((K - 1) * pl) * 2.0 / N**2
+    stay = pc * pc + (1 - pc) * (pl + (K - 1) * pl / N)
+    for x in range(1 << N):
+        assert abs(P[x, x] - stay) < 1e-14
+        for i in range(N):
+            assert abs(P[x, x ^ (1 << i)] - single) < 1e-14
+            for j in range(i + 1, N):
+                assert abs(P[x, x ^ (1 << i) ^ (1 << j)] - double) < 1e-14
+
+
+def test_uniform_p_center_is_the_uniform_root():
+    # p_center = 1/(K+1) is the uniform root: same transition matrix, and the
+    # same trajectories (the root thresholds differ on ~2^-53 of the draws)
+    N, K = 6, 3
+    J = _pm1(N, 15)
+    P0 = oracle.transition_matrix(J, K=K, beta=0.5, weight_mode=1)
+    P1 = oracle.transition_matrix(J, K=K, beta=0.5, weight_mode=1, p_center=1.0 / (K + 1))
+    assert np.abs(P0 - P1).max() < 1e-15
+    Jb = _pm1(48, 16)
+    a = oracle.run(Jb, K=8, beta=0.7, seed=3, chains=4, steps=2000, trace=True)
+    b = oracle.run(Jb, K=8, beta=0.7, seed=3, chains=4, steps=2000, trace=True, p_center=1.0 / 9)
+    assert np.array_equal(a["trace"], b["trace"]) and np.array_equal(a["spins"], b["spins"])
+    with pytest.raises(RuntimeError):
+        oracle.run(Jb, K=8, beta=0.7, p_center=1.0)
+    with pytest.raises(RuntimeError):
+        oracle.run(Jb, K=8, beta=0.7, p_center=1e-9)  # leaf factor below 2^-20
+
+
+def test_nonuniform_root_one_step_sampler_matches_exact_row():
+    # the trajectory code's root threshold and factors sample the enumerated row
+    N, K, beta = 5, 3, 0.6
+    for kind, J in (("pm1", _pm1(N, 72)), ("gauss", _gauss(N, 73))):
+        wm = 1 if kind == "pm1" else 0
+        for p_center in (0.1, 0.7):
+            P = oracle.transition_matrix(J, K=K, beta=beta, weight_mode=wm, p_center=p_center)
+            x0 = 0b10110
+            s0 = np.array([(-1 if (x0 >> i) & 1 else 1) for i in range(N)], dtype=np.int8)
+            C = 30000
+            r = oracle.run(J, K=K, beta=beta, seed=11, chains=C, init=np.tile(s0, (C, 1)), steps=1,
+                           p_center=p_center)
+            ys = ((r["spins"] < 0).astype(np.int64) << np.arange(N)).sum(axis=1)
+            counts = np.bincount(ys, minlength=1 << N).astype(float)
+            assert _chi2_pvalue(counts, P[x0] * C) > 1e-3, (kind, p_center)
+
+
 def test_weight_table_shape():
     W = oracle.weight_table(1.0, 400)
     assert int(W[0]) == 1 << 52
