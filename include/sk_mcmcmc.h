@@ -122,6 +122,16 @@ typedef struct {
                             /*   every M-th step (0 = never): +-J check, Gaussian */
                             /*   resync (see mcmcmc_recompute)                  */
     uint32_t recompute_terms; /* bf16 terms of the Gaussian J split, 1..3 (0=3) */
+    double p_center;        /* root distribution of the star (App. B.2, p_r     */
+                            /*   free; MCMCMC only): 0 = uniform, 1/(K+1) each  */
+                            /*   slot; 0 < p_center < 1: the centre is the root */
+                            /*   with ~p_center, each leaf with (1-p_center)/K, */
+                            /*   and slot weights carry the root probability.  */
+                            /*   The ratio p_center / p_leaf is rounded to a    */
+                            /*   ratio of 20-bit integers F_c : F_l (the larger */
+                            /*   2^20) and the root drawn with F_c/(F_c+K F_l); */
+                            /*   both factors must round to >= 1 (else          */
+                            /*   SK_ERR_INVALID_ARG)                            */
 } sk_run_params;
 
 /*
@@ -370,6 +380,7 @@ typedef struct {
     uint32_t stream_id;
     uint64_t steps;           /* Monte Carlo steps of every chain, 1 .. 2^32-1      */
     const int8_t* init_spins; /* host chains*N (+-1) copied at submit, or NULL      */
+    double p_center;          /* root distribution, as in sk_run_params (0=uniform) */
 } sk_job;
 
 typedef struct {

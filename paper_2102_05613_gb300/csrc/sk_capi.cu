@@ -411,6 +411,12 @@ sk_status mcmcmc_create(sk_instance* in, const sk_run_params* p, sk_run** out) {
     if (p->stream_id > 0xFFFFFFu) return fail(SK_ERR_INVALID_ARG, "stream_id must fit 24 bits");
     if (p->trace_chains > p->chains) return fail(SK_ERR_INVALID_ARG, "trace_chains > chains");
     if (p->recompute_terms > 3) return fail(SK_ERR_INVALID_ARG, "recompute_terms must be 0..3");
+    if (p->rule == SK_RULE_MCMCMC) {
+        JobDev probe{};
+        if (!root_setup(probe, p->K, p->p_center))
+            return fail(SK_ERR_INVALID_ARG, "p_center = %g: need 0 (uniform) or 0 < p_center < 1 with both root "
+                        "factors >= 2^-21", p->p_center);
+    }
     sk_run* r = new sk_run();
     r->inst = in;
     r->p = *p;
@@ -474,6 +480,7 @@ sk_status mcmcmc_create(sk_instance* in, const sk_run_params* p, sk_run** out) {
     j.record_every = r->p.record_every;
     j.trace_chains = r->p.trace_chains;
     j.step_limit = 0xFFFFFFFFu;
+    root_setup(j, r->p.K, r->p.rule == SK_RULE_MCMCMC ? r->p.p_center : 0.0);
     s = init_state(r, p->init_spins, p->init_mem);
     if (s == SK_OK) {
         sk_run* one[1] = {r};
@@ -1107,6 +1114,29 @@ sk_status mcmcmc_batch_free(sk_batch* b) {
 namespace sk {
 // The run stops at `limit` steps in every later advance (used by the server).
 void set_step_limit(sk_run* r, uint32_t limit) { r->job.step_limit = limit; }
+
+bool root_setup(JobDev& j, uint32_t K, double p_center) {
+    j.fcen = j.fleaf = 1u << 20;
+    j.lcen = j.lleaf = 0.0f;
+    if (K < 1) K = 1;
+    if (p_center == 0.0) {  // uniform: centre iff U0 < ceil(2^64 / (K+1))
+        j.root_thr = UINT64_MAX / (static_cast<uint64_t>(K) + 1u) + 1u;
+        return true;
+    }
+    if (!(p_center > 0.0 && p_center < 1.0)) return false;
+    const double pl = (1.0 - p_center) / static_cast<double>(K);
+    const double pm = p_center > pl ? p_center : pl;
+    const uint64_t Fc = static_cast<uint64_t>(p_center / pm * 1048576.0 + 0.5);
+    const uint64_t Fl = static_cast<uint64_t>(pl / pm * 1048576.0 + 0.5);
+    if (Fc < 1u || Fl < 1u) return false;
+    const double pc = static_cast<double>(Fc) / (static_cast<double>(Fc) + static_cast<double>(K) * static_cast<double>(Fl));
+    j.root_thr = static_cast<uint64_t>(std::ldexp(pc, 64));
+    j.fcen = static_cast<uint32_t>(Fc);
+    j.fleaf = static_cast<uint32_t>(Fl);
+    j.lcen = static_cast<float>(std::log2(static_cast<double>(Fc)) - 20.0);
+    j.lleaf = static_cast<float>(std::log2(static_cast<double>(Fl)) - 20.0);
+    return true;
+}
 uint64_t host_step(const sk_run* r) { return r->step; }
 size_t run_footprint(uint32_t N, uint32_t kind, uint32_t chains, uint64_t records) {
     const size_t np = pad_n(N);

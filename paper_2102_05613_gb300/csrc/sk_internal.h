@@ -38,7 +38,12 @@ struct alignas(16) JobDev {
     uint32_t kind, rule, wlen, record_every;
     uint32_t trace_chains;
     uint32_t step_limit;    // the run stops at this step (0xFFFFFFFF: no limit)
-    uint32_t pad_[2];
+    // root of the star: a leaf iff U0 >= root_thr; slot weight factors of the
+    // centre and the leaves as 20-bit integers (+-J, 2^20 = 1) and as log2
+    // (Gaussian, 0 = 1); see root_setup
+    uint32_t fcen, fleaf;
+    uint64_t root_thr;
+    float lcen, lleaf;
 };
 static_assert(sizeof(JobDev) % 16 == 0, "JobDev is copied as 16-byte words");
 
@@ -99,6 +104,15 @@ void set_step_limit(sk_run* r, uint32_t limit);
 uint64_t host_step(const sk_run* r);
 size_t run_footprint(uint32_t N, uint32_t kind, uint32_t chains, uint64_t records);
 size_t instance_footprint(uint32_t N, uint32_t kind);
+
+// Root distribution of the MCMCMC star (sk_capi.cu): p_center = 0 is the
+// uniform root (root_thr = ceil(2^64/(K+1)), i.e. a leaf iff
+// floor(U0 (K+1) / 2^64) != 0, factors 1); 0 < p_center < 1 puts the centre at
+// the root with probability p~_c = F_c / (F_c + K F_l), where F = round(2^20
+// p_r / max(p_c, p_l)) and p_l = (1 - p_center)/K, and weights the centre
+// slot by F_c and the leaf slots by F_l.  Returns false for a p_center
+// outside (0, 1) or one whose smaller factor rounds to 0.
+bool root_setup(JobDev& j, uint32_t K, double p_center);
 
 // Sets the message sk_last_error() returns on this thread (sk_capi.cu).
 void set_error_message(const char* msg);

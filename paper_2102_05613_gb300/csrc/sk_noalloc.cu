@@ -192,6 +192,7 @@ extern "C" sk_status mcmcmc_run_noalloc(uint32_t N, uint32_t kind, const void* c
     job.rule = rule;
     job.wlen = wlen;
     job.step_limit = 0xFFFFFFFFu;  // no per-run step limit
+    sk::root_setup(job, K, 0.0);   // uniform root
     NA_CU(cudaMemcpyAsync(base + o_job, &job, sizeof job, cudaMemcpyHostToDevice, st));
 
     // work items: blocks of W chains, copied from a fixed stack buffer

@@ -149,6 +149,7 @@ sk_status admit(sk_server* s, Job& j) {
     p.beta = j.spec.beta;
     p.seed = j.spec.seed;
     p.stream_id = j.spec.stream_id;
+    p.p_center = j.spec.p_center;
     p.init_spins = j.init.empty() ? nullptr : j.init.data();
     p.init_mem = SK_MEM_HOST;
     r = mcmcmc_create(inst, &p, &j.run);
@@ -363,6 +364,10 @@ sk_status sk_server_submit(sk_server* s, const sk_job* job, uint64_t* ticket) {
         (job->rule != SK_RULE_MCMCMC && job->rule != SK_RULE_METROPOLIS) || !(job->beta >= 0.0) ||
         !(job->scale > 0.0) || job->stream_id > 0xFFFFFFu)
         return SK_ERR_INVALID_ARG;
+    if (job->rule == SK_RULE_MCMCMC) {
+        sk::JobDev probe{};
+        if (!sk::root_setup(probe, job->K, job->p_center)) return SK_ERR_INVALID_ARG;
+    }
     auto j = std::make_shared<Job>();
     j->spec = *job;
     if (j->spec.rule == SK_RULE_METROPOLIS) j->spec.K = 1;

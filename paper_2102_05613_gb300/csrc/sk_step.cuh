@@ -13,7 +13,9 @@
 // One Monte Carlo step (Sec. A.2, Eq. eq_det_balance_graph_solution, on the
 // star of App. B.2 with a uniform root, p_r = 1/(K+1)):
 //   a1  Philox4x32-10 draws, counter (block, step, chain, stream): block 0
-//       gives U0 (root: leaf iff floor(U0 (K+1) / 2^64) != 0) and U1 (node);
+//       gives U0 (root: a leaf iff U0 >= root_thr; for the uniform root
+//       root_thr = ceil(2^64/(K+1)), i.e. floor(U0 (K+1) / 2^64) != 0) and
+//       U1 (node);
 //       blocks 1..ceil(K/4) give site_d = floor(w N / 2^32), d = 1..K.
 //       Group lane l computes block 1+l (+32 when K > 128), so its slots are
 //       d = 4l+1..4l+4 (+128); block 0 is computed G steps at a time.
@@ -21,10 +23,11 @@
 //   a3  candidate energies: centre root dE_d = 2 s_i h_i (i = site_d);
 //       leaf root dE_1 = 2 s_a h_a, dE_d = 2 s_a h_a + 2 s_b h_b - 4 J_ab s_a s_b
 //       (b = site_d != a), 0 when b = a; slot 0 (the current state) is 0.
-//   a4  node choice with probability ~ exp(-beta dE): group min, weights
-//       (+-J: integer table W[(dE-min)/2] ~ 2^52 exp(-2 beta d); Gaussian:
-//       2^x), group inclusive scan in slot order, u = U1 * total, first
-//       slot whose prefix exceeds u.
+//   a4  node choice with probability ~ exp(-beta dE) p_r(slot): group min,
+//       weights (+-J: integer table W[(dE-min)/2] ~ 2^52 exp(-2 beta d), times
+//       F / 2^20 of the slot's root class when the root is not uniform;
+//       Gaussian: 2^(-beta log2(e) (dE-min) + log2 f)), group inclusive scan
+//       in slot order, u = U1 * total, first slot whose prefix exceeds u.
 //   a5  field update for the 0, 1 or 2 flipped spins x: h_k -= 2 s_x J_kx.
 //   a6  records every R steps: E = -scale/2 sum s h, accepted count, and the
 //       overlap q of chain pairs (2m, 2m+1), which share a CTA.
@@ -263,6 +266,8 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
     const W* __restrict__ Wt = reinterpret_cast<const W*>(jb.W);
     const uint32_t wlen = jb.wlen;
     const float nbl2 = -jb.beta_eff * 1.4426950408889634f;  // -beta log2(e)
+    const uint64_t root_thr = jb.root_thr;
+    const bool root_weighted = jb.fcen + jb.fleaf != (2u << 20);  // not both factors 1
     int32_t* trace = (write && chain < jb.trace_chains) ? jb.trace + static_cast<size_t>(chain) * jb.trace_steps
                                                         : nullptr;
     const uint32_t trace_end = trace ? static_cast<uint32_t>(jb.trace_steps) : 0u;
@@ -362,7 +367,7 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
             } else {
                 // ---- MCMCMC: K proposals on the uniform-root star ----
                 const unsigned long long U0 = (static_cast<unsigned long long>(b0.y) << 32) | b0.x;
-                const bool leaf = __umul64hi(U0, static_cast<unsigned long long>(K) + 1ull) != 0ull;
+                const bool leaf = U0 >= root_thr;
                 const uint32_t a = gshfl(g, site[0], 0);
                 const int sa = S[a];
                 const H dEa = static_cast<H>(2 * sa) * hf[a];
@@ -392,23 +397,28 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                 for (int q = 0; q < 4 * NB; ++q) {
                     const uint32_t d = 128u * (q >> 2) + 4u * g.gl + (q & 3) + 1u;
                     W x = 0;
+                    const bool centre = leaf && d == 1u;  // slot 1 of a leaf root
                     if (d <= K) {
                         if constexpr (sizeof(JT) == 1) {
                             const uint32_t idx = static_cast<uint32_t>(dE[q] - m) >> 1;
                             x = idx < wlen ? __ldg(&Wt[idx]) : 0ull;
+                            if (root_weighted)  // floor(x F / 2^20)
+                                x = __umul64hi(x << 11, static_cast<unsigned long long>(centre ? jb.fcen : jb.fleaf) << 33);
                         } else {
-                            x = dev::pow2(nbl2 * (dE[q] - m));
+                            x = dev::pow2(fmaf(nbl2, dE[q] - m, centre ? jb.lcen : jb.lleaf));
                         }
                     }
                     w[q] = x;
                     gsum_[q >> 2] += x;
                 }
-                W w0;
+                W w0;  // slot 0, the root: the centre of a centre root, else a leaf
                 if constexpr (sizeof(JT) == 1) {
                     const uint32_t idx0 = static_cast<uint32_t>(-m) >> 1;
                     w0 = idx0 < wlen ? __ldg(&Wt[idx0]) : 0ull;
+                    if (root_weighted)
+                        w0 = __umul64hi(w0 << 11, static_cast<unsigned long long>(leaf ? jb.fleaf : jb.fcen) << 33);
                 } else {
-                    w0 = dev::pow2(-nbl2 * m);
+                    w0 = dev::pow2(fmaf(-nbl2, m, leaf ? jb.lleaf : jb.lcen));
                 }
                 W incl[NB], tot[NB];
                 W total = w0;

@@ -48,7 +48,8 @@ class RunParams(C.Structure):
                 ("beta", C.c_double), ("seed", C.c_uint64), ("stream_id", C.c_uint32),
                 ("trace_chains", C.c_uint32), ("trace_steps", C.c_uint64),
                 ("init_spins", C.c_void_p), ("init_mem", C.c_uint32),
-                ("recompute_every", C.c_uint32), ("recompute_terms", C.c_uint32)]
+                ("recompute_every", C.c_uint32), ("recompute_terms", C.c_uint32),
+                ("p_center", C.c_double)]
 
 
 class RecomputeStats(C.Structure):
@@ -193,7 +194,7 @@ class Run:
     def __init__(self, inst: Instance, *, chains: int, K: int = 8, rule: int = SK_RULE_MCMCMC,
                  beta: float = 1.0, seed: int = 1, stream_id: int = 0, record_every: int = 0,
                  max_records: int = 0, init=None, trace_chains: int = 0, trace_steps: int = 0,
-                 recompute_every: int = 0, recompute_terms: int = 0):
+                 recompute_every: int = 0, recompute_terms: int = 0, p_center: float = 0.0):
         self.inst = inst
         self.chains, self.K, self.rule = int(chains), int(K), int(rule)
         self.record_every, self.max_records = int(record_every), int(max_records)
@@ -205,6 +206,7 @@ class Run:
         pr.beta, pr.seed, pr.stream_id = float(beta), int(seed), int(stream_id)
         pr.trace_chains, pr.trace_steps = self.trace_chains, self.trace_steps
         pr.recompute_every, pr.recompute_terms = int(recompute_every), int(recompute_terms)
+        pr.p_center = float(p_center)
         if init is not None:
             if isinstance(init, np.ndarray):
                 init = np.ascontiguousarray(init, dtype=np.int8)
@@ -380,7 +382,8 @@ class Job(C.Structure):
     _fields_ = [("N", C.c_uint32), ("kind", C.c_uint32), ("couplings", C.c_void_p),
                 ("couplings_id", C.c_uint64), ("scale", C.c_double), ("chains", C.c_uint32),
                 ("K", C.c_uint32), ("rule", C.c_uint32), ("beta", C.c_double), ("seed", C.c_uint64),
-                ("stream_id", C.c_uint32), ("steps", C.c_uint64), ("init_spins", C.c_void_p)]
+                ("stream_id", C.c_uint32), ("steps", C.c_uint64), ("init_spins", C.c_void_p),
+                ("p_center", C.c_double)]
 
 
 class JobStatus(C.Structure):
@@ -440,11 +443,11 @@ class Server:
                       "sk_server_add_couplings")
 
     def submit(self, *, N, kind, chains, steps, K=8, rule=SK_RULE_MCMCMC, beta=1.0, seed=1,
-               stream_id=0, J=None, couplings_id=0, scale=1.0, init=None) -> int:
+               stream_id=0, J=None, couplings_id=0, scale=1.0, init=None, p_center=0.0) -> int:
         j = Job()
         j.N, j.kind, j.chains, j.steps = int(N), int(kind), int(chains), int(steps)
         j.K, j.rule, j.beta, j.seed, j.stream_id = int(K), int(rule), float(beta), int(seed), int(stream_id)
-        j.couplings_id, j.scale = int(couplings_id), float(scale)
+        j.couplings_id, j.scale, j.p_center = int(couplings_id), float(scale), float(p_center)
         if J is not None:
             J = np.ascontiguousarray(J)
             j.couplings = J.ctypes.data_as(C.c_void_p).value

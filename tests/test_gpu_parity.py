@@ -27,12 +27,12 @@ E_PER_SPIN_TOL = 1e-5
 
 
 def _run_gpu(J, *, chains, K, beta, rule, steps, seed, R=0, init=None, trace=0, scale=1.0,
-             stream_id=0, splits=None):
+             stream_id=0, splits=None, p_center=0.0):
     inst = sk.Instance(J, scale=scale)
     nrec = steps // R if R else 0
     run = sk.Run(inst, chains=chains, K=K, rule=rule, beta=beta, seed=seed, stream_id=stream_id,
                  record_every=R, max_records=nrec, init=init, trace_chains=trace,
-                 trace_steps=steps if trace else 0)
+                 trace_steps=steps if trace else 0, p_center=p_center)
     for s in (splits or [steps]):
         run.advance(s)
     run.wait()
@@ -194,6 +194,64 @@ def test_gauss_statistics_within_3_sigma():
         zs.append(z)
     zs = np.concatenate(zs)
     assert np.mean(np.abs(zs) > 3) <= 0.1 and np.abs(zs).max() < 4.5, zs
+
+
+@pytest.mark.parametrize("N,K,chains,beta,p_center", [
+    (64, 8, 4, 1.0, 0.3),      # centre favoured over each leaf
+    (100, 33, 5, 0.5, 0.01),   # leaves favoured, ragged N and K
+    (96, 128, 2, 2.0, 0.5),    # every lane busy
+    (70, 200, 2, 0.7, 0.2),    # two Philox blocks per lane
+])
+def test_pm1_nonuniform_root_bit_exact(N, K, chains, beta, p_center):
+    """Non-uniform root of the star (App. B.2): root threshold and integer
+    slot factors give the oracle's trajectory exactly."""
+    need_gpu()
+    steps, R = 1500, 100
+    J = inputs.couplings_pm1(N, 3 * N + K)
+    init = inputs.initial_spins(chains, N, 9)
+    g = _run_gpu(J, chains=chains, K=K, beta=beta, rule=sk.SK_RULE_MCMCMC, steps=steps, seed=41,
+                 R=R, init=init, trace=chains, p_center=p_center)
+    o = oracle.run(J, K=K, beta=beta, seed=41, chains=chains, init=init, steps=steps,
+                   record_every=R, trace=True, p_center=p_center)
+    assert np.array_equal(g["trace"], o["trace"])
+    assert np.array_equal(g["E"], o["E"])
+    assert np.array_equal(g["acc"], o["acc"])
+    assert np.array_equal(g["spins"], o["spins"])
+    assert np.array_equal(g["fields"], _fields_exact(J, g["spins"]))
+
+
+@pytest.mark.parametrize("K,N,beta,p_center", [(16, 96, 1.0, 0.7), (128, 128, 1.5, 0.05)])
+def test_gauss_nonuniform_root_decision_replay(K, N, beta, p_center):
+    need_gpu()
+    steps, chains, R = 3000, 4, 300
+    J = inputs.couplings_gauss(N, 19)
+    init = inputs.initial_spins(chains, N, 20)
+    g = _run_gpu(J, chains=chains, K=K, beta=beta, rule=sk.SK_RULE_MCMCMC, steps=steps, seed=23,
+                 R=R, init=init, trace=chains, p_center=p_center)
+    for c in range(chains):
+        r = oracle.replay(J, g["trace"][c], K=K, beta=beta, seed=23, chain=c, init=init[c],
+                          tol=REPLAY_TOL, p_center=p_center)
+        assert r["bad"] == 0, (c, r)
+        assert r["disagree"] <= 3, (c, r)
+        assert np.array_equal(r["spins"], g["spins"][c])
+
+
+def test_uniform_p_center_equals_uniform_root_and_limits():
+    need_gpu()
+    N, K, chains, steps = 80, 12, 4, 2000
+    J = inputs.couplings_pm1(N, 4)
+    init = inputs.initial_spins(chains, N, 5)
+    a = _run_gpu(J, chains=chains, K=K, beta=0.6, rule=sk.SK_RULE_MCMCMC, steps=steps, seed=6,
+                 init=init, trace=chains)
+    b = _run_gpu(J, chains=chains, K=K, beta=0.6, rule=sk.SK_RULE_MCMCMC, steps=steps, seed=6,
+                 init=init, trace=chains, p_center=1.0 / (K + 1))
+    assert np.array_equal(a["trace"], b["trace"]) and np.array_equal(a["spins"], b["spins"])
+    inst = sk.Instance(J)
+    for bad in (1.0, -0.2, 1e-9, float("nan")):
+        with pytest.raises(sk.SKError) as e:
+            sk.Run(inst, chains=2, K=K, p_center=bad)
+        assert e.value.status == sk.SK_ERR_INVALID_ARG
+    inst.close()
 
 
 def test_energy_entry_point():

@@ -21,12 +21,13 @@ JOBS = [  # N, kind, chains, K, rule, beta, steps, seed
     (96, sk.SK_J_PM1, 1, 16, sk.SK_RULE_MCMCMC, 0.5, 2200, 5),
     (300, sk.SK_J_GAUSS, 7, 100, sk.SK_RULE_MCMCMC, 1.5, 900, 6),
 ]
+P_CENTER = {1: 0.1, 4: 0.4}  # jobs with a non-uniform root of the star
 
 
-def _alone(J, N, chains, K, rule, beta, steps, seed, stream_id, init):
+def _alone(J, N, chains, K, rule, beta, steps, seed, stream_id, init, p_center=0.0):
     inst = sk.Instance(J)
     run = sk.Run(inst, chains=chains, K=K, rule=rule, beta=beta, seed=seed, stream_id=stream_id,
-                 init=init)
+                 init=init, p_center=p_center)
     run.advance(steps)
     spins, _ = run.state()
     E = inst.energy(spins)
@@ -46,14 +47,15 @@ def test_results_in_the_mix_equal_results_alone():
         if i == 3:
             time.sleep(0.05)  # later arrivals join while the first jobs run
         tickets.append(srv.submit(N=N, kind=kind, chains=chains, steps=steps, K=K, rule=rule,
-                                  beta=beta, seed=seed, stream_id=i, J=J, init=init))
+                                  beta=beta, seed=seed, stream_id=i, J=J, init=init,
+                                  p_center=P_CENTER.get(i, 0.0)))
     srv.wait_all(timeout_ns=120 * 10**9)
     status = [srv.poll(t) for t in tickets]
     assert all(s["state"] == sk.SK_JOB_DONE for s in status), status
     for i, (t, (N, kind, chains, K, rule, beta, steps, seed)) in enumerate(zip(tickets, JOBS)):
         E, S, _ = srv.result(t, chains, N)
         J, init = data[i]
-        E0, S0 = _alone(J, N, chains, K, rule, beta, steps, seed, i, init)
+        E0, S0 = _alone(J, N, chains, K, rule, beta, steps, seed, i, init, P_CENTER.get(i, 0.0))
         assert np.array_equal(S, S0), i
         assert np.array_equal(E, E0), i
     st = srv.stats()
