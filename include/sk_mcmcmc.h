@@ -283,8 +283,13 @@ sk_status mcmcmc_batch_autotune(sk_batch* b, uint32_t trial_steps, uint32_t* war
 /*
  * mcmcmc_batch_set_layout: forces the layout of every launch class.
  *   lanes    lanes per chain, 4, 8, 16 or 32 (32/lanes chains share a warp),
- *            at least as many as a class's K needs; 0 = default (the fewest
- *            lanes K allows, whole warps for classes of at most 512 chains);
+ *            raised to the fewest a class's K allows (each lane draws up to
+ *            4 Philox blocks of 4 proposals: see below);
+ *            0 = default (one block of 4 proposals per lane, whole warps for
+ *            K > 128 and for classes of at most 512 chains).  Kernels exist
+ *            for 1 block per lane at every width, 2 blocks at 8, 16 and 32
+ *            lanes and 4 blocks at 8 and 16 lanes, so K <= 16 allows 4
+ *            lanes, K <= 128 8 lanes and K <= 256 16 lanes;
  *   staging  0 = default, 1 = the next step's row of J is staged in shared
  *            memory by TMA (two row buffers per chain), 2 = rows are read
  *            through L1 (no buffers, so more chains fit in shared memory).
@@ -299,9 +304,10 @@ sk_status mcmcmc_batch_info(const sk_batch* b, uint32_t* grid, uint32_t* warps_p
 
 /*
  * mcmcmc_batch_classes: the batch's launch classes.  Work items are grouped
- * by kernel class (coupling kind, rule, K > 128), by the fewest lanes per
- * chain K allows (one Philox block of 4 proposals per lane) and by
- * shared-memory size bucket (chains of similar N), one persistent launch per
+ * by coupling kind and rule, by the Philox blocks of proposals a step draws
+ * (ceil(K/4) rounded up to a power of two, so that one kernel shape serves
+ * every run of the class) and by shared-memory size bucket (chains of
+ * similar N), one persistent launch per
  * class, so small-N runs keep many chains per CTA next to large-N runs.
  * *count receives the number of classes; desc (6 x max uint32, may be NULL)
  * receives per class: kernel class, lanes per chain, shared bytes per chain,

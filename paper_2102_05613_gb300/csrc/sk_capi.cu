@@ -119,7 +119,7 @@ struct sk_batch {
     struct Class {
         uint64_t key;
         int cls;                 // kernel class incl. G and staging (step_class)
-        uint32_t G, gmin;        // lanes per chain, fewest allowed
+        uint32_t G, gmin, gdef;  // lanes per chain: chosen, fewest allowed, default
         uint32_t stage;          // row a staged by TMA (1) or read through L1 (0)
         uint32_t per_chain_staged, per_chain_direct;
         uint32_t per_chain;      // shared memory per chain
@@ -681,21 +681,30 @@ constexpr uint32_t kMaxClasses = 64;
 uint32_t run_per_chain(const sk_run* r, bool staged = true) {
     return static_cast<uint32_t>((sk::warp_smem_bytes(r->inst->Npad, r->inst->kind, staged) + 127) / 128 * 128);
 }
-// Fewest lanes per chain for a run: one Philox block (4 slots) per lane;
-// K > 128 takes two blocks per lane on a whole warp.
+// Fewest lanes per chain a kernel covers for the run's K (NB up to 4 Philox
+// blocks per lane), and the default: one block per lane (K <= 4 G), whole
+// warps for K > 128.
 uint32_t run_gmin(const sk_run* r) {
+    for (uint32_t g = 4; g < 32; g <<= 1)
+        if (sk::blocks_per_lane(r->p.rule, r->p.K, g)) return g;
+    return 32;
+}
+uint32_t run_gdefault(const sk_run* r) {
     if (r->p.rule != SK_RULE_MCMCMC) return 4;
     if (r->p.K > 128) return 32;
     uint32_t g = 4;
     while (4 * g < r->p.K) g <<= 1;
     return g;
 }
+// Runs share a launch class when their kernels agree for every G: same
+// coupling type, rule, Philox blocks of sites (as a power of two) and
+// shared-memory bucket.
 uint64_t class_key(const sk_run* r) {
     uint32_t b = 128;
     const uint32_t pc = run_per_chain(r);
     while (b < pc) b <<= 1;
-    const uint64_t kc = static_cast<uint64_t>(sk::step_class(r->inst->kind, r->p.rule, r->p.K, 32, 0)) & ~7ull;
-    return (kc << 40) | (static_cast<uint64_t>(run_gmin(r)) << 32) | b;
+    const uint64_t kb = sk::site_blocks_pow2(r->p.rule, r->p.K);
+    return (static_cast<uint64_t>(r->inst->kind) << 62) | (static_cast<uint64_t>(r->p.rule) << 61) | (kb << 32) | b;
 }
 // Most warps per CTA for G lanes per chain: chains of a pair share a CTA,
 // so with whole-warp chains W is even.
@@ -726,6 +735,7 @@ sk_status plan_batch(sk_batch* b) {
         c.key = g.first;
         const sk_run* r0 = b->runs[g.second[0]];
         c.gmin = run_gmin(r0);
+        c.gdef = run_gdefault(r0);
         uint64_t total = 0;
         for (uint32_t i : g.second) {
             c.per_chain_staged = std::max(c.per_chain_staged, run_per_chain(b->runs[i], true));
@@ -741,13 +751,14 @@ sk_status plan_batch(sk_batch* b) {
         } else {
             c.stage = b->S_override == 2 ? 0u : 1u;
             c.per_chain = c.stage ? c.per_chain_staged : c.per_chain_direct;
-            c.G = b->G_override ? std::max(b->G_override, c.gmin) : (total <= 512 ? 32u : c.gmin);
+            c.G = b->G_override ? std::max(b->G_override, c.gmin) : (total <= 512 ? 32u : c.gdef);
             const uint32_t fit = fit_warps(c.per_chain, c.G);
             c.W = b->W_override ? std::min(b->W_override, fit) : fit;
         }
         if (c.W < 1 || (c.G == 32 && c.W < 2))
             return fail(SK_ERR_INVALID_ARG, "N too large: %u bytes of shared memory per chain", c.per_chain);
-        c.cls = sk::step_class(r0->inst->kind, r0->p.rule, r0->p.K > 128 ? 256 : 1, c.G, c.stage);
+        c.cls = sk::step_class(r0->inst->kind, r0->p.rule, r0->p.K, c.G, c.stage);
+        if (c.cls < 0) return fail(SK_ERR_INVALID_ARG, "no step kernel for K = %u with %u lanes per chain", r0->p.K, c.G);
         int occ = sk::step_kernel_occupancy(c.cls, c.W, c.per_chain);
         while (occ <= 0 && t == b->tuned.end() && c.W > (c.G == 32 ? 2u : 1u)) {  // default choice: step down
             c.W -= c.G == 32 ? 2u : 1u;
@@ -1023,7 +1034,7 @@ sk_status mcmcmc_batch_autotune(sk_batch* b, uint32_t trial_steps, uint32_t* out
                 for (uint32_t G = cls0[k].gmin; G <= 32; G <<= 1) {
                     const uint32_t fit =
                         fit_warps(stage ? cls0[k].per_chain_staged : cls0[k].per_chain_direct, G);
-                    for (uint32_t w : {32u, 24u, 16u, 12u, 8u, 6u, 4u, 2u, 1u})
+                    for (uint32_t w : {32u, 24u, 20u, 16u, 12u, 8u, 6u, 4u, 2u, 1u})
                         if (w <= fit && (G < 32 || (w & 1u) == 0)) cand.push_back((stage << 16) | (G << 8) | w);
                 }
             for (uint32_t gw : cand) {

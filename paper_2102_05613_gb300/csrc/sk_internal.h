@@ -62,14 +62,17 @@ inline size_t warp_smem_bytes(uint32_t npad, uint32_t kind, bool staged = true) 
 
 // Kernel launchers (sk_kernels.cu).  All return cudaGetLastError().
 //
-// The step kernel is instantiated per class = step_class(kind, rule, K, G):
-// the coupling type, the rule, whether K needs two Philox blocks per lane
-// (K > 128, whole-warp chains only), whether row a is staged in shared
-// memory by TMA (stage) or read through L1, and the lanes per chain G (4, 8, 16, 32;
-// 32/G chains per warp).  A CTA holds W warps, i.e. W * 32/G chains, each
-// with `per_chain` bytes of shared memory.  launch_step runs the items of one
-// class; `bump` advances every job's step counter afterwards (set it on the
-// last class).
+// The step kernel is instantiated per class = step_class(kind, rule, K, G,
+// stage): the coupling type, the rule, whether row a is staged in shared
+// memory by TMA (stage) or read through L1, the lanes per chain G (4, 8, 16,
+// 32; 32/G chains per warp) and the Philox blocks of sites each lane draws,
+// NB = blocks_per_lane(rule, K, G) (1, 2 or 4: K up to 4 G NB).  step_class
+// returns -1 for a (K, G) no kernel covers.  A CTA holds W warps, i.e.
+// W * 32/G chains, each with `per_chain` bytes of shared memory.  launch_step
+// runs the items of one class; `bump` advances every job's step counter
+// afterwards (set it on the last class).
+uint32_t site_blocks_pow2(uint32_t rule, uint32_t K);
+uint32_t blocks_per_lane(uint32_t rule, uint32_t K, uint32_t G);
 int step_class(uint32_t kind, uint32_t rule, uint32_t K, uint32_t G, uint32_t stage);
 uint32_t class_lanes(int cls);
 bool class_staged(int cls);

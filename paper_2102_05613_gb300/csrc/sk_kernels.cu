@@ -148,20 +148,41 @@ __global__ void energy_kernel(const JT* __restrict__ J, uint32_t N, uint32_t npa
 
 }  // namespace
 
-// class = kind * 64 + rule * 32 + stage * 16 + (nb - 1) * 8 + log2(G)
+// Philox blocks of sites a step draws, rounded up to a power of two
+// (MCMCMC: ceil(K/4); Metropolis draws block 0 only).
+uint32_t site_blocks_pow2(uint32_t rule, uint32_t K) {
+    uint32_t kb = 1;
+    if (rule == 0)
+        while (4 * kb < K) kb <<= 1;
+    return kb;
+}
+// Blocks per lane for G lanes per chain, or 0 when no kernel has that shape:
+// NB = 1 for every G, 2 for G = 8, 16, 32, 4 for G = 8, 16.
+uint32_t blocks_per_lane(uint32_t rule, uint32_t K, uint32_t G) {
+    const uint32_t kb = site_blocks_pow2(rule, K);
+    const uint32_t nb = kb > G ? kb / G : 1u;
+    if (nb == 1) return (G == 4 || G == 8 || G == 16 || G == 32) ? 1u : 0u;
+    if (nb == 2) return (G == 8 || G == 16 || G == 32) ? 2u : 0u;
+    if (nb == 4) return (G == 8 || G == 16) ? 4u : 0u;
+    return 0u;
+}
+
+// class = kind * 128 + rule * 64 + stage * 32 + log2(NB) * 8 + log2(G), or -1
 int step_class(uint32_t kind, uint32_t rule, uint32_t K, uint32_t G, uint32_t stage) {
-    const int nb = (rule == 0 && K > 128) ? 2 : 1;
+    const uint32_t nb = blocks_per_lane(rule, K, G);
+    if (!nb) return -1;
     int lg = 0;
     while ((1u << lg) < G) ++lg;
-    return static_cast<int>(kind) * 64 + static_cast<int>(rule) * 32 + static_cast<int>(stage != 0) * 16 +
-           (nb - 1) * 8 + lg;
+    const int lnb = nb == 1 ? 0 : (nb == 2 ? 1 : 2);
+    return static_cast<int>(kind) * 128 + static_cast<int>(rule) * 64 + static_cast<int>(stage != 0) * 32 +
+           lnb * 8 + lg;
 }
 uint32_t class_lanes(int cls) { return 1u << (cls & 7); }
-bool class_staged(int cls) { return ((cls >> 4) & 1) != 0; }
+bool class_staged(int cls) { return ((cls >> 5) & 1) != 0; }
 
 #define SK_DISPATCH(F, ...)                                                          \
     do {                                                                             \
-        const int kind_ = cls >> 6, rule_ = (cls >> 5) & 1, stage_ = (cls >> 4) & 1; \
+        const int kind_ = cls >> 7, rule_ = (cls >> 6) & 1, stage_ = (cls >> 5) & 1; \
         if (kind_ == 0 && rule_ == 0) return stage_ ? F##_pm1_mcmcmc_staged(__VA_ARGS__) : F##_pm1_mcmcmc_direct(__VA_ARGS__); \
         if (kind_ == 0) return stage_ ? F##_pm1_metropolis_staged(__VA_ARGS__) : F##_pm1_metropolis_direct(__VA_ARGS__); \
         if (rule_ == 0) return stage_ ? F##_gauss_mcmcmc_staged(__VA_ARGS__) : F##_gauss_mcmcmc_direct(__VA_ARGS__); \
@@ -184,7 +205,7 @@ cudaError_t launch_step(const JobDev* jobs, const WorkItem* items, uint32_t n_it
     cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
     const uint32_t ns = static_cast<uint32_t>(nsteps);
-    const int nb = ((cls >> 3) & 1) + 1, G = 1 << (cls & 7);
+    const int nb = 1 << ((cls >> 3) & 3), G = 1 << (cls & 7);
     e = launch_class(cls, nb, G, jobs, items, n_items, queue, ns, W, per_chain, grid, st);
     if (e != cudaSuccess || !bump) return e;
     bump_steps<<<(n_jobs + 127) / 128, 128, 0, st>>>(jobs, n_jobs, nsteps);
@@ -192,7 +213,7 @@ cudaError_t launch_step(const JobDev* jobs, const WorkItem* items, uint32_t n_it
 }
 
 int step_kernel_occupancy(int cls, uint32_t W, size_t per_chain) {
-    const int nb = ((cls >> 3) & 1) + 1, G = 1 << (cls & 7);
+    const int nb = 1 << ((cls >> 3) & 3), G = 1 << (cls & 7);
     return occupancy_class(cls, nb, G, W, static_cast<uint32_t>(per_chain));
 }
 

@@ -17,8 +17,9 @@
 //       root_thr = ceil(2^64/(K+1)), i.e. floor(U0 (K+1) / 2^64) != 0) and
 //       U1 (node);
 //       blocks 1..ceil(K/4) give site_d = floor(w N / 2^32), d = 1..K.
-//       Group lane l computes block 1+l (+32 when K > 128), so its slots are
-//       d = 4l+1..4l+4 (+128); block 0 is computed G steps at a time.
+//       Group lane l computes blocks 1 + l + G q for q < NB (NB blocks per
+//       lane), so its slots are d = 4Gq + 4l + 1..4 (slot order is lane order
+//       within a q, then q); block 0 is computed G steps at a time.
 //   a2  the row of J at a = site_1 of the NEXT step is staged by TMA.
 //   a3  candidate energies: centre root dE_d = 2 s_i h_i (i = site_d);
 //       leaf root dE_1 = 2 s_a h_a, dE_d = 2 s_a h_a + 2 s_b h_b - 4 J_ab s_a s_b
@@ -122,13 +123,13 @@ __device__ __forceinline__ uint4 block0(Block0& c, uint32_t t, uint32_t chain, u
     return make_uint4(gshfl(g, c.v.x, src), gshfl(g, c.v.y, src), gshfl(g, c.v.z, src), gshfl(g, c.v.w, src));
 }
 
-// Sites of step t held by this lane: slots d = 128 q + 4 gl + e + 1.
+// Sites of step t held by this lane: slots d = 4 G q + 4 gl + e + 1.
 template <int NB, int G>
 __device__ __forceinline__ void draw_sites(uint32_t (&site)[4 * NB], uint32_t t, uint32_t chain, uint32_t c3,
                                            uint32_t k0, uint32_t k1, uint32_t nblk, uint32_t N, const Grp<G>& g) {
 #pragma unroll
     for (int q = 0; q < NB; ++q) {
-        const uint32_t b = 1u + 32u * q + g.gl;
+        const uint32_t b = 1u + static_cast<uint32_t>(G) * q + g.gl;
         uint4 r = make_uint4(0u, 0u, 0u, 0u);
         if (b <= nblk) r = dev::philox4x32_10(make_uint4(b, t, chain, c3), k0, k1);
         site[4 * q + 0] = __umulhi(r.x, N);
@@ -375,7 +376,7 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                 H mloc = 0;
 #pragma unroll
                 for (int q = 0; q < 4 * NB; ++q) {
-                    const uint32_t d = 128u * (q >> 2) + 4u * g.gl + (q & 3) + 1u;
+                    const uint32_t d = 4u * G * (q >> 2) + 4u * g.gl + (q & 3) + 1u;
                     const uint32_t i = site[q];
                     const int si = S[i];
                     const H hi = hf[i];
@@ -395,7 +396,7 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                 for (int q = 0; q < NB; ++q) gsum_[q] = 0;
 #pragma unroll
                 for (int q = 0; q < 4 * NB; ++q) {
-                    const uint32_t d = 128u * (q >> 2) + 4u * g.gl + (q & 3) + 1u;
+                    const uint32_t d = 4u * G * (q >> 2) + 4u * g.gl + (q & 3) + 1u;
                     W x = 0;
                     const bool centre = leaf && d == 1u;  // slot 1 of a leaf root
                     if (d <= K) {
@@ -466,7 +467,7 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                             if (e == my_e) my_site = site[4 * q + e];
                         const uint32_t packed = gshfl(g, (my_site << 2) | static_cast<uint32_t>(my_e & 3), L);
                         sel_site = packed >> 2;
-                        sel_d = 128 * q + 4 * L + static_cast<int>(packed & 3u) + 1;
+                        sel_d = 4 * G * q + 4 * L + static_cast<int>(packed & 3u) + 1;
                         found = true;
                     }
                     base += tot[q];
@@ -524,7 +525,7 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
 }
 
 // MAXT bounds the CTA size and so the register budget per thread
-// (65536 / MAXT): 1024 -> 64, 640 -> 96, 512 -> 128 registers.
+// (65536 / MAXT): 1024 -> 64, 768 -> 80, 640 -> 96, 512 -> 128 registers.
 // STAGE: stage row a by TMA (two row buffers per chain in shared memory) or
 // read it through L1 (no buffers: more chains fit in shared memory).
 template <typename JT, int RULE, int NB, int G, int STAGE, int MAXT>
@@ -646,27 +647,41 @@ cudaError_t launch_g(const JobDev* jobs, const WorkItem* items, uint32_t n_items
                      uint32_t nsteps, uint32_t W, uint32_t per_chain, uint32_t grid, cudaStream_t st) {
     if (W <= 16) return launch_variant<JT, RULE, NB, G, STAGE, 512>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
     if (W <= 20) return launch_variant<JT, RULE, NB, G, STAGE, 640>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
+    if (W <= 24) return launch_variant<JT, RULE, NB, G, STAGE, 768>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
     return launch_variant<JT, RULE, NB, G, STAGE, 1024>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
 }
 template <typename JT, int RULE, int NB, int G, int STAGE>
 int occupancy_g(uint32_t W, uint32_t per_chain) {
     if (W <= 16) return occupancy_variant<JT, RULE, NB, G, STAGE, 512>(W, per_chain);
     if (W <= 20) return occupancy_variant<JT, RULE, NB, G, STAGE, 640>(W, per_chain);
+    if (W <= 24) return occupancy_variant<JT, RULE, NB, G, STAGE, 768>(W, per_chain);
     return occupancy_variant<JT, RULE, NB, G, STAGE, 1024>(W, per_chain);
 }
 
-// Dispatch over (Philox blocks per lane, lanes per chain) for one coupling
-// type, rule and staging choice; K > 128 (two blocks per lane) needs
-// whole-warp chains.
+// Dispatch over (Philox blocks per lane NB, lanes per chain G) for one
+// coupling type, rule and staging choice.  NB = 1 for every G; NB = 2 for
+// G = 8, 16, 32 and NB = 4 for G = 8, 16 (MCMCMC only: K up to 4 G NB).
 template <typename JT, int RULE, int STAGE>
 cudaError_t launch_rule(int nb, int G, const JobDev* jobs, const WorkItem* items, uint32_t n_items, uint32_t* queue,
                         uint32_t nsteps, uint32_t W, uint32_t per_chain, uint32_t grid, cudaStream_t st) {
-    if (nb == 2) {
-        if constexpr (RULE == 0) {
-            if (G == 32) return launch_g<JT, RULE, 2, 32, STAGE>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
+    if constexpr (RULE == 0) {
+        if (nb == 2) {
+            switch (G) {
+                case 8: return launch_g<JT, RULE, 2, 8, STAGE>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
+                case 16: return launch_g<JT, RULE, 2, 16, STAGE>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
+                case 32: return launch_g<JT, RULE, 2, 32, STAGE>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
+                default: return cudaErrorInvalidValue;
+            }
         }
-        return cudaErrorInvalidValue;
+        if (nb == 4) {
+            switch (G) {
+                case 8: return launch_g<JT, RULE, 4, 8, STAGE>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
+                case 16: return launch_g<JT, RULE, 4, 16, STAGE>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
+                default: return cudaErrorInvalidValue;
+            }
+        }
     }
+    if (nb != 1) return cudaErrorInvalidValue;
     switch (G) {
         case 4: return launch_g<JT, RULE, 1, 4, STAGE>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
         case 8: return launch_g<JT, RULE, 1, 8, STAGE>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
@@ -677,12 +692,24 @@ cudaError_t launch_rule(int nb, int G, const JobDev* jobs, const WorkItem* items
 }
 template <typename JT, int RULE, int STAGE>
 int occupancy_rule(int nb, int G, uint32_t W, uint32_t per_chain) {
-    if (nb == 2) {
-        if constexpr (RULE == 0) {
-            if (G == 32) return occupancy_g<JT, RULE, 2, 32, STAGE>(W, per_chain);
+    if constexpr (RULE == 0) {
+        if (nb == 2) {
+            switch (G) {
+                case 8: return occupancy_g<JT, RULE, 2, 8, STAGE>(W, per_chain);
+                case 16: return occupancy_g<JT, RULE, 2, 16, STAGE>(W, per_chain);
+                case 32: return occupancy_g<JT, RULE, 2, 32, STAGE>(W, per_chain);
+                default: return 0;
+            }
         }
-        return 0;
+        if (nb == 4) {
+            switch (G) {
+                case 8: return occupancy_g<JT, RULE, 4, 8, STAGE>(W, per_chain);
+                case 16: return occupancy_g<JT, RULE, 4, 16, STAGE>(W, per_chain);
+                default: return 0;
+            }
+        }
     }
+    if (nb != 1) return 0;
     switch (G) {
         case 4: return occupancy_g<JT, RULE, 1, 4, STAGE>(W, per_chain);
         case 8: return occupancy_g<JT, RULE, 1, 8, STAGE>(W, per_chain);

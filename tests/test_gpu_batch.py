@@ -103,6 +103,54 @@ def test_capture_rejects_default_stream_and_misaligned_recompute():
 
 
 @pytest.mark.parametrize("staging", [1, 2])
+@pytest.mark.parametrize("lanes", [8, 16, 32])
+def test_blocks_per_lane_do_not_change_results(lanes, staging):
+    # several Philox blocks (4 proposals each) per lane: 2 or 4 blocks on 8
+    # or 16 lanes, 2 on 32; ragged K and chain counts; +-J bit-exact and a
+    # Gaussian run replayed by the oracle
+    torch = need_gpu()
+    import oracle
+    specs = [(100, 40, 7, 0.8, "pm1"), (130, 100, 5, 1.1, "pm1"), (96, 128, 6, 0.5, "pm1"),
+             (70, 200, 3, 1.0, "pm1"), (120, 128, 4, 1.0, "gauss")]  # N, K, chains, beta, J
+    steps, R = 600, 100
+    st = torch.cuda.Stream()
+    made = []
+    for i, (N, K, chains, beta, kind) in enumerate(specs):
+        J = inputs.couplings_pm1(N, 70 + i) if kind == "pm1" else inputs.couplings_gauss(N, 70 + i)
+        inst = sk.Instance(J, stream=st)
+        init = inputs.initial_spins(chains, N, 20 + i)
+        run = sk.Run(inst, chains=chains, K=K, beta=beta, seed=8, stream_id=i, record_every=R,
+                     max_records=steps // R, init=init, trace_chains=chains, trace_steps=steps)
+        made.append((J, init, inst, run))
+    b = sk.Batch([m[3] for m in made])
+    b.set_layout(lanes, staging)
+    # K > 128 needs 16 lanes at least, K > 16 needs 8
+    assert {c[1] for c in b.classes()} == {max(lanes, 16 if K > 128 else 8) for (_, K, _, _, _) in specs}
+    b.advance(250)
+    b.advance(steps - 250)
+    for i, ((N, K, chains, beta, kind), (J, init, inst, run)) in enumerate(zip(specs, made)):
+        spins, h, _ = run.state(fields=True)
+        tr = run.trace()
+        if kind == "pm1":
+            E, q, acc = run.observables()
+            o = oracle.run(J, K=K, beta=beta, seed=8, stream=i, chains=chains, init=init,
+                           steps=steps, record_every=R, trace=True)
+            assert np.array_equal(tr, o["trace"]), i
+            assert np.array_equal(E, o["E"]) and np.array_equal(acc, o["acc"]), i
+            assert np.array_equal(spins, o["spins"]), i
+            assert np.array_equal(h, (J.astype(np.int64) @ spins.T.astype(np.int64)).T), i
+        else:
+            for c in range(chains):
+                r = oracle.replay(J, tr[c], K=K, beta=beta, seed=8, stream=i, chain=c,
+                                  init=init[c], tol=1e-4)
+                assert r["bad"] == 0 and np.array_equal(r["spins"], spins[c]), (i, c, r)
+    b.close()
+    for _, _, inst, run in made:
+        run.close()
+        inst.close()
+
+
+@pytest.mark.parametrize("staging", [1, 2])
 @pytest.mark.parametrize("lanes", [4, 8, 16, 32])
 def test_lanes_per_chain_do_not_change_results(lanes, staging):
     # sub-warp chains (32/lanes chains per warp), ragged chain counts (groups
