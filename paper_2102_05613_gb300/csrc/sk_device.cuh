@@ -128,6 +128,14 @@ struct Types<float> {
 
 
 
+// A field of the CTA's shared job descriptor read where it is used (a
+// volatile shared-memory load) instead of being held in a register across
+// the whole step loop.
+template <typename T>
+__device__ __forceinline__ T at_use(const T& x) {
+    return *const_cast<const volatile T*>(&x);
+}
+
 // 2^x on the special-function unit (ex2.approx.ftz: relative error < 2^-22
 // over the range used here, x <= 0).  exp(-beta dE) = 2^(-beta log2(e) dE).
 __device__ __forceinline__ float pow2(float x) {

@@ -53,11 +53,15 @@ struct WorkItem {
     uint32_t job, chain0, nchains, pad;
 };
 
-// Bytes of shared memory one chain needs for spins, fields and (staged) the
-// two J-row buffers.
+// Shared memory of the block-0 draws one chain keeps (16 bytes for each of
+// up to 32 steps).
+constexpr size_t kB0Bytes = 512;
+
+// Bytes of shared memory one chain needs for spins, fields, (staged) the two
+// J-row buffers and its block-0 draws.
 inline size_t warp_smem_bytes(uint32_t npad, uint32_t kind, bool staged = true) {
     size_t bj = kind == 0 ? 1 : 4;
-    return (size_t)npad * (1 + 4 + (staged ? 2 * bj : 0));
+    return (size_t)npad * (1 + 4 + (staged ? 2 * bj : 0)) + kB0Bytes;
 }
 
 // Kernel launchers (sk_kernels.cu).  All return cudaGetLastError().

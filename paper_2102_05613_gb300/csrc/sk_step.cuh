@@ -102,41 +102,36 @@ struct ChainMem {
     void* h;
     void* row[2];
     uint64_t* bar;
+    uint4* b0;  // block 0 of G consecutive steps (kB0Bytes reserved)
 };
 
-// Block 0 of each step, computed for G consecutive steps at once (group lane
-// l holds the step base + l) and broadcast in the group.  Steps are 32-bit.
-struct Block0 {
-    uint4 v;
-    uint32_t base;
-    bool valid;
-};
+// Block 0 (U0, U1) of the G steps base .. base+G-1, computed one step per
+// group lane into the chain's shared memory, where every lane of the group
+// reads the block of its current step.  Steps are 32-bit.
 template <int G>
-__device__ __forceinline__ uint4 block0(Block0& c, uint32_t t, uint32_t chain, uint32_t c3, uint32_t k0,
-                                        uint32_t k1, const Grp<G>& g) {
-    if (!c.valid || t - c.base >= static_cast<uint32_t>(G)) {
-        c.base = t & ~static_cast<uint32_t>(G - 1);
-        c.valid = true;
-        c.v = dev::philox4x32_10(make_uint4(0u, c.base + g.gl, chain, c3), k0, k1);
-    }
-    const int src = static_cast<int>(t - c.base);
-    return make_uint4(gshfl(g, c.v.x, src), gshfl(g, c.v.y, src), gshfl(g, c.v.z, src), gshfl(g, c.v.w, src));
+__device__ __forceinline__ void fill_block0(uint4* b0s, uint32_t base, uint32_t chain, uint32_t c3, uint32_t k0,
+                                            uint32_t k1, const Grp<G>& g) {
+    b0s[g.gl] = dev::philox4x32_10(make_uint4(0u, base + g.gl, chain, c3), k0, k1);
+    __syncwarp(g.mask);
 }
 
-// Sites of step t held by this lane: slots d = 4 G q + 4 gl + e + 1.
+// Sites of step t held by this lane: slots d = 4 G q + 4 gl + e + 1, two
+// 16-bit sites per register (N <= 8192): site k is half k & 1 of sp[k >> 1].
 template <int NB, int G>
-__device__ __forceinline__ void draw_sites(uint32_t (&site)[4 * NB], uint32_t t, uint32_t chain, uint32_t c3,
+__device__ __forceinline__ void draw_sites(uint32_t (&sp)[2 * NB], uint32_t t, uint32_t chain, uint32_t c3,
                                            uint32_t k0, uint32_t k1, uint32_t nblk, uint32_t N, const Grp<G>& g) {
 #pragma unroll
     for (int q = 0; q < NB; ++q) {
         const uint32_t b = 1u + static_cast<uint32_t>(G) * q + g.gl;
         uint4 r = make_uint4(0u, 0u, 0u, 0u);
         if (b <= nblk) r = dev::philox4x32_10(make_uint4(b, t, chain, c3), k0, k1);
-        site[4 * q + 0] = __umulhi(r.x, N);
-        site[4 * q + 1] = __umulhi(r.y, N);
-        site[4 * q + 2] = __umulhi(r.z, N);
-        site[4 * q + 3] = __umulhi(r.w, N);
+        sp[2 * q + 0] = __umulhi(r.x, N) | (__umulhi(r.y, N) << 16);
+        sp[2 * q + 1] = __umulhi(r.z, N) | (__umulhi(r.w, N) << 16);
     }
+}
+template <int NB>
+__device__ __forceinline__ uint32_t site_of(const uint32_t (&sp)[2 * NB], int k) {
+    return (sp[k >> 1] >> (16 * (k & 1))) & 0xFFFFu;
 }
 
 // h_k -= c1 J[x1][k] + c2 J[x2][k] for k < Npad (c2 = 0: one flip); lane gl
@@ -217,8 +212,9 @@ __device__ __forceinline__ double chain_energy(const int8_t* S, const void* h, u
 // `write` groups (real chains, not shadows) store.
 template <typename JT, int G>
 __device__ __noinline__ void record(const JobDev& jb, bool write, uint32_t chain, uint32_t rec, const int8_t* S,
-                                    const void* h, const int8_t* partner_s, uint32_t acc) {
+                                    const void* h, int partner_off, uint32_t acc) {
     const Grp<G> g;
+    const int8_t* partner_s = S + partner_off;
     const bool store = write && rec < jb.rec_capacity;
     const double E = chain_energy<JT, G>(S, h, jb.Npad, jb.scale, g);
     if (store && g.gl == 0) {
@@ -249,55 +245,60 @@ __device__ __noinline__ void record(const JobDev& jb, bool write, uint32_t chain
 // CTA's record barriers.
 template <typename JT, int RULE, int NB, int G, int STAGE>
 __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_t chain, const ChainMem& cm,
-                                           const int8_t* partner_s, uint32_t t0, uint32_t t1, uint32_t& acc,
+                                           int partner_off, uint32_t t0, uint32_t t1, uint32_t& acc,
                                            uint32_t& phase, bool& dead, uint32_t& n_flips, uint32_t& n_rows) {
     using H = typename Types<JT>::H;
     using W = typename Types<JT>::W;
     const Grp<G> g;
-    const uint32_t R = jb.record_every;
-    uint32_t next_rec = R ? (t0 / R + 1u) * R : 0xFFFFFFFFu;
-    uint32_t rec_idx = R ? t0 / R : 0u;
+    // next record point (0: none; a record follows step t when t + 1 == next_rec)
+    uint32_t next_rec = jb.record_every ? (t0 / jb.record_every + 1u) * jb.record_every : 0u;
     // job parameters held in registers for the whole loop
     const uint32_t N = jb.N, npad = jb.Npad, K = jb.K;
     const uint32_t nblk = (K + 3u) >> 2;
     const uint32_t k0 = static_cast<uint32_t>(jb.seed), k1 = static_cast<uint32_t>(jb.seed >> 32);
     const uint32_t c3 = jb.stream & 0xFFFFFFu;  // domain 0: step draws
-    const JT* __restrict__ Jg = static_cast<const JT*>(jb.J);
+    // row r of J (the base pointer is re-read from the job descriptor at each use)
+    auto Jrow = [&](uint32_t r) -> const JT* {
+        return static_cast<const JT*>(dev::at_use(jb.J)) + static_cast<size_t>(r) * npad;
+    };
     const uint32_t rowbytes = npad * static_cast<uint32_t>(sizeof(JT));
     const W* __restrict__ Wt = reinterpret_cast<const W*>(jb.W);
     const uint32_t wlen = jb.wlen;
     const float nbl2 = -jb.beta_eff * 1.4426950408889634f;  // -beta log2(e)
-    const uint64_t root_thr = jb.root_thr;
     const bool root_weighted = jb.fcen + jb.fleaf != (2u << 20);  // not both factors 1
-    int32_t* trace = (write && chain < jb.trace_chains) ? jb.trace + static_cast<size_t>(chain) * jb.trace_steps
-                                                        : nullptr;
-    const uint32_t trace_end = trace ? static_cast<uint32_t>(jb.trace_steps) : 0u;
+    // steps this chain logs its choice for (0: not traced)
+    const uint32_t trace_end = (write && chain < jb.trace_chains)
+                                   ? static_cast<uint32_t>(min(jb.trace_steps, static_cast<uint64_t>(0xFFFFFFFFu)))
+                                   : 0u;
     int8_t* S = cm.s;
     H* hf = static_cast<H*>(cm.h);
 
-    Block0 bc;
-    bc.valid = false;
-    uint32_t site[4 * NB];
+    fill_block0<G>(cm.b0, t0 & ~static_cast<uint32_t>(G - 1), chain, c3, k0, k1, g);
+    uint32_t site[2 * NB];  // packed sites of this step (site_of)
 
     // prologue (staged rows): draw the first step and stage its row
     if constexpr (STAGE) {
         uint32_t first;
         if constexpr (RULE == 0) {
             draw_sites<NB, G>(site, t0, chain, c3, k0, k1, nblk, N, g);
-            first = gshfl(g, site[0], 0);
+            first = gshfl(g, site[0], 0) & 0xFFFFu;
         } else {
-            first = __umulhi(block0<G>(bc, t0, chain, c3, k0, k1, g).x, N);
+            first = __umulhi(cm.b0[t0 & (G - 1)].x, N);
         }
         if (g.gl == 0 && !dead) {
             dev::fence_proxy_async();
-            dev::bulk_load(cm.row[t0 & 1u], Jg + static_cast<size_t>(first) * npad, rowbytes, &cm.bar[t0 & 1u]);
+            dev::bulk_load(cm.row[t0 & 1u], Jrow(first), rowbytes, &cm.bar[t0 & 1u]);
         }
     }
     (void)rowbytes;
 
     for (uint32_t t = t0; t < t1; ++t) {
         const uint32_t buf = t & 1u;
-        const uint4 b0 = block0<G>(bc, t, chain, c3, k0, k1, g);
+        const uint4 b0 = cm.b0[t & (G - 1)];
+        if (((t + 1u) & (G - 1)) == 0u && t + 1u < t1) {  // the next G steps' block 0
+            __syncwarp(g.mask);  // every lane has read this step's entry
+            fill_block0<G>(cm.b0, t + 1u, chain, c3, k0, k1, g);
+        }
         const unsigned long long U1 = (static_cast<unsigned long long>(b0.w) << 32) | b0.z;
         int sel = 0;  // slot chosen (Metropolis: accepted)
         int nflip = 0;
@@ -308,20 +309,20 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
         // direct rows: this step's sites now; staged rows: the next step's
         // sites and the TMA of its first row, one step ahead
         if constexpr (!STAGE && RULE == 0) draw_sites<NB, G>(site, t, chain, c3, k0, k1, nblk, N, g);
-        uint32_t nsite[4 * NB];
+        uint32_t nsite[2 * NB];
         if (STAGE && t + 1u < t1) {
             uint32_t nx;
             if constexpr (RULE == 0) {
                 draw_sites<NB, G>(nsite, t + 1u, chain, c3, k0, k1, nblk, N, g);
-                nx = gshfl(g, nsite[0], 0);
+                nx = gshfl(g, nsite[0], 0) & 0xFFFFu;
             } else {
-                nx = __umulhi(block0<G>(bc, t + 1u, chain, c3, k0, k1, g).x, N);
+                nx = __umulhi(cm.b0[(t + 1u) & (G - 1)].x, N);
             }
             if constexpr (STAGE) {
                 __syncwarp(g.mask);  // every lane of the group is done with buffer buf^1 (step t-1)
                 if (g.gl == 0 && !dead) {
                     dev::fence_proxy_async();
-                    dev::bulk_load(cm.row[buf ^ 1u], Jg + static_cast<size_t>(nx) * npad, rowbytes, &cm.bar[buf ^ 1u]);
+                    dev::bulk_load(cm.row[buf ^ 1u], Jrow(nx), rowbytes, &cm.bar[buf ^ 1u]);
                 }
             }
             (void)nx;
@@ -341,8 +342,8 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
         if constexpr (STAGE) {
             rowA = static_cast<const JT*>(cm.row[buf]);
         } else {
-            const uint32_t a0 = RULE == 0 ? gshfl(g, site[0], 0) : __umulhi(b0.x, N);
-            rowA = Jg + static_cast<size_t>(a0) * npad;
+            const uint32_t a0 = RULE == 0 ? (gshfl(g, site[0], 0) & 0xFFFFu) : __umulhi(b0.x, N);
+            rowA = Jrow(a0);
         }
 
         if (!dead) {
@@ -368,8 +369,8 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
             } else {
                 // ---- MCMCMC: K proposals on the uniform-root star ----
                 const unsigned long long U0 = (static_cast<unsigned long long>(b0.y) << 32) | b0.x;
-                const bool leaf = U0 >= root_thr;
-                const uint32_t a = gshfl(g, site[0], 0);
+                const bool leaf = U0 >= dev::at_use(jb.root_thr);
+                const uint32_t a = gshfl(g, site[0], 0) & 0xFFFFu;
                 const int sa = S[a];
                 const H dEa = static_cast<H>(2 * sa) * hf[a];
                 H dE[4 * NB];
@@ -377,7 +378,7 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
 #pragma unroll
                 for (int q = 0; q < 4 * NB; ++q) {
                     const uint32_t d = 4u * G * (q >> 2) + 4u * g.gl + (q & 3) + 1u;
-                    const uint32_t i = site[q];
+                    const uint32_t i = site_of<NB>(site, q);
                     const int si = S[i];
                     const H hi = hf[i];
                     const H single = static_cast<H>(2 * si) * hi;
@@ -389,16 +390,13 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                     if (d <= K) mloc = mloc < v ? mloc : v;
                 }
                 const H m = gmin(g, mloc);
-                // weights in slot order
-                W w[4 * NB];
-                W gsum_[NB];
-#pragma unroll
-                for (int q = 0; q < NB; ++q) gsum_[q] = 0;
-#pragma unroll
-                for (int q = 0; q < 4 * NB; ++q) {
+                // weights in slot order: exp(-beta (dE - m)) times the slot's
+                // root factor (the centre: slot 1 of a leaf root, slot 0 of a
+                // centre root); recomputed, not stored, where the choice needs them
+                auto slot_w = [&](int q) -> W {
                     const uint32_t d = 4u * G * (q >> 2) + 4u * g.gl + (q & 3) + 1u;
                     W x = 0;
-                    const bool centre = leaf && d == 1u;  // slot 1 of a leaf root
+                    const bool centre = leaf && d == 1u;
                     if (d <= K) {
                         if constexpr (sizeof(JT) == 1) {
                             const uint32_t idx = static_cast<uint32_t>(dE[q] - m) >> 1;
@@ -409,9 +407,13 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                             x = dev::pow2(fmaf(nbl2, dE[q] - m, centre ? jb.lcen : jb.lleaf));
                         }
                     }
-                    w[q] = x;
-                    gsum_[q >> 2] += x;
-                }
+                    return x;
+                };
+                W gsum_[NB];
+#pragma unroll
+                for (int q = 0; q < NB; ++q) gsum_[q] = 0;
+#pragma unroll
+                for (int q = 0; q < 4 * NB; ++q) gsum_[q >> 2] += slot_w(q);
                 W w0;  // slot 0, the root: the centre of a centre root, else a leaf
                 if constexpr (sizeof(JT) == 1) {
                     const uint32_t idx0 = static_cast<uint32_t>(-m) >> 1;
@@ -437,7 +439,8 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                     if (u >= total) u = nextafterf(total, 0.0f);
                 }
                 // first slot whose inclusive prefix exceeds u; the owning
-                // lane finds its entry, one packed shuffle broadcasts it
+                // lane finds its entry (else, a rounding guard, its last
+                // positive weight), one packed shuffle broadcasts it
                 int sel_d = 0;
                 uint32_t sel_site = 0;
                 bool found = u < w0;
@@ -447,24 +450,32 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                     const unsigned ball = gballot(g, !found && base + incl[q] > u);
                     if (!found && ball) {
                         const int L = __ffs(ball) - 1;
-                        W run = base + (incl[q] - gsum_[q]);
-                        int my_e = -1;
+                        // this lane's 4 weights again (bit-identical), their
+                        // sum in the order of the first pass
+                        W x[4];
+                        W mine = 0;
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
-                            if (my_e < 0 && w[4 * q + e] > W(0)) {
-                                run += w[4 * q + e];
-                                if (run > u) my_e = e;
+                            x[e] = slot_w(4 * q + e);
+                            mine += x[e];
+                        }
+                        W run = base + (incl[q] - mine);
+                        int my_e = -1, last_pos = -1;
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            if (x[e] > W(0)) {
+                                last_pos = e;
+                                if (my_e < 0) {
+                                    run += x[e];
+                                    if (run > u) my_e = e;
+                                }
                             }
                         }
-                        if (my_e < 0) {  // rounding guard: last positive weight
-#pragma unroll
-                            for (int e = 0; e < 4; ++e)
-                                if (w[4 * q + e] > W(0)) my_e = e;
-                        }
+                        if (my_e < 0) my_e = last_pos;
                         uint32_t my_site = 0;
 #pragma unroll
                         for (int e = 0; e < 4; ++e)
-                            if (e == my_e) my_site = site[4 * q + e];
+                            if (e == my_e) my_site = site_of<NB>(site, 4 * q + e);
                         const uint32_t packed = gshfl(g, (my_site << 2) | static_cast<uint32_t>(my_e & 3), L);
                         sel_site = packed >> 2;
                         sel_d = 4 * G * q + 4 * L + static_cast<int>(packed & 3u) + 1;
@@ -496,9 +507,9 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                 const int c1 = 2 * S[x1];
                 const int c2 = nflip == 2 ? 2 * S[x2] : 0;
                 if (x1_staged)
-                    update_fields<JT, STAGE != 0, G>(hf, rowA, Jg + static_cast<size_t>(x2) * npad, c1, c2, npad, g.gl);
+                    update_fields<JT, STAGE != 0, G>(hf, rowA, Jrow(x2), c1, c2, npad, g.gl);
                 else
-                    update_fields<JT, false, G>(hf, Jg + static_cast<size_t>(x1) * npad, nullptr, c1, 0, npad, g.gl);
+                    update_fields<JT, false, G>(hf, Jrow(x1), nullptr, c1, 0, npad, g.gl);
                 __syncwarp(g.mask);
                 if (g.gl == 0) {
                     S[x1] = static_cast<int8_t>(-S[x1]);
@@ -508,18 +519,17 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
             }
             n_flips += static_cast<uint32_t>(nflip);
             n_rows += static_cast<uint32_t>(rows);
-            if (t < trace_end && g.gl == 0) trace[t] = sel;
+            if (t < trace_end && g.gl == 0) jb.trace[static_cast<size_t>(chain) * jb.trace_steps + t] = sel;
             __syncwarp(g.mask);
         }
         if constexpr (RULE == 0 && STAGE) {
 #pragma unroll
-            for (int q = 0; q < 4 * NB; ++q) site[q] = nsite[q];
+            for (int q = 0; q < 2 * NB; ++q) site[q] = nsite[q];
         }
         if (t + 1u == next_rec) {
-            record<JT, G>(jb, write && !dead, chain, rec_idx, S, hf, partner_s, acc);
+            record<JT, G>(jb, write && !dead, chain, next_rec / jb.record_every - 1u, S, hf, partner_off, acc);
             acc = 0;
-            next_rec += R;
-            ++rec_idx;
+            next_rec += jb.record_every;
         }
     }
 }
@@ -570,7 +580,9 @@ __global__ void __launch_bounds__(MAXT, 1)
         cm.row[0] = base + 5 * static_cast<size_t>(npad);
         cm.row[1] = base + (5 + bj) * static_cast<size_t>(npad);
         cm.bar = &bars[2 * slot];
-        const int8_t* partner_s = reinterpret_cast<const int8_t*>(smem + static_cast<size_t>(slot ^ 1) * per_chain);
+        cm.b0 = reinterpret_cast<uint4*>(base + (STAGE ? 5 + 2 * bj : 5) * static_cast<size_t>(npad));
+        // the overlap partner (chain slot ^ 1) lives one slice up or down
+        const int partner_off = (slot & 1) ? -static_cast<int>(per_chain) : static_cast<int>(per_chain);
         const uint32_t t0 = static_cast<uint32_t>(*jb.step);
         const uint32_t t1 = static_cast<uint32_t>(
             min(static_cast<uint64_t>(t0) + nsteps, static_cast<uint64_t>(jb.step_limit)));
@@ -589,14 +601,14 @@ __global__ void __launch_bounds__(MAXT, 1)
         __syncwarp();
         if (t1 > t0) {
             if (warp_busy) {
-                chain_loop<JT, RULE, NB, G, STAGE>(jb, own, chain, cm, partner_s, t0, t1, acc, phase, dead,
+                chain_loop<JT, RULE, NB, G, STAGE>(jb, own, chain, cm, partner_off, t0, t1, acc, phase, dead,
                                                    n_flips, n_rows);
             } else {
                 // no chain in this warp: meet the CTA's record barriers only
                 const uint32_t R = jb.record_every;
                 if (R)
                     for (uint32_t p = (t0 / R + 1u) * R, r = t0 / R; p <= t1; p += R, ++r)
-                        record<JT, G>(jb, false, chain, r, cm.s, cm.h, partner_s, 0u);
+                        record<JT, G>(jb, false, chain, r, cm.s, cm.h, partner_off, 0u);
             }
         }
         __syncwarp();
