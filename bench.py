@@ -582,9 +582,7 @@ def run_ours(args):
         hE = [torch.empty((1, CHAINS), dtype=torch.float64).pin_memory() for _ in runs]
         hQ = [torch.empty((1, CHAINS // 2), dtype=torch.float64).pin_memory() for _ in runs]
         hA = [torch.empty((1, CHAINS), dtype=torch.int32).pin_memory() for _ in runs]
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
+        def e2e_step():
             for inst, J in zip(insts, hJ):
                 inst.set_couplings(J)
             for r, S in zip(runs, hS):
@@ -592,6 +590,12 @@ def run_ours(args):
             batch.advance(R)
             for r, e_, q_, a_ in zip(runs, hE, hQ, hA):
                 r.observables(0, 1, out=(e_, q_, a_))
+
+        e2e_step()  # untimed: first-use staging buffers
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
         barrier()
         te = replicas.max_over_ranks(time.perf_counter() - t0, dist, device="cuda")
         h2d = sum(x.numel() * x.element_size() for x in hJ + hS)
@@ -620,7 +624,8 @@ def run_ours(args):
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD, "N": N, "instances": INSTANCES, "chains": CHAINS,
                            "K": K, "beta": BETA, "mc_steps_per_bench_step": R,
-                           "l2": "state (671 MB) larger than L2, streamed every launch",
+                           "l2": f"state ({INSTANCES * CHAINS * N * 5 / 1e6:.0f} MB) larger than L2, "
+                                 "streamed every launch",
                            "launch": info},
                 "mc_steps_per_s": mc_steps,
                 "gpu_launches": 2 * args.steps,

@@ -106,6 +106,8 @@ struct sk_instance {
     void* dJ = nullptr;
     void* dJop = nullptr;   // couplings as tensor-core operands (built on first recompute)
     bool jop_valid = false;
+    void* dJstage = nullptr;              // new couplings, checked before they replace dJ
+    unsigned long long* dflag = nullptr;  // result word of the device input checks
     cudaStream_t st = nullptr;
 };
 
@@ -147,6 +149,7 @@ struct sk_run {
     uint32_t chains = 0;
     int8_t* ds = nullptr;
     void* dh = nullptr;
+    int8_t* dstage = nullptr;  // start spins from the host, checked before use
     uint32_t* dacc = nullptr;
     unsigned long long* dwork = nullptr;
     double* drecE = nullptr;
@@ -168,49 +171,48 @@ struct sk_run {
 
 namespace {
 
-sk_status validate_couplings(uint32_t N, uint32_t kind, const void* J) {
-    if (kind == SK_J_PM1) {
-        const int8_t* a = static_cast<const int8_t*>(J);
-        for (uint32_t i = 0; i < N; ++i) {
-            if (a[static_cast<size_t>(i) * N + i] != 0)
-                return fail(SK_ERR_INVALID_ARG, "J[%u][%u] != 0 (diagonal must be zero)", i, i);
-            for (uint32_t j = 0; j < N; ++j) {
-                const int8_t v = a[static_cast<size_t>(i) * N + j];
-                if (v < -1 || v > 1)
-                    return fail(SK_ERR_INVALID_ARG, "J[%u][%u] = %d is not in {-1,0,1}", i, j, v);
-                if (v != a[static_cast<size_t>(j) * N + i])
-                    return fail(SK_ERR_INVALID_ARG, "J is not symmetric at (%u,%u)", i, j);
-            }
-        }
-    } else {
-        const float* a = static_cast<const float*>(J);
-        for (uint32_t i = 0; i < N; ++i) {
-            if (a[static_cast<size_t>(i) * N + i] != 0.0f)
-                return fail(SK_ERR_INVALID_ARG, "J[%u][%u] != 0 (diagonal must be zero)", i, i);
-            for (uint32_t j = 0; j < N; ++j) {
-                const float v = a[static_cast<size_t>(i) * N + j];
-                if (!std::isfinite(v)) return fail(SK_ERR_INVALID_ARG, "J[%u][%u] is not finite", i, j);
-                if (v != a[static_cast<size_t>(j) * N + i])
-                    return fail(SK_ERR_INVALID_ARG, "J is not symmetric at (%u,%u)", i, j);
-            }
-        }
-    }
+// Reads the result word of a device input check (synchronises the stream).
+sk_status read_flag(sk_instance* in, unsigned long long* out) {
+    SK_CU(cudaMemcpyAsync(out, in->dflag, sizeof(*out), cudaMemcpyDeviceToHost, in->st));
+    SK_CU(cudaStreamSynchronize(in->st));
     return SK_OK;
 }
 
-sk_status upload_couplings(sk_instance* in, const void* J, uint32_t mem) {
+// Copies couplings (host or device, N x N) into the padded device layout and
+// checks them on the device: zero diagonal, entries in {-1,0,1} (+-J) or
+// finite (Gaussian), symmetry.  A new instance takes them directly; an
+// existing one receives them in a staging copy first, so that couplings that
+// fail the check leave the instance unchanged.
+sk_status upload_couplings(sk_instance* in, const void* J, uint32_t mem, bool fresh) {
     const size_t b = jbytes(in->kind);
-    in->jop_valid = false;
-    if (mem == SK_MEM_HOST) {
-        sk_status s = validate_couplings(in->N, in->kind, J);
-        if (s != SK_OK) return s;
-    } else if (mem != SK_MEM_DEVICE) {
+    const size_t bytes = static_cast<size_t>(in->Npad) * in->Npad * b;
+    if (mem != SK_MEM_HOST && mem != SK_MEM_DEVICE)
         return fail(SK_ERR_INVALID_ARG, "mem must be SK_MEM_HOST or SK_MEM_DEVICE");
+    void* dst = in->dJ;
+    if (!fresh) {
+        if (!in->dJstage) {
+            sk_status s = dalloc(&in->dJstage, bytes);
+            if (s != SK_OK) return s;
+        }
+        dst = in->dJstage;
     }
-    SK_CU(cudaMemsetAsync(in->dJ, 0, static_cast<size_t>(in->Npad) * in->Npad * b, in->st));
-    SK_CU(cudaMemcpy2DAsync(in->dJ, in->Npad * b, J, in->N * b, in->N * b, in->N, cudaMemcpyDefault,
-                            in->st));
-    if (mem == SK_MEM_HOST) SK_CU(cudaStreamSynchronize(in->st));
+    if (in->N != in->Npad) SK_CU(cudaMemsetAsync(dst, 0, bytes, in->st));
+    SK_CU(cudaMemcpy2DAsync(dst, in->Npad * b, J, in->N * b, in->N * b, in->N, cudaMemcpyDefault, in->st));
+    SK_CU(sk::launch_check_couplings(dst, in->kind, in->N, in->Npad, in->dflag, in->st));
+    unsigned long long f = 0;
+    sk_status s = read_flag(in, &f);
+    if (s != SK_OK) return s;
+    if (f != ~0ull) {
+        const unsigned code = static_cast<unsigned>(f & 3u);
+        const unsigned i = static_cast<unsigned>((f >> 18) & 0xFFFFu), j = static_cast<unsigned>((f >> 2) & 0xFFFFu);
+        if (code == 1) return fail(SK_ERR_INVALID_ARG, "J[%u][%u] != 0 (diagonal must be zero)", i, j);
+        if (code == 2)
+            return fail(SK_ERR_INVALID_ARG, in->kind == SK_J_PM1 ? "J[%u][%u] is not in {-1,0,1}"
+                                                                 : "J[%u][%u] is not finite", i, j);
+        return fail(SK_ERR_INVALID_ARG, "J is not symmetric at (%u,%u)", i, j);
+    }
+    if (!fresh) SK_CU(cudaMemcpyAsync(in->dJ, dst, bytes, cudaMemcpyDeviceToDevice, in->st));
+    in->jop_valid = false;
     return SK_OK;
 }
 
@@ -226,22 +228,26 @@ sk_status check_run_error(sk_run* r) {
 sk_status init_state(sk_run* r, const int8_t* spins, uint32_t mem) {
     sk_instance* in = r->inst;
     const int8_t* dinit = nullptr;
-    int8_t* tmp = nullptr;
     if (spins) {
+        const size_t n = static_cast<size_t>(r->chains) * in->N;
         if (mem == SK_MEM_DEVICE) {
             dinit = spins;
-        } else if (mem == SK_MEM_HOST) {
-            const size_t n = static_cast<size_t>(r->chains) * in->N;
-            for (size_t i = 0; i < n; ++i)
-                if (spins[i] != 1 && spins[i] != -1)
-                    return fail(SK_ERR_INVALID_ARG, "initial spin %zu is %d, not +-1", i, spins[i]);
-            sk_status s = dalloc(&tmp, n);
-            if (s != SK_OK) return s;
-            SK_CU(cudaMemcpyAsync(tmp, spins, n, cudaMemcpyHostToDevice, in->st));
-            dinit = tmp;
+        } else if (mem == SK_MEM_HOST) {  // through the run's staging buffer
+            if (!r->dstage) {
+                sk_status s = dalloc(&r->dstage, n);
+                if (s != SK_OK) return s;
+            }
+            SK_CU(cudaMemcpyAsync(r->dstage, spins, n, cudaMemcpyHostToDevice, in->st));
+            dinit = r->dstage;
         } else {
             return fail(SK_ERR_INVALID_ARG, "init_mem must be SK_MEM_HOST or SK_MEM_DEVICE");
         }
+        // checked on the device before anything of the run is written
+        SK_CU(sk::launch_check_spins(dinit, n, in->dflag, in->st));
+        unsigned long long f = 0;
+        sk_status s = read_flag(in, &f);
+        if (s != SK_OK) return s;
+        if (f != ~0ull) return fail(SK_ERR_INVALID_ARG, "initial spin %llu is not +-1", f >> 2);
     }
     SK_CU(cudaMemsetAsync(r->dstep, 0, sizeof(uint64_t), in->st));
     SK_CU(cudaMemsetAsync(r->derr, 0, sizeof(int), in->st));
@@ -257,10 +263,6 @@ sk_status init_state(sk_run* r, const int8_t* spins, uint32_t mem) {
     SK_CU(sk::launch_init(&r->job, dinit, r->chains, in->N, in->Npad, in->kind, in->st));
     if (r->dstats) SK_CU(cudaMemsetAsync(r->dstats, 0, 6 * sizeof(unsigned long long), in->st));
     r->n_recomputes = 0;
-    if (tmp) {
-        SK_CU(cudaStreamSynchronize(in->st));
-        cudaFree(tmp);
-    }
     r->step = 0;
     return SK_OK;
 }
@@ -280,6 +282,7 @@ void free_run_buffers(sk_run* r) {
     cudaFree(r->dSop);
     cudaFree(r->ddE);
     cudaFree(r->dstats);
+    cudaFree(r->dstage);
 }
 
 // Operand buffers of the tensor-core recompute, allocated on first use.
@@ -344,9 +347,11 @@ sk_status sk_create_instance(uint32_t N, uint32_t kind, const void* couplings, u
     in->scale = scale;
     in->st = static_cast<cudaStream_t>(stream);
     s = dalloc(&in->dJ, static_cast<size_t>(in->Npad) * in->Npad * jbytes(kind));
-    if (s == SK_OK) s = upload_couplings(in, couplings, mem);
+    if (s == SK_OK) s = dalloc(&in->dflag, sizeof(unsigned long long));
+    if (s == SK_OK) s = upload_couplings(in, couplings, mem, true);
     if (s != SK_OK) {
         cudaFree(in->dJ);
+        cudaFree(in->dflag);
         delete in;
         return s;
     }
@@ -356,7 +361,7 @@ sk_status sk_create_instance(uint32_t N, uint32_t kind, const void* couplings, u
 
 sk_status sk_set_couplings(sk_instance* in, const void* couplings, uint32_t mem) {
     if (!in || !couplings) return fail(SK_ERR_INVALID_ARG, "NULL argument");
-    return upload_couplings(in, couplings, mem);
+    return upload_couplings(in, couplings, mem, false);
 }
 
 sk_status sk_destroy_instance(sk_instance* in) {
@@ -364,6 +369,8 @@ sk_status sk_destroy_instance(sk_instance* in) {
     cudaStreamSynchronize(in->st);
     cudaFree(in->dJ);
     cudaFree(in->dJop);
+    cudaFree(in->dJstage);
+    cudaFree(in->dflag);
     delete in;
     return SK_OK;
 }

@@ -87,6 +87,13 @@ cudaError_t launch_step(const JobDev* jobs, const WorkItem* items, uint32_t n_it
 int step_kernel_occupancy(int cls, uint32_t warps_per_cta, size_t per_chain_bytes);
 cudaError_t launch_init(const JobDev* job, const int8_t* init, uint32_t chains, uint32_t N,
                         uint32_t Npad, uint32_t kind, cudaStream_t st);
+// Device checks of host-supplied inputs: *flag receives the smallest
+// (position << 2 | code) of a violation, all ones when there is none
+// (couplings: position i * 2^16 + j, code 1 diagonal, 2 range or not finite,
+// 3 asymmetric; spins: position = index, code 1 not +-1).
+cudaError_t launch_check_couplings(const void* J, uint32_t kind, uint32_t N, uint32_t Npad,
+                                   unsigned long long* flag, cudaStream_t st);
+cudaError_t launch_check_spins(const int8_t* s, uint64_t n, unsigned long long* flag, cudaStream_t st);
 cudaError_t launch_energy(const void* J, uint32_t kind, uint32_t N, uint32_t Npad, double scale,
                           const int8_t* spins, uint32_t count, double* out, cudaStream_t st);
 

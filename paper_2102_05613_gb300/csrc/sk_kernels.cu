@@ -2,6 +2,8 @@
 // dispatch of the step kernel (sk_step.cuh, instantiated per coupling type
 // and rule in sk_step_*.cu).
 #include <cuda_runtime.h>
+#include <algorithm>
+#include <type_traits>
 #include <stdint.h>
 
 #include "sk_device.cuh"
@@ -49,74 +51,162 @@ __global__ void bump_steps(const JobDev* __restrict__ jobs, uint32_t n_jobs, uin
     }
 }
 
-// Start state: spins from `init` (chains x N, +-1) or Philox domain 1
-// (128 spins per block, bit set -> -1); fields h_i = sum_j J_ji s_j for
-// kInitChains chains per CTA (each J element read once for all of them),
-// exact integers for +-J, compensated (Kahan) float sums for Gaussian J.
-constexpr uint32_t kInitChains = 8;
+// Start spins: from `init` (chains x N, +-1) or Philox domain 1 (128 spins
+// per block, bit set -> -1), written padded to the chain's row (padding 0);
+// each thread writes 4 spins.  Also clears the per-chain counters.
+__global__ void spins_kernel(JobDev jb, const int8_t* __restrict__ init) {
+    const uint32_t npad = jb.Npad, N = jb.N;
+    const uint32_t words = npad / 4;  // 4 spins per thread
+    const uint64_t total = static_cast<uint64_t>(jb.chains) * words;
+    const uint32_t k0 = static_cast<uint32_t>(jb.seed), k1 = static_cast<uint32_t>(jb.seed >> 32);
+    const uint32_t c3 = (1u << 24) | (jb.stream & 0xFFFFFFu);
+    for (uint64_t x = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; x < total;
+         x += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        const uint32_t chain = static_cast<uint32_t>(x / words);
+        const uint32_t i0 = static_cast<uint32_t>(x % words) * 4u;
+        uint32_t packed = 0;
+        if (init) {
+            for (uint32_t k = 0; k < 4u; ++k) {
+                const uint32_t i = i0 + k;
+                const int v = i < N ? init[static_cast<size_t>(chain) * N + i] : 0;
+                packed |= (static_cast<uint32_t>(v) & 0xFFu) << (8u * k);
+            }
+        } else {
+            const uint4 r = philox4x32_10(make_uint4(i0 / 128u, 0u, chain, c3), k0, k1);
+            const uint32_t wv[4] = {r.x, r.y, r.z, r.w};
+            const uint32_t w = wv[(i0 % 128u) / 32u];
+            for (uint32_t k = 0; k < 4u; ++k) {
+                const uint32_t i = i0 + k, b = (i % 128u) & 31u;
+                const int v = i < N ? (((w >> b) & 1u) ? -1 : 1) : 0;
+                packed |= (static_cast<uint32_t>(v) & 0xFFu) << (8u * k);
+            }
+        }
+        reinterpret_cast<uint32_t*>(jb.s)[static_cast<size_t>(chain) * words + i0 / 4u] = packed;
+        if (i0 == 0) {
+            jb.acc_run[chain] = 0;
+            jb.work[2 * static_cast<size_t>(chain)] = 0;
+            jb.work[2 * static_cast<size_t>(chain) + 1] = 0;
+        }
+    }
+}
+
+// Local fields h[c][i] = sum_j J_ij s[c][j] of every chain, a register-tiled
+// product: a CTA computes 128 sites x 64 chains, a thread 8 sites x 4
+// chains, with j in chunks of 32 staged through shared memory (J is
+// symmetric, so rows j of J give the columns needed).  +-J: exact int32.
+// Gaussian: fp32 sums per chunk of 32 terms, added into the running total
+// (blocked summation; rounding error ~ (32 + N/32) 2^-24 sum |J|).
+constexpr uint32_t kFI = 128, kFC = 64, kFJ = 32;
 
 template <typename JT>
-__global__ void __launch_bounds__(256) init_kernel(JobDev jb, const int8_t* __restrict__ init) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    int8_t* s = reinterpret_cast<int8_t*>(sm);  // [kInitChains][npad]
-    const uint32_t N = jb.N, npad = jb.Npad;
-    const uint32_t c0 = blockIdx.x * kInitChains;
-    const uint32_t nc = min(kInitChains, jb.chains - c0);
-    for (uint32_t c = 0; c < nc; ++c) {
-        const uint32_t chain = c0 + c;
-        int8_t* sc = s + static_cast<size_t>(c) * npad;
-        if (init) {
-            for (uint32_t i = threadIdx.x; i < npad; i += blockDim.x)
-                sc[i] = i < N ? init[static_cast<size_t>(chain) * N + i] : 0;
-        } else {
-            const uint32_t k0 = static_cast<uint32_t>(jb.seed), k1 = static_cast<uint32_t>(jb.seed >> 32);
-            const uint32_t c3 = (1u << 24) | (jb.stream & 0xFFFFFFu);
-            for (uint32_t b = threadIdx.x; b * 128u < npad; b += blockDim.x) {
-                const uint4 r = philox4x32_10(make_uint4(b, 0u, chain, c3), k0, k1);
-                const uint32_t wv[4] = {r.x, r.y, r.z, r.w};
-                for (uint32_t k = 0; k < 128u && b * 128u + k < npad; ++k) {
-                    const uint32_t i = b * 128u + k;
-                    sc[i] = i < N ? (((wv[k >> 5] >> (k & 31)) & 1u) ? -1 : 1) : 0;
+__global__ void __launch_bounds__(256) fields_kernel(const JT* __restrict__ J, const int8_t* __restrict__ S,
+                                                     void* __restrict__ Hout, uint32_t npad, uint32_t chains) {
+    using A = typename dev::Types<JT>::H;  // int for +-J, float for Gaussian
+    __shared__ __align__(16) A Js[kFJ][kFI];
+    __shared__ __align__(16) A Ss[kFJ][kFC];
+    const uint32_t tid = threadIdx.x;
+    const uint32_t tx = tid & 15u, ty = tid >> 4;  // sites 4tx..4tx+3 and 64+4tx..; chains 4ty..4ty+3
+    const uint32_t i0 = blockIdx.x * kFI, c0 = blockIdx.y * kFC;
+    A acc[4][8], tot[4][8];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[c][k] = tot[c][k] = A(0);
+    for (uint32_t j0 = 0; j0 < npad; j0 += kFJ) {
+        // J rows j0..j0+31, sites i0..i0+127
+        for (uint32_t e = tid; e < kFJ * kFI / 4u; e += 256u) {
+            const uint32_t jj = e / (kFI / 4u), ii = (e % (kFI / 4u)) * 4u;
+            const uint32_t i = i0 + ii;
+            A v[4] = {A(0), A(0), A(0), A(0)};
+            if (i < npad) {  // npad is a multiple of 32: all four are inside
+                const JT* src = J + static_cast<size_t>(j0 + jj) * npad + i;
+                if constexpr (sizeof(JT) == 1) {
+                    const uint32_t w = __ldg(reinterpret_cast<const unsigned int*>(src));
+                    v[0] = dev::sbyte(w, 0); v[1] = dev::sbyte(w, 1); v[2] = dev::sbyte(w, 2); v[3] = dev::sbyte(w, 3);
+                } else {
+                    const float4 f = __ldg(reinterpret_cast<const float4*>(src));
+                    v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
                 }
             }
+            Js[jj][ii] = v[0]; Js[jj][ii + 1] = v[1]; Js[jj][ii + 2] = v[2]; Js[jj][ii + 3] = v[3];
+        }
+        // spins of chains c0..c0+63 at j0..j0+31, transposed
+        for (uint32_t e = tid; e < kFC * kFJ / 4u; e += 256u) {
+            const uint32_t cc = e / (kFJ / 4u), jj = (e % (kFJ / 4u)) * 4u;
+            const uint32_t c = c0 + cc;
+            uint32_t w = 0;
+            if (c < chains) w = __ldg(reinterpret_cast<const unsigned int*>(S + static_cast<size_t>(c) * npad + j0 + jj));
+#pragma unroll
+            for (uint32_t k = 0; k < 4u; ++k) Ss[jj + k][cc] = static_cast<A>(dev::sbyte(w, k));
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (uint32_t jj = 0; jj < kFJ; ++jj) {
+            A a[8], b[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                a[k] = Js[jj][4 * tx + k];
+                a[4 + k] = Js[jj][64 + 4 * tx + k];
+                b[k] = Ss[jj][4 * ty + k];
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+                for (int k = 0; k < 8; ++k) acc[c][k] += b[c] * a[k];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                tot[c][k] += acc[c][k];
+                acc[c][k] = A(0);
+            }
+    }
+    A* H = static_cast<A*>(Hout);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const uint32_t chain = c0 + 4u * ty + c;
+        if (chain >= chains) continue;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const uint32_t i = i0 + 64u * half + 4u * tx;
+            if (i < npad)
+                *reinterpret_cast<typename std::conditional<sizeof(JT) == 1, int4, float4>::type*>(
+                    H + static_cast<size_t>(chain) * npad + i) = {tot[c][4 * half], tot[c][4 * half + 1],
+                                                                  tot[c][4 * half + 2], tot[c][4 * half + 3]};
         }
     }
-    __syncthreads();
-    for (uint32_t c = 0; c < nc; ++c)
-        for (uint32_t i = threadIdx.x; i < npad; i += blockDim.x)
-            jb.s[static_cast<size_t>(c0 + c) * npad + i] = s[static_cast<size_t>(c) * npad + i];
-    const JT* J = static_cast<const JT*>(jb.J);
-    for (uint32_t i = threadIdx.x; i < npad; i += blockDim.x) {
-        if constexpr (sizeof(JT) == 1) {
-            int acc[kInitChains] = {};
-            for (uint32_t j = 0; j < N; ++j) {
-                const int v = J[static_cast<size_t>(j) * npad + i];
-#pragma unroll
-                for (uint32_t c = 0; c < kInitChains; ++c) acc[c] += v * s[c * npad + j];
-            }
-            for (uint32_t c = 0; c < nc; ++c)
-                static_cast<int*>(jb.h)[static_cast<size_t>(c0 + c) * npad + i] = acc[c];
-        } else {
-            float sum[kInitChains] = {}, comp[kInitChains] = {};
-            for (uint32_t j = 0; j < N; ++j) {
-                const float v = J[static_cast<size_t>(j) * npad + i];
-#pragma unroll
-                for (uint32_t c = 0; c < kInitChains; ++c) {
-                    const float y = (s[c * npad + j] > 0 ? v : -v) - comp[c];
-                    const float tsum = sum[c] + y;
-                    comp[c] = (tsum - sum[c]) - y;
-                    sum[c] = tsum;
-                }
-            }
-            for (uint32_t c = 0; c < nc; ++c)
-                static_cast<float*>(jb.h)[static_cast<size_t>(c0 + c) * npad + i] = sum[c];
-        }
+}
+
+// Validation of host-supplied inputs on the device.  *flag (initialised to
+// all ones) receives the smallest (position << 2 | code) of a violation.
+//   couplings: code 1 diagonal entry != 0, 2 entry outside {-1,0,1} (+-J) or
+//   not finite (Gaussian), 3 J_ij != J_ji; position i * 2^16 + j.
+template <typename JT>
+__global__ void check_couplings_kernel(const JT* __restrict__ J, uint32_t N, uint32_t npad,
+                                       unsigned long long* __restrict__ flag) {
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
+    if (j >= N) return;
+    const JT a = J[static_cast<size_t>(i) * npad + j];
+    const JT b = J[static_cast<size_t>(j) * npad + i];
+    unsigned code = 0;
+    if (i == j && a != JT(0)) code = 1;
+    else if constexpr (sizeof(JT) == 1) {
+        if (a < JT(-1) || a > JT(1)) code = 2;
+        else if (a != b) code = 3;
+    } else {
+        if (!isfinite(a)) code = 2;
+        else if (a != b) code = 3;
     }
-    if (threadIdx.x < nc) {
-        const uint32_t chain = c0 + threadIdx.x;
-        jb.acc_run[chain] = 0;
-        jb.work[2 * static_cast<size_t>(chain)] = 0;
-        jb.work[2 * static_cast<size_t>(chain) + 1] = 0;
+    if (code) atomicMin(flag, ((static_cast<unsigned long long>(i) << 16 | j) << 2) | code);
+}
+//   spins: code 1 for a value other than +-1; position = index.
+__global__ void check_spins_kernel(const int8_t* __restrict__ s, uint64_t n, unsigned long long* __restrict__ flag) {
+    for (uint64_t x = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; x < n;
+         x += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        const int v = s[x];
+        if (v != 1 && v != -1) atomicMin(flag, (static_cast<unsigned long long>(x) << 2) | 1ull);
     }
 }
 
@@ -220,18 +310,36 @@ int step_kernel_occupancy(int cls, uint32_t W, size_t per_chain) {
 cudaError_t launch_init(const JobDev* job, const int8_t* init, uint32_t chains, uint32_t N,
                         uint32_t Npad, uint32_t kind, cudaStream_t st) {
     (void)N;
-    const uint32_t blocks = (chains + kInitChains - 1) / kInitChains;
-    const size_t sm = static_cast<size_t>(kInitChains) * Npad;
-    cudaError_t e;
-    if (kind == 0) {
-        e = cudaFuncSetAttribute(init_kernel<int8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
-        if (e != cudaSuccess) return e;
-        init_kernel<int8_t><<<blocks, 256, sm, st>>>(*job, init);
-    } else {
-        e = cudaFuncSetAttribute(init_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
-        if (e != cudaSuccess) return e;
-        init_kernel<float><<<blocks, 256, sm, st>>>(*job, init);
-    }
+    const uint64_t words = static_cast<uint64_t>(chains) * (Npad / 4);
+    const uint32_t blocks = static_cast<uint32_t>(std::min<uint64_t>((words + 255) / 256, 152ull * 64));
+    spins_kernel<<<blocks, 256, 0, st>>>(*job, init);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const dim3 grid((Npad + kFI - 1) / kFI, (chains + kFC - 1) / kFC);
+    if (kind == 0)
+        fields_kernel<int8_t><<<grid, 256, 0, st>>>(static_cast<const int8_t*>(job->J), job->s, job->h, Npad, chains);
+    else
+        fields_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float*>(job->J), job->s, job->h, Npad, chains);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_couplings(const void* J, uint32_t kind, uint32_t N, uint32_t Npad,
+                                   unsigned long long* flag, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(flag, 0xFF, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((N + 255) / 256, N);
+    if (kind == 0)
+        check_couplings_kernel<int8_t><<<grid, 256, 0, st>>>(static_cast<const int8_t*>(J), N, Npad, flag);
+    else
+        check_couplings_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float*>(J), N, Npad, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_spins(const int8_t* s, uint64_t n, unsigned long long* flag, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(flag, 0xFF, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    const uint32_t blocks = static_cast<uint32_t>(std::min<uint64_t>((n + 255) / 256, 152ull * 64));
+    if (blocks) check_spins_kernel<<<blocks, 256, 0, st>>>(s, n, flag);
     return cudaGetLastError();
 }
 

@@ -334,6 +334,73 @@ def test_invalid_arguments_fail_loudly():
         sk.Instance(np.zeros((8193, 8193), dtype=np.int8))
 
 
+@pytest.mark.parametrize("N,chains", [(700, 100), (64, 65), (2048, 130)])
+def test_start_fields(N, chains):
+    """Fields of the start state (register-tiled h = J s over ragged site and
+    chain tiles): +-J exact, Gaussian within the blocked-summation bound of
+    fp32, (32 + N/32) 2^-24 sum_j |J_ij|."""
+    need_gpu()
+    init = inputs.initial_spins(chains, N, 3)
+    for J in (inputs.couplings_pm1(N, 5), inputs.couplings_gauss(N, 6)):
+        inst = sk.Instance(J)
+        for start in (init, None):
+            run = sk.Run(inst, chains=chains, K=8, init=start, seed=12)
+            spins, h, _ = run.state(fields=True)
+            if start is not None:
+                assert np.array_equal(spins, init)
+            else:
+                for c in (0, chains - 1):
+                    assert np.array_equal(spins[c], oracle.init_spins(12, 0, c, N))
+            exact = J.astype(np.float64) @ spins.T.astype(np.float64)
+            if J.dtype == np.int8:
+                assert np.array_equal(h, exact.T.astype(np.int64))
+            else:
+                bound = (32 + N / 32) * 2.0 ** -24 * np.abs(J).astype(np.float64).sum(axis=1)
+                assert (np.abs(h - exact.T) <= bound[None, :]).all()
+            run.close()
+        inst.close()
+
+
+def test_rejected_inputs_change_nothing():
+    """Couplings or start spins that fail the device checks leave the instance
+    and the run as they were: the chain continues bit-exactly."""
+    need_gpu()
+    N, K, chains = 48, 8, 4
+    J = inputs.couplings_pm1(N, 31)
+    init = inputs.initial_spins(chains, N, 32)
+    inst = sk.Instance(J)
+    run = sk.Run(inst, chains=chains, K=K, beta=0.7, seed=3, init=init, trace_chains=chains,
+                 trace_steps=400)
+    run.advance(200)
+    cases = []
+    b = J.copy(); b[3, 3] = 1; cases.append((b, "diagonal"))
+    b = J.copy(); b[5, 9] = 2; b[9, 5] = 2; cases.append((b, "not in"))
+    b = J.copy(); b[7, 2] = -b[7, 2]; cases.append((b, "symmetric at (2,7)"))
+    for bad, what in cases:
+        with pytest.raises(sk.SKError) as e:
+            inst.set_couplings(bad)
+        assert e.value.status == sk.SK_ERR_INVALID_ARG and what in str(e.value), (what, str(e.value))
+    badS = init.copy(); badS[2, 17] = 0
+    with pytest.raises(sk.SKError) as e:
+        run.reset(badS)
+    assert e.value.status == sk.SK_ERR_INVALID_ARG and str(2 * N + 17) in str(e.value)
+    run.advance(200)
+    tr = run.trace()
+    spins, h, step = run.state(fields=True)
+    o = oracle.run(J, K=K, beta=0.7, seed=3, chains=chains, init=init, steps=400, trace=True)
+    assert step == 400
+    assert np.array_equal(tr, o["trace"]) and np.array_equal(spins, o["spins"])
+    assert np.array_equal(h, (J.astype(np.int64) @ spins.T.astype(np.int64)).T)
+    Jg = inputs.couplings_gauss(N, 33)
+    ig = sk.Instance(Jg)
+    b = Jg.copy(); b[4, 6] = np.nan; b[6, 4] = np.nan
+    with pytest.raises(sk.SKError) as e:
+        ig.set_couplings(b)
+    assert "not finite" in str(e.value)
+    ig.set_couplings(Jg * 0.5)  # a valid replacement is taken
+    run.close(); inst.close(); ig.close()
+
+
 def test_largest_n():
     need_gpu()
     N, K, chains, steps = 8192, 64, 2, 60
