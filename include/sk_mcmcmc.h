@@ -137,7 +137,17 @@ typedef struct {
 /*
  * mcmcmc_create: allocates the chains' state (spins, local fields, records)
  * and initialises it: spins from init_spins or from Philox domain 1, fields
- * h = J s.  The run is at step 0.  Asynchronous on the instance's stream.
+ * h = J s computed on the tensor cores (exact for +-J; for Gaussian
+ * couplings J is split into three bf16 terms, which represent it exactly,
+ * and the products are summed in FP32).  Host start spins are copied to a
+ * per-run staging buffer and checked on the device (each must be +-1;
+ * SK_ERR_INVALID_ARG names the first offending index) before anything of the
+ * run is written.  The run is at step 0.  Device memory: 5 bytes per spin
+ * per chain for spins and fields, plus the tensor-core spin operand (1 byte
+ * per spin for +-J, 2 for Gaussian), 1 byte per spin for a host start, the
+ * records, and once per instance the couplings' operand (Npad^2 bytes for
+ * +-J, 6 Npad^2 for Gaussian).  Synchronises the stream when init_spins is
+ * given (for the check); otherwise asynchronous on the instance's stream.
  */
 sk_status mcmcmc_create(sk_instance* inst, const sk_run_params* p, sk_run** out);
 
@@ -407,8 +417,9 @@ typedef struct {
  * CUDA stream on the current device.  It runs the admitted jobs in quanta of
  * `quantum_steps` steps: between quanta it retires finished jobs (final spins
  * and energies copied back, device memory released) and admits queued jobs,
- * first in first out, while their device footprint (couplings unless already
- * resident, 5 bytes per spin per chain, per-chain counters) fits
+ * first in first out, while their device footprint (couplings and their
+ * tensor-core operand unless already resident, the run's memory as listed
+ * under mcmcmc_create) fits
  * `budget_bytes`; each quantum advances every admitted job in one launch per
  * kernel class.  A job's result does not depend on the other jobs it shared
  * launches with (counter-based draws).  The paper's problem statement

@@ -108,6 +108,12 @@ struct sk_instance {
     bool jop_valid = false;
     void* dJstage = nullptr;              // new couplings, checked before they replace dJ
     unsigned long long* dflag = nullptr;  // result word of the device input checks
+    // host inputs are copied and checked on a side stream, so that the check
+    // does not wait for the compute queued on st; events order the staging
+    // buffers between the two streams
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_side = nullptr;   // side: copy and check done
+    cudaEvent_t ev_jfree = nullptr;  // st: dJstage copied into dJ
     cudaStream_t st = nullptr;
 };
 
@@ -150,6 +156,7 @@ struct sk_run {
     int8_t* ds = nullptr;
     void* dh = nullptr;
     int8_t* dstage = nullptr;  // start spins from the host, checked before use
+    cudaEvent_t ev_sfree = nullptr;  // st: the start kernel has read dstage
     uint32_t* dacc = nullptr;
     unsigned long long* dwork = nullptr;
     double* drecE = nullptr;
@@ -171,10 +178,11 @@ struct sk_run {
 
 namespace {
 
-// Reads the result word of a device input check (synchronises the stream).
-sk_status read_flag(sk_instance* in, unsigned long long* out) {
-    SK_CU(cudaMemcpyAsync(out, in->dflag, sizeof(*out), cudaMemcpyDeviceToHost, in->st));
-    SK_CU(cudaStreamSynchronize(in->st));
+// Reads the result word of a device input check run on stream st
+// (synchronises st).
+sk_status read_flag(sk_instance* in, cudaStream_t st, unsigned long long* out) {
+    SK_CU(cudaMemcpyAsync(out, in->dflag, sizeof(*out), cudaMemcpyDeviceToHost, st));
+    SK_CU(cudaStreamSynchronize(st));
     return SK_OK;
 }
 
@@ -182,7 +190,9 @@ sk_status read_flag(sk_instance* in, unsigned long long* out) {
 // checks them on the device: zero diagonal, entries in {-1,0,1} (+-J) or
 // finite (Gaussian), symmetry.  A new instance takes them directly; an
 // existing one receives them in a staging copy first, so that couplings that
-// fail the check leave the instance unchanged.
+// fail the check leave the instance unchanged.  Host couplings go through the
+// side stream (the check then does not wait for work queued on st); device
+// couplings, which work on st may still be producing, through st.
 sk_status upload_couplings(sk_instance* in, const void* J, uint32_t mem, bool fresh) {
     const size_t b = jbytes(in->kind);
     const size_t bytes = static_cast<size_t>(in->Npad) * in->Npad * b;
@@ -196,11 +206,14 @@ sk_status upload_couplings(sk_instance* in, const void* J, uint32_t mem, bool fr
         }
         dst = in->dJstage;
     }
-    if (in->N != in->Npad) SK_CU(cudaMemsetAsync(dst, 0, bytes, in->st));
-    SK_CU(cudaMemcpy2DAsync(dst, in->Npad * b, J, in->N * b, in->N * b, in->N, cudaMemcpyDefault, in->st));
-    SK_CU(sk::launch_check_couplings(dst, in->kind, in->N, in->Npad, in->dflag, in->st));
+    const bool via_side = !fresh && mem == SK_MEM_HOST;
+    cudaStream_t cs = via_side ? in->side : in->st;
+    if (via_side) SK_CU(cudaStreamWaitEvent(cs, in->ev_jfree, 0));  // the last copy out of the stage is done
+    if (in->N != in->Npad) SK_CU(cudaMemsetAsync(dst, 0, bytes, cs));
+    SK_CU(cudaMemcpy2DAsync(dst, in->Npad * b, J, in->N * b, in->N * b, in->N, cudaMemcpyDefault, cs));
+    SK_CU(sk::launch_check_couplings(dst, in->kind, in->N, in->Npad, in->dflag, cs));
     unsigned long long f = 0;
-    sk_status s = read_flag(in, &f);
+    sk_status s = read_flag(in, cs, &f);
     if (s != SK_OK) return s;
     if (f != ~0ull) {
         const unsigned code = static_cast<unsigned>(f & 3u);
@@ -211,7 +224,10 @@ sk_status upload_couplings(sk_instance* in, const void* J, uint32_t mem, bool fr
                                                                  : "J[%u][%u] is not finite", i, j);
         return fail(SK_ERR_INVALID_ARG, "J is not symmetric at (%u,%u)", i, j);
     }
-    if (!fresh) SK_CU(cudaMemcpyAsync(in->dJ, dst, bytes, cudaMemcpyDeviceToDevice, in->st));
+    if (!fresh) {
+        SK_CU(cudaMemcpyAsync(in->dJ, dst, bytes, cudaMemcpyDeviceToDevice, in->st));
+        SK_CU(cudaEventRecord(in->ev_jfree, in->st));
+    }
     in->jop_valid = false;
     return SK_OK;
 }
@@ -225,6 +241,8 @@ sk_status check_run_error(sk_run* r) {
     return SK_OK;
 }
 
+sk_status ensure_recompute(sk_run* r);
+
 sk_status init_state(sk_run* r, const int8_t* spins, uint32_t mem) {
     sk_instance* in = r->inst;
     const int8_t* dinit = nullptr;
@@ -232,22 +250,28 @@ sk_status init_state(sk_run* r, const int8_t* spins, uint32_t mem) {
         const size_t n = static_cast<size_t>(r->chains) * in->N;
         if (mem == SK_MEM_DEVICE) {
             dinit = spins;
-        } else if (mem == SK_MEM_HOST) {  // through the run's staging buffer
+        } else if (mem == SK_MEM_HOST) {  // through the run's staging buffer, on the side stream
             if (!r->dstage) {
                 sk_status s = dalloc(&r->dstage, n);
                 if (s != SK_OK) return s;
             }
-            SK_CU(cudaMemcpyAsync(r->dstage, spins, n, cudaMemcpyHostToDevice, in->st));
+            SK_CU(cudaStreamWaitEvent(in->side, r->ev_sfree, 0));  // the last start has read the stage
+            SK_CU(cudaMemcpyAsync(r->dstage, spins, n, cudaMemcpyHostToDevice, in->side));
             dinit = r->dstage;
         } else {
             return fail(SK_ERR_INVALID_ARG, "init_mem must be SK_MEM_HOST or SK_MEM_DEVICE");
         }
         // checked on the device before anything of the run is written
-        SK_CU(sk::launch_check_spins(dinit, n, in->dflag, in->st));
+        cudaStream_t cs = mem == SK_MEM_HOST ? in->side : in->st;
+        SK_CU(sk::launch_check_spins(dinit, n, in->dflag, cs));
         unsigned long long f = 0;
-        sk_status s = read_flag(in, &f);
+        sk_status s = read_flag(in, cs, &f);
         if (s != SK_OK) return s;
         if (f != ~0ull) return fail(SK_ERR_INVALID_ARG, "initial spin %llu is not +-1", f >> 2);
+        if (mem == SK_MEM_HOST) {
+            SK_CU(cudaEventRecord(in->ev_side, in->side));
+            SK_CU(cudaStreamWaitEvent(in->st, in->ev_side, 0));
+        }
     }
     SK_CU(cudaMemsetAsync(r->dstep, 0, sizeof(uint64_t), in->st));
     SK_CU(cudaMemsetAsync(r->derr, 0, sizeof(int), in->st));
@@ -260,8 +284,18 @@ sk_status init_state(sk_run* r, const int8_t* spins, uint32_t mem) {
     if (r->dtrace)
         SK_CU(cudaMemsetAsync(r->dtrace, 0xff, static_cast<size_t>(r->p.trace_chains) * r->p.trace_steps * 4,
                               in->st));
-    SK_CU(sk::launch_init(&r->job, dinit, r->chains, in->N, in->Npad, in->kind, in->st));
-    if (r->dstats) SK_CU(cudaMemsetAsync(r->dstats, 0, 6 * sizeof(unsigned long long), in->st));
+    // spins, then the fields h = J s on the tensor cores (e4m3 for +-J:
+    // exact; three bf16 terms of J for Gaussian couplings: fp32 accumulation)
+    SK_CU(sk::launch_init(&r->job, dinit, r->chains, in->N, in->Npad, in->kind, in->st, false));
+    if (dinit == r->dstage && dinit) SK_CU(cudaEventRecord(r->ev_sfree, in->st));
+    {
+        sk_status s = ensure_recompute(r);
+        if (s != SK_OK) return s;
+        SK_CU(sk::launch_recompute(in->kind, r->ds, r->dh, nullptr, r->dSop, in->dJop, r->ddE, r->dstats,
+                                   r->derr, r->chains, in->Npad, 3, 3, in->scale, in->st));
+    }
+    SK_CU(cudaMemsetAsync(r->dstats, 0, 6 * sizeof(unsigned long long), in->st));
+    SK_CU(cudaMemsetAsync(r->ddE, 0, static_cast<size_t>(r->chains) * sizeof(double), in->st));
     r->n_recomputes = 0;
     r->step = 0;
     return SK_OK;
@@ -283,6 +317,7 @@ void free_run_buffers(sk_run* r) {
     cudaFree(r->ddE);
     cudaFree(r->dstats);
     cudaFree(r->dstage);
+    if (r->ev_sfree) cudaEventDestroy(r->ev_sfree);
 }
 
 // Operand buffers of the tensor-core recompute, allocated on first use.
@@ -348,10 +383,19 @@ sk_status sk_create_instance(uint32_t N, uint32_t kind, const void* couplings, u
     in->st = static_cast<cudaStream_t>(stream);
     s = dalloc(&in->dJ, static_cast<size_t>(in->Npad) * in->Npad * jbytes(kind));
     if (s == SK_OK) s = dalloc(&in->dflag, sizeof(unsigned long long));
+    if (s == SK_OK) {
+        cudaError_t e = cudaStreamCreateWithFlags(&in->side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&in->ev_side, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&in->ev_jfree, cudaEventDisableTiming);
+        if (e != cudaSuccess) s = fail(SK_ERR_CUDA, "stream/event creation: %s", cudaGetErrorString(e));
+    }
     if (s == SK_OK) s = upload_couplings(in, couplings, mem, true);
     if (s != SK_OK) {
         cudaFree(in->dJ);
         cudaFree(in->dflag);
+        if (in->ev_side) cudaEventDestroy(in->ev_side);
+        if (in->ev_jfree) cudaEventDestroy(in->ev_jfree);
+        if (in->side) cudaStreamDestroy(in->side);
         delete in;
         return s;
     }
@@ -367,10 +411,14 @@ sk_status sk_set_couplings(sk_instance* in, const void* couplings, uint32_t mem)
 sk_status sk_destroy_instance(sk_instance* in) {
     if (!in) return fail(SK_ERR_INVALID_ARG, "instance is NULL");
     cudaStreamSynchronize(in->st);
+    cudaStreamSynchronize(in->side);
     cudaFree(in->dJ);
     cudaFree(in->dJop);
     cudaFree(in->dJstage);
     cudaFree(in->dflag);
+    cudaEventDestroy(in->ev_side);
+    cudaEventDestroy(in->ev_jfree);
+    cudaStreamDestroy(in->side);
     delete in;
     return SK_OK;
 }
@@ -443,6 +491,8 @@ sk_status mcmcmc_create(sk_instance* in, const sk_run_params* p, sk_run** out) {
     if (s == SK_OK) s = dalloc(&r->dtrace, static_cast<size_t>(r->p.trace_chains) * r->p.trace_steps * 4);
     if (s == SK_OK) s = dalloc(&r->dstep, 8);
     if (s == SK_OK) s = dalloc(&r->derr, 4);
+    if (s == SK_OK && cudaEventCreateWithFlags(&r->ev_sfree, cudaEventDisableTiming) != cudaSuccess)
+        s = fail(SK_ERR_CUDA, "event creation failed");
     if (s == SK_OK && in->kind == SK_J_PM1) {
         const double be = r->p.beta * in->scale;
         std::vector<uint64_t> t = r->p.rule == SK_RULE_MCMCMC ? mcmcmc_table(be, in->N) : metropolis_table(be, in->N);
@@ -1156,14 +1206,20 @@ bool root_setup(JobDev& j, uint32_t K, double p_center) {
     return true;
 }
 uint64_t host_step(const sk_run* r) { return r->step; }
+// Device bytes of a run: spins and fields, per-chain counters, records, the
+// +-J table, the tensor-core spin operand and drift accumulator (the start
+// fields are computed on the tensor cores) and the host-start staging copy.
 size_t run_footprint(uint32_t N, uint32_t kind, uint32_t chains, uint64_t records) {
     const size_t np = pad_n(N);
     return static_cast<size_t>(chains) * np * 5 + static_cast<size_t>(chains) * 20 +
            records * (static_cast<size_t>(chains) * 12 + static_cast<size_t>(chains / 2) * 8) +
-           (kind == SK_J_PM1 ? (4 * static_cast<size_t>(N) + 5) * 8 : 0) + 4096;
+           (kind == SK_J_PM1 ? (4 * static_cast<size_t>(N) + 5) * 8 : 0) +
+           sk::recompute_s_bytes(kind, chains, static_cast<uint32_t>(np)) + static_cast<size_t>(chains) * 8 +
+           static_cast<size_t>(chains) * N + 4096;
 }
+// Device bytes of an instance: the couplings and their tensor-core operand.
 size_t instance_footprint(uint32_t N, uint32_t kind) {
     const size_t np = pad_n(N);
-    return np * np * jbytes(kind);
+    return np * np * jbytes(kind) + sk::recompute_j_bytes(kind, static_cast<uint32_t>(np));
 }
 }  // namespace sk

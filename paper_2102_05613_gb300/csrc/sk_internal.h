@@ -85,8 +85,10 @@ cudaError_t launch_step(const JobDev* jobs, const WorkItem* items, uint32_t n_it
                         uint32_t per_chain_bytes, uint32_t grid, int cls, uint32_t n_jobs,
                         bool bump, cudaStream_t st);
 int step_kernel_occupancy(int cls, uint32_t warps_per_cta, size_t per_chain_bytes);
+// Start state: spins from `init` (device, chains x N) or the Philox start,
+// then (with_fields) h = J s on the CUDA cores (register-tiled fp32 / int32).
 cudaError_t launch_init(const JobDev* job, const int8_t* init, uint32_t chains, uint32_t N,
-                        uint32_t Npad, uint32_t kind, cudaStream_t st);
+                        uint32_t Npad, uint32_t kind, cudaStream_t st, bool with_fields = true);
 // Device checks of host-supplied inputs: *flag receives the smallest
 // (position << 2 | code) of a violation, all ones when there is none
 // (couplings: position i * 2^16 + j, code 1 diagonal, 2 range or not finite,
@@ -100,7 +102,8 @@ cudaError_t launch_energy(const void* J, uint32_t kind, uint32_t N, uint32_t Npa
 // Tensor-core field recompute (sk_recompute.cu).  Operand buffers: J as
 // e4m3 (+-J, npad^2 bytes) or three bf16 terms (Gaussian, 3 npad^2 x 2
 // bytes); spins as e4m3 / bf16 (chains x npad).  mode 0 checks the maintained
-// fields, 1 also replaces them (resync), 2 writes H to `out` only.
+// fields, 1 also replaces them (resync), 2 writes H to `out` only, 3 sets
+// the fields h = H (start state; +-J exact, no statistics).
 // stats[0] = max |h - H| (double bits), [1] = mismatches, [2] = max |dE|.
 size_t recompute_j_bytes(uint32_t kind, uint32_t npad);
 size_t recompute_s_bytes(uint32_t kind, uint32_t chains, uint32_t npad);

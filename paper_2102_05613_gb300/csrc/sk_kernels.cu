@@ -308,13 +308,13 @@ int step_kernel_occupancy(int cls, uint32_t W, size_t per_chain) {
 }
 
 cudaError_t launch_init(const JobDev* job, const int8_t* init, uint32_t chains, uint32_t N,
-                        uint32_t Npad, uint32_t kind, cudaStream_t st) {
+                        uint32_t Npad, uint32_t kind, cudaStream_t st, bool with_fields) {
     (void)N;
     const uint64_t words = static_cast<uint64_t>(chains) * (Npad / 4);
     const uint32_t blocks = static_cast<uint32_t>(std::min<uint64_t>((words + 255) / 256, 152ull * 64));
     spins_kernel<<<blocks, 256, 0, st>>>(*job, init);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess || !with_fields) return e;
     const dim3 grid((Npad + kFI - 1) / kFI, (chains + kFC - 1) / kFC);
     if (kind == 0)
         fields_kernel<int8_t><<<grid, 256, 0, st>>>(static_cast<const int8_t*>(job->J), job->s, job->h, Npad, chains);

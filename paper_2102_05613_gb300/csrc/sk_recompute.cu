@@ -129,7 +129,7 @@ struct Args {
     double* dE;                     // per chain: sum_n s_n (h_n - H_n)
     unsigned long long* stats;      // [0] max |h - H| (double bits), [1] mismatches, [2] max |dE|
     int* err;
-    uint32_t chains, npad, kblocks, terms, mode;  // mode: 0 check, 1 resync, 2 output
+    uint32_t chains, npad, kblocks, terms, mode;  // mode: 0 check, 1 resync, 2 output, 3 set fields
     uint32_t pm1;
 };
 
@@ -249,6 +249,18 @@ __global__ void __launch_bounds__(128, 1)
                     args.out[static_cast<size_t>(row0 + r) * args.npad + n] = T[lane * 33 + r];
             continue;
         }
+        if (args.mode == 3) {  // the fields of a start state: h = H, no statistics
+#pragma unroll
+            for (int r = 0; r < 32; ++r)
+                if (col_ok && row0 + r < args.chains) {
+                    const size_t idx = static_cast<size_t>(row0 + r) * args.npad + n;
+                    if (args.pm1)
+                        static_cast<int*>(args.h)[idx] = __float2int_rn(T[lane * 33 + r]);
+                    else
+                        static_cast<float*>(args.h)[idx] = T[lane * 33 + r];
+                }
+            continue;
+        }
         // all 32 rows' loads first (each field is read once, then written once
         // by this thread), then the arithmetic and the stores
         uint32_t hv[32];
@@ -281,7 +293,7 @@ __global__ void __launch_bounds__(128, 1)
             }
         }
     }
-    if (tile_ok && args.mode != 2) {
+    if (tile_ok && args.mode < 2) {
         // row sums: lane l holds row r's part for columns l (mod 32); transpose
         __syncwarp();
 #pragma unroll
@@ -453,7 +465,7 @@ cudaError_t launch_recompute(uint32_t kind, const int8_t* s, void* h, float* out
         recompute_kernel<true><<<grid, 128, SMEM_BYTES, st>>>(tA, tB[0], tB[0], tB[0], a);
     }
     e = cudaGetLastError();
-    if (e != cudaSuccess || mode == 2) return e;
+    if (e != cudaSuccess || mode >= 2) return e;
     finish_energy<<<(chains + 255) / 256, 256, 0, st>>>(dE, chains, scale, stats);
     return cudaGetLastError();
 }

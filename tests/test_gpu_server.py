@@ -70,8 +70,9 @@ def test_admission_by_footprint_and_oversized_jobs():
     need_gpu()
     N, chains = 1024, 64
     J = inputs.couplings_gauss(N, 9)
-    # each job needs ~4 MB of couplings + ~0.3 MB of state: two fit, not three
-    srv = sk.Server(budget_bytes=9 << 20, quantum_steps=128)
+    # each job needs ~10 MB of couplings and their tensor-core operand + ~0.5 MB
+    # of state: two fit, not three
+    srv = sk.Server(budget_bytes=24 << 20, quantum_steps=128)
     ts = [srv.submit(N=N, kind=sk.SK_J_GAUSS, chains=chains, steps=1024, K=32, seed=k,
                      stream_id=k, J=J) for k in range(4)]
     big = srv.submit(N=2048, kind=sk.SK_J_GAUSS, chains=8, steps=10, K=8,
