@@ -337,9 +337,11 @@ sk_status mcmcmc_batch_free(sk_batch* b);
 
 /*
  * mcmcmc_run_noalloc: runs `steps` Monte Carlo steps of `chains` chains, the
- * same kernels and results as mcmcmc_run with these arguments, without
- * allocating anything: no cudaMalloc, no cudaFree, no allocating library
- * routine.  It is for callers that cannot allocate device memory or let a
+ * same step kernel as mcmcmc_run with these arguments, without allocating
+ * anything: no cudaMalloc, no cudaFree, no allocating library routine.  Its
+ * start fields h = J s come from the CUDA cores (no tensor-core operand
+ * buffers), so results equal mcmcmc_run's bit for bit for +-J couplings and
+ * within the Gaussian parity tolerance otherwise.  It is for callers that cannot allocate device memory or let a
  * library do so: applications whose device memory is owned entirely by their
  * own pool allocator (an extra cudaMalloc would fail or fragment the pool),
  * latency-critical loops that cannot afford cudaMalloc's implicit device
