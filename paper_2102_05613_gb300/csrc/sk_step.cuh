@@ -196,15 +196,20 @@ __device__ __forceinline__ double chain_energy(const int8_t* S, const void* h, u
         const int tot = gsum(g, acc);  // = 2 sum_{i<j} J s s, even
         return scale * static_cast<double>(-(tot / 2));
     } else {
+        // each lane sums its npad/G terms s_k h_k in fp32 (the products are
+        // exact; relative rounding ~ (npad/G) 2^-24), the lanes' partial sums
+        // are combined in double precision (FP64 is slow on this part)
         const float* hf = static_cast<const float*>(h);
-        double acc = 0.0;
+        float acc = 0.0f;
         for (uint32_t k = 4u * g.gl; k < npad; k += 4u * G) {
             const uint32_t sw = *reinterpret_cast<const uint32_t*>(S + k);
             const float4 hv = *reinterpret_cast<const float4*>(hf + k);
-            acc += static_cast<double>(sbyte(sw, 0)) * hv.x + static_cast<double>(sbyte(sw, 1)) * hv.y +
-                   static_cast<double>(sbyte(sw, 2)) * hv.z + static_cast<double>(sbyte(sw, 3)) * hv.w;
+            acc = fmaf(static_cast<float>(sbyte(sw, 0)), hv.x, acc);
+            acc = fmaf(static_cast<float>(sbyte(sw, 1)), hv.y, acc);
+            acc = fmaf(static_cast<float>(sbyte(sw, 2)), hv.z, acc);
+            acc = fmaf(static_cast<float>(sbyte(sw, 3)), hv.w, acc);
         }
-        return -0.5 * scale * gsum(g, acc);
+        return -0.5 * scale * gsum(g, static_cast<double>(acc));
     }
 }
 
