@@ -44,7 +44,7 @@ def lib():
         L.sko_run.argtypes = [i, i, vp, d, i, i, d, u64, u32, u32, u32, vp, u64, u32,
                               vp, vp, vp, vp, vp, vp, u32]
         L.sko_run.restype = i
-        L.sko_run_p.argtypes = L.sko_run.argtypes + [d]
+        L.sko_run_p.argtypes = L.sko_run.argtypes + [d, vp]
         L.sko_run_p.restype = i
         L.sko_replay.argtypes = [i, i, vp, d, i, i, d, u64, u32, u32, vp, u64, vp, d,
                                  vp, vp, vp, vp]
@@ -118,6 +118,7 @@ def run(J, *, rule=MCMCMC, K=8, beta=1.0, scale=1.0, seed=1, stream=0, chain0=0,
     N = J.shape[0]
     nrec = steps // record_every if record_every else 0
     E = np.zeros((nrec, chains))
+    Enw = np.zeros((nrec, chains))
     acc = np.zeros((nrec, chains), dtype=np.uint32)
     q = np.zeros((nrec, chains // 2)) if (want_q and chains >= 2) else None
     fin = np.zeros((chains, N), dtype=np.int8)
@@ -126,10 +127,10 @@ def run(J, *, rule=MCMCMC, K=8, beta=1.0, scale=1.0, seed=1, stream=0, chain0=0,
     init_a = None if init is None else np.ascontiguousarray(init, dtype=np.int8).reshape(chains, N)
     rc = lib().sko_run_p(N, _kind_of(J), _ptr(J), scale, rule, K, beta, seed, stream, chain0,
                          chains, _ptr(init_a), steps, record_every, _ptr(E), _ptr(acc), _ptr(q),
-                         _ptr(fin), _ptr(finE), _ptr(tr), resync_every, float(p_center))
+                         _ptr(fin), _ptr(finE), _ptr(tr), resync_every, float(p_center), _ptr(Enw))
     if rc != 0:
         raise RuntimeError(f"sko_run failed with {rc}")
-    return dict(E=E, acc=acc, q=q, spins=fin, final_E=finE, trace=tr)
+    return dict(E=E, acc=acc, q=q, spins=fin, final_E=finE, trace=tr, E_nw=Enw)
 
 
 def replay(J, slots, *, rule=MCMCMC, K=8, beta=1.0, scale=1.0, seed=1, stream=0, chain=0,

@@ -42,6 +42,14 @@
  *    node rule weights slot j by P_eq(c_j) p_{r(j)}: the centre slot by p_c,
  *    every leaf slot by p_l.  p_c = 1/(K+1) is the uniform root above.
  *
+ *  - Node-weighted estimator.  Sec. A.2, Eq. (eq_monte_carlo_graph): an
+ *    observable may be averaged over all nodes of each step's graph with
+ *    their node probabilities.  For the energy this gives, per step,
+ *    E_nw = sum_j P_node(j) E(c_j) = E(c) + sum_j P_node(j) dE_j, the
+ *    expectation of the next state's energy given the graph; for the
+ *    Metropolis comparator the same conditional expectation over accept /
+ *    reject, E(c) + p_acc dE.  Records store it for the record step.
+ *
  *  - K = 1 of the same rule is the two-node heat-bath chain of Sec. III.A,
  *    Eq. (eq_node_two_conf).  The "standard local Metropolis" comparator of
  *    Sec. IV.B uses the acceptance min(1, P_eq(c1)/P_eq(c0)) of Sec. II.
@@ -331,7 +339,7 @@ static void flip_spin(const sko_ctx* c, int8_t* s, double* h, int x) {
  * Returns 1 when the configuration changed (the acceptance count).
  */
 static int chain_step(const sko_ctx* c, uint32_t chain, uint64_t t, int8_t* s, double* h,
-                      int forced, int* own, double* Pout, double* uout) {
+                      int forced, int* own, double* Pout, double* uout, double* nw) {
     uint32_t w0[4];
     draw_block(c->seed, c->stream, 0u, chain, t, 0u, w0);
     uint64_t U0 = ((uint64_t)w0[1] << 32) | w0[0];
@@ -355,6 +363,8 @@ static int chain_step(const sko_ctx* c, uint32_t chain, uint64_t t, int8_t* s, d
         if (Pout) Pout[0] = pacc;
         if (own) *own = accept;
         if (forced >= 0) accept = forced;
+        /* expected energy change of the step minus the realised one */
+        if (nw) *nw = pacc * dE - (accept ? dE : 0.0);
         if (accept) flip_spin(c, s, h, i);
         return accept;
     }
@@ -390,6 +400,20 @@ static int chain_step(const sko_ctx* c, uint32_t chain, uint64_t t, int8_t* s, d
                                                : (double)(U1 >> 40) * ldexp(1.0, -24) * acc;
     }
     if (forced >= 0) j = forced;
+    if (nw) {
+        /* sum_q P_node(q) dE_q minus the chosen slot's dE: added to the energy
+           after the move it gives E(c) + sum_q P_node(q) dE_q */
+        const double m = min_dE(dE, K + 1);
+        double num = 0.0, den = 0.0;
+        for (int q = 0; q <= K; ++q) {
+            const int centre = is_centre_slot(q, leaf_root);
+            const double w = (c->kind == SKO_PM1) ? (double)weight_int(c, dE[q], m, centre)
+                                                  : weight_dbl(c, dE[q], m, centre);
+            num += w * dE[q];
+            den += w;
+        }
+        *nw = num / den - dE[j];
+    }
     for (int f = 0; f < nflip[j]; ++f) flip_spin(c, s, h, flips[j][f]);
     return nflip[j] > 0;
 }
@@ -459,7 +483,9 @@ static void ctx_free(sko_ctx* c) {
  *   record r stores: rec_E[r*nchains+i] = scale * E of chain i,
  *   rec_acc[r*nchains+i] = steps in the interval whose configuration changed,
  *   rec_q[r*(nchains/2)+m] = (1/N) sum_k s_k s'_k of the pair (2m, 2m+1)
- *   (chain0 must be even for q).  Any output may be NULL.
+ *   (chain0 must be even for q), rec_Enw[r*nchains+i] = scale * the
+ *   node-weighted energy of the record step's graph (see the header).  Any
+ *   output may be NULL.  p_center: the root distribution (root_setup).
  *   trace (nchains*nsteps, may be NULL) receives the slot chosen at each step
  *   (Metropolis: 1 accepted, 0 rejected).
  *   resync_every > 0 recomputes the fields from scratch at that period and
@@ -471,7 +497,7 @@ int sko_run_p(int N, int kind, const void* J, double scale, int rule, int K, dou
               const int8_t* init_spins, uint64_t nsteps, uint32_t record_every,
               double* rec_E, uint32_t* rec_acc, double* rec_q,
               int8_t* final_spins, double* final_E, int32_t* trace, uint32_t resync_every,
-              double p_center) {
+              double p_center, double* rec_Enw) {
     sko_ctx c;
     int rc = ctx_init(&c, N, kind, J, scale, rule, K, beta, seed, stream, p_center);
     if (rc) return rc;
@@ -490,7 +516,10 @@ int sko_run_p(int N, int kind, const void* J, double scale, int rule, int K, dou
         uint32_t acc = 0;
         for (uint64_t t = 0; t < nsteps; ++t) {
             int own = -1;
-            acc += (uint32_t)chain_step(&c, chain, t, s, h, -1, &own, NULL, NULL);
+            const int rec_step = record_every && ((t + 1) % record_every) == 0;
+            double nw = 0.0;
+            acc += (uint32_t)chain_step(&c, chain, t, s, h, -1, &own, NULL, NULL,
+                                        (rec_step && rec_Enw) ? &nw : NULL);
             if (trace) trace[(size_t)ci * nsteps + t] = own;
             if (resync_every && ((t + 1) % resync_every) == 0) {
                 sko_fields(N, kind, J, s, h2);
@@ -504,7 +533,11 @@ int sko_run_p(int N, int kind, const void* J, double scale, int rule, int K, dou
             }
             if (record_every && ((t + 1) % record_every) == 0) {
                 uint64_t r = (t + 1) / record_every - 1;
-                if (rec_E) rec_E[r * nchains + ci] = sko_energy(N, kind, J, scale, s);
+                if (rec_E || rec_Enw) {
+                    const double E = sko_energy(N, kind, J, scale, s);
+                    if (rec_E) rec_E[r * nchains + ci] = E;
+                    if (rec_Enw) rec_Enw[r * nchains + ci] = E + scale * nw;
+                }
                 if (rec_acc) rec_acc[r * nchains + ci] = acc;
                 acc = 0;
                 if (rec_q) {
@@ -536,7 +569,7 @@ int sko_run(int N, int kind, const void* J, double scale, int rule, int K, doubl
             int8_t* final_spins, double* final_E, int32_t* trace, uint32_t resync_every) {
     return sko_run_p(N, kind, J, scale, rule, K, beta, seed, stream, chain0, nchains, init_spins,
                      nsteps, record_every, rec_E, rec_acc, rec_q, final_spins, final_E, trace,
-                     resync_every, 0.0);
+                     resync_every, 0.0, NULL);
 }
 
 /*
@@ -571,7 +604,7 @@ long long sko_replay_p(int N, int kind, const void* J, double scale, int rule, i
         if (g < 0 || g >= nslot) { bad++; if (first < 0) first = (long long)t; break; }
         int own = -1;
         double u = 0.0;
-        chain_step(&c, chain, t, s, h, g, &own, P, &u);
+        chain_step(&c, chain, t, s, h, g, &own, P, &u, NULL);
         if (own != g) {
             dis++;
             int ok;

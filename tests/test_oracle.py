@@ -273,6 +273,80 @@ def test_nonuniform_root_one_step_sampler_matches_exact_row():
             assert _chi2_pvalue(counts, P[x0] * C) > 1e-3, (kind, p_center)
 
 
+def _state(x, N):
+    return np.array([(-1 if (x >> i) & 1 else 1) for i in range(N)], dtype=np.int8)
+
+
+@pytest.mark.parametrize("kind,rule,p_center", [("pm1", oracle.MCMCMC, 0.0), ("gauss", oracle.MCMCMC, 0.0),
+                                                ("gauss", oracle.MCMCMC, 0.6), ("gauss", oracle.METROPOLIS, 0.0),
+                                                ("pm1", oracle.METROPOLIS, 0.0)])
+def test_node_weighted_energy_is_the_conditional_expectation(kind, rule, p_center):
+    # Eq. eq_monte_carlo_graph: sum_j P_node(j) E(c_j) is E[E(next state) | graph];
+    # its average over graphs from a fixed state x is sum_y P(x, y) E(y)
+    N, K, beta = 5, 3, 0.6
+    J = _pm1(N, 74) if kind == "pm1" else _gauss(N, 75)
+    wm = 1 if kind == "pm1" else 0
+    P = oracle.transition_matrix(J, rule=rule, K=K, beta=beta, weight_mode=wm, p_center=p_center)
+    Es = np.array([oracle.energy(J, _state(x, N)) for x in range(1 << N)])
+    x0 = 0b00110
+    want = float(P[x0] @ Es)
+    C = 20000
+    r = oracle.run(J, rule=rule, K=K, beta=beta, seed=13, chains=C, init=np.tile(_state(x0, N), (C, 1)),
+                   steps=1, record_every=1, p_center=p_center)
+    nw, e = r["E_nw"][0], r["E"][0]
+    assert abs(nw.mean() - want) < 4 * nw.std() / math.sqrt(C) + 1e-12, (nw.mean(), want)
+    assert nw.var() < e.var()   # the node average removes the choice's variance
+
+
+def test_node_weighted_energy_by_explicit_star():
+    # one step from a fixed state: build the K+1 configurations of the star
+    # from the step's draws, weight their full energies exp(-beta E), compare
+    N, K, beta, seed = 9, 6, 0.8, 5
+    J = _gauss(N, 76)
+    rng = np.random.default_rng(3)
+    for trial in range(6):
+        s0 = rng.choice(np.array([-1, 1], dtype=np.int8), size=N)
+        chain = trial
+        w = oracle.philox([0, 0, chain, 0], [seed, 0])
+        U0 = (int(w[1]) << 32) | int(w[0])
+        leaf = (U0 * (K + 1)) >> 64 != 0
+        sites = []
+        for d in range(1, K + 1):
+            b = oracle.philox([1 + (d - 1) // 4, 0, chain, 0], [seed, 0])
+            sites.append((int(b[(d - 1) % 4]) * N) >> 32)
+        confs = [s0.copy()]
+        for d in range(1, K + 1):
+            c = s0.copy()
+            if not leaf:
+                c[sites[d - 1]] *= -1
+            else:
+                c[sites[0]] *= -1
+                if d >= 2:
+                    c[sites[d - 1]] *= -1
+            confs.append(c)
+        E = np.array([oracle.energy(J, c) for c in confs])
+        wts = np.exp(-beta * (E - E.min()))
+        want = float((wts * E).sum() / wts.sum())
+        init = np.zeros((chain + 1, N), dtype=np.int8)
+        init[:] = s0
+        r = oracle.run(J, K=K, beta=beta, seed=seed, chains=chain + 1, init=init, steps=1, record_every=1)
+        assert abs(r["E_nw"][0, chain] - want) < 1e-12, (trial, r["E_nw"][0, chain], want)
+
+
+def test_node_weighted_long_run_matches_exact_mean():
+    N, K, beta = 12, 8, 1.0
+    J = _pm1(N, 0)
+    pi = oracle.boltzmann(J, beta)
+    Es = np.array([oracle.energy(J, _state(x, N)) for x in range(1 << N)])
+    exact = float((pi * Es).sum())
+    C = 4000
+    r = oracle.run(J, K=K, beta=beta, seed=21, chains=C, steps=400, record_every=100)
+    nw = r["E_nw"][1:].ravel()
+    e = r["E"][1:].ravel()
+    assert abs(nw.mean() - exact) < 5 * e.std() / math.sqrt(C)
+    assert nw.var() < e.var()
+
+
 def test_weight_table_shape():
     W = oracle.weight_table(1.0, 400)
     assert int(W[0]) == 1 << 52
