@@ -132,6 +132,9 @@ typedef struct {
                             /*   2^20) and the root drawn with F_c/(F_c+K F_l); */
                             /*   both factors must round to >= 1 (else          */
                             /*   SK_ERR_INVALID_ARG)                            */
+    uint32_t node_weighted; /* 1: records also hold the node-weighted energy    */
+                            /*   (mcmcmc_observables_nw); such runs read row a  */
+                            /*   through L1 (no staging)                        */
 } sk_run_params;
 
 /*
@@ -186,6 +189,21 @@ sk_status mcmcmc_wait(sk_run* run, uint64_t timeout_ns);
  */
 sk_status mcmcmc_observables(sk_run* run, uint64_t first, uint64_t count, double* energy,
                              double* overlap, uint32_t* accepted, uint32_t mem);
+
+/*
+ * mcmcmc_observables_nw: copies the node-weighted energies of records
+ * [first, first+count) of a run created with node_weighted = 1
+ * (synchronises; SK_ERR_INVALID_ARG otherwise): energy_nw[r*chains + c]
+ * (double, scale included) is, for the recorded state c and the graph T that
+ * the next step generates from it (Sec. A.2, Eq. eq_monte_carlo_graph),
+ * sum_j P_node(j|T) E(c_j) = E(c) + sum_j P_node(j|T) dE_j over the K+1
+ * slots with the probabilities that step chooses with: the expectation of the
+ * next state's energy given T, an estimator of <E> with less variance than
+ * the energy one step later.  For the Metropolis comparator it is
+ * E(c) + p_acc dE of the next step's proposal.  Summed in double precision
+ * from the step's weights.
+ */
+sk_status mcmcmc_observables_nw(sk_run* run, uint64_t first, uint64_t count, double* energy_nw, uint32_t mem);
 
 /*
  * mcmcmc_state: copies the current spins (chains*N int8) and, if non-NULL,

@@ -44,11 +44,12 @@
  *
  *  - Node-weighted estimator.  Sec. A.2, Eq. (eq_monte_carlo_graph): an
  *    observable may be averaged over all nodes of each step's graph with
- *    their node probabilities.  For the energy this gives, per step,
- *    E_nw = sum_j P_node(j) E(c_j) = E(c) + sum_j P_node(j) dE_j, the
- *    expectation of the next state's energy given the graph; for the
- *    Metropolis comparator the same conditional expectation over accept /
- *    reject, E(c) + p_acc dE.  Records store it for the record step.
+ *    their node probabilities.  For the energy of a state c and the graph T
+ *    the next step generates from it, E_nw = sum_j P_node(j|T) E(c_j) =
+ *    E(c) + sum_j P_node(j|T) dE_j, the expectation of the next state's
+ *    energy given T; for the Metropolis comparator the same conditional
+ *    expectation over accept / reject, E(c) + p_acc dE.  Records store it
+ *    next to E(c), for the graph of the step after the record.
  *
  *  - K = 1 of the same rule is the two-node heat-bath chain of Sec. III.A,
  *    Eq. (eq_node_two_conf).  The "standard local Metropolis" comparator of
@@ -339,7 +340,7 @@ static void flip_spin(const sko_ctx* c, int8_t* s, double* h, int x) {
  * Returns 1 when the configuration changed (the acceptance count).
  */
 static int chain_step(const sko_ctx* c, uint32_t chain, uint64_t t, int8_t* s, double* h,
-                      int forced, int* own, double* Pout, double* uout, double* nw) {
+                      int forced, int* own, double* Pout, double* uout) {
     uint32_t w0[4];
     draw_block(c->seed, c->stream, 0u, chain, t, 0u, w0);
     uint64_t U0 = ((uint64_t)w0[1] << 32) | w0[0];
@@ -363,8 +364,6 @@ static int chain_step(const sko_ctx* c, uint32_t chain, uint64_t t, int8_t* s, d
         if (Pout) Pout[0] = pacc;
         if (own) *own = accept;
         if (forced >= 0) accept = forced;
-        /* expected energy change of the step minus the realised one */
-        if (nw) *nw = pacc * dE - (accept ? dE : 0.0);
         if (accept) flip_spin(c, s, h, i);
         return accept;
     }
@@ -400,22 +399,52 @@ static int chain_step(const sko_ctx* c, uint32_t chain, uint64_t t, int8_t* s, d
                                                : (double)(U1 >> 40) * ldexp(1.0, -24) * acc;
     }
     if (forced >= 0) j = forced;
-    if (nw) {
-        /* sum_q P_node(q) dE_q minus the chosen slot's dE: added to the energy
-           after the move it gives E(c) + sum_q P_node(q) dE_q */
-        const double m = min_dE(dE, K + 1);
-        double num = 0.0, den = 0.0;
-        for (int q = 0; q <= K; ++q) {
-            const int centre = is_centre_slot(q, leaf_root);
-            const double w = (c->kind == SKO_PM1) ? (double)weight_int(c, dE[q], m, centre)
-                                                  : weight_dbl(c, dE[q], m, centre);
-            num += w * dE[q];
-            den += w;
-        }
-        *nw = num / den - dE[j];
-    }
     for (int f = 0; f < nflip[j]; ++f) flip_spin(c, s, h, flips[j][f]);
     return nflip[j] > 0;
+}
+
+/*
+ * Node-weighted energy change of the graph that step t generates from the
+ * state (s, h), without taking the step: sum_j P_node(j) dE_j over its K+1
+ * slots with the probabilities the step chooses with (the same draws,
+ * candidates and weights as chain_step); Metropolis: p_acc dE of its
+ * proposal.
+ */
+static double graph_mean_dE(const sko_ctx* c, uint32_t chain, uint64_t t, const int8_t* s, const double* h) {
+    uint32_t w0[4];
+    draw_block(c->seed, c->stream, 0u, chain, t, 0u, w0);
+    const uint64_t U0 = ((uint64_t)w0[1] << 32) | w0[0];
+    if (c->rule == SKO_METROPOLIS) {
+        const int i = (int)range32(w0[0], (uint32_t)c->N);
+        const double dE = 2.0 * (double)s[i] * h[i];
+        double pacc = 1.0;
+        if (dE > 0.0)
+            pacc = (c->kind == SKO_PM1) ? ldexp((double)c->M[llround(dE * 0.5)], -53)
+                                        : exp(-c->beta * c->scale * dE);
+        return pacc * dE;
+    }
+    const int K = c->K;
+    const int leaf_root = (c->p_center > 0.0) ? (U0 >= c->root_thr) : (range64(U0, (uint64_t)K + 1u) != 0u);
+    uint32_t sites[SKO_MAXSLOT_GUARD] = {0};
+    for (int d = 1; d <= K; ++d) {
+        uint32_t wb[4];
+        draw_block(c->seed, c->stream, 0u, chain, t, (uint32_t)(1 + (d - 1) / 4), wb);
+        sites[d] = range32(wb[(d - 1) % 4], (uint32_t)c->N);
+    }
+    double dE[SKO_MAXSLOT_GUARD];
+    int flips[SKO_MAXSLOT_GUARD][2];
+    int nflip[SKO_MAXSLOT_GUARD];
+    star_candidates(c, s, h, leaf_root, sites, dE, flips, nflip);
+    const double m = min_dE(dE, K + 1);
+    double num = 0.0, den = 0.0;
+    for (int q = 0; q <= K; ++q) {
+        const int centre = is_centre_slot(q, leaf_root);
+        const double w = (c->kind == SKO_PM1) ? (double)weight_int(c, dE[q], m, centre)
+                                              : weight_dbl(c, dE[q], m, centre);
+        num += w * dE[q];
+        den += w;
+    }
+    return num / den;
 }
 
 /*
@@ -484,7 +513,8 @@ static void ctx_free(sko_ctx* c) {
  *   rec_acc[r*nchains+i] = steps in the interval whose configuration changed,
  *   rec_q[r*(nchains/2)+m] = (1/N) sum_k s_k s'_k of the pair (2m, 2m+1)
  *   (chain0 must be even for q), rec_Enw[r*nchains+i] = scale * the
- *   node-weighted energy of the record step's graph (see the header).  Any
+ *   node-weighted energy of the recorded state with the graph of step t+1
+ *   (see the header).  Any
  *   output may be NULL.  p_center: the root distribution (root_setup).
  *   trace (nchains*nsteps, may be NULL) receives the slot chosen at each step
  *   (Metropolis: 1 accepted, 0 rejected).
@@ -516,10 +546,7 @@ int sko_run_p(int N, int kind, const void* J, double scale, int rule, int K, dou
         uint32_t acc = 0;
         for (uint64_t t = 0; t < nsteps; ++t) {
             int own = -1;
-            const int rec_step = record_every && ((t + 1) % record_every) == 0;
-            double nw = 0.0;
-            acc += (uint32_t)chain_step(&c, chain, t, s, h, -1, &own, NULL, NULL,
-                                        (rec_step && rec_Enw) ? &nw : NULL);
+            acc += (uint32_t)chain_step(&c, chain, t, s, h, -1, &own, NULL, NULL);
             if (trace) trace[(size_t)ci * nsteps + t] = own;
             if (resync_every && ((t + 1) % resync_every) == 0) {
                 sko_fields(N, kind, J, s, h2);
@@ -536,7 +563,7 @@ int sko_run_p(int N, int kind, const void* J, double scale, int rule, int K, dou
                 if (rec_E || rec_Enw) {
                     const double E = sko_energy(N, kind, J, scale, s);
                     if (rec_E) rec_E[r * nchains + ci] = E;
-                    if (rec_Enw) rec_Enw[r * nchains + ci] = E + scale * nw;
+                    if (rec_Enw) rec_Enw[r * nchains + ci] = E + scale * graph_mean_dE(&c, chain, t + 1, s, h);
                 }
                 if (rec_acc) rec_acc[r * nchains + ci] = acc;
                 acc = 0;
@@ -604,7 +631,7 @@ long long sko_replay_p(int N, int kind, const void* J, double scale, int rule, i
         if (g < 0 || g >= nslot) { bad++; if (first < 0) first = (long long)t; break; }
         int own = -1;
         double u = 0.0;
-        chain_step(&c, chain, t, s, h, g, &own, P, &u, NULL);
+        chain_step(&c, chain, t, s, h, g, &own, P, &u);
         if (own != g) {
             dis++;
             int ok;

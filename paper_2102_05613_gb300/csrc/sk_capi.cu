@@ -162,6 +162,7 @@ struct sk_run {
     double* drecE = nullptr;
     uint32_t* drecAcc = nullptr;
     double* drecQ = nullptr;
+    double* drecEnw = nullptr;
     int32_t* dtrace = nullptr;
     uint64_t* dW = nullptr;
     uint32_t wlen = 0;
@@ -280,6 +281,7 @@ sk_status init_state(sk_run* r, const int8_t* spins, uint32_t mem) {
         SK_CU(cudaMemsetAsync(r->drecE, 0, R * r->chains * sizeof(double), in->st));
         SK_CU(cudaMemsetAsync(r->drecAcc, 0, R * r->chains * sizeof(uint32_t), in->st));
         if (r->chains >= 2) SK_CU(cudaMemsetAsync(r->drecQ, 0, R * (r->chains / 2) * sizeof(double), in->st));
+        if (r->drecEnw) SK_CU(cudaMemsetAsync(r->drecEnw, 0, R * r->chains * sizeof(double), in->st));
     }
     if (r->dtrace)
         SK_CU(cudaMemsetAsync(r->dtrace, 0xff, static_cast<size_t>(r->p.trace_chains) * r->p.trace_steps * 4,
@@ -309,6 +311,7 @@ void free_run_buffers(sk_run* r) {
     cudaFree(r->drecE);
     cudaFree(r->drecAcc);
     cudaFree(r->drecQ);
+    cudaFree(r->drecEnw);
     cudaFree(r->dtrace);
     cudaFree(r->dW);
     cudaFree(r->dstep);
@@ -488,6 +491,7 @@ sk_status mcmcmc_create(sk_instance* in, const sk_run_params* p, sk_run** out) {
     if (s == SK_OK) s = dalloc(&r->drecE, R * C * 8);
     if (s == SK_OK) s = dalloc(&r->drecAcc, R * C * 4);
     if (s == SK_OK) s = dalloc(&r->drecQ, R * (C / 2) * 8);
+    if (s == SK_OK && r->p.node_weighted) s = dalloc(&r->drecEnw, R * C * 8);
     if (s == SK_OK) s = dalloc(&r->dtrace, static_cast<size_t>(r->p.trace_chains) * r->p.trace_steps * 4);
     if (s == SK_OK) s = dalloc(&r->dstep, 8);
     if (s == SK_OK) s = dalloc(&r->derr, 4);
@@ -518,6 +522,7 @@ sk_status mcmcmc_create(sk_instance* in, const sk_run_params* p, sk_run** out) {
     j.rec_E = r->drecE;
     j.rec_acc = r->drecAcc;
     j.rec_q = r->drecQ;
+    j.rec_Enw = r->drecEnw;
     j.trace = r->dtrace;
     j.err = r->derr;
     j.work = r->dwork;
@@ -611,6 +616,22 @@ sk_status mcmcmc_observables(sk_run* r, uint64_t first, uint64_t count, double* 
     if (overlap && C >= 2)
         SK_CU(cudaMemcpyAsync(overlap, r->drecQ + first * (C / 2), count * (C / 2) * 8, cudaMemcpyDefault, st));
     SK_CU(cudaStreamSynchronize(st));
+    return SK_OK;
+}
+
+sk_status mcmcmc_observables_nw(sk_run* r, uint64_t first, uint64_t count, double* energy_nw, uint32_t mem) {
+    if (!r || !energy_nw) return fail(SK_ERR_INVALID_ARG, "NULL argument");
+    if (!r->drecEnw) return fail(SK_ERR_INVALID_ARG, "the run was created without node_weighted records");
+    if (mem != SK_MEM_HOST && mem != SK_MEM_DEVICE) return fail(SK_ERR_INVALID_ARG, "bad mem");
+    if (first + count > r->p.max_records)
+        return fail(SK_ERR_INVALID_ARG, "records [%llu, %llu) beyond capacity %llu", (unsigned long long)first,
+                    (unsigned long long)(first + count), (unsigned long long)r->p.max_records);
+    sk_status s = mcmcmc_wait(r, 0);
+    if (s != SK_OK) return s;
+    if (count == 0) return SK_OK;
+    const size_t C = r->chains;
+    SK_CU(cudaMemcpyAsync(energy_nw, r->drecEnw + first * C, count * C * 8, cudaMemcpyDefault, r->inst->st));
+    SK_CU(cudaStreamSynchronize(r->inst->st));
     return SK_OK;
 }
 
@@ -754,14 +775,16 @@ uint32_t run_gdefault(const sk_run* r) {
     return g;
 }
 // Runs share a launch class when their kernels agree for every G: same
-// coupling type, rule, Philox blocks of sites (as a power of two) and
-// shared-memory bucket.
+// coupling type, rule, node-weighted records or not, Philox blocks of sites
+// (as a power of two) and shared-memory bucket.
+bool run_nw(const sk_run* r) { return r->p.node_weighted && r->p.record_every && r->p.max_records; }
 uint64_t class_key(const sk_run* r) {
     uint32_t b = 128;
     const uint32_t pc = run_per_chain(r);
     while (b < pc) b <<= 1;
     const uint64_t kb = sk::site_blocks_pow2(r->p.rule, r->p.K);
-    return (static_cast<uint64_t>(r->inst->kind) << 62) | (static_cast<uint64_t>(r->p.rule) << 61) | (kb << 32) | b;
+    return (static_cast<uint64_t>(r->inst->kind) << 62) | (static_cast<uint64_t>(r->p.rule) << 61) |
+           (static_cast<uint64_t>(run_nw(r)) << 60) | (kb << 32) | b;
 }
 // Most warps per CTA for G lanes per chain: chains of a pair share a CTA,
 // so with whole-warp chains W is even.
@@ -799,6 +822,7 @@ sk_status plan_batch(sk_batch* b) {
             c.per_chain_direct = std::max(c.per_chain_direct, run_per_chain(b->runs[i], false));
             total += b->runs[i]->chains;
         }
+        const bool nw = ((c.key >> 60) & 1u) != 0;  // node-weighted records: rows through L1 only
         auto t = b->tuned.find(c.key);
         if (t != b->tuned.end()) {
             c.stage = t->second >> 16;
@@ -806,7 +830,7 @@ sk_status plan_batch(sk_batch* b) {
             c.W = t->second & 0xFFu;
             c.per_chain = c.stage ? c.per_chain_staged : c.per_chain_direct;
         } else {
-            c.stage = b->S_override == 2 ? 0u : 1u;
+            c.stage = (b->S_override == 2 || nw) ? 0u : 1u;
             c.per_chain = c.stage ? c.per_chain_staged : c.per_chain_direct;
             c.G = b->G_override ? std::max(b->G_override, c.gmin) : (total <= 512 ? 32u : c.gdef);
             const uint32_t fit = fit_warps(c.per_chain, c.G);
@@ -814,7 +838,7 @@ sk_status plan_batch(sk_batch* b) {
         }
         if (c.W < 1 || (c.G == 32 && c.W < 2))
             return fail(SK_ERR_INVALID_ARG, "N too large: %u bytes of shared memory per chain", c.per_chain);
-        c.cls = sk::step_class(r0->inst->kind, r0->p.rule, r0->p.K, c.G, c.stage);
+        c.cls = sk::step_class(r0->inst->kind, r0->p.rule, r0->p.K, c.G, nw ? 2u : c.stage);
         if (c.cls < 0) return fail(SK_ERR_INVALID_ARG, "no step kernel for K = %u with %u lanes per chain", r0->p.K, c.G);
         int occ = sk::step_kernel_occupancy(c.cls, c.W, c.per_chain);
         while (occ <= 0 && t == b->tuned.end() && c.W > (c.G == 32 ? 2u : 1u)) {  // default choice: step down
@@ -1087,7 +1111,8 @@ sk_status mcmcmc_batch_autotune(sk_batch* b, uint32_t trial_steps, uint32_t* out
             uint32_t best = (cls0[k].stage << 16) | (cls0[k].G << 8) | cls0[k].W;
             float best_ms = 1e30f;
             std::vector<uint32_t> cand;  // (stage << 16) | (G << 8) | W
-            for (uint32_t stage = 0; stage <= 1; ++stage)
+            const uint32_t max_stage = ((key >> 60) & 1u) ? 0u : 1u;  // node-weighted classes: no staging
+            for (uint32_t stage = 0; stage <= max_stage; ++stage)
                 for (uint32_t G = cls0[k].gmin; G <= 32; G <<= 1) {
                     const uint32_t fit =
                         fit_warps(stage ? cls0[k].per_chain_staged : cls0[k].per_chain_direct, G);

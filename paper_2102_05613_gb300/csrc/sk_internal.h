@@ -25,6 +25,7 @@ struct alignas(16) JobDev {
     double* rec_E;          // [rec][chains]
     uint32_t* rec_acc;      // [rec][chains]
     double* rec_q;          // [rec][chains/2]
+    double* rec_Enw;        // [rec][chains] node-weighted energy of the record step (or null)
     int32_t* trace;         // [trace_chains][trace_steps]
     int* err;               // error word of the run (kDev* codes)
     unsigned long long* work;  // per chain: [spins flipped, J rows the steps needed]
@@ -70,7 +71,8 @@ inline size_t warp_smem_bytes(uint32_t npad, uint32_t kind, bool staged = true) 
 // stage): the coupling type, the rule, whether row a is staged in shared
 // memory by TMA (stage) or read through L1, the lanes per chain G (4, 8, 16,
 // 32; 32/G chains per warp) and the Philox blocks of sites each lane draws,
-// NB = blocks_per_lane(rule, K, G) (1, 2 or 4: K up to 4 G NB).  step_class
+// NB = blocks_per_lane(rule, K, G) (1, 2 or 4: K up to 4 G NB); stage 2 is
+// stage 0 with node-weighted energy records.  step_class
 // returns -1 for a (K, G) no kernel covers.  A CTA holds W warps, i.e.
 // W * 32/G chains, each with `per_chain` bytes of shared memory.  launch_step
 // runs the items of one class; `bump` advances every job's step counter

@@ -35,6 +35,18 @@ int occupancy_gauss_metropolis_staged(int, int, uint32_t, uint32_t);
 cudaError_t launch_step_gauss_metropolis_direct(int, int, const JobDev*, const WorkItem*, uint32_t, uint32_t*,
                                       uint32_t, uint32_t, uint32_t, uint32_t, cudaStream_t);
 int occupancy_gauss_metropolis_direct(int, int, uint32_t, uint32_t);
+cudaError_t launch_step_pm1_mcmcmc_direct_nw(int, int, const JobDev*, const WorkItem*, uint32_t, uint32_t*,
+                                      uint32_t, uint32_t, uint32_t, uint32_t, cudaStream_t);
+int occupancy_pm1_mcmcmc_direct_nw(int, int, uint32_t, uint32_t);
+cudaError_t launch_step_pm1_metropolis_direct_nw(int, int, const JobDev*, const WorkItem*, uint32_t, uint32_t*,
+                                      uint32_t, uint32_t, uint32_t, uint32_t, cudaStream_t);
+int occupancy_pm1_metropolis_direct_nw(int, int, uint32_t, uint32_t);
+cudaError_t launch_step_gauss_mcmcmc_direct_nw(int, int, const JobDev*, const WorkItem*, uint32_t, uint32_t*,
+                                      uint32_t, uint32_t, uint32_t, uint32_t, cudaStream_t);
+int occupancy_gauss_mcmcmc_direct_nw(int, int, uint32_t, uint32_t);
+cudaError_t launch_step_gauss_metropolis_direct_nw(int, int, const JobDev*, const WorkItem*, uint32_t, uint32_t*,
+                                      uint32_t, uint32_t, uint32_t, uint32_t, cudaStream_t);
+int occupancy_gauss_metropolis_direct_nw(int, int, uint32_t, uint32_t);
 
 namespace {
 
@@ -257,26 +269,35 @@ uint32_t blocks_per_lane(uint32_t rule, uint32_t K, uint32_t G) {
     return 0u;
 }
 
-// class = kind * 128 + rule * 64 + stage * 32 + log2(NB) * 8 + log2(G), or -1
+// class = kind * 256 + rule * 128 + stage * 32 + log2(NB) * 8 + log2(G), or -1;
+// stage 0 rows through L1, 1 rows staged by TMA, 2 rows through L1 with
+// node-weighted energy records
 int step_class(uint32_t kind, uint32_t rule, uint32_t K, uint32_t G, uint32_t stage) {
     const uint32_t nb = blocks_per_lane(rule, K, G);
     if (!nb) return -1;
     int lg = 0;
     while ((1u << lg) < G) ++lg;
     const int lnb = nb == 1 ? 0 : (nb == 2 ? 1 : 2);
-    return static_cast<int>(kind) * 128 + static_cast<int>(rule) * 64 + static_cast<int>(stage != 0) * 32 +
+    return static_cast<int>(kind) * 256 + static_cast<int>(rule) * 128 + static_cast<int>(stage > 2 ? 0 : stage) * 32 +
            lnb * 8 + lg;
 }
 uint32_t class_lanes(int cls) { return 1u << (cls & 7); }
-bool class_staged(int cls) { return ((cls >> 5) & 1) != 0; }
+bool class_staged(int cls) { return ((cls >> 5) & 3) == 1; }
 
 #define SK_DISPATCH(F, ...)                                                          \
     do {                                                                             \
-        const int kind_ = cls >> 7, rule_ = (cls >> 6) & 1, stage_ = (cls >> 5) & 1; \
-        if (kind_ == 0 && rule_ == 0) return stage_ ? F##_pm1_mcmcmc_staged(__VA_ARGS__) : F##_pm1_mcmcmc_direct(__VA_ARGS__); \
-        if (kind_ == 0) return stage_ ? F##_pm1_metropolis_staged(__VA_ARGS__) : F##_pm1_metropolis_direct(__VA_ARGS__); \
-        if (rule_ == 0) return stage_ ? F##_gauss_mcmcmc_staged(__VA_ARGS__) : F##_gauss_mcmcmc_direct(__VA_ARGS__); \
-        return stage_ ? F##_gauss_metropolis_staged(__VA_ARGS__) : F##_gauss_metropolis_direct(__VA_ARGS__); \
+        const int kind_ = cls >> 8, rule_ = (cls >> 7) & 1, stage_ = (cls >> 5) & 3; \
+        if (kind_ == 0 && rule_ == 0)                                                \
+            return stage_ == 1 ? F##_pm1_mcmcmc_staged(__VA_ARGS__)                  \
+                 : stage_ == 2 ? F##_pm1_mcmcmc_direct_nw(__VA_ARGS__) : F##_pm1_mcmcmc_direct(__VA_ARGS__); \
+        if (kind_ == 0)                                                              \
+            return stage_ == 1 ? F##_pm1_metropolis_staged(__VA_ARGS__)              \
+                 : stage_ == 2 ? F##_pm1_metropolis_direct_nw(__VA_ARGS__) : F##_pm1_metropolis_direct(__VA_ARGS__); \
+        if (rule_ == 0)                                                              \
+            return stage_ == 1 ? F##_gauss_mcmcmc_staged(__VA_ARGS__)                \
+                 : stage_ == 2 ? F##_gauss_mcmcmc_direct_nw(__VA_ARGS__) : F##_gauss_mcmcmc_direct(__VA_ARGS__); \
+        return stage_ == 1 ? F##_gauss_metropolis_staged(__VA_ARGS__)                \
+             : stage_ == 2 ? F##_gauss_metropolis_direct_nw(__VA_ARGS__) : F##_gauss_metropolis_direct(__VA_ARGS__); \
     } while (0)
 
 namespace {

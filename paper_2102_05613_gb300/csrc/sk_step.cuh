@@ -213,18 +213,135 @@ __device__ __forceinline__ double chain_energy(const int8_t* S, const void* h, u
     }
 }
 
+// Candidate energies of the star (a3): dE[q] of this lane's slots d =
+// 4 G (q/4) + 4 gl + (q%4) + 1 (slots past K excluded from the minimum), a =
+// site_1 (the centre's flip of a leaf root); returns the group minimum of dE
+// over the K+1 slots (slot 0 has dE = 0).
+template <typename JT, int NB, int G, bool STAGED>
+__device__ __forceinline__ typename Types<JT>::H star_energies(const int8_t* S, const typename Types<JT>::H* hf,
+                                                               const JT* rowA, const uint32_t (&site)[2 * NB],
+                                                               bool leaf, uint32_t K, const Grp<G>& g,
+                                                               typename Types<JT>::H (&dE)[4 * NB], uint32_t& a) {
+    using H = typename Types<JT>::H;
+    a = gshfl(g, site[0], 0) & 0xFFFFu;
+    const int sa = S[a];
+    const H dEa = static_cast<H>(2 * sa) * hf[a];
+    H mloc = 0;
+#pragma unroll
+    for (int q = 0; q < 4 * NB; ++q) {
+        const uint32_t d = 4u * G * (q >> 2) + 4u * g.gl + (q & 3) + 1u;
+        const uint32_t i = site_of<NB>(site, q);
+        const int si = S[i];
+        const H hi = hf[i];
+        const H single = static_cast<H>(2 * si) * hi;
+        // leaf root: the centre flipped at b = site_d (0 if b = a)
+        const JT jab = STAGED ? rowA[i] : __ldg(rowA + i);
+        const H dbl = (i == a) ? H(0) : dEa + single - static_cast<H>(4 * sa * si) * static_cast<H>(jab);
+        const H v = !leaf ? single : (d == 1u ? dEa : dbl);
+        dE[q] = v;
+        if (d <= K) mloc = mloc < v ? mloc : v;
+    }
+    return gmin(g, mloc);
+}
+
+// Weight of a slot with candidate energy dEq (a4): exp(-beta (dEq - m)) times
+// its root factor (`centre`: the centre slot, else a leaf).  +-J: the integer
+// table (0 past its end), times F / 2^20 when the root is not uniform;
+// Gaussian: 2^(-beta log2(e) (dEq - m) + log2 f).
+template <typename JT>
+__device__ __forceinline__ typename Types<JT>::W slot_weight(const JobDev& jb, const uint64_t* Wt, uint32_t wlen,
+                                                             typename Types<JT>::H dEq, typename Types<JT>::H m,
+                                                             bool centre, float nbl2, bool root_weighted) {
+    typename Types<JT>::W x;
+    if constexpr (sizeof(JT) == 1) {
+        const uint32_t idx = static_cast<uint32_t>(dEq - m) >> 1;
+        x = idx < wlen ? __ldg(&Wt[idx]) : 0ull;
+        if (root_weighted)  // floor(x F / 2^20)
+            x = __umul64hi(x << 11, static_cast<unsigned long long>(centre ? jb.fcen : jb.fleaf) << 33);
+    } else {
+        (void)Wt;
+        (void)wlen;
+        x = dev::pow2(fmaf(nbl2, dEq - m, centre ? jb.lcen : jb.lleaf));
+    }
+    return x;
+}
+
+// Node-weighted energy change of the graph that step t generates from the
+// chain's current state (Eq. eq_monte_carlo_graph), without taking the step:
+// sum_j P_node(j) dE_j over its K+1 slots with the weights the step chooses
+// with (Metropolis: p_acc dE of its proposal).  The draws are those of step
+// t (Philox again), so the step loop carries nothing for it.
+template <typename JT, int RULE, int NB, int G>
+__device__ __forceinline__ double graph_mean_dE(const JobDev& jb, uint32_t chain, uint32_t t, const int8_t* S,
+                                                const typename Types<JT>::H* hf, const Grp<G>& g) {
+    using H = typename Types<JT>::H;
+    using W = typename Types<JT>::W;
+    const uint32_t N = jb.N, K = jb.K;
+    const uint32_t k0 = static_cast<uint32_t>(jb.seed), k1 = static_cast<uint32_t>(jb.seed >> 32);
+    const uint32_t c3 = jb.stream & 0xFFFFFFu;
+    const float nbl2 = -jb.beta_eff * 1.4426950408889634f;
+    const uint64_t* Wt = static_cast<const uint64_t*>(jb.W);
+    const uint4 b0 = dev::philox4x32_10(make_uint4(0u, t, chain, c3), k0, k1);
+    if constexpr (RULE == 1) {
+        const uint32_t i = __umulhi(b0.x, N);
+        const H dE = static_cast<H>(2 * S[i]) * hf[i];
+        double pacc = 1.0;
+        if (dE > H(0)) {
+            if constexpr (sizeof(JT) == 1) {
+                const uint32_t k = static_cast<uint32_t>(dE) >> 1;
+                pacc = k < jb.wlen ? static_cast<double>(__ldg(&Wt[k])) * 0x1p-53 : 0.0;
+            } else {
+                pacc = static_cast<double>(dev::pow2(nbl2 * dE));
+            }
+        }
+        return pacc * static_cast<double>(dE);
+    } else {
+        const unsigned long long U0 = (static_cast<unsigned long long>(b0.y) << 32) | b0.x;
+        const bool leaf = U0 >= jb.root_thr;
+        const bool root_weighted = jb.fcen + jb.fleaf != (2u << 20);
+        uint32_t site[2 * NB];
+        draw_sites<NB, G>(site, t, chain, c3, k0, k1, (K + 3u) >> 2, N, g);
+        const uint32_t a0 = gshfl(g, site[0], 0) & 0xFFFFu;
+        const JT* rowA = static_cast<const JT*>(jb.J) + static_cast<size_t>(a0) * jb.Npad;
+        H dE[4 * NB];
+        uint32_t a;
+        const H m = star_energies<JT, NB, G, false>(S, hf, rowA, site, leaf, K, g, dE, a);
+        double num = 0.0, den = 0.0;
+#pragma unroll
+        for (int q = 0; q < 4 * NB; ++q) {
+            const uint32_t d = 4u * G * (q >> 2) + 4u * g.gl + (q & 3) + 1u;
+            if (d <= K) {
+                const W x = slot_weight<JT>(jb, Wt, jb.wlen, dE[q], m, leaf && d == 1u, nbl2, root_weighted);
+                num += static_cast<double>(x) * static_cast<double>(dE[q]);
+                den += static_cast<double>(x);
+            }
+        }
+        const W w0 = slot_weight<JT>(jb, Wt, jb.wlen, H(0), m, !leaf, nbl2, root_weighted);  // slot 0
+        return gsum(g, num) / (gsum(g, den) + static_cast<double>(w0));
+    }
+}
+
 // Record point shared by every thread of the CTA (two CTA barriers).  Only
 // `write` groups (real chains, not shadows) store.
-template <typename JT, int G>
+template <typename JT, int RULE, int NB, int G, bool NWR>
 __device__ __noinline__ void record(const JobDev& jb, bool write, uint32_t chain, uint32_t rec, const int8_t* S,
-                                    const void* h, int partner_off, uint32_t acc) {
+                                    const void* h, int partner_off, uint32_t acc, uint32_t t_next) {
     const Grp<G> g;
     const int8_t* partner_s = S + partner_off;
     const bool store = write && rec < jb.rec_capacity;
     const double E = chain_energy<JT, G>(S, h, jb.Npad, jb.scale, g);
+    // node-weighted energy of this state with the graph of the next step
+    // (kernels built for runs that record it; groups without a chain skip it)
+    double dm = 0.0;
+    if constexpr (NWR) {
+        if (store)
+            dm = graph_mean_dE<JT, RULE, NB, G>(jb, chain, t_next, S, static_cast<const typename Types<JT>::H*>(h), g);
+    }
+    (void)t_next;
     if (store && g.gl == 0) {
         jb.rec_E[static_cast<size_t>(rec) * jb.chains + chain] = E;
         jb.rec_acc[static_cast<size_t>(rec) * jb.chains + chain] = acc;
+        if (NWR) jb.rec_Enw[static_cast<size_t>(rec) * jb.chains + chain] = E + jb.scale * dm;
     }
     __syncthreads();
     if ((chain & 1u) == 0u && chain + 1u < jb.chains) {
@@ -254,6 +371,8 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                                            uint32_t& phase, bool& dead, uint32_t& n_flips, uint32_t& n_rows) {
     using H = typename Types<JT>::H;
     using W = typename Types<JT>::W;
+    constexpr bool STAGED = STAGE == 1;  // 0: rows through L1, 2: the same with node-weighted records
+    constexpr bool NWR = STAGE == 2;
     const Grp<G> g;
     // next record point (0: none; a record follows step t when t + 1 == next_rec)
     uint32_t next_rec = jb.record_every ? (t0 / jb.record_every + 1u) * jb.record_every : 0u;
@@ -282,7 +401,7 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
     uint32_t site[2 * NB];  // packed sites of this step (site_of)
 
     // prologue (staged rows): draw the first step and stage its row
-    if constexpr (STAGE) {
+    if constexpr (STAGED) {
         uint32_t first;
         if constexpr (RULE == 0) {
             draw_sites<NB, G>(site, t0, chain, c3, k0, k1, nblk, N, g);
@@ -313,9 +432,9 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
 
         // direct rows: this step's sites now; staged rows: the next step's
         // sites and the TMA of its first row, one step ahead
-        if constexpr (!STAGE && RULE == 0) draw_sites<NB, G>(site, t, chain, c3, k0, k1, nblk, N, g);
+        if constexpr (!STAGED && RULE == 0) draw_sites<NB, G>(site, t, chain, c3, k0, k1, nblk, N, g);
         uint32_t nsite[2 * NB];
-        if (STAGE && t + 1u < t1) {
+        if (STAGED && t + 1u < t1) {
             uint32_t nx;
             if constexpr (RULE == 0) {
                 draw_sites<NB, G>(nsite, t + 1u, chain, c3, k0, k1, nblk, N, g);
@@ -323,7 +442,7 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
             } else {
                 nx = __umulhi(cm.b0[(t + 1u) & (G - 1)].x, N);
             }
-            if constexpr (STAGE) {
+            if constexpr (STAGED) {
                 __syncwarp(g.mask);  // every lane of the group is done with buffer buf^1 (step t-1)
                 if (g.gl == 0 && !dead) {
                     dev::fence_proxy_async();
@@ -332,7 +451,7 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
             }
             (void)nx;
         }
-        if (STAGE && !dead) {
+        if (STAGED && !dead) {
             // every lane waits; the outcome is made group-uniform
             const bool okl = dev::mbar_wait_bounded(&cm.bar[buf], (phase >> buf) & 1u);
             const bool ok = gballot(g, okl) == (G == 32 ? kFull : ((1u << G) - 1u));
@@ -344,7 +463,7 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
         }
         // row a of this step: staged in shared memory, or read through L1 from J
         const JT* rowA;
-        if constexpr (STAGE) {
+        if constexpr (STAGED) {
             rowA = static_cast<const JT*>(cm.row[buf]);
         } else {
             const uint32_t a0 = RULE == 0 ? (gshfl(g, site[0], 0) & 0xFFFFu) : __umulhi(b0.x, N);
@@ -388,7 +507,7 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                     const H hi = hf[i];
                     const H single = static_cast<H>(2 * si) * hi;
                     // leaf root: the centre flipped at b = site_d (0 if b = a)
-                    const JT jab = STAGE ? rowA[i] : __ldg(rowA + i);
+                    const JT jab = STAGED ? rowA[i] : __ldg(rowA + i);
                     const H dbl = (i == a) ? H(0) : dEa + single - static_cast<H>(4 * sa * si) * static_cast<H>(jab);
                     const H v = !leaf ? single : (d == 1u ? dEa : dbl);
                     dE[q] = v;
@@ -512,7 +631,7 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                 const int c1 = 2 * S[x1];
                 const int c2 = nflip == 2 ? 2 * S[x2] : 0;
                 if (x1_staged)
-                    update_fields<JT, STAGE != 0, G>(hf, rowA, Jrow(x2), c1, c2, npad, g.gl);
+                    update_fields<JT, STAGED, G>(hf, rowA, Jrow(x2), c1, c2, npad, g.gl);
                 else
                     update_fields<JT, false, G>(hf, Jrow(x1), nullptr, c1, 0, npad, g.gl);
                 __syncwarp(g.mask);
@@ -527,12 +646,13 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
             if (t < trace_end && g.gl == 0) jb.trace[static_cast<size_t>(chain) * jb.trace_steps + t] = sel;
             __syncwarp(g.mask);
         }
-        if constexpr (RULE == 0 && STAGE) {
+        if constexpr (RULE == 0 && STAGED) {
 #pragma unroll
             for (int q = 0; q < 2 * NB; ++q) site[q] = nsite[q];
         }
         if (t + 1u == next_rec) {
-            record<JT, G>(jb, write && !dead, chain, next_rec / jb.record_every - 1u, S, hf, partner_off, acc);
+            record<JT, RULE, NB, G, NWR>(jb, write && !dead, chain, next_rec / jb.record_every - 1u, S, hf, partner_off, acc,
+                                    next_rec);
             acc = 0;
             next_rec += jb.record_every;
         }
@@ -541,8 +661,9 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
 
 // MAXT bounds the CTA size and so the register budget per thread
 // (65536 / MAXT): 1024 -> 64, 768 -> 80, 640 -> 96, 512 -> 128 registers.
-// STAGE: stage row a by TMA (two row buffers per chain in shared memory) or
-// read it through L1 (no buffers: more chains fit in shared memory).
+// STAGE: 1 stages row a by TMA (two row buffers per chain in shared memory),
+// 0 reads it through L1 (no buffers: more chains fit in shared memory), 2 is
+// 0 with node-weighted energy records (for runs that ask for them).
 template <typename JT, int RULE, int NB, int G, int STAGE, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1)
     step_kernel(const JobDev* __restrict__ jobs, const WorkItem* __restrict__ items, uint32_t n_items,
@@ -585,7 +706,7 @@ __global__ void __launch_bounds__(MAXT, 1)
         cm.row[0] = base + 5 * static_cast<size_t>(npad);
         cm.row[1] = base + (5 + bj) * static_cast<size_t>(npad);
         cm.bar = &bars[2 * slot];
-        cm.b0 = reinterpret_cast<uint4*>(base + (STAGE ? 5 + 2 * bj : 5) * static_cast<size_t>(npad));
+        cm.b0 = reinterpret_cast<uint4*>(base + (STAGE == 1 ? 5 + 2 * bj : 5) * static_cast<size_t>(npad));
         // the overlap partner (chain slot ^ 1) lives one slice up or down
         const int partner_off = (slot & 1) ? -static_cast<int>(per_chain) : static_cast<int>(per_chain);
         const uint32_t t0 = static_cast<uint32_t>(*jb.step);
@@ -613,7 +734,7 @@ __global__ void __launch_bounds__(MAXT, 1)
                 const uint32_t R = jb.record_every;
                 if (R)
                     for (uint32_t p = (t0 / R + 1u) * R, r = t0 / R; p <= t1; p += R, ++r)
-                        record<JT, G>(jb, false, chain, r, cm.s, cm.h, partner_off, 0u);
+                        record<JT, RULE, NB, G, STAGE == 2>(jb, false, chain, r, cm.s, cm.h, partner_off, 0u, p);
             }
         }
         __syncwarp();

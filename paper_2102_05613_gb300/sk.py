@@ -28,7 +28,7 @@ _STATUS = {0: "SK_OK", 1: "SK_ERR_INVALID_ARG", 2: "SK_ERR_OOM", 3: "SK_ERR_CUDA
 # every symbol declared in include/sk_mcmcmc.h
 EXPORTS = ["sk_create_instance", "sk_set_couplings", "sk_destroy_instance", "sk_energy",
            "mcmcmc_create", "mcmcmc_advance", "mcmcmc_run", "mcmcmc_reset", "mcmcmc_wait",
-           "mcmcmc_observables", "mcmcmc_state", "mcmcmc_recompute", "mcmcmc_recompute_stats",
+           "mcmcmc_observables", "mcmcmc_observables_nw", "mcmcmc_state", "mcmcmc_recompute", "mcmcmc_recompute_stats",
            "mcmcmc_trace", "mcmcmc_counters", "mcmcmc_free",
            "mcmcmc_batch_create", "mcmcmc_batch_advance", "mcmcmc_batch_capture",
            "mcmcmc_batch_replay", "mcmcmc_batch_autotune", "mcmcmc_batch_info",
@@ -49,7 +49,7 @@ class RunParams(C.Structure):
                 ("trace_chains", C.c_uint32), ("trace_steps", C.c_uint64),
                 ("init_spins", C.c_void_p), ("init_mem", C.c_uint32),
                 ("recompute_every", C.c_uint32), ("recompute_terms", C.c_uint32),
-                ("p_center", C.c_double)]
+                ("p_center", C.c_double), ("node_weighted", C.c_uint32)]
 
 
 class RecomputeStats(C.Structure):
@@ -86,6 +86,7 @@ def lib(build_if_missing: bool = True):
             "mcmcmc_reset": [vp, vp, u32],
             "mcmcmc_wait": [vp, u64],
             "mcmcmc_observables": [vp, u64, u64, vp, vp, vp, u32],
+            "mcmcmc_observables_nw": [vp, u64, u64, vp, u32],
             "mcmcmc_state": [vp, vp, vp, vp, u32],
             "mcmcmc_trace": [vp, vp, u32],
             "mcmcmc_counters": [vp, vp, vp],
@@ -194,7 +195,8 @@ class Run:
     def __init__(self, inst: Instance, *, chains: int, K: int = 8, rule: int = SK_RULE_MCMCMC,
                  beta: float = 1.0, seed: int = 1, stream_id: int = 0, record_every: int = 0,
                  max_records: int = 0, init=None, trace_chains: int = 0, trace_steps: int = 0,
-                 recompute_every: int = 0, recompute_terms: int = 0, p_center: float = 0.0):
+                 recompute_every: int = 0, recompute_terms: int = 0, p_center: float = 0.0,
+                 node_weighted: bool = False):
         self.inst = inst
         self.chains, self.K, self.rule = int(chains), int(K), int(rule)
         self.record_every, self.max_records = int(record_every), int(max_records)
@@ -207,6 +209,7 @@ class Run:
         pr.trace_chains, pr.trace_steps = self.trace_chains, self.trace_steps
         pr.recompute_every, pr.recompute_terms = int(recompute_every), int(recompute_terms)
         pr.p_center = float(p_center)
+        pr.node_weighted = 1 if node_weighted else 0
         if init is not None:
             if isinstance(init, np.ndarray):
                 init = np.ascontiguousarray(init, dtype=np.int8)
@@ -245,6 +248,14 @@ class Run:
             ptrs = [_ptr_mem(x)[0] for x in (E, q, acc)]
         _check(lib().mcmcmc_observables(self.handle, first, count, ptrs[0], ptrs[1], ptrs[2], mem))
         return E, q, acc
+
+    def observables_nw(self, first: int = 0, count=None):
+        """Node-weighted energies of records [first, first+count) (mcmcmc_observables_nw)."""
+        if count is None:
+            count = self.max_records - first
+        E = np.zeros((count, self.chains))
+        _check(lib().mcmcmc_observables_nw(self.handle, first, count, E.ctypes.data_as(C.c_void_p), SK_MEM_HOST))
+        return E
 
     def state(self, fields: bool = False):
         N = self.inst.N

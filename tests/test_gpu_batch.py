@@ -189,3 +189,38 @@ def test_lanes_per_chain_do_not_change_results(lanes, staging):
     b.close()
     for _, _, inst, run in made:
         run.close(); inst.close()
+
+
+def test_node_weighted_runs_share_a_batch_with_plain_runs():
+    # a run with node-weighted records gets its own launch class (rows through
+    # L1); both kinds stay bit-exact, autotuned or not, and the node-weighted
+    # records equal the oracle's
+    torch = need_gpu()
+    import oracle
+    N, K, chains, steps, R = 120, 24, 6, 400, 100
+    st = torch.cuda.Stream()
+    J = inputs.couplings_pm1(N, 55)
+    init = inputs.initial_spins(chains, N, 56)
+    made = []
+    for i, nw in enumerate((False, True)):
+        inst = sk.Instance(J, stream=st)
+        run = sk.Run(inst, chains=chains, K=K, beta=0.9, seed=4, stream_id=i, record_every=R,
+                     max_records=steps // R, init=init, node_weighted=nw)
+        made.append((inst, run))
+    b = sk.Batch([r for _, r in made])
+    assert len(b.classes()) == 2
+    b.autotune(trial_steps=20)
+    b.advance(steps)
+    for i, (inst, run) in enumerate(made):
+        E, q, acc = run.observables()
+        spins, _ = run.state()
+        o = oracle.run(J, K=K, beta=0.9, seed=4, stream=i, chains=chains, init=init, steps=steps,
+                       record_every=R)
+        assert np.array_equal(E, o["E"]) and np.array_equal(spins, o["spins"]), i
+        if i == 1:
+            nwE = run.observables_nw()
+            assert np.abs(nwE - o["E_nw"]).max() <= 1e-9 * (1 + np.abs(o["E"]).max())
+    b.close()
+    for inst, run in made:
+        run.close()
+        inst.close()

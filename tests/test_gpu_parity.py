@@ -27,24 +27,33 @@ E_PER_SPIN_TOL = 1e-5
 
 
 def _run_gpu(J, *, chains, K, beta, rule, steps, seed, R=0, init=None, trace=0, scale=1.0,
-             stream_id=0, splits=None, p_center=0.0):
+             stream_id=0, splits=None, p_center=0.0, node_weighted=False):
     inst = sk.Instance(J, scale=scale)
     nrec = steps // R if R else 0
     run = sk.Run(inst, chains=chains, K=K, rule=rule, beta=beta, seed=seed, stream_id=stream_id,
                  record_every=R, max_records=nrec, init=init, trace_chains=trace,
-                 trace_steps=steps if trace else 0, p_center=p_center)
+                 trace_steps=steps if trace else 0, p_center=p_center,
+                 node_weighted=node_weighted and R > 0)
     for s in (splits or [steps]):
         run.advance(s)
     run.wait()
     out = {}
     if nrec:
         out["E"], out["q"], out["acc"] = run.observables()
+        if node_weighted:
+            out["E_nw"] = run.observables_nw()
     out["spins"], out["fields"], out["step"] = run.state(fields=True)
     if trace:
         out["trace"] = run.trace()
     run.close()
     inst.close()
     return out
+
+
+def _nw_close(g, o, tol=1e-9):
+    """Node-weighted record energies: the same double-precision sums taken in
+    another order (+-J weights are the same integers on both sides)."""
+    assert np.abs(g["E_nw"] - o["E_nw"]).max() <= tol * (1.0 + np.abs(o["E"]).max())
 
 
 def _fields_exact(J, spins):
@@ -85,13 +94,16 @@ def test_pm1_bit_exact_shapes(N, K, chains, beta):
     steps, R = 1500, 100
     J = inputs.couplings_pm1(N, N + K)
     init = inputs.initial_spins(chains, N, 7)
+    nw = K % 2 == 0  # runs with node-weighted records use their own kernels
     g = _run_gpu(J, chains=chains, K=K, beta=beta, rule=sk.SK_RULE_MCMCMC, steps=steps, seed=99,
-                 R=R, init=init, trace=min(chains, 3))
+                 R=R, init=init, trace=min(chains, 3), node_weighted=nw)
     o = oracle.run(J, K=K, beta=beta, seed=99, chains=chains, init=init, steps=steps,
                    record_every=R, trace=True)
     assert np.array_equal(g["trace"], o["trace"][: min(chains, 3)])
     assert np.array_equal(g["E"], o["E"])
     assert np.array_equal(g["acc"], o["acc"])
+    if nw:
+        _nw_close(g, o)
     if chains >= 2:
         assert np.array_equal(g["q"], o["q"])
     assert np.array_equal(g["spins"], o["spins"])
@@ -105,13 +117,14 @@ def test_pm1_metropolis_bit_exact(N, beta, scale):
     J = inputs.couplings_pm1(N, 5)
     init = inputs.initial_spins(chains, N, 8)
     g = _run_gpu(J, chains=chains, K=1, beta=beta, rule=sk.SK_RULE_METROPOLIS, steps=steps,
-                 seed=3, R=R, init=init, trace=2, scale=scale)
+                 seed=3, R=R, init=init, trace=2, scale=scale, node_weighted=True)
     o = oracle.run(J, rule=oracle.METROPOLIS, beta=beta, scale=scale, seed=3, chains=chains,
                    init=init, steps=steps, record_every=R, trace=True)
     assert np.array_equal(g["trace"], o["trace"][:2])
     assert np.array_equal(g["E"], o["E"])
     assert np.array_equal(g["acc"], o["acc"])
     assert np.array_equal(g["q"], o["q"])
+    _nw_close(g, o)
     assert np.array_equal(g["spins"], o["spins"])
 
 
@@ -173,6 +186,27 @@ def test_gauss_decision_replay(rule, K, N, beta):
         assert abs(g["E"][-1, c] - oracle.energy(J, g["spins"][c])) / N <= E_PER_SPIN_TOL
         h = J.astype(np.float64) @ g["spins"][c].astype(np.float64)
         assert np.abs(g["fields"][c] - h).max() < 1e-4
+
+
+@pytest.mark.parametrize("rule,K", [(sk.SK_RULE_MCMCMC, 32), (sk.SK_RULE_MCMCMC, 128), (sk.SK_RULE_METROPOLIS, 1)])
+def test_gauss_node_weighted_records(rule, K):
+    """Gaussian couplings: where the GPU and the oracle take the same path (the
+    traces agree), the node-weighted record energies agree within the energy
+    tolerance (fp32 weights and fields against fp64)."""
+    need_gpu()
+    N, chains, steps, R = 96, 4, 600, 100
+    J = inputs.couplings_gauss(N, 41)
+    init = inputs.initial_spins(chains, N, 42)
+    g = _run_gpu(J, chains=chains, K=K, beta=1.0, rule=rule, steps=steps, seed=7, R=R, init=init,
+                 trace=chains, node_weighted=True)
+    orule = oracle.MCMCMC if rule == sk.SK_RULE_MCMCMC else oracle.METROPOLIS
+    o = oracle.run(J, rule=orule, K=K, beta=1.0, seed=7, chains=chains, init=init, steps=steps,
+                   record_every=R, trace=True)
+    same = [c for c in range(chains) if np.array_equal(g["trace"][c], o["trace"][c])]
+    assert len(same) >= 2, same
+    for c in same:
+        assert np.abs(g["E_nw"][:, c] - o["E_nw"][:, c]).max() / N <= E_PER_SPIN_TOL
+        assert np.abs(g["E"][:, c] - o["E"][:, c]).max() / N <= E_PER_SPIN_TOL
 
 
 def test_gauss_statistics_within_3_sigma():
@@ -329,6 +363,10 @@ def test_invalid_arguments_fail_loudly():
         sk.Run(inst, chains=2, K=4, beta=-1.0)
     with pytest.raises(sk.SKError):
         sk.Run(inst, chains=2, K=4, init=np.zeros((2, 16), dtype=np.int8))
+    plain = sk.Run(inst, chains=2, K=4, record_every=10, max_records=2)
+    with pytest.raises(sk.SKError):
+        plain.observables_nw()  # created without node-weighted records
+    plain.close()
     inst.close()
     with pytest.raises(sk.SKError):
         sk.Instance(np.zeros((8193, 8193), dtype=np.int8))

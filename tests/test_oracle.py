@@ -281,42 +281,51 @@ def _state(x, N):
                                                 ("gauss", oracle.MCMCMC, 0.6), ("gauss", oracle.METROPOLIS, 0.0),
                                                 ("pm1", oracle.METROPOLIS, 0.0)])
 def test_node_weighted_energy_is_the_conditional_expectation(kind, rule, p_center):
-    # Eq. eq_monte_carlo_graph: sum_j P_node(j) E(c_j) is E[E(next state) | graph];
-    # its average over graphs from a fixed state x is sum_y P(x, y) E(y)
+    # Eq. eq_monte_carlo_graph: for the recorded state x and the graph T of the
+    # next step, sum_j P_node(j) E(c_j) = E[E(next state) | x, T]; averaged over
+    # T it is sum_y P(x, y) E(y), and it has less variance than E(next state)
     N, K, beta = 5, 3, 0.6
     J = _pm1(N, 74) if kind == "pm1" else _gauss(N, 75)
     wm = 1 if kind == "pm1" else 0
     P = oracle.transition_matrix(J, rule=rule, K=K, beta=beta, weight_mode=wm, p_center=p_center)
     Es = np.array([oracle.energy(J, _state(x, N)) for x in range(1 << N)])
+    PE = P @ Es
     x0 = 0b00110
-    want = float(P[x0] @ Es)
     C = 20000
+    # record after step 0 (state x1, graph of step 1) and after step 1 (state x2)
     r = oracle.run(J, rule=rule, K=K, beta=beta, seed=13, chains=C, init=np.tile(_state(x0, N), (C, 1)),
-                   steps=1, record_every=1, p_center=p_center)
-    nw, e = r["E_nw"][0], r["E"][0]
-    assert abs(nw.mean() - want) < 4 * nw.std() / math.sqrt(C) + 1e-12, (nw.mean(), want)
-    assert nw.var() < e.var()   # the node average removes the choice's variance
+                   steps=2, record_every=1, p_center=p_center)
+    init = np.tile(_state(x0, N), (C, 1))
+    r1 = oracle.run(J, rule=rule, K=K, beta=beta, seed=13, chains=C, init=init, steps=1, p_center=p_center)
+    x1 = ((r1["spins"] < 0).astype(np.int64) << np.arange(N)).sum(axis=1)
+    nw, e2 = r["E_nw"][0], r["E"][1]
+    d = nw - PE[x1]
+    assert abs(d.mean()) < 4 * d.std() / math.sqrt(C) + 1e-12, (d.mean(), d.std())
+    assert abs(nw.mean() - e2.mean()) < 4 * e2.std() / math.sqrt(C)
+    assert nw.var() < e2.var()
 
 
 def test_node_weighted_energy_by_explicit_star():
-    # one step from a fixed state: build the K+1 configurations of the star
-    # from the step's draws, weight their full energies exp(-beta E), compare
+    # after one step, build the K+1 configurations of the next step's star
+    # from its draws, weight their full energies exp(-beta E), compare
     N, K, beta, seed = 9, 6, 0.8, 5
     J = _gauss(N, 76)
     rng = np.random.default_rng(3)
-    for trial in range(6):
-        s0 = rng.choice(np.array([-1, 1], dtype=np.int8), size=N)
-        chain = trial
-        w = oracle.philox([0, 0, chain, 0], [seed, 0])
+    C = 6
+    init = rng.choice(np.array([-1, 1], dtype=np.int8), size=(C, N))
+    r = oracle.run(J, K=K, beta=beta, seed=seed, chains=C, init=init, steps=1, record_every=1)
+    for chain in range(C):
+        s1 = r["spins"][chain]
+        w = oracle.philox([0, 1, chain, 0], [seed, 0])
         U0 = (int(w[1]) << 32) | int(w[0])
         leaf = (U0 * (K + 1)) >> 64 != 0
         sites = []
         for d in range(1, K + 1):
-            b = oracle.philox([1 + (d - 1) // 4, 0, chain, 0], [seed, 0])
+            b = oracle.philox([1 + (d - 1) // 4, 1, chain, 0], [seed, 0])
             sites.append((int(b[(d - 1) % 4]) * N) >> 32)
-        confs = [s0.copy()]
+        confs = [s1.copy()]
         for d in range(1, K + 1):
-            c = s0.copy()
+            c = s1.copy()
             if not leaf:
                 c[sites[d - 1]] *= -1
             else:
@@ -327,10 +336,7 @@ def test_node_weighted_energy_by_explicit_star():
         E = np.array([oracle.energy(J, c) for c in confs])
         wts = np.exp(-beta * (E - E.min()))
         want = float((wts * E).sum() / wts.sum())
-        init = np.zeros((chain + 1, N), dtype=np.int8)
-        init[:] = s0
-        r = oracle.run(J, K=K, beta=beta, seed=seed, chains=chain + 1, init=init, steps=1, record_every=1)
-        assert abs(r["E_nw"][0, chain] - want) < 1e-12, (trial, r["E_nw"][0, chain], want)
+        assert abs(r["E_nw"][0, chain] - want) < 1e-12, (chain, r["E_nw"][0, chain], want)
 
 
 def test_node_weighted_long_run_matches_exact_mean():
