@@ -562,8 +562,15 @@ def run_ours(args):
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     alu_peak = sms * 128 * sm_clock * 1e6 / 1e12  # T lane-ops/s
     achieved = ops_launch / mean_launch_s / 1e12
+    # DRAM bytes of one launch: ncu capture of the 16-instance case at the
+    # profiled layout (class 140: 16 lanes x 2 blocks, rows through L1, 24
+    # warps), 295.8 MB, scaled by the chains processed (the state streamed once
+    # per launch grows in proportion); null for any other layout
+    profiled = [140, 16, 3072, 24]
+    traffic = (4 * 295.8e6 * INSTANCES / 64 if N == 512 and info["classes"]
+               and list(info["classes"][0][:4]) == profiled else None)
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
-                "frac": achieved / alu_peak, "traffic": None,
+                "frac": achieved / alu_peak, "traffic": traffic,
                 "peak_source": f"{sms} SMs x 128 lanes x {sm_clock:.0f} MHz (max SM clock, "
                                f"MEASURED_PEAKS.json)",
                 "kernel": "step_kernel", "ops_per_chain_step": ops_ps,
