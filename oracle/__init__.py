@@ -57,6 +57,14 @@ def lib():
         L.sko_transition_matrix.restype = i
         L.sko_transition_matrix_p.argtypes = [i, i, vp, d, i, i, d, i, i, d, vp]
         L.sko_transition_matrix_p.restype = i
+        L.sko_run_graph.argtypes = [i, i, vp, d, i, i, i, i, d, u64, u32, u32, u32, vp, u64, u32,
+                                    vp, vp, vp, vp, vp]
+        L.sko_run_graph.restype = i
+        L.sko_replay_graph.argtypes = [i, i, vp, d, i, i, i, i, d, u64, u32, u32, vp, u64, vp, d,
+                                       vp, vp, vp, vp]
+        L.sko_replay_graph.restype = C.c_longlong
+        L.sko_transition_matrix_graph.argtypes = [i, i, vp, d, i, i, i, i, d, i, i, vp]
+        L.sko_transition_matrix_graph.restype = i
         _lib = L
     return _lib
 
@@ -177,4 +185,66 @@ def transition_matrix(J, *, rule=MCMCMC, K=2, beta=1.0, scale=1.0, root_mode=0,
                                        weight_mode, float(p_center), _ptr(P))
     if rc != 0:
         raise ValueError(f"transition_matrix failed with {rc}")
+    return P
+
+
+TREE, LINE = 1, 2
+
+
+def graph_nodes(graph, arity=2, depth=1, line_nodes=2):
+    """Nodes of a template: (k^(D+1)-1)/(k-1) for the k-ary tree, L for the line."""
+    if graph == TREE:
+        return (arity ** (depth + 1) - 1) // (arity - 1)
+    return line_nodes
+
+
+def run_graph(J, *, graph=TREE, arity=2, depth=1, line_nodes=2, beta=1.0, scale=1.0, seed=1, stream=0,
+              chain0=0, chains=1, init=None, steps=100, record_every=0, trace=False):
+    """MCMCMC on a k-ary tree (uniform root) or a line (binomial root); see sko_run_graph."""
+    J = np.ascontiguousarray(J)
+    N = J.shape[0]
+    nrec = steps // record_every if record_every else 0
+    E = np.zeros((nrec, chains))
+    acc = np.zeros((nrec, chains), dtype=np.uint32)
+    fin = np.zeros((chains, N), dtype=np.int8)
+    finE = np.zeros(chains)
+    tr = np.zeros((chains, steps), dtype=np.int32) if trace else None
+    init_a = None if init is None else np.ascontiguousarray(init, dtype=np.int8).reshape(chains, N)
+    rc = lib().sko_run_graph(N, _kind_of(J), _ptr(J), scale, graph, arity, depth, line_nodes, beta, seed,
+                             stream, chain0, chains, _ptr(init_a), steps, record_every, _ptr(E), _ptr(acc),
+                             _ptr(fin), _ptr(finE), _ptr(tr))
+    if rc != 0:
+        raise RuntimeError(f"sko_run_graph failed with {rc}")
+    return dict(E=E, acc=acc, spins=fin, final_E=finE, trace=tr)
+
+
+def replay_graph(J, slots, *, graph=TREE, arity=2, depth=1, line_nodes=2, beta=1.0, scale=1.0, seed=1,
+                 stream=0, chain=0, init=None, tol=1e-4):
+    J = np.ascontiguousarray(J)
+    N = J.shape[0]
+    sl = np.ascontiguousarray(slots, dtype=np.int32)
+    dis = C.c_longlong(0)
+    first = C.c_longlong(-1)
+    fin = np.zeros(N, dtype=np.int8)
+    finE = C.c_double(0.0)
+    init_a = None if init is None else np.ascontiguousarray(init, dtype=np.int8)
+    bad = lib().sko_replay_graph(N, _kind_of(J), _ptr(J), scale, graph, arity, depth, line_nodes, beta, seed,
+                                 stream, chain, _ptr(init_a), len(sl), _ptr(sl), tol, C.byref(dis),
+                                 C.byref(first), _ptr(fin), C.byref(finE))
+    if bad < 0:
+        raise RuntimeError(f"sko_replay_graph failed with {bad}")
+    return dict(bad=int(bad), disagree=int(dis.value), first_bad=int(first.value), spins=fin,
+                final_E=finE.value)
+
+
+def transition_matrix_graph(J, *, graph=TREE, arity=2, depth=1, line_nodes=2, beta=1.0, scale=1.0,
+                            weight_mode=0, root_weights=1) -> np.ndarray:
+    """Exact one-step transition matrix on a graph by enumeration (N <= 10, <= 8 nodes)."""
+    J = np.ascontiguousarray(J)
+    N = J.shape[0]
+    P = np.zeros((1 << N, 1 << N))
+    rc = lib().sko_transition_matrix_graph(N, _kind_of(J), _ptr(J), scale, graph, arity, depth, line_nodes,
+                                           beta, weight_mode, root_weights, _ptr(P))
+    if rc != 0:
+        raise ValueError(f"transition_matrix_graph failed with {rc}")
     return P

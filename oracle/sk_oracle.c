@@ -785,3 +785,395 @@ int sko_transition_matrix(int N, int kind, const void* J, double scale, int rule
                           double beta, int root_mode, int weight_mode, double* P) {
     return sko_transition_matrix_p(N, kind, J, scale, rule, K, beta, root_mode, weight_mode, 0.0, P);
 }
+
+/* ------------------------------------------------------------------ */
+/* Deeper graphs (App. B): trees populated from a root                  */
+/* ------------------------------------------------------------------ */
+/*
+ * Templates, nodes numbered 0..V-1 with a parent for every node v >= 1:
+ *   SKO_TREE: the full k-ary tree of depth D (App. B.2, populating process),
+ *             V = (k^(D+1) - 1)/(k - 1), parent(v) = (v - 1)/k; uniform root.
+ *   SKO_LINE: the line of L nodes (App. B.1, addition process), parent(v) =
+ *             v - 1.  Adding each of the L - 1 new nodes at either end with
+ *             probability 1/2 leaves the starting configuration at position v
+ *             with probability binom(L-1, v)/2^(L-1) (Eq. eq_create_line_graph,
+ *             read with L - 1 additions for L nodes, C13), which is the
+ *             populating process of App. B.2 on the line with that root
+ *             distribution.
+ * With the root at position r (the current state c), every other node is
+ * generated from its neighbour toward r by flipping the site drawn for the
+ * edge between them, so P_gen(T|c at r) = p_r N^-(V-1) and the node rule
+ * (Eq. eq_det_balance_graph_solution) weights node v by P_eq(c_v) p_v.
+ *
+ * Root distribution and node factors in integers: F_v = 2^20 for the tree;
+ * for the line F_v = round(2^20 c_v / max_u c_u) with c_0 = 1 and
+ * c_(v+1) = c_v (L-1-v)/(v+1) evaluated in double precision in this order
+ * (c_v = binom(L-1, v)).  The root is the first v whose inclusive prefix
+ * sum of F exceeds floor(U0 sum(F) / 2^64); node weights are
+ * floor(W[(dE - m)/2] F_v / 2^20) (+-J) or exp(-beta (dE - m)) F_v / 2^20
+ * (Gaussian); root probabilities and factors are then exactly proportional.
+ * Nodes whose factor rounds to 0 are never the root and never chosen.
+ *
+ * Draws of step t: block 0 as for the star (U0 root, U1 node); the site of
+ * the edge between v and parent(v) is site_v = floor(w N / 2^32), word
+ * (v-1) % 4 of block 1 + (v-1)/4, v = 1..V-1.  The node chosen is the first
+ * in node order whose inclusive weight prefix exceeds u, as for the star.
+ */
+#define SKO_TREE 1
+#define SKO_LINE 2
+#define SKO_MAX_V 8192
+
+typedef struct {
+    int type, V, k;
+    uint64_t* F;
+    uint64_t Fsum;
+} sko_graph;
+
+static int graph_setup(sko_graph* g, int type, int k, int D, int L) {
+    memset(g, 0, sizeof(*g));
+    if (type == SKO_TREE) {
+        if (k < 2 || D < 1) return -1;
+        long long V = 1, lvl = 1;
+        for (int d = 1; d <= D; ++d) {
+            lvl *= k;
+            V += lvl;
+            if (V > SKO_MAX_V) return -1;
+        }
+        g->V = (int)V;
+    } else if (type == SKO_LINE) {
+        if (L < 2 || L > SKO_MAX_V) return -1;
+        g->V = L;
+    } else {
+        return -1;
+    }
+    g->type = type;
+    g->k = k;
+    g->F = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)g->V);
+    if (!g->F) return -2;
+    if (type == SKO_TREE) {
+        for (int v = 0; v < g->V; ++v) g->F[v] = (uint64_t)1 << 20;
+    } else {
+        double* cv = (double*)malloc(sizeof(double) * (size_t)g->V);
+        if (!cv) return -2;
+        const int n = g->V - 1;
+        double cmax = 1.0;
+        cv[0] = 1.0;
+        for (int v = 0; v < n; ++v) {
+            cv[v + 1] = cv[v] * (double)(n - v) / (double)(v + 1);
+            if (cv[v + 1] > cmax) cmax = cv[v + 1];
+        }
+        for (int v = 0; v < g->V; ++v) g->F[v] = (uint64_t)(cv[v] / cmax * 1048576.0 + 0.5);
+        free(cv);
+    }
+    g->Fsum = 0;
+    for (int v = 0; v < g->V; ++v) g->Fsum += g->F[v];
+    return 0;
+}
+
+static void graph_free(sko_graph* g) { free(g->F); }
+
+static int tparent(const sko_graph* g, int v) { return g->type == SKO_TREE ? (v - 1) / g->k : v - 1; }
+
+static int tdepth(const sko_graph* g, int v) {
+    int d = 0;
+    while (v > 0) { v = tparent(g, v); ++d; }
+    return d;
+}
+
+/* Edges (child node ids) on the template path between a and b, in the order
+   a -> ... -> lca -> ... -> b, into edges[] (capacity V); down[] (capacity
+   V) is scratch.  Returns their number. */
+static int tpath(const sko_graph* g, int a, int b, int* edges, int* down) {
+    int da = tdepth(g, a), db = tdepth(g, b);
+    int n = 0, nd = 0;
+    while (da > db) { edges[n++] = a; a = tparent(g, a); --da; }
+    while (db > da) { down[nd++] = b; b = tparent(g, b); --db; }
+    while (a != b) {
+        edges[n++] = a; a = tparent(g, a);
+        down[nd++] = b; b = tparent(g, b);
+    }
+    for (int i = nd - 1; i >= 0; --i) edges[n++] = down[i];
+    return n;
+}
+
+static int graph_root(const sko_graph* g, uint64_t U0) {
+    const uint64_t x = range64(U0, g->Fsum);
+    uint64_t acc = 0;
+    for (int v = 0; v < g->V; ++v) {
+        acc += g->F[v];
+        if (acc > x) return v;
+    }
+    return g->V - 1;
+}
+
+/* Energy change of flipping the sites x[0..n-1] in order (repeats cancel),
+   from (s, h), using scratch copies s2/h2.  Fields updated as in flip_spin. */
+static double flips_dE(const sko_ctx* c, const int8_t* s, const double* h, const uint32_t* x, int n,
+                       int8_t* s2, double* h2) {
+    memcpy(s2, s, (size_t)c->N);
+    memcpy(h2, h, sizeof(double) * (size_t)c->N);
+    double dE = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const int y = (int)x[i];
+        dE += 2.0 * (double)s2[y] * h2[y];
+        flip_spin(c, s2, h2, y);
+    }
+    return dE;
+}
+
+/* Node weights; F = the node's factor (2^20 = 1). */
+static uint64_t graph_weight_int(const sko_ctx* c, uint64_t F, double dE, double m) {
+    long long d = (long long)llround((dE - m) * 0.5);
+    uint64_t w = (d < c->wlen) ? c->W[d] : 0u;
+    return (uint64_t)(((unsigned __int128)w * (unsigned __int128)F) >> 20);
+}
+static double graph_weight_dbl(const sko_ctx* c, uint64_t F, double dE, double m) {
+    if (!F) return 0.0;
+    return exp(-c->beta * c->scale * (dE - m)) * ldexp((double)F, -20);
+}
+
+/*
+ * One step on a graph: root r from U0, the V-1 edge sites, every node's
+ * energy change relative to the root (its path's flips), the node chosen
+ * with probability ~ P_eq(c_v) F_v, and the move (the chosen path's flips).
+ * forced/own/Pout/uout as for chain_step.  Returns 1 if the state changed.
+ */
+static int graph_step(const sko_ctx* c, const sko_graph* g, uint32_t chain, uint64_t t, int8_t* s, double* h,
+                      int forced, int* own, double* Pout, double* uout, uint32_t* site, double* dE,
+                      int8_t* s2, double* h2, int* edges, int* down, uint32_t* xs) {
+    uint32_t w0[4];
+    draw_block(c->seed, c->stream, 0u, chain, t, 0u, w0);
+    const uint64_t U0 = ((uint64_t)w0[1] << 32) | w0[0];
+    const uint64_t U1 = ((uint64_t)w0[3] << 32) | w0[2];
+    const int V = g->V;
+    const int r = graph_root(g, U0);
+    for (int v = 1; v < V; ++v) {
+        uint32_t wb[4];
+        draw_block(c->seed, c->stream, 0u, chain, t, (uint32_t)(1 + (v - 1) / 4), wb);
+        site[v] = range32(wb[(v - 1) % 4], (uint32_t)c->N);
+    }
+    double m = 0.0;
+    for (int v = 0; v < V; ++v) {
+        const int n = tpath(g, r, v, edges, down);
+        for (int i = 0; i < n; ++i) xs[i] = site[edges[i]];
+        dE[v] = flips_dE(c, s, h, xs, n, s2, h2);
+        if (g->F[v] && dE[v] < m) m = dE[v];
+    }
+    /* weights in node order, first inclusive prefix above u */
+    int j = -1;
+    if (c->kind == SKO_PM1) {
+        uint64_t tot = 0;
+        for (int v = 0; v < V; ++v) tot += graph_weight_int(c, g->F[v], dE[v], m);
+        const uint64_t u = range64(U1, tot);
+        uint64_t acc = 0;
+        for (int v = 0; v < V; ++v) {
+            acc += graph_weight_int(c, g->F[v], dE[v], m);
+            if (Pout) Pout[v] = (double)acc;
+            if (j < 0 && acc > u) j = v;
+        }
+        if (uout) *uout = ldexp((double)U1, -64) * (double)tot;
+    } else {
+        double tot = 0.0;
+        for (int v = 0; v < V; ++v) tot += graph_weight_dbl(c, g->F[v], dE[v], m);
+        const double u = (double)(U1 >> 40) * ldexp(1.0, -24) * tot;
+        double acc = 0.0;
+        for (int v = 0; v < V; ++v) {
+            acc += graph_weight_dbl(c, g->F[v], dE[v], m);
+            if (Pout) Pout[v] = acc;
+            if (j < 0 && acc > u) j = v;
+        }
+        if (j < 0)
+            for (int v = V - 1; v >= 0; --v)
+                if (graph_weight_dbl(c, g->F[v], dE[v], m) > 0.0) { j = v; break; }
+        if (uout) *uout = u;
+    }
+    if (own) *own = j;
+    if (forced >= 0) j = forced;
+    const int n = tpath(g, r, j, edges, down);
+    for (int i = 0; i < n; ++i) flip_spin(c, s, h, (int)site[edges[i]]);
+    /* changed iff some site flips an odd number of times */
+    int changed = 0;
+    for (int i = 0; i < n && !changed; ++i) {
+        int cnt = 0;
+        for (int q = 0; q < n; ++q) cnt += site[edges[q]] == site[edges[i]];
+        changed = cnt & 1;
+    }
+    return changed;
+}
+
+/*
+ * Runs chains on a graph (graph_type SKO_TREE with arity/depth, or SKO_LINE
+ * with `line_nodes`); outputs as sko_run (no overlap, no node-weighted
+ * records).  trace receives the node chosen at each step.
+ */
+int sko_run_graph(int N, int kind, const void* J, double scale, int graph_type, int arity, int depth,
+                  int line_nodes, double beta, uint64_t seed, uint32_t stream, uint32_t chain0,
+                  uint32_t nchains, const int8_t* init_spins, uint64_t nsteps, uint32_t record_every,
+                  double* rec_E, uint32_t* rec_acc, int8_t* final_spins, double* final_E, int32_t* trace) {
+    sko_graph g;
+    int rc = graph_setup(&g, graph_type, arity, depth, line_nodes);
+    if (rc) return rc;
+    sko_ctx c;
+    rc = ctx_init(&c, N, kind, J, scale, SKO_MCMCMC, 1, beta, seed, stream, 0.0);
+    if (rc) { graph_free(&g); return rc; }
+    int8_t* s = (int8_t*)malloc((size_t)N);
+    int8_t* s2 = (int8_t*)malloc((size_t)N);
+    double* h = (double*)malloc(sizeof(double) * (size_t)N);
+    double* h2 = (double*)malloc(sizeof(double) * (size_t)N);
+    uint32_t* site = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)g.V);
+    double* dE = (double*)malloc(sizeof(double) * (size_t)g.V);
+    int* edges = (int*)malloc(sizeof(int) * (size_t)g.V);
+    int* down = (int*)malloc(sizeof(int) * (size_t)g.V);
+    uint32_t* xs = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)g.V);
+    if (!s || !s2 || !h || !h2 || !site || !dE || !edges || !down || !xs) { rc = -2; goto done; }
+    for (uint32_t ci = 0; ci < nchains; ++ci) {
+        const uint32_t chain = chain0 + ci;
+        if (init_spins) memcpy(s, init_spins + (size_t)ci * N, (size_t)N);
+        else sko_init_spins(seed, stream, chain, N, s);
+        sko_fields(N, kind, J, s, h);
+        uint32_t acc = 0;
+        for (uint64_t t = 0; t < nsteps; ++t) {
+            int own = -1;
+            acc += (uint32_t)graph_step(&c, &g, chain, t, s, h, -1, &own, NULL, NULL, site, dE, s2, h2,
+                                        edges, down, xs);
+            if (trace) trace[(size_t)ci * nsteps + t] = own;
+            if (record_every && ((t + 1) % record_every) == 0) {
+                const uint64_t r = (t + 1) / record_every - 1;
+                if (rec_E) rec_E[r * nchains + ci] = sko_energy(N, kind, J, scale, s);
+                if (rec_acc) rec_acc[r * nchains + ci] = acc;
+                acc = 0;
+            }
+        }
+        if (final_spins) memcpy(final_spins + (size_t)ci * N, s, (size_t)N);
+        if (final_E) final_E[ci] = sko_energy(N, kind, J, scale, s);
+    }
+done:
+    free(s); free(s2); free(h); free(h2); free(site); free(dE); free(edges); free(down); free(xs);
+    ctx_free(&c);
+    graph_free(&g);
+    return rc;
+}
+
+/* Decision replay on a graph (see sko_replay). */
+long long sko_replay_graph(int N, int kind, const void* J, double scale, int graph_type, int arity, int depth,
+                           int line_nodes, double beta, uint64_t seed, uint32_t stream, uint32_t chain,
+                           const int8_t* init_spins, uint64_t nsteps, const int32_t* slots, double tol,
+                           long long* n_disagree, long long* first_bad, int8_t* final_spins, double* final_E) {
+    sko_graph g;
+    int rc = graph_setup(&g, graph_type, arity, depth, line_nodes);
+    if (rc) return rc;
+    sko_ctx c;
+    rc = ctx_init(&c, N, kind, J, scale, SKO_MCMCMC, 1, beta, seed, stream, 0.0);
+    if (rc) { graph_free(&g); return rc; }
+    const int V = g.V;
+    int8_t* s = (int8_t*)malloc((size_t)N);
+    int8_t* s2 = (int8_t*)malloc((size_t)N);
+    double* h = (double*)malloc(sizeof(double) * (size_t)N);
+    double* h2 = (double*)malloc(sizeof(double) * (size_t)N);
+    uint32_t* site = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)V);
+    double* dE = (double*)malloc(sizeof(double) * (size_t)V);
+    double* P = (double*)malloc(sizeof(double) * (size_t)V);
+    int* edges = (int*)malloc(sizeof(int) * (size_t)V);
+    int* down = (int*)malloc(sizeof(int) * (size_t)V);
+    uint32_t* xs = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)V);
+    long long bad = 0, dis = 0, first = -1;
+    if (!s || !s2 || !h || !h2 || !site || !dE || !P || !edges || !down || !xs) { bad = -2; goto done; }
+    if (init_spins) memcpy(s, init_spins, (size_t)N);
+    else sko_init_spins(seed, stream, chain, N, s);
+    sko_fields(N, kind, J, s, h);
+    for (uint64_t t = 0; t < nsteps; ++t) {
+        const int gs = slots[t];
+        if (gs < 0 || gs >= V) { bad++; if (first < 0) first = (long long)t; break; }
+        int own = -1;
+        double u = 0.0;
+        graph_step(&c, &g, chain, t, s, h, gs, &own, P, &u, site, dE, s2, h2, edges, down, xs);
+        if (own != gs) {
+            dis++;
+            const double PK = P[V - 1];
+            const double lo = gs == 0 ? 0.0 : P[gs - 1];
+            const double hi = P[gs];
+            if (!(u >= lo - tol * PK && u < hi + tol * PK)) { bad++; if (first < 0) first = (long long)t; }
+        }
+    }
+    if (final_spins) memcpy(final_spins, s, (size_t)N);
+    if (final_E) *final_E = sko_energy(N, kind, J, scale, s);
+    if (n_disagree) *n_disagree = dis;
+    if (first_bad) *first_bad = first;
+done:
+    free(s); free(s2); free(h); free(h2); free(site); free(dE); free(P); free(edges); free(down); free(xs);
+    ctx_free(&c);
+    graph_free(&g);
+    return bad;
+}
+
+/*
+ * Exact one-step transition matrix on a graph by enumeration (small N and
+ * V: every root with probability F_r / sum F and every (V-1)-tuple of edge
+ * sites).  weight_mode 0: fp64 weights; 1: the +-J integer weights.
+ * root_weights 0 drops the node factors F_v from the weights while keeping
+ * the root distribution (the negative control for the line).
+ */
+int sko_transition_matrix_graph(int N, int kind, const void* J, double scale, int graph_type, int arity,
+                                int depth, int line_nodes, double beta, int weight_mode, int root_weights,
+                                double* P) {
+    if (N < 1 || N > 10) return -1;
+    sko_graph g;
+    int rc = graph_setup(&g, graph_type, arity, depth, line_nodes);
+    if (rc) return rc;
+    if (g.V > 8) { graph_free(&g); return -1; }
+    sko_ctx c;
+    rc = ctx_init(&c, N < 2 ? 2 : N, kind, J, scale, SKO_MCMCMC, 1, beta, 0, 0, 0.0);
+    c.N = N;
+    if (rc) { graph_free(&g); return rc; }
+    if (weight_mode == 1 && kind != SKO_PM1) { ctx_free(&c); graph_free(&g); return -1; }
+    const int V = g.V;
+    const uint32_t n = 1u << N;
+    memset(P, 0, sizeof(double) * (size_t)n * n);
+    int8_t s[12], s2[12];
+    double h[12], h2[12];
+    uint32_t site[8], xs[8];
+    double dE[8], w[8];
+    int edges[8], down[8];
+    long long ntup = 1;
+    for (int e = 1; e < V; ++e) ntup *= N;
+    for (uint32_t x = 0; x < n; ++x) {
+        spins_of(x, N, s);
+        sko_fields(N, kind, J, s, h);
+        double* row = P + (size_t)x * n;
+        for (int r = 0; r < V; ++r) {
+            const double pr = (double)g.F[r] / (double)g.Fsum;
+            if (pr == 0.0) continue;
+            for (int e = 0; e < V; ++e) site[e] = 0;
+            for (long long tup = 0; tup < ntup; ++tup) {
+                double m = 0.0;
+                for (int v = 0; v < V; ++v) {
+                    const int ne = tpath(&g, r, v, edges, down);
+                    for (int i = 0; i < ne; ++i) xs[i] = site[edges[i]];
+                    dE[v] = flips_dE(&c, s, h, xs, ne, s2, h2);
+                    if (g.F[v] && dE[v] < m) m = dE[v];
+                }
+                double tot = 0.0;
+                for (int v = 0; v < V; ++v) {
+                    const uint64_t F = root_weights ? g.F[v] : (g.F[v] ? ((uint64_t)1 << 20) : 0u);
+                    w[v] = (weight_mode == 1) ? (double)graph_weight_int(&c, F, dE[v], m)
+                                              : graph_weight_dbl(&c, F, dE[v], m);
+                    tot += w[v];
+                }
+                for (int v = 0; v < V; ++v) {
+                    if (w[v] == 0.0) continue;
+                    const int ne = tpath(&g, r, v, edges, down);
+                    uint32_t y = x;
+                    for (int i = 0; i < ne; ++i) y ^= 1u << site[edges[i]];
+                    row[y] += pr * (w[v] / tot) / (double)ntup;
+                }
+                for (int e = 1; e < V; ++e) {  /* odometer over the edge sites */
+                    if (++site[e] < (uint32_t)N) break;
+                    site[e] = 0;
+                }
+            }
+        }
+    }
+    ctx_free(&c);
+    graph_free(&g);
+    return 0;
+}

@@ -353,6 +353,87 @@ def test_node_weighted_long_run_matches_exact_mean():
     assert nw.var() < e.var()
 
 
+GRAPHS = [dict(graph=oracle.TREE, arity=2, depth=1), dict(graph=oracle.TREE, arity=3, depth=1),
+          dict(graph=oracle.TREE, arity=2, depth=2), dict(graph=oracle.LINE, line_nodes=3),
+          dict(graph=oracle.LINE, line_nodes=4), dict(graph=oracle.LINE, line_nodes=6)]
+
+
+@pytest.mark.parametrize("kind", ["pm1", "gauss"])
+@pytest.mark.parametrize("gi", range(len(GRAPHS)))
+def test_graph_detailed_balance(kind, gi):
+    # App. B: a tree populated from a uniformly placed root is self-thermalising;
+    # the line's binomial root position with node weights ~ P_eq binom(L-1, v)
+    # (Eq. eq_create_line_graph) is reversible too
+    N = 4
+    J = _pm1(N, 17) if kind == "pm1" else _gauss(N, 18)
+    beta = 0.5 if kind == "pm1" else 0.9
+    pi = oracle.boltzmann(J, beta)
+    P = oracle.transition_matrix_graph(J, beta=beta, **GRAPHS[gi])
+    stat, db = _check_balance(P, pi, 1e-12)
+    assert stat < 1e-12 and db < 1e-13, (stat, db)
+    if kind == "pm1":
+        P = oracle.transition_matrix_graph(J, beta=beta, weight_mode=1, **GRAPHS[gi])
+        stat, db = _check_balance(P, pi, 1e-12)
+        assert stat < 1e-12 and db < 1e-12, (stat, db)
+
+
+def test_tree_of_depth_one_is_the_star():
+    J = _gauss(5, 19)
+    for K in (1, 2, 3):
+        if K == 1:
+            Pt = oracle.transition_matrix_graph(J, beta=0.8, graph=oracle.LINE, line_nodes=2)
+        else:
+            Pt = oracle.transition_matrix_graph(J, beta=0.8, graph=oracle.TREE, arity=K, depth=1)
+        Ps = oracle.transition_matrix(J, K=K, beta=0.8)
+        assert np.abs(Pt - Ps).max() < 1e-15, K
+
+
+def test_line_beta_zero_closed_form():
+    # L = 3, beta = 0: root at node 0, 1, 2 w.p. 1/4, 1/2, 1/4 and node v chosen
+    # w.p. binom(2, v)/4; worked out by hand over the two edge sites
+    N = 5
+    P = oracle.transition_matrix_graph(_gauss(N, 53), beta=0.0, graph=oracle.LINE, line_nodes=3)
+    stay = 3 / 8 + 1 / (8 * N)
+    single = 1 / (2 * N)
+    double = 1 / (4 * N * N)
+    for x in range(1 << N):
+        assert abs(P[x, x] - stay) < 1e-14
+        for i in range(N):
+            assert abs(P[x, x ^ (1 << i)] - single) < 1e-14
+            for j in range(i + 1, N):
+                assert abs(P[x, x ^ (1 << i) ^ (1 << j)] - double) < 1e-14
+
+
+@pytest.mark.parametrize("gi", [2, 4])
+def test_graph_one_step_sampler_matches_exact_row(gi):
+    N, beta = 4, 0.6
+    J = _pm1(N, 77)
+    P = oracle.transition_matrix_graph(J, beta=beta, weight_mode=1, **GRAPHS[gi])
+    x0 = 0b0110
+    C = 30000
+    r = oracle.run_graph(J, beta=beta, seed=17, chains=C, init=np.tile(_state(x0, N), (C, 1)), steps=1,
+                         **GRAPHS[gi])
+    ys = ((r["spins"] < 0).astype(np.int64) << np.arange(N)).sum(axis=1)
+    counts = np.bincount(ys, minlength=1 << N).astype(float)
+    assert _chi2_pvalue(counts, P[x0] * C) > 1e-3
+
+
+@pytest.mark.parametrize("g", [dict(graph=oracle.TREE, arity=2, depth=3), dict(graph=oracle.LINE, line_nodes=8)])
+def test_graph_long_run_matches_boltzmann_n12(g):
+    N, beta = 12, 1.0
+    J = _pm1(N, 0)
+    pi = oracle.boltzmann(J, beta)
+    Es = np.array([oracle.energy(J, _state(x, N)) for x in range(1 << N)])
+    C = 6000
+    r = oracle.run_graph(J, beta=beta, seed=5, chains=C, steps=150, **g)
+    ys = ((r["spins"] < 0).astype(np.int64) << np.arange(N)).sum(axis=1)
+    counts = np.bincount(ys, minlength=1 << N).astype(float)
+    levels = np.unique(Es)
+    obs = np.array([counts[Es == e].sum() for e in levels])
+    exp_ = np.array([pi[Es == e].sum() for e in levels]) * C
+    assert _chi2_pvalue(obs, exp_) > 1e-3
+
+
 def test_weight_table_shape():
     W = oracle.weight_table(1.0, 400)
     assert int(W[0]) == 1 << 52
