@@ -58,6 +58,13 @@ typedef enum {
 
 typedef enum { SK_J_PM1 = 0, SK_J_GAUSS = 1 } sk_jkind;      /* int8 +-1 / float32 */
 typedef enum { SK_RULE_MCMCMC = 0, SK_RULE_METROPOLIS = 1 } sk_rule;
+
+/* Graph of an MCMCMC step (App. B): the star (K proposals, the default), the
+ * full k-ary tree of depth D populated from a uniformly drawn root position
+ * (App. B.2), or the line of L nodes grown by the addition process, whose
+ * starting configuration ends at position v with probability
+ * binom(L-1, v)/2^(L-1) (App. B.1, Eq. eq_create_line_graph). */
+typedef enum { SK_GRAPH_STAR = 0, SK_GRAPH_TREE = 1, SK_GRAPH_LINE = 2 } sk_graph;
 typedef enum { SK_MEM_HOST = 0, SK_MEM_DEVICE = 1 } sk_mem;
 
 #define SK_MAX_K 256u        /* proposals per step                         */
@@ -135,6 +142,18 @@ typedef struct {
     uint32_t node_weighted; /* 1: records also hold the node-weighted energy    */
                             /*   (mcmcmc_observables_nw); such runs read row a  */
                             /*   through L1 (no staging)                        */
+    uint32_t graph;         /* sk_graph (MCMCMC only; 0 = the star of K)        */
+    uint32_t arity, depth;  /* SK_GRAPH_TREE: k >= 2, 1 <= D <= 16              */
+    uint32_t line_nodes;    /* SK_GRAPH_LINE: L >= 2                            */
+                            /*   Graphs hold at most 8192 nodes; K is then the  */
+                            /*   number of other nodes (V - 1), traces log the  */
+                            /*   node index; p_center and node_weighted apply   */
+                            /*   to the star only.  One chain per warp; node v  */
+                            /*   is the current state with the sites of the     */
+                            /*   template path from the root to v flipped, and  */
+                            /*   is chosen with probability ~ P_eq F_v (F_v the */
+                            /*   line's binomial factor in 20-bit fixed point,  */
+                            /*   1 for trees).                                  */
 } sk_run_params;
 
 /*

@@ -94,6 +94,57 @@ std::vector<uint64_t> metropolis_table(double beta_eff, uint32_t N) {
     return m;
 }
 
+// Node count of a graph template (0 if the parameters are outside the
+// supported range): the full k-ary tree of depth D (k >= 2, 1 <= D <= 16)
+// or the line of L nodes (2 <= L <= 8192); at most 8192 nodes.
+uint32_t graph_nodes(uint32_t graph, uint32_t k, uint32_t D, uint32_t L) {
+    if (graph == SK_GRAPH_TREE) {
+        if (k < 2 || D < 1 || D > 16) return 0;
+        uint64_t V = 1, lvl = 1;
+        for (uint32_t d = 1; d <= D; ++d) {
+            lvl *= k;
+            V += lvl;
+            if (V > 8192) return 0;
+        }
+        return static_cast<uint32_t>(V);
+    }
+    if (graph == SK_GRAPH_LINE) return (L >= 2 && L <= 8192) ? L : 0;
+    return 0;
+}
+
+// Node factors of a graph (App. B): F_v = 2^20 for the tree (uniform root);
+// for the line, F_v = round(2^20 c_v / max c) with c_0 = 1, c_(v+1) =
+// c_v (L-1-v)/(v+1) in double precision (c_v = binom(L-1, v), the addition
+// process's root distribution).  Table layout: F (u32), inclusive prefix
+// sums (u64), log2(F / 2^20) (float), each of V rounded up to 4 entries.
+std::vector<unsigned char> graph_table(uint32_t graph, uint32_t V) {
+    const size_t V16 = (static_cast<size_t>(V) + 3u) & ~static_cast<size_t>(3u);
+    std::vector<unsigned char> t(16 * V16, 0);
+    uint32_t* F = reinterpret_cast<uint32_t*>(t.data());
+    uint64_t* P = reinterpret_cast<uint64_t*>(t.data() + 4 * V16);
+    float* lg = reinterpret_cast<float*>(t.data() + 12 * V16);
+    if (graph == SK_GRAPH_LINE) {
+        std::vector<double> c(V);
+        const uint32_t n = V - 1;
+        double cmax = 1.0;
+        c[0] = 1.0;
+        for (uint32_t v = 0; v < n; ++v) {
+            c[v + 1] = c[v] * static_cast<double>(n - v) / static_cast<double>(v + 1);
+            if (c[v + 1] > cmax) cmax = c[v + 1];
+        }
+        for (uint32_t v = 0; v < V; ++v) F[v] = static_cast<uint32_t>(c[v] / cmax * 1048576.0 + 0.5);
+    } else {
+        for (uint32_t v = 0; v < V; ++v) F[v] = 1u << 20;
+    }
+    uint64_t acc = 0;
+    for (uint32_t v = 0; v < V; ++v) {
+        acc += F[v];
+        P[v] = acc;
+        lg[v] = F[v] ? static_cast<float>(std::log2(static_cast<double>(F[v])) - 20.0) : -INFINITY;
+    }
+    return t;
+}
+
 }  // namespace
 
 namespace sk {
@@ -128,6 +179,7 @@ struct sk_batch {
         uint64_t key;
         int cls;                 // kernel class incl. G and staging (step_class)
         uint32_t G, gmin, gdef;  // lanes per chain: chosen, fewest allowed, default
+        uint32_t graph;          // 1 k-ary tree, 2 line: the graph kernel (one chain per warp); 0 the star
         uint32_t stage;          // row a staged by TMA (1) or read through L1 (0)
         uint32_t per_chain_staged, per_chain_direct;
         uint32_t per_chain;      // shared memory per chain
@@ -163,6 +215,7 @@ struct sk_run {
     uint32_t* drecAcc = nullptr;
     double* drecQ = nullptr;
     double* drecEnw = nullptr;
+    unsigned char* dgtab = nullptr;  // graph runs: node factors and their prefix sums
     int32_t* dtrace = nullptr;
     uint64_t* dW = nullptr;
     uint32_t wlen = 0;
@@ -312,6 +365,7 @@ void free_run_buffers(sk_run* r) {
     cudaFree(r->drecAcc);
     cudaFree(r->drecQ);
     cudaFree(r->drecEnw);
+    cudaFree(r->dgtab);
     cudaFree(r->dtrace);
     cudaFree(r->dW);
     cudaFree(r->dstep);
@@ -469,7 +523,16 @@ sk_status mcmcmc_create(sk_instance* in, const sk_run_params* p, sk_run** out) {
     if (p->stream_id > 0xFFFFFFu) return fail(SK_ERR_INVALID_ARG, "stream_id must fit 24 bits");
     if (p->trace_chains > p->chains) return fail(SK_ERR_INVALID_ARG, "trace_chains > chains");
     if (p->recompute_terms > 3) return fail(SK_ERR_INVALID_ARG, "recompute_terms must be 0..3");
-    if (p->rule == SK_RULE_MCMCMC) {
+    if (p->graph) {
+        if (p->graph != SK_GRAPH_TREE && p->graph != SK_GRAPH_LINE)
+            return fail(SK_ERR_INVALID_ARG, "unknown graph %u", p->graph);
+        if (p->rule != SK_RULE_MCMCMC) return fail(SK_ERR_INVALID_ARG, "graphs need the MCMCMC rule");
+        if (!graph_nodes(p->graph, p->arity, p->depth, p->line_nodes))
+            return fail(SK_ERR_INVALID_ARG, "graph outside the supported range (k >= 2, 1 <= depth <= 16, "
+                        "2 <= line_nodes, at most 8192 nodes)");
+        if (p->p_center != 0.0 || p->node_weighted)
+            return fail(SK_ERR_INVALID_ARG, "p_center and node_weighted apply to the star only");
+    } else if (p->rule == SK_RULE_MCMCMC) {
         JobDev probe{};
         if (!root_setup(probe, p->K, p->p_center))
             return fail(SK_ERR_INVALID_ARG, "p_center = %g: need 0 (uniform) or 0 < p_center < 1 with both root "
@@ -480,6 +543,8 @@ sk_status mcmcmc_create(sk_instance* in, const sk_run_params* p, sk_run** out) {
     r->p = *p;
     r->chains = p->chains;
     if (r->p.rule == SK_RULE_METROPOLIS) r->p.K = 1;
+    const uint32_t V = r->p.graph ? graph_nodes(r->p.graph, r->p.arity, r->p.depth, r->p.line_nodes) : 0;
+    if (V) r->p.K = V - 1;  // proposals per step: the graph's other nodes
     if (!r->p.record_every) r->p.max_records = 0;
     if (!r->p.trace_chains || !r->p.trace_steps) r->p.trace_chains = 0, r->p.trace_steps = 0;
     const size_t C = r->chains, np = in->Npad, R = r->p.max_records;
@@ -492,6 +557,14 @@ sk_status mcmcmc_create(sk_instance* in, const sk_run_params* p, sk_run** out) {
     if (s == SK_OK) s = dalloc(&r->drecAcc, R * C * 4);
     if (s == SK_OK) s = dalloc(&r->drecQ, R * (C / 2) * 8);
     if (s == SK_OK && r->p.node_weighted) s = dalloc(&r->drecEnw, R * C * 8);
+    if (s == SK_OK && V) {
+        const std::vector<unsigned char> t = graph_table(r->p.graph, V);
+        s = dalloc(&r->dgtab, t.size());
+        if (s == SK_OK) {
+            cudaError_t e = cudaMemcpy(r->dgtab, t.data(), t.size(), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) s = fail(SK_ERR_CUDA, "graph table upload: %s", cudaGetErrorString(e));
+        }
+    }
     if (s == SK_OK) s = dalloc(&r->dtrace, static_cast<size_t>(r->p.trace_chains) * r->p.trace_steps * 4);
     if (s == SK_OK) s = dalloc(&r->dstep, 8);
     if (s == SK_OK) s = dalloc(&r->derr, 4);
@@ -542,6 +615,10 @@ sk_status mcmcmc_create(sk_instance* in, const sk_run_params* p, sk_run** out) {
     j.record_every = r->p.record_every;
     j.trace_chains = r->p.trace_chains;
     j.step_limit = 0xFFFFFFFFu;
+    j.gtab = r->dgtab;
+    j.graph = r->p.graph;
+    j.arity = r->p.arity;
+    j.V = V;
     root_setup(j, r->p.K, r->p.rule == SK_RULE_MCMCMC ? r->p.p_center : 0.0);
     s = init_state(r, p->init_spins, p->init_mem);
     if (s == SK_OK) {
@@ -780,6 +857,12 @@ uint32_t run_gdefault(const sk_run* r) {
 bool run_nw(const sk_run* r) { return r->p.node_weighted && r->p.record_every && r->p.max_records; }
 uint64_t class_key(const sk_run* r) {
     uint32_t b = 128;
+    if (r->p.graph) {  // graph runs: by coupling kind, graph type and node count
+        const uint32_t pc = static_cast<uint32_t>(sk::graph_smem_bytes(r->inst->Npad, r->job.V, r->p.graph));
+        while (b < pc) b <<= 1;
+        return (static_cast<uint64_t>(r->inst->kind) << 62) | (1ull << 59) |
+               (static_cast<uint64_t>(r->p.graph) << 56) | (static_cast<uint64_t>(r->job.V) << 32) | b;
+    }
     const uint32_t pc = run_per_chain(r);
     while (b < pc) b <<= 1;
     const uint64_t kb = sk::site_blocks_pow2(r->p.rule, r->p.K);
@@ -821,6 +904,39 @@ sk_status plan_batch(sk_batch* b) {
             c.per_chain_staged = std::max(c.per_chain_staged, run_per_chain(b->runs[i], true));
             c.per_chain_direct = std::max(c.per_chain_direct, run_per_chain(b->runs[i], false));
             total += b->runs[i]->chains;
+        }
+        if ((c.key >> 59) & 1u) {  // graph runs: one chain per warp, W even
+            c.graph = r0->p.graph;
+            c.G = 32;
+            c.gmin = c.gdef = 32;
+            c.stage = 0;
+            c.per_chain = 0;
+            for (uint32_t i : g.second)
+                c.per_chain = std::max(c.per_chain, static_cast<uint32_t>(sk::graph_smem_bytes(
+                                                        b->runs[i]->inst->Npad, b->runs[i]->job.V, c.graph)));
+            const uint32_t fitg = static_cast<uint32_t>(std::min<size_t>(32, kSmemBudget / c.per_chain)) & ~1u;
+            auto tg = b->tuned.find(c.key);
+            c.W = tg != b->tuned.end() ? (tg->second & 0xFFu) : (b->W_override ? std::min(b->W_override, fitg) : fitg);
+            c.W &= ~1u;
+            if (c.W < 2) return fail(SK_ERR_INVALID_ARG, "graph too large: %u bytes of shared memory per chain", c.per_chain);
+            c.cls = 512 + static_cast<int>(r0->inst->kind) * 4 + static_cast<int>(c.graph);
+            int occg = sk::graph_kernel_occupancy(r0->inst->kind, c.W, c.per_chain);
+            while (occg <= 0 && tg == b->tuned.end() && c.W > 2) {
+                c.W -= 2;
+                occg = sk::graph_kernel_occupancy(r0->inst->kind, c.W, c.per_chain);
+            }
+            if (occg <= 0) return fail(SK_ERR_CUDA, "graph kernel cannot be resident with %u warps", c.W);
+            c.first_item = static_cast<uint32_t>(items.size());
+            for (uint32_t i : g.second) {
+                const sk_run* r = b->runs[i];
+                for (uint32_t ch = 0; ch < r->chains; ch += c.W)
+                    items.push_back(WorkItem{i, ch, std::min(c.W, r->chains - ch), 0});
+            }
+            c.n_items = static_cast<uint32_t>(items.size()) - c.first_item;
+            c.grid = std::min<uint32_t>(c.n_items, static_cast<uint32_t>(occg * sms));
+            grid = std::max(grid, c.grid);
+            classes.push_back(c);
+            continue;
         }
         const bool nw = ((c.key >> 60) & 1u) != 0;  // node-weighted records: rows through L1 only
         auto t = b->tuned.find(c.key);
@@ -936,9 +1052,13 @@ sk_status launch_segment(sk_batch* b, uint64_t steps, int only = -1) {
         if (only >= 0 && static_cast<size_t>(only) != k) continue;
         const sk_batch::Class& c = b->classes[k];
         const bool last = only >= 0 || k + 1 == nc;
-        cudaError_t e = sk::launch_step(b->djobs, b->ditems + c.first_item, c.n_items, b->dqueue + k, steps, c.W,
-                                        c.per_chain, c.grid, c.cls, static_cast<uint32_t>(b->runs.size()), last,
-                                        b->st);
+        cudaError_t e =
+            c.graph ? sk::launch_graph(b->djobs, b->ditems + c.first_item, c.n_items, b->dqueue + k, steps, c.W,
+                                       c.per_chain, c.grid, static_cast<uint32_t>((c.cls - 512) / 4),
+                                       static_cast<uint32_t>(b->runs.size()), last, b->st)
+                    : sk::launch_step(b->djobs, b->ditems + c.first_item, c.n_items, b->dqueue + k, steps, c.W,
+                                      c.per_chain, c.grid, c.cls, static_cast<uint32_t>(b->runs.size()), last,
+                                      b->st);
         if (e != cudaSuccess) return fail(SK_ERR_CUDA, "step launch: %s", cudaGetErrorString(e));
     }
     for (sk_run* r : b->runs) r->step = std::min<uint64_t>(r->step + steps, r->job.step_limit);
@@ -1112,7 +1232,12 @@ sk_status mcmcmc_batch_autotune(sk_batch* b, uint32_t trial_steps, uint32_t* out
             float best_ms = 1e30f;
             std::vector<uint32_t> cand;  // (stage << 16) | (G << 8) | W
             const uint32_t max_stage = ((key >> 60) & 1u) ? 0u : 1u;  // node-weighted classes: no staging
-            for (uint32_t stage = 0; stage <= max_stage; ++stage)
+            if ((key >> 59) & 1u) {  // graph classes: warps per CTA only (even)
+                const uint32_t fitg = static_cast<uint32_t>(std::min<size_t>(32, kSmemBudget / cls0[k].per_chain)) & ~1u;
+                for (uint32_t w : {32u, 24u, 20u, 16u, 12u, 8u, 6u, 4u, 2u})
+                    if (w <= fitg) cand.push_back((0u << 16) | (32u << 8) | w);
+            }
+            for (uint32_t stage = 0; stage <= max_stage && !((key >> 59) & 1u); ++stage)
                 for (uint32_t G = cls0[k].gmin; G <= 32; G <<= 1) {
                     const uint32_t fit =
                         fit_warps(stage ? cls0[k].per_chain_staged : cls0[k].per_chain_direct, G);

@@ -45,6 +45,11 @@ struct alignas(16) JobDev {
     uint32_t fcen, fleaf;
     uint64_t root_thr;
     float lcen, lleaf;
+    // graph runs (graph = 1 k-ary tree, 2 line; 0 the star of the step kernel):
+    // gtab = node factors F[V] (u32, 2^20 = 1), their inclusive prefix sums
+    // (u64) and log2(F / 2^20) (float), each array 16-byte aligned
+    const void* gtab;
+    uint32_t graph, arity, V, gpad_;
 };
 static_assert(sizeof(JobDev) % 16 == 0, "JobDev is copied as 16-byte words");
 
@@ -100,6 +105,15 @@ cudaError_t launch_check_couplings(const void* J, uint32_t kind, uint32_t N, uin
 cudaError_t launch_check_spins(const int8_t* s, uint64_t n, unsigned long long* flag, cudaStream_t st);
 cudaError_t launch_energy(const void* J, uint32_t kind, uint32_t N, uint32_t Npad, double scale,
                           const int8_t* spins, uint32_t count, double* out, cudaStream_t st);
+
+// MCMCMC on deeper graphs (sk_graph.cu): one chain per warp, W warps per CTA,
+// `per_chain` bytes of shared memory per chain (graph_smem_bytes).
+size_t graph_smem_bytes(uint32_t npad, uint32_t V, uint32_t graph);
+size_t graph_table_bytes(uint32_t V);
+cudaError_t launch_graph(const JobDev* jobs, const WorkItem* items, uint32_t n_items, uint32_t* queue,
+                         uint64_t nsteps, uint32_t W, uint32_t per_chain, uint32_t grid, uint32_t kind,
+                         uint32_t n_jobs, bool bump, cudaStream_t st);
+int graph_kernel_occupancy(uint32_t kind, uint32_t W, size_t per_chain);
 
 // Tensor-core field recompute (sk_recompute.cu).  Operand buffers: J as
 // e4m3 (+-J, npad^2 bytes) or three bf16 terms (Gaussian, 3 npad^2 x 2

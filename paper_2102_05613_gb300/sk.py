@@ -49,7 +49,8 @@ class RunParams(C.Structure):
                 ("trace_chains", C.c_uint32), ("trace_steps", C.c_uint64),
                 ("init_spins", C.c_void_p), ("init_mem", C.c_uint32),
                 ("recompute_every", C.c_uint32), ("recompute_terms", C.c_uint32),
-                ("p_center", C.c_double), ("node_weighted", C.c_uint32)]
+                ("p_center", C.c_double), ("node_weighted", C.c_uint32), ("graph", C.c_uint32),
+                ("arity", C.c_uint32), ("depth", C.c_uint32), ("line_nodes", C.c_uint32)]
 
 
 class RecomputeStats(C.Structure):
@@ -58,6 +59,7 @@ class RecomputeStats(C.Structure):
 
 
 SK_RECOMPUTE_CHECK, SK_RECOMPUTE_RESYNC, SK_RECOMPUTE_OUTPUT = 0, 1, 2
+SK_GRAPH_STAR, SK_GRAPH_TREE, SK_GRAPH_LINE = 0, 1, 2
 
 
 _lib = None
@@ -196,7 +198,8 @@ class Run:
                  beta: float = 1.0, seed: int = 1, stream_id: int = 0, record_every: int = 0,
                  max_records: int = 0, init=None, trace_chains: int = 0, trace_steps: int = 0,
                  recompute_every: int = 0, recompute_terms: int = 0, p_center: float = 0.0,
-                 node_weighted: bool = False):
+                 node_weighted: bool = False, graph: int = 0, arity: int = 0, depth: int = 0,
+                 line_nodes: int = 0):
         self.inst = inst
         self.chains, self.K, self.rule = int(chains), int(K), int(rule)
         self.record_every, self.max_records = int(record_every), int(max_records)
@@ -210,6 +213,7 @@ class Run:
         pr.recompute_every, pr.recompute_terms = int(recompute_every), int(recompute_terms)
         pr.p_center = float(p_center)
         pr.node_weighted = 1 if node_weighted else 0
+        pr.graph, pr.arity, pr.depth, pr.line_nodes = int(graph), int(arity), int(depth), int(line_nodes)
         if init is not None:
             if isinstance(init, np.ndarray):
                 init = np.ascontiguousarray(init, dtype=np.int8)
