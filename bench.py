@@ -254,8 +254,14 @@ def latency_report(stream):
 # time to thermalise: MCMCMC vs K = 1 Metropolis (Gaussian N = 1024, beta = 1)
 # ---------------------------------------------------------------------------
 TTT_N, TTT_CHAINS, TTT_BETA = 1024, 4096, 1.0
-TTT_METHODS = [("metropolis", 1, 1, 1 << 23), ("mcmcmc_k32", 0, 32, 1 << 21),
-               ("mcmcmc_k128", 0, 128, 1 << 20)]
+# name, rule, K, steps, graph (the graphs of Fig. fig_sk: the 2^7 line, the
+# binary tree of depth 7, the ternary of depth 5, the 16-ary of depth 3)
+TTT_METHODS = [("metropolis", 1, 1, 1 << 23, {}), ("mcmcmc_k32", 0, 32, 1 << 21, {}),
+               ("mcmcmc_k128", 0, 128, 1 << 20, {}),
+               ("line_128", 0, 1, 1 << 16, dict(graph=2, line_nodes=128)),
+               ("tree2_d7", 0, 1, 1 << 15, dict(graph=1, arity=2, depth=7)),
+               ("tree3_d5", 0, 1, 1 << 14, dict(graph=1, arity=3, depth=5)),
+               ("tree16_d3", 0, 1, 1 << 13, dict(graph=1, arity=16, depth=3))]
 TTT_EPS = (1e-2, 3e-3, 1e-3)
 
 
@@ -273,10 +279,13 @@ def run_ttt(args):
     J = inputs.couplings_gauss(TTT_N, 0)
     inst = sk.Instance(J, stream=stream)
     curves = {}
-    for name, rule, Kt, T in TTT_METHODS:
+    only = set(args.ttt_methods.split(",")) if args.ttt_methods else None
+    for name, rule, Kt, T, gkw in TTT_METHODS:
+        if only and name not in only and name != "mcmcmc_k128":
+            continue
         R = T // 2048
         run = sk.Run(inst, chains=TTT_CHAINS, K=Kt, rule=rule, beta=TTT_BETA, seed=7,
-                     record_every=R, max_records=2048)
+                     record_every=R, max_records=2048, **gkw)
         # each method runs with its own autotuned launch geometry (lanes per
         # chain, chains per CTA); tuning leaves the chains untouched
         batch = sk.Batch([run])
@@ -294,7 +303,9 @@ def run_ttt(args):
         E, _, acc = run.observables()
         s_per_step = a.elapsed_time(b) / 1e3 / T
         curves[name] = dict(R=R, T=T, e=E.mean(axis=1) / TTT_N, per_chain=E / TTT_N,
-                            s_per_step=s_per_step, acc=float(acc.mean()) / R, geometry=geometry)
+                            s_per_step=s_per_step, acc=float(acc.mean()) / R, geometry=geometry,
+                            nodes=Kt + 1 if not gkw else (gkw.get("line_nodes") or
+                                                          (gkw["arity"] ** (gkw["depth"] + 1) - 1) // (gkw["arity"] - 1)))
         run.close()
     # e_inf: mean of the last half of the K=128 run's records; sigma: the
     # equilibrium fluctuation of one record (its chain mean) over that half,
@@ -309,7 +320,8 @@ def run_ttt(args):
     for name, c in curves.items():
         t = (np.arange(len(c["e"])) + 1) * c["R"]
         dev = np.abs(c["e"] - e_inf)
-        m = {"steps_run": c["T"], "s_per_step": c["s_per_step"], "launch_classes": c["geometry"],
+        m = {"steps_run": c["T"], "graph_nodes": c["nodes"], "s_per_step": c["s_per_step"],
+             "launch_classes": c["geometry"],
              "chain_steps_per_s": TTT_CHAINS / c["s_per_step"], "acceptance": c["acc"],
              "e_final": float(c["e"][-1]), "t_therm_steps": {}, "t_therm_s": {}}
         for eps in TTT_EPS:
@@ -324,20 +336,25 @@ def run_ttt(args):
             m["t_therm_steps"][str(eps)] = ts
             m["t_therm_s"][str(eps)] = None if ts is None else ts * c["s_per_step"]
         out["methods"][name] = m
-    sp = {}
-    met = out["methods"]["metropolis"]
-    for name in ("mcmcmc_k32", "mcmcmc_k128"):
-        mm = out["methods"][name]
-        sp[name] = {}
+    sp, ss = {}, {}
+    met = out["methods"].get("metropolis")
+    for name, mm in out["methods"].items():
+        if name == "metropolis" or met is None:
+            continue
+        sp[name], ss[name] = {}, {}
         for eps in TTT_EPS:
             a_, b_ = met["t_therm_s"][str(eps)], mm["t_therm_s"][str(eps)]
+            sa, sb = met["t_therm_steps"][str(eps)], mm["t_therm_steps"][str(eps)]
             if b_ is None:
-                sp[name][str(eps)] = None
+                sp[name][str(eps)] = ss[name][str(eps)] = None
             elif a_ is None:
                 sp[name][str(eps)] = f">{met['steps_run'] * met['s_per_step'] / b_:.3g} (Metropolis not thermalised)"
+                ss[name][str(eps)] = f">{met['steps_run'] / sb:.3g}"
             else:
                 sp[name][str(eps)] = a_ / b_
+                ss[name][str(eps)] = sa / sb
     out["wallclock_speedup_vs_metropolis"] = sp
+    out["mc_step_ratio_vs_metropolis"] = ss
     inst.close()
     print(json.dumps(out), flush=True)
     return 0
@@ -658,6 +675,8 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-low-rate", type=float, default=10.0)
     ap.add_argument("--serve-window", type=float, default=5.0)
+    ap.add_argument("--ttt-methods", default="",
+                    help="comma-separated subset of the --ttt methods (the K=128 reference always runs)")
     ap.add_argument("--ttt", action="store_true",
                     help="time-to-thermalise comparison instead of the throughput line")
     ap.add_argument("--no-recompute", action="store_true",
