@@ -65,6 +65,10 @@ def lib():
         L.sko_replay_graph.restype = C.c_longlong
         L.sko_transition_matrix_graph.argtypes = [i, i, vp, d, i, i, i, i, d, i, i, vp]
         L.sko_transition_matrix_graph.restype = i
+        L.sko_setgen_bruteforce.argtypes = [i, vp, u32]
+        L.sko_setgen_bruteforce.restype = d
+        L.sko_setgen_dp.argtypes = [i, vp, vp]
+        L.sko_setgen_dp.restype = i
         _lib = L
     return _lib
 
@@ -248,3 +252,19 @@ def transition_matrix_graph(J, *, graph=TREE, arity=2, depth=1, line_nodes=2, be
     if rc != 0:
         raise ValueError(f"transition_matrix_graph failed with {rc}")
     return P
+
+
+def setgen_bruteforce(P, M: int) -> float:
+    """P_gen(S | S minus M) by enumerating the orders of M's elements (n <= 12)."""
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    return lib().sko_setgen_bruteforce(P.shape[0], _ptr(P), int(M))
+
+
+def setgen_dp(P) -> np.ndarray:
+    """P_gen(S | S minus M) for every mask M by the first-addition recursion (n <= 26)."""
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    n = P.shape[0]
+    out = np.zeros(1 << n)
+    if lib().sko_setgen_dp(n, _ptr(P), _ptr(out)) != 0:
+        raise ValueError("n outside 1..26")
+    return out

@@ -1177,3 +1177,69 @@ int sko_transition_matrix_graph(int N, int kind, const void* J, double scale, in
     graph_free(&g);
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Set generation probabilities (App. D.1, D.2)                         */
+/* ------------------------------------------------------------------ */
+/*
+ * The process of App. D.1: from a set T ⊊ S, repeatedly choose a parent
+ * uniformly from the current set and generate a new element with
+ * P_gen(e | parent), until the set is S.  For the n elements of S, with
+ * P[e*n + p] = P_gen(e | p), and every M ⊆ S given as a bit mask,
+ * Pt(M) = P_gen(S | S \ M) (Eq. eq_def_rec_P): the probability that the
+ * additions, in any order, are exactly the elements of M.  Pt(empty) = 1;
+ * Pt(S) (no starting element) is 0 by convention.
+ *
+ * sko_setgen_bruteforce: the sum over every order of M's elements of the
+ * product of the per-addition probabilities (1/|current|) sum_{p in current}
+ * P_gen(e | p) -- the definition, by enumeration (|M|! orders).
+ */
+static double setgen_orders(int n, const double* P, uint32_t cur, uint32_t left) {
+    if (!left) return 1.0;
+    const int ncur = __builtin_popcount(cur);
+    double tot = 0.0;
+    for (int e = 0; e < n; ++e) {
+        if (!((left >> e) & 1u)) continue;
+        double pe = 0.0;
+        for (int p = 0; p < n; ++p)
+            if ((cur >> p) & 1u) pe += P[(size_t)e * n + p];
+        pe /= (double)ncur;
+        tot += pe * setgen_orders(n, P, cur | (1u << e), left & ~(1u << e));
+    }
+    return tot;
+}
+
+double sko_setgen_bruteforce(int n, const double* P, uint32_t M) {
+    if (n < 1 || n > 12) return -1.0;
+    const uint32_t all = (n == 32) ? 0xFFFFFFFFu : ((1u << n) - 1u);
+    if ((M & ~all) != 0u) return -1.0;
+    if (M == all) return 0.0;
+    return setgen_orders(n, P, all & ~M, M);
+}
+
+/*
+ * sko_setgen_dp: every Pt(M) by the recursion on the first addition (App. D.2,
+ * Eq. eq_rec_set_mul_el as read for the process above): the first added
+ * element e' of M is generated from a parent in the current set S \ M,
+ *   Pt(M) = (1/|S \ M|) sum_{e' in M} [sum_{p in S \ M} P_gen(e' | p)] Pt(M \ {e'}),
+ * taken over masks in increasing order (M \ {e'} < M).  n <= 26.
+ */
+int sko_setgen_dp(int n, const double* P, double* out) {
+    if (n < 1 || n > 26) return -1;
+    const uint32_t all = (1u << n) - 1u;
+    out[0] = 1.0;
+    for (uint32_t M = 1; M <= all; ++M) {
+        if (M == all) { out[M] = 0.0; continue; }
+        const uint32_t cur = all & ~M;
+        double tot = 0.0;
+        for (int e = 0; e < n; ++e) {
+            if (!((M >> e) & 1u)) continue;
+            double a = 0.0;
+            for (int p = 0; p < n; ++p)
+                if ((cur >> p) & 1u) a += P[(size_t)e * n + p];
+            tot += a * out[M & ~(1u << e)];
+        }
+        out[M] = tot / (double)__builtin_popcount(cur);
+    }
+    return 0;
+}

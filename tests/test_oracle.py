@@ -434,6 +434,63 @@ def test_graph_long_run_matches_boltzmann_n12(g):
     assert _chi2_pvalue(obs, exp_) > 1e-3
 
 
+def _setgen_P(n, seed):
+    rng = np.random.default_rng(seed)
+    P = rng.random((n, n))
+    np.fill_diagonal(P, 0.0)
+    col = P.sum(axis=0, keepdims=True)
+    return P / (1.5 * np.where(col > 0, col, 1.0))  # P[e, p] = P_gen(e | p), leaves mass outside S
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 7])
+def test_setgen_recursion_equals_the_process(n):
+    # App. D.2's recursion on the first addition against the definition of
+    # App. D.1: every order of the missing elements, each addition from a
+    # uniformly chosen parent of the current set
+    P = _setgen_P(n, 10 + n)
+    dp = oracle.setgen_dp(P)
+    for M in range(1 << n):
+        bf = oracle.setgen_bruteforce(P, M)
+        assert abs(dp[M] - bf) <= 1e-15 * max(1.0, abs(bf)), (M, dp[M], bf)
+
+
+def test_setgen_closed_forms():
+    # n = 2: the missing element a comes from the only other element b
+    P = _setgen_P(2, 3)
+    dp = oracle.setgen_dp(P)
+    assert dp[0] == 1.0 and abs(dp[1] - P[0, 1]) < 1e-16 and abs(dp[2] - P[1, 0]) < 1e-16 and dp[3] == 0.0
+    # parent-independent proposals q: any order, any parent: |M|! q^|M|
+    n, q = 8, 0.013
+    Pu = np.full((n, n), q)
+    np.fill_diagonal(Pu, 0.0)
+    dp = oracle.setgen_dp(Pu)
+    for M in range((1 << n) - 1):
+        k = bin(M).count("1")
+        assert abs(dp[M] - math.factorial(k) * q ** k) <= 1e-14 * math.factorial(k) * q ** k
+
+
+def test_setgen_printed_normalisation_differs_by_a_cardinality_factor():
+    # reading of App. D.2: the printed recursion carries 1/(|S'| |S minus S'|) and a
+    # 1/|S| base case; against the process it differs by a factor that depends
+    # only on |S'| (it cancels between sets of one cardinality)
+    n = 6
+    P = _setgen_P(n, 99)
+    dp = oracle.setgen_dp(P)
+    printed = np.zeros(1 << n)
+    full = (1 << n) - 1
+    for M in range(1, full):
+        cur = [p for p in range(n) if not (M >> p) & 1]
+        mem = [e for e in range(n) if (M >> e) & 1]
+        if len(mem) == 1:
+            e = mem[0]
+            printed[M] = sum(P[e, p] for p in range(n) if p != e) / n
+        else:
+            printed[M] = sum(P[e, p] * printed[M & ~(1 << e)] for e in mem for p in cur) / (len(mem) * len(cur))
+    for k in range(1, n):
+        ratios = [printed[M] / dp[M] for M in range(1, full) if bin(M).count("1") == k]
+        assert max(ratios) - min(ratios) <= 1e-12 * max(ratios), k
+
+
 def test_weight_table_shape():
     W = oracle.weight_table(1.0, 400)
     assert int(W[0]) == 1 << 52
