@@ -251,6 +251,32 @@ def latency_report(stream):
 
 
 # ---------------------------------------------------------------------------
+# set-generation probabilities (App. D): every subset of n = 24 elements
+# ---------------------------------------------------------------------------
+def setgen_report(stream, n=24):
+    import numpy as np
+    import torch
+    from paper_2102_05613_gb300 import sk
+    rng = np.random.default_rng(0)
+    P = rng.random((n, n))
+    np.fill_diagonal(P, 0.0)
+    P /= 1.5 * P.sum(axis=0, keepdims=True)
+    out = torch.empty(1 << n, dtype=torch.float64, device="cuda")
+    sk.set_generation(P, out=out, stream=stream)  # warm-up
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    sk.set_generation(P, out=out, stream=stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    # terms of the recursion: for each mask M, |M| x |S minus M| parent sums
+    terms = sum(math.comb(n, m) * m * (n - m) for m in range(1, n))
+    return {"workload": f"generation probabilities of all 2^{n} subsets, random P_gen, double precision",
+            "ms": ms, "subsets_per_s": (1 << n) / (ms / 1e3), "terms_per_s": terms / (ms / 1e3)}
+
+
+# ---------------------------------------------------------------------------
 # time to thermalise: MCMCMC vs K = 1 Metropolis (Gaussian N = 1024, beta = 1)
 # ---------------------------------------------------------------------------
 TTT_N, TTT_CHAINS, TTT_BETA = 1024, 4096, 1.0
@@ -635,6 +661,7 @@ def run_ours(args):
     if rank == 0 and not args.no_recompute:
         rc = recompute_report(stream, peaks)
     lat = latency_report(stream) if rank == 0 else None
+    sg = setgen_report(stream) if rank == 0 else None
 
     for r in runs:
         r.close()
@@ -654,7 +681,7 @@ def run_ours(args):
                 "mc_steps_per_s": mc_steps,
                 "gpu_launches": 2 * args.steps,
                 "roofline": roofline, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
-                "recompute": rc, "latency_config1": lat}
+                "recompute": rc, "latency_config1": lat, "set_generation": sg}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

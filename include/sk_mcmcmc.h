@@ -417,6 +417,28 @@ sk_status mcmcmc_run_noalloc(uint32_t N, uint32_t kind, const void* couplings, d
                              double* energy, void* stream);
 
 /* ---------------------------------------------------------------------- */
+/* Generation probabilities of sets of configurations (App. D)             */
+/* ---------------------------------------------------------------------- */
+/*
+ * sk_set_generation: for a set S of n elements and a generation
+ * probability P_gen(e | p) between them, the probability that the growth
+ * process of App. D.1 -- add one element at a time, generated from a parent
+ * chosen uniformly in the current set -- produces S from S \ M, for every
+ * subset M of S (Eq. eq_def_rec_P), by the recursion on the first addition
+ * (App. D.2; the printed recursion's normalisation differs from the process
+ * by a factor that depends only on |M|, which cancels between sets of one
+ * cardinality).  Computed on the device in double precision, one launch per
+ * cardinality, O(n^2 2^n) work.
+ *   n      1..28 elements;
+ *   P      n*n doubles, host, P[e*n + p] = P_gen(e | p) (finite, >= 0; the
+ *          diagonal is not used);
+ *   out    2^n doubles (mem): out[M] for the bit mask M of the missing
+ *          elements, out[0] = 1, out[2^n - 1] = 0 (no starting element);
+ *   stream cudaStream_t (as void*) or NULL.  Synchronises.
+ */
+sk_status sk_set_generation(uint32_t n, const double* P, double* out, uint32_t mem, void* stream);
+
+/* ---------------------------------------------------------------------- */
 /* Request server: continuous batching of sampling jobs                    */
 /* ---------------------------------------------------------------------- */
 typedef struct sk_server sk_server;

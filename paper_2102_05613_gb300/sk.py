@@ -89,6 +89,7 @@ def lib(build_if_missing: bool = True):
             "mcmcmc_wait": [vp, u64],
             "mcmcmc_observables": [vp, u64, u64, vp, vp, vp, u32],
             "mcmcmc_observables_nw": [vp, u64, u64, vp, u32],
+            "sk_set_generation": [u32, vp, vp, u32, vp],
             "mcmcmc_state": [vp, vp, vp, vp, u32],
             "mcmcmc_trace": [vp, vp, u32],
             "mcmcmc_counters": [vp, vp, vp],
@@ -414,6 +415,7 @@ class ServerStats(C.Structure):
 
 
 SK_JOB_QUEUED, SK_JOB_RUNNING, SK_JOB_DONE, SK_JOB_FAILED = range(4)
+EXPORTS += ["sk_set_generation"]
 EXPORTS += ["sk_server_create", "sk_server_add_couplings", "sk_server_submit", "sk_server_poll",
             "sk_server_result", "sk_server_wait_all", "sk_server_stats", "sk_server_destroy"]
 
@@ -505,3 +507,19 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def set_generation(P, out=None, stream=None):
+    """sk_set_generation: P_gen(S | S minus M) for every bit mask M of an
+    n-element set, P[e, p] = P_gen(e | p).  Returns a numpy array unless a
+    device tensor `out` of 2^n doubles is given."""
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    n = P.shape[0]
+    if out is None:
+        res = np.zeros(1 << n)
+        _check(lib().sk_set_generation(n, P.ctypes.data_as(C.c_void_p), res.ctypes.data_as(C.c_void_p),
+                                       SK_MEM_HOST, _stream_handle(stream)))
+        return res
+    p, mem = _ptr_mem(out)
+    _check(lib().sk_set_generation(n, P.ctypes.data_as(C.c_void_p), p, mem, _stream_handle(stream)))
+    return out

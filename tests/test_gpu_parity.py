@@ -451,3 +451,31 @@ def test_largest_n():
     assert np.array_equal(g["trace"], o["trace"])
     assert np.array_equal(g["E"], o["E"])
     assert np.array_equal(g["spins"], o["spins"])
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 12, 20])
+def test_set_generation_against_oracle(n):
+    """sk_set_generation (App. D.2 recursion over subset masks, one launch per
+    cardinality) against the oracle's recursion: double precision, the same
+    order of terms per mask (differences only from fused multiply-adds)."""
+    torch = need_gpu()
+    rng = np.random.default_rng(n)
+    P = rng.random((n, n))
+    np.fill_diagonal(P, 0.0)
+    col = P.sum(axis=0, keepdims=True)
+    P = P / (1.5 * np.where(col > 0, col, 1.0))
+    got = sk.set_generation(P)
+    want = oracle.setgen_dp(P)
+    assert got[0] == 1.0 and got[-1] == 0.0
+    assert np.all(np.abs(got - want) <= 1e-13 * np.abs(want) + 1e-300)
+    dev = torch.zeros(1 << n, dtype=torch.float64, device="cuda")
+    sk.set_generation(P, out=dev)
+    assert np.array_equal(dev.cpu().numpy(), got)
+
+
+def test_set_generation_arguments():
+    need_gpu()
+    with pytest.raises(sk.SKError):
+        sk.set_generation(np.zeros((29, 29)))
+    with pytest.raises(sk.SKError):
+        sk.set_generation(-np.ones((3, 3)))
