@@ -633,13 +633,12 @@ def run_ours(args):
         hQ = [torch.empty((1, CHAINS // 2), dtype=torch.float64).pin_memory() for _ in runs]
         hA = [torch.empty((1, CHAINS), dtype=torch.int32).pin_memory() for _ in runs]
         def e2e_step():
-            for inst, J in zip(insts, hJ):
-                inst.set_couplings(J)
-            for r, S in zip(runs, hS):
-                r.reset(S)
+            # the batched entry points: every instance's (run's) copy and check
+            # enqueued, one wait for all checks, then the new state
+            sk.set_couplings_many(insts, hJ)
+            sk.reset_many(runs, hS)
             batch.advance(R)
-            for r, e_, q_, a_ in zip(runs, hE, hQ, hA):
-                r.observables(0, 1, out=(e_, q_, a_))
+            sk.observables_many(runs, 0, 1, list(zip(hE, hQ, hA)))
 
         e2e_step()  # untimed: first-use staging buffers
         barrier()

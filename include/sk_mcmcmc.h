@@ -98,6 +98,15 @@ sk_status sk_create_instance(uint32_t N, uint32_t kind, const void* couplings, u
  * re-upload a disorder realisation without reallocating. */
 sk_status sk_set_couplings(sk_instance* inst, const void* couplings, uint32_t mem);
 
+/* sk_set_couplings for n distinct instances at once: every copy and check is
+ * enqueued first (host couplings on each instance's side stream, so they
+ * overlap), the checks are read with one wait, and only if all pass do the
+ * new couplings become current -- all or nothing: on SK_ERR_INVALID_ARG no
+ * instance changes and the message names the first failing instance. */
+sk_status sk_set_couplings_many(sk_instance* const* insts, uint32_t n, const void* const* couplings, uint32_t mem);
+
+/* Releases an instance (waits for its streams).  Free every run created on
+ * it (mcmcmc_free) first: runs keep a pointer to their instance. */
 sk_status sk_destroy_instance(sk_instance* inst);
 
 /*
@@ -191,6 +200,12 @@ sk_status mcmcmc_run(sk_instance* inst, const sk_run_params* p, uint64_t steps, 
  */
 sk_status mcmcmc_reset(sk_run* run, const int8_t* spins, uint32_t mem);
 
+/* mcmcmc_reset for n distinct runs at once (spins[i] for run i, or spins ==
+ * NULL / spins[i] == NULL for the Philox start): the copies and checks of
+ * all start spins are enqueued, read with one wait, and only if all pass are
+ * the runs restarted -- all or nothing, as sk_set_couplings_many. */
+sk_status mcmcmc_reset_many(sk_run* const* runs, uint32_t n, const int8_t* const* spins, uint32_t mem);
+
 /*
  * mcmcmc_wait: blocks until the run's stream is idle, at most timeout_ns
  * nanoseconds (0 = no limit): SK_ERR_TIMEOUT if work is still in flight then.
@@ -208,6 +223,14 @@ sk_status mcmcmc_wait(sk_run* run, uint64_t timeout_ns);
  */
 sk_status mcmcmc_observables(sk_run* run, uint64_t first, uint64_t count, double* energy,
                              double* overlap, uint32_t* accepted, uint32_t mem);
+
+/* mcmcmc_observables for n runs with two waits in all: energy[i], overlap[i],
+ * accepted[i] receive run i's records (each array of n pointers, and each
+ * pointer, may be NULL).  Device errors of any run are reported (with the
+ * run's index) before anything is copied. */
+sk_status mcmcmc_observables_many(sk_run* const* runs, uint32_t n, uint64_t first, uint64_t count,
+                                  double* const* energy, double* const* overlap, uint32_t* const* accepted,
+                                  uint32_t mem);
 
 /*
  * mcmcmc_observables_nw: copies the node-weighted energies of records

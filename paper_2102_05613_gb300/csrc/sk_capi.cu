@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <set>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -165,6 +166,7 @@ struct sk_instance {
     cudaStream_t side = nullptr;
     cudaEvent_t ev_side = nullptr;   // side: copy and check done
     cudaEvent_t ev_jfree = nullptr;  // st: dJstage copied into dJ
+    unsigned long long* hflag = nullptr;  // pinned host copy of dflag
     cudaStream_t st = nullptr;
 };
 
@@ -209,6 +211,8 @@ struct sk_run {
     void* dh = nullptr;
     int8_t* dstage = nullptr;  // start spins from the host, checked before use
     cudaEvent_t ev_sfree = nullptr;  // st: the start kernel has read dstage
+    unsigned long long* dflag = nullptr;  // result word of the start-spin check
+    unsigned long long* hflag = nullptr;  // its pinned host copy
     uint32_t* dacc = nullptr;
     unsigned long long* dwork = nullptr;
     double* drecE = nullptr;
@@ -232,24 +236,22 @@ struct sk_run {
 
 namespace {
 
-// Reads the result word of a device input check run on stream st
-// (synchronises st).
-sk_status read_flag(sk_instance* in, cudaStream_t st, unsigned long long* out) {
-    SK_CU(cudaMemcpyAsync(out, in->dflag, sizeof(*out), cudaMemcpyDeviceToHost, st));
-    SK_CU(cudaStreamSynchronize(st));
-    return SK_OK;
-}
 
-// Copies couplings (host or device, N x N) into the padded device layout and
-// checks them on the device: zero diagonal, entries in {-1,0,1} (+-J) or
-// finite (Gaussian), symmetry.  A new instance takes them directly; an
-// existing one receives them in a staging copy first, so that couplings that
-// fail the check leave the instance unchanged.  Host couplings go through the
-// side stream (the check then does not wait for work queued on st); device
+// Couplings (host or device, N x N) into the padded device layout, checked
+// on the device: zero diagonal, entries in {-1,0,1} (+-J) or finite
+// (Gaussian), symmetry.  A new instance takes them directly; an existing one
+// receives them in a staging copy first, so that couplings that fail the
+// check leave the instance unchanged.  Host couplings go through the side
+// stream (the check then does not wait for work queued on st); device
 // couplings, which work on st may still be producing, through st.
-sk_status upload_couplings(sk_instance* in, const void* J, uint32_t mem, bool fresh) {
+// Three phases, so that many instances can be checked with one wait:
+// couplings_stage enqueues copy, check and the read-back of the result;
+// couplings_verify (after the stream it returns has been synchronised)
+// reports a violation; couplings_commit makes the staged copy current.
+sk_status couplings_stage(sk_instance* in, const void* J, uint32_t mem, bool fresh, cudaStream_t* used) {
     const size_t b = jbytes(in->kind);
     const size_t bytes = static_cast<size_t>(in->Npad) * in->Npad * b;
+    if (!J) return fail(SK_ERR_INVALID_ARG, "couplings are NULL");
     if (mem != SK_MEM_HOST && mem != SK_MEM_DEVICE)
         return fail(SK_ERR_INVALID_ARG, "mem must be SK_MEM_HOST or SK_MEM_DEVICE");
     void* dst = in->dJ;
@@ -266,24 +268,39 @@ sk_status upload_couplings(sk_instance* in, const void* J, uint32_t mem, bool fr
     if (in->N != in->Npad) SK_CU(cudaMemsetAsync(dst, 0, bytes, cs));
     SK_CU(cudaMemcpy2DAsync(dst, in->Npad * b, J, in->N * b, in->N * b, in->N, cudaMemcpyDefault, cs));
     SK_CU(sk::launch_check_couplings(dst, in->kind, in->N, in->Npad, in->dflag, cs));
-    unsigned long long f = 0;
-    sk_status s = read_flag(in, cs, &f);
-    if (s != SK_OK) return s;
-    if (f != ~0ull) {
-        const unsigned code = static_cast<unsigned>(f & 3u);
-        const unsigned i = static_cast<unsigned>((f >> 18) & 0xFFFFu), j = static_cast<unsigned>((f >> 2) & 0xFFFFu);
-        if (code == 1) return fail(SK_ERR_INVALID_ARG, "J[%u][%u] != 0 (diagonal must be zero)", i, j);
-        if (code == 2)
-            return fail(SK_ERR_INVALID_ARG, in->kind == SK_J_PM1 ? "J[%u][%u] is not in {-1,0,1}"
-                                                                 : "J[%u][%u] is not finite", i, j);
-        return fail(SK_ERR_INVALID_ARG, "J is not symmetric at (%u,%u)", i, j);
-    }
+    SK_CU(cudaMemcpyAsync(in->hflag, in->dflag, sizeof(unsigned long long), cudaMemcpyDeviceToHost, cs));
+    *used = cs;
+    return SK_OK;
+}
+sk_status couplings_verify(const sk_instance* in) {
+    const unsigned long long f = *in->hflag;
+    if (f == ~0ull) return SK_OK;
+    const unsigned code = static_cast<unsigned>(f & 3u);
+    const unsigned i = static_cast<unsigned>((f >> 18) & 0xFFFFu), j = static_cast<unsigned>((f >> 2) & 0xFFFFu);
+    if (code == 1) return fail(SK_ERR_INVALID_ARG, "J[%u][%u] != 0 (diagonal must be zero)", i, j);
+    if (code == 2)
+        return fail(SK_ERR_INVALID_ARG, in->kind == SK_J_PM1 ? "J[%u][%u] is not in {-1,0,1}"
+                                                             : "J[%u][%u] is not finite", i, j);
+    return fail(SK_ERR_INVALID_ARG, "J is not symmetric at (%u,%u)", i, j);
+}
+sk_status couplings_commit(sk_instance* in, bool fresh) {
     if (!fresh) {
-        SK_CU(cudaMemcpyAsync(in->dJ, dst, bytes, cudaMemcpyDeviceToDevice, in->st));
+        const size_t bytes = static_cast<size_t>(in->Npad) * in->Npad * jbytes(in->kind);
+        SK_CU(cudaEventRecord(in->ev_side, in->side));  // orders a side-stream stage before the copy
+        SK_CU(cudaStreamWaitEvent(in->st, in->ev_side, 0));
+        SK_CU(cudaMemcpyAsync(in->dJ, in->dJstage, bytes, cudaMemcpyDeviceToDevice, in->st));
         SK_CU(cudaEventRecord(in->ev_jfree, in->st));
     }
     in->jop_valid = false;
     return SK_OK;
+}
+sk_status upload_couplings(sk_instance* in, const void* J, uint32_t mem, bool fresh) {
+    cudaStream_t cs = nullptr;
+    sk_status s = couplings_stage(in, J, mem, fresh, &cs);
+    if (s != SK_OK) return s;
+    SK_CU(cudaStreamSynchronize(cs));
+    if ((s = couplings_verify(in)) != SK_OK) return s;
+    return couplings_commit(in, fresh);
 }
 
 sk_status check_run_error(sk_run* r) {
@@ -297,35 +314,59 @@ sk_status check_run_error(sk_run* r) {
 
 sk_status ensure_recompute(sk_run* r);
 
-sk_status init_state(sk_run* r, const int8_t* spins, uint32_t mem) {
+// Start spins of a run in three phases, as for the couplings: spins_stage
+// enqueues the copy of host spins into the run's staging buffer (side
+// stream) and their check (+-1) with the read-back of its result;
+// spins_verify reports a bad spin; init_commit writes the start state.
+sk_status spins_stage(sk_run* r, const int8_t* spins, uint32_t mem, cudaStream_t* used, const int8_t** dinit) {
     sk_instance* in = r->inst;
+    *dinit = nullptr;
+    *used = nullptr;
+    if (!spins) return SK_OK;
+    const size_t n = static_cast<size_t>(r->chains) * in->N;
+    if (mem == SK_MEM_DEVICE) {
+        *dinit = spins;
+    } else if (mem == SK_MEM_HOST) {
+        if (!r->dstage) {
+            sk_status s = dalloc(&r->dstage, n);
+            if (s != SK_OK) return s;
+        }
+        SK_CU(cudaStreamWaitEvent(in->side, r->ev_sfree, 0));  // the last start has read the stage
+        SK_CU(cudaMemcpyAsync(r->dstage, spins, n, cudaMemcpyHostToDevice, in->side));
+        *dinit = r->dstage;
+    } else {
+        return fail(SK_ERR_INVALID_ARG, "init_mem must be SK_MEM_HOST or SK_MEM_DEVICE");
+    }
+    cudaStream_t cs = mem == SK_MEM_HOST ? in->side : in->st;
+    SK_CU(sk::launch_check_spins(*dinit, n, r->dflag, cs));
+    SK_CU(cudaMemcpyAsync(r->hflag, r->dflag, sizeof(unsigned long long), cudaMemcpyDeviceToHost, cs));
+    *used = cs;
+    return SK_OK;
+}
+sk_status spins_verify(const sk_run* r) {
+    const unsigned long long f = *r->hflag;
+    if (f != ~0ull) return fail(SK_ERR_INVALID_ARG, "initial spin %llu is not +-1", f >> 2);
+    return SK_OK;
+}
+sk_status init_commit(sk_run* r, const int8_t* dinit);
+
+sk_status init_state(sk_run* r, const int8_t* spins, uint32_t mem) {
+    cudaStream_t cs = nullptr;
     const int8_t* dinit = nullptr;
-    if (spins) {
-        const size_t n = static_cast<size_t>(r->chains) * in->N;
-        if (mem == SK_MEM_DEVICE) {
-            dinit = spins;
-        } else if (mem == SK_MEM_HOST) {  // through the run's staging buffer, on the side stream
-            if (!r->dstage) {
-                sk_status s = dalloc(&r->dstage, n);
-                if (s != SK_OK) return s;
-            }
-            SK_CU(cudaStreamWaitEvent(in->side, r->ev_sfree, 0));  // the last start has read the stage
-            SK_CU(cudaMemcpyAsync(r->dstage, spins, n, cudaMemcpyHostToDevice, in->side));
-            dinit = r->dstage;
-        } else {
-            return fail(SK_ERR_INVALID_ARG, "init_mem must be SK_MEM_HOST or SK_MEM_DEVICE");
-        }
-        // checked on the device before anything of the run is written
-        cudaStream_t cs = mem == SK_MEM_HOST ? in->side : in->st;
-        SK_CU(sk::launch_check_spins(dinit, n, in->dflag, cs));
-        unsigned long long f = 0;
-        sk_status s = read_flag(in, cs, &f);
-        if (s != SK_OK) return s;
-        if (f != ~0ull) return fail(SK_ERR_INVALID_ARG, "initial spin %llu is not +-1", f >> 2);
-        if (mem == SK_MEM_HOST) {
-            SK_CU(cudaEventRecord(in->ev_side, in->side));
-            SK_CU(cudaStreamWaitEvent(in->st, in->ev_side, 0));
-        }
+    sk_status s = spins_stage(r, spins, mem, &cs, &dinit);
+    if (s != SK_OK) return s;
+    if (cs) {
+        SK_CU(cudaStreamSynchronize(cs));
+        if ((s = spins_verify(r)) != SK_OK) return s;
+    }
+    return init_commit(r, dinit);
+}
+
+sk_status init_commit(sk_run* r, const int8_t* dinit) {
+    sk_instance* in = r->inst;
+    if (dinit && dinit == r->dstage) {  // the staged copy was made on the side stream
+        SK_CU(cudaEventRecord(in->ev_side, in->side));
+        SK_CU(cudaStreamWaitEvent(in->st, in->ev_side, 0));
     }
     SK_CU(cudaMemsetAsync(r->dstep, 0, sizeof(uint64_t), in->st));
     SK_CU(cudaMemsetAsync(r->derr, 0, sizeof(int), in->st));
@@ -375,6 +416,8 @@ void free_run_buffers(sk_run* r) {
     cudaFree(r->dstats);
     cudaFree(r->dstage);
     if (r->ev_sfree) cudaEventDestroy(r->ev_sfree);
+    cudaFree(r->dflag);
+    if (r->hflag) cudaFreeHost(r->hflag);
 }
 
 // Operand buffers of the tensor-core recompute, allocated on first use.
@@ -441,7 +484,8 @@ sk_status sk_create_instance(uint32_t N, uint32_t kind, const void* couplings, u
     s = dalloc(&in->dJ, static_cast<size_t>(in->Npad) * in->Npad * jbytes(kind));
     if (s == SK_OK) s = dalloc(&in->dflag, sizeof(unsigned long long));
     if (s == SK_OK) {
-        cudaError_t e = cudaStreamCreateWithFlags(&in->side, cudaStreamNonBlocking);
+        cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(&in->hflag), sizeof(unsigned long long), cudaHostAllocDefault);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&in->side, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&in->ev_side, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&in->ev_jfree, cudaEventDisableTiming);
         if (e != cudaSuccess) s = fail(SK_ERR_CUDA, "stream/event creation: %s", cudaGetErrorString(e));
@@ -450,6 +494,7 @@ sk_status sk_create_instance(uint32_t N, uint32_t kind, const void* couplings, u
     if (s != SK_OK) {
         cudaFree(in->dJ);
         cudaFree(in->dflag);
+        if (in->hflag) cudaFreeHost(in->hflag);
         if (in->ev_side) cudaEventDestroy(in->ev_side);
         if (in->ev_jfree) cudaEventDestroy(in->ev_jfree);
         if (in->side) cudaStreamDestroy(in->side);
@@ -465,6 +510,31 @@ sk_status sk_set_couplings(sk_instance* in, const void* couplings, uint32_t mem)
     return upload_couplings(in, couplings, mem, false);
 }
 
+sk_status sk_set_couplings_many(sk_instance* const* insts, uint32_t n, const void* const* couplings, uint32_t mem) {
+    if (!insts || !couplings) return fail(SK_ERR_INVALID_ARG, "NULL argument");
+    std::set<const sk_instance*> seen;
+    for (uint32_t i = 0; i < n; ++i) {
+        if (!insts[i] || !couplings[i]) return fail(SK_ERR_INVALID_ARG, "instance or couplings %u is NULL", i);
+        if (!seen.insert(insts[i]).second) return fail(SK_ERR_INVALID_ARG, "instance %u appears twice", i);
+    }
+    std::vector<cudaStream_t> used(n, nullptr);
+    for (uint32_t i = 0; i < n; ++i) {
+        sk_status s = couplings_stage(insts[i], couplings[i], mem, false, &used[i]);
+        if (s != SK_OK) return s;
+    }
+    std::set<cudaStream_t> streams(used.begin(), used.end());
+    for (cudaStream_t cs : streams) SK_CU(cudaStreamSynchronize(cs));
+    for (uint32_t i = 0; i < n; ++i) {
+        sk_status s = couplings_verify(insts[i]);
+        if (s != SK_OK) return fail(s, "instance %u: %s", i, g_err.c_str());
+    }
+    for (uint32_t i = 0; i < n; ++i) {
+        sk_status s = couplings_commit(insts[i], false);
+        if (s != SK_OK) return s;
+    }
+    return SK_OK;
+}
+
 sk_status sk_destroy_instance(sk_instance* in) {
     if (!in) return fail(SK_ERR_INVALID_ARG, "instance is NULL");
     cudaStreamSynchronize(in->st);
@@ -473,6 +543,7 @@ sk_status sk_destroy_instance(sk_instance* in) {
     cudaFree(in->dJop);
     cudaFree(in->dJstage);
     cudaFree(in->dflag);
+    cudaFreeHost(in->hflag);
     cudaEventDestroy(in->ev_side);
     cudaEventDestroy(in->ev_jfree);
     cudaStreamDestroy(in->side);
@@ -570,6 +641,10 @@ sk_status mcmcmc_create(sk_instance* in, const sk_run_params* p, sk_run** out) {
     if (s == SK_OK) s = dalloc(&r->derr, 4);
     if (s == SK_OK && cudaEventCreateWithFlags(&r->ev_sfree, cudaEventDisableTiming) != cudaSuccess)
         s = fail(SK_ERR_CUDA, "event creation failed");
+    if (s == SK_OK) s = dalloc(&r->dflag, sizeof(unsigned long long));
+    if (s == SK_OK && cudaHostAlloc(reinterpret_cast<void**>(&r->hflag), sizeof(unsigned long long),
+                                    cudaHostAllocDefault) != cudaSuccess)
+        s = fail(SK_ERR_OOM, "pinned host allocation failed");
     if (s == SK_OK && in->kind == SK_J_PM1) {
         const double be = r->p.beta * in->scale;
         std::vector<uint64_t> t = r->p.rule == SK_RULE_MCMCMC ? mcmcmc_table(be, in->N) : metropolis_table(be, in->N);
@@ -656,6 +731,73 @@ sk_status mcmcmc_run(sk_instance* in, const sk_run_params* p, uint64_t steps, sk
 sk_status mcmcmc_reset(sk_run* r, const int8_t* spins, uint32_t mem) {
     if (!r) return fail(SK_ERR_INVALID_ARG, "run is NULL");
     return init_state(r, spins, mem);
+}
+
+sk_status mcmcmc_reset_many(sk_run* const* runs, uint32_t n, const int8_t* const* spins, uint32_t mem) {
+    if (!runs) return fail(SK_ERR_INVALID_ARG, "NULL argument");
+    std::set<const sk_run*> seen;
+    for (uint32_t i = 0; i < n; ++i) {
+        if (!runs[i]) return fail(SK_ERR_INVALID_ARG, "run %u is NULL", i);
+        if (!seen.insert(runs[i]).second) return fail(SK_ERR_INVALID_ARG, "run %u appears twice", i);
+    }
+    std::vector<cudaStream_t> used(n, nullptr);
+    std::vector<const int8_t*> dinit(n, nullptr);
+    for (uint32_t i = 0; i < n; ++i) {
+        sk_status s = spins_stage(runs[i], spins ? spins[i] : nullptr, mem, &used[i], &dinit[i]);
+        if (s != SK_OK) return s;
+    }
+    std::set<cudaStream_t> streams;
+    for (cudaStream_t cs : used)
+        if (cs) streams.insert(cs);
+    for (cudaStream_t cs : streams) SK_CU(cudaStreamSynchronize(cs));
+    for (uint32_t i = 0; i < n; ++i) {
+        if (!used[i]) continue;
+        sk_status s = spins_verify(runs[i]);
+        if (s != SK_OK) return fail(s, "run %u: %s", i, g_err.c_str());
+    }
+    for (uint32_t i = 0; i < n; ++i) {
+        sk_status s = init_commit(runs[i], dinit[i]);
+        if (s != SK_OK) return s;
+    }
+    return SK_OK;
+}
+
+sk_status mcmcmc_observables_many(sk_run* const* runs, uint32_t n, uint64_t first, uint64_t count,
+                                  double* const* energy, double* const* overlap, uint32_t* const* accepted,
+                                  uint32_t mem) {
+    if (!runs) return fail(SK_ERR_INVALID_ARG, "NULL argument");
+    if (mem != SK_MEM_HOST && mem != SK_MEM_DEVICE) return fail(SK_ERR_INVALID_ARG, "bad mem");
+    std::set<cudaStream_t> streams;
+    for (uint32_t i = 0; i < n; ++i) {
+        sk_run* r = runs[i];
+        if (!r) return fail(SK_ERR_INVALID_ARG, "run %u is NULL", i);
+        if (first + count > r->p.max_records)
+            return fail(SK_ERR_INVALID_ARG, "run %u: records [%llu, %llu) beyond capacity %llu", i,
+                        (unsigned long long)first, (unsigned long long)(first + count),
+                        (unsigned long long)r->p.max_records);
+        streams.insert(r->inst->st);
+        SK_CU(cudaMemcpyAsync(r->hflag, r->derr, sizeof(int), cudaMemcpyDeviceToHost, r->inst->st));
+    }
+    for (cudaStream_t cs : streams) SK_CU(cudaStreamSynchronize(cs));
+    for (uint32_t i = 0; i < n; ++i) {
+        const int h = *reinterpret_cast<const int*>(runs[i]->hflag);
+        if (h == sk::kDevTimeout) return fail(SK_ERR_TIMEOUT, "run %u: a bounded device wait expired", i);
+        if (h == sk::kDevBounds) return fail(SK_ERR_DEVICE, "run %u: a kernel reported an out-of-range index", i);
+    }
+    if (count == 0) return SK_OK;
+    for (uint32_t i = 0; i < n; ++i) {
+        sk_run* r = runs[i];
+        const size_t C = r->chains;
+        cudaStream_t st = r->inst->st;
+        if (energy && energy[i])
+            SK_CU(cudaMemcpyAsync(energy[i], r->drecE + first * C, count * C * 8, cudaMemcpyDefault, st));
+        if (accepted && accepted[i])
+            SK_CU(cudaMemcpyAsync(accepted[i], r->drecAcc + first * C, count * C * 4, cudaMemcpyDefault, st));
+        if (overlap && overlap[i] && C >= 2)
+            SK_CU(cudaMemcpyAsync(overlap[i], r->drecQ + first * (C / 2), count * (C / 2) * 8, cudaMemcpyDefault, st));
+    }
+    for (cudaStream_t cs : streams) SK_CU(cudaStreamSynchronize(cs));
+    return SK_OK;
 }
 
 sk_status mcmcmc_wait(sk_run* r, uint64_t timeout_ns) {

@@ -11,6 +11,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import sys
 
 import numpy as np
 
@@ -90,6 +91,9 @@ def lib(build_if_missing: bool = True):
             "mcmcmc_observables": [vp, u64, u64, vp, vp, vp, u32],
             "mcmcmc_observables_nw": [vp, u64, u64, vp, u32],
             "sk_set_generation": [u32, vp, vp, u32, vp],
+            "sk_set_couplings_many": [vp, u32, vp, u32],
+            "mcmcmc_reset_many": [vp, u32, vp, u32],
+            "mcmcmc_observables_many": [vp, u32, u64, u64, vp, vp, vp, u32],
             "mcmcmc_state": [vp, vp, vp, vp, u32],
             "mcmcmc_trace": [vp, vp, u32],
             "mcmcmc_counters": [vp, vp, vp],
@@ -186,6 +190,11 @@ class Instance:
             self.handle = None
 
     def __del__(self):
+        # at interpreter exit the order in which objects (and the CUDA
+        # runtime) are torn down is not defined: leave the memory to the
+        # process exit rather than call into the library then
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:
@@ -314,6 +323,11 @@ class Run:
             self.handle = None
 
     def __del__(self):
+        # at interpreter exit the order in which objects (and the CUDA
+        # runtime) are torn down is not defined: leave the memory to the
+        # process exit rather than call into the library then
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:
@@ -371,6 +385,11 @@ class Batch:
             self.handle = None
 
     def __del__(self):
+        # at interpreter exit the order in which objects (and the CUDA
+        # runtime) are torn down is not defined: leave the memory to the
+        # process exit rather than call into the library then
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:
@@ -415,7 +434,7 @@ class ServerStats(C.Structure):
 
 
 SK_JOB_QUEUED, SK_JOB_RUNNING, SK_JOB_DONE, SK_JOB_FAILED = range(4)
-EXPORTS += ["sk_set_generation"]
+EXPORTS += ["sk_set_generation", "sk_set_couplings_many", "mcmcmc_reset_many", "mcmcmc_observables_many"]
 EXPORTS += ["sk_server_create", "sk_server_add_couplings", "sk_server_submit", "sk_server_poll",
             "sk_server_result", "sk_server_wait_all", "sk_server_stats", "sk_server_destroy"]
 
@@ -503,6 +522,11 @@ class Server:
             self.handle = None
 
     def __del__(self):
+        # at interpreter exit the order in which objects (and the CUDA
+        # runtime) are torn down is not defined: leave the memory to the
+        # process exit rather than call into the library then
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:
@@ -523,3 +547,44 @@ def set_generation(P, out=None, stream=None):
     p, mem = _ptr_mem(out)
     _check(lib().sk_set_generation(n, P.ctypes.data_as(C.c_void_p), p, mem, _stream_handle(stream)))
     return out
+
+
+def _ptr_array(items):
+    """(ctypes array of pointers, mem) of numpy arrays / torch tensors (None -> NULL)."""
+    arr = (C.c_void_p * len(items))()
+    mem = SK_MEM_HOST
+    for i, x in enumerate(items):
+        p, m = _ptr_mem(x)
+        arr[i] = p.value if isinstance(p, C.c_void_p) else p
+        if x is not None:
+            mem = m
+    return arr, mem
+
+
+def set_couplings_many(insts, couplings):
+    """sk_set_couplings_many: new couplings for many instances, all or nothing."""
+    cs = [np.ascontiguousarray(J) if isinstance(J, np.ndarray) else J for J in couplings]
+    hs = (C.c_void_p * len(insts))(*[x.handle.value for x in insts])
+    arr, mem = _ptr_array(cs)
+    _check(lib().sk_set_couplings_many(hs, len(insts), arr, mem))
+
+
+def reset_many(runs, spins=None):
+    """mcmcmc_reset_many: restart many runs from given spins (or the Philox start), all or nothing."""
+    hs = (C.c_void_p * len(runs))(*[r.handle.value for r in runs])
+    if spins is None:
+        _check(lib().mcmcmc_reset_many(hs, len(runs), None, SK_MEM_HOST))
+        return
+    ss = [np.ascontiguousarray(x, dtype=np.int8) if isinstance(x, np.ndarray) else x for x in spins]
+    arr, mem = _ptr_array(ss)
+    _check(lib().mcmcmc_reset_many(hs, len(runs), arr, mem))
+
+
+def observables_many(runs, first, count, outs):
+    """mcmcmc_observables_many: records [first, first+count) of many runs into
+    outs[i] = (energy, overlap, accepted) buffers (numpy or pinned/device torch)."""
+    hs = (C.c_void_p * len(runs))(*[r.handle.value for r in runs])
+    E, m1 = _ptr_array([o[0] for o in outs])
+    Q, _ = _ptr_array([o[1] for o in outs])
+    A, _ = _ptr_array([o[2] for o in outs])
+    _check(lib().mcmcmc_observables_many(hs, len(runs), first, count, E, Q, A, m1))

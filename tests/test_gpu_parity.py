@@ -479,3 +479,53 @@ def test_set_generation_arguments():
         sk.set_generation(np.zeros((29, 29)))
     with pytest.raises(sk.SKError):
         sk.set_generation(-np.ones((3, 3)))
+
+
+def test_batched_inputs_and_records_equal_single_calls():
+    """sk_set_couplings_many / mcmcmc_reset_many / mcmcmc_observables_many give
+    the same state and records as the per-instance calls; a bad input in any
+    of them leaves every instance and run unchanged (all or nothing)."""
+    torch = need_gpu()
+    st = torch.cuda.Stream()
+    N, K, chains, R, steps = 72, 16, 6, 50, 200
+    Js = [inputs.couplings_pm1(N, 100 + i) for i in range(3)]
+    Js2 = [inputs.couplings_pm1(N, 200 + i) for i in range(3)]
+    inits = [inputs.initial_spins(chains, N, 300 + i) for i in range(3)]
+    insts = [sk.Instance(J, stream=st) for J in Js]
+    runs = [sk.Run(x, chains=chains, K=K, beta=0.8, seed=5, stream_id=i, record_every=R,
+                   max_records=steps // R) for i, x in enumerate(insts)]
+    b = sk.Batch(runs)
+    sk.set_couplings_many(insts, Js2)
+    sk.reset_many(runs, inits)
+    b.advance(steps)
+    outs = [(np.zeros((steps // R, chains)), np.zeros((steps // R, chains // 2)),
+             np.zeros((steps // R, chains), dtype=np.uint32)) for _ in runs]
+    sk.observables_many(runs, 0, steps // R, outs)
+    for i, r in enumerate(runs):
+        o = oracle.run(Js2[i], K=K, beta=0.8, seed=5, stream=i, chains=chains, init=inits[i], steps=steps,
+                       record_every=R)
+        assert np.array_equal(outs[i][0], o["E"]) and np.array_equal(outs[i][2], o["acc"]), i
+        assert np.array_equal(outs[i][1], o["q"]), i
+        E, q, acc = r.observables()
+        assert np.array_equal(E, outs[i][0])
+    # all or nothing
+    spins_before = [r.state()[0] for r in runs]
+    bad = [J.copy() for J in Js]
+    bad[2][1, 2] = -bad[2][1, 2]
+    with pytest.raises(sk.SKError) as e:
+        sk.set_couplings_many(insts, bad)
+    assert "instance 2" in str(e.value)
+    bs = [x.copy() for x in inits]
+    bs[1][0, 0] = 3
+    with pytest.raises(sk.SKError) as e:
+        sk.reset_many(runs, bs)
+    assert "run 1" in str(e.value)
+    for i, r in enumerate(runs):
+        spins, h, step = r.state(fields=True)
+        assert step == steps and np.array_equal(spins, spins_before[i])
+        assert np.array_equal(h, (Js2[i].astype(np.int64) @ spins.T.astype(np.int64)).T)  # old couplings kept
+    b.close()
+    for r in runs:
+        r.close()
+    for x in insts:
+        x.close()
