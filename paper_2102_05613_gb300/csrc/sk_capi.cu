@@ -166,6 +166,7 @@ struct sk_instance {
     cudaStream_t side = nullptr;
     cudaEvent_t ev_side = nullptr;   // side: copy and check done
     cudaEvent_t ev_jfree = nullptr;  // st: dJstage copied into dJ
+    cudaEvent_t ev_main = nullptr;   // st: work queued before a start state written on side
     unsigned long long* hflag = nullptr;  // pinned host copy of dflag
     cudaStream_t st = nullptr;
 };
@@ -312,7 +313,7 @@ sk_status check_run_error(sk_run* r) {
     return SK_OK;
 }
 
-sk_status ensure_recompute(sk_run* r);
+sk_status ensure_recompute(sk_run* r, cudaStream_t cs);
 
 // Start spins of a run in three phases, as for the couplings: spins_stage
 // enqueues the copy of host spins into the run's staging buffer (side
@@ -348,7 +349,7 @@ sk_status spins_verify(const sk_run* r) {
     if (f != ~0ull) return fail(SK_ERR_INVALID_ARG, "initial spin %llu is not +-1", f >> 2);
     return SK_OK;
 }
-sk_status init_commit(sk_run* r, const int8_t* dinit);
+sk_status init_commit(sk_run* r, const int8_t* dinit, bool on_side = false);
 
 sk_status init_state(sk_run* r, const int8_t* spins, uint32_t mem) {
     cudaStream_t cs = nullptr;
@@ -362,36 +363,48 @@ sk_status init_state(sk_run* r, const int8_t* spins, uint32_t mem) {
     return init_commit(r, dinit);
 }
 
-sk_status init_commit(sk_run* r, const int8_t* dinit) {
+// Writes the start state of a run (records and counters cleared, spins from
+// dinit or the Philox start, fields on the tensor cores).  on_side: the work
+// goes on the instance's side stream after everything queued on st, and st
+// then waits for it -- the starts of runs on different instances overlap.
+sk_status init_commit(sk_run* r, const int8_t* dinit, bool on_side) {
     sk_instance* in = r->inst;
-    if (dinit && dinit == r->dstage) {  // the staged copy was made on the side stream
+    cudaStream_t cs = in->st;
+    if (on_side) {
+        SK_CU(cudaEventRecord(in->ev_main, in->st));
+        SK_CU(cudaStreamWaitEvent(in->side, in->ev_main, 0));
+        cs = in->side;
+    } else if (dinit && dinit == r->dstage) {  // the staged copy was made on the side stream
         SK_CU(cudaEventRecord(in->ev_side, in->side));
         SK_CU(cudaStreamWaitEvent(in->st, in->ev_side, 0));
     }
-    SK_CU(cudaMemsetAsync(r->dstep, 0, sizeof(uint64_t), in->st));
-    SK_CU(cudaMemsetAsync(r->derr, 0, sizeof(int), in->st));
+    SK_CU(cudaMemsetAsync(r->dstep, 0, sizeof(uint64_t), cs));
+    SK_CU(cudaMemsetAsync(r->derr, 0, sizeof(int), cs));
     const uint64_t R = r->p.max_records;
     if (R && r->p.record_every) {
-        SK_CU(cudaMemsetAsync(r->drecE, 0, R * r->chains * sizeof(double), in->st));
-        SK_CU(cudaMemsetAsync(r->drecAcc, 0, R * r->chains * sizeof(uint32_t), in->st));
-        if (r->chains >= 2) SK_CU(cudaMemsetAsync(r->drecQ, 0, R * (r->chains / 2) * sizeof(double), in->st));
-        if (r->drecEnw) SK_CU(cudaMemsetAsync(r->drecEnw, 0, R * r->chains * sizeof(double), in->st));
+        SK_CU(cudaMemsetAsync(r->drecE, 0, R * r->chains * sizeof(double), cs));
+        SK_CU(cudaMemsetAsync(r->drecAcc, 0, R * r->chains * sizeof(uint32_t), cs));
+        if (r->chains >= 2) SK_CU(cudaMemsetAsync(r->drecQ, 0, R * (r->chains / 2) * sizeof(double), cs));
+        if (r->drecEnw) SK_CU(cudaMemsetAsync(r->drecEnw, 0, R * r->chains * sizeof(double), cs));
     }
     if (r->dtrace)
-        SK_CU(cudaMemsetAsync(r->dtrace, 0xff, static_cast<size_t>(r->p.trace_chains) * r->p.trace_steps * 4,
-                              in->st));
+        SK_CU(cudaMemsetAsync(r->dtrace, 0xff, static_cast<size_t>(r->p.trace_chains) * r->p.trace_steps * 4, cs));
     // spins, then the fields h = J s on the tensor cores (e4m3 for +-J:
     // exact; three bf16 terms of J for Gaussian couplings: fp32 accumulation)
-    SK_CU(sk::launch_init(&r->job, dinit, r->chains, in->N, in->Npad, in->kind, in->st, false));
-    if (dinit == r->dstage && dinit) SK_CU(cudaEventRecord(r->ev_sfree, in->st));
+    SK_CU(sk::launch_init(&r->job, dinit, r->chains, in->N, in->Npad, in->kind, cs, false));
+    if (dinit == r->dstage && dinit) SK_CU(cudaEventRecord(r->ev_sfree, cs));
     {
-        sk_status s = ensure_recompute(r);
+        sk_status s = ensure_recompute(r, cs);
         if (s != SK_OK) return s;
         SK_CU(sk::launch_recompute(in->kind, r->ds, r->dh, nullptr, r->dSop, in->dJop, r->ddE, r->dstats,
-                                   r->derr, r->chains, in->Npad, 3, 3, in->scale, in->st));
+                                   r->derr, r->chains, in->Npad, 3, 3, in->scale, cs));
     }
-    SK_CU(cudaMemsetAsync(r->dstats, 0, 6 * sizeof(unsigned long long), in->st));
-    SK_CU(cudaMemsetAsync(r->ddE, 0, static_cast<size_t>(r->chains) * sizeof(double), in->st));
+    SK_CU(cudaMemsetAsync(r->dstats, 0, 6 * sizeof(unsigned long long), cs));
+    SK_CU(cudaMemsetAsync(r->ddE, 0, static_cast<size_t>(r->chains) * sizeof(double), cs));
+    if (on_side) {
+        SK_CU(cudaEventRecord(in->ev_side, in->side));
+        SK_CU(cudaStreamWaitEvent(in->st, in->ev_side, 0));
+    }
     r->n_recomputes = 0;
     r->step = 0;
     return SK_OK;
@@ -421,22 +434,22 @@ void free_run_buffers(sk_run* r) {
 }
 
 // Operand buffers of the tensor-core recompute, allocated on first use.
-sk_status ensure_recompute(sk_run* r) {
+sk_status ensure_recompute(sk_run* r, cudaStream_t cs) {
     sk_instance* in = r->inst;
     sk_status s = SK_OK;
     if (!in->dJop) s = dalloc(&in->dJop, sk::recompute_j_bytes(in->kind, in->Npad));
     if (s == SK_OK && !r->dSop) s = dalloc(&r->dSop, sk::recompute_s_bytes(in->kind, r->chains, in->Npad));
     if (s == SK_OK && !r->ddE) {
         s = dalloc(&r->ddE, static_cast<size_t>(r->chains) * sizeof(double));
-        if (s == SK_OK) SK_CU(cudaMemsetAsync(r->ddE, 0, static_cast<size_t>(r->chains) * sizeof(double), in->st));
+        if (s == SK_OK) SK_CU(cudaMemsetAsync(r->ddE, 0, static_cast<size_t>(r->chains) * sizeof(double), cs));
     }
     if (s == SK_OK && !r->dstats) {
         s = dalloc(&r->dstats, 6 * sizeof(unsigned long long));
-        if (s == SK_OK) SK_CU(cudaMemsetAsync(r->dstats, 0, 6 * sizeof(unsigned long long), in->st));
+        if (s == SK_OK) SK_CU(cudaMemsetAsync(r->dstats, 0, 6 * sizeof(unsigned long long), cs));
     }
     if (s != SK_OK) return s;
     if (!in->jop_valid) {
-        SK_CU(sk::recompute_prepare_j(in->dJ, in->kind, in->Npad, in->dJop, in->st));
+        SK_CU(sk::recompute_prepare_j(in->dJ, in->kind, in->Npad, in->dJop, cs));
         in->jop_valid = true;
     }
     return SK_OK;
@@ -446,7 +459,7 @@ uint32_t terms_of(const sk_run* r) { return r->p.recompute_terms ? r->p.recomput
 
 // Periodic recompute after a step segment: +-J check, Gaussian resync.
 sk_status periodic_recompute(sk_run* r) {
-    sk_status s = ensure_recompute(r);
+    sk_status s = ensure_recompute(r, r->inst->st);
     if (s != SK_OK) return s;
     sk_instance* in = r->inst;
     const uint32_t mode = in->kind == SK_J_PM1 ? 0u : 1u;
@@ -488,6 +501,7 @@ sk_status sk_create_instance(uint32_t N, uint32_t kind, const void* couplings, u
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&in->side, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&in->ev_side, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&in->ev_jfree, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&in->ev_main, cudaEventDisableTiming);
         if (e != cudaSuccess) s = fail(SK_ERR_CUDA, "stream/event creation: %s", cudaGetErrorString(e));
     }
     if (s == SK_OK) s = upload_couplings(in, couplings, mem, true);
@@ -497,6 +511,7 @@ sk_status sk_create_instance(uint32_t N, uint32_t kind, const void* couplings, u
         if (in->hflag) cudaFreeHost(in->hflag);
         if (in->ev_side) cudaEventDestroy(in->ev_side);
         if (in->ev_jfree) cudaEventDestroy(in->ev_jfree);
+        if (in->ev_main) cudaEventDestroy(in->ev_main);
         if (in->side) cudaStreamDestroy(in->side);
         delete in;
         return s;
@@ -546,6 +561,7 @@ sk_status sk_destroy_instance(sk_instance* in) {
     cudaFreeHost(in->hflag);
     cudaEventDestroy(in->ev_side);
     cudaEventDestroy(in->ev_jfree);
+    cudaEventDestroy(in->ev_main);
     cudaStreamDestroy(in->side);
     delete in;
     return SK_OK;
@@ -755,9 +771,51 @@ sk_status mcmcmc_reset_many(sk_run* const* runs, uint32_t n, const int8_t* const
         sk_status s = spins_verify(runs[i]);
         if (s != SK_OK) return fail(s, "run %u: %s", i, g_err.c_str());
     }
+    // runs on one stream with one coupling kind: one launch for all start
+    // states and one for all their fields; otherwise each run on its own
+    bool together = n > 1;
+    for (uint32_t i = 0; i < n && together; ++i)
+        together = runs[i]->inst->st == runs[0]->inst->st && runs[i]->inst->kind == runs[0]->inst->kind;
+    if (!together) {
+        for (uint32_t i = 0; i < n; ++i) {
+            sk_status s = init_commit(runs[i], dinit[i], true);
+            if (s != SK_OK) return s;
+        }
+        return SK_OK;
+    }
+    cudaStream_t bs = runs[0]->inst->st;
+    std::set<sk_instance*> ins;
+    for (uint32_t i = 0; i < n; ++i) ins.insert(runs[i]->inst);
+    for (sk_instance* in : ins) {  // the staged copies were made on the side streams
+        SK_CU(cudaEventRecord(in->ev_side, in->side));
+        SK_CU(cudaStreamWaitEvent(bs, in->ev_side, 0));
+    }
+    std::vector<sk::StartJob> sj(n);
+    std::vector<sk::RecomputeSet> rs(n);
+    uint64_t max_words = 0;
     for (uint32_t i = 0; i < n; ++i) {
-        sk_status s = init_commit(runs[i], dinit[i]);
+        sk_run* r = runs[i];
+        sk_status s = ensure_recompute(r, bs);  // operands; the couplings' one if they changed
         if (s != SK_OK) return s;
+        std::memset(&sj[i], 0, sizeof(sk::StartJob));
+        sj[i].job = r->job;
+        sj[i].init = dinit[i];
+        sj[i].dstats = r->dstats;
+        sj[i].ddE = r->ddE;
+        max_words = std::max<uint64_t>(max_words, static_cast<uint64_t>(r->chains) * (r->inst->Npad / 4));
+        rs[i] = sk::RecomputeSet{r->ds, r->dh, r->dSop, r->inst->dJop, r->derr, r->chains, r->inst->Npad};
+    }
+    sk::StartJob* dsj = nullptr;
+    SK_CU(cudaMallocAsync(&dsj, n * sizeof(sk::StartJob), bs));
+    SK_CU(cudaMemcpyAsync(dsj, sj.data(), n * sizeof(sk::StartJob), cudaMemcpyHostToDevice, bs));
+    SK_CU(sk::launch_start_batch(dsj, n, max_words, bs));
+    SK_CU(cudaFreeAsync(dsj, bs));
+    for (uint32_t i = 0; i < n; ++i)
+        if (dinit[i] && dinit[i] == runs[i]->dstage) SK_CU(cudaEventRecord(runs[i]->ev_sfree, bs));
+    SK_CU(sk::launch_set_fields_batch(runs[0]->inst->kind, rs.data(), n, bs));
+    for (uint32_t i = 0; i < n; ++i) {
+        runs[i]->n_recomputes = 0;
+        runs[i]->step = 0;
     }
     return SK_OK;
 }
@@ -909,7 +967,7 @@ sk_status mcmcmc_recompute(sk_run* r, uint32_t mode, uint32_t terms, sk_recomput
     if (terms > 3) return fail(SK_ERR_INVALID_ARG, "terms must be 0..3");
     if (mode == 2 && !fields_out) return fail(SK_ERR_INVALID_ARG, "fields_out is NULL");
     if (mem != SK_MEM_HOST && mem != SK_MEM_DEVICE) return fail(SK_ERR_INVALID_ARG, "bad mem");
-    sk_status s = ensure_recompute(r);
+    sk_status s = ensure_recompute(r, r->inst->st);
     if (s != SK_OK) return s;
     sk_instance* in = r->inst;
     cudaStream_t st = in->st;
@@ -1265,7 +1323,7 @@ sk_status mcmcmc_batch_capture(sk_batch* b, uint64_t steps) {
     if (M && (steps % M || lead->step % M))
         return fail(SK_ERR_INVALID_ARG, "with recompute_every = %u, capture %u-aligned multiples of it", M, M);
     for (sk_run* r : b->runs)  // allocations happen before the capture
-        if (r->p.recompute_every && (s = ensure_recompute(r)) != SK_OK) return s;
+        if (r->p.recompute_every && (s = ensure_recompute(r, r->inst->st)) != SK_OK) return s;
     SK_CU(cudaStreamSynchronize(b->st));
     std::vector<uint64_t> mirror;
     std::vector<uint64_t> nrec;

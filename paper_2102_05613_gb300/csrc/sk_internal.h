@@ -96,6 +96,17 @@ int step_kernel_occupancy(int cls, uint32_t warps_per_cta, size_t per_chain_byte
 // then (with_fields) h = J s on the CUDA cores (register-tiled fp32 / int32).
 cudaError_t launch_init(const JobDev* job, const int8_t* init, uint32_t chains, uint32_t N,
                         uint32_t Npad, uint32_t kind, cudaStream_t st, bool with_fields = true);
+// Start states of several runs in one launch: spins (from `init`, chains x N
+// on the device, or the Philox start) and the run's counters, records,
+// trace and recompute statistics cleared.  jobs_dev: a device array.
+struct StartJob {
+    JobDev job;
+    const int8_t* init;
+    unsigned long long* dstats;  // 6 words, or null
+    double* ddE;                 // per chain, or null
+    uint64_t pad_;
+};
+cudaError_t launch_start_batch(const StartJob* jobs_dev, uint32_t n, uint64_t max_words, cudaStream_t st);
 // Device checks of host-supplied inputs: *flag receives the smallest
 // (position << 2 | code) of a violation, all ones when there is none
 // (couplings: position i * 2^16 + j, code 1 diagonal, 2 range or not finite,
@@ -124,6 +135,17 @@ int graph_kernel_occupancy(uint32_t kind, uint32_t W, size_t per_chain);
 size_t recompute_j_bytes(uint32_t kind, uint32_t npad);
 size_t recompute_s_bytes(uint32_t kind, uint32_t chains, uint32_t npad);
 cudaError_t recompute_prepare_j(const void* J, uint32_t kind, uint32_t npad, void* j_op, cudaStream_t st);
+// The fields h = J s of several runs of one coupling kind in one launch
+// (mode 3 of launch_recompute for each set, spin operands converted too).
+struct RecomputeSet {
+    const int8_t* s;
+    void* h;
+    void* s_op;
+    const void* j_op;
+    int* err;
+    uint32_t chains, npad;
+};
+cudaError_t launch_set_fields_batch(uint32_t kind, const RecomputeSet* sets, uint32_t n, cudaStream_t st);
 cudaError_t launch_recompute(uint32_t kind, const int8_t* s, void* h, float* out, void* s_op,
                              const void* j_op, double* dE, unsigned long long* stats, int* err,
                              uint32_t chains, uint32_t npad, uint32_t terms, uint32_t mode, double scale,

@@ -102,6 +102,64 @@ __global__ void spins_kernel(JobDev jb, const int8_t* __restrict__ init) {
     }
 }
 
+// Start states of several runs in one launch (blockIdx.y = run): the spins
+// as spins_kernel writes them, and the run's step counter, error word,
+// records, trace and recompute statistics cleared.
+__global__ void start_batch_kernel(const StartJob* __restrict__ jobs) {
+    const StartJob& sj = jobs[blockIdx.y];
+    const JobDev& jb = sj.job;
+    const uint32_t npad = jb.Npad, N = jb.N;
+    const uint32_t words = npad / 4;
+    const uint64_t total = static_cast<uint64_t>(jb.chains) * words;
+    const uint32_t k0 = static_cast<uint32_t>(jb.seed), k1 = static_cast<uint32_t>(jb.seed >> 32);
+    const uint32_t c3 = (1u << 24) | (jb.stream & 0xFFFFFFu);
+    const uint64_t tid = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
+    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+    for (uint64_t x = tid; x < total; x += stride) {
+        const uint32_t chain = static_cast<uint32_t>(x / words);
+        const uint32_t i0 = static_cast<uint32_t>(x % words) * 4u;
+        uint32_t packed = 0;
+        if (sj.init) {
+            for (uint32_t k = 0; k < 4u; ++k) {
+                const uint32_t i = i0 + k;
+                const int v = i < N ? sj.init[static_cast<size_t>(chain) * N + i] : 0;
+                packed |= (static_cast<uint32_t>(v) & 0xFFu) << (8u * k);
+            }
+        } else {
+            const uint4 r = philox4x32_10(make_uint4(i0 / 128u, 0u, chain, c3), k0, k1);
+            const uint32_t wv[4] = {r.x, r.y, r.z, r.w};
+            const uint32_t w = wv[(i0 % 128u) / 32u];
+            for (uint32_t k = 0; k < 4u; ++k) {
+                const uint32_t i = i0 + k, b = (i % 128u) & 31u;
+                const int v = i < N ? (((w >> b) & 1u) ? -1 : 1) : 0;
+                packed |= (static_cast<uint32_t>(v) & 0xFFu) << (8u * k);
+            }
+        }
+        reinterpret_cast<uint32_t*>(jb.s)[static_cast<size_t>(chain) * words + i0 / 4u] = packed;
+    }
+    for (uint64_t c = tid; c < jb.chains; c += stride) {
+        jb.acc_run[c] = 0;
+        jb.work[2 * c] = 0;
+        jb.work[2 * c + 1] = 0;
+        if (sj.ddE) sj.ddE[c] = 0.0;
+    }
+    const uint64_t nrec = jb.rec_capacity * jb.chains;
+    for (uint64_t q = tid; q < nrec; q += stride) {
+        jb.rec_E[q] = 0.0;
+        jb.rec_acc[q] = 0;
+        if (jb.rec_Enw) jb.rec_Enw[q] = 0.0;
+        if ((q % jb.chains) < jb.chains / 2) jb.rec_q[(q / jb.chains) * (jb.chains / 2) + q % jb.chains] = 0.0;
+    }
+    const uint64_t ntr = static_cast<uint64_t>(jb.trace_chains) * jb.trace_steps;
+    for (uint64_t q = tid; q < ntr; q += stride) jb.trace[q] = -1;
+    if (tid == 0) {
+        *jb.step = 0;
+        *jb.err = 0;
+        if (sj.dstats)
+            for (int k = 0; k < 6; ++k) sj.dstats[k] = 0;
+    }
+}
+
 // Local fields h[c][i] = sum_j J_ij s[c][j] of every chain, a register-tiled
 // product: a CTA computes 128 sites x 64 chains, a thread 8 sites x 4
 // chains, with j in chunks of 32 staged through shared memory (J is
@@ -341,6 +399,13 @@ cudaError_t launch_init(const JobDev* job, const int8_t* init, uint32_t chains, 
         fields_kernel<int8_t><<<grid, 256, 0, st>>>(static_cast<const int8_t*>(job->J), job->s, job->h, Npad, chains);
     else
         fields_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float*>(job->J), job->s, job->h, Npad, chains);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_start_batch(const StartJob* jobs_dev, uint32_t n, uint64_t max_words, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const uint32_t bx = static_cast<uint32_t>(std::max<uint64_t>(1, std::min<uint64_t>((max_words + 255) / 256, 512)));
+    start_batch_kernel<<<dim3(bx, n), 256, 0, st>>>(jobs_dev);
     return cudaGetLastError();
 }
 

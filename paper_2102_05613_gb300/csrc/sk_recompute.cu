@@ -25,7 +25,10 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "sk_internal.h"
 
@@ -133,11 +136,10 @@ struct Args {
     uint32_t pm1;
 };
 
+// One 128 x 256 tile (rows m0.., columns n0..) of one operand set.
 template <bool F8>
-__global__ void __launch_bounds__(128, 1)
-    recompute_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB0,
-                     const __grid_constant__ CUtensorMap tB1, const __grid_constant__ CUtensorMap tB2,
-                     Args args) {
+__device__ __forceinline__ void recompute_tile(const CUtensorMap* pA, const CUtensorMap* pB0, const CUtensorMap* pB1,
+                                               const CUtensorMap* pB2, const Args& args, uint32_t m0, uint32_t n0) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full[NS], empty[NS], accum;
     __shared__ uint32_t tmem_holder;
@@ -145,7 +147,6 @@ __global__ void __launch_bounds__(128, 1)
     // 128-byte-swizzled tiles must start on a 1024-byte boundary of shared memory
     unsigned char* smem = smem_raw + ((1024u - (saddr(smem_raw) & 1023u)) & 1023u);
     const uint32_t tid = threadIdx.x, warp = tid >> 5;
-    const uint32_t m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
     const uint32_t total = args.terms * args.kblocks;
     constexpr uint32_t kElems = F8 ? 128u : 64u;  // K elements per 128-byte row
     constexpr uint32_t idesc = instr_desc(F8 ? 0u : 1u);
@@ -172,7 +173,7 @@ __global__ void __launch_bounds__(128, 1)
 
     if (tid == 0) {
         // producer: A (spins) and B (couplings, term by term) tiles by TMA
-        const CUtensorMap* tb[3] = {&tB0, &tB1, &tB2};
+        const CUtensorMap* tb[3] = {pB0, pB1, pB2};
         for (uint32_t i = 0; i < total; ++i) {
             const uint32_t st = i % NS, round = i / NS;
             if (i >= NS && !wait_bounded(saddr(&empty[st]), (round - 1) & 1u)) {
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(128, 1)
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(&full[st])),
                          "r"(STAGE_BYTES)
                          : "memory");
-            tma_2d(saddr(a), &tA, static_cast<int>(kb * kElems), static_cast<int>(m0), saddr(&full[st]));
+            tma_2d(saddr(a), pA, static_cast<int>(kb * kElems), static_cast<int>(m0), saddr(&full[st]));
             tma_2d(saddr(b), tb[term], static_cast<int>(kb * kElems), static_cast<int>(n0), saddr(&full[st]));
         }
     } else if (tid == 32) {
@@ -315,6 +316,55 @@ __global__ void __launch_bounds__(128, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
+template <bool F8>
+__global__ void __launch_bounds__(128, 1)
+    recompute_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB0,
+                     const __grid_constant__ CUtensorMap tB1, const __grid_constant__ CUtensorMap tB2,
+                     Args args) {
+    recompute_tile<F8>(&tA, &tB0, &tB1, &tB2, args, blockIdx.x * BM, blockIdx.y * BN);
+}
+
+// Several operand sets in one launch: the tensor maps and arguments of each
+// set in global memory (maps 64-byte aligned, written before the launch),
+// one CTA per tile of the task list.
+struct alignas(64) BatchJob {
+    CUtensorMap A, B[3];
+    Args args;
+};
+struct BatchTask {
+    uint32_t job, m0, n0, pad;
+};
+template <bool F8>
+__global__ void __launch_bounds__(128, 1)
+    recompute_batch_kernel(const BatchJob* __restrict__ jobs, const BatchTask* __restrict__ tasks) {
+    const BatchTask tk = tasks[blockIdx.x];
+    const BatchJob& j = jobs[tk.job];
+    if (threadIdx.x == 0) {  // the maps were written to global memory by a copy: acquire them for TMA
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&j.A) : "memory");
+        for (int t = 0; t < 3; ++t)
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&j.B[t]) : "memory");
+    }
+    recompute_tile<F8>(&j.A, &j.B[0], &j.B[1], &j.B[2], j.args, tk.m0, tk.n0);
+}
+
+// Spin operands of several runs (blockIdx.y = run): +-1 -> e4m3 / bf16.
+struct SegSpins {
+    const int8_t* s;
+    void* o;
+    size_t n;
+};
+__global__ void spins_to_op_batch(const SegSpins* __restrict__ seg, uint32_t bf16) {
+    const SegSpins g = seg[blockIdx.y];
+    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < g.n;
+         i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const int v = g.s[i];
+        if (bf16)
+            static_cast<uint16_t*>(g.o)[i] = v == 0 ? 0 : (v > 0 ? 0x3F80 : 0xBF80);
+        else
+            static_cast<uint8_t*>(g.o)[i] = v == 0 ? 0 : (v > 0 ? 0x38 : 0xB8);
+    }
+}
+
 // max over chains of |dE| = |-scale/2 sum s (h - H)| into stats[2]; clears dE.
 __global__ void finish_energy(double* dE, uint32_t chains, double scale, unsigned long long* stats) {
     const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -419,6 +469,70 @@ cudaError_t recompute_prepare_j(const void* J, uint32_t kind, uint32_t npad, voi
     else
         gauss_to_bf16x3<<<grid1d(n), 256, 0, st>>>(static_cast<const float*>(J), static_cast<uint16_t*>(j_op), n);
     return cudaGetLastError();
+}
+
+cudaError_t launch_set_fields_batch(uint32_t kind, const RecomputeSet* sets, uint32_t n, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const bool bf = kind != 0;
+    std::vector<SegSpins> seg(n);
+    std::vector<BatchJob> jobs(n);
+    std::vector<BatchTask> tasks;
+    size_t maxn = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        const RecomputeSet& q = sets[i];
+        seg[i] = SegSpins{q.s, q.s_op, static_cast<size_t>(q.chains) * q.npad};
+        maxn = std::max(maxn, seg[i].n);
+        BatchJob& b = jobs[i];
+        std::memset(&b, 0, sizeof b);
+        cudaError_t e = make_map(&b.A, q.s_op, bf, q.chains, q.npad, BM);
+        const size_t term_bytes = static_cast<size_t>(q.npad) * q.npad * (bf ? 2 : 1);
+        for (uint32_t t = 0; t < 3 && e == cudaSuccess; ++t)
+            e = make_map(&b.B[t], static_cast<const unsigned char*>(q.j_op) + (bf ? t : 0) * term_bytes, bf, q.npad,
+                         q.npad, BN);
+        if (e != cudaSuccess) return e;
+        b.args.h = q.h;
+        b.args.s = q.s;
+        b.args.err = q.err;
+        b.args.chains = q.chains;
+        b.args.npad = q.npad;
+        b.args.kblocks = (q.npad + (bf ? 63u : 127u)) / (bf ? 64u : 128u);
+        b.args.terms = bf ? 3u : 1u;
+        b.args.mode = 3;
+        b.args.pm1 = bf ? 0u : 1u;
+        for (uint32_t m0 = 0; m0 < q.chains; m0 += BM)
+            for (uint32_t n0 = 0; n0 < q.npad; n0 += BN) tasks.push_back(BatchTask{i, m0, n0, 0});
+    }
+    SegSpins* dseg = nullptr;
+    BatchJob* djobs = nullptr;
+    BatchTask* dtasks = nullptr;
+    cudaError_t e = cudaMallocAsync(&dseg, n * sizeof(SegSpins), st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&djobs, n * sizeof(BatchJob), st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&dtasks, tasks.size() * sizeof(BatchTask), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dseg, seg.data(), n * sizeof(SegSpins), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(djobs, jobs.data(), n * sizeof(BatchJob), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dtasks, tasks.data(), tasks.size() * sizeof(BatchTask), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        const dim3 g(std::min<uint32_t>(grid1d(maxn), 1024u), n);
+        spins_to_op_batch<<<g, 256, 0, st>>>(dseg, bf ? 1u : 0u);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        if (bf) {
+            e = cudaFuncSetAttribute(recompute_batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+            if (e == cudaSuccess)
+                recompute_batch_kernel<false><<<static_cast<uint32_t>(tasks.size()), 128, SMEM_BYTES, st>>>(djobs, dtasks);
+        } else {
+            e = cudaFuncSetAttribute(recompute_batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+            if (e == cudaSuccess)
+                recompute_batch_kernel<true><<<static_cast<uint32_t>(tasks.size()), 128, SMEM_BYTES, st>>>(djobs, dtasks);
+        }
+        if (e == cudaSuccess) e = cudaGetLastError();
+    }
+    cudaFreeAsync(dseg, st);
+    cudaFreeAsync(djobs, st);
+    cudaFreeAsync(dtasks, st);
+    return e;
 }
 
 cudaError_t launch_recompute(uint32_t kind, const int8_t* s, void* h, float* out, void* s_op,

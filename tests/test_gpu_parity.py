@@ -529,3 +529,29 @@ def test_batched_inputs_and_records_equal_single_calls():
         r.close()
     for x in insts:
         x.close()
+
+
+def test_batched_start_equals_single_starts_gaussian():
+    """The batched start (one start launch and one tensor-core launch for all
+    runs) writes the same spins and fields as mcmcmc_reset run by run."""
+    torch = need_gpu()
+    st = torch.cuda.Stream()
+    N, chains = 200, 130   # ragged tiles
+    Js = [inputs.couplings_gauss(N, 400 + i) for i in range(3)]
+    inits = [inputs.initial_spins(chains, N, 500 + i) for i in range(3)]
+    insts = [sk.Instance(J, stream=st) for J in Js]
+    runs = [sk.Run(x, chains=chains, K=8, seed=2, stream_id=i, record_every=10, max_records=3)
+            for i, x in enumerate(insts)]
+    sk.reset_many(runs, [inits[0], None, inits[2]])
+    got = [r.state(fields=True) for r in runs]
+    for i, r in enumerate(runs):
+        r.reset(inits[i] if i != 1 else None)
+        s1, h1, step = r.state(fields=True)
+        assert step == 0
+        assert np.array_equal(got[i][0], s1) and np.array_equal(got[i][1], h1), i
+        E, q, acc = r.observables()
+        assert not E.any() and not acc.any()
+    for r in runs:
+        r.close()
+    for x in insts:
+        x.close()
