@@ -381,9 +381,64 @@ def run_ttt(args):
                 ss[name][str(eps)] = sa / sb
     out["wallclock_speedup_vs_metropolis"] = sp
     out["mc_step_ratio_vs_metropolis"] = ss
+    out["few_chains"] = ttt_few_chains(inst, out["methods"], only)
     inst.close()
     print(json.dumps(out), flush=True)
     return 0
+
+
+TTT_FEW_CHAINS = (1, 152)
+
+
+def ttt_few_chains(inst, methods, only):
+    """Time to thermalise when only a few chains run (one chain, or one per
+    SM), where a Metropolis step cannot fill the GPU and the graph's nodes
+    are what runs in parallel: seconds per step of each method at C chains
+    (autotuned launch geometry, no records), times the steps to thermalise of
+    the ensemble above (the ensemble mean relaxes the same way whatever the
+    number of chains; only the time per step depends on it)."""
+    import torch
+    from paper_2102_05613_gb300 import sk
+    stream = torch.cuda.current_stream()
+    res = {}
+    for C in TTT_FEW_CHAINS:
+        per = {}
+        for name, rule, Kt, _T, gkw in TTT_METHODS:
+            if name not in methods or (only and name not in only and name != "mcmcmc_k128"):
+                continue
+            run = sk.Run(inst, chains=C, K=Kt, rule=rule, beta=TTT_BETA, seed=11, **gkw)
+            batch = sk.Batch([run])
+            batch.autotune(trial_steps=32)
+            geometry = batch.classes()
+
+            def timed(T):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                a.record(stream)
+                batch.advance(T)
+                b.record(stream)
+                torch.cuda.synchronize()
+                return a.elapsed_time(b) / 1e3
+
+            timed(16)
+            t64 = timed(64)
+            T = int(min(1 << 20, max(64, 64 * 0.25 / max(t64, 1e-9))))  # ~0.25 s of steps
+            s_per_step = timed(T) / T
+            batch.close()
+            run.close()
+            m = methods[name]
+            per[name] = {"s_per_step": s_per_step, "steps_timed": T, "launch_classes": geometry,
+                         "t_therm_s": {e: (None if st_ is None else st_ * s_per_step)
+                                       for e, st_ in m["t_therm_steps"].items()}}
+        sp = {}
+        met = per.get("metropolis")
+        for name, mm in per.items():
+            if name == "metropolis" or met is None:
+                continue
+            sp[name] = {e: (None if (mm["t_therm_s"][e] is None or met["t_therm_s"][e] is None)
+                            else met["t_therm_s"][e] / mm["t_therm_s"][e]) for e in mm["t_therm_s"]}
+        res[str(C)] = {"methods": per, "wallclock_speedup_vs_metropolis": sp}
+    return res
 
 
 # ---------------------------------------------------------------------------

@@ -342,7 +342,8 @@ sk_status mcmcmc_batch_replay(sk_batch* b, uint32_t times);
  * `trial_steps`-step launch for each staging choice, each lanes-per-chain
  * value K allows and each warps-per-CTA value that fits in shared memory
  * (the CTA size also selects the kernel's register budget) and keeps the
- * fastest.
+ * fastest; graph classes try 1, 2, 4, 8 and 16 warps per chain with every
+ * even number of chains per CTA that fits.
  * Trials start from a copy of the runs' state, which is restored afterwards,
  * and run with records and traces off: the runs' trajectories, records and
  * step counters are unchanged.  *warps_per_cta (may be NULL) receives the
@@ -360,6 +361,9 @@ sk_status mcmcmc_batch_autotune(sk_batch* b, uint32_t trial_steps, uint32_t* war
  *            for 1 block per lane at every width, 2 blocks at 8, 16 and 32
  *            lanes and 4 blocks at 8 and 16 lanes, so K <= 16 allows 4
  *            lanes, K <= 128 8 lanes and K <= 256 16 lanes;
+ *            Graph runs (trees and lines) take 64, 128, 256 or 512 lanes
+ *            = 2, 4, 8 or 16 warps per chain (any smaller value: one warp);
+ *            star classes clamp values above 32 to 32;
  *   staging  0 = default, 1 = the next step's row of J is staged in shared
  *            memory by TMA (two row buffers per chain), 2 = rows are read
  *            through L1 (no buffers, so more chains fit in shared memory).

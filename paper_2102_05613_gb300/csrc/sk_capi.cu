@@ -187,13 +187,16 @@ struct sk_batch {
         uint32_t per_chain_staged, per_chain_direct;
         uint32_t per_chain;      // shared memory per chain
         uint32_t W;              // warps per CTA
+        uint32_t nw = 1;         // graph classes: warps per chain
         uint32_t first_item, n_items, grid;
     };
     std::vector<sk_run*> runs;
     std::vector<Class> classes;
     std::map<uint64_t, uint32_t> tuned;  // key -> (stage << 16) | (G << 8) | W chosen by the autotuner
+                                         // (graph classes: (warps per chain << 16) | (32 << 8) | W)
     uint32_t W_override = 0;             // warps_per_cta given at creation (0: as many as fit)
-    uint32_t G_override = 0;             // mcmcmc_batch_set_layout lanes (0: default)
+    uint32_t G_override = 0;             // mcmcmc_batch_set_layout lanes (0: default; graph classes
+                                         // take lanes / 32 warps per chain when lanes >= 64)
     uint32_t S_override = 0;             // mcmcmc_batch_set_layout staging (0: default = staged)
     JobDev* djobs = nullptr;
     WorkItem* ditems = nullptr;
@@ -1105,32 +1108,43 @@ sk_status plan_batch(sk_batch* b) {
             c.per_chain_direct = std::max(c.per_chain_direct, run_per_chain(b->runs[i], false));
             total += b->runs[i]->chains;
         }
-        if ((c.key >> 59) & 1u) {  // graph runs: one chain per warp, W even
+        if ((c.key >> 59) & 1u) {  // graph runs: a team of nw warps per chain, an even number of chains per CTA
             c.graph = r0->p.graph;
-            c.G = 32;
             c.gmin = c.gdef = 32;
             c.stage = 0;
             c.per_chain = 0;
             for (uint32_t i : g.second)
                 c.per_chain = std::max(c.per_chain, static_cast<uint32_t>(sk::graph_smem_bytes(
                                                         b->runs[i]->inst->Npad, b->runs[i]->job.V, c.graph)));
-            const uint32_t fitg = static_cast<uint32_t>(std::min<size_t>(32, kSmemBudget / c.per_chain)) & ~1u;
+            const uint32_t fitc = static_cast<uint32_t>(std::min<size_t>(32, kSmemBudget / c.per_chain)) & ~1u;
+            if (fitc < 2) return fail(SK_ERR_INVALID_ARG, "graph too large: %u bytes of shared memory per chain", c.per_chain);
             auto tg = b->tuned.find(c.key);
-            c.W = tg != b->tuned.end() ? (tg->second & 0xFFu) : (b->W_override ? std::min(b->W_override, fitg) : fitg);
-            c.W &= ~1u;
-            if (c.W < 2) return fail(SK_ERR_INVALID_ARG, "graph too large: %u bytes of shared memory per chain", c.per_chain);
+            if (tg != b->tuned.end()) {
+                c.nw = tg->second >> 16;
+                c.W = tg->second & 0xFFu;
+            } else {
+                c.nw = b->G_override >= 64 ? std::min<uint32_t>(16, b->G_override / 32) : 1u;
+                uint32_t chains = c.nw == 1 ? fitc : std::min<uint32_t>(fitc, 32 / c.nw) & ~1u;
+                if (c.nw > 1) chains = std::min<uint32_t>(chains, 14);
+                if (b->W_override) chains = std::max<uint32_t>(2, std::min(chains, (b->W_override / c.nw) & ~1u));
+                if (chains < 2) return fail(SK_ERR_INVALID_ARG, "graph: %u warps per chain leave no room for two chains", c.nw);
+                c.W = chains * c.nw;
+            }
+            if (!sk::graph_team_ok(c.W, c.nw)) return fail(SK_ERR_INVALID_ARG, "graph layout %u warps, %u per chain", c.W, c.nw);
+            c.G = 32 * c.nw;
             c.cls = 512 + static_cast<int>(r0->inst->kind) * 4 + static_cast<int>(c.graph);
-            int occg = sk::graph_kernel_occupancy(r0->inst->kind, c.W, c.per_chain);
-            while (occg <= 0 && tg == b->tuned.end() && c.W > 2) {
-                c.W -= 2;
-                occg = sk::graph_kernel_occupancy(r0->inst->kind, c.W, c.per_chain);
+            int occg = sk::graph_kernel_occupancy(r0->inst->kind, c.graph, c.W, c.nw, c.per_chain);
+            while (occg <= 0 && tg == b->tuned.end() && c.W > 2 * c.nw) {
+                c.W -= 2 * c.nw;
+                occg = sk::graph_kernel_occupancy(r0->inst->kind, c.graph, c.W, c.nw, c.per_chain);
             }
             if (occg <= 0) return fail(SK_ERR_CUDA, "graph kernel cannot be resident with %u warps", c.W);
             c.first_item = static_cast<uint32_t>(items.size());
+            const uint32_t cpi = c.W / c.nw;  // chains per item
             for (uint32_t i : g.second) {
                 const sk_run* r = b->runs[i];
-                for (uint32_t ch = 0; ch < r->chains; ch += c.W)
-                    items.push_back(WorkItem{i, ch, std::min(c.W, r->chains - ch), 0});
+                for (uint32_t ch = 0; ch < r->chains; ch += cpi)
+                    items.push_back(WorkItem{i, ch, std::min(cpi, r->chains - ch), 0});
             }
             c.n_items = static_cast<uint32_t>(items.size()) - c.first_item;
             c.grid = std::min<uint32_t>(c.n_items, static_cast<uint32_t>(occg * sms));
@@ -1148,7 +1162,7 @@ sk_status plan_batch(sk_batch* b) {
         } else {
             c.stage = (b->S_override == 2 || nw) ? 0u : 1u;
             c.per_chain = c.stage ? c.per_chain_staged : c.per_chain_direct;
-            c.G = b->G_override ? std::max(b->G_override, c.gmin) : (total <= 512 ? 32u : c.gdef);
+            c.G = b->G_override ? std::min(32u, std::max(b->G_override, c.gmin)) : (total <= 512 ? 32u : c.gdef);
             const uint32_t fit = fit_warps(c.per_chain, c.G);
             c.W = b->W_override ? std::min(b->W_override, fit) : fit;
         }
@@ -1234,8 +1248,9 @@ sk_status mcmcmc_batch_create(sk_run* const* runs, uint32_t n, uint32_t W, sk_ba
 
 sk_status mcmcmc_batch_set_layout(sk_batch* b, uint32_t lanes, uint32_t staging) {
     if (!b) return fail(SK_ERR_INVALID_ARG, "batch is NULL");
-    if (lanes && lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32)
-        return fail(SK_ERR_INVALID_ARG, "lanes per chain must be 0, 4, 8, 16 or 32");
+    if (lanes && lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32 && lanes != 64 && lanes != 128 &&
+        lanes != 256 && lanes != 512)
+        return fail(SK_ERR_INVALID_ARG, "lanes per chain must be 0, 4, 8, 16, 32, 64, 128, 256 or 512");
     if (staging > 2) return fail(SK_ERR_INVALID_ARG, "staging must be 0, 1 or 2");
     b->G_override = lanes;
     b->S_override = staging;
@@ -1254,7 +1269,7 @@ sk_status launch_segment(sk_batch* b, uint64_t steps, int only = -1) {
         const bool last = only >= 0 || k + 1 == nc;
         cudaError_t e =
             c.graph ? sk::launch_graph(b->djobs, b->ditems + c.first_item, c.n_items, b->dqueue + k, steps, c.W,
-                                       c.per_chain, c.grid, static_cast<uint32_t>((c.cls - 512) / 4),
+                                       c.nw, c.per_chain, c.grid, static_cast<uint32_t>((c.cls - 512) / 4), c.graph,
                                        static_cast<uint32_t>(b->runs.size()), last, b->st)
                     : sk::launch_step(b->djobs, b->ditems + c.first_item, c.n_items, b->dqueue + k, steps, c.W,
                                       c.per_chain, c.grid, c.cls, static_cast<uint32_t>(b->runs.size()), last,
@@ -1428,14 +1443,16 @@ sk_status mcmcmc_batch_autotune(sk_batch* b, uint32_t trial_steps, uint32_t* out
         const std::vector<sk_batch::Class> cls0 = b->classes;
         for (size_t k = 0; k < cls0.size() && s == SK_OK; ++k) {
             const uint64_t key = cls0[k].key;
-            uint32_t best = (cls0[k].stage << 16) | (cls0[k].G << 8) | cls0[k].W;
+            uint32_t best = cls0[k].graph ? ((cls0[k].nw << 16) | (32u << 8) | cls0[k].W)
+                                          : ((cls0[k].stage << 16) | (cls0[k].G << 8) | cls0[k].W);
             float best_ms = 1e30f;
             std::vector<uint32_t> cand;  // (stage << 16) | (G << 8) | W
             const uint32_t max_stage = ((key >> 60) & 1u) ? 0u : 1u;  // node-weighted classes: no staging
-            if ((key >> 59) & 1u) {  // graph classes: warps per CTA only (even)
-                const uint32_t fitg = static_cast<uint32_t>(std::min<size_t>(32, kSmemBudget / cls0[k].per_chain)) & ~1u;
-                for (uint32_t w : {32u, 24u, 20u, 16u, 12u, 8u, 6u, 4u, 2u})
-                    if (w <= fitg) cand.push_back((0u << 16) | (32u << 8) | w);
+            if ((key >> 59) & 1u) {  // graph classes: warps per chain and chains per CTA (even)
+                const uint32_t fitc = static_cast<uint32_t>(std::min<size_t>(32, kSmemBudget / cls0[k].per_chain)) & ~1u;
+                for (uint32_t nw : {1u, 2u, 4u, 8u, 16u})
+                    for (uint32_t ch : {32u, 24u, 16u, 14u, 12u, 8u, 6u, 4u, 2u})
+                        if (ch <= fitc && sk::graph_team_ok(nw * ch, nw)) cand.push_back((nw << 16) | (32u << 8) | (nw * ch));
             }
             for (uint32_t stage = 0; stage <= max_stage && !((key >> 59) & 1u); ++stage)
                 for (uint32_t G = cls0[k].gmin; G <= 32; G <<= 1) {

@@ -117,14 +117,17 @@ cudaError_t launch_check_spins(const int8_t* s, uint64_t n, unsigned long long* 
 cudaError_t launch_energy(const void* J, uint32_t kind, uint32_t N, uint32_t Npad, double scale,
                           const int8_t* spins, uint32_t count, double* out, cudaStream_t st);
 
-// MCMCMC on deeper graphs (sk_graph.cu): one chain per warp, W warps per CTA,
-// `per_chain` bytes of shared memory per chain (graph_smem_bytes).
+// MCMCMC on deeper graphs (sk_graph.cu): a team of nw warps per chain (1, 2,
+// 4, 8 or 16), W warps per CTA, i.e. W / nw chains (even; at most 14 when
+// nw > 1, the teams' named barriers), `per_chain` bytes of shared memory per
+// chain (graph_smem_bytes).  Work items hold W / nw chains.
 size_t graph_smem_bytes(uint32_t npad, uint32_t V, uint32_t graph);
 size_t graph_table_bytes(uint32_t V);
+bool graph_team_ok(uint32_t W, uint32_t nw);
 cudaError_t launch_graph(const JobDev* jobs, const WorkItem* items, uint32_t n_items, uint32_t* queue,
-                         uint64_t nsteps, uint32_t W, uint32_t per_chain, uint32_t grid, uint32_t kind,
-                         uint32_t n_jobs, bool bump, cudaStream_t st);
-int graph_kernel_occupancy(uint32_t kind, uint32_t W, size_t per_chain);
+                         uint64_t nsteps, uint32_t W, uint32_t nw, uint32_t per_chain, uint32_t grid, uint32_t kind,
+                         uint32_t graph, uint32_t n_jobs, bool bump, cudaStream_t st);
+int graph_kernel_occupancy(uint32_t kind, uint32_t graph, uint32_t W, uint32_t nw, size_t per_chain);
 
 // Tensor-core field recompute (sk_recompute.cu).  Operand buffers: J as
 // e4m3 (+-J, npad^2 bytes) or three bf16 terms (Gaussian, 3 npad^2 x 2

@@ -369,8 +369,9 @@ class Batch:
         return [tuple(int(x) for x in d[6 * k:6 * k + 6]) for k in range(n.value)]
 
     def set_layout(self, lanes: int = 0, staging: int = 0):
-        """mcmcmc_batch_set_layout: lanes per chain (0, 4, 8, 16, 32); staging
-        0 default, 1 TMA-staged rows, 2 rows read through L1."""
+        """mcmcmc_batch_set_layout: lanes per chain (0, 4, 8, 16, 32; graph
+        runs also 64, 128, 256, 512 = 2..16 warps per chain); staging 0
+        default, 1 TMA-staged rows, 2 rows read through L1."""
         _check(lib().mcmcmc_batch_set_layout(self.handle, int(lanes), int(staging)))
 
     def info(self):

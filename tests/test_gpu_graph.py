@@ -77,6 +77,71 @@ def test_gauss_graph_decision_replay(graph, arity, depth, L):
         assert abs(g["E"][-1, c] - oracle.energy(J, g["spins"][c])) / N <= 1e-5
 
 
+TEAM_CASES = [  # graph, arity, depth, line_nodes, N, chains, lanes per chain (32 x warps per chain)
+    (sk.SK_GRAPH_TREE, 2, 7, 0, 100, 5, 64),      # 255 nodes, odd chains: a team without a chain
+    (sk.SK_GRAPH_TREE, 16, 2, 0, 64, 4, 256),
+    (sk.SK_GRAPH_TREE, 3, 5, 0, 96, 3, 512),      # 364 nodes, 16 warps per chain
+    (sk.SK_GRAPH_LINE, 0, 0, 128, 64, 4, 128),
+    (sk.SK_GRAPH_LINE, 0, 0, 37, 100, 3, 512),    # ragged line, fewer nodes than threads
+]
+
+
+def _run_layout(J, graph, arity, depth, L, chains, beta, steps, R, init, seed, lanes):
+    inst = sk.Instance(J)
+    run = sk.Run(inst, chains=chains, K=1, beta=beta, seed=seed, record_every=R, max_records=steps // R,
+                 init=init, trace_chains=chains, trace_steps=steps, graph=graph, arity=arity, depth=depth,
+                 line_nodes=L)
+    b = sk.Batch([run])
+    b.set_layout(lanes=lanes)
+    cls = b.classes()
+    b.advance(steps // 2)
+    b.advance(steps - steps // 2)
+    E, _, acc = run.observables()
+    spins, h, step = run.state(fields=True)
+    tr = run.trace()
+    b.close()
+    run.close()
+    inst.close()
+    return dict(E=E, acc=acc, spins=spins, fields=h, step=step, trace=tr, classes=cls)
+
+
+@pytest.mark.parametrize("case", range(len(TEAM_CASES)))
+def test_pm1_graph_teams_bit_exact(case):
+    """Several warps per chain (named-barrier teams) give the oracle's trajectory."""
+    need_gpu()
+    graph, arity, depth, L, N, chains, lanes = TEAM_CASES[case]
+    steps, R, beta = 120, 40, 0.8
+    J = inputs.couplings_pm1(N, 160 + case)
+    init = inputs.initial_spins(chains, N, 170 + case)
+    g = _run_layout(J, graph, arity, depth, L, chains, beta, steps, R, init, 13, lanes)
+    assert g["classes"][0][1] == lanes
+    o = oracle.run_graph(J, graph=_ograph(graph), arity=arity, depth=depth, line_nodes=L, beta=beta, seed=13,
+                         chains=chains, init=init, steps=steps, record_every=R, trace=True)
+    assert g["step"] == steps
+    assert np.array_equal(g["trace"], o["trace"])
+    assert np.array_equal(g["E"], o["E"])
+    assert np.array_equal(g["acc"], o["acc"])
+    assert np.array_equal(g["spins"], o["spins"])
+    assert np.array_equal(g["fields"], (J.astype(np.int64) @ g["spins"].T.astype(np.int64)).T)
+
+
+@pytest.mark.parametrize("graph,arity,depth,L,lanes", [(sk.SK_GRAPH_TREE, 2, 5, 0, 256),
+                                                       (sk.SK_GRAPH_LINE, 0, 0, 48, 128)])
+def test_gauss_graph_teams_decision_replay(graph, arity, depth, L, lanes):
+    need_gpu()
+    N, chains, steps, R, beta = 96, 4, 300, 100, 1.0
+    J = inputs.couplings_gauss(N, 180)
+    init = inputs.initial_spins(chains, N, 181)
+    g = _run_layout(J, graph, arity, depth, L, chains, beta, steps, R, init, 23, lanes)
+    for c in range(chains):
+        r = oracle.replay_graph(J, g["trace"][c], graph=_ograph(graph), arity=arity, depth=depth, line_nodes=L,
+                                beta=beta, seed=23, chain=c, init=init[c], tol=REPLAY_TOL)
+        assert r["bad"] == 0, (c, r)
+        assert r["disagree"] <= 3, (c, r)
+        assert np.array_equal(r["spins"], g["spins"][c])
+        assert abs(g["E"][-1, c] - oracle.energy(J, g["spins"][c])) / N <= 1e-5
+
+
 def test_star_tree_and_line_share_a_batch():
     torch = need_gpu()
     st = torch.cuda.Stream()
