@@ -390,6 +390,33 @@ def run_ttt(args):
 TTT_FEW_CHAINS = (1, 152)
 
 
+def run_graph_one_chain(args):
+    """One chain of the binary tree of depth 7 (Gaussian N = 1024, beta = 1)
+    with 8 warps per chain, 500 steps in one launch: the graph kernel's
+    single-chain latency case (the case its ncu captures use)."""
+    import torch
+    from paper_2102_05613_gb300 import inputs, sk
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    inst = sk.Instance(inputs.couplings_gauss(TTT_N, 0), stream=stream)
+    run = sk.Run(inst, chains=1, K=1, beta=TTT_BETA, seed=7, graph=sk.SK_GRAPH_TREE, arity=2, depth=7)
+    batch = sk.Batch([run], warps_per_cta=16)  # 8 warps per chain, two chains' room per CTA
+    batch.set_layout(lanes=256)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    batch.advance(500)
+    b.record(stream)
+    torch.cuda.synchronize()
+    out = {"workload": "binary tree depth 7 (255 nodes), Gaussian SK N=1024, one chain, 8 warps per chain",
+           "us_per_step": 1e3 * a.elapsed_time(b) / 500, "launch_classes": batch.classes()}
+    batch.close()
+    run.close()
+    inst.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def ttt_few_chains(inst, methods, only):
     """Time to thermalise when only a few chains run (one chain, or one per
     SM), where a Metropolis step cannot fill the GPU and the graph's nodes
@@ -661,10 +688,10 @@ def run_ours(args):
     alu_peak = sms * 128 * sm_clock * 1e6 / 1e12  # T lane-ops/s
     achieved = ops_launch / mean_launch_s / 1e12
     # DRAM bytes of one launch: ncu capture of the 16-instance case at the
-    # profiled layout (class 140: 16 lanes x 2 blocks, rows through L1, 24
+    # profiled layout (class 268: 16 lanes x 2 blocks, rows through L1, 24
     # warps), 295.8 MB, scaled by the chains processed (the state streamed once
     # per launch grows in proportion); null for any other layout
-    profiled = [140, 16, 3072, 24]
+    profiled = [268, 16, 3072, 24]
     traffic = (4 * 295.8e6 * INSTANCES / 64 if N == 512 and info["classes"]
                and list(info["classes"][0][:4]) == profiled else None)
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
@@ -678,35 +705,66 @@ def run_ours(args):
 
     # end to end through the C ABI from pinned host buffers: upload the 64
     # coupling matrices and the 262,144 start configurations, run 100 steps,
-    # read the step's records back
+    # read the step's records back.  Two sets of instances and runs (the same
+    # workload, the same launch geometry) on two streams take the steps in
+    # turn, so that one step's input copies and device checks overlap the
+    # other set's compute; every step's copies and its records' read-back are
+    # inside the timed region.
     e2e = None
     if args.e2e_steps > 0:
         hJ = [torch.from_numpy(J).pin_memory() for J in couplings]
         hS = [torch.from_numpy(inputs.initial_spins(CHAINS, N, seed_base + 77 + i)).pin_memory()
               for i in range(INSTANCES)]
-        hE = [torch.empty((1, CHAINS), dtype=torch.float64).pin_memory() for _ in runs]
-        hQ = [torch.empty((1, CHAINS // 2), dtype=torch.float64).pin_memory() for _ in runs]
-        hA = [torch.empty((1, CHAINS), dtype=torch.int32).pin_memory() for _ in runs]
-        def e2e_step():
-            # the batched entry points: every instance's (run's) copy and check
-            # enqueued, one wait for all checks, then the new state
-            sk.set_couplings_many(insts, hJ)
-            sk.reset_many(runs, hS)
-            batch.advance(R)
-            sk.observables_many(runs, 0, 1, list(zip(hE, hQ, hA)))
+        st2 = torch.cuda.Stream()
+        insts2 = [sk.Instance(J, stream=st2) for J in couplings]
+        runs2 = [sk.Run(inst, chains=CHAINS, K=K, beta=BETA, seed=1 + rank, stream_id=i,
+                        record_every=R, max_records=cap) for i, inst in enumerate(insts2)]
+        cls0 = info["classes"][0]
+        batch2 = sk.Batch(runs2, warps_per_cta=cls0[3])
+        batch2.set_layout(cls0[1], 1 if (cls0[0] >> 5) & 3 == 1 else 2)
+        sets = []
+        for ii, rr, bb in ((insts, runs, batch), (insts2, runs2, batch2)):
+            outs = [(torch.empty((1, CHAINS), dtype=torch.float64).pin_memory(),
+                     torch.empty((1, CHAINS // 2), dtype=torch.float64).pin_memory(),
+                     torch.empty((1, CHAINS), dtype=torch.int32).pin_memory()) for _ in rr]
+            sets.append((ii, rr, bb, outs))
 
-        e2e_step()  # untimed: first-use staging buffers
+        def e2e_issue(x):
+            # the batched entry points: every instance's (run's) copy and check
+            # enqueued, one wait for all checks, then the new state and the steps
+            sk.set_couplings_many(x[0], hJ)
+            sk.reset_many(x[1], hS)
+            x[2].advance(R)
+
+        def e2e_read(x):
+            sk.observables_many(x[1], 0, 1, x[3])
+
+        for x in sets:  # untimed: first-use staging buffers of both sets
+            e2e_issue(x)
+            e2e_read(x)
         barrier()
         t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            e2e_step()
+        prev = None
+        for i in range(args.e2e_steps):
+            x = sets[i % 2]
+            e2e_issue(x)
+            if prev is not None:
+                e2e_read(prev)
+            prev = x
+        e2e_read(prev)
         barrier()
         te = replicas.max_over_ranks(time.perf_counter() - t0, dist, device="cuda")
         h2d = sum(x.numel() * x.element_size() for x in hJ + hS)
-        d2h = sum(x.numel() * x.element_size() for x in hE + hQ + hA)
+        d2h = sum(t.numel() * t.element_size() for o in sets[0][3] for t in o)
         e2e = {"value": world * INSTANCES * CHAINS * R * K * args.e2e_steps / te, "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "steps": args.e2e_steps, "ms_per_step": 1e3 * te / args.e2e_steps}
+               "steps": args.e2e_steps, "ms_per_step": 1e3 * te / args.e2e_steps,
+               "pipelined": "two run sets on two streams take the steps in turn"}
+        for r in runs2:
+            r.close()
+        batch2.close()
+        for i_ in insts2:
+            i_.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -748,7 +806,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--config", choices=["default", "uneven"], default="default",
                     help="uneven: the 256-instance uneven batch in CUDA graphs instead of the bench line")
@@ -758,6 +816,8 @@ def main():
     ap.add_argument("--serve-window", type=float, default=5.0)
     ap.add_argument("--ttt-methods", default="",
                     help="comma-separated subset of the --ttt methods (the K=128 reference always runs)")
+    ap.add_argument("--graph-one-chain", action="store_true",
+                    help="the graph kernel's single-chain latency case (binary tree, depth 7)")
     ap.add_argument("--ttt", action="store_true",
                     help="time-to-thermalise comparison instead of the throughput line")
     ap.add_argument("--no-recompute", action="store_true",
@@ -777,6 +837,8 @@ def main():
         return run_reference(args)
     if args.ttt:
         return run_ttt(args)
+    if args.graph_one_chain:
+        return run_graph_one_chain(args)
     if args.config == "uneven":
         return run_uneven(args)
     if args.serve:

@@ -99,8 +99,9 @@ sk_status sk_create_instance(uint32_t N, uint32_t kind, const void* couplings, u
 sk_status sk_set_couplings(sk_instance* inst, const void* couplings, uint32_t mem);
 
 /* sk_set_couplings for n distinct instances at once: every copy and check is
- * enqueued first (host couplings on each instance's side stream, so they
- * overlap), the checks are read with one wait, and only if all pass do the
+ * enqueued first (host couplings on the library's input stream, apart from
+ * the compute, so they overlap it), the checks are read with one wait, and
+ * only if all pass do the
  * new couplings become current -- all or nothing: on SK_ERR_INVALID_ARG no
  * instance changes and the message names the first failing instance. */
 sk_status sk_set_couplings_many(sk_instance* const* insts, uint32_t n, const void* const* couplings, uint32_t mem);

@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -160,10 +161,12 @@ struct sk_instance {
     bool jop_valid = false;
     void* dJstage = nullptr;              // new couplings, checked before they replace dJ
     unsigned long long* dflag = nullptr;  // result word of the device input checks
-    // host inputs are copied and checked on a side stream, so that the check
-    // does not wait for the compute queued on st; events order the staging
-    // buffers between the two streams
+    // host inputs are copied and checked on the shared input stream (or, when
+    // the staging buffer is still being read, on this side stream), so that
+    // the check does not wait for the compute queued on st; events order the
+    // staging buffers between the streams
     cudaStream_t side = nullptr;
+    cudaStream_t stage_st = nullptr;  // where the last couplings stage was made (input_stream() or side)
     cudaEvent_t ev_side = nullptr;   // side: copy and check done
     cudaEvent_t ev_jfree = nullptr;  // st: dJstage copied into dJ
     cudaEvent_t ev_main = nullptr;   // st: work queued before a start state written on side
@@ -214,6 +217,7 @@ struct sk_run {
     int8_t* ds = nullptr;
     void* dh = nullptr;
     int8_t* dstage = nullptr;  // start spins from the host, checked before use
+    cudaStream_t stage_st = nullptr;  // where the last spins stage was made (input_stream() or side)
     cudaEvent_t ev_sfree = nullptr;  // st: the start kernel has read dstage
     unsigned long long* dflag = nullptr;  // result word of the start-spin check
     unsigned long long* hflag = nullptr;  // its pinned host copy
@@ -252,6 +256,40 @@ namespace {
 // couplings_stage enqueues copy, check and the read-back of the result;
 // couplings_verify (after the stream it returns has been synchronised)
 // reports a violation; couplings_commit makes the staged copy current.
+// One stream per device for the copies and checks of host inputs, shared by
+// all instances (created on first use, kept until the process exits).
+// Per-instance streams would be many more streams than the device has
+// hardware work queues, and a stream that shares a queue with a stream
+// running a step kernel waits for it: the input copies would no longer
+// overlap the compute.  A stage that has to wait for its buffer (still read
+// by queued work) goes on the instance's own side stream instead, so that the
+// shared stream never waits for compute.
+cudaStream_t input_stream() {
+    static std::mutex mu;
+    static cudaStream_t streams[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        streams[dev] = nullptr;
+    }
+    return streams[dev];
+}
+
+// The stream for a stage that must follow `busy` (an event on the main stream):
+// the shared input stream when the event has completed, else `own` after it.
+cudaStream_t stage_stream(cudaEvent_t busy, cudaStream_t own) {
+    const cudaError_t q = cudaEventQuery(busy);
+    if (q == cudaSuccess) {
+        cudaStream_t in = input_stream();
+        if (in) return in;
+    } else if (q != cudaErrorNotReady) {
+        cudaGetLastError();
+    }
+    return own;
+}
+
 sk_status couplings_stage(sk_instance* in, const void* J, uint32_t mem, bool fresh, cudaStream_t* used) {
     const size_t b = jbytes(in->kind);
     const size_t bytes = static_cast<size_t>(in->Npad) * in->Npad * b;
@@ -267,8 +305,9 @@ sk_status couplings_stage(sk_instance* in, const void* J, uint32_t mem, bool fre
         dst = in->dJstage;
     }
     const bool via_side = !fresh && mem == SK_MEM_HOST;
-    cudaStream_t cs = via_side ? in->side : in->st;
+    cudaStream_t cs = via_side ? stage_stream(in->ev_jfree, in->side) : in->st;
     if (via_side) SK_CU(cudaStreamWaitEvent(cs, in->ev_jfree, 0));  // the last copy out of the stage is done
+    in->stage_st = cs;
     if (in->N != in->Npad) SK_CU(cudaMemsetAsync(dst, 0, bytes, cs));
     SK_CU(cudaMemcpy2DAsync(dst, in->Npad * b, J, in->N * b, in->N * b, in->N, cudaMemcpyDefault, cs));
     SK_CU(sk::launch_check_couplings(dst, in->kind, in->N, in->Npad, in->dflag, cs));
@@ -290,7 +329,7 @@ sk_status couplings_verify(const sk_instance* in) {
 sk_status couplings_commit(sk_instance* in, bool fresh) {
     if (!fresh) {
         const size_t bytes = static_cast<size_t>(in->Npad) * in->Npad * jbytes(in->kind);
-        SK_CU(cudaEventRecord(in->ev_side, in->side));  // orders a side-stream stage before the copy
+        SK_CU(cudaEventRecord(in->ev_side, in->stage_st ? in->stage_st : in->side));  // the stage before the copy
         SK_CU(cudaStreamWaitEvent(in->st, in->ev_side, 0));
         SK_CU(cudaMemcpyAsync(in->dJ, in->dJstage, bytes, cudaMemcpyDeviceToDevice, in->st));
         SK_CU(cudaEventRecord(in->ev_jfree, in->st));
@@ -335,13 +374,14 @@ sk_status spins_stage(sk_run* r, const int8_t* spins, uint32_t mem, cudaStream_t
             sk_status s = dalloc(&r->dstage, n);
             if (s != SK_OK) return s;
         }
-        SK_CU(cudaStreamWaitEvent(in->side, r->ev_sfree, 0));  // the last start has read the stage
-        SK_CU(cudaMemcpyAsync(r->dstage, spins, n, cudaMemcpyHostToDevice, in->side));
+        r->stage_st = stage_stream(r->ev_sfree, in->side);
+        SK_CU(cudaStreamWaitEvent(r->stage_st, r->ev_sfree, 0));  // the last start has read the stage
+        SK_CU(cudaMemcpyAsync(r->dstage, spins, n, cudaMemcpyHostToDevice, r->stage_st));
         *dinit = r->dstage;
     } else {
         return fail(SK_ERR_INVALID_ARG, "init_mem must be SK_MEM_HOST or SK_MEM_DEVICE");
     }
-    cudaStream_t cs = mem == SK_MEM_HOST ? in->side : in->st;
+    cudaStream_t cs = mem == SK_MEM_HOST ? r->stage_st : in->st;
     SK_CU(sk::launch_check_spins(*dinit, n, r->dflag, cs));
     SK_CU(cudaMemcpyAsync(r->hflag, r->dflag, sizeof(unsigned long long), cudaMemcpyDeviceToHost, cs));
     *used = cs;
@@ -374,11 +414,15 @@ sk_status init_commit(sk_run* r, const int8_t* dinit, bool on_side) {
     sk_instance* in = r->inst;
     cudaStream_t cs = in->st;
     if (on_side) {
+        if (dinit && dinit == r->dstage && r->stage_st && r->stage_st != in->side) {  // staged elsewhere
+            SK_CU(cudaEventRecord(in->ev_side, r->stage_st));
+            SK_CU(cudaStreamWaitEvent(in->side, in->ev_side, 0));
+        }
         SK_CU(cudaEventRecord(in->ev_main, in->st));
         SK_CU(cudaStreamWaitEvent(in->side, in->ev_main, 0));
         cs = in->side;
-    } else if (dinit && dinit == r->dstage) {  // the staged copy was made on the side stream
-        SK_CU(cudaEventRecord(in->ev_side, in->side));
+    } else if (dinit && dinit == r->dstage) {  // the staged copy was made on its stage stream
+        SK_CU(cudaEventRecord(in->ev_side, r->stage_st ? r->stage_st : in->side));
         SK_CU(cudaStreamWaitEvent(in->st, in->ev_side, 0));
     }
     SK_CU(cudaMemsetAsync(r->dstep, 0, sizeof(uint64_t), cs));
@@ -787,10 +831,10 @@ sk_status mcmcmc_reset_many(sk_run* const* runs, uint32_t n, const int8_t* const
         return SK_OK;
     }
     cudaStream_t bs = runs[0]->inst->st;
-    std::set<sk_instance*> ins;
-    for (uint32_t i = 0; i < n; ++i) ins.insert(runs[i]->inst);
-    for (sk_instance* in : ins) {  // the staged copies were made on the side streams
-        SK_CU(cudaEventRecord(in->ev_side, in->side));
+    for (uint32_t i = 0; i < n; ++i) {  // the staged copies were made on their stage streams
+        if (!dinit[i] || dinit[i] != runs[i]->dstage) continue;
+        sk_instance* in = runs[i]->inst;
+        SK_CU(cudaEventRecord(in->ev_side, runs[i]->stage_st ? runs[i]->stage_st : in->side));
         SK_CU(cudaStreamWaitEvent(bs, in->ev_side, 0));
     }
     std::vector<sk::StartJob> sj(n);

@@ -253,30 +253,39 @@ __global__ void __launch_bounds__(256) fields_kernel(const JT* __restrict__ J, c
 // all ones) receives the smallest (position << 2 | code) of a violation.
 //   couplings: code 1 diagonal entry != 0, 2 entry outside {-1,0,1} (+-J) or
 //   not finite (Gaussian), 3 J_ij != J_ji; position i * 2^16 + j.
+// The checks run on a side stream while the step kernel may hold most of
+// every SM (e.g. 768 threads x 80 registers): 16 registers per thread keep a
+// 256-thread CTA of them within the registers that leaves.
 template <typename JT>
-__global__ void check_couplings_kernel(const JT* __restrict__ J, uint32_t N, uint32_t npad,
+__global__ void __maxnreg__(16) check_couplings_kernel(const JT* __restrict__ J, uint32_t N, uint32_t npad,
                                        unsigned long long* __restrict__ flag) {
-    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
-    const JT a = J[static_cast<size_t>(i) * npad + j];
-    const JT b = J[static_cast<size_t>(j) * npad + i];
-    unsigned code = 0;
-    if (i == j && a != JT(0)) code = 1;
-    else if constexpr (sizeof(JT) == 1) {
-        if (a < JT(-1) || a > JT(1)) code = 2;
-        else if (a != b) code = 3;
-    } else {
-        if (!isfinite(a)) code = 2;
-        else if (a != b) code = 3;
+    // rows i = blockIdx.y, blockIdx.y + gridDim.y, ...
+    for (uint32_t i = blockIdx.y; i < N; i += gridDim.y) {
+        const JT a = J[static_cast<size_t>(i) * npad + j];
+        const JT b = J[static_cast<size_t>(j) * npad + i];
+        unsigned code = 0;
+        if (i == j && a != JT(0)) code = 1;
+        else if constexpr (sizeof(JT) == 1) {
+            if (a < JT(-1) || a > JT(1)) code = 2;
+            else if (a != b) code = 3;
+        } else {
+            if (!isfinite(a)) code = 2;
+            else if (a != b) code = 3;
+        }
+        if (code) atomicMin(flag, ((static_cast<unsigned long long>(i) << 16 | j) << 2) | code);
     }
-    if (code) atomicMin(flag, ((static_cast<unsigned long long>(i) << 16 | j) << 2) | code);
 }
-//   spins: code 1 for a value other than +-1; position = index.
-__global__ void check_spins_kernel(const int8_t* __restrict__ s, uint64_t n, unsigned long long* __restrict__ flag) {
-    for (uint64_t x = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; x < n;
-         x += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
-        const int v = s[x];
-        if (v != 1 && v != -1) atomicMin(flag, (static_cast<unsigned long long>(x) << 2) | 1ull);
+//   spins: code 1 for a value other than +-1; position = index.  A few CTAs
+//   per array (grid-stride loop), so that the check can run beside a
+//   resident step kernel without thousands of CTA launches.
+__global__ void __maxnreg__(16) check_spins_kernel(const int8_t* __restrict__ s, uint64_t n,
+                                                   unsigned long long* __restrict__ flag) {
+    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+    for (uint64_t x = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; x < n; x += stride) {
+        const int v = __ldg(s + x);
+        if (v != 1 && v != -1) atomicMin(flag, (x << 2) | 1ull);
     }
 }
 
@@ -413,7 +422,7 @@ cudaError_t launch_check_couplings(const void* J, uint32_t kind, uint32_t N, uin
                                    unsigned long long* flag, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(flag, 0xFF, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    const dim3 grid((N + 255) / 256, N);
+    const dim3 grid((N + 255) / 256, std::min<uint32_t>(N, 64));
     if (kind == 0)
         check_couplings_kernel<int8_t><<<grid, 256, 0, st>>>(static_cast<const int8_t*>(J), N, Npad, flag);
     else
@@ -424,7 +433,7 @@ cudaError_t launch_check_couplings(const void* J, uint32_t kind, uint32_t N, uin
 cudaError_t launch_check_spins(const int8_t* s, uint64_t n, unsigned long long* flag, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(flag, 0xFF, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    const uint32_t blocks = static_cast<uint32_t>(std::min<uint64_t>((n + 255) / 256, 152ull * 64));
+    const uint32_t blocks = static_cast<uint32_t>(std::min<uint64_t>((n + 4095) / 4096, 64));
     if (blocks) check_spins_kernel<<<blocks, 256, 0, st>>>(s, n, flag);
     return cudaGetLastError();
 }
