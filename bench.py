@@ -58,7 +58,9 @@ def _cores():
 # clocks during the timed region
 # ---------------------------------------------------------------------------
 class Clocks:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples (every 50 ms) of the SM clock and the throttle
+    reasons; stop() keeps the samples taken inside [mark_start(), stop()]."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -69,38 +71,50 @@ class Clocks:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-i", str(gpu_index), "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                 "-i", str(gpu_index), "-lms", "50"], stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+        self.t0 = time.time()
+
+    def mark_start(self):
+        self.t0 = time.time()
 
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        t1 = time.time()
+        time.sleep(0.1)  # the sample that covers the region's end
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.f.close()
-        sm, smax, reasons = [], [], set()
+        import datetime
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         with open(self.path) as f:
             for line in f:
                 p = [x.strip() for x in line.split(",")]
-                if len(p) < 9:
+                if len(p) < 10:
                     continue
                 try:
-                    sm.append(float(p[1]))
-                    smax.append(float(p[2]))
+                    ts = datetime.datetime.strptime(p[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                    rows.append((ts, float(p[2]), float(p[3]), p[6:10]))
                 except ValueError:
                     continue
-                for n_, v in zip(names, p[5:9]):
-                    if v.lower() == "active":
-                        reasons.add(n_)
         os.unlink(self.path)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(smax) if smax else None,
-                "samples": len(sm), "reasons": sorted(reasons)}
+        inside = [r for r in rows if self.t0 - 0.05 <= r[0] <= t1 + 0.05]
+        if not inside and rows:  # no sample inside a short region: the one nearest to it
+            inside = [min(rows, key=lambda r: abs(r[0] - 0.5 * (self.t0 + t1)))]
+        reasons = set()
+        for r in inside:
+            for n_, v in zip(names, r[3]):
+                if v.lower() == "active":
+                    reasons.add(n_)
+        return {"sm_mhz": statistics.median(r[1] for r in inside) if inside else None,
+                "sm_max_mhz": max(r[2] for r in inside) if inside else None,
+                "samples": len(inside), "region_s": round(t1 - self.t0, 3), "reasons": sorted(reasons)}
 
 
 # ---------------------------------------------------------------------------
@@ -638,14 +652,15 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
+    clocks = Clocks(local)  # sampling from before the warm-up; stop() keeps the timed region's samples
     for _ in range(args.warmup):
         batch.advance(R)
     barrier()
     c0 = [r.counters() for r in runs]
-    clocks = Clocks(local)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     barrier()
+    clocks.mark_start()
     for s, e in ev:
         s.record(stream)
         batch.advance(R)
@@ -803,10 +818,10 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--e2e-steps", type=int, default=6)
+    ap.add_argument("--e2e-steps", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--config", choices=["default", "uneven"], default="default",
                     help="uneven: the 256-instance uneven batch in CUDA graphs instead of the bench line")

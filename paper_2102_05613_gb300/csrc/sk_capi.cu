@@ -355,7 +355,7 @@ sk_status check_run_error(sk_run* r) {
     return SK_OK;
 }
 
-sk_status ensure_recompute(sk_run* r, cudaStream_t cs);
+sk_status ensure_recompute(sk_run* r, cudaStream_t cs, bool prepare_j = true);
 
 // Start spins of a run in three phases, as for the couplings: spins_stage
 // enqueues the copy of host spins into the run's staging buffer (side
@@ -481,7 +481,7 @@ void free_run_buffers(sk_run* r) {
 }
 
 // Operand buffers of the tensor-core recompute, allocated on first use.
-sk_status ensure_recompute(sk_run* r, cudaStream_t cs) {
+sk_status ensure_recompute(sk_run* r, cudaStream_t cs, bool prepare_j) {
     sk_instance* in = r->inst;
     sk_status s = SK_OK;
     if (!in->dJop) s = dalloc(&in->dJop, sk::recompute_j_bytes(in->kind, in->Npad));
@@ -495,7 +495,7 @@ sk_status ensure_recompute(sk_run* r, cudaStream_t cs) {
         if (s == SK_OK) SK_CU(cudaMemsetAsync(r->dstats, 0, 6 * sizeof(unsigned long long), cs));
     }
     if (s != SK_OK) return s;
-    if (!in->jop_valid) {
+    if (prepare_j && !in->jop_valid) {
         SK_CU(sk::recompute_prepare_j(in->dJ, in->kind, in->Npad, in->dJop, cs));
         in->jop_valid = true;
     }
@@ -840,15 +840,28 @@ sk_status mcmcmc_reset_many(sk_run* const* runs, uint32_t n, const int8_t* const
     std::vector<sk::StartJob> sj(n);
     std::vector<sk::RecomputeSet> rs(n);
     uint64_t max_words = 0;
+    // operand buffers, then the coupling operands of every instance whose
+    // couplings changed in one launch
+    std::vector<sk::PrepareJ> prep;
     for (uint32_t i = 0; i < n; ++i) {
         sk_run* r = runs[i];
-        sk_status s = ensure_recompute(r, bs);  // operands; the couplings' one if they changed
+        sk_status s = ensure_recompute(r, bs, false);
         if (s != SK_OK) return s;
+        sk_instance* in = r->inst;
+        if (!in->jop_valid) {
+            prep.push_back(sk::PrepareJ{in->dJ, in->dJop, in->Npad, 0});
+            in->jop_valid = true;
+        }
+    }
+    SK_CU(sk::recompute_prepare_j_batch(runs[0]->inst->kind, prep.data(), static_cast<uint32_t>(prep.size()), bs));
+    for (uint32_t i = 0; i < n; ++i) {
+        sk_run* r = runs[i];
         std::memset(&sj[i], 0, sizeof(sk::StartJob));
         sj[i].job = r->job;
         sj[i].init = dinit[i];
         sj[i].dstats = r->dstats;
         sj[i].ddE = r->ddE;
+        sj[i].s_op = r->dSop;  // the start kernel writes the spin operands too
         max_words = std::max<uint64_t>(max_words, static_cast<uint64_t>(r->chains) * (r->inst->Npad / 4));
         rs[i] = sk::RecomputeSet{r->ds, r->dh, r->dSop, r->inst->dJop, r->derr, r->chains, r->inst->Npad};
     }
@@ -859,7 +872,7 @@ sk_status mcmcmc_reset_many(sk_run* const* runs, uint32_t n, const int8_t* const
     SK_CU(cudaFreeAsync(dsj, bs));
     for (uint32_t i = 0; i < n; ++i)
         if (dinit[i] && dinit[i] == runs[i]->dstage) SK_CU(cudaEventRecord(runs[i]->ev_sfree, bs));
-    SK_CU(sk::launch_set_fields_batch(runs[0]->inst->kind, rs.data(), n, bs));
+    SK_CU(sk::launch_set_fields_batch(runs[0]->inst->kind, rs.data(), n, bs, true));
     for (uint32_t i = 0; i < n; ++i) {
         runs[i]->n_recomputes = 0;
         runs[i]->step = 0;

@@ -104,7 +104,8 @@ struct StartJob {
     const int8_t* init;
     unsigned long long* dstats;  // 6 words, or null
     double* ddE;                 // per chain, or null
-    uint64_t pad_;
+    void* s_op;                  // or null: the spins also written as tensor-core operands
+                                 // (e4m3 for +-J, bf16 for Gaussian couplings)
 };
 cudaError_t launch_start_batch(const StartJob* jobs_dev, uint32_t n, uint64_t max_words, cudaStream_t st);
 // Device checks of host-supplied inputs: *flag receives the smallest
@@ -138,6 +139,13 @@ int graph_kernel_occupancy(uint32_t kind, uint32_t graph, uint32_t W, uint32_t n
 size_t recompute_j_bytes(uint32_t kind, uint32_t npad);
 size_t recompute_s_bytes(uint32_t kind, uint32_t chains, uint32_t npad);
 cudaError_t recompute_prepare_j(const void* J, uint32_t kind, uint32_t npad, void* j_op, cudaStream_t st);
+// recompute_prepare_j for several instances of one kind in one launch.
+struct PrepareJ {
+    const void* J;
+    void* j_op;
+    uint32_t npad, pad_;
+};
+cudaError_t recompute_prepare_j_batch(uint32_t kind, const PrepareJ* jobs, uint32_t n, cudaStream_t st);
 // The fields h = J s of several runs of one coupling kind in one launch
 // (mode 3 of launch_recompute for each set, spin operands converted too).
 struct RecomputeSet {
@@ -148,7 +156,8 @@ struct RecomputeSet {
     int* err;
     uint32_t chains, npad;
 };
-cudaError_t launch_set_fields_batch(uint32_t kind, const RecomputeSet* sets, uint32_t n, cudaStream_t st);
+cudaError_t launch_set_fields_batch(uint32_t kind, const RecomputeSet* sets, uint32_t n, cudaStream_t st,
+                                   bool spins_converted = false);
 cudaError_t launch_recompute(uint32_t kind, const int8_t* s, void* h, float* out, void* s_op,
                              const void* j_op, double* dE, unsigned long long* stats, int* err,
                              uint32_t chains, uint32_t npad, uint32_t terms, uint32_t mode, double scale,

@@ -110,33 +110,51 @@ __global__ void start_batch_kernel(const StartJob* __restrict__ jobs) {
     const JobDev& jb = sj.job;
     const uint32_t npad = jb.Npad, N = jb.N;
     const uint32_t words = npad / 4;
-    const uint64_t total = static_cast<uint64_t>(jb.chains) * words;
     const uint32_t k0 = static_cast<uint32_t>(jb.seed), k1 = static_cast<uint32_t>(jb.seed >> 32);
     const uint32_t c3 = (1u << 24) | (jb.stream & 0xFFFFFFu);
     const uint64_t tid = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
     const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
-    for (uint64_t x = tid; x < total; x += stride) {
-        const uint32_t chain = static_cast<uint32_t>(x / words);
-        const uint32_t i0 = static_cast<uint32_t>(x % words) * 4u;
-        uint32_t packed = 0;
-        if (sj.init) {
-            for (uint32_t k = 0; k < 4u; ++k) {
-                const uint32_t i = i0 + k;
-                const int v = i < N ? sj.init[static_cast<size_t>(chain) * N + i] : 0;
-                packed |= (static_cast<uint32_t>(v) & 0xFFu) << (8u * k);
+    const bool init4 = sj.init && (N % 4u) == 0u && (reinterpret_cast<uintptr_t>(sj.init) & 3u) == 0u;
+    // chain c by CTA, its words of 4 spins by thread (no 64-bit divisions)
+    for (uint32_t chain = blockIdx.x; chain < jb.chains; chain += gridDim.x)
+        for (uint32_t wd = threadIdx.x; wd < words; wd += blockDim.x) {
+            const uint32_t i0 = 4u * wd;
+            uint32_t packed = 0;
+            if (init4) {
+                packed = i0 < N ? reinterpret_cast<const uint32_t*>(sj.init + static_cast<size_t>(chain) * N)[wd] : 0u;
+            } else if (sj.init) {
+                for (uint32_t k = 0; k < 4u; ++k) {
+                    const uint32_t i = i0 + k;
+                    const int v = i < N ? sj.init[static_cast<size_t>(chain) * N + i] : 0;
+                    packed |= (static_cast<uint32_t>(v) & 0xFFu) << (8u * k);
+                }
+            } else {
+                const uint4 r = philox4x32_10(make_uint4(i0 / 128u, 0u, chain, c3), k0, k1);
+                const uint32_t wv[4] = {r.x, r.y, r.z, r.w};
+                const uint32_t w = wv[(i0 % 128u) / 32u];
+                for (uint32_t k = 0; k < 4u; ++k) {
+                    const uint32_t i = i0 + k, b = (i % 128u) & 31u;
+                    const int v = i < N ? (((w >> b) & 1u) ? -1 : 1) : 0;
+                    packed |= (static_cast<uint32_t>(v) & 0xFFu) << (8u * k);
+                }
             }
-        } else {
-            const uint4 r = philox4x32_10(make_uint4(i0 / 128u, 0u, chain, c3), k0, k1);
-            const uint32_t wv[4] = {r.x, r.y, r.z, r.w};
-            const uint32_t w = wv[(i0 % 128u) / 32u];
-            for (uint32_t k = 0; k < 4u; ++k) {
-                const uint32_t i = i0 + k, b = (i % 128u) & 31u;
-                const int v = i < N ? (((w >> b) & 1u) ? -1 : 1) : 0;
-                packed |= (static_cast<uint32_t>(v) & 0xFFu) << (8u * k);
+            const size_t at = static_cast<size_t>(chain) * words + wd;
+            reinterpret_cast<uint32_t*>(jb.s)[at] = packed;
+            if (sj.s_op) {  // +-1 / padding 0 as e4m3 (0x38 / 0xB8) or bf16 (0x3F80 / 0xBF80)
+                uint32_t e8 = 0;
+                uint16_t b16[4];
+                for (uint32_t k = 0; k < 4u; ++k) {
+                    const int v = static_cast<int8_t>((packed >> (8u * k)) & 0xFFu);
+                    e8 |= static_cast<uint32_t>(v == 0 ? 0 : (v > 0 ? 0x38 : 0xB8)) << (8u * k);
+                    b16[k] = static_cast<uint16_t>(v == 0 ? 0 : (v > 0 ? 0x3F80 : 0xBF80));
+                }
+                if (jb.kind == 0)
+                    reinterpret_cast<uint32_t*>(sj.s_op)[at] = e8;
+                else
+                    reinterpret_cast<uint2*>(sj.s_op)[at] =
+                        make_uint2(b16[0] | (static_cast<uint32_t>(b16[1]) << 16), b16[2] | (static_cast<uint32_t>(b16[3]) << 16));
             }
         }
-        reinterpret_cast<uint32_t*>(jb.s)[static_cast<size_t>(chain) * words + i0 / 4u] = packed;
-    }
     for (uint64_t c = tid; c < jb.chains; c += stride) {
         jb.acc_run[c] = 0;
         jb.work[2 * c] = 0;
@@ -413,8 +431,8 @@ cudaError_t launch_init(const JobDev* job, const int8_t* init, uint32_t chains, 
 
 cudaError_t launch_start_batch(const StartJob* jobs_dev, uint32_t n, uint64_t max_words, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    const uint32_t bx = static_cast<uint32_t>(std::max<uint64_t>(1, std::min<uint64_t>((max_words + 255) / 256, 512)));
-    start_batch_kernel<<<dim3(bx, n), 256, 0, st>>>(jobs_dev);
+    (void)max_words;
+    start_batch_kernel<<<dim3(512, n), 128, 0, st>>>(jobs_dev);
     return cudaGetLastError();
 }
 

@@ -471,7 +471,48 @@ cudaError_t recompute_prepare_j(const void* J, uint32_t kind, uint32_t npad, voi
     return cudaGetLastError();
 }
 
-cudaError_t launch_set_fields_batch(uint32_t kind, const RecomputeSet* sets, uint32_t n, cudaStream_t st) {
+namespace {
+// The coupling operands of several instances of one kind in one launch
+// (blockIdx.y = instance): the conversions of pm1_to_e4m3 / gauss_to_bf16x3.
+__global__ void prepare_j_batch(const PrepareJ* __restrict__ jobs, uint32_t pm1) {
+    const PrepareJ p = jobs[blockIdx.y];
+    const size_t n = static_cast<size_t>(p.npad) * p.npad;
+    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        if (pm1) {
+            const int v = static_cast<const int8_t*>(p.J)[i];
+            static_cast<uint8_t*>(p.j_op)[i] = v == 0 ? 0 : (v > 0 ? 0x38 : 0xB8);
+        } else {
+            float r = static_cast<const float*>(p.J)[i];
+            uint16_t* o = static_cast<uint16_t*>(p.j_op);
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                const __nv_bfloat16 b = __float2bfloat16_rn(r);
+                o[t * n + i] = __bfloat16_as_ushort(b);
+                r -= __bfloat162float(b);
+            }
+        }
+    }
+}
+}  // namespace
+
+cudaError_t recompute_prepare_j_batch(uint32_t kind, const PrepareJ* jobs, uint32_t n, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    size_t maxn = 0;
+    for (uint32_t i = 0; i < n; ++i) maxn = std::max(maxn, static_cast<size_t>(jobs[i].npad) * jobs[i].npad);
+    PrepareJ* d = nullptr;
+    cudaError_t e = cudaMallocAsync(&d, n * sizeof(PrepareJ), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d, jobs, n * sizeof(PrepareJ), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        prepare_j_batch<<<dim3(std::min<uint32_t>(grid1d(maxn), 512u), n), 256, 0, st>>>(d, kind == 0 ? 1u : 0u);
+        e = cudaGetLastError();
+    }
+    if (d) cudaFreeAsync(d, st);
+    return e;
+}
+
+cudaError_t launch_set_fields_batch(uint32_t kind, const RecomputeSet* sets, uint32_t n, cudaStream_t st,
+                                   bool spins_converted) {
     if (n == 0) return cudaSuccess;
     const bool bf = kind != 0;
     std::vector<SegSpins> seg(n);
@@ -512,7 +553,7 @@ cudaError_t launch_set_fields_batch(uint32_t kind, const RecomputeSet* sets, uin
     if (e == cudaSuccess) e = cudaMemcpyAsync(djobs, jobs.data(), n * sizeof(BatchJob), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(dtasks, tasks.data(), tasks.size() * sizeof(BatchTask), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && !spins_converted) {
         const dim3 g(std::min<uint32_t>(grid1d(maxn), 1024u), n);
         spins_to_op_batch<<<g, 256, 0, st>>>(dseg, bf ? 1u : 0u);
         e = cudaGetLastError();
