@@ -118,13 +118,17 @@ uint32_t graph_nodes(uint32_t graph, uint32_t k, uint32_t D, uint32_t L) {
 // for the line, F_v = round(2^20 c_v / max c) with c_0 = 1, c_(v+1) =
 // c_v (L-1-v)/(v+1) in double precision (c_v = binom(L-1, v), the addition
 // process's root distribution).  Table layout: F (u32), inclusive prefix
-// sums (u64), log2(F / 2^20) (float), each of V rounded up to 4 entries.
-std::vector<unsigned char> graph_table(uint32_t graph, uint32_t V) {
+// sums (u64), log2(F / 2^20) (float), the node's depth in the tree template
+// (u8; 0 for the line), each of V rounded up to 4 entries.
+std::vector<unsigned char> graph_table(uint32_t graph, uint32_t V, uint32_t arity) {
     const size_t V16 = (static_cast<size_t>(V) + 3u) & ~static_cast<size_t>(3u);
-    std::vector<unsigned char> t(16 * V16, 0);
+    std::vector<unsigned char> t(sk::graph_table_bytes(V), 0);
     uint32_t* F = reinterpret_cast<uint32_t*>(t.data());
     uint64_t* P = reinterpret_cast<uint64_t*>(t.data() + 4 * V16);
     float* lg = reinterpret_cast<float*>(t.data() + 12 * V16);
+    uint8_t* dep = t.data() + 16 * V16;
+    if (graph == SK_GRAPH_TREE)
+        for (uint32_t v = 1; v < V; ++v) dep[v] = static_cast<uint8_t>(dep[(v - 1) / arity] + 1);
     if (graph == SK_GRAPH_LINE) {
         std::vector<double> c(V);
         const uint32_t n = V - 1;
@@ -692,7 +696,7 @@ sk_status mcmcmc_create(sk_instance* in, const sk_run_params* p, sk_run** out) {
     if (s == SK_OK) s = dalloc(&r->drecQ, R * (C / 2) * 8);
     if (s == SK_OK && r->p.node_weighted) s = dalloc(&r->drecEnw, R * C * 8);
     if (s == SK_OK && V) {
-        const std::vector<unsigned char> t = graph_table(r->p.graph, V);
+        const std::vector<unsigned char> t = graph_table(r->p.graph, V, r->p.arity);
         s = dalloc(&r->dgtab, t.size());
         if (s == SK_OK) {
             cudaError_t e = cudaMemcpy(r->dgtab, t.data(), t.size(), cudaMemcpyHostToDevice);

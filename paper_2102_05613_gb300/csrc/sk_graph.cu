@@ -52,8 +52,9 @@ constexpr uint32_t kMiscBytes = 512;     // block 0, per-warp partials, chosen n
 
 struct GTab {
     const uint32_t* F;
-    const uint64_t* P;  // inclusive prefix sums of F
-    const float* lg;    // log2(F / 2^20)
+    const uint64_t* P;    // inclusive prefix sums of F
+    const float* lg;      // log2(F / 2^20)
+    const uint8_t* dep;   // depth of each node in the tree template
 };
 __device__ __forceinline__ GTab gtab(const JobDev& jb) {
     const size_t V16 = (static_cast<size_t>(jb.V) + 3u) & ~static_cast<size_t>(3u);
@@ -62,31 +63,16 @@ __device__ __forceinline__ GTab gtab(const JobDev& jb) {
     t.F = reinterpret_cast<const uint32_t*>(b);
     t.P = reinterpret_cast<const uint64_t*>(b + 4 * V16);
     t.lg = reinterpret_cast<const float*>(b + 12 * V16);
+    t.dep = b + 16 * V16;
     return t;
 }
 
 // Full k-ary tree in level order: parent (v - 1) / k by a 32-bit reciprocal,
 // exact for v, k < 2^16 (the error term (v - 1) (kinv k - 2^32) stays below
-// 2^32); depth from the level boundaries.
+// 2^32); node depths come from the run's graph table.
 struct Tree {
     uint32_t k, kinv;
     __device__ __forceinline__ uint32_t par(uint32_t v) const { return __umulhi(v - 1u, kinv); }
-    __device__ __forceinline__ uint32_t depth(uint32_t v) const {
-        uint32_t d = 0, first = 1u, size = k;
-        while (v >= first) {
-            first += size;
-            size *= k;
-            ++d;
-        }
-        return d;
-    }
-    // depth of the meeting node of a (depth da) and b (depth db)
-    __device__ __forceinline__ uint32_t meet_depth(uint32_t a, uint32_t da, uint32_t b, uint32_t db) const {
-        while (da > db) { a = par(a); --da; }
-        while (db > da) { b = par(b); --db; }
-        while (a != b) { a = par(a); b = par(b); --da; }
-        return da;
-    }
 };
 
 // Team barrier: the NW warps of one chain (a warp barrier when NW = 1); the
@@ -125,7 +111,8 @@ struct GMem {
     int8_t* fs;      // [V] the move: the spin of each flipped site before its flip
     uint4* b0;       // block 0 of the step
     void* red;       // [2][16] per-warp partial results (8 bytes each)
-    uint32_t* misc;  // [0] chosen node, [1] path length of the move
+    uint32_t* misc;  // [0] chosen node, [1] path length of the move, [2] the root
+    uint16_t* anc;   // [17] trees: the root's ancestor at each depth 0..depth(root)
 };
 
 size_t chain_bytes(uint32_t npad, uint32_t V) {
@@ -150,6 +137,7 @@ __device__ __forceinline__ GMem chain_mem(unsigned char* base, uint32_t npad, ui
     g.b0 = reinterpret_cast<uint4*>(m);
     g.red = m + 16;
     g.misc = reinterpret_cast<uint32_t*>(m + 16 + 256);
+    g.anc = reinterpret_cast<uint16_t*>(m + 16 + 256 + 16);
     return g;
 }
 
@@ -223,6 +211,29 @@ __device__ __forceinline__ void graph_loop(const JobDev& jb, bool write, uint32_
             const uint4 r = dev::philox4x32_10(make_uint4(b, t, chain, c3), k0, k1);
             if (b == 0u) {
                 *gm.b0 = r;
+                // root: tree floor(U0 V / 2^64); line the first v with
+                // P[v] > floor(U0 sum F / 2^64)
+                const unsigned long long U0 = (static_cast<unsigned long long>(r.y) << 32) | r.x;
+                uint32_t root;
+                if constexpr (GRAPH == 1) {
+                    root = static_cast<uint32_t>(__umul64hi(U0, static_cast<unsigned long long>(V)));
+                    // the root's ancestors by depth
+                    uint32_t a = root;
+                    for (uint32_t d = __ldg(&tab.dep[root]) + 1u; d-- > 0u;) {
+                        gm.anc[d] = static_cast<uint16_t>(a);
+                        a = d ? tr.par(a) : 0u;
+                    }
+                } else {
+                    const unsigned long long x = __umul64hi(U0, __ldg(&tab.P[V - 1u]));
+                    uint32_t lo = 0, hi = V - 1u;
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (__ldg(&tab.P[mid]) > x) hi = mid;
+                        else lo = mid + 1u;
+                    }
+                    root = lo;
+                }
+                gm.misc[2] = root;
             } else {
                 const uint32_t v0 = 4u * (b - 1u) + 1u;
                 const uint32_t w[4] = {r.x, r.y, r.z, r.w};
@@ -237,21 +248,9 @@ __device__ __forceinline__ void graph_loop(const JobDev& jb, bool write, uint32_
         const unsigned long long U0 = (static_cast<unsigned long long>(b0.y) << 32) | b0.x;
         const unsigned long long U1 = (static_cast<unsigned long long>(b0.w) << 32) | b0.z;
 
-        // ---- root ----
-        uint32_t root;
-        if constexpr (GRAPH == 1) {
-            root = static_cast<uint32_t>(__umul64hi(U0, static_cast<unsigned long long>(V)));
-        } else {  // first v with P[v] > floor(U0 sum F / 2^64)
-            const unsigned long long x = __umul64hi(U0, __ldg(&tab.P[V - 1u]));
-            uint32_t lo = 0, hi = V - 1u;
-            while (lo < hi) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (__ldg(&tab.P[mid]) > x) hi = mid;
-                else lo = mid + 1u;
-            }
-            root = lo;
-        }
-        const uint32_t dr = GRAPH == 1 ? tr.depth(root) : 0u;
+        const uint32_t root = gm.misc[2];
+        const uint32_t dr = GRAPH == 1 ? __ldg(&tab.dep[root]) : 0u;
+        const uint16_t* anc = gm.anc;
 
         // ---- pass 1: x_v and sigma_v ----
         for (uint32_t v = tid; v < V; v += T) {
@@ -263,28 +262,27 @@ __device__ __forceinline__ void graph_loop(const JobDev& jb, bool write, uint32_
             }
             uint32_t x, cnt = 0;
             if constexpr (GRAPH == 1) {
-                const uint32_t dv = tr.depth(v);
-                const uint32_t dm = tr.meet_depth(root, dr, v, dv);
-                gm.fx[v] = static_cast<uint16_t>(dv | (dm << 8));
+                const uint32_t dv = __ldg(&tab.dep[v]);
                 // the edge at v: v's own unless v is an ancestor of r, then
                 // the edge from the child of v toward r
-                uint32_t own = v;
-                if (dm == dv) {
-                    own = root;
-                    for (uint32_t d = dr; d > dv + 1u; --d) own = tr.par(own);
-                }
+                const bool v_anc = dv <= dr && anc[dv] == v;
+                const uint32_t own = v_anc ? anc[dv + 1u] : v;
                 x = gm.site[own];
-                uint32_t a = root;
-#pragma unroll 4
-                for (uint32_t d = dr; d > dm; --d) {
+                // climb from v to the meeting node m with r's ancestors,
+                // counting x among v's side of the path (edges below m) ...
+                uint32_t a = v, d = dv;
+                while (d > dr || a != anc[d]) {
                     cnt += (a != own && gm.site[a] == x) ? 1u : 0u;
                     a = tr.par(a);
+                    --d;
                 }
-                a = v;
+                const uint32_t dm = d;
+                gm.fx[v] = static_cast<uint16_t>(dv | (dm << 8));
+                // ... and on r's side (the edges of r's ancestors below m)
 #pragma unroll 4
-                for (uint32_t d = dv; d > dm; --d) {
-                    cnt += (a != own && gm.site[a] == x) ? 1u : 0u;
-                    a = tr.par(a);
+                for (uint32_t e = dm + 1u; e <= dr; ++e) {
+                    const uint32_t c = anc[e];
+                    cnt += (c != own && gm.site[c] == x) ? 1u : 0u;
                 }
             } else {
                 // line: edge e joins nodes e-1 and e; the path's edges are
@@ -316,12 +314,11 @@ __device__ __forceinline__ void graph_loop(const JobDev& jb, bool write, uint32_
                 const uint32_t dd = gm.fx[v], dv = dd & 0xFFu, dm = dd >> 8;
                 const uint32_t nb = dv - dm;
                 uint32_t ra = dr - dm - (nb == 0u ? 1u : 0u), rb = nb ? nb - 1u : 0u;
-                uint32_t a = root, b = nb ? tr.par(v) : 0u;
+                uint32_t ia = dr, b = nb ? tr.par(v) : 0u;
                 auto next = [&]() -> uint32_t {
-                    if (ra) {
-                        a = tr.par(a);
+                    if (ra) {  // r's ancestors from its parent up
                         --ra;
-                        return a;
+                        return anc[--ia];
                     }
                     const uint32_t w = b;
                     b = tr.par(b);
@@ -342,13 +339,9 @@ __device__ __forceinline__ void graph_loop(const JobDev& jb, bool write, uint32_
             H d = H(0);
             if constexpr (GRAPH == 1) {
                 const uint32_t dd = gm.fx[v], dv = dd & 0xFFu, dm = dd >> 8;
-                uint32_t a = root;
 #pragma unroll 4
-                for (uint32_t d_ = dr; d_ > dm; --d_) {
-                    a = tr.par(a);
-                    d += dl[a];
-                }
-                a = v;
+                for (uint32_t e = dm; e < dr; ++e) d += dl[anc[e]];  // r's ancestors up to m
+                uint32_t a = v;
 #pragma unroll 4
                 for (uint32_t d_ = dv; d_ > dm; --d_) {
                     d += dl[a];
@@ -435,7 +428,9 @@ __device__ __forceinline__ void graph_loop(const JobDev& jb, bool write, uint32_
                         }
                     }
                 }
-                gm.misc[0] = static_cast<uint32_t>(found >= 0 ? found : last);
+                const uint32_t js = static_cast<uint32_t>(found >= 0 ? found : last);
+                gm.misc[0] = js;
+                if constexpr (GRAPH == 1) gm.misc[3] = js < V ? gm.fx[js] : 0u;
             }
         }
         team_sync(nw, team);
@@ -448,15 +443,14 @@ __device__ __forceinline__ void graph_loop(const JobDev& jb, bool write, uint32_
         // of the flips does not matter: the signs are those of the path)
         uint32_t n;
         if constexpr (GRAPH == 1) {
-            const uint32_t dj = tr.depth(jsel);
-            const uint32_t dm = tr.meet_depth(root, dr, jsel, dj);
+            const uint32_t dd = jsel == root ? (dr | (dr << 8)) : gm.misc[3];
+            const uint32_t dj = dd & 0xFFu, dm = dd >> 8;
             const uint32_t na = dr - dm;
             n = na + dj - dm;
             for (uint32_t i = tid; i < n; i += T) {
                 uint32_t w;
                 if (i < na) {
-                    w = root;
-                    for (uint32_t q = 0; q <= i; ++q) w = tr.par(w);
+                    w = anc[dr - 1u - i];
                 } else {
                     w = jsel;
                     for (uint32_t q = na; q < i; ++q) w = tr.par(w);
@@ -652,7 +646,7 @@ size_t graph_smem_bytes(uint32_t npad, uint32_t V, uint32_t graph) {
 }
 size_t graph_table_bytes(uint32_t V) {
     const size_t V16 = (static_cast<size_t>(V) + 3u) & ~static_cast<size_t>(3u);
-    return 16u * V16;
+    return 17u * V16;
 }
 bool graph_team_ok(uint32_t W, uint32_t nw) {
     if (nw != 1u && nw != 2u && nw != 4u && nw != 8u && nw != 16u) return false;
