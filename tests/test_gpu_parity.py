@@ -439,6 +439,34 @@ def test_rejected_inputs_change_nothing():
     run.close(); inst.close(); ig.close()
 
 
+def test_inputs_while_compute_is_queued():
+    """New couplings and start spins given twice in a row while a long advance
+    is still queued: the second copy of each must wait until the first has
+    been consumed (its staging buffer is still to be read), and the run then
+    follows the last couplings and spins bit-exactly."""
+    torch = need_gpu()
+    st = torch.cuda.Stream()
+    N, K, chains, steps = 192, 32, 8, 300
+    J0, J1, J2 = (inputs.couplings_pm1(N, 400 + i) for i in range(3))
+    init1, init2 = inputs.initial_spins(chains, N, 410), inputs.initial_spins(chains, N, 411)
+    inst = sk.Instance(J0, stream=st)
+    big = sk.Run(inst, chains=4096, K=128, beta=1.0, seed=2)  # keeps the stream busy
+    run = sk.Run(inst, chains=chains, K=K, beta=0.9, seed=6, trace_chains=chains, trace_steps=steps)
+    big.advance(400)
+    inst.set_couplings(J1)
+    inst.set_couplings(J2)
+    run.reset(init1)
+    run.reset(init2)
+    run.advance(steps)
+    tr = run.trace()
+    spins, h, step = run.state(fields=True)
+    o = oracle.run(J2, K=K, beta=0.9, seed=6, chains=chains, init=init2, steps=steps, trace=True)
+    assert step == steps
+    assert np.array_equal(tr, o["trace"]) and np.array_equal(spins, o["spins"])
+    assert np.array_equal(h, (J2.astype(np.int64) @ spins.T.astype(np.int64)).T)
+    big.close(); run.close(); inst.close()
+
+
 def test_largest_n():
     need_gpu()
     N, K, chains, steps = 8192, 64, 2, 60
