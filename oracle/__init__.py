@@ -69,6 +69,8 @@ def lib():
         L.sko_setgen_bruteforce.restype = d
         L.sko_setgen_dp.argtypes = [i, vp, vp]
         L.sko_setgen_dp.restype = i
+        L.sko_setgen_cumulative.argtypes = [i, vp, vp]
+        L.sko_setgen_cumulative.restype = i
         _lib = L
     return _lib
 
@@ -258,6 +260,16 @@ def setgen_bruteforce(P, M: int) -> float:
     """P_gen(S | S minus M) by enumerating the orders of M's elements (n <= 12)."""
     P = np.ascontiguousarray(P, dtype=np.float64)
     return lib().sko_setgen_bruteforce(P.shape[0], _ptr(P), int(M))
+
+
+def setgen_cumulative(P) -> np.ndarray:
+    """The same probabilities by the paper's cumulative form (O(n 2^n), n <= 20)."""
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    n = P.shape[0]
+    out = np.zeros(1 << n)
+    if lib().sko_setgen_cumulative(n, _ptr(P), _ptr(out)) != 0:
+        raise ValueError("n outside 1..20")
+    return out
 
 
 def setgen_dp(P) -> np.ndarray:

@@ -1243,3 +1243,45 @@ int sko_setgen_dp(int n, const double* P, double* out) {
     }
     return 0;
 }
+
+/*
+ * sko_setgen_cumulative: the same Pt(M) by the paper's cumulative form
+ * (App. D.2, Eq. eq_rec_set_short): a table c(M, e) = sum_{p in S \ M}
+ * P_gen(e | p) for every e in M, built from smaller sets --
+ *   c({e}, e) = sum_{p != e} P_gen(e | p),
+ *   c(M, e)   = c(M \ {f}, e) - P_gen(e | f) for an f in M, f != e (the
+ *               lowest one): moving f from S \ M into M removes its term --
+ * then Pt(M) = (1/|S \ M|) sum_{e in M} c(M, e) Pt(M \ {e}), O(n 2^n) work
+ * (the printed definition garbles the orientation of P_gen and the sets
+ * summed over; this is the reading under which it equals the recursion).
+ * n <= 20 (a table of n 2^n doubles).
+ */
+int sko_setgen_cumulative(int n, const double* P, double* out) {
+    if (n < 1 || n > 20) return -1;
+    const uint32_t all = (1u << n) - 1u;
+    double* c = (double*)malloc(sizeof(double) * (size_t)n << n);
+    if (!c) return -2;
+    out[0] = 1.0;
+    for (uint32_t M = 1; M <= all; ++M) {
+        if (M == all) { out[M] = 0.0; continue; }
+        double tot = 0.0;
+        for (int e = 0; e < n; ++e) {
+            if (!((M >> e) & 1u)) continue;
+            const uint32_t rest = M & ~(1u << e);
+            double ce;
+            if (!rest) {
+                ce = 0.0;
+                for (int p = 0; p < n; ++p)
+                    if (p != e) ce += P[(size_t)e * n + p];
+            } else {
+                const int f = __builtin_ctz(rest);
+                ce = c[(size_t)(M & ~(1u << f)) * n + e] - P[(size_t)e * n + f];
+            }
+            c[(size_t)M * n + e] = ce;
+            tot += ce * out[rest];
+        }
+        out[M] = tot / (double)(n - __builtin_popcount(M));
+    }
+    free(c);
+    return 0;
+}

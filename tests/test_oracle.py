@@ -454,6 +454,31 @@ def test_setgen_recursion_equals_the_process(n):
         assert abs(dp[M] - bf) <= 1e-15 * max(1.0, abs(bf)), (M, dp[M], bf)
 
 
+@pytest.mark.parametrize("n", [1, 2, 4, 7, 12])
+def test_setgen_cumulative_form_equals_the_recursion(n):
+    # App. D.2's O(n 2^n) form: the cumulative table c(M, e) built by removing
+    # one term per added element, then Eq. eq_rec_set_short; against the
+    # definition (n <= 7) and the first-addition recursion
+    P = _setgen_P(n, 40 + n)
+    cu = oracle.setgen_cumulative(P)
+    dp = oracle.setgen_dp(P)
+    assert np.all(np.abs(cu - dp) <= 1e-14 * np.maximum(1.0, np.abs(dp)))
+    if n <= 7:
+        for M in range(1 << n):
+            bf = oracle.setgen_bruteforce(P, M)
+            assert abs(cu[M] - bf) <= 1e-15 * max(1.0, abs(bf)), (M, cu[M], bf)
+
+
+def test_setgen_cumulative_orientation_matters():
+    # a pin on the reading of the garbled cumulative definition: with P_gen
+    # transposed (generated element and parent swapped) the table gives a
+    # different answer for asymmetric P -- the test above would catch that
+    # mistake
+    n = 5
+    P = _setgen_P(n, 77)
+    assert not np.allclose(oracle.setgen_cumulative(P.T.copy()), oracle.setgen_dp(P))
+
+
 def test_setgen_closed_forms():
     # n = 2: the missing element a comes from the only other element b
     P = _setgen_P(2, 3)
