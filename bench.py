@@ -276,18 +276,22 @@ def setgen_report(stream, n=24):
     np.fill_diagonal(P, 0.0)
     P /= 1.5 * P.sum(axis=0, keepdims=True)
     out = torch.empty(1 << n, dtype=torch.float64, device="cuda")
-    sk.set_generation(P, out=out, stream=stream)  # warm-up
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    a.record(stream)
-    sk.set_generation(P, out=out, stream=stream)
-    b.record(stream)
-    torch.cuda.synchronize()
-    ms = a.elapsed_time(b)
-    # terms of the recursion: for each mask M, |M| x |S minus M| parent sums
-    terms = sum(math.comb(n, m) * m * (n - m) for m in range(1, n))
-    return {"workload": f"generation probabilities of all 2^{n} subsets, random P_gen, double precision",
-            "ms": ms, "subsets_per_s": (1 << n) / (ms / 1e3), "terms_per_s": terms / (ms / 1e3)}
+    res = {"workload": f"generation probabilities of all 2^{n} subsets, random P_gen, double precision"}
+    for name, method in (("direct", sk.SK_SETGEN_DIRECT), ("cumulative", sk.SK_SETGEN_CUMULATIVE)):
+        sk.set_generation(P, out=out, stream=stream, method=method)  # warm-up
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        sk.set_generation(P, out=out, stream=stream, method=method)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        res[name] = {"ms": ms, "subsets_per_s": (1 << n) / (ms / 1e3)}
+    # terms of the direct recursion: for each mask M, |M| x |S minus M| parent
+    # sums; the cumulative form does |M| per mask
+    res["direct"]["terms_per_s"] = sum(math.comb(n, m) * m * (n - m) for m in range(1, n)) / (res["direct"]["ms"] / 1e3)
+    res["cumulative"]["terms_per_s"] = sum(math.comb(n, m) * m for m in range(1, n)) / (res["cumulative"]["ms"] / 1e3)
+    return res
 
 
 # ---------------------------------------------------------------------------

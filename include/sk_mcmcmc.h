@@ -456,7 +456,15 @@ sk_status mcmcmc_run_noalloc(uint32_t N, uint32_t kind, const void* couplings, d
  * (App. D.2; the printed recursion's normalisation differs from the process
  * by a factor that depends only on |M|, which cancels between sets of one
  * cardinality).  Computed on the device in double precision, one launch per
- * cardinality, O(n^2 2^n) work.
+ * cardinality, in one of two forms:
+ *   SK_SETGEN_DIRECT      every sum_{p in S \ M} P_gen(e | p) afresh,
+ *                         O(n^2 2^n) work;
+ *   SK_SETGEN_CUMULATIVE  the paper's cumulative table (Eq. eq_rec_set_short),
+ *                         O(n 2^n) work and n 2^n doubles of device memory
+ *                         (SK_ERR_OOM if they cannot be allocated);
+ *   SK_SETGEN_AUTO        the cumulative form when its table can be
+ *                         allocated, else the direct one.
+ * The two agree to rounding (the cumulative table subtracts terms).
  *   n      1..28 elements;
  *   P      n*n doubles, host, P[e*n + p] = P_gen(e | p) (finite, >= 0; the
  *          diagonal is not used);
@@ -464,7 +472,9 @@ sk_status mcmcmc_run_noalloc(uint32_t N, uint32_t kind, const void* couplings, d
  *          elements, out[0] = 1, out[2^n - 1] = 0 (no starting element);
  *   stream cudaStream_t (as void*) or NULL.  Synchronises.
  */
-sk_status sk_set_generation(uint32_t n, const double* P, double* out, uint32_t mem, void* stream);
+typedef enum { SK_SETGEN_AUTO = 0, SK_SETGEN_DIRECT = 1, SK_SETGEN_CUMULATIVE = 2 } sk_setgen_method;
+sk_status sk_set_generation(uint32_t n, const double* P, double* out, uint32_t mem, uint32_t method,
+                            void* stream);
 
 /* ---------------------------------------------------------------------- */
 /* Request server: continuous batching of sampling jobs                    */

@@ -90,7 +90,7 @@ def lib(build_if_missing: bool = True):
             "mcmcmc_wait": [vp, u64],
             "mcmcmc_observables": [vp, u64, u64, vp, vp, vp, u32],
             "mcmcmc_observables_nw": [vp, u64, u64, vp, u32],
-            "sk_set_generation": [u32, vp, vp, u32, vp],
+            "sk_set_generation": [u32, vp, vp, u32, u32, vp],
             "sk_set_couplings_many": [vp, u32, vp, u32],
             "mcmcmc_reset_many": [vp, u32, vp, u32],
             "mcmcmc_observables_many": [vp, u32, u64, u64, vp, vp, vp, u32],
@@ -534,19 +534,23 @@ class Server:
             pass
 
 
-def set_generation(P, out=None, stream=None):
+SK_SETGEN_AUTO, SK_SETGEN_DIRECT, SK_SETGEN_CUMULATIVE = 0, 1, 2
+
+
+def set_generation(P, out=None, stream=None, method: int = SK_SETGEN_AUTO):
     """sk_set_generation: P_gen(S | S minus M) for every bit mask M of an
-    n-element set, P[e, p] = P_gen(e | p).  Returns a numpy array unless a
-    device tensor `out` of 2^n doubles is given."""
+    n-element set, P[e, p] = P_gen(e | p), by the direct recursion or the
+    cumulative form (method).  Returns a numpy array unless a device tensor
+    `out` of 2^n doubles is given."""
     P = np.ascontiguousarray(P, dtype=np.float64)
     n = P.shape[0]
     if out is None:
         res = np.zeros(1 << n)
         _check(lib().sk_set_generation(n, P.ctypes.data_as(C.c_void_p), res.ctypes.data_as(C.c_void_p),
-                                       SK_MEM_HOST, _stream_handle(stream)))
+                                       SK_MEM_HOST, int(method), _stream_handle(stream)))
         return res
     p, mem = _ptr_mem(out)
-    _check(lib().sk_set_generation(n, P.ctypes.data_as(C.c_void_p), p, mem, _stream_handle(stream)))
+    _check(lib().sk_set_generation(n, P.ctypes.data_as(C.c_void_p), p, mem, int(method), _stream_handle(stream)))
     return out
 
 

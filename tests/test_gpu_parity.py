@@ -481,23 +481,26 @@ def test_largest_n():
     assert np.array_equal(g["spins"], o["spins"])
 
 
+@pytest.mark.parametrize("method", [sk.SK_SETGEN_DIRECT, sk.SK_SETGEN_CUMULATIVE])
 @pytest.mark.parametrize("n", [1, 2, 5, 12, 20])
-def test_set_generation_against_oracle(n):
+def test_set_generation_against_oracle(n, method):
     """sk_set_generation (App. D.2 recursion over subset masks, one launch per
-    cardinality) against the oracle's recursion: double precision, the same
-    order of terms per mask (differences only from fused multiply-adds)."""
+    cardinality), direct and cumulative forms, against the oracle's forms:
+    double precision, the same order of terms per mask (differences only from
+    fused multiply-adds)."""
     torch = need_gpu()
     rng = np.random.default_rng(n)
     P = rng.random((n, n))
     np.fill_diagonal(P, 0.0)
     col = P.sum(axis=0, keepdims=True)
     P = P / (1.5 * np.where(col > 0, col, 1.0))
-    got = sk.set_generation(P)
-    want = oracle.setgen_dp(P)
+    got = sk.set_generation(P, method=method)
+    want = oracle.setgen_dp(P) if method == sk.SK_SETGEN_DIRECT else oracle.setgen_cumulative(P)
     assert got[0] == 1.0 and got[-1] == 0.0
     assert np.all(np.abs(got - want) <= 1e-13 * np.abs(want) + 1e-300)
+    assert np.all(np.abs(got - oracle.setgen_dp(P)) <= 1e-12 * np.abs(want) + 1e-300)
     dev = torch.zeros(1 << n, dtype=torch.float64, device="cuda")
-    sk.set_generation(P, out=dev)
+    sk.set_generation(P, out=dev, method=method)
     assert np.array_equal(dev.cpu().numpy(), got)
 
 
@@ -507,6 +510,9 @@ def test_set_generation_arguments():
         sk.set_generation(np.zeros((29, 29)))
     with pytest.raises(sk.SKError):
         sk.set_generation(-np.ones((3, 3)))
+    with pytest.raises(sk.SKError) as e:
+        sk.set_generation(np.zeros((3, 3)), method=3)
+    assert e.value.status == sk.SK_ERR_INVALID_ARG
 
 
 def test_batched_inputs_and_records_equal_single_calls():
