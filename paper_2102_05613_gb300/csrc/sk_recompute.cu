@@ -12,13 +12,18 @@
 //                      reproduce every fp32 value exactly), kind::f16 with FP32
 //                      accumulation of all terms into one accumulator.
 //
-// One CTA (4 warps) computes a 128 x 256 tile: thread 0 streams A and B
-// tiles with TMA (128-byte swizzle) through a 4-stage mbarrier ring, thread
-// 32 issues the MMAs (K = 32 bytes each) into a 128-lane x 256-column FP32
-// accumulator in tensor memory and commits each stage back to its "empty"
-// barrier, then all 128 threads read their row of the accumulator with
-// tcgen05.ld and compare it with (or replace) the maintained fields.
-// Every wait is bounded; an expired wait sets the run's error word.
+// A persistent CTA per SM works through 128 x 256 output tiles with three
+// roles: one thread of warp 0 streams A and B tiles with TMA (128-byte
+// swizzle) through a 4-stage mbarrier ring, one thread of warp 1 issues the
+// MMAs (K = 32 bytes each) into one of two 128-lane x 256-column FP32
+// accumulators in tensor memory (all 512 columns) and commits each stage back
+// to its "empty" barrier and each finished tile to its accumulator's "full"
+// barrier, and warps 2-9 (two per 32-lane quadrant of tensor memory, one per
+// half of the columns) read the finished accumulator with tcgen05.ld and
+// compare it with (or replace) the maintained fields, then hand the
+// accumulator back -- so one tile's epilogue overlaps the next tile's main
+// loop, with eight warps' loads of the fields in flight.  Every wait is bounded; an expired wait
+// sets the run's error word and stops the CTA's roles.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
@@ -35,11 +40,14 @@
 namespace sk {
 namespace {
 
-constexpr uint32_t BM = 128, BN = 256, NS = 2;  // 2 stages: two CTAs share an SM
+constexpr uint32_t BM = 128, BN = 256, NS = 4;  // 4 pipeline stages, one CTA per SM
 constexpr uint32_t TILE_A = BM * 128, TILE_B = BN * 128;  // bytes, 128 B of K per row
 constexpr uint32_t STAGE_BYTES = TILE_A + TILE_B;
-constexpr uint32_t SMEM_BYTES = NS * STAGE_BYTES + 1024;  // + 1 KB alignment slack
-constexpr uint32_t TMEM_COLS = 256;
+constexpr uint32_t EW = 8;                                 // epilogue warps: 2 per tensor-memory quadrant
+constexpr uint32_t EPI_BYTES = EW * 32 * 33 * 4;           // their 32 x 33 transposes
+constexpr uint32_t SMEM_BYTES = NS * STAGE_BYTES + EPI_BYTES + 1024;  // + 1 KB alignment slack
+constexpr uint32_t TMEM_COLS = 512;                        // two 256-column accumulators
+constexpr uint32_t WS_THREADS = 64 + 32 * EW;              // producer, MMA, epilogue warps
 constexpr long long kBudget = 4000000000ll;  // ~2 s of clock cycles per wait
 
 __device__ __forceinline__ uint32_t saddr(const void* p) {
@@ -104,15 +112,6 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                  : "memory");
 }
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -136,105 +135,38 @@ struct Args {
     uint32_t pm1;
 };
 
-// One 128 x 256 tile (rows m0.., columns n0..) of one operand set.
-template <bool F8>
-__device__ __forceinline__ void recompute_tile(const CUtensorMap* pA, const CUtensorMap* pB0, const CUtensorMap* pB1,
-                                               const CUtensorMap* pB2, const Args& args, uint32_t m0, uint32_t n0) {
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t full[NS], empty[NS], accum;
-    __shared__ uint32_t tmem_holder;
-    __shared__ int dead;
-    // 128-byte-swizzled tiles must start on a 1024-byte boundary of shared memory
-    unsigned char* smem = smem_raw + ((1024u - (saddr(smem_raw) & 1023u)) & 1023u);
-    const uint32_t tid = threadIdx.x, warp = tid >> 5;
-    const uint32_t total = args.terms * args.kblocks;
-    constexpr uint32_t kElems = F8 ? 128u : 64u;  // K elements per 128-byte row
-    constexpr uint32_t idesc = instr_desc(F8 ? 0u : 1u);
+// Several operand sets in one launch: the tensor maps and arguments of each
+// set in global memory (maps 64-byte aligned, written before the launch).
+struct alignas(64) BatchJob {
+    CUtensorMap A, B[3];
+    Args args;
+};
+struct BatchTask {
+    uint32_t job, m0, n0, pad;
+};
 
-    if (tid == 0) {
-        for (uint32_t i = 0; i < NS; ++i) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&full[i])) : "memory");
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&empty[i])) : "memory");
-        }
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&accum)) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        dead = 0;
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_holder)),
-                     "r"(TMEM_COLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = tmem_holder;
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
 
-    if (tid == 0) {
-        // producer: A (spins) and B (couplings, term by term) tiles by TMA
-        const CUtensorMap* tb[3] = {pB0, pB1, pB2};
-        for (uint32_t i = 0; i < total; ++i) {
-            const uint32_t st = i % NS, round = i / NS;
-            if (i >= NS && !wait_bounded(saddr(&empty[st]), (round - 1) & 1u)) {
-                atomicExch(args.err, kDevTimeout);
-                dead = 1;
-                break;
-            }
-            const uint32_t term = i / args.kblocks, kb = i % args.kblocks;
-            unsigned char* a = smem + st * STAGE_BYTES;
-            unsigned char* b = a + TILE_A;
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(&full[st])),
-                         "r"(STAGE_BYTES)
-                         : "memory");
-            tma_2d(saddr(a), pA, static_cast<int>(kb * kElems), static_cast<int>(m0), saddr(&full[st]));
-            tma_2d(saddr(b), tb[term], static_cast<int>(kb * kElems), static_cast<int>(n0), saddr(&full[st]));
-        }
-    } else if (tid == 32) {
-        // MMA issuer: 4 MMAs of K = 32 bytes per stage, accumulate in TMEM
-        for (uint32_t i = 0; i < total; ++i) {
-            const uint32_t st = i % NS, round = i / NS;
-            if (!wait_bounded(saddr(&full[st]), round & 1u)) {
-                atomicExch(args.err, kDevTimeout);
-                dead = 1;
-                break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a = saddr(smem + st * STAGE_BYTES);
-            const uint32_t b = a + TILE_A;
-#pragma unroll
-            for (uint32_t kk = 0; kk < 4; ++kk)
-                mma<F8>(tmem, sw128_desc(a + 32 * kk), sw128_desc(b + 32 * kk), idesc, (i | kk) != 0u);
-            mma_commit(saddr(&empty[st]));
-        }
-        mma_commit(saddr(&accum));  // completes when every MMA issued above has
-    }
-    __syncwarp();
-
-    // epilogue.  Warp w reads accumulator rows 32w..32w+31 (chains m0 + 32w + r)
-    // 32 columns at a time (thread = row), transposes the 32 x 32 block through
-    // shared memory (the pipeline buffers are free now) and walks it row by row
-    // with lane = column, so that every access to the fields and spins in
-    // global memory is one contiguous 128-byte row segment.  Per-row sums are
-    // kept per lane and reduced once at the end.
-    const bool ok = wait_bounded(saddr(&accum), 0u);
-    if (!ok && (tid & 31) == 0) atomicExch(args.err, kDevTimeout);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const bool tile_ok = ok && !dead;
-    const uint32_t lane = tid & 31;
-    float* T = reinterpret_cast<float*>(smem) + warp * (32 * 33);  // [32 columns][33] per warp
-    const uint32_t taddr = tmem + ((warp * 32u) << 16);
-    const uint32_t row0 = m0 + warp * 32u;
-    float psum[32];   // per row r: this lane's part of sum_n s_n (h_n - H_n)
+// The epilogue of one finished accumulator for one warp: accumulator rows
+// 32 q .. 32 q + 31 (chains row0 ..), columns c0 .. c1-1, read 32 columns at a
+// time (thread = row), transposed through the warp's 32 x 33 buffer T and
+// walked row by row with lane = column, so that every access to the fields
+// and spins in global memory is one contiguous 128-byte row segment.
+// Per-row sums are kept per lane and reduced once at the end.
+__device__ __forceinline__ void epilogue_rows(uint32_t taddr, float* T, const Args& args, uint32_t row0,
+                                              uint32_t n0, uint32_t c0, uint32_t c1, bool tile_ok) {
+    const uint32_t lane = threadIdx.x & 31;
+    // per row r: this lane's part of sum_n s_n (h_n - H_n), an int32 (+-J) or
+    // a float (Gaussian) kept in the same 32-bit word
+    uint32_t rsum[32];
     float pmax = 0.0f;
-    int imax = 0, isum[32];
+    int imax = 0;
     unsigned long long mism = 0;
 #pragma unroll
-    for (int r = 0; r < 32; ++r) {
-        psum[r] = 0.0f;
-        isum[r] = 0;
-    }
-    for (uint32_t col = 0; col < BN; col += 32) {
+    for (int r = 0; r < 32; ++r) rsum[r] = 0u;  // 0 and 0.0f have the same bits
+    for (uint32_t col = c0; col < c1; col += 32) {
         uint32_t v[32];
         tmem_ld32(taddr + col, v);
         __syncwarp();
@@ -284,11 +216,11 @@ __device__ __forceinline__ void recompute_tile(const CUtensorMap* pA, const CUte
                 const int d = static_cast<int>(hv[r]) - __float2int_rn(H);
                 mism += d != 0;
                 imax = max(imax, abs(d));
-                isum[r] += sv[r] * d;
+                rsum[r] = static_cast<uint32_t>(static_cast<int>(rsum[r]) + sv[r] * d);
             } else {
                 const float d = __uint_as_float(hv[r]) - H;
                 pmax = fmaxf(pmax, fabsf(d));
-                psum[r] = fmaf(static_cast<float>(sv[r]), d, psum[r]);
+                rsum[r] = __float_as_uint(fmaf(static_cast<float>(sv[r]), d, __uint_as_float(rsum[r])));
                 if (args.mode == 1)
                     static_cast<float*>(args.h)[static_cast<size_t>(row0 + r) * args.npad + n] = H;
             }
@@ -298,7 +230,8 @@ __device__ __forceinline__ void recompute_tile(const CUtensorMap* pA, const CUte
         // row sums: lane l holds row r's part for columns l (mod 32); transpose
         __syncwarp();
 #pragma unroll
-        for (int r = 0; r < 32; ++r) T[r * 33 + lane] = args.pm1 ? static_cast<float>(isum[r]) : psum[r];
+        for (int r = 0; r < 32; ++r)
+            T[r * 33 + lane] = args.pm1 ? static_cast<float>(static_cast<int>(rsum[r])) : __uint_as_float(rsum[r]);
         __syncwarp();
         const uint32_t c = row0 + lane;
         if (c < args.chains) {
@@ -306,45 +239,208 @@ __device__ __forceinline__ void recompute_tile(const CUtensorMap* pA, const CUte
             for (int l = 0; l < 32; ++l) rs += static_cast<double>(T[lane * 33 + l]);
             atomicAdd(&args.dE[c], rs);
         }
-        const double dmax = args.pm1 ? static_cast<double>(imax) : static_cast<double>(pmax);
-        atomicMax(&args.stats[0], static_cast<unsigned long long>(__double_as_longlong(dmax)));
-        if (mism) atomicAdd(&args.stats[1], mism);
+        // the warp's maximum and mismatch count, then one atomic each (every
+        // warp of every tile updates the same two words)
+        if (args.pm1) {
+            imax = __reduce_max_sync(0xffffffffu, imax);
+        } else {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) pmax = fmaxf(pmax, __shfl_xor_sync(0xffffffffu, pmax, o));
+        }
+        const unsigned mw = __reduce_add_sync(0xffffffffu, static_cast<unsigned>(mism));
+        if (lane == 0) {
+            const double dmax = args.pm1 ? static_cast<double>(imax) : static_cast<double>(pmax);
+            atomicMax(&args.stats[0], static_cast<unsigned long long>(__double_as_longlong(dmax)));
+            if (mw) atomicAdd(&args.stats[1], static_cast<unsigned long long>(mw));
+        }
+    }
+    __syncwarp();
+}
+
+// The persistent kernel.  BATCH: task t is tasks[t] of operand set
+// jobs[tasks[t].job] (maps in global memory, acquired before use); else the
+// maps and arguments are the kernel's parameters and task t is output tile
+// (t / tiles_n, t % tiles_n).
+template <bool F8, bool BATCH>
+__global__ void __launch_bounds__(WS_THREADS, 1)
+    recompute_ws_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB0,
+                        const __grid_constant__ CUtensorMap tB1, const __grid_constant__ CUtensorMap tB2,
+                        const Args args0, const BatchJob* __restrict__ jobs, const BatchTask* __restrict__ tasks,
+                        uint32_t ntasks, uint32_t tiles_n) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full[NS], empty[NS], tfull[2], tempty[2];
+    __shared__ uint32_t tmem_holder;
+    __shared__ int dead;
+    // 128-byte-swizzled tiles must start on a 1024-byte boundary of shared memory
+    unsigned char* smem = smem_raw + ((1024u - (saddr(smem_raw) & 1023u)) & 1023u);
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr uint32_t kElems = F8 ? 128u : 64u;  // K elements per 128-byte row
+    constexpr uint32_t idesc = instr_desc(F8 ? 0u : 1u);
+    volatile int* vdead = &dead;
+
+    if (threadIdx.x == 0) {
+        for (uint32_t i = 0; i < NS; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&full[i])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&empty[i])) : "memory");
+        }
+        for (uint32_t i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&tfull[i])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(&tempty[i])), "r"(EW) : "memory");
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        dead = 0;
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_holder)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0)
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_holder;
+
+    // the task's maps, arguments and tile origin
+    auto task = [&](uint32_t t, const CUtensorMap*& A, const CUtensorMap* (&B)[3], const Args*& a, uint32_t& m0,
+                    uint32_t& n0) {
+        if constexpr (BATCH) {
+            const BatchTask tk = tasks[t];
+            const BatchJob& j = jobs[tk.job];
+            A = &j.A;
+            B[0] = &j.B[0];
+            B[1] = &j.B[1];
+            B[2] = &j.B[2];
+            a = &j.args;
+            m0 = tk.m0;
+            n0 = tk.n0;
+        } else {
+            A = &tA;
+            B[0] = &tB0;
+            B[1] = &tB1;
+            B[2] = &tB2;
+            a = &args0;
+            m0 = (t / tiles_n) * BM;
+            n0 = (t % tiles_n) * BN;
+        }
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {  // producer: A (spins) and B (couplings, term by term) tiles by TMA
+            uint32_t g = 0;
+            for (uint32_t t = blockIdx.x; t < ntasks && !*vdead; t += gridDim.x) {
+                const CUtensorMap* A;
+                const CUtensorMap* B[3];
+                const Args* a;
+                uint32_t m0, n0;
+                task(t, A, B, a, m0, n0);
+                if constexpr (BATCH) {  // maps written to global memory by a copy: acquire them for TMA
+                    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(A) : "memory");
+                    for (int q = 0; q < 3; ++q)
+                        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(B[q]) : "memory");
+                }
+                const uint32_t total = a->terms * a->kblocks;
+                for (uint32_t i = 0; i < total; ++i, ++g) {
+                    const uint32_t st = g % NS;
+                    if (g >= NS && !wait_bounded(saddr(&empty[st]), ((g / NS) - 1u) & 1u)) {
+                        atomicExch(a->err, kDevTimeout);
+                        *vdead = 1;
+                    }
+                    if (*vdead) break;
+                    const uint32_t term = i / a->kblocks, kb = i % a->kblocks;
+                    unsigned char* sa = smem + st * STAGE_BYTES;
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(&full[st])),
+                                 "r"(STAGE_BYTES)
+                                 : "memory");
+                    tma_2d(saddr(sa), A, static_cast<int>(kb * kElems), static_cast<int>(m0), saddr(&full[st]));
+                    tma_2d(saddr(sa + TILE_A), B[term], static_cast<int>(kb * kElems), static_cast<int>(n0),
+                           saddr(&full[st]));
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {  // MMA issuer: 4 MMAs of K = 32 bytes per stage into accumulator j % 2
+            uint32_t g = 0, j = 0;
+            for (uint32_t t = blockIdx.x; t < ntasks && !*vdead; t += gridDim.x, ++j) {
+                const CUtensorMap* A;
+                const CUtensorMap* B[3];
+                const Args* a;
+                uint32_t m0, n0;
+                task(t, A, B, a, m0, n0);
+                const uint32_t b = j & 1u;
+                if (j >= 2 && !wait_bounded(saddr(&tempty[b]), ((j >> 1) - 1u) & 1u)) {  // epilogue done with it
+                    atomicExch(a->err, kDevTimeout);
+                    *vdead = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t acc = tmem + 256u * b;
+                const uint32_t total = a->terms * a->kblocks;
+                for (uint32_t i = 0; i < total; ++i, ++g) {
+                    const uint32_t st = g % NS;
+                    if (!wait_bounded(saddr(&full[st]), (g / NS) & 1u)) {
+                        atomicExch(a->err, kDevTimeout);
+                        *vdead = 1;
+                    }
+                    if (*vdead) break;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t sa = saddr(smem + st * STAGE_BYTES);
+                    const uint32_t sb = sa + TILE_A;
+#pragma unroll
+                    for (uint32_t kk = 0; kk < 4; ++kk)
+                        mma<F8>(acc, sw128_desc(sa + 32 * kk), sw128_desc(sb + 32 * kk), idesc, (i | kk) != 0u);
+                    mma_commit(saddr(&empty[st]));
+                }
+                mma_commit(saddr(&tfull[b]));  // completes when the tile's MMAs have
+            }
+        }
+    } else {
+        // epilogue warps 2..9: tensor-memory lane quadrant warp % 4, column
+        // half (warp - 2) / 4
+        const uint32_t qd = warp & 3u, half = (warp - 2u) >> 2;
+        float* T = reinterpret_cast<float*>(smem + NS * STAGE_BYTES) + (warp - 2u) * (32 * 33);
+        uint32_t j = 0;
+        for (uint32_t t = blockIdx.x; t < ntasks; t += gridDim.x, ++j) {
+            const CUtensorMap* A;
+            const CUtensorMap* B[3];
+            const Args* a;
+            uint32_t m0, n0;
+            task(t, A, B, a, m0, n0);
+            const uint32_t b = j & 1u;
+            // every lane waits; the outcome is made warp-uniform
+            const bool ok = __all_sync(0xffffffffu, !*vdead && wait_bounded(saddr(&tfull[b]), (j >> 1) & 1u));
+            if (!ok && lane == 0) {
+                atomicExch(a->err, kDevTimeout);
+                *vdead = 1;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const bool live = __all_sync(0xffffffffu, !*vdead);
+            epilogue_rows(tmem + ((qd * 32u) << 16) + 256u * b, T, *a, m0 + qd * 32u, n0, half * (BN / 2),
+                          (half + 1) * (BN / 2), ok && live);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(saddr(&tempty[b]));
+            if (!ok) break;
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
-template <bool F8>
-__global__ void __launch_bounds__(128, 1)
-    recompute_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB0,
-                     const __grid_constant__ CUtensorMap tB1, const __grid_constant__ CUtensorMap tB2,
-                     Args args) {
-    recompute_tile<F8>(&tA, &tB0, &tB1, &tB2, args, blockIdx.x * BM, blockIdx.y * BN);
-}
-
-// Several operand sets in one launch: the tensor maps and arguments of each
-// set in global memory (maps 64-byte aligned, written before the launch),
-// one CTA per tile of the task list.
-struct alignas(64) BatchJob {
-    CUtensorMap A, B[3];
-    Args args;
-};
-struct BatchTask {
-    uint32_t job, m0, n0, pad;
-};
-template <bool F8>
-__global__ void __launch_bounds__(128, 1)
-    recompute_batch_kernel(const BatchJob* __restrict__ jobs, const BatchTask* __restrict__ tasks) {
-    const BatchTask tk = tasks[blockIdx.x];
-    const BatchJob& j = jobs[tk.job];
-    if (threadIdx.x == 0) {  // the maps were written to global memory by a copy: acquire them for TMA
-        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&j.A) : "memory");
-        for (int t = 0; t < 3; ++t)
-            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&j.B[t]) : "memory");
+int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            n = v;
+        else
+            n = 1;
     }
-    recompute_tile<F8>(&j.A, &j.B[0], &j.B[1], &j.B[2], j.args, tk.m0, tk.n0);
+    return n;
 }
 
 // Spin operands of several runs (blockIdx.y = run): +-1 -> e4m3 / bf16.
@@ -559,14 +655,24 @@ cudaError_t launch_set_fields_batch(uint32_t kind, const RecomputeSet* sets, uin
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
+        CUtensorMap none;
+        std::memset(&none, 0, sizeof none);
+        Args a0;
+        std::memset(&a0, 0, sizeof a0);
+        const uint32_t nt = static_cast<uint32_t>(tasks.size());
+        const uint32_t grid = std::min<uint32_t>(nt, static_cast<uint32_t>(sm_count()));
         if (bf) {
-            e = cudaFuncSetAttribute(recompute_batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+            e = cudaFuncSetAttribute(recompute_ws_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     SMEM_BYTES);
             if (e == cudaSuccess)
-                recompute_batch_kernel<false><<<static_cast<uint32_t>(tasks.size()), 128, SMEM_BYTES, st>>>(djobs, dtasks);
+                recompute_ws_kernel<false, true><<<grid, WS_THREADS, SMEM_BYTES, st>>>(none, none, none, none, a0,
+                                                                                      djobs, dtasks, nt, 0u);
         } else {
-            e = cudaFuncSetAttribute(recompute_batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+            e = cudaFuncSetAttribute(recompute_ws_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     SMEM_BYTES);
             if (e == cudaSuccess)
-                recompute_batch_kernel<true><<<static_cast<uint32_t>(tasks.size()), 128, SMEM_BYTES, st>>>(djobs, dtasks);
+                recompute_ws_kernel<true, true><<<grid, WS_THREADS, SMEM_BYTES, st>>>(none, none, none, none, a0,
+                                                                                     djobs, dtasks, nt, 0u);
         }
         if (e == cudaSuccess) e = cudaGetLastError();
     }
@@ -609,15 +715,21 @@ cudaError_t launch_recompute(uint32_t kind, const int8_t* s, void* h, float* out
     a.terms = terms;
     a.mode = mode;
     a.pm1 = bf ? 0u : 1u;
-    const dim3 grid((chains + BM - 1) / BM, (npad + BN - 1) / BN);
+    const uint32_t tiles_n = (npad + BN - 1) / BN;
+    const uint32_t nt = ((chains + BM - 1) / BM) * tiles_n;
+    const uint32_t grid = std::min<uint32_t>(nt, static_cast<uint32_t>(sm_count()));
     if (bf) {
-        e = cudaFuncSetAttribute(recompute_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+        e = cudaFuncSetAttribute(recompute_ws_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 SMEM_BYTES);
         if (e != cudaSuccess) return e;
-        recompute_kernel<false><<<grid, 128, SMEM_BYTES, st>>>(tA, tB[0], tB[1], tB[2], a);
+        recompute_ws_kernel<false, false><<<grid, WS_THREADS, SMEM_BYTES, st>>>(tA, tB[0], tB[1], tB[2], a, nullptr,
+                                                                               nullptr, nt, tiles_n);
     } else {
-        e = cudaFuncSetAttribute(recompute_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+        e = cudaFuncSetAttribute(recompute_ws_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 SMEM_BYTES);
         if (e != cudaSuccess) return e;
-        recompute_kernel<true><<<grid, 128, SMEM_BYTES, st>>>(tA, tB[0], tB[0], tB[0], a);
+        recompute_ws_kernel<true, false><<<grid, WS_THREADS, SMEM_BYTES, st>>>(tA, tB[0], tB[0], tB[0], a, nullptr,
+                                                                              nullptr, nt, tiles_n);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess || mode >= 2) return e;
