@@ -660,7 +660,7 @@ cudaError_t launch_set_fields_batch(uint32_t kind, const RecomputeSet* sets, uin
         Args a0;
         std::memset(&a0, 0, sizeof a0);
         const uint32_t nt = static_cast<uint32_t>(tasks.size());
-        const uint32_t grid = std::min<uint32_t>(nt, static_cast<uint32_t>(sm_count()));
+        const uint32_t grid = std::max<uint32_t>(1u, std::min<uint32_t>(nt, static_cast<uint32_t>(sm_count())));
         if (bf) {
             e = cudaFuncSetAttribute(recompute_ws_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      SMEM_BYTES);
@@ -717,6 +717,7 @@ cudaError_t launch_recompute(uint32_t kind, const int8_t* s, void* h, float* out
     a.pm1 = bf ? 0u : 1u;
     const uint32_t tiles_n = (npad + BN - 1) / BN;
     const uint32_t nt = ((chains + BM - 1) / BM) * tiles_n;
+    if (nt == 0) return cudaSuccess;
     const uint32_t grid = std::min<uint32_t>(nt, static_cast<uint32_t>(sm_count()));
     if (bf) {
         e = cudaFuncSetAttribute(recompute_ws_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
