@@ -137,11 +137,13 @@ __device__ __forceinline__ uint32_t site_of(const uint32_t (&sp)[2 * NB], int k)
 // h_k -= c1 J[x1][k] + c2 J[x2][k] for k < Npad (c2 = 0: one flip); lane gl
 // owns elements 4 gl + 4 G v.  r1 is the staged row (shared memory) when
 // STAGED, else a row of J in global memory; r2 is global and read only when
-// c2 != 0.
-template <typename JT, bool STAGED, int G>
+// c2 != 0.  UNROLL iterations' row loads are in flight together: 2 where
+// other chains hide the L2 latency within tight registers, 8 in the 128-register
+// variant (few warps per SM), where a lone chain waits for each round trip.
+template <typename JT, bool STAGED, int G, int UNROLL>
 __device__ __forceinline__ void update_fields(typename Types<JT>::H* hf, const JT* r1, const JT* r2, int c1,
                                               int c2, uint32_t npad, int gl) {
-#pragma unroll 2
+#pragma unroll UNROLL
     for (uint32_t k = 4u * gl; k < npad; k += 4u * G) {
         if constexpr (sizeof(JT) == 1) {
             int4 hv = *reinterpret_cast<int4*>(hf + k);
@@ -365,7 +367,7 @@ __device__ __noinline__ void record(const JobDev& jb, bool write, uint32_t chain
 // nothing, so that every lane reaches the same barriers).  `dead` is set
 // after a timed-out wait: the group then stops working but still meets the
 // CTA's record barriers.
-template <typename JT, int RULE, int NB, int G, int STAGE>
+template <typename JT, int RULE, int NB, int G, int STAGE, int UNROLL>
 __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_t chain, const ChainMem& cm,
                                            int partner_off, uint32_t t0, uint32_t t1, uint32_t& acc,
                                            uint32_t& phase, bool& dead, uint32_t& n_flips, uint32_t& n_rows) {
@@ -631,9 +633,9 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                 const int c1 = 2 * S[x1];
                 const int c2 = nflip == 2 ? 2 * S[x2] : 0;
                 if (x1_staged)
-                    update_fields<JT, STAGED, G>(hf, rowA, Jrow(x2), c1, c2, npad, g.gl);
+                    update_fields<JT, STAGED, G, UNROLL>(hf, rowA, Jrow(x2), c1, c2, npad, g.gl);
                 else
-                    update_fields<JT, false, G>(hf, Jrow(x1), nullptr, c1, 0, npad, g.gl);
+                    update_fields<JT, false, G, UNROLL>(hf, Jrow(x1), nullptr, c1, 0, npad, g.gl);
                 __syncwarp(g.mask);
                 if (g.gl == 0) {
                     S[x1] = static_cast<int8_t>(-S[x1]);
@@ -727,7 +729,8 @@ __global__ void __launch_bounds__(MAXT, 1)
         __syncwarp();
         if (t1 > t0) {
             if (warp_busy) {
-                chain_loop<JT, RULE, NB, G, STAGE>(jb, own, chain, cm, partner_off, t0, t1, acc, phase, dead,
+                chain_loop<JT, RULE, NB, G, STAGE, (MAXT <= 512 ? 8 : 2)>(jb, own, chain, cm, partner_off, t0, t1, acc,
+                                                                          phase, dead,
                                                    n_flips, n_rows);
             } else {
                 // no chain in this warp: meet the CTA's record barriers only
