@@ -142,7 +142,7 @@ __device__ __forceinline__ GMem chain_mem(unsigned char* base, uint32_t npad, ui
 }
 
 // sum over n path nodes w (next() yields them) of sigma_w row[x_w], the J
-// loads issued eight at a time
+// loads issued eight at a time (the remainder together too)
 template <typename JT, typename H, typename Next>
 __device__ __forceinline__ H path_dot(const JT* __restrict__ row, uint32_t n, const uint16_t* xs, const int8_t* sg,
                                       Next&& next) {
@@ -158,15 +158,17 @@ __device__ __forceinline__ H path_dot(const JT* __restrict__ row, uint32_t n, co
 #pragma unroll
         for (int q = 0; q < 8; ++q) acc += static_cast<H>(sg[w[q]]) * static_cast<H>(j[q]);
     }
-    for (; i + 2u <= n; i += 2u) {
-        const uint32_t w0 = next(), w1 = next();
-        const JT j0 = __ldg(row + xs[w0]), j1 = __ldg(row + xs[w1]);
-        acc += static_cast<H>(sg[w0]) * static_cast<H>(j0);
-        acc += static_cast<H>(sg[w1]) * static_cast<H>(j1);
-    }
-    if (i < n) {
-        const uint32_t w0 = next();
-        acc += static_cast<H>(sg[w0]) * static_cast<H>(__ldg(row + xs[w0]));
+    if (i < n) {  // the last n - i < 8 terms, their loads issued together
+        const uint32_t r = n - i;
+        uint32_t w[8];
+        JT j[8];
+#pragma unroll
+        for (uint32_t q = 0; q < 8u; ++q) w[q] = q < r ? next() : 0u;
+#pragma unroll
+        for (uint32_t q = 0; q < 8u; ++q) j[q] = q < r ? __ldg(row + xs[w[q]]) : JT(0);
+#pragma unroll
+        for (uint32_t q = 0; q < 8u; ++q)
+            if (q < r) acc += static_cast<H>(sg[w[q]]) * static_cast<H>(j[q]);
     }
     return acc;
 }
@@ -490,9 +492,18 @@ __device__ __forceinline__ void graph_loop(const JobDev& jb, bool write, uint32_
 #pragma unroll
                     for (int q = 0; q < 4; ++q) upd(j[q], 2 * gm.fs[i + q]);
                 }
-                for (; i < n; ++i)
-                    upd(__ldg(reinterpret_cast<const unsigned int*>(col + static_cast<size_t>(gm.fx[i]) * npad)),
-                        2 * gm.fs[i]);
+                if (i < n) {  // the last n - i < 4 rows together
+                    const uint32_t r = n - i;
+                    uint32_t j[3];
+#pragma unroll
+                    for (uint32_t q = 0; q < 3u; ++q)
+                        j[q] = q < r ? __ldg(reinterpret_cast<const unsigned int*>(
+                                           col + static_cast<size_t>(gm.fx[i + q]) * npad))
+                                     : 0u;
+#pragma unroll
+                    for (uint32_t q = 0; q < 3u; ++q)
+                        if (q < r) upd(j[q], 2 * gm.fs[i + q]);
+                }
                 *reinterpret_cast<int4*>(hf + k) = hv;
             } else {
                 float4 hv = *reinterpret_cast<float4*>(hf + k);
@@ -511,9 +522,17 @@ __device__ __forceinline__ void graph_loop(const JobDev& jb, bool write, uint32_
 #pragma unroll
                     for (int q = 0; q < 4; ++q) upd(j[q], static_cast<float>(2 * gm.fs[i + q]));
                 }
-                for (; i < n; ++i)
-                    upd(__ldg(reinterpret_cast<const float4*>(col + static_cast<size_t>(gm.fx[i]) * npad)),
-                        static_cast<float>(2 * gm.fs[i]));
+                if (i < n) {  // the last n - i < 4 rows together
+                    const uint32_t r = n - i;
+                    float4 j[3];
+#pragma unroll
+                    for (uint32_t q = 0; q < 3u; ++q)
+                        j[q] = q < r ? __ldg(reinterpret_cast<const float4*>(col + static_cast<size_t>(gm.fx[i + q]) * npad))
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (uint32_t q = 0; q < 3u; ++q)
+                        if (q < r) upd(j[q], static_cast<float>(2 * gm.fs[i + q]));
+                }
                 *reinterpret_cast<float4*>(hf + k) = hv;
             }
         }
