@@ -467,6 +467,61 @@ def test_inputs_while_compute_is_queued():
     big.close(); run.close(); inst.close()
 
 
+@pytest.mark.parametrize("rule,K,lanes", [(sk.SK_RULE_MCMCMC, 8, 32), (sk.SK_RULE_MCMCMC, 128, 32),
+                                           (sk.SK_RULE_MCMCMC, 128, 16), (sk.SK_RULE_MCMCMC, 200, 16),
+                                           (sk.SK_RULE_MCMCMC, 40, 8), (sk.SK_RULE_METROPOLIS, 1, 32)])
+def test_few_warps_variant_bit_exact(rule, K, lanes):
+    """The 128-register step kernel (at most 16 warps per CTA: the update's
+    row loads eight iterations deep, and for MCMCMC with rows through L1 the
+    next step's draws and J_ab gathered during the update) follows the
+    oracle bit-exactly, ragged N and chain counts included."""
+    torch = need_gpu()
+    st = torch.cuda.Stream()
+    N, chains, steps, R = 333, 7, 300, 100
+    J = inputs.couplings_pm1(N, 500 + K)
+    init = inputs.initial_spins(chains, N, 501 + K)
+    inst = sk.Instance(J, stream=st)
+    run = sk.Run(inst, chains=chains, K=K, rule=rule, beta=0.8, seed=17, record_every=R,
+                 max_records=steps // R, init=init, trace_chains=chains, trace_steps=steps)
+    b = sk.Batch([run], warps_per_cta=8)
+    b.set_layout(lanes, 2)
+    assert b.info()["warps_per_cta"] <= 16
+    b.advance(steps // 3)
+    b.advance(steps - steps // 3)
+    tr = run.trace()
+    E, _, acc = run.observables()
+    spins, h, step = run.state(fields=True)
+    o = oracle.run(J, K=K, rule=rule, beta=0.8, seed=17, chains=chains, init=init, steps=steps,
+                   record_every=R, trace=True)
+    assert step == steps
+    assert np.array_equal(tr, o["trace"]) and np.array_equal(E, o["E"]) and np.array_equal(acc, o["acc"])
+    assert np.array_equal(spins, o["spins"])
+    assert np.array_equal(h, (J.astype(np.int64) @ spins.T.astype(np.int64)).T)
+    b.close(); run.close(); inst.close()
+
+
+def test_few_warps_variant_gaussian_replay():
+    # the same variant on Gaussian couplings: every chain's recorded
+    # trajectory is one the oracle's node rule takes from the same draws
+    torch = need_gpu()
+    st = torch.cuda.Stream()
+    N, K, chains, steps = 257, 96, 5, 400
+    J = inputs.couplings_gauss(N, 610)
+    init = inputs.initial_spins(chains, N, 611)
+    inst = sk.Instance(J, stream=st)
+    run = sk.Run(inst, chains=chains, K=K, beta=1.0, seed=23, init=init, trace_chains=chains,
+                 trace_steps=steps)
+    b = sk.Batch([run], warps_per_cta=16)
+    b.set_layout(32, 2)
+    b.advance(steps)
+    tr = run.trace()
+    spins, _ = run.state()
+    for c in range(chains):
+        r = oracle.replay(J, tr[c], K=K, beta=1.0, seed=23, chain=c, init=init[c], tol=1e-4)
+        assert r["bad"] == 0 and np.array_equal(r["spins"], spins[c]), (c, r)
+    b.close(); run.close(); inst.close()
+
+
 def test_largest_n():
     need_gpu()
     N, K, chains, steps = 8192, 64, 2, 60
