@@ -721,6 +721,19 @@ def run_ours(args):
                 "J_rows_per_chain_step": rows_ps, "flips_per_chain_step": flips_ps,
                 "J_bytes_per_chain_step": rows_ps * N * 4,
                 "mean_launch_ms": 1e3 * mean_launch_s}
+    # second line: the bytes one chain-step moves through the SM's L1 /
+    # shared-memory data path, r N b_J (J rows, from L2 through L1) + K (b_s +
+    # b_h) (spin and field gathers at the proposal sites) + 2 f N b_h (the
+    # field read-modify-write of each flipped spin), against that path's
+    # nominal 128 bytes per clock per SM
+    l1_bytes = rows_ps * N * 4 + K * (1 + 4) + 2 * flips_ps * N * 4
+    l1_peak = sms * 128 * sm_clock * 1e6 / 1e9  # GB/s
+    l1_achieved = l1_bytes * INSTANCES * CHAINS * R / mean_launch_s / 1e9
+    roofline["l1_data_path"] = {"achieved": l1_achieved, "peak": l1_peak, "unit": "GB/s",
+                                "frac": l1_achieved / l1_peak, "bytes_per_chain_step": l1_bytes,
+                                "J_GBps": rows_ps * N * 4 * INSTANCES * CHAINS * R / mean_launch_s / 1e9,
+                                "peak_source": f"nominal 128 B per clock per SM x {sms} SMs x "
+                                               f"{sm_clock:.0f} MHz"}
 
     # end to end through the C ABI from pinned host buffers: upload the 64
     # coupling matrices and the 262,144 start configurations, run 100 steps,
