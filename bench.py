@@ -295,7 +295,8 @@ def setgen_report(stream, n=24):
 
 
 # ---------------------------------------------------------------------------
-# time to thermalise: MCMCMC vs K = 1 Metropolis (Gaussian N = 1024, beta = 1)
+# time to thermalise: MCMCMC vs K = 1 Metropolis (Gaussian N = 1024; beta = 1 by
+# default, the paper's T = T_c; --ttt-beta for colder or hotter runs)
 # ---------------------------------------------------------------------------
 TTT_N, TTT_CHAINS, TTT_BETA = 1024, 4096, 1.0
 # name, rule, K, steps, graph (the graphs of Fig. fig_sk: the 2^7 line, the
@@ -324,11 +325,13 @@ def run_ttt(args):
     inst = sk.Instance(J, stream=stream)
     curves = {}
     only = set(args.ttt_methods.split(",")) if args.ttt_methods else None
+    beta, scale = args.ttt_beta, args.ttt_scale
     for name, rule, Kt, T, gkw in TTT_METHODS:
         if only and name not in only and name != "mcmcmc_k128":
             continue
+        T *= scale
         R = T // 2048
-        run = sk.Run(inst, chains=TTT_CHAINS, K=Kt, rule=rule, beta=TTT_BETA, seed=7,
+        run = sk.Run(inst, chains=TTT_CHAINS, K=Kt, rule=rule, beta=beta, seed=7,
                      record_every=R, max_records=2048, **gkw)
         # each method runs with its own autotuned launch geometry (lanes per
         # chain, chains per CTA); tuning leaves the chains untouched
@@ -358,7 +361,7 @@ def run_ttt(args):
     tail = ref["e"][1024:]
     e_inf = float(tail.mean())
     sig = float(tail.std(ddof=1))
-    out = {"workload": f"gaussian-sk N={TTT_N} J seed 0, beta={TTT_BETA}, {TTT_CHAINS} chains from "
+    out = {"workload": f"gaussian-sk N={TTT_N} J seed 0, beta={beta}, {TTT_CHAINS} chains from "
                        f"a random start, records every T/2048 steps",
            "e_inf": e_inf, "sigma_inf": sig, "methods": {}}
     for name, c in curves.items():
@@ -399,7 +402,7 @@ def run_ttt(args):
                 ss[name][str(eps)] = sa / sb
     out["wallclock_speedup_vs_metropolis"] = sp
     out["mc_step_ratio_vs_metropolis"] = ss
-    out["few_chains"] = ttt_few_chains(inst, out["methods"], only)
+    out["few_chains"] = ttt_few_chains(inst, out["methods"], only, beta)
     inst.close()
     print(json.dumps(out), flush=True)
     return 0
@@ -435,7 +438,7 @@ def run_graph_one_chain(args):
     return 0
 
 
-def ttt_few_chains(inst, methods, only):
+def ttt_few_chains(inst, methods, only, beta):
     """Time to thermalise when only a few chains run (one chain, or one per
     SM), where a Metropolis step cannot fill the GPU and the graph's nodes
     are what runs in parallel: seconds per step of each method at C chains
@@ -451,7 +454,7 @@ def ttt_few_chains(inst, methods, only):
         for name, rule, Kt, _T, gkw in TTT_METHODS:
             if name not in methods or (only and name not in only and name != "mcmcmc_k128"):
                 continue
-            run = sk.Run(inst, chains=C, K=Kt, rule=rule, beta=TTT_BETA, seed=11, **gkw)
+            run = sk.Run(inst, chains=C, K=Kt, rule=rule, beta=beta, seed=11, **gkw)
             batch = sk.Batch([run])
             batch.autotune(trial_steps=32)
             geometry = batch.classes()
@@ -848,6 +851,10 @@ def main():
     ap.add_argument("--serve-window", type=float, default=5.0)
     ap.add_argument("--ttt-methods", default="",
                     help="comma-separated subset of the --ttt methods (the K=128 reference always runs)")
+    ap.add_argument("--ttt-beta", type=float, default=TTT_BETA,
+                    help="inverse temperature of the --ttt comparison (1 = T_c, the paper's setting)")
+    ap.add_argument("--ttt-scale", type=int, default=1,
+                    help="multiplies every --ttt method's steps (colder runs relax more slowly)")
     ap.add_argument("--graph-one-chain", action="store_true",
                     help="the graph kernel's single-chain latency case (binary tree, depth 7)")
     ap.add_argument("--ttt", action="store_true",
