@@ -631,7 +631,11 @@ sk_status sk_energy(const sk_instance* in, const int8_t* spins, uint32_t count, 
         for (size_t i = 0; i < n; ++i)
             if (spins[i] != 1 && spins[i] != -1) return fail(SK_ERR_INVALID_ARG, "spin %zu is not +-1", i);
         if ((s = dalloc(&tmp, n)) != SK_OK) return s;
-        SK_CU(cudaMemcpyAsync(tmp, spins, n, cudaMemcpyHostToDevice, in->st));
+        const cudaError_t e = cudaMemcpyAsync(tmp, spins, n, cudaMemcpyHostToDevice, in->st);
+        if (e != cudaSuccess) {
+            cudaFree(tmp);
+            return fail(SK_ERR_CUDA, "sk_energy: %s", cudaGetErrorString(e));
+        }
         dsp = tmp;
     } else if (mem != SK_MEM_DEVICE) {
         return fail(SK_ERR_INVALID_ARG, "mem must be SK_MEM_HOST or SK_MEM_DEVICE");

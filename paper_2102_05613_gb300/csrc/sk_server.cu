@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -64,8 +65,13 @@ struct Job {
 
 }  // namespace
 
+// Threads: the worker alone creates and frees device objects; `mu` guards
+// the queue, the job table, the active list's changes, job statuses and the
+// counters, which the caller's threads read; `used` is atomic because the
+// worker changes it while admitting without holding `mu`.
 struct sk_server {
-    uint64_t budget = 0, used = 0;
+    uint64_t budget = 0;
+    std::atomic<uint64_t> used{0};
     uint32_t quantum = 256;
     cudaStream_t st = nullptr;
     std::mutex mu;
@@ -228,7 +234,10 @@ void loop(sk_server* s) {
                 still.push_back(j);
             }
         }
-        s->active.swap(still);
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->active.swap(still);
+        }
         // 2. admit queued jobs that fit, first in first out
         {
             std::unique_lock<std::mutex> lk(s->mu);
@@ -278,6 +287,8 @@ void loop(sk_server* s) {
                 for (auto& j : s->active) {
                     j->status.state = SK_JOB_FAILED;
                     j->status.error = SK_ERR_CUDA;
+                    j->status.t_done = since(s);
+                    s->completed++;
                 }
                 s->done_cv.notify_all();
                 break;
@@ -294,12 +305,12 @@ void loop(sk_server* s) {
         const auto a = Clock::now();
         sk_status r = mcmcmc_batch_advance(batch, s->quantum);
         if (r == SK_OK && cudaStreamSynchronize(s->st) != cudaSuccess) r = SK_ERR_CUDA;
+        std::lock_guard<std::mutex> lk(s->mu);
         s->busy_s += std::chrono::duration<double>(Clock::now() - a).count();
         s->chain_steps += cs;
         s->candidates += cand;
         s->quanta++;
         if (r != SK_OK) {
-            std::lock_guard<std::mutex> lk(s->mu);
             s->fatal = r;
             s->done_cv.notify_all();
             break;
@@ -307,6 +318,7 @@ void loop(sk_server* s) {
     }
     if (batch) mcmcmc_batch_free(batch);
     for (auto& j : s->active) release(s, *j);
+    std::lock_guard<std::mutex> lk(s->mu);
     s->active.clear();
 }
 
