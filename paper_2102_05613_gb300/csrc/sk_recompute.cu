@@ -167,14 +167,31 @@ __device__ __forceinline__ void epilogue_rows(uint32_t taddr, float* T, const Ar
 #pragma unroll
     for (int r = 0; r < 32; ++r) rsum[r] = 0u;  // 0 and 0.0f have the same bits
     for (uint32_t col = c0; col < c1; col += 32) {
+        const uint32_t n = n0 + col + lane;
+        const bool col_ok = tile_ok && n0 + col < args.npad;  // npad is a multiple of 32
+        // check / resync: the 32 rows' maintained fields and spins are loaded
+        // first, so that their round trip covers the accumulator load and the
+        // transpose (each field is read once, then written once by this thread)
+        uint32_t hv[32];
+        int sv[32];
+        if (args.mode < 2) {
+#pragma unroll
+            for (int r = 0; r < 32; ++r) {
+                hv[r] = 0u;
+                sv[r] = 0;
+                if (col_ok && row0 + r < args.chains) {
+                    const size_t idx = static_cast<size_t>(row0 + r) * args.npad + n;
+                    hv[r] = __ldg(static_cast<const unsigned int*>(args.h) + idx);
+                    sv[r] = __ldg(args.s + idx);
+                }
+            }
+        }
         uint32_t v[32];
         tmem_ld32(taddr + col, v);
         __syncwarp();
 #pragma unroll
         for (int j = 0; j < 32; ++j) T[j * 33 + lane] = __uint_as_float(v[j]);  // T[column][row]
         __syncwarp();
-        const uint32_t n = n0 + col + lane;
-        const bool col_ok = tile_ok && n0 + col < args.npad;  // npad is a multiple of 32
         if (args.mode == 2) {
 #pragma unroll
             for (int r = 0; r < 32; ++r)
@@ -193,20 +210,6 @@ __device__ __forceinline__ void epilogue_rows(uint32_t taddr, float* T, const Ar
                         static_cast<float*>(args.h)[idx] = T[lane * 33 + r];
                 }
             continue;
-        }
-        // all 32 rows' loads first (each field is read once, then written once
-        // by this thread), then the arithmetic and the stores
-        uint32_t hv[32];
-        int sv[32];
-#pragma unroll
-        for (int r = 0; r < 32; ++r) {
-            hv[r] = 0u;
-            sv[r] = 0;
-            if (col_ok && row0 + r < args.chains) {
-                const size_t idx = static_cast<size_t>(row0 + r) * args.npad + n;
-                hv[r] = __ldg(static_cast<const unsigned int*>(args.h) + idx);
-                sv[r] = __ldg(args.s + idx);
-            }
         }
 #pragma unroll
         for (int r = 0; r < 32; ++r) {
