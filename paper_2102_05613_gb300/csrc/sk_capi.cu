@@ -212,6 +212,12 @@ struct sk_batch {
     cudaStream_t st = nullptr;
     cudaGraphExec_t graph = nullptr;  // mcmcmc_batch_capture
     uint64_t graph_steps = 0;
+    // several classes: their launches fork from `st` onto side streams and
+    // join back, so that one class's last CTAs share the SMs with the next
+    // class's first ones instead of leaving them idle
+    static constexpr uint32_t kSide = 4;
+    cudaStream_t side[kSide] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[kSide] = {};
 };
 
 struct sk_run {
@@ -1150,6 +1156,8 @@ uint32_t fit_warps(uint32_t per_chain, uint32_t G) {
 // lanes per chain and warps per CTA: the autotuned or forced values, else
 // the fewest lanes K allows (whole-warp chains for runs of few chains, where
 // latency matters) and as many warps as fit.  Uploads them.
+sk_status ensure_side_streams(sk_batch* b);
+
 sk_status plan_batch(sk_batch* b) {
     std::map<uint64_t, std::vector<uint32_t>> groups;  // key -> run indices (in order)
     const uint32_t n = static_cast<uint32_t>(b->runs.size());
@@ -1266,6 +1274,7 @@ sk_status plan_batch(sk_batch* b) {
     cudaFree(b->ditems);
     b->ditems = d;
     b->classes = classes;
+    if (sk_status s2 = ensure_side_streams(b); s2 != SK_OK) return s2;
     b->n_items = static_cast<uint32_t>(items.size());
     b->grid = grid;
     if (b->graph) {  // the captured launches used the old plan
@@ -1326,20 +1335,64 @@ sk_status mcmcmc_batch_set_layout(sk_batch* b, uint32_t lanes, uint32_t staging)
 namespace {
 // Launches `steps` steps of the batch's classes (only class `only` if >= 0);
 // the step counters are bumped after the last launched class.
+// Creates the side streams and events of a batch with several classes
+// (before any capture: creation is not a stream operation to record).
+sk_status ensure_side_streams(sk_batch* b) {
+    if (b->classes.size() < 2 || b->ev_fork) return SK_OK;
+    cudaError_t e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    for (uint32_t i = 0; i < sk_batch::kSide && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join[i], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return fail(SK_ERR_CUDA, "side streams: %s", cudaGetErrorString(e));
+    return SK_OK;
+}
+
+void free_side_streams(sk_batch* b) {
+    for (uint32_t i = 0; i < sk_batch::kSide; ++i) {
+        if (b->side[i]) cudaStreamDestroy(b->side[i]);
+        if (b->ev_join[i]) cudaEventDestroy(b->ev_join[i]);
+        b->side[i] = nullptr;
+        b->ev_join[i] = nullptr;
+    }
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    b->ev_fork = nullptr;
+}
+
+// Launches `steps` steps of every class (or of class `only`, on the batch's
+// stream).  Several classes: class k runs on side stream k mod kSide after
+// the work queued so far on the batch's stream, the batch's stream waits for
+// all of them, then the runs' step counters advance.  The classes touch
+// disjoint runs and have their own work counters, and no kernel waits for
+// another, so any overlap of their CTAs is safe.
 sk_status launch_segment(sk_batch* b, uint64_t steps, int only = -1) {
     const size_t nc = b->classes.size();
+    const bool fork = only < 0 && nc > 1 && b->ev_fork;
+    const uint32_t nside = fork ? static_cast<uint32_t>(std::min<size_t>(nc, sk_batch::kSide)) : 0u;
+    if (fork) {
+        SK_CU(cudaEventRecord(b->ev_fork, b->st));
+        for (uint32_t i = 0; i < nside; ++i) SK_CU(cudaStreamWaitEvent(b->side[i], b->ev_fork, 0));
+    }
     for (size_t k = 0; k < nc; ++k) {
         if (only >= 0 && static_cast<size_t>(only) != k) continue;
         const sk_batch::Class& c = b->classes[k];
-        const bool last = only >= 0 || k + 1 == nc;
+        const bool last = !fork && (only >= 0 || k + 1 == nc);
+        cudaStream_t cs = fork ? b->side[k % nside] : b->st;
         cudaError_t e =
             c.graph ? sk::launch_graph(b->djobs, b->ditems + c.first_item, c.n_items, b->dqueue + k, steps, c.W,
                                        c.nw, c.per_chain, c.grid, static_cast<uint32_t>((c.cls - 512) / 4), c.graph,
-                                       static_cast<uint32_t>(b->runs.size()), last, b->st)
+                                       static_cast<uint32_t>(b->runs.size()), last, cs)
                     : sk::launch_step(b->djobs, b->ditems + c.first_item, c.n_items, b->dqueue + k, steps, c.W,
-                                      c.per_chain, c.grid, c.cls, static_cast<uint32_t>(b->runs.size()), last,
-                                      b->st);
+                                      c.per_chain, c.grid, c.cls, static_cast<uint32_t>(b->runs.size()), last, cs);
         if (e != cudaSuccess) return fail(SK_ERR_CUDA, "step launch: %s", cudaGetErrorString(e));
+    }
+    if (fork) {
+        for (uint32_t i = 0; i < nside; ++i) {
+            SK_CU(cudaEventRecord(b->ev_join[i], b->side[i]));
+            SK_CU(cudaStreamWaitEvent(b->st, b->ev_join[i], 0));
+        }
+        const cudaError_t e = sk::launch_bump_steps(b->djobs, static_cast<uint32_t>(b->runs.size()), steps, b->st);
+        if (e != cudaSuccess) return fail(SK_ERR_CUDA, "step counters: %s", cudaGetErrorString(e));
     }
     for (sk_run* r : b->runs) r->step = std::min<uint64_t>(r->step + steps, r->job.step_limit);
     return SK_OK;
@@ -1602,6 +1655,7 @@ sk_status mcmcmc_batch_free(sk_batch* b) {
     if (!b) return fail(SK_ERR_INVALID_ARG, "batch is NULL");
     cudaStreamSynchronize(b->st);
     if (b->graph) cudaGraphExecDestroy(b->graph);
+    free_side_streams(b);
     cudaFree(b->djobs);
     cudaFree(b->ditems);
     cudaFree(b->dqueue);

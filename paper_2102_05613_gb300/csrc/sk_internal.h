@@ -92,6 +92,9 @@ cudaError_t launch_step(const JobDev* jobs, const WorkItem* items, uint32_t n_it
                         uint32_t per_chain_bytes, uint32_t grid, int cls, uint32_t n_jobs,
                         bool bump, cudaStream_t st);
 int step_kernel_occupancy(int cls, uint32_t warps_per_cta, size_t per_chain_bytes);
+// Advances every job's step counter by nsteps (capped at its step limit):
+// what `bump` does, for launches whose classes ran on several streams.
+cudaError_t launch_bump_steps(const JobDev* jobs, uint32_t n_jobs, uint64_t nsteps, cudaStream_t st);
 // Start state: spins from `init` (device, chains x N) or the Philox start,
 // then (with_fields) h = J s on the CUDA cores (register-tiled fp32 / int32).
 cudaError_t launch_init(const JobDev* job, const int8_t* init, uint32_t chains, uint32_t N,

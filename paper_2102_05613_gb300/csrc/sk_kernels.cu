@@ -404,6 +404,10 @@ cudaError_t launch_step(const JobDev* jobs, const WorkItem* items, uint32_t n_it
     const int nb = 1 << ((cls >> 3) & 3), G = 1 << (cls & 7);
     e = launch_class(cls, nb, G, jobs, items, n_items, queue, ns, W, per_chain, grid, st);
     if (e != cudaSuccess || !bump) return e;
+    return launch_bump_steps(jobs, n_jobs, nsteps, st);
+}
+
+cudaError_t launch_bump_steps(const JobDev* jobs, uint32_t n_jobs, uint64_t nsteps, cudaStream_t st) {
     bump_steps<<<(n_jobs + 127) / 128, 128, 0, st>>>(jobs, n_jobs, nsteps);
     return cudaGetLastError();
 }
