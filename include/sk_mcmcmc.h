@@ -357,17 +357,19 @@ sk_status mcmcmc_batch_autotune(sk_batch* b, uint32_t trial_steps, uint32_t* war
  *   lanes    lanes per chain, 4, 8, 16 or 32 (32/lanes chains share a warp),
  *            raised to the fewest a class's K allows (each lane draws up to
  *            4 Philox blocks of 4 proposals: see below);
- *            0 = default (one block of 4 proposals per lane, whole warps for
- *            K > 128 and for classes of at most 512 chains).  Kernels exist
+ *            0 = default (whole-warp chains, 32 lanes); a value that
+ *            leaves no room for one warp's chains in a CTA's shared memory
+ *            is raised until they fit.  Kernels exist
  *            for 1 block per lane at every width, 2 blocks at 8, 16 and 32
  *            lanes and 4 blocks at 8 and 16 lanes, so K <= 16 allows 4
  *            lanes, K <= 128 8 lanes and K <= 256 16 lanes;
  *            Graph runs (trees and lines) take 64, 128, 256 or 512 lanes
  *            = 2, 4, 8 or 16 warps per chain (any smaller value: one warp);
  *            star classes clamp values above 32 to 32;
- *   staging  0 = default, 1 = the next step's row of J is staged in shared
- *            memory by TMA (two row buffers per chain), 2 = rows are read
- *            through L1 (no buffers, so more chains fit in shared memory).
+ *   staging  0 = default (rows through L1), 1 = the next step's row of J is
+ *            staged in shared memory by TMA (two row buffers per chain),
+ *            2 = rows are read through L1 (no buffers, so more chains fit in
+ *            shared memory).
  * Drops autotuned choices and a captured graph.  Results do not depend on it.
  */
 sk_status mcmcmc_batch_set_layout(sk_batch* b, uint32_t lanes, uint32_t staging);

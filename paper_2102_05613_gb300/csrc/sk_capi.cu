@@ -188,7 +188,7 @@ struct sk_batch {
     struct Class {
         uint64_t key;
         int cls;                 // kernel class incl. G and staging (step_class)
-        uint32_t G, gmin, gdef;  // lanes per chain: chosen, fewest allowed, default
+        uint32_t G, gmin;        // lanes per chain: chosen, fewest allowed
         uint32_t graph;          // 1 k-ary tree, 2 line: the graph kernel (one chain per warp); 0 the star
         uint32_t stage;          // row a staged by TMA (1) or read through L1 (0)
         uint32_t per_chain_staged, per_chain_direct;
@@ -1111,19 +1111,11 @@ uint32_t run_per_chain(const sk_run* r, bool staged = true) {
     return static_cast<uint32_t>((sk::warp_smem_bytes(r->inst->Npad, r->inst->kind, staged) + 127) / 128 * 128);
 }
 // Fewest lanes per chain a kernel covers for the run's K (NB up to 4 Philox
-// blocks per lane), and the default: one block per lane (K <= 4 G), whole
-// warps for K > 128.
+// blocks per lane).
 uint32_t run_gmin(const sk_run* r) {
     for (uint32_t g = 4; g < 32; g <<= 1)
         if (sk::blocks_per_lane(r->p.rule, r->p.K, g)) return g;
     return 32;
-}
-uint32_t run_gdefault(const sk_run* r) {
-    if (r->p.rule != SK_RULE_MCMCMC) return 4;
-    if (r->p.K > 128) return 32;
-    uint32_t g = 4;
-    while (4 * g < r->p.K) g <<= 1;
-    return g;
 }
 // Runs share a launch class when their kernels agree for every G: same
 // coupling type, rule, node-weighted records or not, Philox blocks of sites
@@ -1157,6 +1149,7 @@ uint32_t fit_warps(uint32_t per_chain, uint32_t G) {
 // the fewest lanes K allows (whole-warp chains for runs of few chains, where
 // latency matters) and as many warps as fit.  Uploads them.
 sk_status ensure_side_streams(sk_batch* b);
+void free_side_streams(sk_batch* b);
 
 sk_status plan_batch(sk_batch* b) {
     std::map<uint64_t, std::vector<uint32_t>> groups;  // key -> run indices (in order)
@@ -1174,16 +1167,13 @@ sk_status plan_batch(sk_batch* b) {
         c.key = g.first;
         const sk_run* r0 = b->runs[g.second[0]];
         c.gmin = run_gmin(r0);
-        c.gdef = run_gdefault(r0);
-        uint64_t total = 0;
         for (uint32_t i : g.second) {
             c.per_chain_staged = std::max(c.per_chain_staged, run_per_chain(b->runs[i], true));
             c.per_chain_direct = std::max(c.per_chain_direct, run_per_chain(b->runs[i], false));
-            total += b->runs[i]->chains;
         }
         if ((c.key >> 59) & 1u) {  // graph runs: a team of nw warps per chain, an even number of chains per CTA
             c.graph = r0->p.graph;
-            c.gmin = c.gdef = 32;
+            c.gmin = 32;
             c.stage = 0;
             c.per_chain = 0;
             for (uint32_t i : g.second)
@@ -1233,10 +1223,14 @@ sk_status plan_batch(sk_batch* b) {
             c.W = t->second & 0xFFu;
             c.per_chain = c.stage ? c.per_chain_staged : c.per_chain_direct;
         } else {
-            c.stage = (b->S_override == 2 || nw) ? 0u : 1u;
+            // untuned default: rows through L1 and whole-warp chains, the
+            // layout the autotuner picks for most classes; forced lanes that
+            // leave no room for one warp's chains are raised until they fit
+            c.stage = (b->S_override == 1 && !nw) ? 1u : 0u;
             c.per_chain = c.stage ? c.per_chain_staged : c.per_chain_direct;
-            c.G = b->G_override ? std::min(32u, std::max(b->G_override, c.gmin)) : (total <= 512 ? 32u : c.gdef);
-            const uint32_t fit = fit_warps(c.per_chain, c.G);
+            c.G = b->G_override ? std::min(32u, std::max(b->G_override, c.gmin)) : 32u;
+            uint32_t fit = fit_warps(c.per_chain, c.G);
+            while (c.G < 32 && fit < 1) fit = fit_warps(c.per_chain, c.G <<= 1);
             c.W = b->W_override ? std::min(b->W_override, fit) : fit;
         }
         if (c.W < 1 || (c.G == 32 && c.W < 2))
@@ -1310,6 +1304,7 @@ sk_status mcmcmc_batch_create(sk_run* const* runs, uint32_t n, uint32_t W, sk_ba
     }
     if (s == SK_OK) s = plan_batch(b);
     if (s != SK_OK) {
+        free_side_streams(b);
         cudaFree(b->djobs);
         cudaFree(b->ditems);
         cudaFree(b->dqueue);

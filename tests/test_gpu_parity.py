@@ -522,6 +522,47 @@ def test_few_warps_variant_gaussian_replay():
     b.close(); run.close(); inst.close()
 
 
+def test_large_n_many_chains_small_k_gets_a_layout():
+    # a large-N run forced to 4 lanes per chain with TMA-staged rows: 8
+    # chains per warp do not fit in one CTA's shared memory, so the plan
+    # gives each chain more lanes; +-J bit-exact against the oracle, and a
+    # Gaussian run's fields equal to J s of its final spins
+    torch = need_gpu()
+    st = torch.cuda.Stream()
+    N, chains, K, steps = 4500, 600, 8, 20
+    J = inputs.couplings_pm1(N, 620)
+    init = inputs.initial_spins(chains, N, 621)
+    inst = sk.Instance(J, stream=st)
+    run = sk.Run(inst, chains=chains, K=K, beta=1.0, seed=3, init=init)
+    b = sk.Batch([run])
+    b.set_layout(4, 1)
+    assert b.classes()[0][1] > 4
+    b.advance(steps)
+    b.close()
+    spins, h, step = run.state(fields=True)
+    assert step == steps
+    for c0 in (0, chains - 3):  # chains are independent: the oracle runs a few of them
+        o = oracle.run(J, K=K, beta=1.0, seed=3, chain0=c0, chains=3, init=init[c0:c0 + 3], steps=steps,
+                       want_q=False)
+        assert np.array_equal(spins[c0:c0 + 3], o["spins"]), c0
+    sub = np.r_[0:8, chains - 8:chains]
+    exact = (J.astype(np.float64) @ spins[sub].T.astype(np.float64)).T  # integers: exact in fp64
+    assert np.array_equal(h[sub], exact.astype(np.int32))
+    run.close(); inst.close()
+    Jg = inputs.couplings_gauss(3000, 622)
+    inst = sk.Instance(Jg, stream=st)
+    run = sk.Run(inst, chains=chains, rule=sk.SK_RULE_METROPOLIS, beta=1.0, seed=4)
+    b = sk.Batch([run])
+    b.set_layout(4, 1)
+    assert b.classes()[0][1] > 4
+    b.advance(steps)
+    b.close()
+    spins, h, _ = run.state(fields=True)
+    exact = (Jg.astype(np.float64) @ spins[sub].T.astype(np.float64)).T
+    assert np.abs(h[sub] - exact).max() < 1e-4
+    run.close(); inst.close()
+
+
 def test_largest_n():
     need_gpu()
     N, K, chains, steps = 8192, 64, 2, 60
