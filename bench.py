@@ -595,7 +595,9 @@ def _serve_once(rate, duration, pool, budget, quantum, seed):
             "offered_candidates_per_s": offered / duration,
             # saturated: the backlog outlives the arrival window by more than half of it
             "saturated": span > 1.5 * duration,
-            "device_busy_s": sstat["busy_seconds"], "quanta": sstat["quanta"]}
+            "device_busy_s": sstat["busy_seconds"], "quanta": sstat["quanta"],
+            "host_admit_s": sstat["admit_seconds"], "host_retire_s": sstat["retire_seconds"],
+            "host_plan_s": sstat["plan_seconds"]}
 
 
 def run_serve(args):

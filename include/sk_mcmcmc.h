@@ -511,6 +511,10 @@ typedef struct {
     uint64_t chain_steps, candidates, quanta, completed;
     double busy_seconds, elapsed_seconds;  /* device-busy and wall time              */
     uint64_t device_bytes_in_use, queued, running;
+    /* the worker's host time between quanta: admitting jobs (their device
+     * state and start fields), retiring them (read-back and release), and
+     * rebuilding the batch plan when the mix of jobs changed              */
+    double admit_seconds, retire_seconds, plan_seconds;
 } sk_server_stats_t;
 
 /*

@@ -646,11 +646,13 @@ sk_status sk_energy(const sk_instance* in, const int8_t* spins, uint32_t count, 
     } else if (mem != SK_MEM_DEVICE) {
         return fail(SK_ERR_INVALID_ARG, "mem must be SK_MEM_HOST or SK_MEM_DEVICE");
     }
-    if ((s = dalloc(&dE, count * sizeof(double))) != SK_OK) {
+    const size_t tiles = sk::energy_tiles(in->N, count);
+    if ((s = dalloc(&dE, count * (1 + tiles) * sizeof(double))) != SK_OK) {
         cudaFree(tmp);
         return s;
     }
-    cudaError_t e = sk::launch_energy(in->dJ, in->kind, in->N, in->Npad, in->scale, dsp, count, dE, in->st);
+    cudaError_t e = sk::launch_energy(in->dJ, in->kind, in->N, in->Npad, in->scale, dsp, count, dE, in->st,
+                                      tiles > 1 ? dE + count : nullptr);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out_E, dE, count * sizeof(double), cudaMemcpyDeviceToHost, in->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(in->st);
     cudaFree(tmp);

@@ -118,8 +118,14 @@ cudaError_t launch_start_batch(const StartJob* jobs_dev, uint32_t n, uint64_t ma
 cudaError_t launch_check_couplings(const void* J, uint32_t kind, uint32_t N, uint32_t Npad,
                                    unsigned long long* flag, cudaStream_t st);
 cudaError_t launch_check_spins(const int8_t* s, uint64_t n, unsigned long long* flag, cudaStream_t st);
+// E of `count` configurations (spins count x N, device) into out[count].
+// With `partial` (energy_tiles(N, count) * count doubles of scratch) the
+// columns of J are split over several CTAs per block of configurations;
+// without it one CTA covers all columns.
+uint32_t energy_tiles(uint32_t N, uint32_t count);
 cudaError_t launch_energy(const void* J, uint32_t kind, uint32_t N, uint32_t Npad, double scale,
-                          const int8_t* spins, uint32_t count, double* out, cudaStream_t st);
+                          const int8_t* spins, uint32_t count, double* out, cudaStream_t st,
+                          double* partial = nullptr);
 
 // MCMCMC on deeper graphs (sk_graph.cu): a team of nw warps per chain (1, 2,
 // 4, 8 or 16), W warps per CTA, i.e. W / nw chains (even; at most 14 when

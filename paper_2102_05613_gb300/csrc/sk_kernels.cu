@@ -308,29 +308,78 @@ __global__ void __maxnreg__(16) check_spins_kernel(const int8_t* __restrict__ s,
 }
 
 // E(s) = -scale sum_{i<j} J_ij s_i s_j = -scale/2 sum_i s_i sum_j J_ij s_j.
+// E(s) = -scale sum_{i<j} J_ij s_i s_j = -scale/2 sum_i s_i h_i with
+// h_i = sum_j J_ij s_j, for kEnergyChains configurations per CTA, so that each
+// coupling is read once per block of configurations rather than once per
+// configuration.  Bit c of sb[j] is set when configuration c has s_j = -1.
+// +-J: h_i summed in int32 (|h_i| <= N), exact; Gaussian: in double, the
+// terms in the order j = 0, 1, ...; the per-thread parts are reduced in a
+// fixed order, so results repeat bit for bit.  With gridDim.y > 1 the CTA
+// (x, y) takes the columns i = y B + t (mod gridDim.y B) and writes its part
+// to partial[c][y] (summed by energy_finish); configuration blocks vary
+// fastest in launch order, so the CTAs resident at a time share a few column
+// tiles of J in L2.
+constexpr uint32_t kEnergyChains = 8;
 template <typename JT>
-__global__ void energy_kernel(const JT* __restrict__ J, uint32_t N, uint32_t npad, double scale,
-                              const int8_t* __restrict__ spins, double* __restrict__ out) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    int8_t* s = reinterpret_cast<int8_t*>(sm);
-    __shared__ double red[32];
-    const uint32_t c = blockIdx.x;
-    for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) s[i] = spins[static_cast<size_t>(c) * N + i];
-    __syncthreads();
-    double part = 0.0;
-    for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) {
-        double hi = 0.0;
-        for (uint32_t j = 0; j < N; ++j) hi += static_cast<double>(J[static_cast<size_t>(j) * npad + i]) * s[j];
-        part += hi * s[i];
+__global__ void __launch_bounds__(256) energy_kernel(const JT* __restrict__ J, uint32_t N, uint32_t npad,
+                                                      double scale, const int8_t* __restrict__ spins,
+                                                      uint32_t count, double* __restrict__ out,
+                                                      double* __restrict__ partial) {
+    using A = typename std::conditional<sizeof(JT) == 1, int, double>::type;
+    constexpr uint32_t CB = kEnergyChains;
+    extern __shared__ __align__(16) unsigned char sb[];
+    __shared__ double red[CB][8];
+    const uint32_t c0 = blockIdx.x * CB;
+    const uint32_t nc = min(CB, count - c0);
+    for (uint32_t j = threadIdx.x; j < N; j += blockDim.x) {
+        uint32_t m = 0;
+        for (uint32_t c = 0; c < nc; ++c)
+            if (spins[static_cast<size_t>(c0 + c) * N + j] < 0) m |= 1u << c;
+        sb[j] = static_cast<unsigned char>(m);
     }
-    part = warp_sum(part);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
     __syncthreads();
-    if (threadIdx.x < 32) {
-        double v = threadIdx.x < blockDim.x / 32 ? red[threadIdx.x] : 0.0;
-        v = warp_sum(v);
-        if (threadIdx.x == 0) out[c] = -0.5 * scale * v;
+    double part[CB];
+#pragma unroll
+    for (uint32_t c = 0; c < CB; ++c) part[c] = 0.0;
+    for (uint32_t i = blockIdx.y * blockDim.x + threadIdx.x; i < N; i += gridDim.y * blockDim.x) {
+        A hi[CB];
+#pragma unroll
+        for (uint32_t c = 0; c < CB; ++c) hi[c] = A(0);
+#pragma unroll 4
+        for (uint32_t j = 0; j < N; ++j) {
+            const A v = static_cast<A>(J[static_cast<size_t>(j) * npad + i]);
+            const uint32_t m = sb[j];
+#pragma unroll
+            for (uint32_t c = 0; c < CB; ++c) hi[c] += ((m >> c) & 1u) ? -v : v;
+        }
+        const uint32_t mi = sb[i];
+#pragma unroll
+        for (uint32_t c = 0; c < CB; ++c) part[c] += static_cast<double>(((mi >> c) & 1u) ? -hi[c] : hi[c]);
     }
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (uint32_t c = 0; c < CB; ++c) {
+        const double v = warp_sum(part[c]);
+        if (lane == 0) red[c][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < nc) {
+        double v = 0.0;
+        for (uint32_t w = 0; w < blockDim.x / 32; ++w) v += red[threadIdx.x][w];
+        if (gridDim.y == 1)
+            out[c0 + threadIdx.x] = -0.5 * scale * v;
+        else
+            partial[static_cast<size_t>(c0 + threadIdx.x) * gridDim.y + blockIdx.y] = v;
+    }
+}
+
+__global__ void energy_finish(const double* __restrict__ partial, uint32_t tiles, uint32_t count, double scale,
+                              double* __restrict__ out) {
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= count) return;
+    double v = 0.0;
+    for (uint32_t y = 0; y < tiles; ++y) v += partial[static_cast<size_t>(c) * tiles + y];
+    out[c] = -0.5 * scale * v;
 }
 
 }  // namespace
@@ -460,13 +509,25 @@ cudaError_t launch_check_spins(const int8_t* s, uint64_t n, unsigned long long* 
     return cudaGetLastError();
 }
 
+uint32_t energy_tiles(uint32_t N, uint32_t count) {
+    // enough CTAs for two waves of 152 SMs, at most one column per thread
+    const uint32_t blocks = (count + kEnergyChains - 1) / kEnergyChains;
+    const uint32_t most = (N + 255) / 256;
+    return std::max(1u, std::min(most, (304u + blocks - 1) / blocks));
+}
+
 cudaError_t launch_energy(const void* J, uint32_t kind, uint32_t N, uint32_t Npad, double scale,
-                          const int8_t* spins, uint32_t count, double* out, cudaStream_t st) {
+                          const int8_t* spins, uint32_t count, double* out, cudaStream_t st, double* partial) {
     const size_t sm = (N + 15) / 16 * 16;
+    const uint32_t tiles = partial ? energy_tiles(N, count) : 1u;
+    const dim3 grid((count + kEnergyChains - 1) / kEnergyChains, tiles);
     if (kind == 0)
-        energy_kernel<int8_t><<<count, 256, sm, st>>>(static_cast<const int8_t*>(J), N, Npad, scale, spins, out);
+        energy_kernel<int8_t><<<grid, 256, sm, st>>>(static_cast<const int8_t*>(J), N, Npad, scale, spins, count,
+                                                     out, partial);
     else
-        energy_kernel<float><<<count, 256, sm, st>>>(static_cast<const float*>(J), N, Npad, scale, spins, out);
+        energy_kernel<float><<<grid, 256, sm, st>>>(static_cast<const float*>(J), N, Npad, scale, spins, count,
+                                                    out, partial);
+    if (tiles > 1) energy_finish<<<(count + 255) / 256, 256, 0, st>>>(partial, tiles, count, scale, out);
     return cudaGetLastError();
 }
 

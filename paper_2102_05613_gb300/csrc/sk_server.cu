@@ -86,7 +86,7 @@ struct sk_server {
     Clock::time_point t0;
     // counters
     uint64_t chain_steps = 0, candidates = 0, quanta = 0, completed = 0;
-    double busy_s = 0;
+    double busy_s = 0, admit_s = 0, retire_s = 0, plan_s = 0;
     sk_status fatal = SK_OK;
 };
 
@@ -221,6 +221,7 @@ void loop(sk_server* s) {
     bool dirty = true;
     for (;;) {
         // 1. retire finished jobs
+        const auto tr0 = Clock::now();
         std::vector<std::shared_ptr<Job>> still;
         for (auto& j : s->active) {
             if (sk::host_step(j->run) >= j->spec.steps) {
@@ -237,6 +238,7 @@ void loop(sk_server* s) {
         {
             std::lock_guard<std::mutex> lk(s->mu);
             s->active.swap(still);
+            s->retire_s += std::chrono::duration<double>(Clock::now() - tr0).count();
         }
         // 2. admit queued jobs that fit, first in first out
         {
@@ -257,8 +259,10 @@ void loop(sk_server* s) {
                     mcmcmc_batch_free(batch);
                     batch = nullptr;
                 }
+                const auto ta0 = Clock::now();
                 const sk_status r = admit(s, *j);
                 lk.lock();
+                s->admit_s += std::chrono::duration<double>(Clock::now() - ta0).count();
                 if (r != SK_OK) {
                     release(s, *j);
                     j->status.state = SK_JOB_FAILED;
@@ -277,6 +281,7 @@ void loop(sk_server* s) {
         if (s->active.empty()) continue;
         // 3. one quantum of every admitted job in one launch per kernel class
         if (dirty || !batch) {
+            const auto tp0 = Clock::now();
             if (batch) mcmcmc_batch_free(batch);
             batch = nullptr;
             std::vector<sk_run*> runs;
@@ -294,6 +299,8 @@ void loop(sk_server* s) {
                 break;
             }
             dirty = false;
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->plan_s += std::chrono::duration<double>(Clock::now() - tp0).count();
         }
         uint64_t cs = 0, cand = 0;
         for (auto& j : s->active) {
@@ -471,6 +478,9 @@ sk_status sk_server_stats(sk_server* s, sk_server_stats_t* out) {
     out->device_bytes_in_use = s->used;
     out->queued = s->queue.size();
     out->running = s->active.size();
+    out->admit_seconds = s->admit_s;
+    out->retire_seconds = s->retire_s;
+    out->plan_seconds = s->plan_s;
     return SK_OK;
 }
 

@@ -431,7 +431,8 @@ class ServerStats(C.Structure):
     _fields_ = [("chain_steps", C.c_uint64), ("candidates", C.c_uint64), ("quanta", C.c_uint64),
                 ("completed", C.c_uint64), ("busy_seconds", C.c_double),
                 ("elapsed_seconds", C.c_double), ("device_bytes_in_use", C.c_uint64),
-                ("queued", C.c_uint64), ("running", C.c_uint64)]
+                ("queued", C.c_uint64), ("running", C.c_uint64), ("admit_seconds", C.c_double),
+                ("retire_seconds", C.c_double), ("plan_seconds", C.c_double)]
 
 
 SK_JOB_QUEUED, SK_JOB_RUNNING, SK_JOB_DONE, SK_JOB_FAILED = range(4)

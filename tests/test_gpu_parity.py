@@ -288,19 +288,22 @@ def test_uniform_p_center_equals_uniform_root_and_limits():
     inst.close()
 
 
-def test_energy_entry_point():
+@pytest.mark.parametrize("N,count", [(200, 9), (1000, 20), (1500, 3)])
+def test_energy_entry_point(N, count):
+    # one CTA per block of 8 configurations (ragged last block); above 256
+    # spins the columns of J are split over several CTAs and summed after
     need_gpu()
-    for J in (inputs.couplings_pm1(200, 1), inputs.couplings_gauss(200, 2)):
-        S = inputs.initial_spins(9, 200, 3)
+    for J in (inputs.couplings_pm1(N, 1), inputs.couplings_gauss(N, 2)):
+        S = inputs.initial_spins(count, N, 3)
         inst = sk.Instance(J, scale=0.5)
         E = inst.energy(S)
         inst.close()
-        for c in range(9):
+        for c in range(count):
             want = oracle.energy(J, S[c], scale=0.5)
             if J.dtype == np.int8:
                 assert E[c] == want
             else:
-                assert abs(E[c] - want) <= 1e-9 * 200
+                assert abs(E[c] - want) <= 1e-9 * N
 
 
 def test_batch_equals_runs_alone():
