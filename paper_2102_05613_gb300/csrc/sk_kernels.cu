@@ -267,15 +267,18 @@ __global__ void __launch_bounds__(256) fields_kernel(const JT* __restrict__ J, c
     }
 }
 
+constexpr uint32_t kCheckThreads = 256;
 // Validation of host-supplied inputs on the device.  *flag (initialised to
 // all ones) receives the smallest (position << 2 | code) of a violation.
 //   couplings: code 1 diagonal entry != 0, 2 entry outside {-1,0,1} (+-J) or
 //   not finite (Gaussian), 3 J_ij != J_ji; position i * 2^16 + j.
-// The checks run on a side stream while the step kernel may hold most of
-// every SM (e.g. 768 threads x 80 registers): 16 registers per thread keep a
-// 256-thread CTA of them within the registers that leaves.
+// The checks run on an input stream of their own.  A CTA of 256 threads at
+// 24 registers (the fewest a thread is given) does not fit beside a step
+// kernel of 768 threads x 80 registers, so there they wait for its CTAs to
+// finish; 128-thread CTAs that do fit beside it slowed the step kernel by
+// more than the wait costs the end-to-end step.
 template <typename JT>
-__global__ void __maxnreg__(16) check_couplings_kernel(const JT* __restrict__ J, uint32_t N, uint32_t npad,
+__global__ void __maxnreg__(24) check_couplings_kernel(const JT* __restrict__ J, uint32_t N, uint32_t npad,
                                        unsigned long long* __restrict__ flag) {
     const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
@@ -298,7 +301,7 @@ __global__ void __maxnreg__(16) check_couplings_kernel(const JT* __restrict__ J,
 //   spins: code 1 for a value other than +-1; position = index.  A few CTAs
 //   per array (grid-stride loop), so that the check can run beside a
 //   resident step kernel without thousands of CTA launches.
-__global__ void __maxnreg__(16) check_spins_kernel(const int8_t* __restrict__ s, uint64_t n,
+__global__ void __maxnreg__(24) check_spins_kernel(const int8_t* __restrict__ s, uint64_t n,
                                                    unsigned long long* __restrict__ flag) {
     const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
     for (uint64_t x = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; x < n; x += stride) {
@@ -307,7 +310,6 @@ __global__ void __maxnreg__(16) check_spins_kernel(const int8_t* __restrict__ s,
     }
 }
 
-// E(s) = -scale sum_{i<j} J_ij s_i s_j = -scale/2 sum_i s_i sum_j J_ij s_j.
 // E(s) = -scale sum_{i<j} J_ij s_i s_j = -scale/2 sum_i s_i h_i with
 // h_i = sum_j J_ij s_j, for kEnergyChains configurations per CTA, so that each
 // coupling is read once per block of configurations rather than once per
@@ -493,11 +495,11 @@ cudaError_t launch_check_couplings(const void* J, uint32_t kind, uint32_t N, uin
                                    unsigned long long* flag, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(flag, 0xFF, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    const dim3 grid((N + 255) / 256, std::min<uint32_t>(N, 64));
+    const dim3 grid((N + kCheckThreads - 1) / kCheckThreads, std::min<uint32_t>(N, 64));
     if (kind == 0)
-        check_couplings_kernel<int8_t><<<grid, 256, 0, st>>>(static_cast<const int8_t*>(J), N, Npad, flag);
+        check_couplings_kernel<int8_t><<<grid, kCheckThreads, 0, st>>>(static_cast<const int8_t*>(J), N, Npad, flag);
     else
-        check_couplings_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float*>(J), N, Npad, flag);
+        check_couplings_kernel<float><<<grid, kCheckThreads, 0, st>>>(static_cast<const float*>(J), N, Npad, flag);
     return cudaGetLastError();
 }
 
@@ -505,7 +507,7 @@ cudaError_t launch_check_spins(const int8_t* s, uint64_t n, unsigned long long* 
     cudaError_t e = cudaMemsetAsync(flag, 0xFF, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
     const uint32_t blocks = static_cast<uint32_t>(std::min<uint64_t>((n + 4095) / 4096, 64));
-    if (blocks) check_spins_kernel<<<blocks, 256, 0, st>>>(s, n, flag);
+    if (blocks) check_spins_kernel<<<blocks, kCheckThreads, 0, st>>>(s, n, flag);
     return cudaGetLastError();
 }
 
