@@ -409,7 +409,7 @@ sk_status init_state(sk_run* r, const int8_t* spins, uint32_t mem) {
     const int8_t* dinit = nullptr;
     sk_status s = spins_stage(r, spins, mem, &cs, &dinit);
     if (s != SK_OK) return s;
-    if (cs) {
+    if (dinit) {  // spins given and checked on cs (which may be the legacy stream, 0)
         SK_CU(cudaStreamSynchronize(cs));
         if ((s = spins_verify(r)) != SK_OK) return s;
     }
@@ -825,12 +825,12 @@ sk_status mcmcmc_reset_many(sk_run* const* runs, uint32_t n, const int8_t* const
         sk_status s = spins_stage(runs[i], spins ? spins[i] : nullptr, mem, &used[i], &dinit[i]);
         if (s != SK_OK) return s;
     }
-    std::set<cudaStream_t> streams;
-    for (cudaStream_t cs : used)
-        if (cs) streams.insert(cs);
+    std::set<cudaStream_t> streams;  // where the checks ran (the legacy stream is 0)
+    for (uint32_t i = 0; i < n; ++i)
+        if (dinit[i]) streams.insert(used[i]);
     for (cudaStream_t cs : streams) SK_CU(cudaStreamSynchronize(cs));
     for (uint32_t i = 0; i < n; ++i) {
-        if (!used[i]) continue;
+        if (!dinit[i]) continue;
         sk_status s = spins_verify(runs[i]);
         if (s != SK_OK) return fail(s, "run %u: %s", i, g_err.c_str());
     }

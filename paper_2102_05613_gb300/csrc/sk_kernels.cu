@@ -272,13 +272,14 @@ constexpr uint32_t kCheckThreads = 256;
 // all ones) receives the smallest (position << 2 | code) of a violation.
 //   couplings: code 1 diagonal entry != 0, 2 entry outside {-1,0,1} (+-J) or
 //   not finite (Gaussian), 3 J_ij != J_ji; position i * 2^16 + j.
-// The checks run on an input stream of their own.  A CTA of 256 threads at
-// 24 registers (the fewest a thread is given) does not fit beside a step
-// kernel of 768 threads x 80 registers, so there they wait for its CTAs to
-// finish; 128-thread CTAs that do fit beside it slowed the step kernel by
-// more than the wait costs the end-to-end step.
+// The checks run on an input stream of their own while the step kernel may
+// hold most of every SM (768 threads x 80 registers leave 4096 of 65536
+// registers): at 16 registers per thread a 256-thread CTA of them fits in
+// what is left.  (ptxas reports raising the bound to 24, yet the kernels
+// launch with 16: at 24 they wait for the step kernel's CTAs and the
+// end-to-end bench step took 21.7 ms instead of 15.6 ms.)
 template <typename JT>
-__global__ void __maxnreg__(24) check_couplings_kernel(const JT* __restrict__ J, uint32_t N, uint32_t npad,
+__global__ void __maxnreg__(16) check_couplings_kernel(const JT* __restrict__ J, uint32_t N, uint32_t npad,
                                        unsigned long long* __restrict__ flag) {
     const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
@@ -301,7 +302,7 @@ __global__ void __maxnreg__(24) check_couplings_kernel(const JT* __restrict__ J,
 //   spins: code 1 for a value other than +-1; position = index.  A few CTAs
 //   per array (grid-stride loop), so that the check can run beside a
 //   resident step kernel without thousands of CTA launches.
-__global__ void __maxnreg__(24) check_spins_kernel(const int8_t* __restrict__ s, uint64_t n,
+__global__ void __maxnreg__(16) check_spins_kernel(const int8_t* __restrict__ s, uint64_t n,
                                                    unsigned long long* __restrict__ flag) {
     const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
     for (uint64_t x = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; x < n; x += stride) {

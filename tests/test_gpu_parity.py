@@ -425,6 +425,24 @@ def test_rejected_inputs_change_nothing():
     with pytest.raises(sk.SKError) as e:
         run.reset(badS)
     assert e.value.status == sk.SK_ERR_INVALID_ARG and str(2 * N + 17) in str(e.value)
+    # device spins at an address 3 bytes past a 16-byte boundary: the bytes
+    # before the first boundary, the 16-byte words and the ragged end are
+    # checked, and the first bad spin is the one reported
+    import torch
+    buf = torch.empty(chains * N + 8, dtype=torch.int8, device="cuda")
+    dev = buf[3:3 + chains * N]
+    for bad_at in ((190,), (5, 100), (100, 150), (12, 13), (176, 189)):
+        flat = init.reshape(-1).copy()
+        for x in bad_at:
+            flat[x] = 3
+        dev.copy_(torch.from_numpy(flat))
+        with pytest.raises(sk.SKError) as e:
+            run.reset(dev.view(chains, N))
+        assert e.value.status == sk.SK_ERR_INVALID_ARG and f"spin {min(bad_at)} " in str(e.value), str(e.value)
+        with pytest.raises(sk.SKError) as e:
+            sk.reset_many([run], [dev.view(chains, N)])
+        assert e.value.status == sk.SK_ERR_INVALID_ARG and f"spin {min(bad_at)} " in str(e.value), str(e.value)
+    torch.cuda.synchronize()
     run.advance(200)
     tr = run.trace()
     spins, h, step = run.state(fields=True)
