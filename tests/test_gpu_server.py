@@ -60,6 +60,10 @@ def test_results_in_the_mix_equal_results_alone():
         assert np.array_equal(E, E0), i
     st = srv.stats()
     assert st["completed"] == len(JOBS) and st["chain_steps"] > 0
+    # the worker's host time between quanta, by phase, within the wall time
+    phases = st["admit_seconds"] + st["retire_seconds"] + st["plan_seconds"]
+    assert min(st["admit_seconds"], st["retire_seconds"], st["plan_seconds"]) > 0
+    assert phases + st["busy_seconds"] <= st["elapsed_seconds"]
     # work overlapped: some job was admitted before another one finished
     starts = sorted((s["t_admit"], s["t_done"]) for s in status)
     assert any(b[0] < a[1] for a, b in zip(starts, starts[1:]))
