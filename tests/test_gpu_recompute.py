@@ -38,6 +38,29 @@ def _run(J, chains, steps, seed=3, K=16, beta=1.0, **kw):
     return inst, run, init
 
 
+@pytest.mark.parametrize("N,chains", [(100, 37), (300, 257)])
+def test_pm1_check_reports_stale_fields(N, chains):
+    # fields maintained under the old couplings, checked against new ones:
+    # the mismatch count, the largest field difference and the largest
+    # energy difference 0.5 |sum_n s_n (h_n - H_n)| equal the exact ones
+    need_gpu()
+    J = inputs.couplings_pm1(N, N + 1)
+    inst, run, _ = _run(J, chains, 200)
+    spins, h, _ = run.state(fields=True)
+    J2 = J.copy()
+    rng = np.random.default_rng(N)
+    for _ in range(7):  # a few symmetric sign flips of off-diagonal couplings
+        i, j = rng.choice(N, size=2, replace=False)
+        J2[i, j] = J2[j, i] = -J2[i, j]
+    inst.set_couplings(J2)
+    st, _ = run.recompute(sk.SK_RECOMPUTE_CHECK)
+    d = h.astype(np.int64) - (J2.astype(np.int64) @ spins.T.astype(np.int64)).T
+    assert st["mismatches"] == int(np.count_nonzero(d))
+    assert st["max_field_drift"] == float(np.abs(d).max())
+    assert st["max_energy_drift"] == float(np.abs(0.5 * (spins * d).sum(axis=1)).max())
+    run.close(); inst.close()
+
+
 @pytest.mark.parametrize("N,chains", [(64, 6), (100, 130), (300, 257), (2048, 300)])
 def test_pm1_recompute_is_exact(N, chains):
     need_gpu()
