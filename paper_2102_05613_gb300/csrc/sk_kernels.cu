@@ -311,17 +311,18 @@ __global__ void __maxnreg__(16) check_spins_kernel(const int8_t* __restrict__ s,
     }
 }
 
-// E(s) = -scale sum_{i<j} J_ij s_i s_j = -scale/2 sum_i s_i h_i with
-// h_i = sum_j J_ij s_j, for kEnergyChains configurations per CTA, so that each
-// coupling is read once per block of configurations rather than once per
-// configuration.  Bit c of sb[j] is set when configuration c has s_j = -1.
-// +-J: h_i summed in int32 (|h_i| <= N), exact; Gaussian: in double, the
-// terms in the order j = 0, 1, ...; the per-thread parts are reduced in a
-// fixed order, so results repeat bit for bit.  With gridDim.y > 1 the CTA
-// (x, y) takes the columns i = y B + t (mod gridDim.y B) and writes its part
-// to partial[c][y] (summed by energy_finish); configuration blocks vary
-// fastest in launch order, so the CTAs resident at a time share a few column
-// tiles of J in L2.
+// E(s) = -scale sum_i s_i g_i with g_i = sum_{j>i} J_ij s_j (the couplings
+// below the diagonal, read down column i), for kEnergyChains configurations
+// per CTA, so that each coupling is read once per block of configurations
+// rather than once per configuration.  A thread takes the column pair
+// (p, N-1-p), N-1 terms in all, so that threads and CTAs get equal work.
+// Bit c of sb[j] is set when configuration c has s_j = -1.  +-J: g_i summed
+// in int32 (|g_i| < N), exact; Gaussian: in double, the terms in the order
+// j = i+1, i+2, ...; the per-thread parts are reduced in a fixed order, so
+// results repeat bit for bit.  With gridDim.y > 1 the CTA (x, y) takes the
+// pairs p = y B + t (mod gridDim.y B) and writes its part to partial[c][y]
+// (summed by energy_finish); configuration blocks vary fastest in launch
+// order, so the CTAs resident at a time share a few column tiles of J in L2.
 constexpr uint32_t kEnergyChains = 8;
 template <typename JT>
 __global__ void __launch_bounds__(256) energy_kernel(const JT* __restrict__ J, uint32_t N, uint32_t npad,
@@ -344,20 +345,25 @@ __global__ void __launch_bounds__(256) energy_kernel(const JT* __restrict__ J, u
     double part[CB];
 #pragma unroll
     for (uint32_t c = 0; c < CB; ++c) part[c] = 0.0;
-    for (uint32_t i = blockIdx.y * blockDim.x + threadIdx.x; i < N; i += gridDim.y * blockDim.x) {
-        A hi[CB];
+    const uint32_t P = (N + 1) / 2;  // column pairs; the middle column of an odd N stands alone
+    for (uint32_t p = blockIdx.y * blockDim.x + threadIdx.x; p < P; p += gridDim.y * blockDim.x) {
+        for (uint32_t half = 0; half < 2; ++half) {
+            const uint32_t i = half ? N - 1 - p : p;
+            if (half && i == p) break;
+            A hi[CB];
 #pragma unroll
-        for (uint32_t c = 0; c < CB; ++c) hi[c] = A(0);
+            for (uint32_t c = 0; c < CB; ++c) hi[c] = A(0);
 #pragma unroll 4
-        for (uint32_t j = 0; j < N; ++j) {
-            const A v = static_cast<A>(J[static_cast<size_t>(j) * npad + i]);
-            const uint32_t m = sb[j];
+            for (uint32_t j = i + 1; j < N; ++j) {
+                const A v = static_cast<A>(J[static_cast<size_t>(j) * npad + i]);
+                const uint32_t m = sb[j];
 #pragma unroll
-            for (uint32_t c = 0; c < CB; ++c) hi[c] += ((m >> c) & 1u) ? -v : v;
+                for (uint32_t c = 0; c < CB; ++c) hi[c] += ((m >> c) & 1u) ? -v : v;
+            }
+            const uint32_t mi = sb[i];
+#pragma unroll
+            for (uint32_t c = 0; c < CB; ++c) part[c] += static_cast<double>(((mi >> c) & 1u) ? -hi[c] : hi[c]);
         }
-        const uint32_t mi = sb[i];
-#pragma unroll
-        for (uint32_t c = 0; c < CB; ++c) part[c] += static_cast<double>(((mi >> c) & 1u) ? -hi[c] : hi[c]);
     }
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -370,7 +376,7 @@ __global__ void __launch_bounds__(256) energy_kernel(const JT* __restrict__ J, u
         double v = 0.0;
         for (uint32_t w = 0; w < blockDim.x / 32; ++w) v += red[threadIdx.x][w];
         if (gridDim.y == 1)
-            out[c0 + threadIdx.x] = -0.5 * scale * v;
+            out[c0 + threadIdx.x] = -scale * v;
         else
             partial[static_cast<size_t>(c0 + threadIdx.x) * gridDim.y + blockIdx.y] = v;
     }
@@ -382,7 +388,7 @@ __global__ void energy_finish(const double* __restrict__ partial, uint32_t tiles
     if (c >= count) return;
     double v = 0.0;
     for (uint32_t y = 0; y < tiles; ++y) v += partial[static_cast<size_t>(c) * tiles + y];
-    out[c] = -0.5 * scale * v;
+    out[c] = -scale * v;
 }
 
 }  // namespace
@@ -513,9 +519,9 @@ cudaError_t launch_check_spins(const int8_t* s, uint64_t n, unsigned long long* 
 }
 
 uint32_t energy_tiles(uint32_t N, uint32_t count) {
-    // enough CTAs for two waves of 152 SMs, at most one column per thread
+    // enough CTAs for two waves of 152 SMs, at most one column pair per thread
     const uint32_t blocks = (count + kEnergyChains - 1) / kEnergyChains;
-    const uint32_t most = (N + 255) / 256;
+    const uint32_t most = ((N + 1) / 2 + 255) / 256;
     return std::max(1u, std::min(most, (304u + blocks - 1) / blocks));
 }
 
