@@ -412,25 +412,39 @@ TTT_FEW_CHAINS = (1, 152)
 
 
 def run_graph_one_chain(args):
-    """One chain of the binary tree of depth 7 (Gaussian N = 1024, beta = 1)
-    with 8 warps per chain, 500 steps in one launch: the graph kernel's
-    single-chain latency case (the case its ncu captures use)."""
+    """The binary tree of depth 7 (Gaussian N = 1024, beta = 1), 500 steps in
+    one launch: with one chain (8 warps per chain) the graph kernel's
+    latency case, with --graph-chains C its throughput case (the layout given
+    by --warps-per-cta / --lanes, else autotuned); the cases its ncu captures
+    use."""
     import torch
     from paper_2102_05613_gb300 import inputs, sk
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
+    C = args.graph_chains
     inst = sk.Instance(inputs.couplings_gauss(TTT_N, 0), stream=stream)
-    run = sk.Run(inst, chains=1, K=1, beta=TTT_BETA, seed=7, graph=sk.SK_GRAPH_TREE, arity=2, depth=7)
-    batch = sk.Batch([run], warps_per_cta=16)  # 8 warps per chain, two chains' room per CTA
-    batch.set_layout(lanes=256)
+    run = sk.Run(inst, chains=C, K=1, beta=TTT_BETA, seed=7, graph=sk.SK_GRAPH_TREE, arity=2, depth=7)
+    if C == 1:
+        batch = sk.Batch([run], warps_per_cta=16)  # 8 warps per chain, two chains' room per CTA
+        batch.set_layout(lanes=256)
+    elif args.warps_per_cta:
+        batch = sk.Batch([run], warps_per_cta=args.warps_per_cta)
+        batch.set_layout(lanes=args.lanes or 32)
+    else:
+        batch = sk.Batch([run])
+        batch.autotune(trial_steps=20)
+    if C > 1:
+        batch.advance(20)  # warm-up launch (the one-chain case times its first launch)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     a.record(stream)
     batch.advance(500)
     b.record(stream)
     torch.cuda.synchronize()
-    out = {"workload": "binary tree depth 7 (255 nodes), Gaussian SK N=1024, one chain, 8 warps per chain",
-           "us_per_step": 1e3 * a.elapsed_time(b) / 500, "launch_classes": batch.classes()}
+    ms = a.elapsed_time(b)
+    out = {"workload": f"binary tree depth 7 (255 nodes), Gaussian SK N=1024, {C} chain(s)",
+           "us_per_step": 1e3 * ms / 500, "chain_steps_per_s": C * 500 / (ms / 1e3),
+           "launch_classes": batch.classes()}
     batch.close()
     run.close()
     inst.close()
@@ -857,6 +871,8 @@ def main():
                     help="inverse temperature of the --ttt comparison (1 = T_c, the paper's setting)")
     ap.add_argument("--ttt-scale", type=int, default=1,
                     help="multiplies every --ttt method's steps (colder runs relax more slowly)")
+    ap.add_argument("--graph-chains", type=int, default=1,
+                    help="chains of the --graph-one-chain case (1: the latency case)")
     ap.add_argument("--graph-one-chain", action="store_true",
                     help="the graph kernel's single-chain latency case (binary tree, depth 7)")
     ap.add_argument("--ttt", action="store_true",
