@@ -63,6 +63,10 @@ def lib():
         L.sko_replay_graph.argtypes = [i, i, vp, d, i, i, i, i, d, u64, u32, u32, vp, u64, vp, d,
                                        vp, vp, vp, vp]
         L.sko_replay_graph.restype = C.c_longlong
+        L.sko_run_detail.argtypes = [i, i, vp, d, i, i, d, u64, u32, u32, vp, u64, d, vp, vp, vp]
+        L.sko_run_detail.restype = i
+        L.sko_run_graph_detail.argtypes = [i, i, vp, d, i, i, i, i, d, u64, u32, u32, vp, u64, vp, vp, vp]
+        L.sko_run_graph_detail.restype = i
         L.sko_transition_matrix_graph.argtypes = [i, i, vp, d, i, i, i, i, d, i, i, vp]
         L.sko_transition_matrix_graph.restype = i
         L.sko_setgen_bruteforce.argtypes = [i, vp, u32]
@@ -168,6 +172,25 @@ def replay(J, slots, *, rule=MCMCMC, K=8, beta=1.0, scale=1.0, seed=1, stream=0,
                 spins=fin, final_E=finE.value)
 
 
+def run_detail(J, *, rule=MCMCMC, K=8, beta=1.0, scale=1.0, seed=1, stream=0, chain=0, init=None,
+               steps=100, p_center=0.0):
+    """One chain's own trajectory with each step's choice, draw u and
+    inclusive prefix sums P of the slot weights (Metropolis: P = the
+    acceptance probability), see sko_run_detail."""
+    J = np.ascontiguousarray(J)
+    N = J.shape[0]
+    stride = 1 if rule == METROPOLIS else K + 1
+    own = np.zeros(steps, dtype=np.int32)
+    u = np.zeros(steps)
+    P = np.zeros((steps, stride))
+    init_a = None if init is None else np.ascontiguousarray(init, dtype=np.int8)
+    rc = lib().sko_run_detail(N, _kind_of(J), _ptr(J), scale, rule, K, beta, seed, stream, chain,
+                              _ptr(init_a), steps, float(p_center), _ptr(own), _ptr(u), _ptr(P))
+    if rc != 0:
+        raise RuntimeError(f"sko_run_detail failed with {rc}")
+    return dict(own=own, u=u, P=P)
+
+
 def boltzmann(J, beta, scale=1.0) -> np.ndarray:
     """Exact P_eq over all 2^N states (state bit i set <=> s_i = -1)."""
     J = np.ascontiguousarray(J)
@@ -241,6 +264,23 @@ def replay_graph(J, slots, *, graph=TREE, arity=2, depth=1, line_nodes=2, beta=1
         raise RuntimeError(f"sko_replay_graph failed with {bad}")
     return dict(bad=int(bad), disagree=int(dis.value), first_bad=int(first.value), spins=fin,
                 final_E=finE.value)
+
+
+def run_graph_detail(J, *, graph=TREE, arity=2, depth=1, line_nodes=2, beta=1.0, scale=1.0, seed=1,
+                     stream=0, chain=0, init=None, steps=100):
+    """run_detail on a graph: P has one column per node."""
+    J = np.ascontiguousarray(J)
+    N = J.shape[0]
+    V = graph_nodes(graph, arity, depth, line_nodes)
+    own = np.zeros(steps, dtype=np.int32)
+    u = np.zeros(steps)
+    P = np.zeros((steps, V))
+    init_a = None if init is None else np.ascontiguousarray(init, dtype=np.int8)
+    rc = lib().sko_run_graph_detail(N, _kind_of(J), _ptr(J), scale, graph, arity, depth, line_nodes, beta,
+                                    seed, stream, chain, _ptr(init_a), steps, _ptr(own), _ptr(u), _ptr(P))
+    if rc != 0:
+        raise RuntimeError(f"sko_run_graph_detail failed with {rc}")
+    return dict(own=own, u=u, P=P)
 
 
 def transition_matrix_graph(J, *, graph=TREE, arity=2, depth=1, line_nodes=2, beta=1.0, scale=1.0,

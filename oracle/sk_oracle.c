@@ -655,6 +655,42 @@ long long sko_replay_p(int N, int kind, const void* J, double scale, int rule, i
     return bad;
 }
 
+/*
+ * One chain's own trajectory together with what each step's choice is taken
+ * from, so that tests can place a replayed slot relative to the draw:
+ * own[t] = the slot the step chose (Metropolis: 1 accepted, 0 rejected),
+ * u[t] = its draw on the scale of the prefix sums, P[t * stride + j] = the
+ * inclusive prefix sums of the slot weights in slot order (stride K + 1;
+ * Metropolis: stride 1, P = the acceptance probability).  Returns 0 or a
+ * negative error as sko_run.
+ */
+int sko_run_detail(int N, int kind, const void* J, double scale, int rule, int K, double beta,
+                   uint64_t seed, uint32_t stream, uint32_t chain, const int8_t* init_spins,
+                   uint64_t nsteps, double p_center, int32_t* own, double* u, double* P) {
+    sko_ctx c;
+    int rc = ctx_init(&c, N, kind, J, scale, rule, K, beta, seed, stream, p_center);
+    if (rc) return rc;
+    const int stride = (rule == SKO_METROPOLIS) ? 1 : K + 1;
+    int8_t* s = (int8_t*)malloc((size_t)N);
+    double* h = (double*)malloc(sizeof(double) * (size_t)N);
+    if (!s || !h) { free(s); free(h); ctx_free(&c); return -2; }
+    if (init_spins) memcpy(s, init_spins, (size_t)N);
+    else sko_init_spins(seed, stream, chain, N, s);
+    sko_fields(N, kind, J, s, h);
+    double Pb[SKO_MAXSLOT_GUARD];
+    for (uint64_t t = 0; t < nsteps; ++t) {
+        int o = -1;
+        double uu = 0.0;
+        chain_step(&c, chain, t, s, h, -1, &o, Pb, &uu);
+        own[t] = o;
+        u[t] = uu;
+        memcpy(P + (size_t)t * (size_t)stride, Pb, sizeof(double) * (size_t)stride);
+    }
+    free(s); free(h);
+    ctx_free(&c);
+    return 0;
+}
+
 /* sko_replay_p with the uniform root. */
 long long sko_replay(int N, int kind, const void* J, double scale, int rule, int K, double beta,
                      uint64_t seed, uint32_t stream, uint32_t chain, const int8_t* init_spins,
@@ -1046,6 +1082,46 @@ int sko_run_graph(int N, int kind, const void* J, double scale, int graph_type, 
         }
         if (final_spins) memcpy(final_spins + (size_t)ci * N, s, (size_t)N);
         if (final_E) final_E[ci] = sko_energy(N, kind, J, scale, s);
+    }
+done:
+    free(s); free(s2); free(h); free(h2); free(site); free(dE); free(edges); free(down); free(xs);
+    ctx_free(&c);
+    graph_free(&g);
+    return rc;
+}
+
+/* One chain's own trajectory on a graph with each step's node choice, draw
+ * and inclusive prefix sums (P[t * V + v]), as sko_run_detail. */
+int sko_run_graph_detail(int N, int kind, const void* J, double scale, int graph_type, int arity, int depth,
+                         int line_nodes, double beta, uint64_t seed, uint32_t stream, uint32_t chain,
+                         const int8_t* init_spins, uint64_t nsteps, int32_t* own, double* u, double* P) {
+    sko_graph g;
+    int rc = graph_setup(&g, graph_type, arity, depth, line_nodes);
+    if (rc) return rc;
+    sko_ctx c;
+    rc = ctx_init(&c, N, kind, J, scale, SKO_MCMCMC, 1, beta, seed, stream, 0.0);
+    if (rc) { graph_free(&g); return rc; }
+    const int V = g.V;
+    int8_t* s = (int8_t*)malloc((size_t)N);
+    int8_t* s2 = (int8_t*)malloc((size_t)N);
+    double* h = (double*)malloc(sizeof(double) * (size_t)N);
+    double* h2 = (double*)malloc(sizeof(double) * (size_t)N);
+    uint32_t* site = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)V);
+    double* dE = (double*)malloc(sizeof(double) * (size_t)V);
+    int* edges = (int*)malloc(sizeof(int) * (size_t)V);
+    int* down = (int*)malloc(sizeof(int) * (size_t)V);
+    uint32_t* xs = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)V);
+    if (!s || !s2 || !h || !h2 || !site || !dE || !edges || !down || !xs) { rc = -2; goto done; }
+    if (init_spins) memcpy(s, init_spins, (size_t)N);
+    else sko_init_spins(seed, stream, chain, N, s);
+    sko_fields(N, kind, J, s, h);
+    for (uint64_t t = 0; t < nsteps; ++t) {
+        int o = -1;
+        double uu = 0.0;
+        graph_step(&c, &g, chain, t, s, h, -1, &o, P + (size_t)t * (size_t)V, &uu, site, dE, s2, h2, edges,
+                   down, xs);
+        own[t] = o;
+        u[t] = uu;
     }
 done:
     free(s); free(s2); free(h); free(h2); free(site); free(dE); free(edges); free(down); free(xs);
