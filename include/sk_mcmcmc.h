@@ -421,6 +421,9 @@ sk_status mcmcmc_batch_free(sk_batch* b);
  *   chains, K, rule, beta, seed, stream_id   as in sk_run_params;
  *   spins                device pointer, chains*N int8 +-1: the start state
  *                        on input, the state after `steps` steps on output;
+ *                        checked on the device first: a value other than +-1
+ *                        returns SK_ERR_INVALID_ARG naming its chain and site
+ *                        and leaves every buffer unchanged;
  *   energy               device pointer, chains doubles: E of the final states;
  *   stream               cudaStream_t (as void*) or NULL.
  * No records, traces or counters are kept.
@@ -438,8 +441,10 @@ sk_status mcmcmc_batch_free(sk_batch* b);
  * before any stream capture begins.  Every call reuses the same array, which
  * keeps the previous call's contents; the call clears what must start at
  * zero.  Calls that overlap on the GPU (from several host threads or
- * streams) race on the array: serialise them.  The call returns when its work
- * on `stream` has finished; a timed-out device wait gives SK_ERR_TIMEOUT.
+ * streams) race on the array: serialise them.  The call is synchronous: it
+ * waits on `stream` for the spin check, for its descriptor copies and for the
+ * final error word, and returns when all its work on `stream` has finished; a
+ * timed-out device wait gives SK_ERR_TIMEOUT.
  */
 sk_status mcmcmc_run_noalloc(uint32_t N, uint32_t kind, const void* couplings, double scale,
                              uint32_t chains, uint32_t K, uint32_t rule, double beta,

@@ -131,9 +131,22 @@ extern "C" sk_status mcmcmc_run_noalloc(uint32_t N, uint32_t kind, const void* c
     uint32_t* queue = reinterpret_cast<uint32_t*>(base + o_ctl);
     int* err = reinterpret_cast<int*>(base + o_ctl + 4);
     uint64_t* step = reinterpret_cast<uint64_t*>(base + o_ctl + 8);
+    unsigned long long* bad_spin = reinterpret_cast<unsigned long long*>(base + o_ctl + 16);
 
     // the array keeps the previous call's contents: clear what starts at zero
     NA_CU(cudaMemsetAsync(base + o_ctl, 0, 256, st));
+
+    // the start spins must be +-1: the first offending index is recorded in
+    // the control block (the check sets its word to all ones first)
+    {
+        NA_CU(sk::launch_check_spins(spins, static_cast<uint64_t>(chains) * N, bad_spin, st));
+        unsigned long long hbad = 0;
+        NA_CU(cudaMemcpyAsync(&hbad, bad_spin, sizeof hbad, cudaMemcpyDeviceToHost, st));
+        NA_CU(cudaStreamSynchronize(st));
+        if (hbad != ~0ull)
+            return nfail(SK_ERR_INVALID_ARG, "start spin %llu (chain %llu, site %llu) is not +-1", hbad >> 2,
+                         (hbad >> 2) / N, (hbad >> 2) % N);
+    }
     NA_CU(cudaMemsetAsync(base + o_J, 0, static_cast<size_t>(Npad) * Npad * bj, st));
     NA_CU(cudaMemcpy2DAsync(base + o_J, Npad * bj, couplings, N * bj, N * bj, N,
                             cudaMemcpyDeviceToDevice, st));

@@ -401,10 +401,38 @@ def run_noalloc(couplings, spins, energy, *, scale=1.0, K=8, rule=SK_RULE_MCMCMC
                 seed=1, stream_id=0, steps=0, stream=None):
     """mcmcmc_run_noalloc: device couplings (N x N torch tensor, int8 or
     float32), device spins (chains x N int8, updated in place) and a device
-    float64 energy vector (chains), all owned by the caller."""
+    float64 energy vector (chains), all owned by the caller.  The buffers are
+    checked here (type, shape, contiguity, one CUDA device) before the C call,
+    which trusts the pointers it is given: TypeError or ValueError otherwise."""
+    for name, t in (("couplings", couplings), ("spins", spins), ("energy", energy)):
+        if not all(hasattr(t, a) for a in ("data_ptr", "dtype", "shape", "is_contiguous", "device")):
+            raise TypeError(f"{name} must be a torch tensor")
+    kinds = {"torch.int8": SK_J_PM1, "torch.float32": SK_J_GAUSS}
+    if str(couplings.dtype) not in kinds:
+        raise TypeError("couplings must be int8 (+-J) or float32 (Gaussian)")
+    if str(spins.dtype) != "torch.int8":
+        raise TypeError("spins must be int8")
+    if str(energy.dtype) != "torch.float64":
+        raise TypeError("energy must be float64")
+    if couplings.dim() != 2 or couplings.shape[0] != couplings.shape[1]:
+        raise ValueError(f"couplings must be a square matrix, got shape {tuple(couplings.shape)}")
     N = int(couplings.shape[0])
-    kind = SK_J_PM1 if str(couplings.dtype) == "torch.int8" else SK_J_GAUSS
+    if spins.dim() != 2 or spins.shape[1] != N or spins.shape[0] < 1:
+        raise ValueError(f"spins must have shape (chains, {N}), got {tuple(spins.shape)}")
     chains = int(spins.shape[0])
+    if energy.numel() != chains:
+        raise ValueError(f"energy must hold {chains} values, got {energy.numel()}")
+    for name, t in (("couplings", couplings), ("spins", spins), ("energy", energy)):
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    devs = {str(t.device) for t in (couplings, spins, energy)}
+    if any(not t.is_cuda for t in (couplings, spins, energy)) or len(devs) != 1:
+        raise ValueError(f"couplings, spins and energy must be on one CUDA device, got {sorted(devs)}")
+    import torch
+    if couplings.device.index != torch.cuda.current_device():
+        raise ValueError(f"the buffers are on {couplings.device}, the current device is "
+                         f"cuda:{torch.cuda.current_device()}")
+    kind = kinds[str(couplings.dtype)]
     _check(lib().mcmcmc_run_noalloc(N, kind, C.c_void_p(couplings.data_ptr()), float(scale), chains,
                                     int(K), int(rule), float(beta), int(seed), int(stream_id),
                                     int(steps), C.c_void_p(spins.data_ptr()),
