@@ -1,12 +1,15 @@
 """The continuous-batching request server: jobs of different N, couplings,
 K, beta, rule and length that arrive while others run are admitted by device
 footprint, share launches, and each result equals the same job run alone
-(bit for bit: the draws are counter-based and every kernel is deterministic)."""
+(bit for bit: the draws are counter-based and every kernel is deterministic).
+The +-J jobs' results also equal the FP64 oracle's trajectories bit for bit,
+and every job's energies equal the oracle's energies of its final spins."""
 import time
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_2102_05613_gb300 import inputs, sk
 
 from gpu_util import need_gpu
@@ -58,6 +61,14 @@ def test_results_in_the_mix_equal_results_alone():
         E0, S0 = _alone(J, N, chains, K, rule, beta, steps, seed, i, init, P_CENTER.get(i, 0.0))
         assert np.array_equal(S, S0), i
         assert np.array_equal(E, E0), i
+        # the job's energies are the FP64 energies of its spins (exact for +-J)
+        Eo = np.array([oracle.energy(J, S[c]) for c in range(chains)])
+        assert np.abs(E - Eo).max() <= (0.0 if kind == sk.SK_J_PM1 else 1e-9 * N), i
+        if kind == sk.SK_J_PM1:  # the oracle's trajectory, bit for bit
+            orule = oracle.METROPOLIS if rule == sk.SK_RULE_METROPOLIS else oracle.MCMCMC
+            o = oracle.run(J, rule=orule, K=K, beta=beta, seed=seed, stream=i, chains=chains,
+                           init=init, steps=steps, p_center=P_CENTER.get(i, 0.0))
+            assert np.array_equal(S, o["spins"]), i
     st = srv.stats()
     assert st["completed"] == len(JOBS) and st["chain_steps"] > 0
     # the worker's host time between quanta, by phase, within the wall time
