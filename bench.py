@@ -187,7 +187,7 @@ def run_reference(args):
 RC_N, RC_CHAINS, RC_ITERS = 2048, 8192, 20
 
 
-def recompute_report(stream, peaks):
+def recompute_report(stream, peaks, fp8_measured=None):
     """Times mcmcmc_recompute on +-J (FP8 e4m3, check) and Gaussian (bf16 x3,
     resync) couplings with N = 2048 and 8192 chains, and states the error of
     each recompute format against the FP64 product on 64 chains."""
@@ -217,11 +217,14 @@ def recompute_report(stream, peaks):
         ms = statistics.median(a.elapsed_time(b) for a, b in ev)
         # executed flops: one product for FP8, three (one per bf16 term) for the split
         exec_flops = out["flops_per_recompute"] * (1 if kind == sk.SK_J_PM1 else 3)
-        peak = bf16_peak * (2.0 if kind == sk.SK_J_PM1 else 1.0)
+        if kind == sk.SK_J_PM1:
+            peak = fp8_measured or bf16_peak * 2.0
+            src = ("measured this run: cuBLASLt e4m3 GEMM 8192^3" if fp8_measured
+                   else "measured bf16 x 2 (nominal fp8/bf16 ratio)")
+        else:
+            peak, src = bf16_peak, "measured bf16 (MEASURED_PEAKS.json)"
         ent = {"ms": ms, "algorithmic_tflops": out["flops_per_recompute"] / ms / 1e9,
-               "executed_tflops": exec_flops / ms / 1e9, "peak_tflops": peak,
-               "peak_source": ("measured bf16 x 2 (nominal fp8/bf16 ratio)" if kind == sk.SK_J_PM1
-                               else "measured bf16"),
+               "executed_tflops": exec_flops / ms / 1e9, "peak_tflops": peak, "peak_source": src,
                "frac_executed": exec_flops / ms / 1e9 / peak,
                "check": st}
         # error of each format against the FP64 product on the first 64 chains
@@ -301,31 +304,34 @@ def setgen_report(stream, n=24):
 TTT_N, TTT_CHAINS, TTT_BETA = 1024, 4096, 1.0
 # name, rule, K, steps, graph (the graphs of Fig. fig_sk: the 2^7 line, the
 # binary tree of depth 7, the ternary of depth 5, the 16-ary of depth 3)
-TTT_METHODS = [("metropolis", 1, 1, 1 << 23, {}), ("mcmcmc_k32", 0, 32, 1 << 21, {}),
-               ("mcmcmc_k128", 0, 128, 1 << 20, {}),
+TTT_METHODS = [("metropolis", 1, 1, 1 << 23, {}),
+               ("mcmcmc_k2", 0, 2, 1 << 23, {}), ("mcmcmc_k4", 0, 4, 1 << 22, {}),
+               ("mcmcmc_k8", 0, 8, 1 << 22, {}), ("mcmcmc_k16", 0, 16, 1 << 21, {}),
+               ("mcmcmc_k32", 0, 32, 1 << 21, {}), ("mcmcmc_k128", 0, 128, 1 << 20, {}),
                ("line_128", 0, 1, 1 << 16, dict(graph=2, line_nodes=128)),
                ("tree2_d7", 0, 1, 1 << 15, dict(graph=1, arity=2, depth=7)),
                ("tree3_d5", 0, 1, 1 << 14, dict(graph=1, arity=3, depth=5)),
                ("tree16_d3", 0, 1, 1 << 13, dict(graph=1, arity=16, depth=3))]
+# the default bench line: Metropolis against the star at every K of the sweep
+TTT_LINE_METHODS = ("metropolis", "mcmcmc_k2", "mcmcmc_k4", "mcmcmc_k8", "mcmcmc_k16", "mcmcmc_k32",
+                    "mcmcmc_k128")
 TTT_EPS = (1e-2, 3e-3, 1e-3)
 
 
-def run_ttt(args):
+def ttt_measure(only, beta, scale):
     """e(t) = chain-mean E/N every T/2048 steps from a random start; e_inf and
     sigma_inf (one record's equilibrium fluctuation) from the last half of the
     K=128 run; t_therm(eps) = the first record after which
     |e - e_inf| <= eps + 3 sigma_inf holds for good; wall-clock = t_therm x
-    the method's measured seconds per step."""
+    the method's measured seconds per step (4096 chains, autotuned layout), and
+    the same for 1 and 152 chains (few_chains)."""
     import numpy as np
     import torch
     from paper_2102_05613_gb300 import inputs, sk
-    torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     J = inputs.couplings_gauss(TTT_N, 0)
     inst = sk.Instance(J, stream=stream)
     curves = {}
-    only = set(args.ttt_methods.split(",")) if args.ttt_methods else None
-    beta, scale = args.ttt_beta, args.ttt_scale
     for name, rule, Kt, T, gkw in TTT_METHODS:
         if only and name not in only and name != "mcmcmc_k128":
             continue
@@ -403,8 +409,24 @@ def run_ttt(args):
     out["wallclock_speedup_vs_metropolis"] = sp
     out["mc_step_ratio_vs_metropolis"] = ss
     out["few_chains"] = ttt_few_chains(inst, out["methods"], only, beta)
+    # the best MCMCMC variant at each chain count and accuracy (wall-clock)
+    best = {}
+    for label, table in [(str(TTT_CHAINS), sp)] + [(c, v["wallclock_speedup_vs_metropolis"])
+                                                    for c, v in out["few_chains"].items()]:
+        best[label] = {}
+        for eps in TTT_EPS:
+            cand = [(v[str(eps)], n) for n, v in table.items() if isinstance(v.get(str(eps)), float)]
+            best[label][str(eps)] = None if not cand else {"method": max(cand)[1], "speedup": max(cand)[0]}
+    out["best_wallclock_speedup_vs_metropolis"] = best
     inst.close()
-    print(json.dumps(out), flush=True)
+    return out
+
+
+def run_ttt(args):
+    import torch
+    torch.cuda.set_device(0)
+    only = set(args.ttt_methods.split(",")) if args.ttt_methods else None
+    print(json.dumps(ttt_measure(only, args.ttt_beta, args.ttt_scale)), flush=True)
     return 0
 
 
@@ -639,6 +661,95 @@ def run_serve(args):
 
 
 # ---------------------------------------------------------------------------
+# measured ceilings: L2 and shared-memory bandwidth (the library's probes,
+# sk_peaks.h) and the FP8 tensor-core rate (a cuBLASLt FP8 GEMM, timed the
+# way the driver times the bf16 one), each best of several launches
+# ---------------------------------------------------------------------------
+def measure_peaks(stream):
+    import torch
+    from paper_2102_05613_gb300 import sk
+    out = {}
+    out["l2_read_gbps"] = max(sk.peak_l2_read(48 << 20, passes=64, reps=3, stream=stream) for _ in range(3))
+    out["smem_vec16_gbps"] = max(sk.peak_smem(sk.SK_PEAK_SMEM_VEC16, iters=1024, reps=3, stream=stream)
+                                 for _ in range(3))
+    out["smem_gather4_gbps"] = max(sk.peak_smem(sk.SK_PEAK_SMEM_GATHER4, iters=1024, reps=3, stream=stream)
+                                   for _ in range(3))
+    out["how"] = ("L2: 48 MiB resident working set, 16-byte ld.global.cg loads, 4 CTAs x 512 threads "
+                  "per SM, 64 sweeps per launch; shared memory: 64 KiB per CTA, 2 CTAs x 1024 threads "
+                  "per SM, 16 loads in flight per thread, conflict-free 16-byte loads (a warp reads 512 "
+                  "contiguous bytes) and random 4-byte gathers (useful bytes); best of 3 x 3 launches, "
+                  "CUDA events")
+    try:
+        M = 8192
+        a = torch.randn(M, M, device="cuda").to(torch.float8_e4m3fn)
+        b = torch.randn(M, M, device="cuda").to(torch.float8_e4m3fn).t()
+        one = torch.ones((), device="cuda")
+        for _ in range(3):
+            torch._scaled_mm(a, b, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)
+        best = float("inf")
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch._scaled_mm(a, b, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        out["fp8_tflops"] = 2.0 * M ** 3 / (best * 1e-3) / 1e12
+        out["fp8_how"] = "torch._scaled_mm e4m3 8192^3 (cuBLASLt), best of 10, CUDA events"
+        del a, b
+    except Exception as e:  # noqa: BLE001 -- reported, and the nominal ratio is used instead
+        out["fp8_tflops"] = None
+        out["fp8_how"] = f"unavailable ({type(e).__name__}: {e})"
+    return out
+
+
+# ---------------------------------------------------------------------------
+# BASELINE config 2 in full: beta in {0.5, 1, 2, 3} x K in {1 (Metropolis),
+# 32, 128}, 64 instances x 4096 chains, 1e4 steps, records every 100
+# ---------------------------------------------------------------------------
+SWEEP_BETAS, SWEEP_KS, SWEEP_STEPS = (0.5, 1.0, 2.0, 3.0), (1, 32, 128), 10_000
+
+
+def config2_sweep(stream, insts):
+    import torch
+    from paper_2102_05613_gb300 import sk
+    res = []
+    for Kc in SWEEP_KS:
+        rule = sk.SK_RULE_METROPOLIS if Kc == 1 else sk.SK_RULE_MCMCMC
+        geometry = None
+        for beta in SWEEP_BETAS:
+            runs = [sk.Run(inst, chains=CHAINS, K=Kc, rule=rule, beta=beta, seed=3, stream_id=i,
+                           record_every=R, max_records=SWEEP_STEPS // R) for i, inst in enumerate(insts)]
+            if geometry is None:
+                batch = sk.Batch(runs)
+                batch.autotune(trial_steps=10)
+                geometry = batch.classes()
+            else:  # the layout tuned at the first beta (it does not depend on beta)
+                batch = sk.Batch(runs, warps_per_cta=geometry[0][3])
+                batch.set_layout(geometry[0][1], 1 if (geometry[0][0] >> 5) & 3 == 1 else 2)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            for _ in range(SWEEP_STEPS // R):
+                batch.advance(R)
+            b.record(stream)
+            torch.cuda.synchronize()
+            s_ = a.elapsed_time(b) / 1e3
+            E, _, acc = runs[0].observables()
+            cs = len(insts) * CHAINS * SWEEP_STEPS
+            res.append({"rule": "metropolis" if Kc == 1 else "mcmcmc", "K": Kc, "beta": beta,
+                        "seconds": s_, "mc_steps_per_s": cs / s_, "candidate_configs_per_s": cs * Kc / s_,
+                        "acceptance": float(acc[-10:].mean()) / R,
+                        "e_final_instance0": float(E[-1].mean()) / N, "launch_classes": geometry})
+            batch.close()
+            for r_ in runs:
+                r_.close()
+    return {"workload": f"gaussian-sk N={N}, {len(insts)} instances x {CHAINS} chains, {SWEEP_STEPS} steps "
+                        f"from the Philox random start, records every {R} steps; Metropolis is K = 1",
+            "runs": res}
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def run_ours(args):
@@ -700,59 +811,72 @@ def run_ours(args):
     value = world * chain_steps_rank * K / T
     mc_steps = world * chain_steps_rank / T
 
-    # ALU roofline of the step kernel.  Algorithmic lane-operations of one
-    # chain-step (MCMCMC, K proposals, N spins, f = measured spins flipped per
-    # step, r = J rows the steps needed):
-    #   Philox4x32-10 draws  (ceil(K/4) + 1/32) blocks x 84  (10 rounds x 8 ops
-    #                         + 4 range reductions)
-    #   candidate energies    4 K
-    #   min + weights         4 (K + 1)   (compare, subtract, scale, 2^x)
-    #   prefix sum + choice   2 (K + 1)
-    #   field update          f N          (one FMA per spin per flipped spin)
-    # against 152 SMs x 128 lanes x the maximum SM clock.
+    # Roofline of the step kernel (the batched step is bound by the memory
+    # level that holds J and the chains' state).  Algorithmic bytes of one
+    # chain-step, from the kernel's counters (r = J rows the steps needed, f =
+    # spins flipped per step):
+    #   J rows               r N b_J          (from L2, through L1)
+    #   proposal gathers     K (b_s + b_h)    (shared memory)
+    #   field update         2 f N b_h        (shared-memory read-modify-write)
+    # All three pass the SM's L1 / shared-memory data path: their sum against
+    # the measured conflict-free shared-memory bandwidth is the headline
+    # fraction; the J-row bytes against the measured L2 read bandwidth and the
+    # lane-operation count against the ALU peak are reported beside it.
     flips = sum(b[0] - a[0] for a, b in zip(c0, c1))
     rows = sum(b[1] - a[1] for a, b in zip(c0, c1))
     cs = INSTANCES * CHAINS * R * args.steps
     rows_ps, flips_ps = rows / cs, flips / cs
-    ops_ps = (math.ceil(K / 4) + 1 / 32) * 84 + 4 * K + 6 * (K + 1) + flips_ps * N
-    ops_launch = ops_ps * INSTANCES * CHAINS * R
+    bJ, bs, bh = 4, 1, 4
+    bytes_J = rows_ps * N * bJ
+    bytes_gather = K * (bs + bh)
+    bytes_update = 2 * flips_ps * N * bh
+    bytes_ps = bytes_J + bytes_gather + bytes_update
     mean_launch_s = statistics.mean(launch_ms) / 1e3
+    cs_launch = INSTANCES * CHAINS * R
     peaks = {}
     pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk_path):
         peaks = json.load(open(pk_path))
+    mp = measure_peaks(stream) if rank == 0 else {}
     sm_clock = peaks.get("sm_max_mhz") or 2070.0
     sms = torch.cuda.get_device_properties(local).multi_processor_count
-    alu_peak = sms * 128 * sm_clock * 1e6 / 1e12  # T lane-ops/s
-    achieved = ops_launch / mean_launch_s / 1e12
     # DRAM bytes of one launch: ncu capture of the 16-instance case at the
-    # profiled layout (class 268: 16 lanes x 2 blocks, rows through L1, 24
-    # warps), 295.8 MB, scaled by the chains processed (the state streamed once
+    # profiled layout, scaled by the chains processed (the state streamed once
     # per launch grows in proportion); null for any other layout
     profiled = [268, 16, 3072, 24]
     traffic = (4 * 295.8e6 * INSTANCES / 64 if N == 512 and info["classes"]
                and list(info["classes"][0][:4]) == profiled else None)
-    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
-                "frac": achieved / alu_peak, "traffic": traffic,
-                "peak_source": f"{sms} SMs x 128 lanes x {sm_clock:.0f} MHz (max SM clock, "
-                               f"MEASURED_PEAKS.json)",
-                "kernel": "step_kernel", "ops_per_chain_step": ops_ps,
-                "J_rows_per_chain_step": rows_ps, "flips_per_chain_step": flips_ps,
-                "J_bytes_per_chain_step": rows_ps * N * 4,
-                "mean_launch_ms": 1e3 * mean_launch_s}
-    # second line: the bytes one chain-step moves through the SM's L1 /
-    # shared-memory data path, r N b_J (J rows, from L2 through L1) + K (b_s +
-    # b_h) (spin and field gathers at the proposal sites) + 2 f N b_h (the
-    # field read-modify-write of each flipped spin), against that path's
-    # nominal 128 bytes per clock per SM
-    l1_bytes = rows_ps * N * 4 + K * (1 + 4) + 2 * flips_ps * N * 4
-    l1_peak = sms * 128 * sm_clock * 1e6 / 1e9  # GB/s
-    l1_achieved = l1_bytes * INSTANCES * CHAINS * R / mean_launch_s / 1e9
-    roofline["l1_data_path"] = {"achieved": l1_achieved, "peak": l1_peak, "unit": "GB/s",
-                                "frac": l1_achieved / l1_peak, "bytes_per_chain_step": l1_bytes,
-                                "J_GBps": rows_ps * N * 4 * INSTANCES * CHAINS * R / mean_launch_s / 1e9,
-                                "peak_source": f"nominal 128 B per clock per SM x {sms} SMs x "
-                                               f"{sm_clock:.0f} MHz"}
+    smem_peak = mp.get("smem_vec16_gbps")
+    achieved = bytes_ps * cs_launch / mean_launch_s / 1e9
+    roofline = {"bound": "smem", "achieved": achieved, "peak": smem_peak, "unit": "GB/s",
+                "frac": (achieved / smem_peak) if smem_peak else None, "traffic": traffic,
+                "peak_source": "measured this run: conflict-free 16-byte shared-memory loads (sk_peak_smem)",
+                "kernel": "step_kernel", "mean_launch_ms": 1e3 * mean_launch_s,
+                "chain_steps_per_launch": cs_launch,
+                "bytes_per_chain_step": bytes_ps,
+                "terms": {"J_rows_r_N_bJ": bytes_J, "gathers_K_bs_bh": bytes_gather,
+                          "field_update_2fN_bh": bytes_update},
+                "J_rows_per_chain_step": rows_ps, "flips_per_chain_step": flips_ps}
+    l2_peak = mp.get("l2_read_gbps")
+    l2_ach = bytes_J * cs_launch / mean_launch_s / 1e9
+    roofline["l2"] = {"achieved": l2_ach, "peak": l2_peak, "unit": "GB/s",
+                      "frac": (l2_ach / l2_peak) if l2_peak else None, "bytes_per_chain_step": bytes_J,
+                      "peak_source": "measured this run: 48 MiB resident, ld.global.cg (sk_peak_l2_read)"}
+    g4 = mp.get("smem_gather4_gbps")
+    g_ach = bytes_gather * cs_launch / mean_launch_s / 1e9
+    roofline["gathers_vs_random_gather_peak"] = {
+        "achieved": g_ach, "peak": g4, "unit": "GB/s", "frac": (g_ach / g4) if g4 else None,
+        "note": "the proposal gathers alone against random 4-byte shared-memory gathers"}
+    # lane operations (MCMCMC): Philox (ceil(K/4) + 1/32) blocks x 84 (10 rounds
+    # x 8 ops + 4 range reductions), candidate energies 4 K, min + weights
+    # 4 (K + 1), prefix + choice 2 (K + 1), field update f N, against 152 SMs x
+    # 128 lanes x the maximum SM clock
+    ops_ps = (math.ceil(K / 4) + 1 / 32) * 84 + 4 * K + 6 * (K + 1) + flips_ps * N
+    alu_peak = sms * 128 * sm_clock * 1e6 / 1e12
+    alu_ach = ops_ps * cs_launch / mean_launch_s / 1e12
+    roofline["alu"] = {"achieved": alu_ach, "peak": alu_peak, "unit": "Tops/s", "frac": alu_ach / alu_peak,
+                       "ops_per_chain_step": ops_ps,
+                       "peak_source": f"{sms} SMs x 128 lanes x {sm_clock:.0f} MHz"}
 
     # end to end through the C ABI from pinned host buffers: upload the 64
     # coupling matrices and the 262,144 start configurations, run 100 steps,
@@ -822,15 +946,17 @@ def run_ours(args):
         cpu = cpu_baseline(couplings)
     rc = None
     if rank == 0 and not args.no_recompute:
-        rc = recompute_report(stream, peaks)
+        rc = recompute_report(stream, peaks, mp.get("fp8_tflops"))
     lat = latency_report(stream) if rank == 0 else None
     sg = setgen_report(stream) if rank == 0 else None
+    sweep = config2_sweep(stream, insts) if (rank == 0 and not args.no_sweep) else None
 
     for r in runs:
         r.close()
     batch.close()
     for i in insts:
         i.close()
+    ttt = ttt_measure(set(TTT_LINE_METHODS), TTT_BETA, 1) if (rank == 0 and not args.no_ttt) else None
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -844,7 +970,8 @@ def run_ours(args):
                 "mc_steps_per_s": mc_steps,
                 "gpu_launches": 2 * args.steps,
                 "roofline": roofline, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
-                "recompute": rc, "latency_config1": lat, "set_generation": sg}
+                "recompute": rc, "latency_config1": lat, "set_generation": sg,
+                "peaks_measured": mp, "time_to_thermalise": ttt, "config2_sweep": sweep}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -879,6 +1006,10 @@ def main():
                     help="time-to-thermalise comparison instead of the throughput line")
     ap.add_argument("--no-recompute", action="store_true",
                     help="skip the tensor-core recompute measurement")
+    ap.add_argument("--no-ttt", action="store_true",
+                    help="skip the time-to-thermalise comparison in the bench line")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the beta x K sweep of the full workload in the bench line")
     ap.add_argument("--instances", type=int, default=INSTANCES,
                     help="smaller cases for profiling only; the bench line uses the default")
     ap.add_argument("--chains", type=int, default=CHAINS)

@@ -34,7 +34,8 @@ EXPORTS = ["sk_create_instance", "sk_set_couplings", "sk_destroy_instance", "sk_
            "mcmcmc_batch_create", "mcmcmc_batch_advance", "mcmcmc_batch_capture",
            "mcmcmc_batch_replay", "mcmcmc_batch_autotune", "mcmcmc_batch_info",
            "mcmcmc_batch_classes", "mcmcmc_batch_set_layout",
-           "mcmcmc_batch_free", "mcmcmc_run_noalloc", "sk_last_error"]
+           "mcmcmc_batch_free", "mcmcmc_run_noalloc", "sk_last_error",
+           "sk_peak_l2_read", "sk_peak_smem"]
 
 
 class SKError(RuntimeError):
@@ -110,6 +111,8 @@ def lib(build_if_missing: bool = True):
             "mcmcmc_batch_info": [vp, vp, vp, vp, vp],
             "mcmcmc_batch_free": [vp],
             "mcmcmc_run_noalloc": [u32, u32, vp, d, u32, u32, u32, d, u64, u32, u64, vp, vp, vp],
+            "sk_peak_l2_read": [u64, u32, u32, vp, C.POINTER(d)],
+            "sk_peak_smem": [u32, u32, u32, vp, C.POINTER(d)],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -437,6 +440,28 @@ def run_noalloc(couplings, spins, energy, *, scale=1.0, K=8, rule=SK_RULE_MCMCMC
                                     int(K), int(rule), float(beta), int(seed), int(stream_id),
                                     int(steps), C.c_void_p(spins.data_ptr()),
                                     C.c_void_p(energy.data_ptr()), _stream_handle(stream)))
+
+
+# ---------------------------------------------------------------------------
+# measured memory ceilings (sk_peaks.h)
+# ---------------------------------------------------------------------------
+SK_PEAK_SMEM_VEC16, SK_PEAK_SMEM_GATHER4 = 0, 1
+
+
+def peak_l2_read(working_set_bytes: int = 48 << 20, passes: int = 8, reps: int = 5, stream=None) -> float:
+    """sk_peak_l2_read: L2 read bandwidth (GB/s) on a resident working set."""
+    out = C.c_double(0.0)
+    _check(lib().sk_peak_l2_read(int(working_set_bytes), int(passes), int(reps), _stream_handle(stream),
+                                 C.byref(out)))
+    return out.value
+
+
+def peak_smem(mode: int = SK_PEAK_SMEM_VEC16, iters: int = 4096, reps: int = 5, stream=None) -> float:
+    """sk_peak_smem: shared-memory load bandwidth (GB/s), conflict-free 16-byte
+    loads or random 4-byte gathers (useful bytes)."""
+    out = C.c_double(0.0)
+    _check(lib().sk_peak_smem(int(mode), int(iters), int(reps), _stream_handle(stream), C.byref(out)))
+    return out.value
 
 
 # ---------------------------------------------------------------------------
