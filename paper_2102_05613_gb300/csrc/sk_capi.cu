@@ -1233,7 +1233,23 @@ sk_status plan_batch(sk_batch* b) {
             c.G = b->G_override ? std::min(32u, std::max(b->G_override, c.gmin)) : 32u;
             uint32_t fit = fit_warps(c.per_chain, c.G);
             while (c.G < 32 && fit < 1) fit = fit_warps(c.per_chain, c.G <<= 1);
-            c.W = b->W_override ? std::min(b->W_override, fit) : fit;
+            if (b->W_override) {
+                c.W = std::min(b->W_override, fit);
+            } else {
+                // as many warps as the class's chains need when spread over the
+                // SMs, at most as many as fit: a class of few chains gets small
+                // CTAs and with them the 128-register step kernel (8 row loads of
+                // the field update in flight), which is what a lone chain's
+                // latency wants; whole-warp chains keep an even count so that
+                // overlap pairs share a CTA
+                uint64_t total = 0;
+                for (uint32_t i : g.second) total += b->runs[i]->chains;
+                const uint32_t spw = 32u / c.G;
+                const uint64_t per_sm = (total + static_cast<uint64_t>(sms) - 1) / static_cast<uint64_t>(sms);
+                uint32_t need = static_cast<uint32_t>(std::min<uint64_t>(32, (per_sm + spw - 1) / spw));
+                if (c.G == 32) need = std::max(2u, (need + 1u) & ~1u);
+                c.W = std::max(1u, std::min(fit, need));
+            }
         }
         if (c.W < 1 || (c.G == 32 && c.W < 2))
             return fail(SK_ERR_INVALID_ARG, "N too large: %u bytes of shared memory per chain", c.per_chain);

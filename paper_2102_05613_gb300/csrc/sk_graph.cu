@@ -367,7 +367,7 @@ __device__ __forceinline__ void graph_loop(const JobDev& jb, bool write, uint32_
         H mloc = H(0);
         for (uint32_t v = v0; v < v1; ++v)
             if (__ldg(&tab.F[v]) && dE[v] < mloc) mloc = dE[v];
-        mloc = step::gmin(g, mloc);
+        mloc = step::gmin<false>(g, mloc);
         if (nw > 1u) {
             if (lane == 0u) rmin[wt] = mloc;
             team_sync(nw, team);

@@ -38,6 +38,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "sk_device.cuh"
 #include "sk_internal.h"
 
@@ -66,14 +68,29 @@ template <int G, typename T>
 __device__ __forceinline__ T gshfl(const Grp<G>& g, T v, int src) {
     return __shfl_sync(g.mask, v, src, G);
 }
-template <int G, typename T>
+// Group minimum: log2(G) butterfly shuffles, or (REDUX) one warp reduction
+// over the group's lanes (redux.sync; the groups of a warp reduce
+// independently, each under its own mask).  The reduction is shorter on a
+// lone chain's critical path but costs issue slots where many chains share an
+// SM, so only the few-chain variant takes it.
+template <bool REDUX, int G, typename T>
 __device__ __forceinline__ T gmin(const Grp<G>& g, T v) {
+    if constexpr (REDUX) {
+        if constexpr (std::is_integral<T>::value) {
+            return __reduce_min_sync(g.mask, v);
+        } else {
+            float r;
+            asm volatile("redux.sync.min.f32 %0, %1, %2;" : "=f"(r) : "f"(v), "r"(g.mask));
+            return r;
+        }
+    } else {
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) {
-        const T y = __shfl_xor_sync(g.mask, v, o, G);
-        v = y < v ? y : v;
+        for (int o = G / 2; o > 0; o >>= 1) {
+            const T y = __shfl_xor_sync(g.mask, v, o, G);
+            v = y < v ? y : v;
+        }
+        return v;
     }
-    return v;
 }
 template <int G, typename T>
 __device__ __forceinline__ T gsum(const Grp<G>& g, T v) {
@@ -103,7 +120,19 @@ struct ChainMem {
     void* row[2];
     uint64_t* bar;
     uint4* b0;  // block 0 of G consecutive steps (kB0Bytes reserved)
+    const unsigned long long* wsm;  // +-J: the first kWCache weight-table entries
 };
+
+// +-J weight-table entries held in shared memory per work item: at moderate
+// beta the table is this short (W[d] ~ 2^52 e^{-2 beta d} rounds to 0 past
+// d ~ 18/beta), and the lookups then cost a shared-memory load instead of a
+// trip to L2; longer tables read the rest from global memory.
+constexpr uint32_t kWCache = 64;
+__device__ __forceinline__ unsigned long long wt_lookup(const unsigned long long* wsm,
+                                                        const unsigned long long* Wt, uint32_t wlen,
+                                                        uint32_t idx) {
+    return idx < kWCache ? wsm[idx] : (idx < wlen ? __ldg(&Wt[idx]) : 0ull);
+}
 
 // Block 0 (U0, U1) of the G steps base .. base+G-1, computed one step per
 // group lane into the chain's shared memory, where every lane of the group
@@ -137,12 +166,90 @@ __device__ __forceinline__ uint32_t site_of(const uint32_t (&sp)[2 * NB], int k)
 // h_k -= c1 J[x1][k] + c2 J[x2][k] for k < Npad (c2 = 0: one flip); lane gl
 // owns elements 4 gl + 4 G v.  r1 is the staged row (shared memory) when
 // STAGED, else a row of J in global memory; r2 is global and read only when
-// c2 != 0.  UNROLL iterations' row loads are in flight together: 2 where
-// other chains hide the L2 latency within tight registers, 8 in the 128-register
-// variant (few warps per SM), where a lone chain waits for each round trip.
-template <typename JT, bool STAGED, int G, int UNROLL>
+// c2 != 0.  Two forms:
+//  - CHUNKED (the MCMCMC 128-register variant: few warps per SM, where a lone
+//    chain waits for each round trip and a double flip reads two rows):
+//    chunks of UNROLL iterations whose row loads are all issued before any
+//    field of the chunk is read or written, so that a chunk costs one round
+//    trip to L2 even when the first row is staged in shared memory beside
+//    the fields (loads could not otherwise move past the stores);
+//  - otherwise one loop unrolled UNROLL times: 2 where many chains per SM
+//    hide each other's L2 latency within tight registers, 8 for Metropolis
+//    in the 128-register variant (one row, no second-row branch).
+// The terms are added in the same order either way (the first flip's, then
+// the second's), so both give the same fields bit for bit.
+template <typename JT, bool STAGED, int G, int UNROLL, bool CHUNKED>
 __device__ __forceinline__ void update_fields(typename Types<JT>::H* hf, const JT* r1, const JT* r2, int c1,
                                               int c2, uint32_t npad, int gl) {
+    if constexpr (CHUNKED) {
+        constexpr uint32_t kStride = 4u * G;
+        for (uint32_t k0 = 4u * gl; k0 < npad; k0 += kStride * UNROLL) {
+            if constexpr (sizeof(JT) == 1) {
+                uint32_t j1[UNROLL], j2[UNROLL];
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) {
+                    const uint32_t k = k0 + kStride * u;
+                    j1[u] = j2[u] = 0u;
+                    if (k < npad) {
+                        j1[u] = STAGED ? *reinterpret_cast<const uint32_t*>(r1 + k)
+                                       : __ldg(reinterpret_cast<const unsigned int*>(r1 + k));
+                        if (c2) j2[u] = __ldg(reinterpret_cast<const unsigned int*>(r2 + k));
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) {
+                    const uint32_t k = k0 + kStride * u;
+                    if (k < npad) {
+                        int4 hv = *reinterpret_cast<int4*>(hf + k);
+                        hv.x -= c1 * sbyte(j1[u], 0);
+                        hv.y -= c1 * sbyte(j1[u], 1);
+                        hv.z -= c1 * sbyte(j1[u], 2);
+                        hv.w -= c1 * sbyte(j1[u], 3);
+                        if (c2) {
+                            hv.x -= c2 * sbyte(j2[u], 0);
+                            hv.y -= c2 * sbyte(j2[u], 1);
+                            hv.z -= c2 * sbyte(j2[u], 2);
+                            hv.w -= c2 * sbyte(j2[u], 3);
+                        }
+                        *reinterpret_cast<int4*>(hf + k) = hv;
+                    }
+                }
+            } else {
+                float4 j1[UNROLL], j2[UNROLL];
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) {
+                    const uint32_t k = k0 + kStride * u;
+                    j1[u] = j2[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (k < npad) {
+                        j1[u] = STAGED ? *reinterpret_cast<const float4*>(r1 + k)
+                                       : __ldg(reinterpret_cast<const float4*>(r1 + k));
+                        if (c2) j2[u] = __ldg(reinterpret_cast<const float4*>(r2 + k));
+                    }
+                }
+                const float f1 = static_cast<float>(c1);
+                const float f2 = static_cast<float>(c2);
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) {
+                    const uint32_t k = k0 + kStride * u;
+                    if (k < npad) {
+                        float4 hv = *reinterpret_cast<float4*>(hf + k);
+                        hv.x = fmaf(-f1, j1[u].x, hv.x);
+                        hv.y = fmaf(-f1, j1[u].y, hv.y);
+                        hv.z = fmaf(-f1, j1[u].z, hv.z);
+                        hv.w = fmaf(-f1, j1[u].w, hv.w);
+                        if (c2) {
+                            hv.x = fmaf(-f2, j2[u].x, hv.x);
+                            hv.y = fmaf(-f2, j2[u].y, hv.y);
+                            hv.z = fmaf(-f2, j2[u].z, hv.z);
+                            hv.w = fmaf(-f2, j2[u].w, hv.w);
+                        }
+                        *reinterpret_cast<float4*>(hf + k) = hv;
+                    }
+                }
+            }
+        }
+        return;
+    }
 #pragma unroll UNROLL
     for (uint32_t k = 4u * gl; k < npad; k += 4u * G) {
         if constexpr (sizeof(JT) == 1) {
@@ -243,7 +350,7 @@ __device__ __forceinline__ typename Types<JT>::H star_energies(const int8_t* S, 
         dE[q] = v;
         if (d <= K) mloc = mloc < v ? mloc : v;
     }
-    return gmin(g, mloc);
+    return gmin<false>(g, mloc);
 }
 
 // Weight of a slot with candidate energy dEq (a4): exp(-beta (dEq - m)) times
@@ -375,6 +482,11 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
     using W = typename Types<JT>::W;
     constexpr bool STAGED = STAGE == 1;  // 0: rows through L1, 2: the same with node-weighted records
     constexpr bool NWR = STAGE == 2;
+    // the 128-register variant (few warps per SM, where one chain's step is a
+    // chain of latencies) keeps the slot weights in registers for the node
+    // search and draws the next step's sites during the current step
+    constexpr bool KEEPW = UNROLL >= 8;
+    constexpr bool AHEAD = STAGED || KEEPW;
     const Grp<G> g;
     // next record point (0: none; a record follows step t when t + 1 == next_rec)
     uint32_t next_rec = jb.record_every ? (t0 / jb.record_every + 1u) * jb.record_every : 0u;
@@ -402,6 +514,7 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
     fill_block0<G>(cm.b0, t0 & ~static_cast<uint32_t>(G - 1), chain, c3, k0, k1, g);
     uint32_t site[2 * NB];  // packed sites of this step (site_of)
 
+    if constexpr (!STAGED && AHEAD && RULE == 0) draw_sites<NB, G>(site, t0, chain, c3, k0, k1, nblk, N, g);
     // prologue (staged rows): draw the first step and stage its row
     if constexpr (STAGED) {
         uint32_t first;
@@ -434,7 +547,7 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
 
         // direct rows: this step's sites now; staged rows: the next step's
         // sites and the TMA of its first row, one step ahead
-        if constexpr (!STAGED && RULE == 0) draw_sites<NB, G>(site, t, chain, c3, k0, k1, nblk, N, g);
+        if constexpr (!AHEAD && RULE == 0) draw_sites<NB, G>(site, t, chain, c3, k0, k1, nblk, N, g);
         uint32_t nsite[2 * NB];
         if (STAGED && t + 1u < t1) {
             uint32_t nx;
@@ -481,7 +594,7 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                 bool accept;
                 if constexpr (sizeof(JT) == 1) {
                     const uint32_t k = static_cast<uint32_t>(dE) >> 1;
-                    accept = dE <= 0 || (k < wlen && (U1 >> 11) < __ldg(&Wt[k]));
+                    accept = dE <= 0 || (U1 >> 11) < wt_lookup(cm.wsm, Wt, wlen, k);
                 } else {
                     accept = dE <= 0.0f || static_cast<float>(U1 >> 40) * 0x1p-24f < dev::pow2(nbl2 * dE);
                 }
@@ -494,6 +607,8 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                 rows = nflip;
             } else {
                 // ---- MCMCMC: K proposals on the uniform-root star ----
+                // (few-chain variant: the next step's sites, interleaved with this step's work)
+                if constexpr (!STAGED && AHEAD) draw_sites<NB, G>(nsite, t + 1u, chain, c3, k0, k1, nblk, N, g);
                 const unsigned long long U0 = (static_cast<unsigned long long>(b0.y) << 32) | b0.x;
                 const bool leaf = U0 >= dev::at_use(jb.root_thr);
                 const uint32_t a = gshfl(g, site[0], 0) & 0xFFFFu;
@@ -515,7 +630,7 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                     dE[q] = v;
                     if (d <= K) mloc = mloc < v ? mloc : v;
                 }
-                const H m = gmin(g, mloc);
+                const H m = gmin<KEEPW>(g, mloc);
                 // weights in slot order: exp(-beta (dE - m)) times the slot's
                 // root factor (the centre: slot 1 of a leaf root, slot 0 of a
                 // centre root); recomputed, not stored, where the choice needs them
@@ -526,7 +641,7 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                     if (d <= K) {
                         if constexpr (sizeof(JT) == 1) {
                             const uint32_t idx = static_cast<uint32_t>(dE[q] - m) >> 1;
-                            x = idx < wlen ? __ldg(&Wt[idx]) : 0ull;
+                            x = wt_lookup(cm.wsm, Wt, wlen, idx);
                             if (root_weighted)  // floor(x F / 2^20)
                                 x = __umul64hi(x << 11, static_cast<unsigned long long>(centre ? jb.fcen : jb.fleaf) << 33);
                         } else {
@@ -536,14 +651,19 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                     return x;
                 };
                 W gsum_[NB];
+                W xs[KEEPW ? 4 * NB : 1];
 #pragma unroll
                 for (int q = 0; q < NB; ++q) gsum_[q] = 0;
 #pragma unroll
-                for (int q = 0; q < 4 * NB; ++q) gsum_[q >> 2] += slot_w(q);
+                for (int q = 0; q < 4 * NB; ++q) {
+                    const W xq = slot_w(q);
+                    if constexpr (KEEPW) xs[q] = xq;
+                    gsum_[q >> 2] += xq;
+                }
                 W w0;  // slot 0, the root: the centre of a centre root, else a leaf
                 if constexpr (sizeof(JT) == 1) {
                     const uint32_t idx0 = static_cast<uint32_t>(-m) >> 1;
-                    w0 = idx0 < wlen ? __ldg(&Wt[idx0]) : 0ull;
+                    w0 = wt_lookup(cm.wsm, Wt, wlen, idx0);
                     if (root_weighted)
                         w0 = __umul64hi(w0 << 11, static_cast<unsigned long long>(leaf ? jb.fleaf : jb.fcen) << 33);
                 } else {
@@ -576,13 +696,16 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                     const unsigned ball = gballot(g, !found && base + incl[q] > u);
                     if (!found && ball) {
                         const int L = __ffs(ball) - 1;
-                        // this lane's 4 weights again (bit-identical), their
-                        // sum in the order of the first pass
+                        // this lane's 4 weights (kept, or recomputed bit-identically),
+                        // their sum in the order of the first pass
                         W x[4];
                         W mine = 0;
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
-                            x[e] = slot_w(4 * q + e);
+                            if constexpr (KEEPW)
+                                x[e] = xs[4 * q + e];
+                            else
+                                x[e] = slot_w(4 * q + e);
                             mine += x[e];
                         }
                         W run = base + (incl[q] - mine);
@@ -632,10 +755,11 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
             if (nflip) {
                 const int c1 = 2 * S[x1];
                 const int c2 = nflip == 2 ? 2 * S[x2] : 0;
+                constexpr bool CHUNKED = RULE == 0 && UNROLL >= 8;
                 if (x1_staged)
-                    update_fields<JT, STAGED, G, UNROLL>(hf, rowA, Jrow(x2), c1, c2, npad, g.gl);
+                    update_fields<JT, STAGED, G, UNROLL, CHUNKED>(hf, rowA, Jrow(x2), c1, c2, npad, g.gl);
                 else
-                    update_fields<JT, false, G, UNROLL>(hf, Jrow(x1), nullptr, c1, 0, npad, g.gl);
+                    update_fields<JT, false, G, UNROLL, CHUNKED>(hf, Jrow(x1), nullptr, c1, 0, npad, g.gl);
                 __syncwarp(g.mask);
                 if (g.gl == 0) {
                     S[x1] = static_cast<int8_t>(-S[x1]);
@@ -648,7 +772,7 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
             if (t < trace_end && g.gl == 0) jb.trace[static_cast<size_t>(chain) * jb.trace_steps + t] = sel;
             __syncwarp(g.mask);
         }
-        if constexpr (RULE == 0 && STAGED) {
+        if constexpr (RULE == 0 && AHEAD) {
 #pragma unroll
             for (int q = 0; q < 2 * NB; ++q) site[q] = nsite[q];
         }
@@ -674,6 +798,7 @@ __global__ void __launch_bounds__(MAXT, 1)
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(16) JobDev s_job;
     __shared__ __align__(8) uint64_t bars[2 * 256];
+    __shared__ unsigned long long s_wt[sizeof(JT) == 1 ? kWCache : 1];
     __shared__ uint32_t s_item;
     const Grp<G> g;
     const int warp = threadIdx.x >> 5;
@@ -697,6 +822,11 @@ __global__ void __launch_bounds__(MAXT, 1)
             reinterpret_cast<uint4*>(&s_job)[threadIdx.x] = reinterpret_cast<const uint4*>(&jobs[wi.job])[threadIdx.x];
         __syncthreads();
         const JobDev& jb = s_job;
+        if constexpr (sizeof(JT) == 1) {  // the start of the +-J weight table (0 past its end)
+            for (uint32_t i = threadIdx.x; i < kWCache; i += blockDim.x)
+                s_wt[i] = i < jb.wlen ? reinterpret_cast<const unsigned long long*>(jb.W)[i] : 0ull;
+            __syncthreads();
+        }
         const bool warp_busy = static_cast<uint32_t>(warp * SPW) < wi.nchains;  // some group has a chain
         const bool own = static_cast<uint32_t>(slot) < wi.nchains;              // this group has a chain
         const uint32_t chain = own ? wi.chain0 + slot : wi.chain0;              // shadows copy the first
@@ -709,6 +839,7 @@ __global__ void __launch_bounds__(MAXT, 1)
         cm.row[1] = base + (5 + bj) * static_cast<size_t>(npad);
         cm.bar = &bars[2 * slot];
         cm.b0 = reinterpret_cast<uint4*>(base + (STAGE == 1 ? 5 + 2 * bj : 5) * static_cast<size_t>(npad));
+        cm.wsm = s_wt;
         // the overlap partner (chain slot ^ 1) lives one slice up or down
         const int partner_off = (slot & 1) ? -static_cast<int>(per_chain) : static_cast<int>(per_chain);
         const uint32_t t0 = static_cast<uint32_t>(*jb.step);
