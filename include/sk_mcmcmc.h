@@ -53,7 +53,9 @@ typedef enum {
     SK_ERR_CUDA = 3,        /* a CUDA runtime call failed (no device, ...)     */
     SK_ERR_TIMEOUT = 4,     /* a bounded device wait expired; state is invalid */
     SK_ERR_NOT_READY = 5,   /* work still in flight (non-blocking query)       */
-    SK_ERR_DEVICE = 6       /* a kernel reported an inconsistency (bounds)     */
+    SK_ERR_DEVICE = 6,      /* a kernel reported an inconsistency (bounds)     */
+    SK_ERR_BUSY = 7,        /* the object is still in use by another object    */
+    SK_ERR_CANCELLED = 8    /* the request was cancelled before it finished    */
 } sk_status;
 
 typedef enum { SK_J_PM1 = 0, SK_J_GAUSS = 1 } sk_jkind;      /* int8 +-1 / float32 */
@@ -79,20 +81,46 @@ typedef struct sk_batch sk_batch;        /* runs advanced by one launch       */
 /* ---------------------------------------------------------------------- */
 
 /*
- * sk_create_instance: uploads an N x N coupling matrix.
+ * sk_create_instance: one disorder realisation of N spins on the device,
+ * uploaded from the caller or drawn from a seed.
  *   N          2 .. SK_MAX_N spins.
  *   kind       SK_J_PM1: couplings are int8 with values in {-1, 0, +1};
  *              SK_J_GAUSS: couplings are float32.
- *   couplings  N*N row-major, symmetric, zero diagonal (checked for host
- *              input: SK_ERR_INVALID_ARG otherwise); mem says where it lives.
+ *   couplings  N*N row-major, symmetric, zero diagonal, in the memory `mem`
+ *              says (copied; checked on the device: SK_ERR_INVALID_ARG
+ *              names the first offending entry); or NULL: the couplings are
+ *              drawn on the device from `seed` (mem is ignored) --
+ *              Philox4x32-10 (Salmon et al., SC'11) with key = seed, domain 2,
+ *              one draw per pair i < j shared by J_ij and J_ji:
+ *                SK_J_PM1:   counter (j >> 7, i, 0, 2 << 24), bit j & 127 of
+ *                            the block (word (j & 127) >> 5, bit j & 31):
+ *                            set -> -1, clear -> +1 (equiprobable +-1);
+ *                SK_J_GAUSS: counter (j, i, 1, 2 << 24) = (w0, w1, w2, w3),
+ *                            uniforms u1 = (2^26 (w0 >> 5) + (w1 >> 6)) 2^-53
+ *                            and u2 alike from (w2, w3), the Box-Muller normal
+ *                            z = sqrt(-2 ln(1 - u1)) cos(2 pi u2) in double
+ *                            precision, J_ij = (float)(z / sqrt(N)): the
+ *                            N(0, 1/N) couplings of Sec. IV.A's model after
+ *                            J -> -J/sqrt(N); the device's double-precision
+ *                            log and cos may round the last bit differently
+ *                            from another library's, so another
+ *                            implementation of this recipe agrees to within
+ *                            one float32 unit in the last place;
+ *   seed       the Philox key when couplings is NULL, else unused.
  *   scale      energy multiplier (> 0): E = -scale sum_{i<j} J s s.  1.0 for
  *              the +-J model with integer energies; 1/sqrt(N) gives the +-J
  *              model on the paper's Gaussian temperature scale.
  *   stream     cudaStream_t (as void*) for this instance's copies, or NULL.
  * The device copy is padded to Npad = ceil(N/32)*32 rows and columns.
  */
-sk_status sk_create_instance(uint32_t N, uint32_t kind, const void* couplings, uint32_t mem,
+sk_status sk_create_instance(uint32_t N, uint32_t kind, const void* couplings, uint32_t mem, uint64_t seed,
                              double scale, void* stream, sk_instance** out);
+
+/* sk_get_couplings: copies the instance's N x N couplings (row-major, int8
+ * for SK_J_PM1, float32 for SK_J_GAUSS) into `out` (mem: host or device) and
+ * synchronises the instance's stream -- to save a drawn realisation or check
+ * it against another implementation. */
+sk_status sk_get_couplings(const sk_instance* inst, void* out, uint32_t mem);
 
 /* Replaces the couplings of an existing instance (same N and kind); used to
  * re-upload a disorder realisation without reallocating. */
@@ -106,8 +134,9 @@ sk_status sk_set_couplings(sk_instance* inst, const void* couplings, uint32_t me
  * instance changes and the message names the first failing instance. */
 sk_status sk_set_couplings_many(sk_instance* const* insts, uint32_t n, const void* const* couplings, uint32_t mem);
 
-/* Releases an instance (waits for its streams).  Free every run created on
- * it (mcmcmc_free) first: runs keep a pointer to their instance. */
+/* Releases an instance (waits for its streams).  Runs keep a pointer to
+ * their instance: while a run created on it has not been freed
+ * (mcmcmc_free), the call returns SK_ERR_BUSY and releases nothing. */
 sk_status sk_destroy_instance(sk_instance* inst);
 
 /*
@@ -164,7 +193,20 @@ typedef struct {
                             /*   is chosen with probability ~ P_eq F_v (F_v the */
                             /*   line's binomial factor in 20-bit fixed point,  */
                             /*   1 for trees).                                  */
+    uint32_t fault_inject;  /* tests of the failure path only, 0 otherwise:     */
+                            /*   SK_FAULT_WITHHOLD_ROW withholds the first row  */
+                            /*   copy of chain 0 in a layout with staged rows   */
+                            /*   (mcmcmc_batch_set_layout staging 1);           */
+                            /*   SK_FAULT_WITHHOLD_TILE withholds the first     */
+                            /*   operand tile of the first CTA of each field    */
+                            /*   recompute (mcmcmc_recompute): the waits for    */
+                            /*   them expire (~2 s each), the kernel lets its   */
+                            /*   other copies and MMAs finish, returns, and the */
+                            /*   call reports SK_ERR_TIMEOUT; nothing faults    */
 } sk_run_params;
+
+#define SK_FAULT_WITHHOLD_ROW 1u
+#define SK_FAULT_WITHHOLD_TILE 2u
 
 /*
  * mcmcmc_create: allocates the chains' state (spins, local fields, records)
@@ -306,6 +348,9 @@ sk_status mcmcmc_trace(sk_run* run, int32_t* slots, uint32_t mem);
  */
 sk_status mcmcmc_counters(sk_run* run, uint64_t* flips, uint64_t* rows);
 
+/* Releases a run (waits for its stream).  While the run belongs to a batch
+ * that has not been freed (mcmcmc_batch_free), the call returns SK_ERR_BUSY
+ * and releases nothing. */
 sk_status mcmcmc_free(sk_run* run);
 
 /* ---------------------------------------------------------------------- */
@@ -488,7 +533,13 @@ sk_status sk_set_generation(uint32_t n, const double* P, double* out, uint32_t m
 /* ---------------------------------------------------------------------- */
 typedef struct sk_server sk_server;
 
-typedef enum { SK_JOB_QUEUED = 0, SK_JOB_RUNNING = 1, SK_JOB_DONE = 2, SK_JOB_FAILED = 3 } sk_job_state;
+typedef enum {
+    SK_JOB_QUEUED = 0,
+    SK_JOB_RUNNING = 1,
+    SK_JOB_DONE = 2,
+    SK_JOB_FAILED = 3,
+    SK_JOB_CANCELLED = 4
+} sk_job_state;
 
 typedef struct {
     uint32_t N, kind;         /* couplings: N spins, sk_jkind                       */
@@ -553,9 +604,21 @@ sk_status sk_server_poll(sk_server* s, uint64_t ticket, sk_job_status* status);
 /* Result of a finished job: energies (chains doubles), spins (chains*N int8,
  * may be NULL), spins flipped in total (may be NULL); host pointers.  Returns
  * SK_ERR_NOT_READY while the job is queued or running, the job's error if it
- * failed.  The job is forgotten afterwards. */
+ * failed, SK_ERR_CANCELLED if it was cancelled.  The job is forgotten
+ * afterwards. */
 sk_status sk_server_result(sk_server* s, uint64_t ticket, double* energies, int8_t* spins,
                            uint64_t* flips);
+
+/*
+ * sk_server_cancel: withdraws a job.  A queued job leaves the queue at once;
+ * a running job stops at the end of the quantum in flight and its device
+ * memory is released (its partial state is not kept).  Either way its state
+ * becomes SK_JOB_CANCELLED and sk_server_result returns SK_ERR_CANCELLED; the
+ * other jobs are not affected (their draws do not depend on the mix).
+ * Cancelling a cancelled job is a no-op; a finished or failed job, or an
+ * unknown ticket, gives SK_ERR_INVALID_ARG.
+ */
+sk_status sk_server_cancel(sk_server* s, uint64_t ticket);
 
 /* Blocks until no job is queued or running (timeout_ns 0 = no limit). */
 sk_status sk_server_wait_all(sk_server* s, uint64_t timeout_ns);

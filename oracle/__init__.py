@@ -37,6 +37,8 @@ def lib():
         L.sko_energy.restype = d
         L.sko_fields.argtypes = [i, i, vp, vp, vp]
         L.sko_fields.restype = None
+        L.sko_gen_couplings.argtypes = [i, i, u64, vp]
+        L.sko_gen_couplings.restype = None
         L.sko_init_spins.argtypes = [u64, u32, u32, i, vp]
         L.sko_init_spins.restype = None
         L.sko_weight_table.argtypes = [d, i, vp]
@@ -113,6 +115,14 @@ def fields(J: np.ndarray, s: np.ndarray) -> np.ndarray:
     h = np.zeros(J.shape[0])
     lib().sko_fields(J.shape[0], _kind_of(J), _ptr(J), _ptr(s), _ptr(h))
     return h
+
+
+def gen_couplings(N: int, kind: int, seed: int) -> np.ndarray:
+    """Couplings drawn from a seed by Philox domain 2 (+-1 bits, or the
+    Box-Muller N(0, 1/N) normal rounded to float32); see sko_gen_couplings."""
+    out = np.zeros((N, N), dtype=np.int8 if kind == PM1 else np.float32)
+    lib().sko_gen_couplings(N, kind, seed, _ptr(out))
+    return out
 
 
 def init_spins(seed: int, stream: int, chain: int, N: int) -> np.ndarray:

@@ -135,6 +135,48 @@ double sko_energy(int N, int kind, const void* J, double scale, const int8_t* s)
     return -scale * e;
 }
 
+/*
+ * Couplings drawn from a seed, the instance generator of the library's
+ * sk_create_instance with couplings NULL, written out here separately:
+ * Philox4x32-10 with key = (seed low, seed high), domain 2, one draw per pair
+ * i < j shared by J_ij and J_ji:
+ *   +-J (kind 0):      counter (j >> 7, i, 0, 2 << 24), bit j mod 128 of the
+ *                      block (word (j mod 128) / 32, bit j mod 32): set -> -1;
+ *   Gaussian (kind 1): counter (j, i, 1, 2 << 24) -> (w0, w1, w2, w3); the
+ *                      53-bit uniforms u1 = (2^26 (w0 >> 5) + (w1 >> 6)) 2^-53
+ *                      and u2 from (w2, w3); the Box-Muller normal (Box &
+ *                      Muller 1958) z = sqrt(-2 ln(1 - u1)) cos(2 pi u2);
+ *                      J_ij = (float)(z / sqrt(N)), so J ~ N(0, 1/N).
+ * Zero diagonal.  out: N*N int8 (kind 0) or float (kind 1), row-major.
+ */
+void sko_gen_couplings(int N, int kind, uint64_t seed, void* out) {
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (int i = 0; i < N; ++i) {
+        if (kind == SKO_PM1) ((int8_t*)out)[(size_t)i * N + i] = 0;
+        else ((float*)out)[(size_t)i * N + i] = 0.0f;
+        for (int j = i + 1; j < N; ++j) {
+            uint32_t w[4];
+            if (kind == SKO_PM1) {
+                const uint32_t ctr[4] = {(uint32_t)j >> 7, (uint32_t)i, 0u, 2u << 24};
+                sko_philox(ctr, key, w);
+                const int b = j % 128;
+                const int8_t v = ((w[b / 32] >> (b % 32)) & 1u) ? (int8_t)-1 : (int8_t)1;
+                ((int8_t*)out)[(size_t)i * N + j] = v;
+                ((int8_t*)out)[(size_t)j * N + i] = v;
+            } else {
+                const uint32_t ctr[4] = {(uint32_t)j, (uint32_t)i, 1u, 2u << 24};
+                sko_philox(ctr, key, w);
+                const double u1 = ((double)(w[0] >> 5) * 67108864.0 + (double)(w[1] >> 6)) * ldexp(1.0, -53);
+                const double u2 = ((double)(w[2] >> 5) * 67108864.0 + (double)(w[3] >> 6)) * ldexp(1.0, -53);
+                const double z = sqrt(-2.0 * log(1.0 - u1)) * cos(6.283185307179586476925286766559 * u2);
+                const float v = (float)(z / sqrt((double)N));
+                ((float*)out)[(size_t)i * N + j] = v;
+                ((float*)out)[(size_t)j * N + i] = v;
+            }
+        }
+    }
+}
+
 /* h_i = sum_j J_ij s_j (unscaled). */
 void sko_fields(int N, int kind, const void* J, const int8_t* s, double* h) {
     for (int i = 0; i < N; ++i) {

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <set>
@@ -158,6 +159,7 @@ void set_error_message(const char* msg) { g_err = msg; }
 }  // namespace sk
 
 struct sk_instance {
+    std::atomic<int> runs{0};  // runs created on the instance and not yet freed
     uint32_t N = 0, Npad = 0, kind = 0;
     double scale = 1.0;
     void* dJ = nullptr;
@@ -221,6 +223,7 @@ struct sk_batch {
 };
 
 struct sk_run {
+    std::atomic<int> batches{0};  // live batches holding the run (its own included)
     sk_instance* inst = nullptr;
     sk_run_params p{};
     uint32_t chains = 0;
@@ -535,13 +538,14 @@ extern "C" {
 
 const char* sk_last_error(void) { return g_err.c_str(); }
 
-sk_status sk_create_instance(uint32_t N, uint32_t kind, const void* couplings, uint32_t mem,
+sk_status sk_create_instance(uint32_t N, uint32_t kind, const void* couplings, uint32_t mem, uint64_t seed,
                              double scale, void* stream, sk_instance** out) {
     if (!out) return fail(SK_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (N < 2 || N > SK_MAX_N) return fail(SK_ERR_INVALID_ARG, "N = %u outside 2..%u", N, SK_MAX_N);
     if (kind != SK_J_PM1 && kind != SK_J_GAUSS) return fail(SK_ERR_INVALID_ARG, "unknown coupling kind %u", kind);
-    if (!couplings) return fail(SK_ERR_INVALID_ARG, "couplings is NULL");
+    if (couplings && mem != SK_MEM_HOST && mem != SK_MEM_DEVICE)
+        return fail(SK_ERR_INVALID_ARG, "mem must be SK_MEM_HOST or SK_MEM_DEVICE");
     if (!(scale > 0.0) || !std::isfinite(scale)) return fail(SK_ERR_INVALID_ARG, "scale must be > 0");
     sk_status s = check_device();
     if (s != SK_OK) return s;
@@ -561,7 +565,20 @@ sk_status sk_create_instance(uint32_t N, uint32_t kind, const void* couplings, u
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&in->ev_main, cudaEventDisableTiming);
         if (e != cudaSuccess) s = fail(SK_ERR_CUDA, "stream/event creation: %s", cudaGetErrorString(e));
     }
-    if (s == SK_OK) s = upload_couplings(in, couplings, mem, true);
+    if (s == SK_OK) {
+        if (couplings) {
+            s = upload_couplings(in, couplings, mem, true);
+        } else {  // drawn on the device from the seed, then checked like any input
+            cudaError_t e = sk::launch_gen_couplings(in->dJ, kind, N, in->Npad, seed, in->st);
+            if (e == cudaSuccess) e = sk::launch_check_couplings(in->dJ, kind, N, in->Npad, in->dflag, in->st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(in->hflag, in->dflag, sizeof(unsigned long long), cudaMemcpyDeviceToHost, in->st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(in->st);
+            if (e != cudaSuccess) s = fail(SK_ERR_CUDA, "coupling generation: %s", cudaGetErrorString(e));
+            if (s == SK_OK) s = couplings_verify(in);
+            if (s == SK_OK) s = couplings_commit(in, true);
+        }
+    }
     if (s != SK_OK) {
         cudaFree(in->dJ);
         cudaFree(in->dflag);
@@ -574,6 +591,16 @@ sk_status sk_create_instance(uint32_t N, uint32_t kind, const void* couplings, u
         return s;
     }
     *out = in;
+    return SK_OK;
+}
+
+sk_status sk_get_couplings(const sk_instance* in, void* out, uint32_t mem) {
+    if (!in || !out) return fail(SK_ERR_INVALID_ARG, "NULL argument");
+    if (mem != SK_MEM_HOST && mem != SK_MEM_DEVICE)
+        return fail(SK_ERR_INVALID_ARG, "mem must be SK_MEM_HOST or SK_MEM_DEVICE");
+    const size_t b = jbytes(in->kind);
+    SK_CU(cudaMemcpy2DAsync(out, in->N * b, in->dJ, in->Npad * b, in->N * b, in->N, cudaMemcpyDefault, in->st));
+    SK_CU(cudaStreamSynchronize(in->st));
     return SK_OK;
 }
 
@@ -609,6 +636,8 @@ sk_status sk_set_couplings_many(sk_instance* const* insts, uint32_t n, const voi
 
 sk_status sk_destroy_instance(sk_instance* in) {
     if (!in) return fail(SK_ERR_INVALID_ARG, "instance is NULL");
+    if (const int n = in->runs.load(); n > 0)
+        return fail(SK_ERR_BUSY, "%d run(s) created on this instance are not freed", n);
     cudaStreamSynchronize(in->st);
     cudaStreamSynchronize(in->side);
     cudaFree(in->dJ);
@@ -673,6 +702,8 @@ sk_status mcmcmc_create(sk_instance* in, const sk_run_params* p, sk_run** out) {
     if (p->stream_id > 0xFFFFFFu) return fail(SK_ERR_INVALID_ARG, "stream_id must fit 24 bits");
     if (p->trace_chains > p->chains) return fail(SK_ERR_INVALID_ARG, "trace_chains > chains");
     if (p->recompute_terms > 3) return fail(SK_ERR_INVALID_ARG, "recompute_terms must be 0..3");
+    if (p->fault_inject & ~(SK_FAULT_WITHHOLD_ROW | SK_FAULT_WITHHOLD_TILE))
+        return fail(SK_ERR_INVALID_ARG, "unknown fault_inject bits");
     if (p->graph) {
         if (p->graph != SK_GRAPH_TREE && p->graph != SK_GRAPH_LINE)
             return fail(SK_ERR_INVALID_ARG, "unknown graph %u", p->graph);
@@ -773,6 +804,9 @@ sk_status mcmcmc_create(sk_instance* in, const sk_run_params* p, sk_run** out) {
     j.graph = r->p.graph;
     j.arity = r->p.arity;
     j.V = V;
+    static_assert(sk::kFaultWithholdRow == SK_FAULT_WITHHOLD_ROW && sk::kFaultWithholdTile == SK_FAULT_WITHHOLD_TILE,
+                  "fault bits of the ABI and the kernels");
+    j.fault = r->p.fault_inject;
     root_setup(j, r->p.K, r->p.rule == SK_RULE_MCMCMC ? r->p.p_center : 0.0);
     s = init_state(r, p->init_spins, p->init_mem);
     if (s == SK_OK) {
@@ -787,6 +821,7 @@ sk_status mcmcmc_create(sk_instance* in, const sk_run_params* p, sk_run** out) {
         g_err = keep;
         return s;
     }
+    in->runs++;
     *out = r;
     return SK_OK;
 }
@@ -1051,7 +1086,8 @@ sk_status mcmcmc_recompute(sk_run* r, uint32_t mode, uint32_t terms, sk_recomput
     if (mode == 2 && (s = dalloc(&dout, static_cast<size_t>(r->chains) * in->Npad * 4)) != SK_OK) return s;
     SK_CU(cudaMemsetAsync(r->dstats + 3, 0, 3 * sizeof(unsigned long long), st));
     cudaError_t e = sk::launch_recompute(in->kind, r->ds, r->dh, dout, r->dSop, in->dJop, r->ddE, r->dstats + 3,
-                                         r->derr, r->chains, in->Npad, terms ? terms : 3u, mode, in->scale, st);
+                                         r->derr, r->chains, in->Npad, terms ? terms : 3u, mode, in->scale, st,
+                                         r->job.fault & sk::kFaultWithholdTile);
     if (!stats && mode != 2) {  // enqueue only
         if (e != cudaSuccess) return fail(SK_ERR_CUDA, "recompute: %s", cudaGetErrorString(e));
         return SK_OK;
@@ -1098,10 +1134,14 @@ sk_status mcmcmc_recompute_stats(sk_run* r, sk_recompute_stats* stats) {
 
 sk_status mcmcmc_free(sk_run* r) {
     if (!r) return fail(SK_ERR_INVALID_ARG, "run is NULL");
+    if (const int n = r->batches.load() - (r->self ? 1 : 0); n > 0)
+        return fail(SK_ERR_BUSY, "the run belongs to %d batch(es) that are not freed", n);
     cudaStreamSynchronize(r->inst->st);
     if (r->self) mcmcmc_batch_free(r->self);
+    sk_instance* in = r->inst;
     free_run_buffers(r);
     delete r;
+    in->runs--;
     return SK_OK;
 }
 
@@ -1329,6 +1369,7 @@ sk_status mcmcmc_batch_create(sk_run* const* runs, uint32_t n, uint32_t W, sk_ba
         delete b;
         return s;
     }
+    for (sk_run* r : b->runs) r->batches++;
     *out = b;
     return SK_OK;
 }
@@ -1667,6 +1708,7 @@ sk_status mcmcmc_batch_classes(const sk_batch* b, uint32_t max, uint32_t* count,
 sk_status mcmcmc_batch_free(sk_batch* b) {
     if (!b) return fail(SK_ERR_INVALID_ARG, "batch is NULL");
     cudaStreamSynchronize(b->st);
+    for (sk_run* r : b->runs) r->batches--;
     if (b->graph) cudaGraphExecDestroy(b->graph);
     free_side_streams(b);
     cudaFree(b->djobs);

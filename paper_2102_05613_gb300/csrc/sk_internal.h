@@ -11,6 +11,9 @@ constexpr uint32_t kPadTo = 32;      // Npad = round_up(N, 32)
 
 // Error codes written by kernels into the launch's error word.
 enum : int { kDevOk = 0, kDevTimeout = 1, kDevBounds = 2 };
+// JobDev::fault bits (sk_run_params.fault_inject; tests of the bounded waits)
+constexpr uint32_t kFaultWithholdRow = 1u;
+constexpr uint32_t kFaultWithholdTile = 2u;
 
 // One run as seen by the kernels.  Row-major layouts, leading dimension Npad:
 //   J[Npad][Npad] (int8 or float), s[chains][Npad] int8 (+-1, padding 0),
@@ -49,7 +52,8 @@ struct alignas(16) JobDev {
     // gtab = node factors F[V] (u32, 2^20 = 1), their inclusive prefix sums
     // (u64) and log2(F / 2^20) (float), each array 16-byte aligned
     const void* gtab;
-    uint32_t graph, arity, V, gpad_;
+    uint32_t graph, arity, V;
+    uint32_t fault;         // sk_run_params.fault_inject (tests of the bounded waits)
 };
 static_assert(sizeof(JobDev) % 16 == 0, "JobDev is copied as 16-byte words");
 
@@ -115,6 +119,9 @@ cudaError_t launch_start_batch(const StartJob* jobs_dev, uint32_t n, uint64_t ma
 // (position << 2 | code) of a violation, all ones when there is none
 // (couplings: position i * 2^16 + j, code 1 diagonal, 2 range or not finite,
 // 3 asymmetric; spins: position = index, code 1 not +-1).
+// Couplings of N spins drawn on the device from `seed` (Philox domain 2)
+// into the padded Npad x Npad matrix J (see gen_couplings_kernel).
+cudaError_t launch_gen_couplings(void* J, uint32_t kind, uint32_t N, uint32_t Npad, uint64_t seed, cudaStream_t st);
 cudaError_t launch_check_couplings(const void* J, uint32_t kind, uint32_t N, uint32_t Npad,
                                    unsigned long long* flag, cudaStream_t st);
 cudaError_t launch_check_spins(const int8_t* s, uint64_t n, unsigned long long* flag, cudaStream_t st);
@@ -170,7 +177,7 @@ cudaError_t launch_set_fields_batch(uint32_t kind, const RecomputeSet* sets, uin
 cudaError_t launch_recompute(uint32_t kind, const int8_t* s, void* h, float* out, void* s_op,
                              const void* j_op, double* dE, unsigned long long* stats, int* err,
                              uint32_t chains, uint32_t npad, uint32_t terms, uint32_t mode, double scale,
-                             cudaStream_t st);
+                             cudaStream_t st, uint32_t fault = 0);
 
 }  // namespace sk
 struct sk_run;

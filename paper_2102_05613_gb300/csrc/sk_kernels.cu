@@ -299,6 +299,45 @@ __global__ void __maxnreg__(16) check_couplings_kernel(const JT* __restrict__ J,
         if (code) atomicMin(flag, ((static_cast<unsigned long long>(i) << 16 | j) << 2) | code);
     }
 }
+// Couplings drawn on the device for an instance created without couplings
+// (sk_create_instance with couplings NULL): Philox4x32-10 with key = seed,
+// domain 2, one draw per pair i < j, shared by J_ij and J_ji:
+//   +-J:      block (j >> 7, i, 0, 2 << 24), bit j & 127 (word (j & 127) >> 5,
+//             bit j & 31): set -> -1, clear -> +1;
+//   Gaussian: block (j, i, 1, 2 << 24) = (w0, w1, w2, w3); two 53-bit
+//             uniforms u1 = (2^26 (w0 >> 5) + (w1 >> 6)) 2^-53 and u2 from
+//             (w2, w3) alike; the Box-Muller normal z = sqrt(-2 ln(1 - u1))
+//             cos(2 pi u2) in double precision, J_ij = (float)(z / sqrt(N)),
+//             a sample of N(0, 1/N).
+// The diagonal and the padding are 0.  One thread per element of the padded
+// matrix (each pair is drawn twice, once for each of its two elements).
+template <typename JT>
+__global__ void gen_couplings_kernel(JT* __restrict__ J, uint32_t N, uint32_t npad, uint32_t k0, uint32_t k1) {
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= npad) return;
+    for (uint32_t r = blockIdx.y; r < npad; r += gridDim.y) {
+        JT v = JT(0);
+        if (r < N && c < N && r != c) {
+            const uint32_t i = min(r, c), j = max(r, c);
+            if constexpr (sizeof(JT) == 1) {
+                const uint4 w = dev::philox4x32_10(make_uint4(j >> 7, i, 0u, 2u << 24), k0, k1);
+                const uint32_t b = j & 127u;
+                const uint32_t word = b < 32u ? w.x : b < 64u ? w.y : b < 96u ? w.z : w.w;
+                v = ((word >> (b & 31u)) & 1u) ? JT(-1) : JT(1);
+            } else {
+                const uint4 w = dev::philox4x32_10(make_uint4(j, i, 1u, 2u << 24), k0, k1);
+                const double u1 = (static_cast<double>(w.x >> 5) * 67108864.0 + static_cast<double>(w.y >> 6)) *
+                                  0x1p-53;
+                const double u2 = (static_cast<double>(w.z >> 5) * 67108864.0 + static_cast<double>(w.w >> 6)) *
+                                  0x1p-53;
+                const double z = sqrt(-2.0 * log(1.0 - u1)) * cos(6.283185307179586476925286766559 * u2);
+                v = static_cast<float>(z / sqrt(static_cast<double>(N)));
+            }
+        }
+        J[static_cast<size_t>(r) * npad + c] = v;
+    }
+}
+
 //   spins: code 1 for a value other than +-1; position = index.  A few CTAs
 //   per array (grid-stride loop), so that the check can run beside a
 //   resident step kernel without thousands of CTA launches.
@@ -507,6 +546,16 @@ cudaError_t launch_check_couplings(const void* J, uint32_t kind, uint32_t N, uin
         check_couplings_kernel<int8_t><<<grid, kCheckThreads, 0, st>>>(static_cast<const int8_t*>(J), N, Npad, flag);
     else
         check_couplings_kernel<float><<<grid, kCheckThreads, 0, st>>>(static_cast<const float*>(J), N, Npad, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gen_couplings(void* J, uint32_t kind, uint32_t N, uint32_t Npad, uint64_t seed, cudaStream_t st) {
+    const dim3 grid((Npad + 255) / 256, std::min<uint32_t>(Npad, 1024));
+    const uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
+    if (kind == 0)
+        gen_couplings_kernel<int8_t><<<grid, 256, 0, st>>>(static_cast<int8_t*>(J), N, Npad, k0, k1);
+    else
+        gen_couplings_kernel<float><<<grid, 256, 0, st>>>(static_cast<float*>(J), N, Npad, k0, k1);
     return cudaGetLastError();
 }
 

@@ -61,6 +61,7 @@ struct Job {
     std::vector<double> energies;
     std::vector<int8_t> spins;
     uint64_t flips = 0;
+    std::atomic<bool> cancel{false};  // set by sk_server_cancel while the job runs
 };
 
 }  // namespace
@@ -128,7 +129,7 @@ sk_status admit(sk_server* s, Job& j) {
         if (res->N != j.spec.N || res->kind != j.spec.kind || res->scale != j.spec.scale)
             return SK_ERR_INVALID_ARG;
         if (!res->inst) {
-            r = sk_create_instance(res->N, res->kind, res->host.data(), SK_MEM_HOST, res->scale, s->st,
+            r = sk_create_instance(res->N, res->kind, res->host.data(), SK_MEM_HOST, 0, res->scale, s->st,
                                    &res->inst);
             if (r != SK_OK) {
                 res->inst = nullptr;
@@ -140,7 +141,7 @@ sk_status admit(sk_server* s, Job& j) {
         j.shared = res;
         res->users++;
     } else {
-        r = sk_create_instance(j.spec.N, j.spec.kind, j.couplings.data(), SK_MEM_HOST, j.spec.scale, s->st,
+        r = sk_create_instance(j.spec.N, j.spec.kind, j.couplings.data(), SK_MEM_HOST, 0, j.spec.scale, s->st,
                                &inst);
         if (r != SK_OK) return r;
         j.own_inst = inst;
@@ -224,7 +225,20 @@ void loop(sk_server* s) {
         const auto tr0 = Clock::now();
         std::vector<std::shared_ptr<Job>> still;
         for (auto& j : s->active) {
-            if (sk::host_step(j->run) >= j->spec.steps) {
+            if (j->cancel.load()) {  // withdrawn while running: release, keep nothing
+                if (batch) {
+                    mcmcmc_batch_free(batch);
+                    batch = nullptr;
+                }
+                release(s, *j);
+                std::lock_guard<std::mutex> lk(s->mu);
+                j->status.state = SK_JOB_CANCELLED;
+                j->status.error = SK_ERR_CANCELLED;
+                j->status.t_done = since(s);
+                s->completed++;
+                s->done_cv.notify_all();
+                dirty = true;
+            } else if (sk::host_step(j->run) >= j->spec.steps) {
                 if (batch) {
                     mcmcmc_batch_free(batch);
                     batch = nullptr;
@@ -441,11 +455,42 @@ sk_status sk_server_result(sk_server* s, uint64_t ticket, double* energies, int8
         if (j->status.state == SK_JOB_QUEUED || j->status.state == SK_JOB_RUNNING) return SK_ERR_NOT_READY;
         s->jobs.erase(it);
     }
+    if (j->status.state == SK_JOB_CANCELLED) return SK_ERR_CANCELLED;
     if (j->status.state == SK_JOB_FAILED) return j->status.error ? j->status.error : SK_ERR_CUDA;
     if (energies) std::memcpy(energies, j->energies.data(), j->energies.size() * sizeof(double));
     if (spins) std::memcpy(spins, j->spins.data(), j->spins.size());
     if (flips) *flips = j->flips;
     return SK_OK;
+}
+
+sk_status sk_server_cancel(sk_server* s, uint64_t ticket) {
+    if (!s) return SK_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->jobs.find(ticket);
+    if (it == s->jobs.end()) return SK_ERR_INVALID_ARG;
+    Job& j = *it->second;
+    switch (j.status.state) {
+        case SK_JOB_CANCELLED:
+            return SK_OK;
+        case SK_JOB_QUEUED: {
+            for (auto q = s->queue.begin(); q != s->queue.end(); ++q)
+                if (q->get() == &j) {
+                    s->queue.erase(q);
+                    break;
+                }
+            j.status.state = SK_JOB_CANCELLED;
+            j.status.error = SK_ERR_CANCELLED;
+            j.status.t_done = since(s);
+            s->completed++;
+            s->done_cv.notify_all();
+            return SK_OK;
+        }
+        case SK_JOB_RUNNING:  // the worker releases it at the next quantum boundary
+            j.cancel = true;
+            return SK_OK;
+        default:
+            return SK_ERR_INVALID_ARG;
+    }
 }
 
 sk_status sk_server_wait_all(sk_server* s, uint64_t timeout_ns) {

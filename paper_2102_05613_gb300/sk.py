@@ -17,17 +17,19 @@ import numpy as np
 
 from . import build as _build
 
-SK_OK, SK_ERR_INVALID_ARG, SK_ERR_OOM, SK_ERR_CUDA, SK_ERR_TIMEOUT, SK_ERR_NOT_READY, SK_ERR_DEVICE = range(7)
+(SK_OK, SK_ERR_INVALID_ARG, SK_ERR_OOM, SK_ERR_CUDA, SK_ERR_TIMEOUT, SK_ERR_NOT_READY, SK_ERR_DEVICE,
+ SK_ERR_BUSY, SK_ERR_CANCELLED) = range(9)
 SK_J_PM1, SK_J_GAUSS = 0, 1
 SK_RULE_MCMCMC, SK_RULE_METROPOLIS = 0, 1
 SK_MEM_HOST, SK_MEM_DEVICE = 0, 1
 SK_MAX_K, SK_MAX_N = 256, 8192
 
 _STATUS = {0: "SK_OK", 1: "SK_ERR_INVALID_ARG", 2: "SK_ERR_OOM", 3: "SK_ERR_CUDA",
-           4: "SK_ERR_TIMEOUT", 5: "SK_ERR_NOT_READY", 6: "SK_ERR_DEVICE"}
+           4: "SK_ERR_TIMEOUT", 5: "SK_ERR_NOT_READY", 6: "SK_ERR_DEVICE", 7: "SK_ERR_BUSY",
+           8: "SK_ERR_CANCELLED"}
 
 # every symbol declared in include/sk_mcmcmc.h
-EXPORTS = ["sk_create_instance", "sk_set_couplings", "sk_destroy_instance", "sk_energy",
+EXPORTS = ["sk_create_instance", "sk_get_couplings", "sk_set_couplings", "sk_destroy_instance", "sk_energy",
            "mcmcmc_create", "mcmcmc_advance", "mcmcmc_run", "mcmcmc_reset", "mcmcmc_wait",
            "mcmcmc_observables", "mcmcmc_observables_nw", "mcmcmc_state", "mcmcmc_recompute", "mcmcmc_recompute_stats",
            "mcmcmc_trace", "mcmcmc_counters", "mcmcmc_free",
@@ -52,7 +54,8 @@ class RunParams(C.Structure):
                 ("init_spins", C.c_void_p), ("init_mem", C.c_uint32),
                 ("recompute_every", C.c_uint32), ("recompute_terms", C.c_uint32),
                 ("p_center", C.c_double), ("node_weighted", C.c_uint32), ("graph", C.c_uint32),
-                ("arity", C.c_uint32), ("depth", C.c_uint32), ("line_nodes", C.c_uint32)]
+                ("arity", C.c_uint32), ("depth", C.c_uint32), ("line_nodes", C.c_uint32),
+                ("fault_inject", C.c_uint32)]
 
 
 class RecomputeStats(C.Structure):
@@ -61,6 +64,7 @@ class RecomputeStats(C.Structure):
 
 
 SK_RECOMPUTE_CHECK, SK_RECOMPUTE_RESYNC, SK_RECOMPUTE_OUTPUT = 0, 1, 2
+SK_FAULT_WITHHOLD_ROW, SK_FAULT_WITHHOLD_TILE = 1, 2
 SK_GRAPH_STAR, SK_GRAPH_TREE, SK_GRAPH_LINE = 0, 1, 2
 
 
@@ -80,7 +84,8 @@ def lib(build_if_missing: bool = True):
         vp, u32, u64, d = C.c_void_p, C.c_uint32, C.c_uint64, C.c_double
         P = C.POINTER(C.c_void_p)
         sig = {
-            "sk_create_instance": [u32, u32, vp, u32, d, vp, P],
+            "sk_create_instance": [u32, u32, vp, u32, u64, d, vp, P],
+            "sk_get_couplings": [vp, vp, u32],
             "sk_set_couplings": [vp, vp, u32],
             "sk_destroy_instance": [vp],
             "sk_energy": [vp, vp, u32, u32, vp],
@@ -151,26 +156,41 @@ def _stream_handle(stream):
 class Instance:
     """sk_create_instance / sk_destroy_instance (couplings resident on the GPU)."""
 
-    def __init__(self, J, scale: float = 1.0, stream=None):
-        if isinstance(J, np.ndarray):
-            J = np.ascontiguousarray(J)
-            dt = J.dtype
+    def __init__(self, J, scale: float = 1.0, stream=None, *, N: int = 0, kind: int = SK_J_GAUSS, seed: int = 0):
+        """J: the couplings (numpy host array or torch CUDA tensor, int8 for
+        +-J, float32 for Gaussian), or None to draw N spins' couplings of
+        `kind` on the device from `seed` (see sk_create_instance)."""
+        if J is None:
+            if not 2 <= int(N) <= SK_MAX_N or kind not in (SK_J_PM1, SK_J_GAUSS):
+                raise ValueError("drawn couplings need 2 <= N <= SK_MAX_N and a coupling kind")
+            self.kind, self.N = int(kind), int(N)
+            p, mem = None, SK_MEM_HOST
         else:
-            dt = {"torch.int8": np.int8, "torch.float32": np.float32}[str(J.dtype)]
-        if dt == np.int8:
-            self.kind = SK_J_PM1
-        elif dt == np.float32:
-            self.kind = SK_J_GAUSS
-        else:
-            raise TypeError("couplings must be int8 (+-J) or float32 (Gaussian)")
-        self.N = int(J.shape[0])
+            if isinstance(J, np.ndarray):
+                J = np.ascontiguousarray(J)
+                dt = J.dtype
+            else:
+                dt = {"torch.int8": np.int8, "torch.float32": np.float32}[str(J.dtype)]
+            if dt == np.int8:
+                self.kind = SK_J_PM1
+            elif dt == np.float32:
+                self.kind = SK_J_GAUSS
+            else:
+                raise TypeError("couplings must be int8 (+-J) or float32 (Gaussian)")
+            self.N = int(J.shape[0])
+            p, mem = _ptr_mem(J)
         self.scale = float(scale)
         self._stream = stream
         h = C.c_void_p()
-        p, mem = _ptr_mem(J)
-        _check(lib().sk_create_instance(self.N, self.kind, p, mem, self.scale,
+        _check(lib().sk_create_instance(self.N, self.kind, p, mem, int(seed), self.scale,
                                         _stream_handle(stream), C.byref(h)))
         self.handle = h
+
+    def couplings(self) -> np.ndarray:
+        """sk_get_couplings: the N x N couplings as a host array."""
+        out = np.zeros((self.N, self.N), dtype=np.int8 if self.kind == SK_J_PM1 else np.float32)
+        _check(lib().sk_get_couplings(self.handle, out.ctypes.data_as(C.c_void_p), SK_MEM_HOST))
+        return out
 
     def set_couplings(self, J):
         p, mem = _ptr_mem(J if not isinstance(J, np.ndarray) else np.ascontiguousarray(J))
@@ -212,7 +232,7 @@ class Run:
                  max_records: int = 0, init=None, trace_chains: int = 0, trace_steps: int = 0,
                  recompute_every: int = 0, recompute_terms: int = 0, p_center: float = 0.0,
                  node_weighted: bool = False, graph: int = 0, arity: int = 0, depth: int = 0,
-                 line_nodes: int = 0):
+                 line_nodes: int = 0, fault_inject: int = 0):
         self.inst = inst
         self.chains, self.K, self.rule = int(chains), int(K), int(rule)
         self.record_every, self.max_records = int(record_every), int(max_records)
@@ -227,6 +247,7 @@ class Run:
         pr.p_center = float(p_center)
         pr.node_weighted = 1 if node_weighted else 0
         pr.graph, pr.arity, pr.depth, pr.line_nodes = int(graph), int(arity), int(depth), int(line_nodes)
+        pr.fault_inject = int(fault_inject)
         if init is not None:
             if isinstance(init, np.ndarray):
                 init = np.ascontiguousarray(init, dtype=np.int8)
@@ -488,10 +509,11 @@ class ServerStats(C.Structure):
                 ("retire_seconds", C.c_double), ("plan_seconds", C.c_double)]
 
 
-SK_JOB_QUEUED, SK_JOB_RUNNING, SK_JOB_DONE, SK_JOB_FAILED = range(4)
+SK_JOB_QUEUED, SK_JOB_RUNNING, SK_JOB_DONE, SK_JOB_FAILED, SK_JOB_CANCELLED = range(5)
 EXPORTS += ["sk_set_generation", "sk_set_couplings_many", "mcmcmc_reset_many", "mcmcmc_observables_many"]
 EXPORTS += ["sk_server_create", "sk_server_add_couplings", "sk_server_submit", "sk_server_poll",
-            "sk_server_result", "sk_server_wait_all", "sk_server_stats", "sk_server_destroy"]
+            "sk_server_result", "sk_server_wait_all", "sk_server_stats", "sk_server_destroy",
+            "sk_server_cancel"]
 
 
 def _server_sigs(L):
@@ -502,6 +524,7 @@ def _server_sigs(L):
            "sk_server_poll": [vp, u64, C.POINTER(JobStatus)],
            "sk_server_result": [vp, u64, vp, vp, C.POINTER(C.c_uint64)],
            "sk_server_wait_all": [vp, u64],
+           "sk_server_cancel": [vp, u64],
            "sk_server_stats": [vp, C.POINTER(ServerStats)],
            "sk_server_destroy": [vp]}
     for name, args in sig.items():
@@ -562,6 +585,10 @@ class Server:
                                              S.ctypes.data_as(C.c_void_p), C.byref(f)),
                       "sk_server_result")
         return E, S, f.value
+
+    def cancel(self, ticket: int):
+        """sk_server_cancel: withdraw a queued or running job."""
+        _check_server(lib().sk_server_cancel(self.handle, int(ticket)), "sk_server_cancel")
 
     def wait_all(self, timeout_ns: int = 0):
         _check_server(lib().sk_server_wait_all(self.handle, int(timeout_ns)), "sk_server_wait_all")

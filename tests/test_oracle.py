@@ -634,3 +634,61 @@ def test_high_temperature_energy_gaussian():
                    record_every=1000)
     got = r["E"][10:].mean()
     assert abs(got - want) < 0.08 * abs(want), (got, want)
+
+
+# ---------------------------------------------------------------------------
+# couplings drawn from a seed (Philox domain 2): the generator behind
+# sk_create_instance with NULL couplings, pinned by the properties its
+# definition fixes
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kind", [oracle.PM1, oracle.GAUSS])
+def test_generated_couplings_are_a_valid_instance(kind):
+    N = 200
+    J = oracle.gen_couplings(N, kind, 12345)
+    assert np.array_equal(J, J.T)
+    assert np.all(np.diag(J) == 0)
+    if kind == oracle.PM1:
+        assert set(np.unique(J[~np.eye(N, dtype=bool)])) == {-1, 1}
+    else:
+        assert np.all(np.isfinite(J))
+    assert not np.array_equal(J, oracle.gen_couplings(N, kind, 12346))   # another seed, another draw
+    assert np.array_equal(J, oracle.gen_couplings(N, kind, 12345))       # deterministic
+
+
+def test_generated_pm1_couplings_are_equiprobable_bits():
+    # the +-J signs are the block's bits: fair coin flips, independent of position
+    N = 700
+    J = oracle.gen_couplings(N, oracle.PM1, 7)
+    up = J[np.triu_indices(N, 1)]
+    n = up.size
+    z = (np.sum(up == 1) - n / 2) / math.sqrt(n / 4)
+    assert abs(z) < 4.5, z
+    # neighbouring columns (bits of one word) and rows are uncorrelated
+    a = J[np.triu_indices(N, 2)].astype(float)
+    b = np.roll(J, -1, axis=1)[np.triu_indices(N, 2)].astype(float)
+    assert abs(np.mean(a * b)) < 4.5 / math.sqrt(a.size)
+    # the mapping as defined: J_01 = -1 iff bit 1 of word 0 of block (0, 0, 0, 2 << 24)
+    w = oracle.philox([0, 0, 0, 2 << 24], [7, 0])
+    assert J[0, 1] == (-1 if (int(w[0]) >> 1) & 1 else 1)
+    w = oracle.philox([600 >> 7, 3, 0, 2 << 24], [7, 0])
+    b = 600 % 128
+    assert J[3, 600] == (-1 if (int(w[b // 32]) >> (b % 32)) & 1 else 1)
+
+
+def test_generated_gaussian_couplings_are_n01_over_n():
+    scipy_stats = pytest.importorskip("scipy.stats")
+    N = 600
+    J = oracle.gen_couplings(N, oracle.GAUSS, 99).astype(np.float64)
+    x = J[np.triu_indices(N, 1)] * math.sqrt(N)   # should be N(0, 1)
+    n = x.size
+    assert abs(x.mean()) < 4.5 / math.sqrt(n)
+    assert abs(x.var() - 1.0) < 4.5 * math.sqrt(2.0 / n)
+    assert scipy_stats.kstest(x, "norm").pvalue > 1e-3
+    # fourth moment of a normal: 3
+    assert abs(np.mean(x ** 4) - 3.0) < 4.5 * math.sqrt(96.0 / n)
+    # the Box-Muller recipe as defined, for one pair
+    w = [int(v) for v in oracle.philox([5, 2, 1, 2 << 24], [99, 0])]
+    u1 = ((w[0] >> 5) * 67108864.0 + (w[1] >> 6)) * 2.0 ** -53
+    u2 = ((w[2] >> 5) * 67108864.0 + (w[3] >> 6)) * 2.0 ** -53
+    z = math.sqrt(-2.0 * math.log(1.0 - u1)) * math.cos(2.0 * math.pi * u2)
+    assert abs(J[2, 5] - np.float32(z / math.sqrt(N))) <= np.spacing(np.float32(abs(J[2, 5])))
