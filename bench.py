@@ -935,9 +935,9 @@ def run_ours(args):
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "steps": args.e2e_steps, "ms_per_step": 1e3 * te / args.e2e_steps,
                "pipelined": "two run sets on two streams take the steps in turn"}
+        batch2.close()
         for r in runs2:
             r.close()
-        batch2.close()
         for i_ in insts2:
             i_.close()
 
@@ -951,9 +951,9 @@ def run_ours(args):
     sg = setgen_report(stream) if rank == 0 else None
     sweep = config2_sweep(stream, insts) if (rank == 0 and not args.no_sweep) else None
 
+    batch.close()
     for r in runs:
         r.close()
-    batch.close()
     for i in insts:
         i.close()
     ttt = ttt_measure(set(TTT_LINE_METHODS), TTT_BETA, 1) if (rank == 0 and not args.no_ttt) else None

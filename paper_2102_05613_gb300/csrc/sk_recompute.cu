@@ -133,6 +133,7 @@ struct Args {
     int* err;
     uint32_t chains, npad, kblocks, terms, mode;  // mode: 0 check, 1 resync, 2 output, 3 set fields
     uint32_t pm1;
+    uint32_t fault;                 // kFaultWithholdTile: tests of the bounded waits
 };
 
 // Several operand sets in one launch: the tensor maps and arguments of each
@@ -271,7 +272,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
                         const Args args0, const BatchJob* __restrict__ jobs, const BatchTask* __restrict__ tasks,
                         uint32_t ntasks, uint32_t tiles_n) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t full[NS], empty[NS], tfull[2], tempty[2];
+    __shared__ __align__(8) uint64_t full[NS], empty[NS], tfull[2], tempty[2], drain;
     __shared__ uint32_t tmem_holder;
     __shared__ int dead;
     // 128-byte-swizzled tiles must start on a 1024-byte boundary of shared memory
@@ -290,6 +291,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&tfull[i])) : "memory");
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(&tempty[i])), "r"(EW) : "memory");
         }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&drain)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         dead = 0;
     }
@@ -331,6 +333,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
     if (warp == 0) {
         if (lane == 0) {  // producer: A (spins) and B (couplings, term by term) tiles by TMA
             uint32_t g = 0;
+            uint32_t withheld = 0xFFFFFFFFu;  // a stage a test of the bounded waits leaves unfilled
             for (uint32_t t = blockIdx.x; t < ntasks && !*vdead; t += gridDim.x) {
                 const CUtensorMap* A;
                 const CUtensorMap* B[3];
@@ -350,6 +353,10 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
                         *vdead = 1;
                     }
                     if (*vdead) break;
+                    if ((a->fault & kFaultWithholdTile) && blockIdx.x == 0 && g == 0) {
+                        withheld = g;
+                        continue;
+                    }
                     const uint32_t term = i / a->kblocks, kb = i % a->kblocks;
                     unsigned char* sa = smem + st * STAGE_BYTES;
                     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(&full[st])),
@@ -360,6 +367,11 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
                            saddr(&full[st]));
                 }
             }
+            // the copies of the last NS stages issued have landed before the
+            // CTA may leave (at once after a normal run, where the MMA warp
+            // consumed them; bounded after an expired wait)
+            for (uint32_t q = g > NS ? g - NS : 0u; q < g; ++q)
+                if (q != withheld) wait_bounded(saddr(&full[q % NS]), (q / NS) & 1u);
         }
     } else if (warp == 1) {
         if (lane == 0) {  // MMA issuer: 4 MMAs of K = 32 bytes per stage into accumulator j % 2
@@ -396,6 +408,11 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
                 }
                 mma_commit(saddr(&tfull[b]));  // completes when the tile's MMAs have
             }
+            // every MMA issued has finished before the accumulators' tensor
+            // memory is released (at once after a normal run; bounded after an
+            // expired wait)
+            mma_commit(saddr(&drain));
+            wait_bounded(saddr(&drain), 0u);
         }
     } else {
         // epilogue warps 2..9: tensor-memory lane quadrant warp % 4, column
@@ -639,6 +656,7 @@ cudaError_t launch_set_fields_batch(uint32_t kind, const RecomputeSet* sets, uin
         b.args.terms = bf ? 3u : 1u;
         b.args.mode = 3;
         b.args.pm1 = bf ? 0u : 1u;
+        b.args.fault = 0u;
         for (uint32_t m0 = 0; m0 < q.chains; m0 += BM)
             for (uint32_t n0 = 0; n0 < q.npad; n0 += BN) tasks.push_back(BatchTask{i, m0, n0, 0});
     }
@@ -688,7 +706,7 @@ cudaError_t launch_set_fields_batch(uint32_t kind, const RecomputeSet* sets, uin
 cudaError_t launch_recompute(uint32_t kind, const int8_t* s, void* h, float* out, void* s_op,
                              const void* j_op, double* dE, unsigned long long* stats, int* err,
                              uint32_t chains, uint32_t npad, uint32_t terms, uint32_t mode, double scale,
-                             cudaStream_t st) {
+                             cudaStream_t st, uint32_t fault) {
     const bool bf = kind != 0;
     if (!bf) terms = 1;
     if (terms < 1 || terms > 3) return cudaErrorInvalidValue;
@@ -718,6 +736,7 @@ cudaError_t launch_recompute(uint32_t kind, const int8_t* s, void* h, float* out
     a.terms = terms;
     a.mode = mode;
     a.pm1 = bf ? 0u : 1u;
+    a.fault = fault;
     const uint32_t tiles_n = (npad + BN - 1) / BN;
     const uint32_t nt = ((chains + BM - 1) / BM) * tiles_n;
     if (nt == 0) return cudaSuccess;

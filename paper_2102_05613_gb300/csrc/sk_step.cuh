@@ -524,7 +524,9 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
         } else {
             first = __umulhi(cm.b0[t0 & (G - 1)].x, N);
         }
-        if (g.gl == 0 && !dead) {
+        // (a test of the bounded wait may withhold chain 0's first copy)
+        const bool withhold = (jb.fault & kFaultWithholdRow) && chain == 0u && t0 == 0u;
+        if (g.gl == 0 && !dead && !withhold) {
             dev::fence_proxy_async();
             dev::bulk_load(cm.row[t0 & 1u], Jrow(first), rowbytes, &cm.bar[t0 & 1u]);
         }
@@ -568,12 +570,19 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
         }
         if (STAGED && !dead) {
             // every lane waits; the outcome is made group-uniform
-            const bool okl = dev::mbar_wait_bounded(&cm.bar[buf], (phase >> buf) & 1u);
+            const uint32_t par = (phase >> buf) & 1u;
+            const bool okl = dev::mbar_wait_bounded(&cm.bar[buf], par);
             const bool ok = gballot(g, okl) == (G == 32 ? kFull : ((1u << G) - 1u));
             phase ^= 1u << buf;
             if (!ok) {
                 dead = true;
                 if (g.gl == 0) atomicExch(jb.err, kDevTimeout);
+                // let this group's copies in flight land before it can leave
+                // the kernel (each wait again bounded): the row just waited
+                // for and the next step's row, issued before the wait
+                dev::mbar_wait_bounded(&cm.bar[buf], par);
+                if (t + 1u < t1) dev::mbar_wait_bounded(&cm.bar[buf ^ 1u], (phase >> (buf ^ 1u)) & 1u);
+                __syncwarp(g.mask);
             }
         }
         // row a of this step: staged in shared memory, or read through L1 from J

@@ -1,0 +1,25 @@
+"""The measured memory ceilings the step kernel's roofline divides by
+(sk_peaks.h): positive, ordered as the hardware orders them (random 4-byte
+gathers below conflict-free 16-byte loads), and within a plausible factor of
+the nominal figures (shared memory 128 bytes per clock per SM; L2 below
+shared memory)."""
+import pytest
+
+from paper_2102_05613_gb300 import sk
+
+from gpu_util import need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def test_peak_probes_are_plausible():
+    torch = need_gpu()
+    props = torch.cuda.get_device_properties(0)
+    sms = props.multi_processor_count
+    vec = sk.peak_smem(sk.SK_PEAK_SMEM_VEC16, iters=256, reps=2)
+    gat = sk.peak_smem(sk.SK_PEAK_SMEM_GATHER4, iters=256, reps=2)
+    l2 = sk.peak_l2_read(32 << 20, passes=16, reps=2)
+    nominal_smem = sms * 128 * 2.1e9 / 1e9  # GB/s at the part's top clock
+    assert 0.2 * nominal_smem < vec < 1.05 * nominal_smem, (vec, nominal_smem)
+    assert 0.0 < gat < vec
+    assert 0.0 < l2 < vec
