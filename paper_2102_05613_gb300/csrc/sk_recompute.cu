@@ -33,6 +33,7 @@
 #include <algorithm>
 #include <cstring>
 #include <mutex>
+#include <set>
 #include <vector>
 
 #include "sk_internal.h"
@@ -44,8 +45,7 @@ constexpr uint32_t BM = 128, BN = 256, NS = 4;  // 4 pipeline stages, one CTA pe
 constexpr uint32_t TILE_A = BM * 128, TILE_B = BN * 128;  // bytes, 128 B of K per row
 constexpr uint32_t STAGE_BYTES = TILE_A + TILE_B;
 constexpr uint32_t EW = 8;                                 // epilogue warps: 2 per tensor-memory quadrant
-constexpr uint32_t EPI_BYTES = EW * 32 * 33 * 4;           // their 32 x 33 transposes
-constexpr uint32_t SMEM_BYTES = NS * STAGE_BYTES + EPI_BYTES + 1024;  // + 1 KB alignment slack
+constexpr uint32_t SMEM_BYTES = NS * STAGE_BYTES + 1024;  // + 1 KB alignment slack
 constexpr uint32_t TMEM_COLS = 512;                        // two 256-column accumulators
 constexpr uint32_t WS_THREADS = 64 + 32 * EW;              // producer, MMA, epilogue warps
 constexpr long long kBudget = 4000000000ll;  // ~2 s of clock cycles per wait
@@ -150,99 +150,101 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
+// Byte e (0..3) of a 32-bit word as a signed value.
+__device__ __forceinline__ int sbyte32(uint32_t w, int e) {
+    return static_cast<int>(static_cast<int32_t>(w << (24 - 8 * e)) >> 24);
+}
+__device__ __forceinline__ uint32_t word_of(const uint4& q, int e) {
+    return e == 0 ? q.x : e == 1 ? q.y : e == 2 ? q.z : q.w;
+}
+
 // The epilogue of one finished accumulator for one warp: accumulator rows
-// 32 q .. 32 q + 31 (chains row0 ..), columns c0 .. c1-1, read 32 columns at a
-// time (thread = row), transposed through the warp's 32 x 33 buffer T and
-// walked row by row with lane = column, so that every access to the fields
-// and spins in global memory is one contiguous 128-byte row segment.
-// Per-row sums are kept per lane and reduced once at the end.
-__device__ __forceinline__ void epilogue_rows(uint32_t taddr, float* T, const Args& args, uint32_t row0,
-                                              uint32_t n0, uint32_t c0, uint32_t c1, bool tile_ok) {
+// row0 .. row0 + 31 (tcgen05.ld 32x32b gives lane l the accumulator row
+// row0 + l), the NCB blocks of 32 columns starting at column c0.  Each lane
+// reads and writes its own row's segment of the fields and spins -- 128
+// bytes of int32 / float fields as eight 16-byte loads and 32 bytes of spins
+// as two -- so no transpose is needed, and the row's sum s (h - H) stays in
+// the lane (an int32 for +-J, exact; a float otherwise) until one
+// double-precision atomic per row.  A block's loads are issued before its
+// accumulator columns are read from tensor memory (the first block's before
+// the wait for the accumulator), so that their round trip covers that read.
+constexpr uint32_t NCB = BN / 2 / 32;  // column blocks per epilogue warp and tile
+// One column block's fields and spins of this lane's row (check and resync).
+struct RowBlock {
+    uint4 h[8], s[2];
+};
+__device__ __forceinline__ void load_row_block(RowBlock& rb, const Args& args, uint32_t row, uint32_t n, bool ok) {
+    if (args.mode < 2 && ok && n < args.npad) {  // npad is a multiple of 32
+        const size_t idx = static_cast<size_t>(row) * args.npad + n;  // 32-element aligned
+        const uint4* hp = reinterpret_cast<const uint4*>(static_cast<const unsigned int*>(args.h) + idx);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) rb.h[q] = __ldg(hp + q);
+        const uint4* sp = reinterpret_cast<const uint4*>(args.s + idx);
+        rb.s[0] = __ldg(sp);
+        rb.s[1] = __ldg(sp + 1);
+    }
+}
+// first: the first column block, loaded by the caller (before it waited for
+// the accumulator) with load_row_block(first, args, row0 + lane, n0 + c0, ..).
+__device__ __forceinline__ void epilogue_rows(uint32_t taddr, const Args& args, uint32_t row0, uint32_t n0,
+                                              uint32_t c0, bool tile_ok, const RowBlock& first) {
     const uint32_t lane = threadIdx.x & 31;
-    // per row r: this lane's part of sum_n s_n (h_n - H_n), an int32 (+-J) or
-    // a float (Gaussian) kept in the same 32-bit word
-    uint32_t rsum[32];
-    float pmax = 0.0f;
-    int imax = 0;
-    unsigned long long mism = 0;
+    const uint32_t row = row0 + lane;
+    const bool row_ok = tile_ok && row < args.chains;
+    const bool reads = args.mode < 2;
+    int isum = 0, imax = 0;
+    float fsum = 0.0f, pmax = 0.0f;
+    unsigned mism = 0;
+    RowBlock rb = first;
 #pragma unroll
-    for (int r = 0; r < 32; ++r) rsum[r] = 0u;  // 0 and 0.0f have the same bits
-    for (uint32_t col = c0; col < c1; col += 32) {
-        const uint32_t n = n0 + col + lane;
-        const bool col_ok = tile_ok && n0 + col < args.npad;  // npad is a multiple of 32
-        // check / resync: the 32 rows' maintained fields and spins are loaded
-        // first, so that their round trip covers the accumulator load and the
-        // transpose (each field is read once, then written once by this thread)
-        uint32_t hv[32];
-        int sv[32];
-        if (args.mode < 2) {
-#pragma unroll
-            for (int r = 0; r < 32; ++r) {
-                hv[r] = 0u;
-                sv[r] = 0;
-                if (col_ok && row0 + r < args.chains) {
-                    const size_t idx = static_cast<size_t>(row0 + r) * args.npad + n;
-                    hv[r] = __ldg(static_cast<const unsigned int*>(args.h) + idx);
-                    sv[r] = __ldg(args.s + idx);
-                }
-            }
-        }
+    for (uint32_t cb = 0; cb < NCB; ++cb) {
+        if (cb > 0) load_row_block(rb, args, row, n0 + c0 + 32u * cb, row_ok);
+        const uint32_t n = n0 + c0 + 32u * cb;
+        const bool ok = row_ok && n < args.npad;
+        const size_t idx = static_cast<size_t>(row) * args.npad + n;
         uint32_t v[32];
-        tmem_ld32(taddr + col, v);
-        __syncwarp();
+        tmem_ld32(taddr + c0 + 32u * cb, v);  // every lane: the load is warp-collective
+        if (!ok) continue;
+        if (args.mode >= 2) {  // output H, or the fields of a start state (h = H)
+            uint4* dst = args.mode == 2 ? reinterpret_cast<uint4*>(args.out + idx)
+                                        : reinterpret_cast<uint4*>(static_cast<unsigned int*>(args.h) + idx);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) T[j * 33 + lane] = __uint_as_float(v[j]);  // T[column][row]
-        __syncwarp();
-        if (args.mode == 2) {
-#pragma unroll
-            for (int r = 0; r < 32; ++r)
-                if (col_ok && row0 + r < args.chains)
-                    args.out[static_cast<size_t>(row0 + r) * args.npad + n] = T[lane * 33 + r];
-            continue;
-        }
-        if (args.mode == 3) {  // the fields of a start state: h = H, no statistics
-#pragma unroll
-            for (int r = 0; r < 32; ++r)
-                if (col_ok && row0 + r < args.chains) {
-                    const size_t idx = static_cast<size_t>(row0 + r) * args.npad + n;
-                    if (args.pm1)
-                        static_cast<int*>(args.h)[idx] = __float2int_rn(T[lane * 33 + r]);
-                    else
-                        static_cast<float*>(args.h)[idx] = T[lane * 33 + r];
+            for (int q = 0; q < 8; ++q) {
+                uint4 w = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                if (args.mode == 3 && args.pm1) {
+                    w.x = static_cast<uint32_t>(__float2int_rn(__uint_as_float(w.x)));
+                    w.y = static_cast<uint32_t>(__float2int_rn(__uint_as_float(w.y)));
+                    w.z = static_cast<uint32_t>(__float2int_rn(__uint_as_float(w.z)));
+                    w.w = static_cast<uint32_t>(__float2int_rn(__uint_as_float(w.w)));
                 }
+                dst[q] = w;
+            }
             continue;
         }
 #pragma unroll
-        for (int r = 0; r < 32; ++r) {
-            if (!col_ok || row0 + r >= args.chains) continue;
-            const float H = T[lane * 33 + r];
+        for (int k = 0; k < 32; ++k) {
+            const float H = __uint_as_float(v[k]);
+            const uint32_t hw = word_of(rb.h[k >> 2], k & 3);
+            const int sv = sbyte32(word_of(rb.s[k >> 4], (k >> 2) & 3), k & 3);
             if (args.pm1) {
-                const int d = static_cast<int>(hv[r]) - __float2int_rn(H);
+                const int d = static_cast<int>(hw) - __float2int_rn(H);
                 mism += d != 0;
                 imax = max(imax, abs(d));
-                rsum[r] = static_cast<uint32_t>(static_cast<int>(rsum[r]) + sv[r] * d);
+                isum += sv * d;
             } else {
-                const float d = __uint_as_float(hv[r]) - H;
+                const float d = __uint_as_float(hw) - H;
                 pmax = fmaxf(pmax, fabsf(d));
-                rsum[r] = __float_as_uint(fmaf(static_cast<float>(sv[r]), d, __uint_as_float(rsum[r])));
-                if (args.mode == 1)
-                    static_cast<float*>(args.h)[static_cast<size_t>(row0 + r) * args.npad + n] = H;
+                fsum = fmaf(static_cast<float>(sv), d, fsum);
             }
         }
-    }
-    if (tile_ok && args.mode < 2) {
-        // row sums: lane l holds row r's part for columns l (mod 32); transpose
-        __syncwarp();
+        if (args.mode == 1) {  // resync: the maintained fields become H
+            uint4* dst = reinterpret_cast<uint4*>(static_cast<unsigned int*>(args.h) + idx);
 #pragma unroll
-        for (int r = 0; r < 32; ++r)
-            T[r * 33 + lane] = args.pm1 ? static_cast<float>(static_cast<int>(rsum[r])) : __uint_as_float(rsum[r]);
-        __syncwarp();
-        const uint32_t c = row0 + lane;
-        if (c < args.chains) {
-            double rs = 0.0;
-            for (int l = 0; l < 32; ++l) rs += static_cast<double>(T[lane * 33 + l]);
-            atomicAdd(&args.dE[c], rs);
+            for (int q = 0; q < 8; ++q) dst[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
         }
+    }
+    if (tile_ok && reads) {
+        if (row_ok) atomicAdd(&args.dE[row], args.pm1 ? static_cast<double>(isum) : static_cast<double>(fsum));
         // the warp's maximum and mismatch count, then one atomic each (every
         // warp of every tile updates the same two words)
         if (args.pm1) {
@@ -251,7 +253,7 @@ __device__ __forceinline__ void epilogue_rows(uint32_t taddr, float* T, const Ar
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) pmax = fmaxf(pmax, __shfl_xor_sync(0xffffffffu, pmax, o));
         }
-        const unsigned mw = __reduce_add_sync(0xffffffffu, static_cast<unsigned>(mism));
+        const unsigned mw = __reduce_add_sync(0xffffffffu, mism);
         if (lane == 0) {
             const double dmax = args.pm1 ? static_cast<double>(imax) : static_cast<double>(pmax);
             atomicMax(&args.stats[0], static_cast<unsigned long long>(__double_as_longlong(dmax)));
@@ -418,7 +420,6 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
         // epilogue warps 2..9: tensor-memory lane quadrant warp % 4, column
         // half (warp - 2) / 4
         const uint32_t qd = warp & 3u, half = (warp - 2u) >> 2;
-        float* T = reinterpret_cast<float*>(smem + NS * STAGE_BYTES) + (warp - 2u) * (32 * 33);
         uint32_t j = 0;
         for (uint32_t t = blockIdx.x; t < ntasks; t += gridDim.x, ++j) {
             const CUtensorMap* A;
@@ -427,6 +428,10 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
             uint32_t m0, n0;
             task(t, A, B, a, m0, n0);
             const uint32_t b = j & 1u;
+            // the first column block's fields and spins do not depend on the
+            // accumulator: their loads go out before the wait for it
+            RowBlock first;
+            load_row_block(first, *a, m0 + qd * 32u + lane, n0 + half * (BN / 2), m0 + qd * 32u + lane < a->chains);
             // every lane waits; the outcome is made warp-uniform
             const bool ok = __all_sync(0xffffffffu, !*vdead && wait_bounded(saddr(&tfull[b]), (j >> 1) & 1u));
             if (!ok && lane == 0) {
@@ -435,8 +440,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const bool live = __all_sync(0xffffffffu, !*vdead);
-            epilogue_rows(tmem + ((qd * 32u) << 16) + 256u * b, T, *a, m0 + qd * 32u, n0, half * (BN / 2),
-                          (half + 1) * (BN / 2), ok && live);
+            epilogue_rows(tmem + ((qd * 32u) << 16) + 256u * b, *a, m0 + qd * 32u, n0, half * (BN / 2), ok && live,
+                          first);
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(saddr(&tempty[b]));
@@ -484,25 +489,59 @@ __global__ void spins_to_op_batch(const SegSpins* __restrict__ seg, uint32_t bf1
 // max over chains of |dE| = |-scale/2 sum s (h - H)| into stats[2]; clears dE.
 __global__ void finish_energy(double* dE, uint32_t chains, double scale, unsigned long long* stats) {
     const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= chains) return;
-    const double e = fabs(0.5 * scale * dE[c]);
-    dE[c] = 0.0;
-    atomicMax(&stats[2], static_cast<unsigned long long>(__double_as_longlong(e)));
+    double e = 0.0;
+    if (c < chains) {
+        e = fabs(0.5 * scale * dE[c]);
+        dE[c] = 0.0;
+    }
+    // the warp's largest drift, then one atomic per warp (non-negative doubles
+    // order as their bit patterns)
+    unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(e));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, b, o);
+        b = y > b ? y : b;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(&stats[2], b);
 }
 
 // Operand conversion: spins +-1 (padding 0) -> e4m3 bytes or bf16 words.
+// 16 spins per thread and iteration (n is a multiple of 32: rows of npad).
+__device__ __forceinline__ uint32_t e4m3_of4(uint32_t w) {  // four spins -> four e4m3 bytes
+    uint32_t o = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int v = static_cast<int>(static_cast<int32_t>(w << (24 - 8 * e)) >> 24);
+        o |= static_cast<uint32_t>(v == 0 ? 0u : (v > 0 ? 0x38u : 0xB8u)) << (8 * e);  // e4m3: +-1.0
+    }
+    return o;
+}
+__device__ __forceinline__ uint32_t bf16_of2(uint32_t w, int e) {  // spins e, e+1 -> two bf16 words
+    uint32_t o = 0;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int v = static_cast<int>(static_cast<int32_t>(w << (24 - 8 * (e + k))) >> 24);
+        o |= static_cast<uint32_t>(v == 0 ? 0u : (v > 0 ? 0x3F80u : 0xBF80u)) << (16 * k);  // bf16: +-1.0
+    }
+    return o;
+}
 __global__ void spins_to_e4m3(const int8_t* __restrict__ s, uint8_t* __restrict__ o, size_t n) {
-    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
+    const uint4* in = reinterpret_cast<const uint4*>(s);
+    uint4* out = reinterpret_cast<uint4*>(o);
+    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n / 16;
          i += static_cast<size_t>(gridDim.x) * blockDim.x) {
-        const int v = s[i];
-        o[i] = v == 0 ? 0 : (v > 0 ? 0x38 : 0xB8);  // e4m3: +-1.0
+        const uint4 w = in[i];
+        out[i] = make_uint4(e4m3_of4(w.x), e4m3_of4(w.y), e4m3_of4(w.z), e4m3_of4(w.w));
     }
 }
 __global__ void spins_to_bf16(const int8_t* __restrict__ s, uint16_t* __restrict__ o, size_t n) {
-    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
+    const uint4* in = reinterpret_cast<const uint4*>(s);
+    uint4* out = reinterpret_cast<uint4*>(o);
+    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n / 16;
          i += static_cast<size_t>(gridDim.x) * blockDim.x) {
-        const int v = s[i];
-        o[i] = v == 0 ? 0 : (v > 0 ? 0x3F80 : 0xBF80);  // bf16: +-1.0
+        const uint4 w = in[i];
+        out[2 * i] = make_uint4(bf16_of2(w.x, 0), bf16_of2(w.x, 2), bf16_of2(w.y, 0), bf16_of2(w.y, 2));
+        out[2 * i + 1] = make_uint4(bf16_of2(w.z, 0), bf16_of2(w.z, 2), bf16_of2(w.w, 0), bf16_of2(w.w, 2));
     }
 }
 // J in {-1, 0, +1} -> e4m3 bytes.
@@ -703,6 +742,57 @@ cudaError_t launch_set_fields_batch(uint32_t kind, const RecomputeSet* sets, uin
     return e;
 }
 
+namespace {
+// The dynamic shared-memory attribute of a recompute kernel variant, set once
+// per device and variant.
+template <typename F>
+cudaError_t smem_attribute(F kernel, int variant) {
+    static std::mutex mu;
+    static std::set<std::pair<int, int>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count({dev, variant})) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e == cudaSuccess) done.insert({dev, variant});
+    return e;
+}
+
+// Operand tensor maps by (spin operand, coupling operand, type, shape): a map
+// holds only addresses and shapes, so one encoded for the same buffers and
+// shape is valid again; a few recent entries are kept.
+cudaError_t cached_maps(const void* s_op, const void* j_op, bool bf, uint32_t chains, uint32_t npad, CUtensorMap* tA,
+                        CUtensorMap* tB) {
+    struct Entry {
+        const void *s_op, *j_op;
+        bool bf;
+        uint32_t chains, npad;
+        CUtensorMap A, B[3];
+    };
+    static std::mutex mu;
+    static std::vector<Entry> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    for (const Entry& c : cache)
+        if (c.s_op == s_op && c.j_op == j_op && c.bf == bf && c.chains == chains && c.npad == npad) {
+            *tA = c.A;
+            for (int t = 0; t < 3; ++t) tB[t] = c.B[t];
+            return cudaSuccess;
+        }
+    Entry c{s_op, j_op, bf, chains, npad, {}, {}};
+    cudaError_t e = make_map(&c.A, s_op, bf, chains, npad, BM);
+    const size_t term_bytes = static_cast<size_t>(npad) * npad * (bf ? 2 : 1);
+    for (uint32_t t = 0; t < 3 && e == cudaSuccess; ++t)
+        e = make_map(&c.B[t], static_cast<const unsigned char*>(j_op) + (bf ? t : 0) * term_bytes, bf, npad, npad, BN);
+    if (e != cudaSuccess) return e;
+    if (cache.size() >= 32) cache.erase(cache.begin());
+    cache.push_back(c);
+    *tA = c.A;
+    for (int t = 0; t < 3; ++t) tB[t] = c.B[t];
+    return cudaSuccess;
+}
+}  // namespace
+
 cudaError_t launch_recompute(uint32_t kind, const int8_t* s, void* h, float* out, void* s_op,
                              const void* j_op, double* dE, unsigned long long* stats, int* err,
                              uint32_t chains, uint32_t npad, uint32_t terms, uint32_t mode, double scale,
@@ -710,19 +800,18 @@ cudaError_t launch_recompute(uint32_t kind, const int8_t* s, void* h, float* out
     const bool bf = kind != 0;
     if (!bf) terms = 1;
     if (terms < 1 || terms > 3) return cudaErrorInvalidValue;
-    const size_t ns = static_cast<size_t>(chains) * npad;
+    const size_t ns = static_cast<size_t>(chains) * npad;  // a multiple of 32
     if (bf)
-        spins_to_bf16<<<grid1d(ns), 256, 0, st>>>(s, static_cast<uint16_t*>(s_op), ns);
+        spins_to_bf16<<<grid1d(ns / 16), 256, 0, st>>>(s, static_cast<uint16_t*>(s_op), ns);
     else
-        spins_to_e4m3<<<grid1d(ns), 256, 0, st>>>(s, static_cast<uint8_t*>(s_op), ns);
+        spins_to_e4m3<<<grid1d(ns / 16), 256, 0, st>>>(s, static_cast<uint8_t*>(s_op), ns);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    // the operand maps of this (spins, couplings, shape): encoded once and
+    // reused by later recomputes of the same buffers, so that the host work
+    // between the conversion and the main kernel stays short
     CUtensorMap tA, tB[3];
-    e = make_map(&tA, s_op, bf, chains, npad, BM);
-    const size_t term_bytes = static_cast<size_t>(npad) * npad * (bf ? 2 : 1);
-    for (uint32_t t = 0; t < 3 && e == cudaSuccess; ++t)
-        e = make_map(&tB[t], static_cast<const unsigned char*>(j_op) + (bf ? t : 0) * term_bytes, bf, npad, npad, BN);
-    if (e != cudaSuccess) return e;
+    if ((e = cached_maps(s_op, j_op, bf, chains, npad, &tA, tB)) != cudaSuccess) return e;
     Args a;
     a.h = h;
     a.s = s;
@@ -742,15 +831,11 @@ cudaError_t launch_recompute(uint32_t kind, const int8_t* s, void* h, float* out
     if (nt == 0) return cudaSuccess;
     const uint32_t grid = std::min<uint32_t>(nt, static_cast<uint32_t>(sm_count()));
     if (bf) {
-        e = cudaFuncSetAttribute(recompute_ws_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 SMEM_BYTES);
-        if (e != cudaSuccess) return e;
+        if ((e = smem_attribute(recompute_ws_kernel<false, false>, 0)) != cudaSuccess) return e;
         recompute_ws_kernel<false, false><<<grid, WS_THREADS, SMEM_BYTES, st>>>(tA, tB[0], tB[1], tB[2], a, nullptr,
                                                                                nullptr, nt, tiles_n);
     } else {
-        e = cudaFuncSetAttribute(recompute_ws_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 SMEM_BYTES);
-        if (e != cudaSuccess) return e;
+        if ((e = smem_attribute(recompute_ws_kernel<true, false>, 1)) != cudaSuccess) return e;
         recompute_ws_kernel<true, false><<<grid, WS_THREADS, SMEM_BYTES, st>>>(tA, tB[0], tB[0], tB[0], a, nullptr,
                                                                               nullptr, nt, tiles_n);
     }
