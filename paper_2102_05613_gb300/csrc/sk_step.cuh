@@ -487,6 +487,10 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
     // search and draws the next step's sites during the current step
     constexpr bool KEEPW = UNROLL >= 8;
     constexpr bool AHEAD = STAGED || KEEPW;
+    // staged rows in the few-chain variant: sites drawn two steps ahead, so
+    // that the copy of the next step's row goes out at the start of a step
+    // with no Philox rounds in front of it
+    constexpr bool AHEAD2 = STAGED && KEEPW && RULE == 0;
     const Grp<G> g;
     // next record point (0: none; a record follows step t when t + 1 == next_rec)
     uint32_t next_rec = jb.record_every ? (t0 / jb.record_every + 1u) * jb.record_every : 0u;
@@ -513,6 +517,7 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
 
     fill_block0<G>(cm.b0, t0 & ~static_cast<uint32_t>(G - 1), chain, c3, k0, k1, g);
     uint32_t site[2 * NB];  // packed sites of this step (site_of)
+    uint32_t site1[AHEAD2 ? 2 * NB : 1];  // AHEAD2: the sites of the next step
 
     if constexpr (!STAGED && AHEAD && RULE == 0) draw_sites<NB, G>(site, t0, chain, c3, k0, k1, nblk, N, g);
     // prologue (staged rows): draw the first step and stage its row
@@ -521,6 +526,7 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
         if constexpr (RULE == 0) {
             draw_sites<NB, G>(site, t0, chain, c3, k0, k1, nblk, N, g);
             first = gshfl(g, site[0], 0) & 0xFFFFu;
+            if constexpr (AHEAD2) draw_sites<NB, G>(site1, t0 + 1u, chain, c3, k0, k1, nblk, N, g);
         } else {
             first = __umulhi(cm.b0[t0 & (G - 1)].x, N);
         }
@@ -553,7 +559,9 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
         uint32_t nsite[2 * NB];
         if (STAGED && t + 1u < t1) {
             uint32_t nx;
-            if constexpr (RULE == 0) {
+            if constexpr (AHEAD2) {
+                nx = gshfl(g, site1[0], 0) & 0xFFFFu;
+            } else if constexpr (RULE == 0) {
                 draw_sites<NB, G>(nsite, t + 1u, chain, c3, k0, k1, nblk, N, g);
                 nx = gshfl(g, nsite[0], 0) & 0xFFFFu;
             } else {
@@ -618,6 +626,7 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                 // ---- MCMCMC: K proposals on the uniform-root star ----
                 // (few-chain variant: the next step's sites, interleaved with this step's work)
                 if constexpr (!STAGED && AHEAD) draw_sites<NB, G>(nsite, t + 1u, chain, c3, k0, k1, nblk, N, g);
+                if constexpr (AHEAD2) draw_sites<NB, G>(nsite, t + 2u, chain, c3, k0, k1, nblk, N, g);
                 const unsigned long long U0 = (static_cast<unsigned long long>(b0.y) << 32) | b0.x;
                 const bool leaf = U0 >= dev::at_use(jb.root_thr);
                 const uint32_t a = gshfl(g, site[0], 0) & 0xFFFFu;
@@ -781,7 +790,13 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
             if (t < trace_end && g.gl == 0) jb.trace[static_cast<size_t>(chain) * jb.trace_steps + t] = sel;
             __syncwarp(g.mask);
         }
-        if constexpr (RULE == 0 && AHEAD) {
+        if constexpr (AHEAD2) {
+#pragma unroll
+            for (int q = 0; q < 2 * NB; ++q) {
+                site[q] = site1[q];
+                site1[q] = nsite[q];
+            }
+        } else if constexpr (RULE == 0 && AHEAD) {
 #pragma unroll
             for (int q = 0; q < 2 * NB; ++q) site[q] = nsite[q];
         }
