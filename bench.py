@@ -245,6 +245,18 @@ def recompute_report(stream, peaks, fp8_measured=None):
 # ---------------------------------------------------------------------------
 # single-chain latency: +-J N = 64 (J seed 0), K = 8, beta = 1, 1e5 steps
 # ---------------------------------------------------------------------------
+def dependent_shuffles(G, wide):
+    """Warp-collective rounds on one MCMCMC step's critical path with G lanes
+    per chain (the few-chain variant): the broadcast of site a, the group
+    minimum (one redux), the inclusive scan of the slot weights (log2 G
+    shuffle levels; 64-bit +-J weights move as two shuffles issued together),
+    the total's broadcast, the ballot of the lanes past the draw and the
+    broadcast of the chosen slot."""
+    lg = int(math.log2(G))
+    return {"shuffle_rounds": 1 + lg + 1 + 1, "redux": 1, "ballot": 1,
+            "shuffle_instructions": 1 + lg * (2 if wide else 1) + (2 if wide else 1) + 1}
+
+
 def latency_report(stream):
     import torch
     from paper_2102_05613_gb300 import inputs, sk
@@ -261,10 +273,53 @@ def latency_report(stream):
     b.record(stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b)
+    batch = sk.Batch([run])
+    layout = batch.classes()[0]
+    batch.close()
     run.close()
     inst.close()
     return {"workload": "+-J SK N=64, J seed 0, one chain, MCMCMC K=8, beta=1, 1e5 steps, Philox seed 1",
-            "ns_per_step": 1e6 * ms / steps, "candidate_configs_per_s": 8 * steps / (ms / 1e3)}
+            "ns_per_step": 1e6 * ms / steps, "candidate_configs_per_s": 8 * steps / (ms / 1e3),
+            "layout": {"lanes_per_chain": layout[1], "warps_per_cta": layout[3]},
+            "dependent_collectives_per_step": dependent_shuffles(layout[1], True)}
+
+
+def run_latency(args):
+    """One-chain step times (the latency regime): config 1 and the Gaussian
+    N = 1024 instance of the thermalisation runs at several K, and Metropolis;
+    default layouts and autotuned ones, best of 3 timed launches."""
+    import torch
+    from paper_2102_05613_gb300 import inputs, sk
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    out = {"config1": latency_report(stream), "gauss_n1024_one_chain": {}}
+    J = inputs.couplings_gauss(TTT_N, 0)
+    inst = sk.Instance(J, stream=stream)
+    for name, rule, Kt in (("metropolis", 1, 1), ("mcmcmc_k8", 0, 8), ("mcmcmc_k32", 0, 32),
+                           ("mcmcmc_k128", 0, 128)):
+        res = {}
+        for tuned in (False, True):
+            run = sk.Run(inst, chains=1, K=Kt, rule=rule, beta=TTT_BETA, seed=1)
+            b = sk.Batch([run])
+            if tuned:
+                b.autotune(trial_steps=64)
+            b.advance(500)
+            best = float("inf")
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                b.advance(20000)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                best = min(best, 1e6 * e0.elapsed_time(e1) / 20000)
+            res["autotuned" if tuned else "default"] = {"ns_per_step": best, "layout": b.classes()[0]}
+            b.close()
+            run.close()
+        out["gauss_n1024_one_chain"][name] = res
+    inst.close()
+    print(json.dumps(out), flush=True)
+    return 0
 
 
 # ---------------------------------------------------------------------------
@@ -308,6 +363,12 @@ TTT_METHODS = [("metropolis", 1, 1, 1 << 23, {}),
                ("mcmcmc_k2", 0, 2, 1 << 23, {}), ("mcmcmc_k4", 0, 4, 1 << 22, {}),
                ("mcmcmc_k8", 0, 8, 1 << 22, {}), ("mcmcmc_k16", 0, 16, 1 << 21, {}),
                ("mcmcmc_k32", 0, 32, 1 << 21, {}), ("mcmcmc_k128", 0, 128, 1 << 20, {}),
+               # the root distribution of the star (App. B.2 leaves p_r free): the centre
+               # as the root with probability p_center, each leaf with (1 - p_center)/K
+               ("mcmcmc_k32_pc0.5", 0, 32, 1 << 21, dict(p_center=0.5)),
+               ("mcmcmc_k32_pc0.05", 0, 32, 1 << 21, dict(p_center=0.05)),
+               ("mcmcmc_k128_pc0.5", 0, 128, 1 << 20, dict(p_center=0.5)),
+               ("mcmcmc_k128_pc0.05", 0, 128, 1 << 20, dict(p_center=0.05)),
                ("line_128", 0, 1, 1 << 16, dict(graph=2, line_nodes=128)),
                ("tree2_d7", 0, 1, 1 << 15, dict(graph=1, arity=2, depth=7)),
                ("tree3_d5", 0, 1, 1 << 14, dict(graph=1, arity=3, depth=5)),
@@ -357,8 +418,8 @@ def ttt_measure(only, beta, scale):
         s_per_step = a.elapsed_time(b) / 1e3 / T
         curves[name] = dict(R=R, T=T, e=E.mean(axis=1) / TTT_N, per_chain=E / TTT_N,
                             s_per_step=s_per_step, acc=float(acc.mean()) / R, geometry=geometry,
-                            nodes=Kt + 1 if not gkw else (gkw.get("line_nodes") or
-                                                          (gkw["arity"] ** (gkw["depth"] + 1) - 1) // (gkw["arity"] - 1)))
+                            nodes=Kt + 1 if not gkw.get("graph") else (gkw.get("line_nodes") or
+                                                                       (gkw["arity"] ** (gkw["depth"] + 1) - 1) // (gkw["arity"] - 1)))
         run.close()
     # e_inf: mean of the last half of the K=128 run's records; sigma: the
     # equilibrium fluctuation of one record (its chain mean) over that half,
@@ -1002,6 +1063,8 @@ def main():
                     help="chains of the --graph-one-chain case (1: the latency case)")
     ap.add_argument("--graph-one-chain", action="store_true",
                     help="the graph kernel's single-chain latency case (binary tree, depth 7)")
+    ap.add_argument("--latency", action="store_true",
+                    help="one-chain step times (config 1, Gaussian N=1024 at several K, Metropolis)")
     ap.add_argument("--ttt", action="store_true",
                     help="time-to-thermalise comparison instead of the throughput line")
     ap.add_argument("--no-recompute", action="store_true",
@@ -1025,6 +1088,8 @@ def main():
         return run_reference(args)
     if args.ttt:
         return run_ttt(args)
+    if args.latency:
+        return run_latency(args)
     if args.graph_one_chain:
         return run_graph_one_chain(args)
     if args.config == "uneven":
