@@ -284,40 +284,65 @@ def latency_report(stream):
             "dependent_collectives_per_step": dependent_shuffles(layout[1], True)}
 
 
+def _one_chain_ns(batch, stream, steps=20000):
+    """Best of 3 timed launches of `steps` steps (CUDA events), ns per step."""
+    import torch
+    batch.advance(500)
+    best = float("inf")
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        batch.advance(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        best = min(best, 1e6 * e0.elapsed_time(e1) / steps)
+    return best
+
+
+LATENCY_CLUSTERS = {64: (1, 2, 4), 512: (8, 16), 1024: ()}
+
+
 def run_latency(args):
-    """One-chain step times (the latency regime): config 1 and the Gaussian
-    N = 1024 instance of the thermalisation runs at several K, and Metropolis;
-    default layouts and autotuned ones, best of 3 timed launches."""
+    """One-chain step times (the latency regime): config 1 and Gaussian
+    instances of N = 1024 (the thermalisation runs) and N = 512 (whose columns
+    of J fit a cluster's shared memory) at several K, and Metropolis; default
+    layouts, autotuned ones and forced cluster-per-chain layouts, best of 3
+    timed launches."""
     import torch
     from paper_2102_05613_gb300 import inputs, sk
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
-    out = {"config1": latency_report(stream), "gauss_n1024_one_chain": {}}
-    J = inputs.couplings_gauss(TTT_N, 0)
-    inst = sk.Instance(J, stream=stream)
-    for name, rule, Kt in (("metropolis", 1, 1), ("mcmcmc_k8", 0, 8), ("mcmcmc_k32", 0, 32),
-                           ("mcmcmc_k128", 0, 128)):
-        res = {}
-        for tuned in (False, True):
-            run = sk.Run(inst, chains=1, K=Kt, rule=rule, beta=TTT_BETA, seed=1)
-            b = sk.Batch([run])
-            if tuned:
-                b.autotune(trial_steps=64)
-            b.advance(500)
-            best = float("inf")
-            for _ in range(3):
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                torch.cuda.synchronize()
-                e0.record(stream)
-                b.advance(20000)
-                e1.record(stream)
-                torch.cuda.synchronize()
-                best = min(best, 1e6 * e0.elapsed_time(e1) / 20000)
-            res["autotuned" if tuned else "default"] = {"ns_per_step": best, "layout": b.classes()[0]}
-            b.close()
-            run.close()
-        out["gauss_n1024_one_chain"][name] = res
+    out = {"config1": latency_report(stream)}
+    # config 1 in the cluster layouts
+    inst = sk.Instance(inputs.couplings_pm1(64, 0), stream=stream)
+    for C in LATENCY_CLUSTERS[64]:
+        run = sk.Run(inst, chains=1, K=8, beta=1.0, seed=1)
+        b = sk.Batch([run])
+        b.set_cluster(C)
+        out["config1"][f"cluster{C}_ns_per_step"] = _one_chain_ns(b, stream)
+        b.close()
+        run.close()
     inst.close()
+    for N in (1024, 512):
+        key = f"gauss_n{N}_one_chain"
+        out[key] = {}
+        inst = sk.Instance(inputs.couplings_gauss(N, 0), stream=stream)
+        for name, rule, Kt in (("metropolis", 1, 1), ("mcmcmc_k8", 0, 8), ("mcmcmc_k32", 0, 32),
+                               ("mcmcmc_k128", 0, 128)):
+            res = {}
+            for mode in ("default", "autotuned") + tuple(f"cluster{C}" for C in LATENCY_CLUSTERS[N]):
+                run = sk.Run(inst, chains=1, K=Kt, rule=rule, beta=TTT_BETA, seed=1)
+                b = sk.Batch([run])
+                if mode == "autotuned":
+                    b.autotune(trial_steps=64)
+                elif mode.startswith("cluster"):
+                    b.set_cluster(int(mode[7:]))
+                res[mode] = {"ns_per_step": _one_chain_ns(b, stream), "layout": b.classes()[0]}
+                b.close()
+                run.close()
+            out[key][name] = res
+        inst.close()
     print(json.dumps(out), flush=True)
     return 0
 

@@ -196,7 +196,9 @@ typedef struct {
     uint32_t fault_inject;  /* tests of the failure path only, 0 otherwise:     */
                             /*   SK_FAULT_WITHHOLD_ROW withholds the first row  */
                             /*   copy of chain 0 in a layout with staged rows   */
-                            /*   (mcmcmc_batch_set_layout staging 1);           */
+                            /*   (mcmcmc_batch_set_layout staging 1), or the    */
+                            /*   last row of the first CTA's slice of J in the  */
+                            /*   cluster layout (mcmcmc_batch_set_cluster);     */
                             /*   SK_FAULT_WITHHOLD_TILE withholds the first     */
                             /*   operand tile of the first CTA of each field    */
                             /*   recompute (mcmcmc_recompute): the waits for    */
@@ -389,7 +391,9 @@ sk_status mcmcmc_batch_replay(sk_batch* b, uint32_t times);
  * value K allows and each warps-per-CTA value that fits in shared memory
  * (the CTA size also selects the kernel's register budget) and keeps the
  * fastest; graph classes try 1, 2, 4, 8 and 16 warps per chain with every
- * even number of chains per CTA that fits.
+ * even number of chains per CTA that fits; star classes of at most 64 chains
+ * also try the cluster-per-chain layout (mcmcmc_batch_set_cluster) at every
+ * cluster size and chains-per-cluster value the class can take.
  * Trials start from a copy of the runs' state, which is restored afterwards,
  * and run with records and traces off: the runs' trajectories, records and
  * step counters are unchanged.  *warps_per_cta (may be NULL) receives the
@@ -419,6 +423,36 @@ sk_status mcmcmc_batch_autotune(sk_batch* b, uint32_t trial_steps, uint32_t* war
  */
 sk_status mcmcmc_batch_set_layout(sk_batch* b, uint32_t lanes, uint32_t staging);
 
+/*
+ * mcmcmc_batch_set_cluster: forces the cluster-per-chain layout (ctas > 0) or
+ * returns to the warp layouts (ctas = 0) for every star launch class that can
+ * take it; the other classes keep their layout.
+ *   ctas     CTAs per thread-block cluster: 1, 2, 4, 8 or 16 (16 needs the
+ *            device's non-portable cluster size).  CTA r of a cluster holds
+ *            the slice [r Npad/ctas, (r+1) Npad/ctas) of each of its chains'
+ *            spins and fields and the same columns of every row of J, copied
+ *            once per work item into its shared memory; the owner of each
+ *            proposed site publishes what the step needs about it to every
+ *            CTA of the cluster, one cluster barrier per step, and every CTA
+ *            makes the same choice (sk_cluster.cuh in the sources).  A class
+ *            can take it when each run's Npad/ctas spins make whole 16-byte
+ *            rows of J (int8: 16 spins, fp32: 4), K <= 256, the run records
+ *            no node-weighted energies, and N (Npad/ctas) bytes of J (x4 for
+ *            Gaussian couplings) plus the chains' slices fit in one CTA's
+ *            shared memory (about 220 KB): e.g. N <= 1536 for +-J and
+ *            N <= 896 for Gaussian couplings at 16 CTAs;
+ *   chains   chains per cluster (one warp each in every CTA): 1, 2, 4 or 8;
+ *            0 = 2, or 1 when every run of the class has one chain; 1 is
+ *            raised to 2 for runs of several chains (overlap pairs share a
+ *            cluster).
+ * Results do not depend on it: trajectories equal those of whole-warp
+ * chains (mcmcmc_batch_set_layout lanes 32) bit for bit, records up to the
+ * order of the energy's partial sums (Gaussian couplings).  Drops autotuned
+ * choices and a captured graph.  SK_ERR_CUDA when no cluster of that size can
+ * be resident; the previous plan is kept on any error.
+ */
+sk_status mcmcmc_batch_set_cluster(sk_batch* b, uint32_t ctas, uint32_t chains);
+
 /* Launch geometry of the batch (for reports): the largest grid, warps per
  * CTA and dynamic shared memory of the first launch class, total work items. */
 sk_status mcmcmc_batch_info(const sk_batch* b, uint32_t* grid, uint32_t* warps_per_cta,
@@ -433,7 +467,9 @@ sk_status mcmcmc_batch_info(const sk_batch* b, uint32_t* grid, uint32_t* warps_p
  * class, so small-N runs keep many chains per CTA next to large-N runs.
  * *count receives the number of classes; desc (6 x max uint32, may be NULL)
  * receives per class: kernel class, lanes per chain, shared bytes per chain,
- * warps per CTA, work items, CTAs.
+ * warps per CTA, work items, CTAs.  Cluster-per-chain classes report kernel
+ * class 1024 + 2 kind + rule, 32 x (CTAs per cluster) lanes per chain, the
+ * bytes of one chain's slices per CTA and chains per cluster as warps per CTA.
  */
 sk_status mcmcmc_batch_classes(const sk_batch* b, uint32_t max, uint32_t* count, uint32_t* desc);
 

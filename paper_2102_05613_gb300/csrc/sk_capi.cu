@@ -195,18 +195,25 @@ struct sk_batch {
         uint32_t stage;          // row a staged by TMA (1) or read through L1 (0)
         uint32_t per_chain_staged, per_chain_direct;
         uint32_t per_chain;      // shared memory per chain
-        uint32_t W;              // warps per CTA
+        uint32_t W;              // warps per CTA (cluster classes: chains per cluster)
         uint32_t nw = 1;         // graph classes: warps per chain
         uint32_t first_item, n_items, grid;
+        // cluster-per-chain layout: CTAs per cluster (0: a warp layout), the
+        // J columns each CTA holds, the coupling kind, rule and Philox blocks
+        // per lane of the kernel
+        uint32_t cluster = 0, jbytes = 0, kind = 0, rule = 0, nb = 0;
     };
     std::vector<sk_run*> runs;
     std::vector<Class> classes;
     std::map<uint64_t, uint32_t> tuned;  // key -> (stage << 16) | (G << 8) | W chosen by the autotuner
-                                         // (graph classes: (warps per chain << 16) | (32 << 8) | W)
+                                         // (graph classes: (warps per chain << 16) | (32 << 8) | W;
+                                         // cluster layout: (CTAs per cluster << 24) | (32 << 8) | chains)
     uint32_t W_override = 0;             // warps_per_cta given at creation (0: as many as fit)
     uint32_t G_override = 0;             // mcmcmc_batch_set_layout lanes (0: default; graph classes
                                          // take lanes / 32 warps per chain when lanes >= 64)
     uint32_t S_override = 0;             // mcmcmc_batch_set_layout staging (0: default = staged)
+    uint32_t C_override = 0;             // mcmcmc_batch_set_cluster CTAs per cluster (0: warp layouts)
+    uint32_t CW_override = 0;            // mcmcmc_batch_set_cluster chains per cluster (0: default)
     JobDev* djobs = nullptr;
     WorkItem* ditems = nullptr;
     uint32_t* dqueue = nullptr;  // one work counter per class (up to kMaxClasses)
@@ -1148,6 +1155,9 @@ sk_status mcmcmc_free(sk_run* r) {
 namespace {
 
 constexpr uint32_t kMaxClasses = 64;
+// The autotuner tries the cluster-per-chain layout for classes of at most
+// this many chains (where one chain's latency, not throughput, is at stake).
+constexpr uint64_t kClusterTuneChains = 64;
 
 uint32_t run_per_chain(const sk_run* r, bool staged = true) {
     return static_cast<uint32_t>((sk::warp_smem_bytes(r->inst->Npad, r->inst->kind, staged) + 127) / 128 * 128);
@@ -1184,6 +1194,47 @@ uint32_t fit_warps(uint32_t per_chain, uint32_t G) {
     uint32_t w = static_cast<uint32_t>(std::min<size_t>(32, kSmemBudget / (static_cast<size_t>(per_chain) * spw)));
     if (G == 32) w &= ~1u;
     return w;
+}
+
+// The cluster-per-chain layout for the star class of runs `idx` with C CTAs
+// per cluster and W chains per cluster (0: 2, or 1 when every run has one
+// chain; W = 1 only then, so that overlap pairs share a cluster).  Returns
+// false, with c untouched, when the class cannot take it: node-weighted
+// records, K beyond 2 Philox blocks per lane, a slice that is not whole
+// 16-byte units or shared memory that does not fit.
+bool plan_cluster_class(const sk_batch* b, const std::vector<uint32_t>& idx, uint32_t C, uint32_t W,
+                        sk_batch::Class& c) {
+    const sk_run* r0 = b->runs[idx[0]];
+    if (run_nw(r0) || r0->p.graph) return false;
+    bool single = true;
+    uint32_t nb = 0;
+    size_t jbytes = 0, pc = 0;
+    for (uint32_t i : idx) {
+        const sk_run* r = b->runs[i];
+        if (r->chains > 1) single = false;
+        const uint32_t n = sk::blocks_per_lane(r->p.rule, r->p.K, 32);
+        if (n == 0 || n > 2) return false;
+        nb = std::max(nb, n);
+        if (!sk::cluster_shape_ok(r->inst->kind, r->inst->Npad, C)) return false;
+        jbytes = std::max(jbytes, sk::cluster_slice_bytes(r->inst->kind, r->inst->N, r->inst->Npad, C));
+    }
+    for (uint32_t i : idx) pc = std::max(pc, sk::cluster_chain_bytes(r0->p.rule, nb, b->runs[i]->inst->Npad, C));
+    if (W == 0) W = single ? 1u : 2u;
+    if (W == 1 && !single) W = 2;
+    if (W != 1 && W != 2 && W != 4 && W != sk::kClusterMaxChains) return false;
+    if (jbytes + W * pc > kSmemBudget) return false;
+    c.cluster = C;
+    c.W = W;
+    c.G = 32 * C;
+    c.gmin = 32;
+    c.stage = 0;
+    c.per_chain = static_cast<uint32_t>(pc);
+    c.jbytes = static_cast<uint32_t>(jbytes);
+    c.kind = r0->inst->kind;
+    c.rule = r0->p.rule;
+    c.nb = nb;
+    c.cls = 1024 + static_cast<int>(c.kind) * 2 + static_cast<int>(c.rule);
+    return true;
 }
 
 // Work items of the batch, grouped by launch class, each class with its own
@@ -1257,10 +1308,34 @@ sk_status plan_batch(sk_batch* b) {
             classes.push_back(c);
             continue;
         }
+        {  // the cluster-per-chain layout: autotuned, or forced by mcmcmc_batch_set_cluster
+            auto tc = b->tuned.find(c.key);
+            const bool tuned_cl = tc != b->tuned.end() && (tc->second >> 24) != 0;
+            const uint32_t C = tuned_cl ? (tc->second >> 24) : (tc == b->tuned.end() ? b->C_override : 0u);
+            const uint32_t Wc = tuned_cl ? (tc->second & 0xFFu) : b->CW_override;
+            if (C && plan_cluster_class(b, g.second, C, Wc, c)) {
+                const int occ = sk::cluster_occupancy(c.kind, c.rule, c.nb, C, c.W, c.jbytes, c.per_chain);
+                if (occ <= 0)
+                    return fail(SK_ERR_CUDA, "no cluster of %u CTAs with %u bytes of shared memory can be resident", C,
+                                c.jbytes + c.W * c.per_chain);
+                c.first_item = static_cast<uint32_t>(items.size());
+                for (uint32_t i : g.second) {
+                    const sk_run* r = b->runs[i];
+                    for (uint32_t ch = 0; ch < r->chains; ch += c.W)
+                        items.push_back(WorkItem{i, ch, std::min(c.W, r->chains - ch), 0});
+                }
+                c.n_items = static_cast<uint32_t>(items.size()) - c.first_item;
+                c.grid = std::min<uint32_t>(c.n_items, static_cast<uint32_t>(occ)) * C;  // CTAs
+                grid = std::max(grid, c.grid);
+                classes.push_back(c);
+                continue;
+            }
+            if (tuned_cl) return fail(SK_ERR_INVALID_ARG, "launch class cannot take %u-CTA clusters", C);
+        }
         const bool nw = ((c.key >> 60) & 1u) != 0;  // node-weighted records: rows through L1 only
         auto t = b->tuned.find(c.key);
         if (t != b->tuned.end()) {
-            c.stage = t->second >> 16;
+            c.stage = (t->second >> 16) & 0xFFu;
             c.G = (t->second >> 8) & 0xFFu;
             c.W = t->second & 0xFFu;
             c.per_chain = c.stage ? c.per_chain_staged : c.per_chain_direct;
@@ -1382,8 +1457,31 @@ sk_status mcmcmc_batch_set_layout(sk_batch* b, uint32_t lanes, uint32_t staging)
     if (staging > 2) return fail(SK_ERR_INVALID_ARG, "staging must be 0, 1 or 2");
     b->G_override = lanes;
     b->S_override = staging;
+    b->C_override = 0;
+    b->CW_override = 0;
     b->tuned.clear();
     return plan_batch(b);
+}
+
+sk_status mcmcmc_batch_set_cluster(sk_batch* b, uint32_t ctas, uint32_t chains) {
+    if (!b) return fail(SK_ERR_INVALID_ARG, "batch is NULL");
+    if (ctas != 0 && ctas != 1 && ctas != 2 && ctas != 4 && ctas != 8 && ctas != 16)
+        return fail(SK_ERR_INVALID_ARG, "CTAs per cluster must be 0, 1, 2, 4, 8 or 16");
+    if (chains != 0 && chains != 1 && chains != 2 && chains != 4 && chains != sk::kClusterMaxChains)
+        return fail(SK_ERR_INVALID_ARG, "chains per cluster must be 0, 1, 2, 4 or 8");
+    const uint32_t c0 = b->C_override, w0 = b->CW_override;
+    const std::map<uint64_t, uint32_t> t0 = b->tuned;
+    b->C_override = ctas;
+    b->CW_override = chains;
+    b->tuned.clear();
+    const sk_status s = plan_batch(b);
+    if (s != SK_OK) {  // keep the previous plan
+        b->C_override = c0;
+        b->CW_override = w0;
+        b->tuned = t0;
+        plan_batch(b);
+    }
+    return s;
 }
 
 namespace {
@@ -1433,7 +1531,10 @@ sk_status launch_segment(sk_batch* b, uint64_t steps, int only = -1) {
         const bool last = !fork && (only >= 0 || k + 1 == nc);
         cudaStream_t cs = fork ? b->side[k % nside] : b->st;
         cudaError_t e =
-            c.graph ? sk::launch_graph(b->djobs, b->ditems + c.first_item, c.n_items, b->dqueue + k, steps, c.W,
+            c.cluster ? sk::launch_cluster(b->djobs, b->ditems + c.first_item, c.n_items, b->dqueue + k, steps, c.kind,
+                                           c.rule, c.nb, c.cluster, c.W, c.jbytes, c.per_chain, c.grid / c.cluster,
+                                           static_cast<uint32_t>(b->runs.size()), last, cs)
+            : c.graph ? sk::launch_graph(b->djobs, b->ditems + c.first_item, c.n_items, b->dqueue + k, steps, c.W,
                                        c.nw, c.per_chain, c.grid, static_cast<uint32_t>((c.cls - 512) / 4), c.graph,
                                        static_cast<uint32_t>(b->runs.size()), last, cs)
                     : sk::launch_step(b->djobs, b->ditems + c.first_item, c.n_items, b->dqueue + k, steps, c.W,
@@ -1615,8 +1716,9 @@ sk_status mcmcmc_batch_autotune(sk_batch* b, uint32_t trial_steps, uint32_t* out
         const std::vector<sk_batch::Class> cls0 = b->classes;
         for (size_t k = 0; k < cls0.size() && s == SK_OK; ++k) {
             const uint64_t key = cls0[k].key;
-            uint32_t best = cls0[k].graph ? ((cls0[k].nw << 16) | (32u << 8) | cls0[k].W)
-                                          : ((cls0[k].stage << 16) | (cls0[k].G << 8) | cls0[k].W);
+            uint32_t best = cls0[k].graph     ? ((cls0[k].nw << 16) | (32u << 8) | cls0[k].W)
+                            : cls0[k].cluster ? ((cls0[k].cluster << 24) | (32u << 8) | cls0[k].W)
+                                              : ((cls0[k].stage << 16) | (cls0[k].G << 8) | cls0[k].W);
             float best_ms = 1e30f;
             std::vector<uint32_t> cand;  // (stage << 16) | (G << 8) | W
             const uint32_t max_stage = ((key >> 60) & 1u) ? 0u : 1u;  // node-weighted classes: no staging
@@ -1633,6 +1735,22 @@ sk_status mcmcmc_batch_autotune(sk_batch* b, uint32_t trial_steps, uint32_t* out
                     for (uint32_t w : {32u, 24u, 20u, 16u, 12u, 8u, 6u, 4u, 2u, 1u})
                         if (w <= fit && (G < 32 || (w & 1u) == 0)) cand.push_back((stage << 16) | (G << 8) | w);
                 }
+            // star classes of few chains: the cluster-per-chain layout as well
+            // (shapes the class cannot take fail to plan and are skipped)
+            if (!((key >> 59) & 1u) && !((key >> 60) & 1u)) {
+                uint64_t total = 0;
+                bool single = true;
+                for (const sk_run* r : b->runs)
+                    if (class_key(r) == key) {
+                        total += r->chains;
+                        single = single && r->chains == 1;
+                    }
+                if (total <= kClusterTuneChains)
+                    for (uint32_t C : {1u, 2u, 4u, 8u, 16u})
+                        for (uint32_t w : {1u, 2u, 4u, 8u})
+                            if ((w > 1 || single) && w <= std::max<uint64_t>(2, total))
+                                cand.push_back((C << 24) | (32u << 8) | w);
+            }
             for (uint32_t gw : cand) {
                 b->tuned[key] = gw;
                 if (plan_batch(b) != SK_OK) continue;  // not resident: skip the candidate
@@ -1684,8 +1802,10 @@ sk_status mcmcmc_batch_info(const sk_batch* b, uint32_t* grid, uint32_t* W, uint
     if (!b) return fail(SK_ERR_INVALID_ARG, "batch is NULL");
     if (grid) *grid = b->grid;
     if (W) *W = b->classes.empty() ? 0 : b->classes[0].W;
-    if (smem)
-        *smem = b->classes.empty() ? 0 : b->classes[0].per_chain * b->classes[0].W * (32 / b->classes[0].G);
+    if (smem) {
+        const sk_batch::Class* c = b->classes.empty() ? nullptr : &b->classes[0];
+        *smem = !c ? 0 : c->cluster ? c->jbytes + c->W * c->per_chain : c->per_chain * c->W * (32 / c->G);
+    }
     if (items) *items = b->n_items;
     return SK_OK;
 }

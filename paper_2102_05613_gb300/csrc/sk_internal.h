@@ -134,6 +134,46 @@ cudaError_t launch_energy(const void* J, uint32_t kind, uint32_t N, uint32_t Npa
                           const int8_t* spins, uint32_t count, double* out, cudaStream_t st,
                           double* partial = nullptr);
 
+// Cluster-per-chain layout (sk_cluster*.cu): a cluster of C CTAs (1, 2, 4,
+// 8 or 16) holds W chains of one run (one warp per chain in each CTA; W = 1,
+// 2, 4 or 8); CTA r keeps the slice [r Npad/C, (r+1) Npad/C) of each chain's
+// spins and fields and the same columns of every row of J.  Shared memory of
+// a CTA: cluster_slice_bytes for J, then cluster_chain_bytes per chain.
+// cluster_shape_ok: Npad splits into C slices whose rows of J are whole
+// 16-byte units (bulk copies).  launch_cluster runs the items of one class
+// (W chains each) on `clusters` clusters; nb = Philox blocks per lane at 32
+// lanes (blocks_per_lane(rule, K, 32)).
+constexpr uint32_t kClusterMaxChains = 8;
+constexpr uint32_t kClusterMaxCtas = 16;
+// Exchange arrays of one chain: two (by step parity) of 4 nb x 32 slot
+// entries of 16 bytes (Metropolis: one entry each), then the list of the
+// slots this CTA owns in a step (16-bit slot numbers).
+__host__ __device__ constexpr uint32_t cluster_list_bytes(uint32_t rule, uint32_t nb) {
+    return rule == 1 ? 16u : 4u * nb * 32u * 2u;
+}
+__host__ __device__ constexpr uint32_t cluster_x_bytes(uint32_t rule, uint32_t nb) {
+    return (rule == 1 ? 32u : 2u * 4u * nb * 32u * 16u) + cluster_list_bytes(rule, nb);
+}
+bool cluster_shape_ok(uint32_t kind, uint32_t npad, uint32_t C);
+size_t cluster_slice_bytes(uint32_t kind, uint32_t N, uint32_t npad, uint32_t C);
+size_t cluster_chain_bytes(uint32_t rule, uint32_t nb, uint32_t npad, uint32_t C);
+cudaError_t launch_cluster(const JobDev* jobs, const WorkItem* items, uint32_t n_items, uint32_t* queue,
+                           uint64_t nsteps, uint32_t kind, uint32_t rule, uint32_t nb, uint32_t C, uint32_t W,
+                           uint32_t jbytes, uint32_t pc, uint32_t clusters, uint32_t n_jobs, bool bump,
+                           cudaStream_t st);
+// Clusters that can be resident at once with this shape (0: none).
+int cluster_occupancy(uint32_t kind, uint32_t rule, uint32_t nb, uint32_t C, uint32_t W, uint32_t jbytes,
+                      uint32_t pc);
+// Per coupling type (sk_cluster_pm1.cu, sk_cluster_gauss.cu).
+cudaError_t launch_cluster_pm1(uint32_t rule, uint32_t nb, const JobDev* jobs, const WorkItem* items,
+                               uint32_t n_items, uint32_t* queue, uint32_t nsteps, uint32_t C, uint32_t W,
+                               uint32_t jbytes, uint32_t pc, uint32_t clusters, cudaStream_t st);
+cudaError_t launch_cluster_gauss(uint32_t rule, uint32_t nb, const JobDev* jobs, const WorkItem* items,
+                                 uint32_t n_items, uint32_t* queue, uint32_t nsteps, uint32_t C, uint32_t W,
+                                 uint32_t jbytes, uint32_t pc, uint32_t clusters, cudaStream_t st);
+int occupancy_cluster_pm1(uint32_t rule, uint32_t nb, uint32_t C, uint32_t W, uint32_t jbytes, uint32_t pc);
+int occupancy_cluster_gauss(uint32_t rule, uint32_t nb, uint32_t C, uint32_t W, uint32_t jbytes, uint32_t pc);
+
 // MCMCMC on deeper graphs (sk_graph.cu): a team of nw warps per chain (1, 2,
 // 4, 8 or 16), W warps per CTA, i.e. W / nw chains (even; at most 14 when
 // nw > 1, the teams' named barriers), `per_chain` bytes of shared memory per

@@ -35,7 +35,7 @@ EXPORTS = ["sk_create_instance", "sk_get_couplings", "sk_set_couplings", "sk_des
            "mcmcmc_trace", "mcmcmc_counters", "mcmcmc_free",
            "mcmcmc_batch_create", "mcmcmc_batch_advance", "mcmcmc_batch_capture",
            "mcmcmc_batch_replay", "mcmcmc_batch_autotune", "mcmcmc_batch_info",
-           "mcmcmc_batch_classes", "mcmcmc_batch_set_layout",
+           "mcmcmc_batch_classes", "mcmcmc_batch_set_layout", "mcmcmc_batch_set_cluster",
            "mcmcmc_batch_free", "mcmcmc_run_noalloc", "sk_last_error",
            "sk_peak_l2_read", "sk_peak_smem"]
 
@@ -113,6 +113,7 @@ def lib(build_if_missing: bool = True):
             "mcmcmc_batch_autotune": [vp, u32, vp],
             "mcmcmc_batch_classes": [vp, u32, vp, vp],
             "mcmcmc_batch_set_layout": [vp, u32, u32],
+            "mcmcmc_batch_set_cluster": [vp, u32, u32],
             "mcmcmc_batch_info": [vp, vp, vp, vp, vp],
             "mcmcmc_batch_free": [vp],
             "mcmcmc_run_noalloc": [u32, u32, vp, d, u32, u32, u32, d, u64, u32, u64, vp, vp, vp],
@@ -397,6 +398,13 @@ class Batch:
         runs also 64, 128, 256, 512 = 2..16 warps per chain); staging 0
         default, 1 TMA-staged rows, 2 rows read through L1."""
         _check(lib().mcmcmc_batch_set_layout(self.handle, int(lanes), int(staging)))
+
+    def set_cluster(self, ctas: int, chains: int = 0):
+        """mcmcmc_batch_set_cluster: the cluster-per-chain layout with `ctas`
+        CTAs per cluster (1, 2, 4, 8, 16; 0 = back to the warp layouts) and
+        `chains` chains per cluster (0 default, 1, 2, 4, 8), for every star
+        class that can take it."""
+        _check(lib().mcmcmc_batch_set_cluster(self.handle, int(ctas), int(chains)))
 
     def info(self):
         v = [C.c_uint32(0) for _ in range(4)]
