@@ -335,7 +335,7 @@ def run_latency(args):
                 run = sk.Run(inst, chains=1, K=Kt, rule=rule, beta=TTT_BETA, seed=1)
                 b = sk.Batch([run])
                 if mode == "autotuned":
-                    b.autotune(trial_steps=64)
+                    b.autotune(trial_steps=512)
                 elif mode.startswith("cluster"):
                     b.set_cluster(int(mode[7:]))
                 res[mode] = {"ns_per_step": _one_chain_ns(b, stream), "layout": b.classes()[0]}
@@ -404,7 +404,7 @@ TTT_LINE_METHODS = ("metropolis", "mcmcmc_k2", "mcmcmc_k4", "mcmcmc_k8", "mcmcmc
 TTT_EPS = (1e-2, 3e-3, 1e-3)
 
 
-def ttt_measure(only, beta, scale):
+def ttt_measure(only, beta, scale, N=TTT_N):
     """e(t) = chain-mean E/N every T/2048 steps from a random start; e_inf and
     sigma_inf (one record's equilibrium fluctuation) from the last half of the
     K=128 run; t_therm(eps) = the first record after which
@@ -415,7 +415,7 @@ def ttt_measure(only, beta, scale):
     import torch
     from paper_2102_05613_gb300 import inputs, sk
     stream = torch.cuda.current_stream()
-    J = inputs.couplings_gauss(TTT_N, 0)
+    J = inputs.couplings_gauss(N, 0)
     inst = sk.Instance(J, stream=stream)
     curves = {}
     for name, rule, Kt, T, gkw in TTT_METHODS:
@@ -441,7 +441,7 @@ def ttt_measure(only, beta, scale):
         batch.close()
         E, _, acc = run.observables()
         s_per_step = a.elapsed_time(b) / 1e3 / T
-        curves[name] = dict(R=R, T=T, e=E.mean(axis=1) / TTT_N, per_chain=E / TTT_N,
+        curves[name] = dict(R=R, T=T, e=E.mean(axis=1) / N, per_chain=E / N,
                             s_per_step=s_per_step, acc=float(acc.mean()) / R, geometry=geometry,
                             nodes=Kt + 1 if not gkw.get("graph") else (gkw.get("line_nodes") or
                                                                        (gkw["arity"] ** (gkw["depth"] + 1) - 1) // (gkw["arity"] - 1)))
@@ -453,7 +453,7 @@ def ttt_measure(only, beta, scale):
     tail = ref["e"][1024:]
     e_inf = float(tail.mean())
     sig = float(tail.std(ddof=1))
-    out = {"workload": f"gaussian-sk N={TTT_N} J seed 0, beta={beta}, {TTT_CHAINS} chains from "
+    out = {"workload": f"gaussian-sk N={N} J seed 0, beta={beta}, {TTT_CHAINS} chains from "
                        f"a random start, records every T/2048 steps",
            "e_inf": e_inf, "sigma_inf": sig, "methods": {}}
     for name, c in curves.items():
@@ -512,7 +512,7 @@ def run_ttt(args):
     import torch
     torch.cuda.set_device(0)
     only = set(args.ttt_methods.split(",")) if args.ttt_methods else None
-    print(json.dumps(ttt_measure(only, args.ttt_beta, args.ttt_scale)), flush=True)
+    print(json.dumps(ttt_measure(only, args.ttt_beta, args.ttt_scale, args.ttt_n)), flush=True)
     return 0
 
 
@@ -578,7 +578,9 @@ def ttt_few_chains(inst, methods, only, beta):
                 continue
             run = sk.Run(inst, chains=C, K=Kt, rule=rule, beta=beta, seed=11, **gkw)
             batch = sk.Batch([run])
-            batch.autotune(trial_steps=32)
+            # trials long enough that the launch's fixed cost does not decide
+            # between layouts a few per cent apart
+            batch.autotune(trial_steps=32 if gkw.get("graph") else 512)
             geometry = batch.classes()
 
             def timed(T):
@@ -1082,6 +1084,8 @@ def main():
                     help="comma-separated subset of the --ttt methods (the K=128 reference always runs)")
     ap.add_argument("--ttt-beta", type=float, default=TTT_BETA,
                     help="inverse temperature of the --ttt comparison (1 = T_c, the paper's setting)")
+    ap.add_argument("--ttt-n", type=int, default=TTT_N,
+                    help="spins of the --ttt instance (512: its columns of J fit a cluster's shared memory)")
     ap.add_argument("--ttt-scale", type=int, default=1,
                     help="multiplies every --ttt method's steps (colder runs relax more slowly)")
     ap.add_argument("--graph-chains", type=int, default=1,

@@ -387,7 +387,8 @@ sk_status mcmcmc_batch_replay(sk_batch* b, uint32_t times);
 
 /*
  * mcmcmc_batch_autotune: for each launch class of the batch, times a
- * `trial_steps`-step launch for each staging choice, each lanes-per-chain
+ * `trial_steps`-step launch (the better of two, after a warm-up launch) for
+ * each staging choice, each lanes-per-chain
  * value K allows and each warps-per-CTA value that fits in shared memory
  * (the CTA size also selects the kernel's register budget) and keeps the
  * fastest; graph classes try 1, 2, 4, 8 and 16 warps per chain with every
@@ -445,9 +446,8 @@ sk_status mcmcmc_batch_set_layout(sk_batch* b, uint32_t lanes, uint32_t staging)
  *            0 = 2, or 1 when every run of the class has one chain; 1 is
  *            raised to 2 for runs of several chains (overlap pairs share a
  *            cluster).
- * Results do not depend on it: trajectories equal those of whole-warp
- * chains (mcmcmc_batch_set_layout lanes 32) bit for bit, records up to the
- * order of the energy's partial sums (Gaussian couplings).  Drops autotuned
+ * Results do not depend on it: trajectories and records equal those of
+ * whole-warp chains (mcmcmc_batch_set_layout lanes 32) bit for bit.  Drops autotuned
  * choices and a captured graph.  SK_ERR_CUDA when no cluster of that size can
  * be resident; the previous plan is kept on any error.
  */

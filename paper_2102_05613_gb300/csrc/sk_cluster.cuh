@@ -32,7 +32,8 @@
 //      columns of J -- the field update of the warp layout, element by element
 //      in the same order -- and the owner of a flipped site flips it.
 // Records (E = -scale/2 sum s h, the accepted count, the overlap q of chains
-// 2m, 2m+1, which share the cluster) add the CTAs' partial sums in rank 0.
+// 2m, 2m+1, which share the cluster) are formed in rank 0, equal to the
+// whole-warp layout's bit for bit.
 // C = 1 is a plain CTA with the whole of J in shared memory: the exchange is
 // local and the barrier a warp synchronisation.
 #pragma once
@@ -74,11 +75,21 @@ __device__ __forceinline__ void st_cluster(uint32_t addr, uint4 v) {
                  "r"(v.w)
                  : "memory");
 }
-// The same without a compiler memory barrier: for the fan-out of entries
-// already in this CTA's exchange array, whose loads may be scheduled ahead.
-__device__ __forceinline__ void st_cluster_nb(uint32_t addr, uint4 v) {
-    asm volatile("st.shared::cluster.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z),
-                 "r"(v.w));
+// Stores into CTA r's shared memory that count their bytes on an mbarrier of
+// that CTA (complete_tx): the receiver learns of their arrival by waiting on
+// its own barrier, without a cluster-wide barrier.
+__device__ __forceinline__ void st_async(uint32_t addr, uint4 v, uint32_t rbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(addr),
+                 "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "r"(rbar));
+}
+__device__ __forceinline__ void st_async(uint32_t addr, uint32_t v, uint32_t rbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(addr), "r"(v),
+                 "r"(rbar));
+}
+// One local arrival that also expects `bytes` of complete_tx in this phase.
+__device__ __forceinline__ void expect_bytes(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(dev::smem_addr(bar)), "r"(bytes)
+                 : "memory");
 }
 __device__ __forceinline__ void st_cluster(uint32_t addr, uint32_t v) {
     asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
@@ -126,81 +137,102 @@ struct ClMem {
     unsigned char* xg;         // exchange arrays (two, by step parity): generic pointer
     uint32_t xs;               // the same as a shared-memory address
     uint16_t* list;            // slots whose entries this CTA owns in the current step
-    uint32_t xr;               // the exchange arrays of CTA (lane mod C), where this lane's fan-out goes
+    uint64_t* xbar;            // two mbarriers (by step parity): the step's entries and headers arrived
+    uint32_t xr;               // the exchange region of CTA (lane mod C), where this lane's fan-out goes
+    uint32_t xbr;              // that CTA's two mbarriers
+    uint32_t xbytes;           // bytes each CTA receives per step (entries and headers)
     uint32_t lc;               // log2 C
     uint32_t ws, lo, C, rank;
     const unsigned long long* wsm;  // +-J: the first kWCache weight-table entries
 };
 
-// Record point (one CTA barrier, one cluster barrier): the CTA's partial sums
-// of s.h and of the overlap with the partner chain go to rank 0, which adds
-// them in rank order and stores.  Shadow warps meet both barriers in
-// shadow_steps.
+// Record point (one CTA barrier, two cluster barriers): the CTA's partial sum
+// of the overlap with the partner chain (and, +-J, of s.h) goes to rank 0,
+// which adds them in rank order; for Gaussian couplings rank 0 reads the
+// spins and fields of every CTA's slice and sums s_k h_k in the order of the
+// whole-warp layout (lane l: fp32 over k = 4l + 128v .. 4l + 128v + 3 for
+// v = 0, 1, ..., the lanes' sums added in double precision by a butterfly),
+// so the records equal that layout's bit for bit.  The other CTAs keep their
+// slices unchanged until rank 0 has read them (the second barrier).  Shadow
+// warps meet the same barriers in shadow_steps.
+// (The chain's slices come as values, not as its ClMem: a struct whose
+// address escapes to a call stays in local memory, and accesses through its
+// pointers would become generic instead of shared-memory ones.)
 template <typename JT, bool ONE>
-__device__ __noinline__ void record(const JobDev& jb, bool write, uint32_t chain, uint32_t rec, const ClMem& cm,
-                                    const int8_t* partner_s, uint32_t acc, uint32_t rec_xs, const double* rec_g,
-                                    uint32_t slot) {
-    const int lane = threadIdx.x & 31;
+__device__ __noinline__ void record(const JobDev& jb, bool write, uint32_t chain, uint32_t rec, const int8_t* cs,
+                                    const void* ch, uint32_t ws, uint32_t C, uint32_t rank, const int8_t* partner_s,
+                                    uint32_t acc, uint32_t rec_xs, const double* rec_g, uint32_t slot) {
+    const uint32_t lane = threadIdx.x & 31;
     __syncthreads();  // the partner chain's flips of this step are done
-    double e_part, q_part;
+    double e_part = 0.0;
     int dot = 0;
     if constexpr (sizeof(JT) == 1) {
-        const int* hf = static_cast<const int*>(cm.h);
+        const int* hf = static_cast<const int*>(ch);
         int e = 0;
-        for (uint32_t k = lane; k < cm.ws; k += 32) e += cm.s[k] * hf[k];
+        for (uint32_t k = lane; k < ws; k += 32) e += cs[k] * hf[k];
         e_part = static_cast<double>(__reduce_add_sync(kFull, e));
-    } else {
-        // fp32 partial sums per lane (the products are exact), combined in
-        // double precision
-        const float* hf = static_cast<const float*>(cm.h);
-        float e = 0.0f;
-        for (uint32_t k = lane; k < cm.ws; k += 32) e = fmaf(static_cast<float>(cm.s[k]), hf[k], e);
-        e_part = dev::warp_sum(static_cast<double>(e));
     }
     const bool pair = (chain & 1u) == 0u && chain + 1u < jb.chains && partner_s != nullptr;
     if (pair)
-        for (uint32_t k = lane; k < cm.ws; k += 32) dot += cm.s[k] * partner_s[k];
-    q_part = static_cast<double>(__reduce_add_sync(kFull, dot));
-    const uint32_t at = rec_xs + (slot * kMaxC + cm.rank) * 16u;
+        for (uint32_t k = lane; k < ws; k += 32) dot += cs[k] * partner_s[k];
+    const double q_part = static_cast<double>(__reduce_add_sync(kFull, dot));
+    const uint32_t at = rec_xs + (slot * kMaxC + rank) * 16u;
     if (lane == 0) {
         if constexpr (ONE)
             asm volatile("st.shared.v2.f64 [%0], {%1, %2};" ::"r"(at), "d"(e_part), "d"(q_part) : "memory");
         else
             st_cluster(map_rank(at, 0), e_part, q_part);
     }
-    sync_all<ONE>();
-    if (cm.rank == 0 && lane == 0 && write && rec < jb.rec_capacity) {
-        double es = 0.0, qs = 0.0;
-        for (uint32_t r = 0; r < cm.C; ++r) {
-            es += rec_g[2 * (slot * kMaxC + r)];
-            qs += rec_g[2 * (slot * kMaxC + r) + 1];
-        }
+    sync_all<ONE>();  // partial sums in rank 0; every slice holds this step's state
+    if (rank == 0) {
         double E;
         if constexpr (sizeof(JT) == 1) {
+            double es = 0.0;
+            for (uint32_t r = 0; r < C; ++r) es += rec_g[2 * (slot * kMaxC + r)];
             const long long tot = static_cast<long long>(es);  // 2 sum_{i<j} J s s, even
             E = jb.scale * static_cast<double>(-(tot / 2));
         } else {
-            E = -0.5 * jb.scale * es;
+            const uint32_t s_xs = dev::smem_addr(cs), h_xs = dev::smem_addr(ch);
+            float e = 0.0f;
+            for (uint32_t k0 = 4u * lane; k0 < jb.Npad; k0 += 128u) {
+#pragma unroll
+                for (uint32_t u = 0; u < 4; ++u) {
+                    const uint32_t k = k0 + u, r = k / ws, c = k - r * ws;
+                    float hv;
+                    int sv;
+                    if constexpr (ONE) {
+                        hv = static_cast<const float*>(ch)[c];
+                        sv = cs[c];
+                    } else {
+                        asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(hv) : "r"(map_rank(h_xs + 4u * c, r)));
+                        asm volatile("ld.shared::cluster.s8 %0, [%1];" : "=r"(sv) : "r"(map_rank(s_xs + c, r)));
+                    }
+                    e = fmaf(static_cast<float>(sv), hv, e);
+                }
+            }
+            E = -0.5 * jb.scale * dev::warp_sum(static_cast<double>(e));
         }
-        jb.rec_E[static_cast<size_t>(rec) * jb.chains + chain] = E;
-        jb.rec_acc[static_cast<size_t>(rec) * jb.chains + chain] = acc;
-        if (pair) jb.rec_q[static_cast<size_t>(rec) * (jb.chains / 2) + chain / 2] = qs / static_cast<double>(jb.N);
+        if (lane == 0 && write && rec < jb.rec_capacity) {
+            double qs = 0.0;
+            for (uint32_t r = 0; r < C; ++r) qs += rec_g[2 * (slot * kMaxC + r) + 1];
+            jb.rec_E[static_cast<size_t>(rec) * jb.chains + chain] = E;
+            jb.rec_acc[static_cast<size_t>(rec) * jb.chains + chain] = acc;
+            if (pair) jb.rec_q[static_cast<size_t>(rec) * (jb.chains / 2) + chain / 2] = qs / static_cast<double>(jb.N);
+        }
     }
+    sync_all<ONE>();  // rank 0 has read the slices
 }
 
 // A warp without a chain of its own meets the barriers of the chains'
-// steps and records, in the same order.
+// records, in the same order.
 template <bool ONE>
 __device__ __forceinline__ void shadow_steps(const JobDev& jb, uint32_t t0, uint32_t t1) {
     const uint32_t R = jb.record_every;
     uint32_t next_rec = R ? (t0 / R + 1u) * R : 0u;
     for (uint32_t t = t0; t < t1; ++t) {
-        if constexpr (!ONE) {
-            arrive();
-            wait();
-        }
         if (t + 1u == next_rec) {
             __syncthreads();
+            sync_all<ONE>();
             sync_all<ONE>();
             next_rec += R;
         }
@@ -212,11 +244,12 @@ template <typename JT, int RULE, int NB, bool ONE>
 __device__ __forceinline__ void chain_steps(const JobDev& jb, bool write, uint32_t chain, const ClMem& cm,
                                             const int8_t* partner_s, uint32_t rec_xs, const double* rec_g,
                                             uint32_t slot, uint32_t t0, uint32_t t1, uint32_t& acc,
-                                            uint32_t& n_flips, uint32_t& n_rows) {
+                                            uint32_t& n_flips, uint32_t& n_rows, uint32_t& xph, bool& xdead) {
     using H = typename Types<JT>::H;
     using W = typename Types<JT>::W;
     constexpr int G = 32;
-    constexpr uint32_t kXBuf = (cluster_x_bytes(RULE, NB) - cluster_list_bytes(RULE, NB)) / 2;  // one array
+    constexpr uint32_t kXBuf = cluster_xbuf_bytes(RULE, NB);  // one exchange array
+    constexpr uint32_t kHdr = 2u * kXBuf + cluster_list_bytes(RULE, NB);  // the step headers
     const Grp<G> g;
     const uint32_t lane = static_cast<uint32_t>(g.gl);
     uint32_t next_rec = jb.record_every ? (t0 / jb.record_every + 1u) * jb.record_every : 0u;
@@ -259,17 +292,28 @@ __device__ __forceinline__ void chain_steps(const JobDev& jb, bool write, uint32
             a = step::gshfl(g, site[0], 0) & 0xFFFFu;
             const JT* rowa = Jr + static_cast<size_t>(a) * ws;
             const unsigned lt = (1u << lane) - 1u;
+            // all of the lane's entries are loaded before any is stored (the
+            // stores could otherwise alias the next slot's loads)
+            uint4 ent[4 * NB];
+            uint32_t owned = 0;
 #pragma unroll
             for (int q = 0; q < 4 * NB; ++q) {
                 const uint32_t d = 128u * (q >> 2) + 4u * lane + (q & 3) + 1u;
                 const uint32_t c = step::site_of<NB>(site, q) - lo;  // wraps when not owned
-                const bool owned = d <= K && c < ws;
+                ent[q] = make_uint4(0u, 0u, 0u, 0u);
+                if (d <= K && c < ws) {
+                    owned |= 1u << q;
+                    ent[q] = make_uint4(to_bits(hf[c]), to_bits(rowa[c]), static_cast<uint32_t>(static_cast<int>(S[c])), 0u);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4 * NB; ++q) {
+                const bool own_q = (owned >> q) & 1u;
                 const uint32_t slot = static_cast<uint32_t>(q) * 32u + lane;
-                if (owned)
-                    X[slot] = make_uint4(to_bits(hf[c]), to_bits(rowa[c]), static_cast<uint32_t>(static_cast<int>(S[c])), 0u);
+                if (own_q) X[slot] = ent[q];
                 if constexpr (!ONE) {
-                    const unsigned ball = __ballot_sync(kFull, owned);
-                    if (owned) cm.list[n_own + __popc(ball & lt)] = static_cast<uint16_t>(slot);
+                    const unsigned ball = __ballot_sync(kFull, own_q);
+                    if (own_q) cm.list[n_own + __popc(ball & lt)] = static_cast<uint16_t>(slot);
                     n_own += __popc(ball);
                 }
             }
@@ -284,18 +328,35 @@ __device__ __forceinline__ void chain_steps(const JobDev& jb, bool write, uint32
             }
         }
         __syncwarp();
+        const uint32_t p = t & 1u;
         if constexpr (!ONE) {
+            // every CTA also sends every CTA a header for the step: a CTA that
+            // has received all headers of step t knows that every CTA is done
+            // reading the exchange array of step t - 1, which step t + 1 reuses
+            // (those reads returned their values, which decided step t - 1,
+            // before the header of step t was issued)
 #pragma unroll 4
             for (uint32_t e = lane >> cm.lc; e < n_own; e += 32u >> cm.lc) {
                 const uint32_t off = xo + 16u * cm.list[e];
-                st_cluster_nb(cm.xr + off, *reinterpret_cast<const uint4*>(cm.xg + off));
+                st_async(cm.xr + off, *reinterpret_cast<const uint4*>(cm.xg + off), cm.xbr + 8u * p);
             }
+            if (lane < cm.C) st_async(cm.xr + kHdr + 64u * p + 4u * cm.rank, t, cm.xbr + 8u * p);
         }
         // the next step's sites, while the stores travel
         if constexpr (RULE == 0) step::draw_sites<NB, G>(nsite, t + 1u, chain, c3, k0, k1, nblk, N, g);
         if constexpr (!ONE) {
-            arrive();
-            wait();
+            if (!xdead) {
+                // every lane waits (bounded); the outcome is made warp-uniform
+                const bool ok = __all_sync(kFull, dev::mbar_wait_bounded(&cm.xbar[p], (xph >> p) & 1u));
+                xph ^= 1u << p;
+                if (!ok) {
+                    xdead = true;
+                    if (lane == 0) atomicExch(jb.err, kDevTimeout);
+                } else if (lane == 0 && t + 2u < t1) {
+                    expect_bytes(&cm.xbar[p], cm.xbytes);  // the phase of step t + 2
+                }
+            }
+            __syncwarp();
         }
 
         // ---- choose (the same in every CTA) ----
@@ -489,7 +550,8 @@ __device__ __forceinline__ void chain_steps(const JobDev& jb, bool write, uint32
             for (int q = 0; q < 2 * NB; ++q) site[q] = nsite[q];
         }
         if (t + 1u == next_rec) {
-            record<JT, ONE>(jb, write, chain, next_rec / jb.record_every - 1u, cm, partner_s, acc, rec_xs, rec_g, slot);
+            record<JT, ONE>(jb, write, chain, next_rec / jb.record_every - 1u, cm.s, cm.h, cm.ws, cm.C, cm.rank,
+                            partner_s, acc, rec_xs, rec_g, slot);
             acc = 0;
             next_rec += jb.record_every;
         }
@@ -519,6 +581,14 @@ __global__ void __launch_bounds__(32 * kClusterMaxChains, 1)
         dev::mbar_init(&s_bar, 1);
         s_fail = 0;
     }
+    // the exchange mbarriers of this warp's chain slot
+    uint64_t* xbar = reinterpret_cast<uint64_t*>(smem + jbytes + static_cast<size_t>(warp) * pc + kX - 16u);
+    if (!ONE && lane == 0) {
+        dev::mbar_init(&xbar[0], 1);
+        dev::mbar_init(&xbar[1], 1);
+    }
+    uint32_t xph = 0;    // parity each exchange mbarrier's current phase completes with
+    bool xdead = false;  // an exchange wait expired: no further waits in this launch
     dev::fence_mbar_init();
     __syncthreads();
     if constexpr (!ONE) sync_all<false>();  // every CTA of the cluster runs before any remote store
@@ -605,9 +675,12 @@ __global__ void __launch_bounds__(32 * kClusterMaxChains, 1)
         cm.jr = smem;
         cm.xg = base;
         cm.xs = dev::smem_addr(base);
-        cm.list = reinterpret_cast<uint16_t*>(base + kX - cluster_list_bytes(RULE, NB));
+        cm.list = reinterpret_cast<uint16_t*>(base + 2u * cluster_xbuf_bytes(RULE, NB));
         cm.lc = static_cast<uint32_t>(__ffs(static_cast<int>(C)) - 1);
         cm.xr = ONE ? cm.xs : map_rank(cm.xs, lane & (C - 1u));
+        cm.xbar = xbar;
+        cm.xbr = ONE ? 0u : map_rank(dev::smem_addr(xbar), lane & (C - 1u));
+        cm.xbytes = 16u * (RULE == 1 ? 1u : jb.K) + 4u * C;
         cm.b0 = reinterpret_cast<uint4*>(base + kX);
         cm.s = reinterpret_cast<int8_t*>(base + kX + kB0Bytes);
         cm.h = base + kX + kB0Bytes + ((ws + 15u) & ~15u);
@@ -633,10 +706,19 @@ __global__ void __launch_bounds__(32 * kClusterMaxChains, 1)
             acc = jb.acc_run[chain];
         }
         __syncwarp();
+        if constexpr (!ONE) {
+            // arm the exchange barriers for the first two steps before any CTA
+            // of the cluster can send them
+            if (!dead && own && !xdead && lane == 0) {
+                if (t0 < t1) expect_bytes(&xbar[t0 & 1u], cm.xbytes);
+                if (t0 + 1u < t1) expect_bytes(&xbar[(t0 + 1u) & 1u], cm.xbytes);
+            }
+            sync_all<false>();
+        }
         if (!dead && t1 > t0) {
             if (own)
                 chain_steps<JT, RULE, NB, ONE>(jb, true, chain, cm, partner_s, dev::smem_addr(s_rec), s_rec, warp, t0,
-                                               t1, acc, n_flips, n_rows);
+                                               t1, acc, n_flips, n_rows, xph, xdead);
             else
                 shadow_steps<ONE>(jb, t0, t1);
         }
@@ -654,6 +736,13 @@ __global__ void __launch_bounds__(32 * kClusterMaxChains, 1)
             }
         }
         __syncthreads();  // s_job, s_wt and the chain slots are reused by the next item
+    }
+    if (xdead) {
+        // an exchange wait expired: give stores still in flight to this CTA
+        // (about a millisecond) time to land before it leaves
+        const long long start = clock64();
+        while (clock64() - start < 2000000ll) {
+        }
     }
 }
 

@@ -80,15 +80,18 @@ inline size_t warp_smem_bytes(uint32_t npad, uint32_t kind, bool staged = true) 
 // stage): the coupling type, the rule, whether row a is staged in shared
 // memory by TMA (stage) or read through L1, the lanes per chain G (4, 8, 16,
 // 32; 32/G chains per warp) and the Philox blocks of sites each lane draws,
-// NB = blocks_per_lane(rule, K, G) (1, 2 or 4: K up to 4 G NB); stage 2 is
-// stage 0 with node-weighted energy records.  step_class
+// NB = blocks_per_lane(rule, K, G) (1, 2 or 4: K up to 4 G NB; Metropolis,
+// which draws one block, takes NB = 2 for the chunked field update of the
+// 128-register variant when npad / (4 G) is not a multiple of 8, see
+// update_fields in sk_step.cuh); stage 2 is stage 0 with node-weighted
+// energy records.  step_class
 // returns -1 for a (K, G) no kernel covers.  A CTA holds W warps, i.e.
 // W * 32/G chains, each with `per_chain` bytes of shared memory.  launch_step
 // runs the items of one class; `bump` advances every job's step counter
 // afterwards (set it on the last class).
 uint32_t site_blocks_pow2(uint32_t rule, uint32_t K);
 uint32_t blocks_per_lane(uint32_t rule, uint32_t K, uint32_t G);
-int step_class(uint32_t kind, uint32_t rule, uint32_t K, uint32_t G, uint32_t stage);
+int step_class(uint32_t kind, uint32_t rule, uint32_t K, uint32_t G, uint32_t stage, uint32_t npad = 0);
 uint32_t class_lanes(int cls);
 bool class_staged(int cls);
 cudaError_t launch_step(const JobDev* jobs, const WorkItem* items, uint32_t n_items,
@@ -145,14 +148,19 @@ cudaError_t launch_energy(const void* J, uint32_t kind, uint32_t N, uint32_t Npa
 // lanes (blocks_per_lane(rule, K, 32)).
 constexpr uint32_t kClusterMaxChains = 8;
 constexpr uint32_t kClusterMaxCtas = 16;
-// Exchange arrays of one chain: two (by step parity) of 4 nb x 32 slot
-// entries of 16 bytes (Metropolis: one entry each), then the list of the
-// slots this CTA owns in a step (16-bit slot numbers).
+// Exchange region of one chain in each CTA: two exchange arrays (by step
+// parity) of 4 nb x 32 slot entries of 16 bytes (Metropolis: one entry),
+// the list of the slots this CTA owns in a step (16-bit slot numbers), two
+// arrays of kClusterMaxCtas 4-byte step headers and two mbarriers.
+__host__ __device__ constexpr uint32_t cluster_xbuf_bytes(uint32_t rule, uint32_t nb) {
+    return rule == 1 ? 16u : 4u * nb * 32u * 16u;
+}
 __host__ __device__ constexpr uint32_t cluster_list_bytes(uint32_t rule, uint32_t nb) {
     return rule == 1 ? 16u : 4u * nb * 32u * 2u;
 }
+constexpr uint32_t kClusterHdrBytes = 2u * 16u * 4u;
 __host__ __device__ constexpr uint32_t cluster_x_bytes(uint32_t rule, uint32_t nb) {
-    return (rule == 1 ? 32u : 2u * 4u * nb * 32u * 16u) + cluster_list_bytes(rule, nb);
+    return 2u * cluster_xbuf_bytes(rule, nb) + cluster_list_bytes(rule, nb) + kClusterHdrBytes + 16u;
 }
 bool cluster_shape_ok(uint32_t kind, uint32_t npad, uint32_t C);
 size_t cluster_slice_bytes(uint32_t kind, uint32_t N, uint32_t npad, uint32_t C);

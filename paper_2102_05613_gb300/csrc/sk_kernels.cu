@@ -453,10 +453,14 @@ uint32_t blocks_per_lane(uint32_t rule, uint32_t K, uint32_t G) {
 
 // class = kind * 256 + rule * 128 + stage * 32 + log2(NB) * 8 + log2(G), or -1;
 // stage 0 rows through L1, 1 rows staged by TMA, 2 rows through L1 with
-// node-weighted energy records
-int step_class(uint32_t kind, uint32_t rule, uint32_t K, uint32_t G, uint32_t stage) {
-    const uint32_t nb = blocks_per_lane(rule, K, G);
+// node-weighted energy records.  Metropolis draws one block; its NB field
+// names the field update of the 128-register variant instead: 2 (chunks)
+// when a lane's share of a row of npad couplings, npad / (4 G) float4 or
+// int32 words, is not a whole number of 8-word passes, else 1.
+int step_class(uint32_t kind, uint32_t rule, uint32_t K, uint32_t G, uint32_t stage, uint32_t npad) {
+    uint32_t nb = blocks_per_lane(rule, K, G);
     if (!nb) return -1;
+    if (rule == 1 && npad && (npad / (4u * G)) % 8u != 0u) nb = 2;
     int lg = 0;
     while ((1u << lg) < G) ++lg;
     const int lnb = nb == 1 ? 0 : (nb == 2 ? 1 : 2);

@@ -167,18 +167,21 @@ __device__ __forceinline__ uint32_t site_of(const uint32_t (&sp)[2 * NB], int k)
 // owns elements 4 gl + 4 G v.  r1 is the staged row (shared memory) when
 // STAGED, else a row of J in global memory; r2 is global and read only when
 // c2 != 0.  Two forms:
-//  - CHUNKED (the MCMCMC 128-register variant: few warps per SM, where a lone
-//    chain waits for each round trip and a double flip reads two rows):
-//    chunks of UNROLL iterations whose row loads are all issued before any
-//    field of the chunk is read or written, so that a chunk costs one round
-//    trip to L2 even when the first row is staged in shared memory beside
-//    the fields (loads could not otherwise move past the stores);
+//  - CHUNKED (the 128-register variant: few warps per SM, where a lone
+//    chain waits for each round trip and an MCMCMC double flip reads two
+//    rows): chunks of UNROLL iterations whose row loads are all issued
+//    before any field of the chunk is read or written, so that a chunk costs
+//    one round trip to L2 even when the first row is staged in shared memory
+//    beside the fields (loads could not otherwise move past the stores);
+//    without TWO (Metropolis) there is no second row;
 //  - otherwise one loop unrolled UNROLL times: 2 where many chains per SM
 //    hide each other's L2 latency within tight registers, 8 for Metropolis
-//    in the 128-register variant (one row, no second-row branch).
+//    in the 128-register variant when each lane's share of the row is a
+//    multiple of 8 passes (otherwise the loop's remainder would take one
+//    round trip per element, and the planner takes the chunked form).
 // The terms are added in the same order either way (the first flip's, then
 // the second's), so both give the same fields bit for bit.
-template <typename JT, bool STAGED, int G, int UNROLL, bool CHUNKED>
+template <typename JT, bool STAGED, int G, int UNROLL, bool CHUNKED, bool TWO = true>
 __device__ __forceinline__ void update_fields(typename Types<JT>::H* hf, const JT* r1, const JT* r2, int c1,
                                               int c2, uint32_t npad, int gl) {
     if constexpr (CHUNKED) {
@@ -193,7 +196,7 @@ __device__ __forceinline__ void update_fields(typename Types<JT>::H* hf, const J
                     if (k < npad) {
                         j1[u] = STAGED ? *reinterpret_cast<const uint32_t*>(r1 + k)
                                        : __ldg(reinterpret_cast<const unsigned int*>(r1 + k));
-                        if (c2) j2[u] = __ldg(reinterpret_cast<const unsigned int*>(r2 + k));
+                        if (TWO && c2) j2[u] = __ldg(reinterpret_cast<const unsigned int*>(r2 + k));
                     }
                 }
 #pragma unroll
@@ -205,7 +208,7 @@ __device__ __forceinline__ void update_fields(typename Types<JT>::H* hf, const J
                         hv.y -= c1 * sbyte(j1[u], 1);
                         hv.z -= c1 * sbyte(j1[u], 2);
                         hv.w -= c1 * sbyte(j1[u], 3);
-                        if (c2) {
+                        if (TWO && c2) {
                             hv.x -= c2 * sbyte(j2[u], 0);
                             hv.y -= c2 * sbyte(j2[u], 1);
                             hv.z -= c2 * sbyte(j2[u], 2);
@@ -223,7 +226,7 @@ __device__ __forceinline__ void update_fields(typename Types<JT>::H* hf, const J
                     if (k < npad) {
                         j1[u] = STAGED ? *reinterpret_cast<const float4*>(r1 + k)
                                        : __ldg(reinterpret_cast<const float4*>(r1 + k));
-                        if (c2) j2[u] = __ldg(reinterpret_cast<const float4*>(r2 + k));
+                        if (TWO && c2) j2[u] = __ldg(reinterpret_cast<const float4*>(r2 + k));
                     }
                 }
                 const float f1 = static_cast<float>(c1);
@@ -237,7 +240,7 @@ __device__ __forceinline__ void update_fields(typename Types<JT>::H* hf, const J
                         hv.y = fmaf(-f1, j1[u].y, hv.y);
                         hv.z = fmaf(-f1, j1[u].z, hv.z);
                         hv.w = fmaf(-f1, j1[u].w, hv.w);
-                        if (c2) {
+                        if (TWO && c2) {
                             hv.x = fmaf(-f2, j2[u].x, hv.x);
                             hv.y = fmaf(-f2, j2[u].y, hv.y);
                             hv.z = fmaf(-f2, j2[u].z, hv.z);
@@ -474,7 +477,7 @@ __device__ __noinline__ void record(const JobDev& jb, bool write, uint32_t chain
 // nothing, so that every lane reaches the same barriers).  `dead` is set
 // after a timed-out wait: the group then stops working but still meets the
 // CTA's record barriers.
-template <typename JT, int RULE, int NB, int G, int STAGE, int UNROLL>
+template <typename JT, int RULE, int NB, int G, int STAGE, int UNROLL, bool RCH>
 __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_t chain, const ChainMem& cm,
                                            int partner_off, uint32_t t0, uint32_t t1, uint32_t& acc,
                                            uint32_t& phase, bool& dead, uint32_t& n_flips, uint32_t& n_rows) {
@@ -773,11 +776,14 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
             if (nflip) {
                 const int c1 = 2 * S[x1];
                 const int c2 = nflip == 2 ? 2 * S[x2] : 0;
-                constexpr bool CHUNKED = RULE == 0 && UNROLL >= 8;
+                // MCMCMC in the 128-register variant: chunks; Metropolis there:
+                // chunks in the RCH instantiation (rows whose per-lane share is
+                // not a whole number of unrolled passes), else the unrolled loop
+                constexpr bool CHUNKED = UNROLL >= 8 && (RULE == 0 || RCH);
                 if (x1_staged)
-                    update_fields<JT, STAGED, G, UNROLL, CHUNKED>(hf, rowA, Jrow(x2), c1, c2, npad, g.gl);
+                    update_fields<JT, STAGED, G, UNROLL, CHUNKED, RULE == 0>(hf, rowA, Jrow(x2), c1, c2, npad, g.gl);
                 else
-                    update_fields<JT, false, G, UNROLL, CHUNKED>(hf, Jrow(x1), nullptr, c1, 0, npad, g.gl);
+                    update_fields<JT, false, G, UNROLL, CHUNKED, false>(hf, Jrow(x1), nullptr, c1, 0, npad, g.gl);
                 __syncwarp(g.mask);
                 if (g.gl == 0) {
                     S[x1] = static_cast<int8_t>(-S[x1]);
@@ -814,7 +820,7 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
 // STAGE: 1 stages row a by TMA (two row buffers per chain in shared memory),
 // 0 reads it through L1 (no buffers: more chains fit in shared memory), 2 is
 // 0 with node-weighted energy records (for runs that ask for them).
-template <typename JT, int RULE, int NB, int G, int STAGE, int MAXT>
+template <typename JT, int RULE, int NB, int G, int STAGE, int MAXT, bool RCH = false>
 __global__ void __launch_bounds__(MAXT, 1)
     step_kernel(const JobDev* __restrict__ jobs, const WorkItem* __restrict__ items, uint32_t n_items,
                 uint32_t* __restrict__ queue, uint32_t nsteps, uint32_t per_chain) {
@@ -884,7 +890,7 @@ __global__ void __launch_bounds__(MAXT, 1)
         __syncwarp();
         if (t1 > t0) {
             if (warp_busy) {
-                chain_loop<JT, RULE, NB, G, STAGE, (MAXT <= 512 ? 8 : 2)>(jb, own, chain, cm, partner_off, t0, t1, acc,
+                chain_loop<JT, RULE, NB, G, STAGE, (MAXT <= 512 ? 8 : 2), RCH>(jb, own, chain, cm, partner_off, t0, t1, acc,
                                                                           phase, dead,
                                                    n_flips, n_rows);
             } else {
@@ -913,42 +919,47 @@ __global__ void __launch_bounds__(MAXT, 1)
     }
 }
 
-template <typename JT, int RULE, int NB, int G, int STAGE, int MAXT>
+template <typename JT, int RULE, int NB, int G, int STAGE, int MAXT, bool RCH = false>
 cudaError_t launch_variant(const JobDev* jobs, const WorkItem* items, uint32_t n_items, uint32_t* queue,
                            uint32_t nsteps, uint32_t W, uint32_t per_chain, uint32_t grid, cudaStream_t st) {
     const size_t smem = static_cast<size_t>(per_chain) * W * (32 / G);
-    cudaError_t e = cudaFuncSetAttribute(step_kernel<JT, RULE, NB, G, STAGE, MAXT>,
+    cudaError_t e = cudaFuncSetAttribute(step_kernel<JT, RULE, NB, G, STAGE, MAXT, RCH>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    step_kernel<JT, RULE, NB, G, STAGE, MAXT><<<grid, 32 * W, smem, st>>>(jobs, items, n_items, queue, nsteps, per_chain);
+    step_kernel<JT, RULE, NB, G, STAGE, MAXT, RCH><<<grid, 32 * W, smem, st>>>(jobs, items, n_items, queue, nsteps,
+                                                                               per_chain);
     return cudaGetLastError();
 }
 
-template <typename JT, int RULE, int NB, int G, int STAGE, int MAXT>
+template <typename JT, int RULE, int NB, int G, int STAGE, int MAXT, bool RCH = false>
 int occupancy_variant(uint32_t W, uint32_t per_chain) {
     const size_t smem = static_cast<size_t>(per_chain) * W * (32 / G);
     int n = 0;
-    if (cudaFuncSetAttribute(step_kernel<JT, RULE, NB, G, STAGE, MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(smem)) != cudaSuccess)
+    if (cudaFuncSetAttribute(step_kernel<JT, RULE, NB, G, STAGE, MAXT, RCH>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
         return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<JT, RULE, NB, G, STAGE, MAXT>, 32 * W, smem) !=
-        cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<JT, RULE, NB, G, STAGE, MAXT, RCH>, 32 * W,
+                                                      smem) != cudaSuccess)
         return 0;
     return n;
 }
 
-// The register budget follows the CTA size: the largest variant that fits W warps.
-template <typename JT, int RULE, int NB, int G, int STAGE>
+// The register budget follows the CTA size: the largest variant that fits W
+// warps.  RCH (Metropolis) selects the chunked field update of the
+// 128-register variant; the larger CTAs have one form.
+template <typename JT, int RULE, int NB, int G, int STAGE, bool RCH = false>
 cudaError_t launch_g(const JobDev* jobs, const WorkItem* items, uint32_t n_items, uint32_t* queue,
                      uint32_t nsteps, uint32_t W, uint32_t per_chain, uint32_t grid, cudaStream_t st) {
-    if (W <= 16) return launch_variant<JT, RULE, NB, G, STAGE, 512>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
+    if (W <= 16)
+        return launch_variant<JT, RULE, NB, G, STAGE, 512, RCH>(jobs, items, n_items, queue, nsteps, W, per_chain,
+                                                                grid, st);
     if (W <= 20) return launch_variant<JT, RULE, NB, G, STAGE, 640>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
     if (W <= 24) return launch_variant<JT, RULE, NB, G, STAGE, 768>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
     return launch_variant<JT, RULE, NB, G, STAGE, 1024>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
 }
-template <typename JT, int RULE, int NB, int G, int STAGE>
+template <typename JT, int RULE, int NB, int G, int STAGE, bool RCH = false>
 int occupancy_g(uint32_t W, uint32_t per_chain) {
-    if (W <= 16) return occupancy_variant<JT, RULE, NB, G, STAGE, 512>(W, per_chain);
+    if (W <= 16) return occupancy_variant<JT, RULE, NB, G, STAGE, 512, RCH>(W, per_chain);
     if (W <= 20) return occupancy_variant<JT, RULE, NB, G, STAGE, 640>(W, per_chain);
     if (W <= 24) return occupancy_variant<JT, RULE, NB, G, STAGE, 768>(W, per_chain);
     return occupancy_variant<JT, RULE, NB, G, STAGE, 1024>(W, per_chain);
@@ -977,6 +988,17 @@ cudaError_t launch_rule(int nb, int G, const JobDev* jobs, const WorkItem* items
             }
         }
     }
+    if constexpr (RULE == 1) {  // Metropolis: nb = 2 names the chunked field update (one Philox block)
+        if (nb == 2) {
+            switch (G) {
+                case 4: return launch_g<JT, RULE, 1, 4, STAGE, true>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
+                case 8: return launch_g<JT, RULE, 1, 8, STAGE, true>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
+                case 16: return launch_g<JT, RULE, 1, 16, STAGE, true>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
+                case 32: return launch_g<JT, RULE, 1, 32, STAGE, true>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
+                default: return cudaErrorInvalidValue;
+            }
+        }
+    }
     if (nb != 1) return cudaErrorInvalidValue;
     switch (G) {
         case 4: return launch_g<JT, RULE, 1, 4, STAGE>(jobs, items, n_items, queue, nsteps, W, per_chain, grid, st);
@@ -1001,6 +1023,17 @@ int occupancy_rule(int nb, int G, uint32_t W, uint32_t per_chain) {
             switch (G) {
                 case 8: return occupancy_g<JT, RULE, 4, 8, STAGE>(W, per_chain);
                 case 16: return occupancy_g<JT, RULE, 4, 16, STAGE>(W, per_chain);
+                default: return 0;
+            }
+        }
+    }
+    if constexpr (RULE == 1) {
+        if (nb == 2) {
+            switch (G) {
+                case 4: return occupancy_g<JT, RULE, 1, 4, STAGE, true>(W, per_chain);
+                case 8: return occupancy_g<JT, RULE, 1, 8, STAGE, true>(W, per_chain);
+                case 16: return occupancy_g<JT, RULE, 1, 16, STAGE, true>(W, per_chain);
+                case 32: return occupancy_g<JT, RULE, 1, 32, STAGE, true>(W, per_chain);
                 default: return 0;
             }
         }

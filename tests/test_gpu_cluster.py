@@ -2,9 +2,9 @@
 fields and columns of J spread over the CTAs of a thread-block cluster.
 +-J runs follow the oracle bit for bit at every cluster size (trajectory,
 trace, records, final spins and fields), Gaussian runs equal the whole-warp
-layout bit for bit (the same arithmetic in every CTA), the autotuner may pick
-the layout without changing results, and the slice copy's bounded wait
-expires cleanly."""
+layout bit for bit (the same arithmetic in every CTA, records included), the
+autotuner may pick the layout without changing results, and the slice copy's
+bounded wait expires cleanly."""
 import numpy as np
 import pytest
 
@@ -112,9 +112,9 @@ def _gauss_runs(st, N, specs, steps, R):
 def test_gauss_cluster_layout_equals_whole_warp_chains(N, ctas):
     # Gaussian couplings: every CTA computes the candidate energies, weights
     # and scan with the 32-lane arithmetic and updates its slice element by
-    # element as the warp layout does, so trajectories and fields are equal
-    # bit for bit; the energy records differ only in the order of partial sums
-    # (sizes whose columns of fp32 J fit a CTA at each cluster size)
+    # element as the warp layout does, and rank 0 sums the energy records in
+    # that layout's order, so trajectories, fields and records are equal bit
+    # for bit (sizes whose columns of fp32 J fit a CTA at each cluster size)
     torch = need_gpu()
     steps, R = 600, 100
     specs = [(32, 0, 2, 1.0), (128, 0, 3, 2.0), (200, 0, 1, 0.5), (1, 1, 2, 1.0)]
@@ -135,14 +135,8 @@ def test_gauss_cluster_layout_equals_whole_warp_chains(N, ctas):
     for i, ((oa, sa, ta), (ob, sb, tb)) in enumerate(zip(*res)):
         assert np.array_equal(ta, tb), i
         assert np.array_equal(sa[0], sb[0]) and np.array_equal(sa[1], sb[1]), i
-        assert np.array_equal(oa[1], ob[1]) and np.array_equal(oa[2], ob[2]), i  # q, accepted
-        # energies: each lane adds at most Npad/32 exact products s_k h_k in
-        # fp32 in either layout, grouped differently; relative rounding of the
-        # sum of |s h| below (Npad/32 + 1) 2^-24, i.e. < 2e-6 at Npad = 512
-        tol = (N / 32 + 1) * 2.0 ** -24
-        bound = tol * 0.5 * np.abs(sa[0].astype(np.float64) * sa[1].astype(np.float64)).sum(axis=1)
-        assert np.all(np.abs(oa[0][-1] - ob[0][-1]) <= bound), i
-        assert np.allclose(oa[0], ob[0], rtol=2 * tol, atol=0), i
+        for x, y in zip(oa, ob):  # energies, overlaps, accepted counts
+            assert np.array_equal(x, y), i
 
 
 def test_gauss_cluster_layout_decisions_replay_in_the_oracle():
