@@ -254,6 +254,8 @@ struct sk_run {
     uint64_t* dstep = nullptr;
     int* derr = nullptr;
     void* dSop = nullptr;                 // spins as tensor-core operands
+    bool sop_valid = false;               // dSop holds the current spins (queued work included)
+    unsigned int* dCnt = nullptr;         // per 32 chains: the recompute's tile arrivals (zero between)
     double* ddE = nullptr;                // per chain energy drift accumulator
     unsigned long long* dstats = nullptr; // [0..2] periodic recomputes, [3..5] last explicit one
     uint64_t n_recomputes = 0;
@@ -465,6 +467,7 @@ sk_status init_commit(sk_run* r, const int8_t* dinit, bool on_side) {
         if (s != SK_OK) return s;
         SK_CU(sk::launch_recompute(in->kind, r->ds, r->dh, nullptr, r->dSop, in->dJop, r->ddE, r->dstats,
                                    r->derr, r->chains, in->Npad, 3, 3, in->scale, cs));
+        r->sop_valid = true;  // the conversion of the start spins
     }
     SK_CU(cudaMemsetAsync(r->dstats, 0, 6 * sizeof(unsigned long long), cs));
     SK_CU(cudaMemsetAsync(r->ddE, 0, static_cast<size_t>(r->chains) * sizeof(double), cs));
@@ -492,6 +495,7 @@ void free_run_buffers(sk_run* r) {
     cudaFree(r->dstep);
     cudaFree(r->derr);
     cudaFree(r->dSop);
+    cudaFree(r->dCnt);
     cudaFree(r->ddE);
     cudaFree(r->dstats);
     cudaFree(r->dstage);
@@ -506,6 +510,11 @@ sk_status ensure_recompute(sk_run* r, cudaStream_t cs, bool prepare_j) {
     sk_status s = SK_OK;
     if (!in->dJop) s = dalloc(&in->dJop, sk::recompute_j_bytes(in->kind, in->Npad));
     if (s == SK_OK && !r->dSop) s = dalloc(&r->dSop, sk::recompute_s_bytes(in->kind, r->chains, in->Npad));
+    if (s == SK_OK && !r->dCnt) {  // groups of 32 chains of the 128-chain tiles
+        const size_t words = 4 * ((static_cast<size_t>(r->chains) + 127) / 128);
+        s = dalloc(&r->dCnt, words * sizeof(unsigned int));
+        if (s == SK_OK) SK_CU(cudaMemsetAsync(r->dCnt, 0, words * sizeof(unsigned int), cs));
+    }
     if (s == SK_OK && !r->ddE) {
         s = dalloc(&r->ddE, static_cast<size_t>(r->chains) * sizeof(double));
         if (s == SK_OK) SK_CU(cudaMemsetAsync(r->ddE, 0, static_cast<size_t>(r->chains) * sizeof(double), cs));
@@ -531,7 +540,8 @@ sk_status periodic_recompute(sk_run* r) {
     sk_instance* in = r->inst;
     const uint32_t mode = in->kind == SK_J_PM1 ? 0u : 1u;
     SK_CU(sk::launch_recompute(in->kind, r->ds, r->dh, nullptr, r->dSop, in->dJop, r->ddE, r->dstats, r->derr,
-                               r->chains, in->Npad, terms_of(r), mode, in->scale, in->st));
+                               r->chains, in->Npad, terms_of(r), mode, in->scale, in->st, 0, r->sop_valid, r->dCnt));
+    r->sop_valid = true;
     ++r->n_recomputes;
     return SK_OK;
 }
@@ -816,6 +826,9 @@ sk_status mcmcmc_create(sk_instance* in, const sk_run_params* p, sk_run** out) {
     j.fault = r->p.fault_inject;
     root_setup(j, r->p.K, r->p.rule == SK_RULE_MCMCMC ? r->p.p_center : 0.0);
     s = init_state(r, p->init_spins, p->init_mem);
+    // runs that recompute periodically have the step kernels write their
+    // spins' tensor-core operands too
+    j.s_op = r->p.recompute_every ? r->dSop : nullptr;
     if (s == SK_OK) {
         sk_run* one[1] = {r};
         s = mcmcmc_batch_create(one, 1, 0, &r->self);
@@ -931,6 +944,7 @@ sk_status mcmcmc_reset_many(sk_run* const* runs, uint32_t n, const int8_t* const
     for (uint32_t i = 0; i < n; ++i)
         if (dinit[i] && dinit[i] == runs[i]->dstage) SK_CU(cudaEventRecord(runs[i]->ev_sfree, bs));
     SK_CU(sk::launch_set_fields_batch(runs[0]->inst->kind, rs.data(), n, bs, true));
+    for (uint32_t i = 0; i < n; ++i) runs[i]->sop_valid = true;  // written by the start kernel
     for (uint32_t i = 0; i < n; ++i) {
         runs[i]->n_recomputes = 0;
         runs[i]->step = 0;
@@ -1094,7 +1108,8 @@ sk_status mcmcmc_recompute(sk_run* r, uint32_t mode, uint32_t terms, sk_recomput
     SK_CU(cudaMemsetAsync(r->dstats + 3, 0, 3 * sizeof(unsigned long long), st));
     cudaError_t e = sk::launch_recompute(in->kind, r->ds, r->dh, dout, r->dSop, in->dJop, r->ddE, r->dstats + 3,
                                          r->derr, r->chains, in->Npad, terms ? terms : 3u, mode, in->scale, st,
-                                         r->job.fault & sk::kFaultWithholdTile);
+                                         r->job.fault & sk::kFaultWithholdTile, r->sop_valid, r->dCnt);
+    r->sop_valid = true;
     if (!stats && mode != 2) {  // enqueue only
         if (e != cudaSuccess) return fail(SK_ERR_CUDA, "recompute: %s", cudaGetErrorString(e));
         return SK_OK;
@@ -1549,7 +1564,12 @@ sk_status launch_segment(sk_batch* b, uint64_t steps, int only = -1) {
         const cudaError_t e = sk::launch_bump_steps(b->djobs, static_cast<uint32_t>(b->runs.size()), steps, b->st);
         if (e != cudaSuccess) return fail(SK_ERR_CUDA, "step counters: %s", cudaGetErrorString(e));
     }
-    for (sk_run* r : b->runs) r->step = std::min<uint64_t>(r->step + steps, r->job.step_limit);
+    for (sk_run* r : b->runs) {
+        r->step = std::min<uint64_t>(r->step + steps, r->job.step_limit);
+        // the step and cluster kernels rewrite the operands of runs that keep
+        // them; the graph kernel does not
+        r->sop_valid = r->job.s_op != nullptr && !r->p.graph;
+    }
     return SK_OK;
 }
 }  // namespace
@@ -1777,7 +1797,10 @@ sk_status mcmcmc_batch_autotune(sk_batch* b, uint32_t trial_steps, uint32_t* out
             }
             b->tuned[key] = best;
         }
-        for (size_t i = 0; i < b->runs.size(); ++i) b->runs[i]->step = mirror[i];
+        for (size_t i = 0; i < b->runs.size(); ++i) {
+            b->runs[i]->step = mirror[i];
+            b->runs[i]->sop_valid = false;  // the trials' spins, not the restored ones
+        }
         std::vector<JobDev> jobs;
         for (sk_run* r : b->runs) jobs.push_back(r->job);
         cudaMemcpy(b->djobs, jobs.data(), jobs.size() * sizeof(JobDev), cudaMemcpyHostToDevice);

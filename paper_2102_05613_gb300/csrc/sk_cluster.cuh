@@ -729,6 +729,16 @@ __global__ void __launch_bounds__(32 * kClusterMaxChains, 1)
                 gs[k] = cm.s[k];
                 reinterpret_cast<uint32_t*>(gh)[k] = reinterpret_cast<const uint32_t*>(cm.h)[k];
             }
+            if (jb.s_op) {  // the spins as tensor-core operands for the next recompute
+                const size_t o = static_cast<size_t>(chain) * npad + lo;
+                for (uint32_t k = lane; k < ws; k += 32) {
+                    const int v = cm.s[k];
+                    if constexpr (sizeof(JT) == 1)
+                        static_cast<uint8_t*>(jb.s_op)[o + k] = v == 0 ? 0 : (v > 0 ? 0x38 : 0xB8);
+                    else
+                        static_cast<uint16_t*>(jb.s_op)[o + k] = v == 0 ? 0 : (v > 0 ? 0x3F80 : 0xBF80);
+                }
+            }
             if (rank == 0 && lane == 0) {
                 jb.acc_run[chain] = acc;
                 jb.work[2 * static_cast<size_t>(chain)] += n_flips;

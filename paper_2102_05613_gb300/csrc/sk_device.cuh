@@ -128,6 +128,39 @@ struct Types<float> {
 
 
 
+// Spins +-1 (padding 0) as tensor-core operands: four spins of a 32-bit word
+// as four e4m3 bytes (+-1.0 = 0x38 / 0xB8), or spins e, e+1 of it as two bf16
+// words (+-1.0 = 0x3F80 / 0xBF80).
+__device__ __forceinline__ uint32_t e4m3_of4(uint32_t w) {
+    uint32_t o = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int v = static_cast<int>(static_cast<int32_t>(w << (24 - 8 * e)) >> 24);
+        o |= static_cast<uint32_t>(v == 0 ? 0u : (v > 0 ? 0x38u : 0xB8u)) << (8 * e);
+    }
+    return o;
+}
+__device__ __forceinline__ uint32_t bf16_of2(uint32_t w, int e) {
+    uint32_t o = 0;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int v = static_cast<int>(static_cast<int32_t>(w << (24 - 8 * (e + k))) >> 24);
+        o |= static_cast<uint32_t>(v == 0 ? 0u : (v > 0 ? 0x3F80u : 0xBF80u)) << (16 * k);
+    }
+    return o;
+}
+// Sixteen spins (one 16-byte word) written as operands at spin index i16*16
+// of the operand array (bf: bf16, else e4m3).
+__device__ __forceinline__ void spins_to_op16(void* op, size_t i16, uint4 w, bool bf) {
+    if (bf) {
+        uint4* o = static_cast<uint4*>(op) + 2 * i16;
+        o[0] = make_uint4(bf16_of2(w.x, 0), bf16_of2(w.x, 2), bf16_of2(w.y, 0), bf16_of2(w.y, 2));
+        o[1] = make_uint4(bf16_of2(w.z, 0), bf16_of2(w.z, 2), bf16_of2(w.w, 0), bf16_of2(w.w, 2));
+    } else {
+        static_cast<uint4*>(op)[i16] = make_uint4(e4m3_of4(w.x), e4m3_of4(w.y), e4m3_of4(w.z), e4m3_of4(w.w));
+    }
+}
+
 // A field of the CTA's shared job descriptor read where it is used (a
 // volatile shared-memory load) instead of being held in a register across
 // the whole step loop.

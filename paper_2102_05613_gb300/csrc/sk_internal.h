@@ -54,6 +54,12 @@ struct alignas(16) JobDev {
     const void* gtab;
     uint32_t graph, arity, V;
     uint32_t fault;         // sk_run_params.fault_inject (tests of the bounded waits)
+    // the chains' spins as tensor-core operands [chains][Npad] (e4m3 bytes for
+    // +-J, bf16 words for Gaussian couplings), written by the step kernels when
+    // they write the spins back, so that the periodic recompute needs no
+    // conversion; null when the run does not recompute periodically
+    void* s_op;
+    uint64_t pad_;
 };
 static_assert(sizeof(JobDev) % 16 == 0, "JobDev is copied as 16-byte words");
 
@@ -222,10 +228,15 @@ struct RecomputeSet {
 };
 cudaError_t launch_set_fields_batch(uint32_t kind, const RecomputeSet* sets, uint32_t n, cudaStream_t st,
                                    bool spins_converted = false);
+// spins_converted: s_op already holds the spins (written by the step
+// kernels); cnt: ceil(chains / 32) zeroed words that the check and resync
+// modes use to find the last tile of each group of 32 chains, which then
+// takes the group's energy-drift maximum (and leaves the words zero).
 cudaError_t launch_recompute(uint32_t kind, const int8_t* s, void* h, float* out, void* s_op,
                              const void* j_op, double* dE, unsigned long long* stats, int* err,
                              uint32_t chains, uint32_t npad, uint32_t terms, uint32_t mode, double scale,
-                             cudaStream_t st, uint32_t fault = 0);
+                             cudaStream_t st, uint32_t fault = 0, bool spins_converted = false,
+                             unsigned int* cnt = nullptr);
 
 }  // namespace sk
 struct sk_run;

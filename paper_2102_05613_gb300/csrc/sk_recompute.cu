@@ -36,6 +36,7 @@
 #include <set>
 #include <vector>
 
+#include "sk_device.cuh"
 #include "sk_internal.h"
 
 namespace sk {
@@ -130,6 +131,8 @@ struct Args {
     float* out;                     // OUTPUT mode: H [chains][npad]
     double* dE;                     // per chain: sum_n s_n (h_n - H_n)
     unsigned long long* stats;      // [0] max |h - H| (double bits), [1] mismatches, [2] max |dE|
+    unsigned int* cnt;              // per 32 chains: epilogue warps done with their rows (or null)
+    double scale;                   // energy scale of the drift
     int* err;
     uint32_t chains, npad, kblocks, terms, mode;  // mode: 0 check, 1 resync, 2 output, 3 set fields
     uint32_t pm1;
@@ -258,6 +261,37 @@ __device__ __forceinline__ void epilogue_rows(uint32_t taddr, const Args& args, 
             const double dmax = args.pm1 ? static_cast<double>(imax) : static_cast<double>(pmax);
             atomicMax(&args.stats[0], static_cast<unsigned long long>(__double_as_longlong(dmax)));
             if (mw) atomicAdd(&args.stats[1], static_cast<unsigned long long>(mw));
+        }
+        if (args.cnt) {
+            // the energy drift of these 32 chains is complete once the epilogue
+            // warps of all their tiles (two column halves each) have added to
+            // it: the last of them takes |scale/2 dE| of each chain into the
+            // maximum and clears dE and the count for the next recompute
+            const uint32_t arrivals = 2u * ((args.npad + BN - 1) / BN);
+            unsigned last = 0;
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence();
+                last = atomicAdd(&args.cnt[row0 / 32u], 1u) == arrivals - 1u;
+            }
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (last) {
+                __threadfence();
+                double e = 0.0;
+                if (row < args.chains)
+                    e = fabs(0.5 * args.scale * __longlong_as_double(static_cast<long long>(
+                                                    atomicExch(reinterpret_cast<unsigned long long*>(&args.dE[row]), 0ull))));
+                unsigned long long bmax = static_cast<unsigned long long>(__double_as_longlong(e));
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const unsigned long long y = __shfl_xor_sync(0xffffffffu, bmax, o);
+                    bmax = y > bmax ? y : bmax;
+                }
+                if (lane == 0) {
+                    atomicMax(&args.stats[2], bmax);  // non-negative doubles order as their bits
+                    args.cnt[row0 / 32u] = 0u;
+                }
+            }
         }
     }
     __syncwarp();
@@ -505,26 +539,10 @@ __global__ void finish_energy(double* dE, uint32_t chains, double scale, unsigne
     if ((threadIdx.x & 31) == 0) atomicMax(&stats[2], b);
 }
 
-// Operand conversion: spins +-1 (padding 0) -> e4m3 bytes or bf16 words.
+// Operand conversion: spins +-1 (padding 0) -> e4m3 bytes or bf16 words,
 // 16 spins per thread and iteration (n is a multiple of 32: rows of npad).
-__device__ __forceinline__ uint32_t e4m3_of4(uint32_t w) {  // four spins -> four e4m3 bytes
-    uint32_t o = 0;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        const int v = static_cast<int>(static_cast<int32_t>(w << (24 - 8 * e)) >> 24);
-        o |= static_cast<uint32_t>(v == 0 ? 0u : (v > 0 ? 0x38u : 0xB8u)) << (8 * e);  // e4m3: +-1.0
-    }
-    return o;
-}
-__device__ __forceinline__ uint32_t bf16_of2(uint32_t w, int e) {  // spins e, e+1 -> two bf16 words
-    uint32_t o = 0;
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int v = static_cast<int>(static_cast<int32_t>(w << (24 - 8 * (e + k))) >> 24);
-        o |= static_cast<uint32_t>(v == 0 ? 0u : (v > 0 ? 0x3F80u : 0xBF80u)) << (16 * k);  // bf16: +-1.0
-    }
-    return o;
-}
+using dev::bf16_of2;
+using dev::e4m3_of4;
 __global__ void spins_to_e4m3(const int8_t* __restrict__ s, uint8_t* __restrict__ o, size_t n) {
     const uint4* in = reinterpret_cast<const uint4*>(s);
     uint4* out = reinterpret_cast<uint4*>(o);
@@ -796,17 +814,19 @@ cudaError_t cached_maps(const void* s_op, const void* j_op, bool bf, uint32_t ch
 cudaError_t launch_recompute(uint32_t kind, const int8_t* s, void* h, float* out, void* s_op,
                              const void* j_op, double* dE, unsigned long long* stats, int* err,
                              uint32_t chains, uint32_t npad, uint32_t terms, uint32_t mode, double scale,
-                             cudaStream_t st, uint32_t fault) {
+                             cudaStream_t st, uint32_t fault, bool spins_converted, unsigned int* cnt) {
     const bool bf = kind != 0;
     if (!bf) terms = 1;
     if (terms < 1 || terms > 3) return cudaErrorInvalidValue;
     const size_t ns = static_cast<size_t>(chains) * npad;  // a multiple of 32
-    if (bf)
-        spins_to_bf16<<<grid1d(ns / 16), 256, 0, st>>>(s, static_cast<uint16_t*>(s_op), ns);
-    else
-        spins_to_e4m3<<<grid1d(ns / 16), 256, 0, st>>>(s, static_cast<uint8_t*>(s_op), ns);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
+    if (!spins_converted) {
+        if (bf)
+            spins_to_bf16<<<grid1d(ns / 16), 256, 0, st>>>(s, static_cast<uint16_t*>(s_op), ns);
+        else
+            spins_to_e4m3<<<grid1d(ns / 16), 256, 0, st>>>(s, static_cast<uint8_t*>(s_op), ns);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     // the operand maps of this (spins, couplings, shape): encoded once and
     // reused by later recomputes of the same buffers, so that the host work
     // between the conversion and the main kernel stays short
@@ -818,6 +838,8 @@ cudaError_t launch_recompute(uint32_t kind, const int8_t* s, void* h, float* out
     a.out = out;
     a.dE = dE;
     a.stats = stats;
+    a.cnt = mode < 2 ? cnt : nullptr;
+    a.scale = scale;
     a.err = err;
     a.chains = chains;
     a.npad = npad;
@@ -840,7 +862,7 @@ cudaError_t launch_recompute(uint32_t kind, const int8_t* s, void* h, float* out
                                                                               nullptr, nt, tiles_n);
     }
     e = cudaGetLastError();
-    if (e != cudaSuccess || mode >= 2) return e;
+    if (e != cudaSuccess || mode >= 2 || a.cnt) return e;
     finish_energy<<<(chains + 255) / 256, 256, 0, st>>>(dE, chains, scale, stats);
     return cudaGetLastError();
 }

@@ -906,6 +906,10 @@ __global__ void __launch_bounds__(MAXT, 1)
             uint4* gs = reinterpret_cast<uint4*>(jb.s + static_cast<size_t>(chain) * npad);
             const uint4* ss = reinterpret_cast<const uint4*>(cm.s);
             for (uint32_t k = g.gl; k < npad / 16; k += G) gs[k] = ss[k];
+            if (jb.s_op) {  // the spins as tensor-core operands for the next recompute
+                const size_t base16 = static_cast<size_t>(chain) * (npad / 16);
+                for (uint32_t k = g.gl; k < npad / 16; k += G) dev::spins_to_op16(jb.s_op, base16 + k, ss[k], bj != 1);
+            }
             uint4* gh = reinterpret_cast<uint4*>(static_cast<int*>(jb.h) + static_cast<size_t>(chain) * npad);
             const uint4* sh = reinterpret_cast<const uint4*>(cm.h);
             for (uint32_t k = g.gl; k < npad / 4; k += G) gh[k] = sh[k];
