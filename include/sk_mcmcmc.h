@@ -363,7 +363,10 @@ sk_status mcmcmc_free(sk_run* run);
 /*
  * mcmcmc_batch_create: plans work items (blocks of chains of one run) for
  * the runs.  warps_per_cta 0 lets the library choose (as many as fit);
- * otherwise at most that many warps per CTA (1..32).
+ * otherwise at most that many warps per CTA (1..32).  Whole-warp chains
+ * (32 lanes) of a pair share a CTA, so an odd count is raised by one for
+ * launch classes with runs of several chains; one warp is allowed where
+ * every run of the class has one chain.
  */
 sk_status mcmcmc_batch_create(sk_run* const* runs, uint32_t n_runs, uint32_t warps_per_cta,
                               sk_batch** out);

@@ -1348,6 +1348,8 @@ sk_status plan_batch(sk_batch* b) {
             if (tuned_cl) return fail(SK_ERR_INVALID_ARG, "launch class cannot take %u-CTA clusters", C);
         }
         const bool nw = ((c.key >> 60) & 1u) != 0;  // node-weighted records: rows through L1 only
+        bool single = true;  // every run of the class has one chain: no overlap pairs
+        for (uint32_t i : g.second) single = single && b->runs[i]->chains == 1;
         auto t = b->tuned.find(c.key);
         if (t != b->tuned.end()) {
             c.stage = (t->second >> 16) & 0xFFu;
@@ -1363,25 +1365,28 @@ sk_status plan_batch(sk_batch* b) {
             c.G = b->G_override ? std::min(32u, std::max(b->G_override, c.gmin)) : 32u;
             uint32_t fit = fit_warps(c.per_chain, c.G);
             while (c.G < 32 && fit < 1) fit = fit_warps(c.per_chain, c.G <<= 1);
+            if (c.G == 32 && single && fit < 1 && kSmemBudget >= c.per_chain) fit = 1;
             if (b->W_override) {
                 c.W = std::min(b->W_override, fit);
+                // whole-warp chains come in pairs (overlap q) unless every run has one chain
+                if (c.G == 32 && (c.W & 1u) && !single) c.W = std::min(c.W + 1u, fit);
             } else {
                 // as many warps as the class's chains need when spread over the
                 // SMs, at most as many as fit: a class of few chains gets small
                 // CTAs and with them the 128-register step kernel (8 row loads of
                 // the field update in flight), which is what a lone chain's
                 // latency wants; whole-warp chains keep an even count so that
-                // overlap pairs share a CTA
+                // overlap pairs share a CTA (one warp where every run has one chain)
                 uint64_t total = 0;
                 for (uint32_t i : g.second) total += b->runs[i]->chains;
                 const uint32_t spw = 32u / c.G;
                 const uint64_t per_sm = (total + static_cast<uint64_t>(sms) - 1) / static_cast<uint64_t>(sms);
                 uint32_t need = static_cast<uint32_t>(std::min<uint64_t>(32, (per_sm + spw - 1) / spw));
-                if (c.G == 32) need = std::max(2u, (need + 1u) & ~1u);
+                if (c.G == 32) need = single ? std::max(1u, need) : std::max(2u, (need + 1u) & ~1u);
                 c.W = std::max(1u, std::min(fit, need));
             }
         }
-        if (c.W < 1 || (c.G == 32 && c.W < 2))
+        if (c.W < 1 || (c.G == 32 && c.W < 2 && !single))
             return fail(SK_ERR_INVALID_ARG, "N too large: %u bytes of shared memory per chain", c.per_chain);
         c.cls = sk::step_class(r0->inst->kind, r0->p.rule, r0->p.K, c.G, nw ? 2u : c.stage, r0->inst->Npad);
         if (c.cls < 0) return fail(SK_ERR_INVALID_ARG, "no step kernel for K = %u with %u lanes per chain", r0->p.K, c.G);
@@ -1742,6 +1747,9 @@ sk_status mcmcmc_batch_autotune(sk_batch* b, uint32_t trial_steps, uint32_t* out
             float best_ms = 1e30f;
             std::vector<uint32_t> cand;  // (stage << 16) | (G << 8) | W
             const uint32_t max_stage = ((key >> 60) & 1u) ? 0u : 1u;  // node-weighted classes: no staging
+            bool single_k = true;  // one-chain runs only: whole-warp chains need no partner warp
+            for (const sk_run* r : b->runs)
+                if (class_key(r) == key) single_k = single_k && r->chains == 1;
             if ((key >> 59) & 1u) {  // graph classes: warps per chain and chains per CTA (even)
                 const uint32_t fitc = static_cast<uint32_t>(std::min<size_t>(32, kSmemBudget / cls0[k].per_chain)) & ~1u;
                 for (uint32_t nw : {1u, 2u, 4u, 8u, 16u})
@@ -1753,7 +1761,8 @@ sk_status mcmcmc_batch_autotune(sk_batch* b, uint32_t trial_steps, uint32_t* out
                     const uint32_t fit =
                         fit_warps(stage ? cls0[k].per_chain_staged : cls0[k].per_chain_direct, G);
                     for (uint32_t w : {32u, 24u, 20u, 16u, 12u, 8u, 6u, 4u, 2u, 1u})
-                        if (w <= fit && (G < 32 || (w & 1u) == 0)) cand.push_back((stage << 16) | (G << 8) | w);
+                        if (w <= std::max(fit, single_k ? 1u : 0u) && (G < 32 || (w & 1u) == 0 || single_k))
+                            cand.push_back((stage << 16) | (G << 8) | w);
                 }
             // star classes of few chains: the cluster-per-chain layout as well
             // (shapes the class cannot take fail to plan and are skipped)
