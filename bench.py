@@ -187,7 +187,7 @@ def run_reference(args):
 RC_N, RC_CHAINS, RC_ITERS = 2048, 8192, 20
 
 
-def recompute_report(stream, peaks, fp8_measured=None):
+def recompute_report(stream, peaks, fp8_measured=None, own_mma=None):
     """Times mcmcmc_recompute on +-J (FP8 e4m3, check) and Gaussian (bf16 x3,
     resync) couplings with N = 2048 and 8192 chains, and states the error of
     each recompute format against the FP64 product on 64 chains."""
@@ -229,6 +229,10 @@ def recompute_report(stream, peaks, fp8_measured=None):
                "executed_tflops": exec_flops / ms / 1e9, "peak_tflops": peak, "peak_source": src,
                "frac_executed": exec_flops / ms / 1e9 / peak,
                "check": st}
+        own = (own_mma or {}).get("own_mma_fp8_tflops" if kind == sk.SK_J_PM1 else "own_mma_bf16_tflops")
+        if own:  # against the kernel's own MMA loop with nothing else to do
+            ent["own_mma_tflops"] = own
+            ent["frac_of_own_mma"] = exec_flops / ms / 1e9 / own
         # error of each format against the FP64 product on the first 64 chains
         spins, _ = run.state()
         ex = (J.astype(np.float64) @ spins[:64].T.astype(np.float64)).T
@@ -790,6 +794,14 @@ def measure_peaks(stream):
     except Exception as e:  # noqa: BLE001 -- reported, and the nominal ratio is used instead
         out["fp8_tflops"] = None
         out["fp8_how"] = f"unavailable ({type(e).__name__}: {e})"
+    # the recompute kernel's own MMA loop with its operand ring filled once (no
+    # epilogue, no operand traffic): what its tcgen05 issue reaches at best
+    out["own_mma_fp8_tflops"] = max(sk.peak_tensor(sk.SK_J_PM1, tiles=64, reps=3, stream=stream) for _ in range(3))
+    out["own_mma_bf16_tflops"] = max(sk.peak_tensor(sk.SK_J_GAUSS, tiles=64, reps=3, stream=stream)
+                                     for _ in range(3))
+    out["own_mma_how"] = ("sk_peak_tensor: the recompute kernel, one CTA per SM, 64 tiles of 128 x 256 per CTA "
+                          "(K = 2048 e4m3 / 1024 bf16) issued over a 4-stage ring loaded once; best of 3 x 3 "
+                          "launches, CUDA events")
     return out
 
 
@@ -1036,7 +1048,7 @@ def run_ours(args):
         cpu = cpu_baseline(couplings)
     rc = None
     if rank == 0 and not args.no_recompute:
-        rc = recompute_report(stream, peaks, mp.get("fp8_tflops"))
+        rc = recompute_report(stream, peaks, mp.get("fp8_tflops"), mp)
     lat = latency_report(stream) if rank == 0 else None
     sg = setgen_report(stream) if rank == 0 else None
     sweep = config2_sweep(stream, insts) if (rank == 0 and not args.no_sweep) else None

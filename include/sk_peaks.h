@@ -1,6 +1,7 @@
 /*
  * sk_peaks.h -- measured ceilings of the memory levels that bound the
- * sampler's step kernel, for its roofline.
+ * sampler's step kernel, and of the tensor pipe as the field recompute's own
+ * MMA loop drives it, for their rooflines.
  *
  * The batched MCMCMC step is bound by the memory level that holds the
  * couplings and the chains' state: the couplings' rows come from L2 (through
@@ -49,6 +50,18 @@ sk_status sk_peak_l2_read(uint64_t working_set_bytes, uint32_t passes, uint32_t 
  */
 typedef enum { SK_PEAK_SMEM_VEC16 = 0, SK_PEAK_SMEM_GATHER4 = 1 } sk_peak_smem_mode;
 sk_status sk_peak_smem(uint32_t mode, uint32_t iters, uint32_t reps, void* stream, double* gbps);
+
+/*
+ * sk_peak_tensor: the tensor-pipe rate of the library's own field-recompute
+ * kernel (the tcgen05 MMA loop that the periodic J.S recompute runs) with
+ * nothing else to do: each CTA (one per SM) fills its 4-stage operand ring
+ * once by TMA and then issues the MMAs of `tiles` 128 x 256 output tiles over
+ * it (K = 2048 for kind 0, FP8 e4m3 with kind::f8f6f4; K = 1024 for kind 1,
+ * bf16 with kind::f16), accumulators in tensor memory, no epilogue work.
+ * *tflops = 2 x 128 x 256 x K x tiles x SMs / time (1e12 per second).
+ * kind 0 or 1; tiles 1..4096; reps >= 1.
+ */
+sk_status sk_peak_tensor(uint32_t kind, uint32_t tiles, uint32_t reps, void* stream, double* tflops);
 
 #ifdef __cplusplus
 }

@@ -232,6 +232,11 @@ cudaError_t launch_set_fields_batch(uint32_t kind, const RecomputeSet* sets, uin
 // kernels); cnt: ceil(chains / 32) zeroed words that the check and resync
 // modes use to find the last tile of each group of 32 chains, which then
 // takes the group's energy-drift maximum (and leaves the words zero).
+// Tensor-pipe probe: the recompute kernel with its operand ring filled once
+// and the MMAs re-issued over it (no epilogue), `tiles` 128 x 256 tiles of
+// K = 2048 (FP8, kind 0) or 1024 (bf16, kind 1) per CTA, one CTA per SM;
+// *tflops = 2 M N K per tile x tiles / time of `reps` launches.
+cudaError_t tensor_peak_probe(uint32_t kind, uint32_t tiles, uint32_t reps, cudaStream_t st, double* tflops);
 cudaError_t launch_recompute(uint32_t kind, const int8_t* s, void* h, float* out, void* s_op,
                              const void* j_op, double* dE, unsigned long long* stats, int* err,
                              uint32_t chains, uint32_t npad, uint32_t terms, uint32_t mode, double scale,

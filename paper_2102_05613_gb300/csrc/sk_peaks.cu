@@ -1,4 +1,5 @@
-// sk_peaks.cu -- measured ceilings of L2 and shared memory (sk_peaks.h).
+// sk_peaks.cu -- measured ceilings of L2 and shared memory, and the tensor
+// pipe under the recompute kernel's MMA loop (sk_peaks.h).
 //
 // Small probe kernels whose only work is loads, timed with CUDA events; the
 // step kernel's roofline divides its algorithmic bytes by these.  Every
@@ -195,4 +196,14 @@ out:
     if (e1) cudaEventDestroy(e1);
     if (sink) cudaFree(sink);
     return st_;
+}
+
+extern "C" sk_status sk_peak_tensor(uint32_t kind, uint32_t tiles, uint32_t reps, void* stream, double* tflops) {
+    if (!tflops) return pfail(SK_ERR_INVALID_ARG, "NULL output");
+    if (kind > 1) return pfail(SK_ERR_INVALID_ARG, "kind must be 0 (FP8) or 1 (bf16)");
+    if (tiles == 0 || tiles > 4096 || reps == 0) return pfail(SK_ERR_INVALID_ARG, "tiles must be 1..4096, reps >= 1");
+    const cudaError_t e = sk::tensor_peak_probe(kind, tiles, reps, static_cast<cudaStream_t>(stream), tflops);
+    if (e == cudaErrorLaunchTimeout) return pfail(SK_ERR_TIMEOUT, "a wait of the tensor probe expired");
+    if (e != cudaSuccess) return pfail(SK_ERR_CUDA, "tensor probe: %s", cudaGetErrorString(e));
+    return SK_OK;
 }

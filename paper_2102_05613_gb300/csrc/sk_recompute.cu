@@ -137,6 +137,7 @@ struct Args {
     uint32_t chains, npad, kblocks, terms, mode;  // mode: 0 check, 1 resync, 2 output, 3 set fields
     uint32_t pm1;
     uint32_t fault;                 // kFaultWithholdTile: tests of the bounded waits
+    uint32_t compute_only;          // tensor-pipe probe: operands loaded once, MMAs only
 };
 
 // Several operand sets in one launch: the tensor maps and arguments of each
@@ -384,6 +385,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
                 const uint32_t total = a->terms * a->kblocks;
                 for (uint32_t i = 0; i < total; ++i, ++g) {
                     const uint32_t st = g % NS;
+                    if (a->compute_only && g >= NS) break;  // the probe fills the ring once
                     if (g >= NS && !wait_bounded(saddr(&empty[st]), ((g / NS) - 1u) & 1u)) {
                         atomicExch(a->err, kDevTimeout);
                         *vdead = 1;
@@ -429,7 +431,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
                 const uint32_t total = a->terms * a->kblocks;
                 for (uint32_t i = 0; i < total; ++i, ++g) {
                     const uint32_t st = g % NS;
-                    if (!wait_bounded(saddr(&full[st]), (g / NS) & 1u)) {
+                    // (the probe waits for each stage once, then reuses it)
+                    if ((!a->compute_only || g < NS) && !wait_bounded(saddr(&full[st]), (g / NS) & 1u)) {
                         atomicExch(a->err, kDevTimeout);
                         *vdead = 1;
                     }
@@ -440,7 +443,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
 #pragma unroll
                     for (uint32_t kk = 0; kk < 4; ++kk)
                         mma<F8>(acc, sw128_desc(sa + 32 * kk), sw128_desc(sb + 32 * kk), idesc, (i | kk) != 0u);
-                    mma_commit(saddr(&empty[st]));
+                    if (!a->compute_only) mma_commit(saddr(&empty[st]));
                 }
                 mma_commit(saddr(&tfull[b]));  // completes when the tile's MMAs have
             }
@@ -465,7 +468,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
             // the first column block's fields and spins do not depend on the
             // accumulator: their loads go out before the wait for it
             RowBlock first;
-            load_row_block(first, *a, m0 + qd * 32u + lane, n0 + half * (BN / 2), m0 + qd * 32u + lane < a->chains);
+            if (!a->compute_only)
+                load_row_block(first, *a, m0 + qd * 32u + lane, n0 + half * (BN / 2), m0 + qd * 32u + lane < a->chains);
             // every lane waits; the outcome is made warp-uniform
             const bool ok = __all_sync(0xffffffffu, !*vdead && wait_bounded(saddr(&tfull[b]), (j >> 1) & 1u));
             if (!ok && lane == 0) {
@@ -474,8 +478,9 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const bool live = __all_sync(0xffffffffu, !*vdead);
-            epilogue_rows(tmem + ((qd * 32u) << 16) + 256u * b, *a, m0 + qd * 32u, n0, half * (BN / 2), ok && live,
-                          first);
+            if (!a->compute_only)
+                epilogue_rows(tmem + ((qd * 32u) << 16) + 256u * b, *a, m0 + qd * 32u, n0, half * (BN / 2),
+                              ok && live, first);
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(saddr(&tempty[b]));
@@ -848,6 +853,7 @@ cudaError_t launch_recompute(uint32_t kind, const int8_t* s, void* h, float* out
     a.mode = mode;
     a.pm1 = bf ? 0u : 1u;
     a.fault = fault;
+    a.compute_only = 0;
     const uint32_t tiles_n = (npad + BN - 1) / BN;
     const uint32_t nt = ((chains + BM - 1) / BM) * tiles_n;
     if (nt == 0) return cudaSuccess;
@@ -865,6 +871,70 @@ cudaError_t launch_recompute(uint32_t kind, const int8_t* s, void* h, float* out
     if (e != cudaSuccess || mode >= 2 || a.cnt) return e;
     finish_energy<<<(chains + 255) / 256, 256, 0, st>>>(dE, chains, scale, stats);
     return cudaGetLastError();
+}
+
+cudaError_t tensor_peak_probe(uint32_t kind, uint32_t tiles, uint32_t reps, cudaStream_t st, double* tflops) {
+    const bool bf = kind != 0;
+    const uint32_t kblocks = 16;  // K = 2048 (FP8) or 1024 (bf16): 16 stages of 128 bytes per row
+    const uint32_t K = kblocks * (bf ? 64u : 128u);
+    const uint32_t grid = static_cast<uint32_t>(sm_count());
+    const uint32_t nt = grid * tiles;
+    const size_t esz = bf ? 2 : 1;
+    void* A = nullptr;
+    void* B = nullptr;
+    int* err = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float ms = 0.0f;
+    // operands of each CTA's first tile (all zero: the values do not matter)
+    cudaError_t e = cudaMalloc(&A, static_cast<size_t>(grid) * BM * K * esz);
+    if (e == cudaSuccess) e = cudaMalloc(&B, static_cast<size_t>(BN) * K * esz);
+    if (e == cudaSuccess) e = cudaMalloc(&err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(A, 0, static_cast<size_t>(grid) * BM * K * esz, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(B, 0, static_cast<size_t>(BN) * K * esz, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), st);
+    CUtensorMap tA, tB;
+    if (e == cudaSuccess) e = make_map(&tA, A, bf, static_cast<uint64_t>(grid) * BM, K, BM);
+    if (e == cudaSuccess) e = make_map(&tB, B, bf, BN, K, BN);
+    Args a{};
+    a.err = err;
+    a.chains = grid * BM;
+    a.npad = K;
+    a.kblocks = kblocks;
+    a.terms = 1;
+    a.mode = 2;
+    a.pm1 = bf ? 0u : 1u;
+    a.compute_only = 1;
+    auto launch = [&]() {
+        // task t: rows (t / 1) * BM, columns 0; each CTA's first task is its own block of A
+        if (bf)
+            recompute_ws_kernel<false, false><<<grid, WS_THREADS, SMEM_BYTES, st>>>(tA, tB, tB, tB, a, nullptr,
+                                                                                   nullptr, nt, 1u);
+        else
+            recompute_ws_kernel<true, false><<<grid, WS_THREADS, SMEM_BYTES, st>>>(tA, tB, tB, tB, a, nullptr,
+                                                                                  nullptr, nt, 1u);
+        return cudaGetLastError();
+    };
+    if (e == cudaSuccess)
+        e = bf ? smem_attribute(recompute_ws_kernel<false, false>, 0) : smem_attribute(recompute_ws_kernel<true, false>, 1);
+    if (e == cudaSuccess) e = launch();  // warm-up
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    for (uint32_t r = 0; r < reps && e == cudaSuccess; ++r) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && herr) e = cudaErrorLaunchTimeout;  // a bounded wait expired
+    if (e == cudaSuccess)
+        *tflops = 2.0 * BM * BN * static_cast<double>(K) * nt * reps / (ms * 1e-3) / 1e12;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(A);
+    cudaFree(B);
+    cudaFree(err);
+    return e;
 }
 
 }  // namespace sk

@@ -37,7 +37,7 @@ EXPORTS = ["sk_create_instance", "sk_get_couplings", "sk_set_couplings", "sk_des
            "mcmcmc_batch_replay", "mcmcmc_batch_autotune", "mcmcmc_batch_info",
            "mcmcmc_batch_classes", "mcmcmc_batch_set_layout", "mcmcmc_batch_set_cluster",
            "mcmcmc_batch_free", "mcmcmc_run_noalloc", "sk_last_error",
-           "sk_peak_l2_read", "sk_peak_smem"]
+           "sk_peak_l2_read", "sk_peak_smem", "sk_peak_tensor"]
 
 
 class SKError(RuntimeError):
@@ -119,6 +119,7 @@ def lib(build_if_missing: bool = True):
             "mcmcmc_run_noalloc": [u32, u32, vp, d, u32, u32, u32, d, u64, u32, u64, vp, vp, vp],
             "sk_peak_l2_read": [u64, u32, u32, vp, C.POINTER(d)],
             "sk_peak_smem": [u32, u32, u32, vp, C.POINTER(d)],
+            "sk_peak_tensor": [u32, u32, u32, vp, C.POINTER(d)],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -490,6 +491,14 @@ def peak_smem(mode: int = SK_PEAK_SMEM_VEC16, iters: int = 4096, reps: int = 5, 
     loads or random 4-byte gathers (useful bytes)."""
     out = C.c_double(0.0)
     _check(lib().sk_peak_smem(int(mode), int(iters), int(reps), _stream_handle(stream), C.byref(out)))
+    return out.value
+
+
+def peak_tensor(kind: int = SK_J_PM1, tiles: int = 64, reps: int = 5, stream=None) -> float:
+    """sk_peak_tensor: TFLOP/s of the recompute kernel's own tcgen05 MMA loop
+    with its operand ring filled once (kind 0: FP8 e4m3, 1: bf16)."""
+    out = C.c_double(0.0)
+    _check(lib().sk_peak_tensor(int(kind), int(tiles), int(reps), _stream_handle(stream), C.byref(out)))
     return out.value
 
 

@@ -52,7 +52,9 @@ def test_binding_loads_and_reports_errors_without_compute():
 def test_peak_probes_reject_bad_arguments_without_compute():
     # the memory-ceiling probes (sk_peaks.h) check their arguments before any device work
     for call in (lambda: sk.peak_l2_read(1 << 20), lambda: sk.peak_l2_read(48 << 20, passes=0),
-                 lambda: sk.peak_smem(7), lambda: sk.peak_smem(sk.SK_PEAK_SMEM_VEC16, iters=0)):
+                 lambda: sk.peak_smem(7), lambda: sk.peak_smem(sk.SK_PEAK_SMEM_VEC16, iters=0),
+                 lambda: sk.peak_tensor(2), lambda: sk.peak_tensor(0, tiles=0),
+                 lambda: sk.peak_tensor(1, tiles=5000), lambda: sk.peak_tensor(0, reps=0)):
         with pytest.raises(sk.SKError) as e:
             call()
         assert e.value.status == sk.SK_ERR_INVALID_ARG

@@ -23,3 +23,15 @@ def test_peak_probes_are_plausible():
     assert 0.2 * nominal_smem < vec < 1.05 * nominal_smem, (vec, nominal_smem)
     assert 0.0 < gat < vec
     assert 0.0 < l2 < vec
+
+
+def test_tensor_probe_is_plausible():
+    # the recompute kernel's own MMA loop with nothing else to do: positive,
+    # below the part's nominal dense rates (4.5 PFLOP/s FP8, 2.25 PFLOP/s bf16)
+    # with room for clocks, and FP8 faster than bf16
+    need_gpu()
+    f8 = sk.peak_tensor(sk.SK_J_PM1, tiles=32, reps=2)
+    b16 = sk.peak_tensor(sk.SK_J_GAUSS, tiles=32, reps=2)
+    assert 100.0 < f8 < 4700.0, f8
+    assert 50.0 < b16 < 2400.0, b16
+    assert f8 > b16
