@@ -14,14 +14,19 @@
 //      the counters of the warp layouts (Philox4x32-10, (block, step, chain,
 //      stream)), so each CTA knows the proposals without communication;
 //   2  publish: the owner of each proposed site i = site_d writes the entry
-//      (h_i, J_ai, s_i) of slot d, a = site_1, into the exchange array of the
-//      chain in every CTA of the cluster (shared-memory stores across the
-//      cluster); Metropolis publishes its one site;
-//   3  one cluster barrier (arrive with release, wait with acquire), the
-//      only synchronisation of the step; the next step's sites are drawn
-//      between the arrive and the wait.  The exchange arrays alternate with
-//      the step's parity, so a CTA that passes the barrier of step t has
-//      every CTA's reads of step t-1's array behind it;
+//      (h_i, J_ai, s_i) of slot d, a = site_1, into its own exchange array and
+//      lists the slot; the warp's lanes then copy the listed entries into the
+//      same slot of every CTA's exchange array (lane l to CTA l mod C) as
+//      st.async stores whose bytes complete on the receiving CTA's own
+//      mbarrier, and every CTA sends every CTA a 4-byte header for the step;
+//      Metropolis publishes its one site;
+//   3  each CTA waits (bounded) on its own mbarrier for the step's 16 K + 4 C
+//      bytes, the only synchronisation of the step; the next step's sites are
+//      drawn while the stores travel.  The exchange arrays alternate with the
+//      step's parity: a CTA that has all headers of step t knows that every
+//      CTA has finished reading step t-1's array, which step t+1 reuses, and
+//      a receiver arms the barrier of step t+2 right after its wait of step t,
+//      before its own header of step t+1 can let any sender into step t+2;
 //   4  choose: every CTA computes the candidate energies, their minimum, the
 //      slot weights, the scan in slot order and the chosen slot from the
 //      exchange array with the arithmetic of the warp layout's 32-lane chains
