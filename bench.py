@@ -645,9 +645,19 @@ def run_uneven(args):
             runs.append(sk.Run(insts[-1], chains=sp["chains"], K=sp["K"], beta=sp["beta"], seed=3,
                                stream_id=i, record_every=R, max_records=args.warmup + args.steps + 2))
     torch.cuda.synchronize()
-    batch = sk.Batch(runs)
+    # --uneven-warps W: one CTA shape for every class (whole-warp chains, rows
+    # through L1, W warps per CTA) instead of the autotuner's per-class choice,
+    # the shape a single kernel for all classes would have to fix
+    # --uneven-fused W: every run in one persistent launch of W-warp CTAs
+    W = args.uneven_warps
+    batch = sk.Batch(runs, warps_per_cta=W)
     t0 = time.perf_counter()
-    batch.autotune(trial_steps=10)
+    if args.uneven_fused:
+        batch.set_fused(args.uneven_fused)
+    elif W:
+        batch.set_layout(32, 2)
+    else:
+        batch.autotune(trial_steps=10)
     tune_s = time.perf_counter() - t0
     batch.capture(R)
     batch.replay(args.warmup)
@@ -669,6 +679,10 @@ def run_uneven(args):
            "[0.5, 3], MCMCMC; one CUDA graph = 100 steps of every chain (one persistent launch per "
            "launch class)", "metric": UNIT, "value": cand / T, "mc_steps_per_s": cs / T,
            "ms_per_step": 1e3 * T / args.steps, "steps": args.steps, "warmup": args.warmup,
+           "layout": (f"one persistent launch for every run: 32 lanes per chain, rows through L1, "
+                      f"{args.uneven_fused} warps per CTA" if args.uneven_fused else
+                      f"one shape for every class: 32 lanes per chain, rows through L1, {W} warps per CTA"
+                      if W else "autotuned per class"),
            "autotune_s": tune_s, "classes": batch.classes(), "clocks": clk,
            "chains_total": sum(sp["chains"] for sp in specs)}
     batch.close()
@@ -1098,6 +1112,11 @@ def main():
                     help="comma-separated subset of the --ttt methods (the K=128 reference always runs)")
     ap.add_argument("--ttt-beta", type=float, default=TTT_BETA,
                     help="inverse temperature of the --ttt comparison (1 = T_c, the paper's setting)")
+    ap.add_argument("--uneven-warps", type=int, default=0,
+                    help="--config uneven: one CTA shape for every class (this many warps, 32 lanes per "
+                         "chain) instead of the autotuned per-class layouts")
+    ap.add_argument("--uneven-fused", type=int, default=0,
+                    help="--config uneven: every run in one persistent launch of this many warps per CTA")
     ap.add_argument("--ttt-n", type=int, default=TTT_N,
                     help="spins of the --ttt instance (512: its columns of J fit a cluster's shared memory)")
     ap.add_argument("--ttt-scale", type=int, default=1,

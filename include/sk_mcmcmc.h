@@ -397,7 +397,10 @@ sk_status mcmcmc_batch_replay(sk_batch* b, uint32_t times);
  * fastest; graph classes try 1, 2, 4, 8 and 16 warps per chain with every
  * even number of chains per CTA that fits; star classes of at most 64 chains
  * also try the cluster-per-chain layout (mcmcmc_batch_set_cluster) at every
- * cluster size and chains-per-cluster value the class can take.
+ * cluster size and chains-per-cluster value the class can take.  Then the
+ * whole batch is timed with those per-class launches and with its star runs
+ * in one fused launch (mcmcmc_batch_set_fused) of 4, 8 and 16 warps per CTA,
+ * and the fastest of the four is kept.
  * Trials start from a copy of the runs' state, which is restored afterwards,
  * and run with records and traces off: the runs' trajectories, records and
  * step counters are unchanged.  *warps_per_cta (may be NULL) receives the
@@ -456,6 +459,25 @@ sk_status mcmcmc_batch_set_layout(sk_batch* b, uint32_t lanes, uint32_t staging)
  */
 sk_status mcmcmc_batch_set_cluster(sk_batch* b, uint32_t ctas, uint32_t chains);
 
+/*
+ * mcmcmc_batch_set_fused: runs every star run of the batch (MCMCMC and
+ * Metropolis, any coupling kind, N, K; not graph runs nor runs that record
+ * node-weighted energies, which keep their own launches) in one persistent
+ * launch (warps_per_cta = 2, 4, 8 or 16), or returns to one launch per
+ * launch class (0).  The fused launch fixes one CTA shape for all its runs:
+ * whole-warp chains (32 lanes), rows of J through L1, the 128-register
+ * budget; each work item holds up to warps_per_cta chains of one run (an
+ * even number for runs of several chains) and is dispatched to its run's
+ * kernel variant (coupling kind, rule, Philox blocks per lane); items run
+ * largest first.  Results do not depend on it: trajectories and records equal
+ * those of whole-warp per-class launches (mcmcmc_batch_set_layout lanes 32,
+ * staging 2) bit for bit.  mcmcmc_batch_set_layout and a nonzero
+ * mcmcmc_batch_set_cluster turn it off; mcmcmc_batch_autotune may turn it on
+ * or off (it keeps whichever runs the whole batch faster).  Drops autotuned
+ * choices and a captured graph; the previous plan is kept on any error.
+ */
+sk_status mcmcmc_batch_set_fused(sk_batch* b, uint32_t warps_per_cta);
+
 /* Launch geometry of the batch (for reports): the largest grid, warps per
  * CTA and dynamic shared memory of the first launch class, total work items. */
 sk_status mcmcmc_batch_info(const sk_batch* b, uint32_t* grid, uint32_t* warps_per_cta,
@@ -472,7 +494,9 @@ sk_status mcmcmc_batch_info(const sk_batch* b, uint32_t* grid, uint32_t* warps_p
  * receives per class: kernel class, lanes per chain, shared bytes per chain,
  * warps per CTA, work items, CTAs.  Cluster-per-chain classes report kernel
  * class 1024 + 2 kind + rule, 32 x (CTAs per cluster) lanes per chain, the
- * bytes of one chain's slices per CTA and chains per cluster as warps per CTA.
+ * bytes of one chain's slices per CTA and chains per cluster as warps per CTA;
+ * the fused launch (mcmcmc_batch_set_fused) reports kernel class 2048, 32
+ * lanes, the largest run's bytes per chain and its warps per CTA.
  */
 sk_status mcmcmc_batch_classes(const sk_batch* b, uint32_t max, uint32_t* count, uint32_t* desc);
 

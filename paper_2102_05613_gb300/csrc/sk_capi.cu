@@ -202,6 +202,10 @@ struct sk_batch {
         // J columns each CTA holds, the coupling kind, rule and Philox blocks
         // per lane of the kernel
         uint32_t cluster = 0, jbytes = 0, kind = 0, rule = 0, nb = 0;
+        // fused launch: every star item of the batch in one kernel (fsmem:
+        // its dynamic shared memory)
+        bool fused = false;
+        uint32_t fsmem = 0;
     };
     std::vector<sk_run*> runs;
     std::vector<Class> classes;
@@ -214,6 +218,7 @@ struct sk_batch {
     uint32_t S_override = 0;             // mcmcmc_batch_set_layout staging (0: default = staged)
     uint32_t C_override = 0;             // mcmcmc_batch_set_cluster CTAs per cluster (0: warp layouts)
     uint32_t CW_override = 0;            // mcmcmc_batch_set_cluster chains per cluster (0: default)
+    uint32_t fused_W = 0;                // mcmcmc_batch_set_fused warps per CTA (0: per-class launches)
     JobDev* djobs = nullptr;
     WorkItem* ditems = nullptr;
     uint32_t* dqueue = nullptr;  // one work counter per class (up to kMaxClasses)
@@ -1259,11 +1264,21 @@ bool plan_cluster_class(const sk_batch* b, const std::vector<uint32_t>& idx, uin
 sk_status ensure_side_streams(sk_batch* b);
 void free_side_streams(sk_batch* b);
 
+// Runs the fused launch takes: star runs without node-weighted records.
+bool fused_eligible(const sk_run* r) { return !r->p.graph && !run_nw(r); }
+
 sk_status plan_batch(sk_batch* b) {
     std::map<uint64_t, std::vector<uint32_t>> groups;  // key -> run indices (in order)
+    std::vector<uint32_t> fidx;                        // runs of the fused launch
     const uint32_t n = static_cast<uint32_t>(b->runs.size());
-    for (uint32_t i = 0; i < n; ++i) groups[class_key(b->runs[i])].push_back(i);
-    if (groups.size() > kMaxClasses) return fail(SK_ERR_INVALID_ARG, "too many launch classes in one batch");
+    for (uint32_t i = 0; i < n; ++i) {
+        if (b->fused_W && fused_eligible(b->runs[i]))
+            fidx.push_back(i);
+        else
+            groups[class_key(b->runs[i])].push_back(i);
+    }
+    if (groups.size() + (fidx.empty() ? 0 : 1) > kMaxClasses)
+        return fail(SK_ERR_INVALID_ARG, "too many launch classes in one batch");
     std::vector<WorkItem> items;
     std::vector<sk_batch::Class> classes;
     int dev = 0, sms = 0;
@@ -1409,6 +1424,61 @@ sk_status plan_batch(sk_batch* b) {
         grid = std::max(grid, c.grid);
         classes.push_back(c);
     }
+    if (!fidx.empty()) {
+        // one launch of W-warp CTAs for all of them: whole-warp chains, rows
+        // through L1.  Each CTA gets the share of an SM's shared memory that
+        // its register budget (W warps x 32 lanes x 128 registers) leaves it,
+        // at least room for two chains of the largest run; an item holds as
+        // many chains of one run as fit, up to W, an even number for runs of
+        // several chains (overlap pairs share a CTA).
+        sk_batch::Class c{};
+        c.fused = true;
+        c.key = ~0ull;
+        c.W = b->fused_W;
+        c.G = 32;
+        c.gmin = 32;
+        c.cls = 2048;
+        uint32_t pcmax = 0;
+        bool multi = false;
+        for (uint32_t i : fidx) {
+            pcmax = std::max(pcmax, run_per_chain(b->runs[i], false));
+            multi = multi || b->runs[i]->chains > 1;
+        }
+        const uint32_t ctas = std::max<uint32_t>(1, 65536u / (32u * c.W * 128u));
+        // an SM's 228 KB less, per CTA, the kilobyte the hardware reserves and
+        // the kernel's static arrays (under a kilobyte)
+        size_t S = std::min<size_t>(kSmemBudget, (228u * 1024u) / ctas - 2048u);
+        S = std::max<size_t>(S, std::min<size_t>(kSmemBudget, (multi ? 2u : 1u) * pcmax));
+        if (pcmax > S || (multi && 2u * pcmax > S))
+            return fail(SK_ERR_INVALID_ARG, "N too large for the fused launch: %u bytes of shared memory per chain",
+                        pcmax);
+        c.fsmem = static_cast<uint32_t>(S);
+        c.per_chain = pcmax;
+        c.first_item = static_cast<uint32_t>(items.size());
+        for (uint32_t i : fidx) {
+            const sk_run* r = b->runs[i];
+            const uint32_t pc = run_per_chain(r, false);
+            uint32_t cpi = std::min<uint32_t>(c.W, static_cast<uint32_t>(S / pc));
+            if (r->chains > 1) cpi &= ~1u;
+            const uint32_t v = sk::fused_variant(r->inst->kind, r->p.rule, r->p.K, r->inst->Npad);
+            for (uint32_t ch = 0; ch < r->chains; ch += cpi)
+                items.push_back(WorkItem{i, ch, std::min(cpi, r->chains - ch), (v << 24) | pc});
+        }
+        // largest items first (work per step ~ chains x (Npad + 4 K)), so the
+        // launch does not end on a few long items
+        auto cost = [&](const WorkItem& w) {
+            const sk_run* r = b->runs[w.job];
+            return static_cast<uint64_t>(w.nchains) * (r->inst->Npad + 4u * r->p.K);
+        };
+        std::stable_sort(items.begin() + c.first_item, items.end(),
+                         [&](const WorkItem& x, const WorkItem& y) { return cost(x) > cost(y); });
+        c.n_items = static_cast<uint32_t>(items.size()) - c.first_item;
+        const int occ = sk::fused_occupancy(c.W, c.fsmem);
+        if (occ <= 0) return fail(SK_ERR_CUDA, "fused kernel cannot be resident with %u warps", c.W);
+        c.grid = std::min<uint32_t>(c.n_items, static_cast<uint32_t>(occ * sms));
+        grid = std::max(grid, c.grid);
+        classes.push_back(c);
+    }
     WorkItem* d = nullptr;
     sk_status s = dalloc(&d, items.size() * sizeof(WorkItem));
     if (s != SK_OK) return s;
@@ -1479,8 +1549,33 @@ sk_status mcmcmc_batch_set_layout(sk_batch* b, uint32_t lanes, uint32_t staging)
     b->S_override = staging;
     b->C_override = 0;
     b->CW_override = 0;
+    b->fused_W = 0;
     b->tuned.clear();
     return plan_batch(b);
+}
+
+sk_status mcmcmc_batch_set_fused(sk_batch* b, uint32_t warps_per_cta) {
+    if (!b) return fail(SK_ERR_INVALID_ARG, "batch is NULL");
+    const uint32_t W = warps_per_cta;
+    if (W != 0 && W != 2 && W != 4 && W != 8 && W != 16)
+        return fail(SK_ERR_INVALID_ARG, "warps per CTA of the fused launch must be 0, 2, 4, 8 or 16");
+    const uint32_t w0 = b->fused_W, c0 = b->C_override, cw0 = b->CW_override;
+    const std::map<uint64_t, uint32_t> t0 = b->tuned;
+    b->fused_W = W;
+    if (W) {
+        b->C_override = 0;
+        b->CW_override = 0;
+    }
+    b->tuned.clear();
+    const sk_status s = plan_batch(b);
+    if (s != SK_OK) {  // keep the previous plan
+        b->fused_W = w0;
+        b->C_override = c0;
+        b->CW_override = cw0;
+        b->tuned = t0;
+        plan_batch(b);
+    }
+    return s;
 }
 
 sk_status mcmcmc_batch_set_cluster(sk_batch* b, uint32_t ctas, uint32_t chains) {
@@ -1489,15 +1584,17 @@ sk_status mcmcmc_batch_set_cluster(sk_batch* b, uint32_t ctas, uint32_t chains) 
         return fail(SK_ERR_INVALID_ARG, "CTAs per cluster must be 0, 1, 2, 4, 8 or 16");
     if (chains != 0 && chains != 1 && chains != 2 && chains != 4 && chains != sk::kClusterMaxChains)
         return fail(SK_ERR_INVALID_ARG, "chains per cluster must be 0, 1, 2, 4 or 8");
-    const uint32_t c0 = b->C_override, w0 = b->CW_override;
+    const uint32_t c0 = b->C_override, w0 = b->CW_override, f0 = b->fused_W;
     const std::map<uint64_t, uint32_t> t0 = b->tuned;
     b->C_override = ctas;
     b->CW_override = chains;
+    if (ctas) b->fused_W = 0;
     b->tuned.clear();
     const sk_status s = plan_batch(b);
     if (s != SK_OK) {  // keep the previous plan
         b->C_override = c0;
         b->CW_override = w0;
+        b->fused_W = f0;
         b->tuned = t0;
         plan_batch(b);
     }
@@ -1551,7 +1648,9 @@ sk_status launch_segment(sk_batch* b, uint64_t steps, int only = -1) {
         const bool last = !fork && (only >= 0 || k + 1 == nc);
         cudaStream_t cs = fork ? b->side[k % nside] : b->st;
         cudaError_t e =
-            c.cluster ? sk::launch_cluster(b->djobs, b->ditems + c.first_item, c.n_items, b->dqueue + k, steps, c.kind,
+            c.fused ? sk::launch_fused(b->djobs, b->ditems + c.first_item, c.n_items, b->dqueue + k, steps, c.W,
+                                       c.fsmem, c.grid, static_cast<uint32_t>(b->runs.size()), last, cs)
+            : c.cluster ? sk::launch_cluster(b->djobs, b->ditems + c.first_item, c.n_items, b->dqueue + k, steps, c.kind,
                                            c.rule, c.nb, c.cluster, c.W, c.jbytes, c.per_chain, c.grid / c.cluster,
                                            static_cast<uint32_t>(b->runs.size()), last, cs)
             : c.graph ? sk::launch_graph(b->djobs, b->ditems + c.first_item, c.n_items, b->dqueue + k, steps, c.W,
@@ -1730,6 +1829,7 @@ sk_status mcmcmc_batch_autotune(sk_batch* b, uint32_t trial_steps, uint32_t* out
         quiet.push_back(j);
     }
     const std::map<uint64_t, uint32_t> tuned0 = b->tuned;
+    const uint32_t fused_before = b->fused_W;
     std::vector<uint64_t> mirror;
     for (sk_run* r : b->runs) mirror.push_back(r->step);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1737,9 +1837,16 @@ sk_status mcmcmc_batch_autotune(sk_batch* b, uint32_t trial_steps, uint32_t* out
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         cudaMemcpy(b->djobs, quiet.data(), quiet.size() * sizeof(JobDev), cudaMemcpyHostToDevice);
-        // each launch class is tuned on its own (its launches do not interact)
+        // each launch class is tuned on its own (its launches do not interact),
+        // with the star runs in their per-class launches
+        const uint32_t fused0 = b->fused_W;
+        if (fused0) {
+            b->fused_W = 0;
+            if ((s = plan_batch(b)) != SK_OK) b->fused_W = fused0;
+        }
         const std::vector<sk_batch::Class> cls0 = b->classes;
         for (size_t k = 0; k < cls0.size() && s == SK_OK; ++k) {
+            if (cls0[k].fused) continue;  // one shape for all its runs, set by mcmcmc_batch_set_fused
             const uint64_t key = cls0[k].key;
             uint32_t best = cls0[k].graph     ? ((cls0[k].nw << 16) | (32u << 8) | cls0[k].W)
                             : cls0[k].cluster ? ((cls0[k].cluster << 24) | (32u << 8) | cls0[k].W)
@@ -1806,6 +1913,45 @@ sk_status mcmcmc_batch_autotune(sk_batch* b, uint32_t trial_steps, uint32_t* out
             }
             b->tuned[key] = best;
         }
+        // then the whole batch with those per-class launches against the
+        // fused launch of its star runs at 4, 8 and 16 warps per CTA; the
+        // fastest is kept
+        bool star_runs = false;
+        for (const sk_run* r : b->runs) star_runs = star_runs || fused_eligible(r);
+        if (s == SK_OK && star_runs) {
+            auto time_batch = [&](float* out) -> sk_status {
+                sk_status s2 = launch_segment(b, trial_steps);  // warm-up
+                restore();
+                float t = 1e30f;
+                for (int rep = 0; rep < 2 && s2 == SK_OK; ++rep) {
+                    cudaEventRecord(e0, b->st);
+                    s2 = launch_segment(b, trial_steps);
+                    cudaEventRecord(e1, b->st);
+                    cudaEventSynchronize(e1);
+                    float m = 0;
+                    cudaEventElapsedTime(&m, e0, e1);
+                    t = std::min(t, m);
+                    restore();
+                }
+                *out = t;
+                return s2;
+            };
+            uint32_t best_w = 0;
+            float best_ms = 1e30f;
+            for (uint32_t w : {0u, 4u, 8u, 16u}) {
+                b->fused_W = w;
+                if (plan_batch(b) != SK_OK) continue;  // not resident: skip
+                float ms = 0;
+                if ((s = time_batch(&ms)) != SK_OK) break;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best_w = w;
+                }
+            }
+            b->fused_W = best_w;
+        } else if (s == SK_OK) {
+            b->fused_W = fused0;
+        }
         for (size_t i = 0; i < b->runs.size(); ++i) {
             b->runs[i]->step = mirror[i];
             b->runs[i]->sop_valid = false;  // the trials' spins, not the restored ones
@@ -1826,6 +1972,7 @@ sk_status mcmcmc_batch_autotune(sk_batch* b, uint32_t trial_steps, uint32_t* out
     }
     if (s != SK_OK) {
         b->tuned = tuned0;
+        b->fused_W = fused_before;
         plan_batch(b);
         return s;
     }
@@ -1841,7 +1988,10 @@ sk_status mcmcmc_batch_info(const sk_batch* b, uint32_t* grid, uint32_t* W, uint
     if (W) *W = b->classes.empty() ? 0 : b->classes[0].W;
     if (smem) {
         const sk_batch::Class* c = b->classes.empty() ? nullptr : &b->classes[0];
-        *smem = !c ? 0 : c->cluster ? c->jbytes + c->W * c->per_chain : c->per_chain * c->W * (32 / c->G);
+        *smem = !c ? 0
+                : c->fused ? c->fsmem
+                : c->cluster ? c->jbytes + c->W * c->per_chain
+                             : c->per_chain * c->W * (32 / c->G);
     }
     if (items) *items = b->n_items;
     return SK_OK;

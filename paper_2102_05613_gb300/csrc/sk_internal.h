@@ -188,6 +188,17 @@ cudaError_t launch_cluster_gauss(uint32_t rule, uint32_t nb, const JobDev* jobs,
 int occupancy_cluster_pm1(uint32_t rule, uint32_t nb, uint32_t C, uint32_t W, uint32_t jbytes, uint32_t pc);
 int occupancy_cluster_gauss(uint32_t rule, uint32_t nb, uint32_t C, uint32_t W, uint32_t jbytes, uint32_t pc);
 
+// Fused launch (sk_fused.cu): every star work item of a batch in one
+// persistent kernel of W warps per CTA (W <= 16), whole-warp chains, rows
+// through L1.  WorkItem::pad = (fused_variant << 24) | shared bytes per chain
+// of the item's run; `smem` the launch's dynamic shared memory (at least the
+// largest item's chains times its slice).
+uint32_t fused_variant(uint32_t kind, uint32_t rule, uint32_t K, uint32_t npad);
+cudaError_t launch_fused(const JobDev* jobs, const WorkItem* items, uint32_t n_items, uint32_t* queue,
+                         uint64_t nsteps, uint32_t W, uint32_t smem, uint32_t grid, uint32_t n_jobs, bool bump,
+                         cudaStream_t st);
+int fused_occupancy(uint32_t W, uint32_t smem);  // CTAs per SM (0: none)
+
 // MCMCMC on deeper graphs (sk_graph.cu): a team of nw warps per chain (1, 2,
 // 4, 8 or 16), W warps per CTA, i.e. W / nw chains (even; at most 14 when
 // nw > 1, the teams' named barriers), `per_chain` bytes of shared memory per

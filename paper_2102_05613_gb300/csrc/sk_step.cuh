@@ -251,44 +251,44 @@ __device__ __forceinline__ void update_fields(typename Types<JT>::H* hf, const J
                 }
             }
         }
-        return;
-    }
+    } else {
 #pragma unroll UNROLL
-    for (uint32_t k = 4u * gl; k < npad; k += 4u * G) {
-        if constexpr (sizeof(JT) == 1) {
-            int4 hv = *reinterpret_cast<int4*>(hf + k);
-            const uint32_t j1 = STAGED ? *reinterpret_cast<const uint32_t*>(r1 + k)
-                                       : __ldg(reinterpret_cast<const unsigned int*>(r1 + k));
-            hv.x -= c1 * sbyte(j1, 0);
-            hv.y -= c1 * sbyte(j1, 1);
-            hv.z -= c1 * sbyte(j1, 2);
-            hv.w -= c1 * sbyte(j1, 3);
-            if (c2) {
-                const uint32_t j2 = __ldg(reinterpret_cast<const unsigned int*>(r2 + k));
-                hv.x -= c2 * sbyte(j2, 0);
-                hv.y -= c2 * sbyte(j2, 1);
-                hv.z -= c2 * sbyte(j2, 2);
-                hv.w -= c2 * sbyte(j2, 3);
+        for (uint32_t k = 4u * gl; k < npad; k += 4u * G) {
+            if constexpr (sizeof(JT) == 1) {
+                int4 hv = *reinterpret_cast<int4*>(hf + k);
+                const uint32_t j1 = STAGED ? *reinterpret_cast<const uint32_t*>(r1 + k)
+                                           : __ldg(reinterpret_cast<const unsigned int*>(r1 + k));
+                hv.x -= c1 * sbyte(j1, 0);
+                hv.y -= c1 * sbyte(j1, 1);
+                hv.z -= c1 * sbyte(j1, 2);
+                hv.w -= c1 * sbyte(j1, 3);
+                if (c2) {
+                    const uint32_t j2 = __ldg(reinterpret_cast<const unsigned int*>(r2 + k));
+                    hv.x -= c2 * sbyte(j2, 0);
+                    hv.y -= c2 * sbyte(j2, 1);
+                    hv.z -= c2 * sbyte(j2, 2);
+                    hv.w -= c2 * sbyte(j2, 3);
+                }
+                *reinterpret_cast<int4*>(hf + k) = hv;
+            } else {
+                float4 hv = *reinterpret_cast<float4*>(hf + k);
+                const float4 j1 = STAGED ? *reinterpret_cast<const float4*>(r1 + k)
+                                         : __ldg(reinterpret_cast<const float4*>(r1 + k));
+                const float f1 = static_cast<float>(c1);
+                hv.x = fmaf(-f1, j1.x, hv.x);
+                hv.y = fmaf(-f1, j1.y, hv.y);
+                hv.z = fmaf(-f1, j1.z, hv.z);
+                hv.w = fmaf(-f1, j1.w, hv.w);
+                if (c2) {
+                    const float4 j2 = __ldg(reinterpret_cast<const float4*>(r2 + k));
+                    const float f2 = static_cast<float>(c2);
+                    hv.x = fmaf(-f2, j2.x, hv.x);
+                    hv.y = fmaf(-f2, j2.y, hv.y);
+                    hv.z = fmaf(-f2, j2.z, hv.z);
+                    hv.w = fmaf(-f2, j2.w, hv.w);
+                }
+                *reinterpret_cast<float4*>(hf + k) = hv;
             }
-            *reinterpret_cast<int4*>(hf + k) = hv;
-        } else {
-            float4 hv = *reinterpret_cast<float4*>(hf + k);
-            const float4 j1 = STAGED ? *reinterpret_cast<const float4*>(r1 + k)
-                                     : __ldg(reinterpret_cast<const float4*>(r1 + k));
-            const float f1 = static_cast<float>(c1);
-            hv.x = fmaf(-f1, j1.x, hv.x);
-            hv.y = fmaf(-f1, j1.y, hv.y);
-            hv.z = fmaf(-f1, j1.z, hv.z);
-            hv.w = fmaf(-f1, j1.w, hv.w);
-            if (c2) {
-                const float4 j2 = __ldg(reinterpret_cast<const float4*>(r2 + k));
-                const float f2 = static_cast<float>(c2);
-                hv.x = fmaf(-f2, j2.x, hv.x);
-                hv.y = fmaf(-f2, j2.y, hv.y);
-                hv.z = fmaf(-f2, j2.z, hv.z);
-                hv.w = fmaf(-f2, j2.w, hv.w);
-            }
-            *reinterpret_cast<float4*>(hf + k) = hv;
         }
     }
 }
@@ -434,14 +434,16 @@ __device__ __forceinline__ double graph_mean_dE(const JobDev& jb, uint32_t chain
 }
 
 // Record point shared by every thread of the CTA (two CTA barriers).  Only
-// `write` groups (real chains, not shadows) store.
+// `write` groups (real chains, not shadows) read their slices and store:
+// groups without a chain may have no slice of their own (the fused launch
+// sizes its shared memory for the item's chains only).
 template <typename JT, int RULE, int NB, int G, bool NWR>
 __device__ __noinline__ void record(const JobDev& jb, bool write, uint32_t chain, uint32_t rec, const int8_t* S,
                                     const void* h, int partner_off, uint32_t acc, uint32_t t_next) {
     const Grp<G> g;
     const int8_t* partner_s = S + partner_off;
     const bool store = write && rec < jb.rec_capacity;
-    const double E = chain_energy<JT, G>(S, h, jb.Npad, jb.scale, g);
+    const double E = write ? chain_energy<JT, G>(S, h, jb.Npad, jb.scale, g) : 0.0;
     // node-weighted energy of this state with the graph of the next step
     // (kernels built for runs that record it; groups without a chain skip it)
     double dm = 0.0;
@@ -456,7 +458,7 @@ __device__ __noinline__ void record(const JobDev& jb, bool write, uint32_t chain
         if (NWR) jb.rec_Enw[static_cast<size_t>(rec) * jb.chains + chain] = E + jb.scale * dm;
     }
     __syncthreads();
-    if ((chain & 1u) == 0u && chain + 1u < jb.chains) {
+    if (write && (chain & 1u) == 0u && chain + 1u < jb.chains) {
         int dot = 0;
         for (uint32_t k = 4u * g.gl; k < jb.Npad; k += 4u * G) {
             const uint32_t a = *reinterpret_cast<const uint32_t*>(S + k);
@@ -815,6 +817,85 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
     }
 }
 
+// One work item (a block of chains of one run) on the CTA: every warp loads
+// its chains' spins and fields into their shared-memory slices (per_chain
+// bytes each, chain slot = warp * 32/G + lane / G), runs the steps of the
+// launch, and writes the state back (spins, fields, the spins' tensor-core
+// operands of a recomputing run, counters).  Warps without a chain meet the
+// CTA's record barriers only.  The job descriptor `jb` (and, +-J, the start of
+// the weight table in `s_wt`) is in shared memory, filled by the caller.
+template <typename JT, int RULE, int NB, int G, int STAGE, int UNROLL, bool RCH>
+__device__ __forceinline__ void run_item(const WorkItem& wi, const JobDev& jb, unsigned char* smem, uint64_t* bars,
+                                         const unsigned long long* s_wt, uint32_t nsteps, uint32_t per_chain,
+                                         uint32_t& phase, bool& dead) {
+    constexpr int SPW = 32 / G;  // chains per warp
+    constexpr size_t bj = sizeof(JT);
+    const Grp<G> g;
+    const int warp = threadIdx.x >> 5;
+    const int slot = warp * SPW + (threadIdx.x & 31) / G;  // chain slot of this group in the CTA
+    const bool warp_busy = static_cast<uint32_t>(warp * SPW) < wi.nchains;  // some group has a chain
+    const bool own = static_cast<uint32_t>(slot) < wi.nchains;              // this group has a chain
+    const uint32_t chain = own ? wi.chain0 + slot : wi.chain0;              // shadows copy the first
+    const uint32_t npad = jb.Npad;
+    ChainMem cm;
+    unsigned char* base = smem + static_cast<size_t>(slot) * per_chain;
+    cm.s = reinterpret_cast<int8_t*>(base);
+    cm.h = base + npad;
+    cm.row[0] = base + 5 * static_cast<size_t>(npad);
+    cm.row[1] = base + (5 + bj) * static_cast<size_t>(npad);
+    cm.bar = &bars[2 * slot];
+    cm.b0 = reinterpret_cast<uint4*>(base + (STAGE == 1 ? 5 + 2 * bj : 5) * static_cast<size_t>(npad));
+    cm.wsm = s_wt;
+    // the overlap partner (chain slot ^ 1) lives one slice up or down
+    const int partner_off = (slot & 1) ? -static_cast<int>(per_chain) : static_cast<int>(per_chain);
+    const uint32_t t0 = static_cast<uint32_t>(*jb.step);
+    const uint32_t t1 =
+        static_cast<uint32_t>(min(static_cast<uint64_t>(t0) + nsteps, static_cast<uint64_t>(jb.step_limit)));
+    uint32_t acc = 0, n_flips = 0, n_rows = 0;
+    if (warp_busy) {
+        // load the chain's state: spins (npad bytes), fields (4 npad bytes)
+        const uint4* gs = reinterpret_cast<const uint4*>(jb.s + static_cast<size_t>(chain) * npad);
+        uint4* ss = reinterpret_cast<uint4*>(cm.s);
+        for (uint32_t k = g.gl; k < npad / 16; k += G) ss[k] = gs[k];
+        const uint4* gh =
+            reinterpret_cast<const uint4*>(static_cast<const int*>(jb.h) + static_cast<size_t>(chain) * npad);
+        uint4* sh = reinterpret_cast<uint4*>(cm.h);
+        for (uint32_t k = g.gl; k < npad / 4; k += G) sh[k] = gh[k];
+        acc = jb.acc_run[chain];
+    }
+    __syncwarp();
+    if (t1 > t0) {
+        if (warp_busy) {
+            chain_loop<JT, RULE, NB, G, STAGE, UNROLL, RCH>(jb, own, chain, cm, partner_off, t0, t1, acc, phase,
+                                                            dead, n_flips, n_rows);
+        } else {
+            // no chain in this warp: meet the CTA's record barriers only
+            const uint32_t R = jb.record_every;
+            if (R)
+                for (uint32_t p = (t0 / R + 1u) * R, r = t0 / R; p <= t1; p += R, ++r)
+                    record<JT, RULE, NB, G, STAGE == 2>(jb, false, chain, r, cm.s, cm.h, partner_off, 0u, p);
+        }
+    }
+    __syncwarp();
+    if (own) {
+        uint4* gs = reinterpret_cast<uint4*>(jb.s + static_cast<size_t>(chain) * npad);
+        const uint4* ss = reinterpret_cast<const uint4*>(cm.s);
+        for (uint32_t k = g.gl; k < npad / 16; k += G) gs[k] = ss[k];
+        if (jb.s_op) {  // the spins as tensor-core operands for the next recompute
+            const size_t base16 = static_cast<size_t>(chain) * (npad / 16);
+            for (uint32_t k = g.gl; k < npad / 16; k += G) dev::spins_to_op16(jb.s_op, base16 + k, ss[k], bj != 1);
+        }
+        uint4* gh = reinterpret_cast<uint4*>(static_cast<int*>(jb.h) + static_cast<size_t>(chain) * npad);
+        const uint4* sh = reinterpret_cast<const uint4*>(cm.h);
+        for (uint32_t k = g.gl; k < npad / 4; k += G) gh[k] = sh[k];
+        if (g.gl == 0) {
+            jb.acc_run[chain] = acc;
+            jb.work[2 * static_cast<size_t>(chain)] += n_flips;
+            jb.work[2 * static_cast<size_t>(chain) + 1] += n_rows;
+        }
+    }
+}
+
 // MAXT bounds the CTA size and so the register budget per thread
 // (65536 / MAXT): 1024 -> 64, 768 -> 80, 640 -> 96, 512 -> 128 registers.
 // STAGE: 1 stages row a by TMA (two row buffers per chain in shared memory),
@@ -841,7 +922,6 @@ __global__ void __launch_bounds__(MAXT, 1)
     __syncthreads();
     uint32_t phase = 0;
     bool dead = false;  // a bounded wait of this group expired: skip all further work
-    constexpr size_t bj = sizeof(JT);
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(queue, 1u);
         __syncthreads();
@@ -857,68 +937,8 @@ __global__ void __launch_bounds__(MAXT, 1)
                 s_wt[i] = i < jb.wlen ? reinterpret_cast<const unsigned long long*>(jb.W)[i] : 0ull;
             __syncthreads();
         }
-        const bool warp_busy = static_cast<uint32_t>(warp * SPW) < wi.nchains;  // some group has a chain
-        const bool own = static_cast<uint32_t>(slot) < wi.nchains;              // this group has a chain
-        const uint32_t chain = own ? wi.chain0 + slot : wi.chain0;              // shadows copy the first
-        const uint32_t npad = jb.Npad;
-        ChainMem cm;
-        unsigned char* base = smem + static_cast<size_t>(slot) * per_chain;
-        cm.s = reinterpret_cast<int8_t*>(base);
-        cm.h = base + npad;
-        cm.row[0] = base + 5 * static_cast<size_t>(npad);
-        cm.row[1] = base + (5 + bj) * static_cast<size_t>(npad);
-        cm.bar = &bars[2 * slot];
-        cm.b0 = reinterpret_cast<uint4*>(base + (STAGE == 1 ? 5 + 2 * bj : 5) * static_cast<size_t>(npad));
-        cm.wsm = s_wt;
-        // the overlap partner (chain slot ^ 1) lives one slice up or down
-        const int partner_off = (slot & 1) ? -static_cast<int>(per_chain) : static_cast<int>(per_chain);
-        const uint32_t t0 = static_cast<uint32_t>(*jb.step);
-        const uint32_t t1 = static_cast<uint32_t>(
-            min(static_cast<uint64_t>(t0) + nsteps, static_cast<uint64_t>(jb.step_limit)));
-        uint32_t acc = 0, n_flips = 0, n_rows = 0;
-        if (warp_busy) {
-            // load the chain's state: spins (npad bytes), fields (4 npad bytes)
-            const uint4* gs = reinterpret_cast<const uint4*>(jb.s + static_cast<size_t>(chain) * npad);
-            uint4* ss = reinterpret_cast<uint4*>(cm.s);
-            for (uint32_t k = g.gl; k < npad / 16; k += G) ss[k] = gs[k];
-            const uint4* gh = reinterpret_cast<const uint4*>(static_cast<const int*>(jb.h) +
-                                                             static_cast<size_t>(chain) * npad);
-            uint4* sh = reinterpret_cast<uint4*>(cm.h);
-            for (uint32_t k = g.gl; k < npad / 4; k += G) sh[k] = gh[k];
-            acc = jb.acc_run[chain];
-        }
-        __syncwarp();
-        if (t1 > t0) {
-            if (warp_busy) {
-                chain_loop<JT, RULE, NB, G, STAGE, (MAXT <= 512 ? 8 : 2), RCH>(jb, own, chain, cm, partner_off, t0, t1, acc,
-                                                                          phase, dead,
-                                                   n_flips, n_rows);
-            } else {
-                // no chain in this warp: meet the CTA's record barriers only
-                const uint32_t R = jb.record_every;
-                if (R)
-                    for (uint32_t p = (t0 / R + 1u) * R, r = t0 / R; p <= t1; p += R, ++r)
-                        record<JT, RULE, NB, G, STAGE == 2>(jb, false, chain, r, cm.s, cm.h, partner_off, 0u, p);
-            }
-        }
-        __syncwarp();
-        if (own) {
-            uint4* gs = reinterpret_cast<uint4*>(jb.s + static_cast<size_t>(chain) * npad);
-            const uint4* ss = reinterpret_cast<const uint4*>(cm.s);
-            for (uint32_t k = g.gl; k < npad / 16; k += G) gs[k] = ss[k];
-            if (jb.s_op) {  // the spins as tensor-core operands for the next recompute
-                const size_t base16 = static_cast<size_t>(chain) * (npad / 16);
-                for (uint32_t k = g.gl; k < npad / 16; k += G) dev::spins_to_op16(jb.s_op, base16 + k, ss[k], bj != 1);
-            }
-            uint4* gh = reinterpret_cast<uint4*>(static_cast<int*>(jb.h) + static_cast<size_t>(chain) * npad);
-            const uint4* sh = reinterpret_cast<const uint4*>(cm.h);
-            for (uint32_t k = g.gl; k < npad / 4; k += G) gh[k] = sh[k];
-            if (g.gl == 0) {
-                jb.acc_run[chain] = acc;
-                jb.work[2 * static_cast<size_t>(chain)] += n_flips;
-                jb.work[2 * static_cast<size_t>(chain) + 1] += n_rows;
-            }
-        }
+        run_item<JT, RULE, NB, G, STAGE, (MAXT <= 512 ? 8 : 2), RCH>(wi, jb, smem, bars, s_wt, nsteps, per_chain,
+                                                                     phase, dead);
         __syncthreads();  // s_job and the smem slices are reused by the next item
     }
 }

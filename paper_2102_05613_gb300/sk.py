@@ -36,6 +36,7 @@ EXPORTS = ["sk_create_instance", "sk_get_couplings", "sk_set_couplings", "sk_des
            "mcmcmc_batch_create", "mcmcmc_batch_advance", "mcmcmc_batch_capture",
            "mcmcmc_batch_replay", "mcmcmc_batch_autotune", "mcmcmc_batch_info",
            "mcmcmc_batch_classes", "mcmcmc_batch_set_layout", "mcmcmc_batch_set_cluster",
+           "mcmcmc_batch_set_fused",
            "mcmcmc_batch_free", "mcmcmc_run_noalloc", "sk_last_error",
            "sk_peak_l2_read", "sk_peak_smem", "sk_peak_tensor"]
 
@@ -114,6 +115,7 @@ def lib(build_if_missing: bool = True):
             "mcmcmc_batch_classes": [vp, u32, vp, vp],
             "mcmcmc_batch_set_layout": [vp, u32, u32],
             "mcmcmc_batch_set_cluster": [vp, u32, u32],
+            "mcmcmc_batch_set_fused": [vp, u32],
             "mcmcmc_batch_info": [vp, vp, vp, vp, vp],
             "mcmcmc_batch_free": [vp],
             "mcmcmc_run_noalloc": [u32, u32, vp, d, u32, u32, u32, d, u64, u32, u64, vp, vp, vp],
@@ -406,6 +408,11 @@ class Batch:
         `chains` chains per cluster (0 default, 1, 2, 4, 8), for every star
         class that can take it."""
         _check(lib().mcmcmc_batch_set_cluster(self.handle, int(ctas), int(chains)))
+
+    def set_fused(self, warps_per_cta: int):
+        """mcmcmc_batch_set_fused: every star run in one persistent launch of
+        warps_per_cta (2, 4, 8, 16) warps per CTA; 0 = one launch per class."""
+        _check(lib().mcmcmc_batch_set_fused(self.handle, int(warps_per_cta)))
 
     def info(self):
         v = [C.c_uint32(0) for _ in range(4)]
