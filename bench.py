@@ -525,6 +525,34 @@ def run_ttt(args):
 TTT_FEW_CHAINS = (1, 152)
 
 
+def run_cluster_one_chain(args):
+    """One Gaussian N = 512 chain, K = 32, beta = 1, on clusters of
+    --cluster-one-chain CTAs (the layout the autotuner picks for it): a warm-up
+    launch, then 2000 steps in one launch, CUDA events."""
+    import torch
+    from paper_2102_05613_gb300 import inputs, sk
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    inst = sk.Instance(inputs.couplings_gauss(512, 0), stream=stream)
+    run = sk.Run(inst, chains=1, K=32, beta=1.0, seed=1)
+    b = sk.Batch([run])
+    b.set_cluster(args.cluster_one_chain)
+    b.advance(200)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    b.advance(2000)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out = {"workload": "Gaussian SK N=512, one chain, K=32, beta=1", "ctas_per_cluster": args.cluster_one_chain,
+           "ns_per_step": 1e6 * e0.elapsed_time(e1) / 2000, "launch_classes": b.classes()}
+    b.close()
+    run.close()
+    inst.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_graph_one_chain(args):
     """The binary tree of depth 7 (Gaussian N = 1024, beta = 1), 500 steps in
     one launch: with one chain (8 warps per chain) the graph kernel's
@@ -628,7 +656,7 @@ def run_uneven(args):
     from paper_2102_05613_gb300 import inputs, sk
     torch.cuda.set_device(0)
     st = torch.cuda.Stream()
-    specs = inputs.uneven_batch(256, seed=0)
+    specs = inputs.uneven_batch(args.uneven_instances, seed=0)
     g = torch.Generator(device="cuda")
     insts, runs = [], []
     with torch.cuda.stream(st):
@@ -674,10 +702,10 @@ def run_uneven(args):
     T = ev[0][0].elapsed_time(ev[-1][1]) / 1e3
     cand = sum(sp["chains"] * sp["K"] for sp in specs) * R * args.steps
     cs = sum(sp["chains"] for sp in specs) * R * args.steps
-    out = {"config": "uneven batch", "workload": "256 SK instances, N uniform in 128..4096 (even: +-J "
+    out = {"config": "uneven batch", "workload": f"{len(specs)} SK instances, N uniform in 128..4096 (even: +-J "
            "int8, odd: Gaussian fp32), 256..2048 chains, K uniform in 16..256, beta uniform in "
-           "[0.5, 3], MCMCMC; one CUDA graph = 100 steps of every chain (one persistent launch per "
-           "launch class)", "metric": UNIT, "value": cand / T, "mc_steps_per_s": cs / T,
+           "[0.5, 3], MCMCMC; one CUDA graph = 100 steps of every chain (launches: see layout and "
+           "classes)", "metric": UNIT, "value": cand / T, "mc_steps_per_s": cs / T,
            "ms_per_step": 1e3 * T / args.steps, "steps": args.steps, "warmup": args.warmup,
            "layout": (f"one persistent launch for every run: 32 lanes per chain, rows through L1, "
                       f"{args.uneven_fused} warps per CTA" if args.uneven_fused else
@@ -1115,6 +1143,11 @@ def main():
     ap.add_argument("--uneven-warps", type=int, default=0,
                     help="--config uneven: one CTA shape for every class (this many warps, 32 lanes per "
                          "chain) instead of the autotuned per-class layouts")
+    ap.add_argument("--uneven-instances", type=int, default=256,
+                    help="--config uneven: instances (256 = BASELINE config 4; fewer for profiler captures)")
+    ap.add_argument("--cluster-one-chain", type=int, default=0,
+                    help="one Gaussian N=512 chain, K=32, on clusters of this many CTAs: 2000 steps in one "
+                         "launch after a warm-up launch (the cluster kernel's profiler case)")
     ap.add_argument("--uneven-fused", type=int, default=0,
                     help="--config uneven: every run in one persistent launch of this many warps per CTA")
     ap.add_argument("--ttt-n", type=int, default=TTT_N,
@@ -1156,6 +1189,8 @@ def main():
         return run_graph_one_chain(args)
     if args.config == "uneven":
         return run_uneven(args)
+    if args.cluster_one_chain:
+        return run_cluster_one_chain(args)
     if args.serve:
         return run_serve(args)
     return run_ours(args)
