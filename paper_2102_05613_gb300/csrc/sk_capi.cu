@@ -94,6 +94,9 @@ std::vector<uint64_t> metropolis_table(double beta_eff, uint32_t N) {
     std::vector<uint64_t> m(N + 1);
     for (uint32_t k = 0; k <= N; ++k)
         m[k] = static_cast<uint64_t>(std::nearbyint(std::ldexp(std::exp(-2.0 * beta_eff * k), 53)));
+    // entries that round to 0 are dropped from the end: lookups past the
+    // table's end read 0, and a short table fits the kernels' shared copy
+    while (m.size() > 1 && m.back() == 0) m.pop_back();
     return m;
 }
 

@@ -22,7 +22,7 @@ struct alignas(16) JobDev {
     const void* J;
     int8_t* s;
     void* h;
-    const uint64_t* W;      // +-J tables: MCMCMC W[d] (wlen) or Metropolis M[k] (N+1)
+    const uint64_t* W;      // +-J tables: MCMCMC W[d] or Metropolis M[k], wlen entries (0 past the end)
     uint64_t* step;         // device step counter of the run
     uint32_t* acc_run;      // per chain: accepted steps since the last record
     double* rec_E;          // [rec][chains]

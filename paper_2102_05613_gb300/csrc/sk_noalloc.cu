@@ -162,7 +162,7 @@ extern "C" sk_status mcmcmc_run_noalloc(uint32_t N, uint32_t kind, const void* c
             const double x = rule == SK_RULE_MCMCMC ? std::ldexp(std::exp(-2.0 * be * d), 52)
                                                     : std::ldexp(std::exp(-2.0 * be * d), 53);
             const double v = std::nearbyint(x);
-            if (rule == SK_RULE_MCMCMC && !(v > 0.0)) {
+            if (!(v > 0.0)) {  // the table ends where its entries round to 0
                 done = true;
                 break;
             }

@@ -128,10 +128,20 @@ struct ChainMem {
 // d ~ 18/beta), and the lookups then cost a shared-memory load instead of a
 // trip to L2; longer tables read the rest from global memory.
 constexpr uint32_t kWCache = 64;
+// SMALL: the whole table is in wsm (wlen <= kWCache, zeros past its end), and
+// the lookup is compiled without the global-memory fallback, which every
+// lookup would otherwise carry (~50 ns per step of a lone chain).
+template <bool SMALL = false>
 __device__ __forceinline__ unsigned long long wt_lookup(const unsigned long long* wsm,
                                                         const unsigned long long* Wt, uint32_t wlen,
                                                         uint32_t idx) {
-    return idx < kWCache ? wsm[idx] : (idx < wlen ? __ldg(&Wt[idx]) : 0ull);
+    if constexpr (SMALL) {
+        (void)Wt;
+        (void)wlen;
+        return idx < kWCache ? wsm[idx] : 0ull;
+    } else {
+        return idx < kWCache ? wsm[idx] : (idx < wlen ? __ldg(&Wt[idx]) : 0ull);
+    }
 }
 
 // Block 0 (U0, U1) of the G steps base .. base+G-1, computed one step per
@@ -479,7 +489,7 @@ __device__ __noinline__ void record(const JobDev& jb, bool write, uint32_t chain
 // nothing, so that every lane reaches the same barriers).  `dead` is set
 // after a timed-out wait: the group then stops working but still meets the
 // CTA's record barriers.
-template <typename JT, int RULE, int NB, int G, int STAGE, int UNROLL, bool RCH>
+template <typename JT, int RULE, int NB, int G, int STAGE, int UNROLL, bool RCH, bool WS = false>
 __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_t chain, const ChainMem& cm,
                                            int partner_off, uint32_t t0, uint32_t t1, uint32_t& acc,
                                            uint32_t& phase, bool& dead, uint32_t& n_flips, uint32_t& n_rows) {
@@ -616,7 +626,7 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                 bool accept;
                 if constexpr (sizeof(JT) == 1) {
                     const uint32_t k = static_cast<uint32_t>(dE) >> 1;
-                    accept = dE <= 0 || (U1 >> 11) < wt_lookup(cm.wsm, Wt, wlen, k);
+                    accept = dE <= 0 || (U1 >> 11) < wt_lookup<WS>(cm.wsm, Wt, wlen, k);
                 } else {
                     accept = dE <= 0.0f || static_cast<float>(U1 >> 40) * 0x1p-24f < dev::pow2(nbl2 * dE);
                 }
@@ -664,7 +674,7 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                     if (d <= K) {
                         if constexpr (sizeof(JT) == 1) {
                             const uint32_t idx = static_cast<uint32_t>(dE[q] - m) >> 1;
-                            x = wt_lookup(cm.wsm, Wt, wlen, idx);
+                            x = wt_lookup<WS>(cm.wsm, Wt, wlen, idx);
                             if (root_weighted)  // floor(x F / 2^20)
                                 x = __umul64hi(x << 11, static_cast<unsigned long long>(centre ? jb.fcen : jb.fleaf) << 33);
                         } else {
@@ -686,7 +696,7 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                 W w0;  // slot 0, the root: the centre of a centre root, else a leaf
                 if constexpr (sizeof(JT) == 1) {
                     const uint32_t idx0 = static_cast<uint32_t>(-m) >> 1;
-                    w0 = wt_lookup(cm.wsm, Wt, wlen, idx0);
+                    w0 = wt_lookup<WS>(cm.wsm, Wt, wlen, idx0);
                     if (root_weighted)
                         w0 = __umul64hi(w0 << 11, static_cast<unsigned long long>(leaf ? jb.fleaf : jb.fcen) << 33);
                 } else {
@@ -866,8 +876,14 @@ __device__ __forceinline__ void run_item(const WorkItem& wi, const JobDev& jb, u
     __syncwarp();
     if (t1 > t0) {
         if (warp_busy) {
-            chain_loop<JT, RULE, NB, G, STAGE, UNROLL, RCH>(jb, own, chain, cm, partner_off, t0, t1, acc, phase,
-                                                            dead, n_flips, n_rows);
+            // +-J weight tables that fit the shared-memory copy take the loop
+            // compiled without the lookups' global fallback
+            if (sizeof(JT) == 1 && jb.wlen <= kWCache)
+                chain_loop<JT, RULE, NB, G, STAGE, UNROLL, RCH, sizeof(JT) == 1>(jb, own, chain, cm, partner_off, t0,
+                                                                                t1, acc, phase, dead, n_flips, n_rows);
+            else
+                chain_loop<JT, RULE, NB, G, STAGE, UNROLL, RCH>(jb, own, chain, cm, partner_off, t0, t1, acc, phase,
+                                                                dead, n_flips, n_rows);
         } else {
             // no chain in this warp: meet the CTA's record barriers only
             const uint32_t R = jb.record_every;
