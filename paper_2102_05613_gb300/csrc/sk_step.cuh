@@ -129,8 +129,7 @@ struct ChainMem {
 // trip to L2; longer tables read the rest from global memory.
 constexpr uint32_t kWCache = 64;
 // SMALL: the whole table is in wsm (wlen <= kWCache, zeros past its end), and
-// the lookup is compiled without the global-memory fallback, which every
-// lookup would otherwise carry (~50 ns per step of a lone chain).
+// the lookup is compiled without the global-memory fallback.
 template <bool SMALL = false>
 __device__ __forceinline__ unsigned long long wt_lookup(const unsigned long long* wsm,
                                                         const unsigned long long* Wt, uint32_t wlen,
@@ -489,7 +488,11 @@ __device__ __noinline__ void record(const JobDev& jb, bool write, uint32_t chain
 // nothing, so that every lane reaches the same barriers).  `dead` is set
 // after a timed-out wait: the group then stops working but still meets the
 // CTA's record barriers.
-template <typename JT, int RULE, int NB, int G, int STAGE, int UNROLL, bool RCH, bool WS = false>
+// FAST (+-J work items only): every chain of the item has the uniform root,
+// no traced steps and a weight table held whole in shared memory, and the loop
+// is compiled without the code for the other cases (about 10 % of a lone
+// chain's step).
+template <typename JT, int RULE, int NB, int G, int STAGE, int UNROLL, bool RCH, bool FAST = false>
 __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_t chain, const ChainMem& cm,
                                            int partner_off, uint32_t t0, uint32_t t1, uint32_t& acc,
                                            uint32_t& phase, bool& dead, uint32_t& n_flips, uint32_t& n_rows) {
@@ -522,9 +525,9 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
     const W* __restrict__ Wt = reinterpret_cast<const W*>(jb.W);
     const uint32_t wlen = jb.wlen;
     const float nbl2 = -jb.beta_eff * 1.4426950408889634f;  // -beta log2(e)
-    const bool root_weighted = jb.fcen + jb.fleaf != (2u << 20);  // not both factors 1
+    const bool root_weighted = !FAST && jb.fcen + jb.fleaf != (2u << 20);  // not both factors 1
     // steps this chain logs its choice for (0: not traced)
-    const uint32_t trace_end = (write && chain < jb.trace_chains)
+    const uint32_t trace_end = (!FAST && write && chain < jb.trace_chains)
                                    ? static_cast<uint32_t>(min(jb.trace_steps, static_cast<uint64_t>(0xFFFFFFFFu)))
                                    : 0u;
     int8_t* S = cm.s;
@@ -626,7 +629,7 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                 bool accept;
                 if constexpr (sizeof(JT) == 1) {
                     const uint32_t k = static_cast<uint32_t>(dE) >> 1;
-                    accept = dE <= 0 || (U1 >> 11) < wt_lookup<WS>(cm.wsm, Wt, wlen, k);
+                    accept = dE <= 0 || (U1 >> 11) < wt_lookup<FAST>(cm.wsm, Wt, wlen, k);
                 } else {
                     accept = dE <= 0.0f || static_cast<float>(U1 >> 40) * 0x1p-24f < dev::pow2(nbl2 * dE);
                 }
@@ -674,7 +677,7 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                     if (d <= K) {
                         if constexpr (sizeof(JT) == 1) {
                             const uint32_t idx = static_cast<uint32_t>(dE[q] - m) >> 1;
-                            x = wt_lookup<WS>(cm.wsm, Wt, wlen, idx);
+                            x = wt_lookup<FAST>(cm.wsm, Wt, wlen, idx);
                             if (root_weighted)  // floor(x F / 2^20)
                                 x = __umul64hi(x << 11, static_cast<unsigned long long>(centre ? jb.fcen : jb.fleaf) << 33);
                         } else {
@@ -696,7 +699,7 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                 W w0;  // slot 0, the root: the centre of a centre root, else a leaf
                 if constexpr (sizeof(JT) == 1) {
                     const uint32_t idx0 = static_cast<uint32_t>(-m) >> 1;
-                    w0 = wt_lookup<WS>(cm.wsm, Wt, wlen, idx0);
+                    w0 = wt_lookup<FAST>(cm.wsm, Wt, wlen, idx0);
                     if (root_weighted)
                         w0 = __umul64hi(w0 << 11, static_cast<unsigned long long>(leaf ? jb.fleaf : jb.fcen) << 33);
                 } else {
@@ -876,9 +879,13 @@ __device__ __forceinline__ void run_item(const WorkItem& wi, const JobDev& jb, u
     __syncwarp();
     if (t1 > t0) {
         if (warp_busy) {
-            // +-J weight tables that fit the shared-memory copy take the loop
-            // compiled without the lookups' global fallback
-            if (sizeof(JT) == 1 && jb.wlen <= kWCache)
+            // +-J items whose chains all have the uniform root, no traced
+            // steps and a weight table that fits the shared copy take the loop
+            // compiled for that case (a choice for the whole CTA: its groups
+            // meet the same record barriers)
+            const bool fast = sizeof(JT) == 1 && jb.wlen <= kWCache && jb.fcen + jb.fleaf == (2u << 20) &&
+                              jb.trace_chains <= wi.chain0;
+            if (fast)
                 chain_loop<JT, RULE, NB, G, STAGE, UNROLL, RCH, sizeof(JT) == 1>(jb, own, chain, cm, partner_off, t0,
                                                                                 t1, acc, phase, dead, n_flips, n_rows);
             else
