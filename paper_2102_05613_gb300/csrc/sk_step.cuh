@@ -107,6 +107,22 @@ __device__ __forceinline__ T gscan(const Grp<G>& g, T v) {  // inclusive, in lan
     }
     return v;
 }
+// The same scan over the group's first L lanes (L a power of two <= G): the
+// levels whose offset reaches past them are left out.  Those lanes get the
+// prefixes of the full scan bit for bit (a lane below L adds nothing at a
+// left-out level); the lanes past them hold partial sums and must be ignored.
+// Where the other lanes hold 0 and the values are integers, lane L-1 holds the
+// group total exactly.
+template <int L, int G, typename T>
+__device__ __forceinline__ T gscan_first(const Grp<G>& g, T v) {
+    static_assert(L <= G && (L & (L - 1)) == 0, "L: a power of two <= G");
+#pragma unroll
+    for (int o = 1; o < L; o <<= 1) {
+        const T y = __shfl_up_sync(g.mask, v, o, G);
+        if (g.gl >= o) v += y;
+    }
+    return v;
+}
 template <int G>
 __device__ __forceinline__ unsigned gballot(const Grp<G>& g, bool p) {
     const unsigned b = __ballot_sync(g.mask, p);
@@ -166,6 +182,32 @@ __device__ __forceinline__ void draw_sites(uint32_t (&sp)[2 * NB], uint32_t t, u
         sp[2 * q + 0] = __umulhi(r.x, N) | (__umulhi(r.y, N) << 16);
         sp[2 * q + 1] = __umulhi(r.z, N) | (__umulhi(r.w, N) << 16);
     }
+}
+// Small-K chains (K <= 8: every slot sits in group lanes 0 and 1) draw the
+// sites of G / 2 steps at once, one Philox block per lane: lane l computes
+// what lane l % 2 of draw_sites computes for step tb + l / 2, and at each
+// step a shuffle hands each lane the words of lane 2 j + gl % 2 (j = t - tb).
+// Lanes past 1 so get copies of real sites where draw_sites gives them zeros;
+// their slots are past K, where the sites only serve as (in-range) indices
+// of loads whose values are not used.
+constexpr int kSmallKLanes = 2;
+constexpr uint32_t kSmallKMax = 4u * kSmallKLanes;
+template <int G>
+__device__ __forceinline__ void draw_site_batch(uint32_t (&bat)[2], uint32_t tb, uint32_t chain, uint32_t c3,
+                                                uint32_t k0, uint32_t k1, uint32_t nblk, uint32_t N,
+                                                const Grp<G>& g) {
+    const uint32_t b = 1u + static_cast<uint32_t>(g.gl % kSmallKLanes);
+    uint4 r = make_uint4(0u, 0u, 0u, 0u);
+    if (b <= nblk)
+        r = dev::philox4x32_10(make_uint4(b, tb + static_cast<uint32_t>(g.gl / kSmallKLanes), chain, c3), k0, k1);
+    bat[0] = __umulhi(r.x, N) | (__umulhi(r.y, N) << 16);
+    bat[1] = __umulhi(r.z, N) | (__umulhi(r.w, N) << 16);
+}
+template <int G>
+__device__ __forceinline__ void take_sites(uint32_t (&sp)[2], const uint32_t (&bat)[2], uint32_t j, const Grp<G>& g) {
+    const int src = static_cast<int>(j) * kSmallKLanes + (g.gl & (kSmallKLanes - 1));
+    sp[0] = __shfl_sync(g.mask, bat[0], src, G);
+    sp[1] = __shfl_sync(g.mask, bat[1], src, G);
 }
 template <int NB>
 __device__ __forceinline__ uint32_t site_of(const uint32_t (&sp)[2 * NB], int k) {
@@ -491,8 +533,12 @@ __device__ __noinline__ void record(const JobDev& jb, bool write, uint32_t chain
 // FAST (+-J work items only): every chain of the item has the uniform root,
 // no traced steps and a weight table held whole in shared memory, and the loop
 // is compiled without the code for the other cases (about 10 % of a lone
-// chain's step).
-template <typename JT, int RULE, int NB, int G, int STAGE, int UNROLL, bool RCH, bool FAST = false>
+// chain's step).  SMALLK (FAST items with K <= 8 in the few-chain variant,
+// rows through L1): the slot-weight scan covers group lanes 0 and 1 only (the
+// integer total is the same in any order) and the sites come in batches of
+// G / 2 steps (draw_site_batch).
+template <typename JT, int RULE, int NB, int G, int STAGE, int UNROLL, bool RCH, bool FAST = false,
+          bool SMALLK = false>
 __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_t chain, const ChainMem& cm,
                                            int partner_off, uint32_t t0, uint32_t t1, uint32_t& acc,
                                            uint32_t& phase, bool& dead, uint32_t& n_flips, uint32_t& n_rows) {
@@ -509,6 +555,9 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
     // that the copy of the next step's row goes out at the start of a step
     // with no Philox rounds in front of it
     constexpr bool AHEAD2 = STAGED && KEEPW && RULE == 0;
+    static_assert(!SMALLK || (FAST && RULE == 0 && NB == 1 && !STAGED && KEEPW && G >= 2 * kSmallKLanes),
+                  "SMALLK: +-J MCMCMC in the few-chain variant, rows through L1");
+    constexpr uint32_t SPB = G / kSmallKLanes;  // SMALLK: steps per site batch
     const Grp<G> g;
     // next record point (0: none; a record follows step t when t + 1 == next_rec)
     uint32_t next_rec = jb.record_every ? (t0 / jb.record_every + 1u) * jb.record_every : 0u;
@@ -537,7 +586,16 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
     uint32_t site[2 * NB];  // packed sites of this step (site_of)
     uint32_t site1[AHEAD2 ? 2 * NB : 1];  // AHEAD2: the sites of the next step
 
-    if constexpr (!STAGED && AHEAD && RULE == 0) draw_sites<NB, G>(site, t0, chain, c3, k0, k1, nblk, N, g);
+    uint32_t bat[2];      // SMALLK: this lane's words of the site batch of steps tb .. tb+SPB-1
+    uint32_t tb = t0;
+    if constexpr (SMALLK) {
+        draw_site_batch<G>(bat, tb, chain, c3, k0, k1, nblk, N, g);
+        take_sites<G>(site, bat, 0u, g);
+    } else if constexpr (!STAGED && AHEAD && RULE == 0) {
+        draw_sites<NB, G>(site, t0, chain, c3, k0, k1, nblk, N, g);
+    }
+    (void)SPB;
+    (void)tb;
     // prologue (staged rows): draw the first step and stage its row
     if constexpr (STAGED) {
         uint32_t first;
@@ -643,7 +701,17 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
             } else {
                 // ---- MCMCMC: K proposals on the uniform-root star ----
                 // (few-chain variant: the next step's sites, interleaved with this step's work)
-                if constexpr (!STAGED && AHEAD) draw_sites<NB, G>(nsite, t + 1u, chain, c3, k0, k1, nblk, N, g);
+                if constexpr (SMALLK) {
+                    uint32_t j = t + 1u - tb;
+                    if (j == SPB) {
+                        tb += SPB;
+                        j = 0;
+                        draw_site_batch<G>(bat, tb, chain, c3, k0, k1, nblk, N, g);
+                    }
+                    take_sites<G>(nsite, bat, j, g);
+                } else if constexpr (!STAGED && AHEAD) {
+                    draw_sites<NB, G>(nsite, t + 1u, chain, c3, k0, k1, nblk, N, g);
+                }
                 if constexpr (AHEAD2) draw_sites<NB, G>(nsite, t + 2u, chain, c3, k0, k1, nblk, N, g);
                 const unsigned long long U0 = (static_cast<unsigned long long>(b0.y) << 32) | b0.x;
                 const bool leaf = U0 >= dev::at_use(jb.root_thr);
@@ -709,8 +777,13 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                 W total = w0;
 #pragma unroll
                 for (int q = 0; q < NB; ++q) {
-                    incl[q] = gscan(g, gsum_[q]);
-                    tot[q] = gshfl(g, incl[q], G - 1);
+                    if constexpr (SMALLK) {  // slots in lanes 0 and 1 only
+                        incl[q] = gscan_first<kSmallKLanes>(g, gsum_[q]);
+                        tot[q] = gshfl(g, incl[q], kSmallKLanes - 1);
+                    } else {
+                        incl[q] = gscan(g, gsum_[q]);
+                        tot[q] = gshfl(g, incl[q], G - 1);
+                    }
                     total += tot[q];
                 }
                 W u;
@@ -729,7 +802,8 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                 W base = w0;
 #pragma unroll
                 for (int q = 0; q < NB; ++q) {
-                    const unsigned ball = gballot(g, !found && base + incl[q] > u);
+                    const unsigned ball =
+                        gballot(g, !found && base + incl[q] > u && (!SMALLK || g.gl < kSmallKLanes));
                     if (!found && ball) {
                         const int L = __ffs(ball) - 1;
                         // this lane's 4 weights (kept, or recomputed bit-identically),
@@ -885,7 +959,12 @@ __device__ __forceinline__ void run_item(const WorkItem& wi, const JobDev& jb, u
             // meet the same record barriers)
             const bool fast = sizeof(JT) == 1 && jb.wlen <= kWCache && jb.fcen + jb.fleaf == (2u << 20) &&
                               jb.trace_chains <= wi.chain0;
-            if (fast)
+            constexpr bool kSmall = sizeof(JT) == 1 && RULE == 0 && NB == 1 && STAGE != 1 && UNROLL >= 8 &&
+                                    G >= 2 * kSmallKLanes;
+            if (kSmall && fast && jb.K <= kSmallKMax)
+                chain_loop<JT, RULE, NB, G, STAGE, UNROLL, RCH, sizeof(JT) == 1, kSmall>(
+                    jb, own, chain, cm, partner_off, t0, t1, acc, phase, dead, n_flips, n_rows);
+            else if (fast)
                 chain_loop<JT, RULE, NB, G, STAGE, UNROLL, RCH, sizeof(JT) == 1>(jb, own, chain, cm, partner_off, t0,
                                                                                 t1, acc, phase, dead, n_flips, n_rows);
             else

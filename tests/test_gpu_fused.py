@@ -182,6 +182,41 @@ def test_fused_items_with_idle_warps_at_record_points():
     b.close(); run.close(); small.close(); inst.close()
 
 
+def test_fused_untraced_runs_bit_exact():
+    # untraced uniform-root +-J runs (the loop compiled for that case; K <= 8
+    # with two-lane scans and batched site draws) beside Gaussian ones in one
+    # fused launch: +-J bit-exact against the oracle
+    torch = need_gpu()
+    st = torch.cuda.Stream()
+    steps, R = 500, 100
+    specs = [(sk.SK_J_PM1, 64, 8, 1), (sk.SK_J_PM1, 150, 3, 4), (sk.SK_J_PM1, 333, 1, 3),
+             (sk.SK_J_PM1, 100, 24, 2), (sk.SK_J_GAUSS, 128, 8, 2)]
+    made = []
+    for i, (kind, N, K, chains) in enumerate(specs):
+        J = inputs.couplings(N, kind, 900 + i)
+        init = inputs.initial_spins(chains, N, 950 + i)
+        inst = sk.Instance(J, stream=st)
+        run = sk.Run(inst, chains=chains, K=K, beta=1.1, seed=8, stream_id=i, record_every=R,
+                     max_records=steps // R, init=init)
+        made.append((J, init, inst, run))
+    b = sk.Batch([m[3] for m in made])
+    b.set_fused(8)
+    b.advance(123)
+    b.advance(steps - 123)
+    for i, ((kind, N, K, chains), (J, init, _, run)) in enumerate(zip(specs, made)):
+        if kind != sk.SK_J_PM1:
+            continue
+        o = oracle.run(J, K=K, beta=1.1, seed=8, stream=i, chains=chains, init=init, steps=steps, record_every=R)
+        E, q, acc = run.observables()
+        spins, h, _ = run.state(fields=True)
+        assert np.array_equal(E, o["E"]) and np.array_equal(acc, o["acc"]), i
+        if chains > 1:
+            assert np.array_equal(q, o["q"]), i
+        assert np.array_equal(spins, o["spins"]), i
+        assert np.array_equal(h, (J.astype(np.int64) @ spins.T.astype(np.int64)).T), i
+    _close(b, made)
+
+
 def test_autotuner_compares_fused_and_per_class_launches():
     # the autotuner may keep the fused launch or the per-class ones; either
     # way the runs' results equal a plain advance's (+-J: bit-exact)

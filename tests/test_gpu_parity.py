@@ -521,6 +521,38 @@ def test_few_warps_variant_bit_exact(rule, K, lanes):
     b.close(); run.close(); inst.close()
 
 
+@pytest.mark.parametrize("K,lanes,chains", [(8, 32, 1), (8, 32, 7), (5, 16, 5), (4, 8, 6), (1, 4, 9),
+                                            (3, 32, 2), (9, 32, 3), (40, 8, 5)])
+def test_untraced_uniform_root_loop_bit_exact(K, lanes, chains):
+    """+-J items whose chains have the uniform root, no traced steps and a
+    weight table short enough for shared memory run the step loop compiled
+    for that case; for K <= 8 in the 128-register variant it scans the slot
+    weights of two lanes only and draws the sites of lanes/2 steps at once.
+    Energies, acceptances, overlaps, spins and fields follow the oracle bit
+    for bit over advances of ragged lengths (site batches cut at any step)."""
+    torch = need_gpu()
+    st = torch.cuda.Stream()
+    N, steps, R = 200, 333, 111
+    J = inputs.couplings_pm1(N, 700 + K)
+    init = inputs.initial_spins(chains, N, 701 + K)
+    inst = sk.Instance(J, stream=st)
+    run = sk.Run(inst, chains=chains, K=K, beta=0.9, seed=23, record_every=R, max_records=steps // R, init=init)
+    b = sk.Batch([run], warps_per_cta=8)
+    b.set_layout(lanes, 2)
+    for n in (37, 100, steps - 137):
+        b.advance(n)
+    E, q, acc = run.observables()
+    spins, h, step = run.state(fields=True)
+    o = oracle.run(J, K=K, beta=0.9, seed=23, chains=chains, init=init, steps=steps, record_every=R)
+    assert step == steps
+    assert np.array_equal(E, o["E"]) and np.array_equal(acc, o["acc"])
+    if chains > 1:
+        assert np.array_equal(q, o["q"])
+    assert np.array_equal(spins, o["spins"])
+    assert np.array_equal(h, (J.astype(np.int64) @ spins.T.astype(np.int64)).T)
+    b.close(); run.close(); inst.close()
+
+
 def test_few_warps_variant_gaussian_replay():
     # the same variant on Gaussian couplings: every chain's recorded
     # trajectory is one the oracle's node rule takes from the same draws
