@@ -183,29 +183,26 @@ __device__ __forceinline__ void draw_sites(uint32_t (&sp)[2 * NB], uint32_t t, u
         sp[2 * q + 1] = __umulhi(r.z, N) | (__umulhi(r.w, N) << 16);
     }
 }
-// Small-K chains (K <= 8: every slot sits in group lanes 0 and 1) draw the
-// sites of G / 2 steps at once, one Philox block per lane: lane l computes
-// what lane l % 2 of draw_sites computes for step tb + l / 2, and at each
-// step a shuffle hands each lane the words of lane 2 j + gl % 2 (j = t - tb).
-// Lanes past 1 so get copies of real sites where draw_sites gives them zeros;
-// their slots are past K, where the sites only serve as (in-range) indices
-// of loads whose values are not used.
-constexpr int kSmallKLanes = 2;
-constexpr uint32_t kSmallKMax = 4u * kSmallKLanes;
-template <int G>
+// Small-K chains (every slot in group lanes 0 .. SL-1, i.e. K <= 4 SL) draw
+// the sites of G / SL steps at once, one Philox block per lane: lane l
+// computes what lane l % SL of draw_sites computes for step tb + l / SL, and
+// at each step a shuffle hands each lane the words of lane SL j + gl % SL
+// (j = t - tb).  Lanes past SL-1 so get copies of real sites where
+// draw_sites gives them zeros; their slots are past K, where the sites only
+// serve as (in-range) indices of loads whose values are not used.
+template <int SL, int G>
 __device__ __forceinline__ void draw_site_batch(uint32_t (&bat)[2], uint32_t tb, uint32_t chain, uint32_t c3,
                                                 uint32_t k0, uint32_t k1, uint32_t nblk, uint32_t N,
                                                 const Grp<G>& g) {
-    const uint32_t b = 1u + static_cast<uint32_t>(g.gl % kSmallKLanes);
+    const uint32_t b = 1u + static_cast<uint32_t>(g.gl % SL);
     uint4 r = make_uint4(0u, 0u, 0u, 0u);
-    if (b <= nblk)
-        r = dev::philox4x32_10(make_uint4(b, tb + static_cast<uint32_t>(g.gl / kSmallKLanes), chain, c3), k0, k1);
+    if (b <= nblk) r = dev::philox4x32_10(make_uint4(b, tb + static_cast<uint32_t>(g.gl / SL), chain, c3), k0, k1);
     bat[0] = __umulhi(r.x, N) | (__umulhi(r.y, N) << 16);
     bat[1] = __umulhi(r.z, N) | (__umulhi(r.w, N) << 16);
 }
-template <int G>
+template <int SL, int G>
 __device__ __forceinline__ void take_sites(uint32_t (&sp)[2], const uint32_t (&bat)[2], uint32_t j, const Grp<G>& g) {
-    const int src = static_cast<int>(j) * kSmallKLanes + (g.gl & (kSmallKLanes - 1));
+    const int src = static_cast<int>(j) * SL + (g.gl & (SL - 1));
     sp[0] = __shfl_sync(g.mask, bat[0], src, G);
     sp[1] = __shfl_sync(g.mask, bat[1], src, G);
 }
@@ -533,12 +530,11 @@ __device__ __noinline__ void record(const JobDev& jb, bool write, uint32_t chain
 // FAST (+-J work items only): every chain of the item has the uniform root,
 // no traced steps and a weight table held whole in shared memory, and the loop
 // is compiled without the code for the other cases (about 10 % of a lone
-// chain's step).  SMALLK (FAST items with K <= 8 in the few-chain variant,
-// rows through L1): the slot-weight scan covers group lanes 0 and 1 only (the
-// integer total is the same in any order) and the sites come in batches of
-// G / 2 steps (draw_site_batch).
-template <typename JT, int RULE, int NB, int G, int STAGE, int UNROLL, bool RCH, bool FAST = false,
-          bool SMALLK = false>
+// chain's step).  SL > 0 (MCMCMC with K <= 4 SL in the few-chain variant,
+// rows through L1): the sites come in batches of G / SL steps
+// (draw_site_batch), and for +-J the slot-weight scan covers group lanes
+// 0 .. SL-1 only (the integer total is the same in any order).
+template <typename JT, int RULE, int NB, int G, int STAGE, int UNROLL, bool RCH, bool FAST = false, int SL = 0>
 __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_t chain, const ChainMem& cm,
                                            int partner_off, uint32_t t0, uint32_t t1, uint32_t& acc,
                                            uint32_t& phase, bool& dead, uint32_t& n_flips, uint32_t& n_rows) {
@@ -555,9 +551,11 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
     // that the copy of the next step's row goes out at the start of a step
     // with no Philox rounds in front of it
     constexpr bool AHEAD2 = STAGED && KEEPW && RULE == 0;
-    static_assert(!SMALLK || (FAST && RULE == 0 && NB == 1 && !STAGED && KEEPW && G >= 2 * kSmallKLanes),
-                  "SMALLK: +-J MCMCMC in the few-chain variant, rows through L1");
-    constexpr uint32_t SPB = G / kSmallKLanes;  // SMALLK: steps per site batch
+    constexpr bool BATCH = SL > 0;                     // sites in batches of SPB steps
+    constexpr bool SCANSL = BATCH && sizeof(JT) == 1;  // +-J: the scan over SL lanes
+    static_assert(!BATCH || (RULE == 0 && NB == 1 && !STAGED && KEEPW && (SL & (SL - 1)) == 0 && G >= 2 * SL),
+                  "site batches: MCMCMC in the few-chain variant, rows through L1");
+    constexpr uint32_t SPB = BATCH ? G / SL : 1;
     const Grp<G> g;
     // next record point (0: none; a record follows step t when t + 1 == next_rec)
     uint32_t next_rec = jb.record_every ? (t0 / jb.record_every + 1u) * jb.record_every : 0u;
@@ -586,11 +584,11 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
     uint32_t site[2 * NB];  // packed sites of this step (site_of)
     uint32_t site1[AHEAD2 ? 2 * NB : 1];  // AHEAD2: the sites of the next step
 
-    uint32_t bat[2];      // SMALLK: this lane's words of the site batch of steps tb .. tb+SPB-1
+    uint32_t bat[2];      // BATCH: this lane's words of the site batch of steps tb .. tb+SPB-1
     uint32_t tb = t0;
-    if constexpr (SMALLK) {
-        draw_site_batch<G>(bat, tb, chain, c3, k0, k1, nblk, N, g);
-        take_sites<G>(site, bat, 0u, g);
+    if constexpr (BATCH) {
+        draw_site_batch<SL, G>(bat, tb, chain, c3, k0, k1, nblk, N, g);
+        take_sites<SL, G>(site, bat, 0u, g);
     } else if constexpr (!STAGED && AHEAD && RULE == 0) {
         draw_sites<NB, G>(site, t0, chain, c3, k0, k1, nblk, N, g);
     }
@@ -701,14 +699,14 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
             } else {
                 // ---- MCMCMC: K proposals on the uniform-root star ----
                 // (few-chain variant: the next step's sites, interleaved with this step's work)
-                if constexpr (SMALLK) {
+                if constexpr (BATCH) {
                     uint32_t j = t + 1u - tb;
                     if (j == SPB) {
                         tb += SPB;
                         j = 0;
-                        draw_site_batch<G>(bat, tb, chain, c3, k0, k1, nblk, N, g);
+                        draw_site_batch<SL, G>(bat, tb, chain, c3, k0, k1, nblk, N, g);
                     }
-                    take_sites<G>(nsite, bat, j, g);
+                    take_sites<SL, G>(nsite, bat, j, g);
                 } else if constexpr (!STAGED && AHEAD) {
                     draw_sites<NB, G>(nsite, t + 1u, chain, c3, k0, k1, nblk, N, g);
                 }
@@ -777,9 +775,9 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                 W total = w0;
 #pragma unroll
                 for (int q = 0; q < NB; ++q) {
-                    if constexpr (SMALLK) {  // slots in lanes 0 and 1 only
-                        incl[q] = gscan_first<kSmallKLanes>(g, gsum_[q]);
-                        tot[q] = gshfl(g, incl[q], kSmallKLanes - 1);
+                    if constexpr (SCANSL) {  // slots in lanes 0 .. SL-1 only
+                        incl[q] = gscan_first<(SCANSL ? SL : 1)>(g, gsum_[q]);
+                        tot[q] = gshfl(g, incl[q], SL - 1);
                     } else {
                         incl[q] = gscan(g, gsum_[q]);
                         tot[q] = gshfl(g, incl[q], G - 1);
@@ -803,7 +801,7 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
 #pragma unroll
                 for (int q = 0; q < NB; ++q) {
                     const unsigned ball =
-                        gballot(g, !found && base + incl[q] > u && (!SMALLK || g.gl < kSmallKLanes));
+                        gballot(g, !found && base + incl[q] > u && (!SCANSL || g.gl < SL));
                     if (!found && ball) {
                         const int L = __ffs(ball) - 1;
                         // this lane's 4 weights (kept, or recomputed bit-identically),
@@ -955,21 +953,33 @@ __device__ __forceinline__ void run_item(const WorkItem& wi, const JobDev& jb, u
         if (warp_busy) {
             // +-J items whose chains all have the uniform root, no traced
             // steps and a weight table that fits the shared copy take the loop
-            // compiled for that case (a choice for the whole CTA: its groups
-            // meet the same record barriers)
+            // compiled for that case; MCMCMC items with K <= 8 or K <= 32 in
+            // the few-chain variant (rows through L1) take their sites in
+            // batches of G/2 or G/8 steps (a choice for the whole CTA: its
+            // groups meet the same record barriers)
             const bool fast = sizeof(JT) == 1 && jb.wlen <= kWCache && jb.fcen + jb.fleaf == (2u << 20) &&
                               jb.trace_chains <= wi.chain0;
-            constexpr bool kSmall = sizeof(JT) == 1 && RULE == 0 && NB == 1 && STAGE != 1 && UNROLL >= 8 &&
-                                    G >= 2 * kSmallKLanes;
-            if (kSmall && fast && jb.K <= kSmallKMax)
-                chain_loop<JT, RULE, NB, G, STAGE, UNROLL, RCH, sizeof(JT) == 1, kSmall>(
+            constexpr bool kBatch = RULE == 0 && NB == 1 && STAGE != 1 && UNROLL >= 8;
+            constexpr int kSL2 = kBatch && G >= 4 ? 2 : 0;
+            constexpr int kSL8 = kBatch && G >= 16 ? 8 : 0;
+            auto loop = [&](auto fast_c, auto sl_c) {
+                chain_loop<JT, RULE, NB, G, STAGE, UNROLL, RCH, decltype(fast_c)::value, decltype(sl_c)::value>(
                     jb, own, chain, cm, partner_off, t0, t1, acc, phase, dead, n_flips, n_rows);
-            else if (fast)
-                chain_loop<JT, RULE, NB, G, STAGE, UNROLL, RCH, sizeof(JT) == 1>(jb, own, chain, cm, partner_off, t0,
-                                                                                t1, acc, phase, dead, n_flips, n_rows);
-            else
-                chain_loop<JT, RULE, NB, G, STAGE, UNROLL, RCH>(jb, own, chain, cm, partner_off, t0, t1, acc, phase,
-                                                                dead, n_flips, n_rows);
+            };
+            using Fast = std::integral_constant<bool, sizeof(JT) == 1>;
+            using Slow = std::integral_constant<bool, false>;
+            const uint32_t K = jb.K;
+            if (kSL2 && K <= 4u * kSL2) {
+                if (fast) loop(Fast{}, std::integral_constant<int, kSL2>{});
+                else loop(Slow{}, std::integral_constant<int, kSL2>{});
+            } else if (kSL8 && K <= 4u * kSL8) {
+                if (fast) loop(Fast{}, std::integral_constant<int, kSL8>{});
+                else loop(Slow{}, std::integral_constant<int, kSL8>{});
+            } else if (fast) {
+                loop(Fast{}, std::integral_constant<int, 0>{});
+            } else {
+                loop(Slow{}, std::integral_constant<int, 0>{});
+            }
         } else {
             // no chain in this warp: meet the CTA's record barriers only
             const uint32_t R = jb.record_every;

@@ -522,12 +522,14 @@ def test_few_warps_variant_bit_exact(rule, K, lanes):
 
 
 @pytest.mark.parametrize("K,lanes,chains", [(8, 32, 1), (8, 32, 7), (5, 16, 5), (4, 8, 6), (1, 4, 9),
-                                            (3, 32, 2), (9, 32, 3), (40, 8, 5)])
+                                            (3, 32, 2), (9, 32, 3), (32, 16, 4), (17, 16, 2), (24, 32, 3),
+                                            (33, 32, 3), (40, 8, 5)])
 def test_untraced_uniform_root_loop_bit_exact(K, lanes, chains):
     """+-J items whose chains have the uniform root, no traced steps and a
     weight table short enough for shared memory run the step loop compiled
-    for that case; for K <= 8 in the 128-register variant it scans the slot
-    weights of two lanes only and draws the sites of lanes/2 steps at once.
+    for that case; for K <= 8 (K <= 32) in the 128-register variant it scans
+    the slot weights of 2 (8) lanes only and draws the sites of lanes/2
+    (lanes/8) steps at once.
     Energies, acceptances, overlaps, spins and fields follow the oracle bit
     for bit over advances of ragged lengths (site batches cut at any step)."""
     torch = need_gpu()
@@ -553,20 +555,23 @@ def test_untraced_uniform_root_loop_bit_exact(K, lanes, chains):
     b.close(); run.close(); inst.close()
 
 
-def test_few_warps_variant_gaussian_replay():
-    # the same variant on Gaussian couplings: every chain's recorded
-    # trajectory is one the oracle's node rule takes from the same draws
+@pytest.mark.parametrize("K,lanes", [(96, 32), (8, 32), (32, 32), (20, 16), (5, 4)])
+def test_few_warps_variant_gaussian_replay(K, lanes):
+    # the same variant on Gaussian couplings (K <= 32: sites drawn in
+    # batches of steps): every chain's recorded trajectory is one the
+    # oracle's node rule takes from the same draws
     torch = need_gpu()
     st = torch.cuda.Stream()
-    N, K, chains, steps = 257, 96, 5, 400
+    N, chains, steps = 257, 5, 400
     J = inputs.couplings_gauss(N, 610)
     init = inputs.initial_spins(chains, N, 611)
     inst = sk.Instance(J, stream=st)
     run = sk.Run(inst, chains=chains, K=K, beta=1.0, seed=23, init=init, trace_chains=chains,
                  trace_steps=steps)
     b = sk.Batch([run], warps_per_cta=16)
-    b.set_layout(32, 2)
-    b.advance(steps)
+    b.set_layout(lanes, 2)
+    b.advance(150)
+    b.advance(steps - 150)
     tr = run.trace()
     spins, _ = run.state()
     for c in range(chains):
