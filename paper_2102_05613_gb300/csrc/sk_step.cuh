@@ -206,6 +206,18 @@ __device__ __forceinline__ void take_sites(uint32_t (&sp)[2], const uint32_t (&b
     sp[0] = __shfl_sync(g.mask, bat[0], src, G);
     sp[1] = __shfl_sync(g.mask, bat[1], src, G);
 }
+// One slot per lane (slot d = gl + 1): lane gl takes site gl % 4 of what
+// draw_sites gives lane gl / 4, i.e. of batch lane SL j + gl / 4 (lanes past
+// 4 SL - 1, whose slots are past K, take in-range sites of the same step).
+template <int SL, int G>
+__device__ __forceinline__ void take_site1(uint32_t (&sp)[2], const uint32_t (&bat)[2], uint32_t j, const Grp<G>& g) {
+    const int src = static_cast<int>(j) * SL + ((g.gl >> 2) & (SL - 1));
+    const uint32_t w0 = __shfl_sync(g.mask, bat[0], src, G);
+    const uint32_t w1 = __shfl_sync(g.mask, bat[1], src, G);
+    const uint32_t w = (g.gl & 2) ? w1 : w0;
+    sp[0] = (w >> (16 * (g.gl & 1))) & 0xFFFFu;
+    sp[1] = 0u;
+}
 template <int NB>
 __device__ __forceinline__ uint32_t site_of(const uint32_t (&sp)[2 * NB], int k) {
     return (sp[k >> 1] >> (16 * (k & 1))) & 0xFFFFu;
@@ -556,6 +568,12 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
     static_assert(!BATCH || (RULE == 0 && NB == 1 && !STAGED && KEEPW && (SL & (SL - 1)) == 0 && G >= 2 * SL),
                   "site batches: MCMCMC in the few-chain variant, rows through L1");
     constexpr uint32_t SPB = BATCH ? G / SL : 1;
+    // whole-warp groups with site batches hold one slot per lane (slot
+    // d = lane + 1, K <= 32), so that a step's candidate work is one slot
+    // deep instead of four; their +-J scan covers the first 4 SL lanes
+    constexpr bool SPL1 = BATCH && G == 32;
+    constexpr int NQ = SPL1 ? 1 : 4 * NB;  // slots per lane
+    constexpr int SCANL = SPL1 ? (4 * SL < G ? 4 * SL : G) : (SL > 0 ? SL : 1);
     const Grp<G> g;
     // next record point (0: none; a record follows step t when t + 1 == next_rec)
     uint32_t next_rec = jb.record_every ? (t0 / jb.record_every + 1u) * jb.record_every : 0u;
@@ -588,7 +606,10 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
     uint32_t tb = t0;
     if constexpr (BATCH) {
         draw_site_batch<SL, G>(bat, tb, chain, c3, k0, k1, nblk, N, g);
-        take_sites<SL, G>(site, bat, 0u, g);
+        if constexpr (SPL1)
+            take_site1<SL, G>(site, bat, 0u, g);
+        else
+            take_sites<SL, G>(site, bat, 0u, g);
     } else if constexpr (!STAGED && AHEAD && RULE == 0) {
         draw_sites<NB, G>(site, t0, chain, c3, k0, k1, nblk, N, g);
     }
@@ -706,7 +727,10 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                         j = 0;
                         draw_site_batch<SL, G>(bat, tb, chain, c3, k0, k1, nblk, N, g);
                     }
-                    take_sites<SL, G>(nsite, bat, j, g);
+                    if constexpr (SPL1)
+                        take_site1<SL, G>(nsite, bat, j, g);
+                    else
+                        take_sites<SL, G>(nsite, bat, j, g);
                 } else if constexpr (!STAGED && AHEAD) {
                     draw_sites<NB, G>(nsite, t + 1u, chain, c3, k0, k1, nblk, N, g);
                 }
@@ -716,12 +740,17 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                 const uint32_t a = gshfl(g, site[0], 0) & 0xFFFFu;
                 const int sa = S[a];
                 const H dEa = static_cast<H>(2 * sa) * hf[a];
+                // slot of this lane's entry q
+                auto slot_d = [&](int q) -> uint32_t {
+                    return SPL1 ? static_cast<uint32_t>(g.gl) + 1u
+                                : 4u * G * (q >> 2) + 4u * g.gl + static_cast<uint32_t>(q & 3) + 1u;
+                };
                 H dE[4 * NB];
                 H mloc = 0;
 #pragma unroll
-                for (int q = 0; q < 4 * NB; ++q) {
-                    const uint32_t d = 4u * G * (q >> 2) + 4u * g.gl + (q & 3) + 1u;
-                    const uint32_t i = site_of<NB>(site, q);
+                for (int q = 0; q < NQ; ++q) {
+                    const uint32_t d = slot_d(q);
+                    const uint32_t i = SPL1 ? site[0] : site_of<NB>(site, q);
                     const int si = S[i];
                     const H hi = hf[i];
                     const H single = static_cast<H>(2 * si) * hi;
@@ -737,7 +766,7 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                 // root factor (the centre: slot 1 of a leaf root, slot 0 of a
                 // centre root); recomputed, not stored, where the choice needs them
                 auto slot_w = [&](int q) -> W {
-                    const uint32_t d = 4u * G * (q >> 2) + 4u * g.gl + (q & 3) + 1u;
+                    const uint32_t d = slot_d(q);
                     W x = 0;
                     const bool centre = leaf && d == 1u;
                     if (d <= K) {
@@ -757,7 +786,7 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
 #pragma unroll
                 for (int q = 0; q < NB; ++q) gsum_[q] = 0;
 #pragma unroll
-                for (int q = 0; q < 4 * NB; ++q) {
+                for (int q = 0; q < NQ; ++q) {
                     const W xq = slot_w(q);
                     if constexpr (KEEPW) xs[q] = xq;
                     gsum_[q >> 2] += xq;
@@ -775,9 +804,9 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                 W total = w0;
 #pragma unroll
                 for (int q = 0; q < NB; ++q) {
-                    if constexpr (SCANSL) {  // slots in lanes 0 .. SL-1 only
-                        incl[q] = gscan_first<(SCANSL ? SL : 1)>(g, gsum_[q]);
-                        tot[q] = gshfl(g, incl[q], SL - 1);
+                    if constexpr (SCANSL) {  // slots in lanes 0 .. SCANL-1 only
+                        incl[q] = gscan_first<SCANL>(g, gsum_[q]);
+                        tot[q] = gshfl(g, incl[q], SCANL - 1);
                     } else {
                         incl[q] = gscan(g, gsum_[q]);
                         tot[q] = gshfl(g, incl[q], G - 1);
@@ -798,10 +827,25 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                 uint32_t sel_site = 0;
                 bool found = u < w0;
                 W base = w0;
+                if constexpr (SPL1) {
+                    // the first lane whose prefix exceeds u; a rounding guard
+                    // takes the last lane up to it with a positive weight
+                    if (!found) {
+                        const unsigned over = gballot(g, base + incl[0] > u && (!SCANSL || g.gl < SCANL));
+                        const int L0 = over ? __ffs(over) - 1 : G - 1;
+                        const unsigned pos = gballot(g, xs[0] > W(0)) & ((2u << L0) - 1u);
+                        if (pos) {
+                            const int L = 31 - __clz(pos);
+                            sel_site = gshfl(g, site[0], L) & 0xFFFFu;
+                            sel_d = L + 1;
+                            found = true;
+                        }
+                    }
+                }
 #pragma unroll
-                for (int q = 0; q < NB; ++q) {
+                for (int q = 0; q < (SPL1 ? 0 : NB); ++q) {
                     const unsigned ball =
-                        gballot(g, !found && base + incl[q] > u && (!SCANSL || g.gl < SL));
+                        gballot(g, !found && base + incl[q] > u && (!SCANSL || g.gl < SCANL));
                     if (!found && ball) {
                         const int L = __ffs(ball) - 1;
                         // this lane's 4 weights (kept, or recomputed bit-identically),
