@@ -397,7 +397,9 @@ sk_status mcmcmc_batch_replay(sk_batch* b, uint32_t times);
  * fastest; graph classes try 1, 2, 4, 8 and 16 warps per chain with every
  * even number of chains per CTA that fits; star classes of at most 64 chains
  * also try the cluster-per-chain layout (mcmcmc_batch_set_cluster) at every
- * cluster size and chains-per-cluster value the class can take.  Then the
+ * cluster size and chains-per-cluster value the class can take, and star
+ * classes of at most 1024 chains the team layout (64 and 128 lanes, see
+ * mcmcmc_batch_set_layout) where the class can take it.  Then the
  * whole batch is timed with those per-class launches and with its star runs
  * in one fused launch (mcmcmc_batch_set_fused) of 4, 8 and 16 warps per CTA,
  * and the fastest of the four is kept.
@@ -421,7 +423,13 @@ sk_status mcmcmc_batch_autotune(sk_batch* b, uint32_t trial_steps, uint32_t* war
  *            lanes, K <= 128 8 lanes and K <= 256 16 lanes;
  *            Graph runs (trees and lines) take 64, 128, 256 or 512 lanes
  *            = 2, 4, 8 or 16 warps per chain (any smaller value: one warp);
- *            star classes clamp values above 32 to 32;
+ *            star classes take 64 lanes as the team layout of 2 warps per
+ *            chain and 128 or more as that of 4 warps: one proposal slot per
+ *            thread, one chain per team, one team per CTA where every run of
+ *            the class has one chain, else two (overlap pairs share a CTA);
+ *            MCMCMC with K <= 32 x warps per chain, or Metropolis, and no
+ *            node-weighted records (other classes fall back to 32 lanes).
+ *            +-J trajectories are those of the warp layouts bit for bit;
  *   staging  0 = default (rows through L1), 1 = the next step's row of J is
  *            staged in shared memory by TMA (two row buffers per chain),
  *            2 = rows are read through L1 (no buffers, so more chains fit in
@@ -496,7 +504,9 @@ sk_status mcmcmc_batch_info(const sk_batch* b, uint32_t* grid, uint32_t* warps_p
  * class 1024 + 2 kind + rule, 32 x (CTAs per cluster) lanes per chain, the
  * bytes of one chain's slices per CTA and chains per cluster as warps per CTA;
  * the fused launch (mcmcmc_batch_set_fused) reports kernel class 2048, 32
- * lanes, the largest run's bytes per chain and its warps per CTA.
+ * lanes, the largest run's bytes per chain and its warps per CTA; team
+ * classes report kernel class 4096 + 2 kind + rule, 32 x (warps per chain)
+ * lanes, the bytes per chain and the chains per CTA as warps per CTA.
  */
 sk_status mcmcmc_batch_classes(const sk_batch* b, uint32_t max, uint32_t* count, uint32_t* desc);
 

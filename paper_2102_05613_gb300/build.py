@@ -18,7 +18,8 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libsk_mcmcmc.so")
 SOURCES = ["sk_kernels.cu", "sk_capi.cu", "sk_noalloc.cu", "sk_recompute.cu", "sk_server.cu", "sk_graph.cu", "sk_setgen.cu", "sk_peaks.cu",
-           "sk_cluster.cu", "sk_cluster_pm1.cu", "sk_cluster_gauss.cu", "sk_fused.cu"] + [
+           "sk_cluster.cu", "sk_cluster_pm1.cu", "sk_cluster_gauss.cu", "sk_fused.cu",
+           "sk_team.cu", "sk_team_pm1.cu", "sk_team_gauss.cu"] + [
     f"sk_step_{c}_{r}_{s}.cu" for c in ("pm1", "gauss") for r in ("mcmcmc", "metropolis")
     for s in ("staged", "direct", "direct_nw")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -209,12 +209,16 @@ struct sk_batch {
         // its dynamic shared memory)
         bool fused = false;
         uint32_t fsmem = 0;
+        // team layout: warps per chain (2 or 4; 0: another layout); W is then
+        // the chains (teams) per CTA
+        uint32_t team = 0;
     };
     std::vector<sk_run*> runs;
     std::vector<Class> classes;
     std::map<uint64_t, uint32_t> tuned;  // key -> (stage << 16) | (G << 8) | W chosen by the autotuner
                                          // (graph classes: (warps per chain << 16) | (32 << 8) | W;
-                                         // cluster layout: (CTAs per cluster << 24) | (32 << 8) | chains)
+                                         // cluster layout: (CTAs per cluster << 24) | (32 << 8) | chains;
+                                         // team layout: G = 64 or 128 lanes, W = chains per CTA)
     uint32_t W_override = 0;             // warps_per_cta given at creation (0: as many as fit)
     uint32_t G_override = 0;             // mcmcmc_batch_set_layout lanes (0: default; graph classes
                                          // take lanes / 32 warps per chain when lanes >= 64)
@@ -1181,6 +1185,9 @@ constexpr uint32_t kMaxClasses = 64;
 // The autotuner tries the cluster-per-chain layout for classes of at most
 // this many chains (where one chain's latency, not throughput, is at stake).
 constexpr uint64_t kClusterTuneChains = 64;
+// ... and the team layout for classes of at most this many chains (a few
+// teams per SM at most).
+constexpr uint64_t kTeamTuneChains = 1024;
 
 uint32_t run_per_chain(const sk_run* r, bool staged = true) {
     return static_cast<uint32_t>((sk::warp_smem_bytes(r->inst->Npad, r->inst->kind, staged) + 127) / 128 * 128);
@@ -1257,6 +1264,39 @@ bool plan_cluster_class(const sk_batch* b, const std::vector<uint32_t>& idx, uin
     c.rule = r0->p.rule;
     c.nb = nb;
     c.cls = 1024 + static_cast<int>(c.kind) * 2 + static_cast<int>(c.rule);
+    return true;
+}
+
+// The team layout for the star class of runs `idx`: T warps per chain, W
+// chains per CTA (0: 2, or 1 when every run has one chain; W = 1 only then, so
+// that overlap pairs share a CTA).  Returns false for classes it cannot take:
+// graph runs, node-weighted records, MCMCMC with K > 32 T, or more shared
+// memory than a CTA has.
+bool plan_team_class(const sk_batch* b, const std::vector<uint32_t>& idx, uint32_t T, uint32_t W,
+                     sk_batch::Class& c) {
+    const sk_run* r0 = b->runs[idx[0]];
+    if (run_nw(r0) || r0->p.graph) return false;
+    bool single = true;
+    size_t pc = 0;
+    for (uint32_t i : idx) {
+        const sk_run* r = b->runs[i];
+        if (!sk::team_ok(r->p.rule, r->p.K, T)) return false;
+        single = single && r->chains == 1;
+        pc = std::max(pc, sk::team_chain_bytes(r->inst->Npad, T));
+    }
+    if (W == 0) W = single ? 1u : 2u;
+    if ((W != 1 && W != 2) || (W == 1 && !single)) return false;
+    if (W * pc > kSmemBudget) return false;
+    c.team = T;
+    c.W = W;
+    c.G = 32 * T;
+    c.gmin = 32;
+    c.stage = 0;
+    c.per_chain = static_cast<uint32_t>(pc);
+    c.kind = r0->inst->kind;
+    c.rule = r0->p.rule;
+    c.nb = 0;
+    c.cls = 4096 + static_cast<int>(c.kind) * 2 + static_cast<int>(c.rule);
     return true;
 }
 
@@ -1364,6 +1404,31 @@ sk_status plan_batch(sk_batch* b) {
                 continue;
             }
             if (tuned_cl) return fail(SK_ERR_INVALID_ARG, "launch class cannot take %u-CTA clusters", C);
+        }
+        {  // the team layout: autotuned (64 or 128 lanes in the tuned code), or
+           // forced by mcmcmc_batch_set_layout with 64 or more lanes
+            auto tt = b->tuned.find(c.key);
+            const bool tuned_t = tt != b->tuned.end() && (tt->second >> 24) == 0 && ((tt->second >> 8) & 0xFFu) >= 64;
+            const uint32_t lanes = tuned_t ? ((tt->second >> 8) & 0xFFu) : (tt == b->tuned.end() ? b->G_override : 0u);
+            if (lanes >= 64 &&
+                plan_team_class(b, g.second, lanes >= 128 ? 4u : 2u, tuned_t ? (tt->second & 0xFFu) : 0u, c)) {
+                const int occ = sk::team_occupancy(c.kind, c.rule, c.team, c.W, c.per_chain);
+                if (occ <= 0)
+                    return fail(SK_ERR_CUDA, "no team CTA of %u warps with %u bytes of shared memory can be resident",
+                                c.team * c.W, c.W * c.per_chain);
+                c.first_item = static_cast<uint32_t>(items.size());
+                for (uint32_t i : g.second) {
+                    const sk_run* r = b->runs[i];
+                    for (uint32_t ch = 0; ch < r->chains; ch += c.W)
+                        items.push_back(WorkItem{i, ch, std::min(c.W, r->chains - ch), 0});
+                }
+                c.n_items = static_cast<uint32_t>(items.size()) - c.first_item;
+                c.grid = std::min<uint32_t>(c.n_items, static_cast<uint32_t>(occ * sms));
+                grid = std::max(grid, c.grid);
+                classes.push_back(c);
+                continue;
+            }
+            if (tuned_t) return fail(SK_ERR_INVALID_ARG, "launch class cannot take the %u-lane team layout", lanes);
         }
         const bool nw = ((c.key >> 60) & 1u) != 0;  // node-weighted records: rows through L1 only
         bool single = true;  // every run of the class has one chain: no overlap pairs
@@ -1656,6 +1721,9 @@ sk_status launch_segment(sk_batch* b, uint64_t steps, int only = -1) {
             : c.cluster ? sk::launch_cluster(b->djobs, b->ditems + c.first_item, c.n_items, b->dqueue + k, steps, c.kind,
                                            c.rule, c.nb, c.cluster, c.W, c.jbytes, c.per_chain, c.grid / c.cluster,
                                            static_cast<uint32_t>(b->runs.size()), last, cs)
+            : c.team  ? sk::launch_team(b->djobs, b->ditems + c.first_item, c.n_items, b->dqueue + k, steps, c.kind,
+                                        c.rule, c.team, c.W, c.per_chain, c.grid,
+                                        static_cast<uint32_t>(b->runs.size()), last, cs)
             : c.graph ? sk::launch_graph(b->djobs, b->ditems + c.first_item, c.n_items, b->dqueue + k, steps, c.W,
                                        c.nw, c.per_chain, c.grid, static_cast<uint32_t>((c.cls - 512) / 4), c.graph,
                                        static_cast<uint32_t>(b->runs.size()), last, cs)
@@ -1889,6 +1957,10 @@ sk_status mcmcmc_batch_autotune(sk_batch* b, uint32_t trial_steps, uint32_t* out
                         for (uint32_t w : {1u, 2u, 4u, 8u})
                             if ((w > 1 || single) && w <= std::max<uint64_t>(2, total))
                                 cand.push_back((C << 24) | (32u << 8) | w);
+                // and the team layout (2 or 4 warps per chain) for classes of at
+                // most a few chains per SM (shapes it cannot take are skipped)
+                if (total <= kTeamTuneChains)
+                    for (uint32_t T : {2u, 4u}) cand.push_back(((32u * T) << 8) | (single ? 1u : 2u));
             }
             for (uint32_t gw : cand) {
                 b->tuned[key] = gw;
@@ -1994,6 +2066,7 @@ sk_status mcmcmc_batch_info(const sk_batch* b, uint32_t* grid, uint32_t* W, uint
         *smem = !c ? 0
                 : c->fused ? c->fsmem
                 : c->cluster ? c->jbytes + c->W * c->per_chain
+                : c->team    ? c->W * c->per_chain
                              : c->per_chain * c->W * (32 / c->G);
     }
     if (items) *items = b->n_items;

@@ -188,6 +188,31 @@ cudaError_t launch_cluster_gauss(uint32_t rule, uint32_t nb, const JobDev* jobs,
 int occupancy_cluster_pm1(uint32_t rule, uint32_t nb, uint32_t C, uint32_t W, uint32_t jbytes, uint32_t pc);
 int occupancy_cluster_gauss(uint32_t rule, uint32_t nb, uint32_t C, uint32_t W, uint32_t jbytes, uint32_t pc);
 
+// Team layout (sk_team*.cu): one chain per team of T = 2 or 4 warps, one
+// proposal slot per thread (MCMCMC takes K <= 32 T; Metropolis any run),
+// `teams` (1 or 2) chains of one run per CTA, team_chain_bytes of shared
+// memory per chain: spins, fields, the site ring, T block-0 buffers and the
+// team's exchange words.  launch_team runs the items of one class.
+inline size_t team_chain_bytes(uint32_t npad, uint32_t T) {
+    return ((size_t)5 * npad + 1024u * T + 64u + 127u) & ~(size_t)127;
+}
+inline bool team_ok(uint32_t rule, uint32_t K, uint32_t T) {
+    return (T == 2 || T == 4) && (rule == 1 || (K >= 1 && K <= 32u * T));
+}
+cudaError_t launch_team(const JobDev* jobs, const WorkItem* items, uint32_t n_items, uint32_t* queue,
+                        uint64_t nsteps, uint32_t kind, uint32_t rule, uint32_t T, uint32_t teams, uint32_t per_chain,
+                        uint32_t grid, uint32_t n_jobs, bool bump, cudaStream_t st);
+int team_occupancy(uint32_t kind, uint32_t rule, uint32_t T, uint32_t teams, uint32_t per_chain);  // CTAs per SM
+// Per coupling type (sk_team_pm1.cu, sk_team_gauss.cu).
+cudaError_t launch_team_pm1(const JobDev* jobs, const WorkItem* items, uint32_t n_items, uint32_t* queue,
+                            uint32_t nsteps, uint32_t rule, uint32_t T, uint32_t teams, uint32_t per_chain,
+                            uint32_t grid, cudaStream_t st);
+cudaError_t launch_team_gauss(const JobDev* jobs, const WorkItem* items, uint32_t n_items, uint32_t* queue,
+                              uint32_t nsteps, uint32_t rule, uint32_t T, uint32_t teams, uint32_t per_chain,
+                              uint32_t grid, cudaStream_t st);
+int occupancy_team_pm1(uint32_t rule, uint32_t T, uint32_t teams, uint32_t per_chain);
+int occupancy_team_gauss(uint32_t rule, uint32_t T, uint32_t teams, uint32_t per_chain);
+
 // Fused launch (sk_fused.cu): every star work item of a batch in one
 // persistent kernel of W warps per CTA (W <= 16), whole-warp chains, rows
 // through L1.  WorkItem::pad = (fused_variant << 24) | shared bytes per chain

@@ -398,8 +398,10 @@ class Batch:
 
     def set_layout(self, lanes: int = 0, staging: int = 0):
         """mcmcmc_batch_set_layout: lanes per chain (0, 4, 8, 16, 32; graph
-        runs also 64, 128, 256, 512 = 2..16 warps per chain); staging 0
-        default, 1 TMA-staged rows, 2 rows read through L1."""
+        runs also 64, 128, 256, 512 = 2..16 warps per chain; star runs 64 or
+        128 = the team layout of 2 or 4 warps per chain, one slot per
+        thread); staging 0 default, 1 TMA-staged rows, 2 rows read through
+        L1."""
         _check(lib().mcmcmc_batch_set_layout(self.handle, int(lanes), int(staging)))
 
     def set_cluster(self, ctas: int, chains: int = 0):
