@@ -251,15 +251,21 @@ def recompute_report(stream, peaks, fp8_measured=None, own_mma=None):
 # ---------------------------------------------------------------------------
 # single-chain latency: +-J N = 64 (J seed 0), K = 8, beta = 1, 1e5 steps
 # ---------------------------------------------------------------------------
-def dependent_shuffles(G, wide):
+def dependent_shuffles(G, wide, K=8):
     """Warp-collective rounds on one MCMCMC step's critical path with G lanes
     per chain (the few-chain variant): the broadcast of site a, the group
-    minimum (one redux), the inclusive scan of the slot weights (log2 G
-    shuffle levels; 64-bit +-J weights move as two shuffles issued together),
-    the total's broadcast, the ballot of the lanes past the draw and the
-    broadcast of the chosen slot."""
-    lg = int(math.log2(G))
-    return {"shuffle_rounds": 1 + lg + 1 + 1, "redux": 1, "ballot": 1,
+    minimum (one redux), the inclusive scan of the slot weights (64-bit +-J
+    weights move as two shuffles issued together), the total's broadcast, the
+    ballot(s) of the lanes past the draw and the broadcast of the chosen slot.
+    Whole-warp chains with K <= 32 hold one slot per lane (slot d = lane + 1,
+    two ballots: past the draw, positive weight) and their +-J scan covers the
+    lanes that hold slots (8 for K <= 8, 32 for K <= 32); otherwise four slots
+    per lane and a log2 G level scan.  The shuffles that hand out the next
+    step's sites from the batch do not wait on the step and are not counted."""
+    one_slot = G == 32 and K <= 32
+    lanes = (8 if K <= 8 else 32) if (one_slot and wide) else G
+    lg = int(math.log2(lanes))
+    return {"shuffle_rounds": 1 + lg + 1 + 1, "redux": 1, "ballot": 2 if one_slot else 1,
             "shuffle_instructions": 1 + lg * (2 if wide else 1) + (2 if wide else 1) + 1}
 
 
@@ -287,7 +293,7 @@ def latency_report(stream):
     return {"workload": "+-J SK N=64, J seed 0, one chain, MCMCMC K=8, beta=1, 1e5 steps, Philox seed 1",
             "ns_per_step": 1e6 * ms / steps, "candidate_configs_per_s": 8 * steps / (ms / 1e3),
             "layout": {"lanes_per_chain": layout[1], "warps_per_cta": layout[3]},
-            "dependent_collectives_per_step": dependent_shuffles(layout[1], True)}
+            "dependent_collectives_per_step": dependent_shuffles(layout[1], True, 8)}
 
 
 def _one_chain_ns(batch, stream, steps=20000):
