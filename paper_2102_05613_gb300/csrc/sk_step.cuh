@@ -563,6 +563,11 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
     // that the copy of the next step's row goes out at the start of a step
     // with no Philox rounds in front of it
     constexpr bool AHEAD2 = STAGED && KEEPW && RULE == 0;
+    // the slot weights are kept for the node search also in the throughput
+    // variants with two Philox blocks per lane (their register budget holds
+    // the 8 weights without spills there; a recomputation costs 4 exponentials
+    // and their lookups in the owning lanes of every group)
+    constexpr bool KEEPXS = KEEPW || NB == 2;
     constexpr bool BATCH = SL > 0;                     // sites in batches of SPB steps
     constexpr bool SCANSL = BATCH && sizeof(JT) == 1;  // +-J: the scan over SL lanes
     static_assert(!BATCH || (RULE == 0 && NB == 1 && !STAGED && KEEPW && (SL & (SL - 1)) == 0 && G >= 2 * SL),
@@ -782,13 +787,13 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                     return x;
                 };
                 W gsum_[NB];
-                W xs[KEEPW ? 4 * NB : 1];
+                W xs[KEEPXS ? 4 * NB : 1];
 #pragma unroll
                 for (int q = 0; q < NB; ++q) gsum_[q] = 0;
 #pragma unroll
                 for (int q = 0; q < NQ; ++q) {
                     const W xq = slot_w(q);
-                    if constexpr (KEEPW) xs[q] = xq;
+                    if constexpr (KEEPXS) xs[q] = xq;
                     gsum_[q >> 2] += xq;
                 }
                 W w0;  // slot 0, the root: the centre of a centre root, else a leaf
@@ -854,7 +859,7 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                         W mine = 0;
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
-                            if constexpr (KEEPW)
+                            if constexpr (KEEPXS)
                                 x[e] = xs[4 * q + e];
                             else
                                 x[e] = slot_w(4 * q + e);
