@@ -847,8 +847,75 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
                         }
                     }
                 }
+                // Gaussian weights with several blocks per lane: all blocks'
+                // ballots first (a block's only where no earlier one holds u),
+                // then one search in the block that does, so that the groups of
+                // a warp search together even when their draws fall in
+                // different blocks (for the 64-bit +-J weights the selects cost
+                // more than the second pass they save)
+                constexpr bool ONESEARCH = KEEPXS && !SPL1 && NB > 1 && sizeof(JT) == 4;
+                if constexpr (ONESEARCH) {
+                    unsigned ballq[NB];
+                    W baseq[NB];
+                    bool prior = false;
 #pragma unroll
-                for (int q = 0; q < (SPL1 ? 0 : NB); ++q) {
+                    for (int q = 0; q < NB; ++q) {
+                        ballq[q] = gballot(g, !found && !prior && base + incl[q] > u);
+                        baseq[q] = base;
+                        prior = prior || ballq[q] != 0u;
+                        base += tot[q];
+                    }
+                    if (!found && prior) {
+                        int qf = 0;
+                        unsigned ball = 0;
+                        W bse = 0, inc = 0;
+                        W x[4];
+#pragma unroll
+                        for (int q = NB - 1; q >= 0; --q)
+                            if (ballq[q]) {
+                                qf = q;
+                                ball = ballq[q];
+                                bse = baseq[q];
+                                inc = incl[q];
+                            }
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            x[e] = xs[e];
+#pragma unroll
+                            for (int q = 1; q < NB; ++q)
+                                if (q == qf) x[e] = xs[4 * q + e];
+                        }
+                        const int L = __ffs(ball) - 1;
+                        W mine = 0;
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) mine += x[e];
+                        W run = bse + (inc - mine);
+                        int my_e = -1, last_pos = -1;
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            if (x[e] > W(0)) {
+                                last_pos = e;
+                                if (my_e < 0) {
+                                    run += x[e];
+                                    if (run > u) my_e = e;
+                                }
+                            }
+                        }
+                        if (my_e < 0) my_e = last_pos;
+                        uint32_t my_site = 0;
+#pragma unroll
+                        for (int q = 0; q < NB; ++q)
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                if (q == qf && e == my_e) my_site = site_of<NB>(site, 4 * q + e);
+                        const uint32_t packed = gshfl(g, (my_site << 2) | static_cast<uint32_t>(my_e & 3), L);
+                        sel_site = packed >> 2;
+                        sel_d = 4 * G * qf + 4 * L + static_cast<int>(packed & 3u) + 1;
+                        found = true;
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < ((SPL1 || ONESEARCH) ? 0 : NB); ++q) {
                     const unsigned ball =
                         gballot(g, !found && base + incl[q] > u && (!SCANSL || g.gl < SCANL));
                     if (!found && ball) {
