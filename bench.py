@@ -994,7 +994,7 @@ def run_ours(args):
     # profiled layout, scaled by the chains processed (the state streamed once
     # per launch grows in proportion); null for any other layout
     profiled = [268, 16, 3072, 24]
-    traffic = (4 * 296.3e6 * INSTANCES / 64 if N == 512 and info["classes"]
+    traffic = (4 * 296.8e6 * INSTANCES / 64 if N == 512 and info["classes"]
                and list(info["classes"][0][:4]) == profiled else None)
     smem_peak = mp.get("smem_vec16_gbps")
     achieved = bytes_ps * cs_launch / mean_launch_s / 1e9
