@@ -542,10 +542,11 @@ __device__ __noinline__ void record(const JobDev& jb, bool write, uint32_t chain
 // FAST (+-J work items only): every chain of the item has the uniform root,
 // no traced steps and a weight table held whole in shared memory, and the loop
 // is compiled without the code for the other cases (about 10 % of a lone
-// chain's step).  SL > 0 (MCMCMC with K <= 4 SL in the few-chain variant,
-// rows through L1): the sites come in batches of G / SL steps
-// (draw_site_batch), and for +-J the slot-weight scan covers group lanes
-// 0 .. SL-1 only (the integer total is the same in any order).
+// chain's step).  SL > 0 (MCMCMC with K <= 4 SL and one block per lane in
+// the few-chain variant, or in 16-lane and whole-warp chains of the others;
+// rows through L1): the sites come in batches of G / SL steps (draw_site_batch; whole-warp
+// chains hold one slot per lane), and for +-J the slot-weight scan covers
+// only the lanes that hold slots (the integer total is the same in any order).
 template <typename JT, int RULE, int NB, int G, int STAGE, int UNROLL, bool RCH, bool FAST = false, int SL = 0>
 __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_t chain, const ChainMem& cm,
                                            int partner_off, uint32_t t0, uint32_t t1, uint32_t& acc,
@@ -563,20 +564,21 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
     // that the copy of the next step's row goes out at the start of a step
     // with no Philox rounds in front of it
     constexpr bool AHEAD2 = STAGED && KEEPW && RULE == 0;
-    // the slot weights are kept for the node search also in the throughput
-    // variants with two Philox blocks per lane (their register budget holds
-    // the 8 weights without spills there; a recomputation costs 4 exponentials
-    // and their lookups in the owning lanes of every group)
-    constexpr bool KEEPXS = KEEPW || NB == 2;
     constexpr bool BATCH = SL > 0;                     // sites in batches of SPB steps
     constexpr bool SCANSL = BATCH && sizeof(JT) == 1;  // +-J: the scan over SL lanes
-    static_assert(!BATCH || (RULE == 0 && NB == 1 && !STAGED && KEEPW && (SL & (SL - 1)) == 0 && G >= 2 * SL),
-                  "site batches: MCMCMC in the few-chain variant, rows through L1");
+    static_assert(!BATCH || (RULE == 0 && NB == 1 && !STAGED && (SL & (SL - 1)) == 0 && G >= 2 * SL),
+                  "site batches: MCMCMC with one block per lane, rows through L1");
     constexpr uint32_t SPB = BATCH ? G / SL : 1;
     // whole-warp groups with site batches hold one slot per lane (slot
     // d = lane + 1, K <= 32), so that a step's candidate work is one slot
     // deep instead of four; their +-J scan covers the first 4 SL lanes
     constexpr bool SPL1 = BATCH && G == 32;
+    // the slot weights are kept for the node search also in the throughput
+    // variants with two Philox blocks per lane (their register budget holds
+    // the 8 weights without spills there; a recomputation costs 4 exponentials
+    // and their lookups in the owning lanes of every group) and with one slot
+    // per lane (one weight)
+    constexpr bool KEEPXS = KEEPW || NB == 2 || SPL1;
     constexpr int NQ = SPL1 ? 1 : 4 * NB;  // slots per lane
     constexpr int SCANL = SPL1 ? (4 * SL < G ? 4 * SL : G) : (SL > 0 ? SL : 1);
     const Grp<G> g;
@@ -655,7 +657,20 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
 
         // direct rows: this step's sites now; staged rows: the next step's
         // sites and the TMA of its first row, one step ahead
-        if constexpr (!AHEAD && RULE == 0) draw_sites<NB, G>(site, t, chain, c3, k0, k1, nblk, N, g);
+        if constexpr (BATCH && !AHEAD) {  // this step's sites out of the batch
+            uint32_t j = t - tb;
+            if (j == SPB) {
+                tb += SPB;
+                j = 0;
+                draw_site_batch<SL, G>(bat, tb, chain, c3, k0, k1, nblk, N, g);
+            }
+            if constexpr (SPL1)
+                take_site1<SL, G>(site, bat, j, g);
+            else
+                take_sites<SL, G>(site, bat, j, g);
+        } else if constexpr (!AHEAD && RULE == 0) {
+            draw_sites<NB, G>(site, t, chain, c3, k0, k1, nblk, N, g);
+        }
         uint32_t nsite[2 * NB];
         if (STAGED && t + 1u < t1) {
             uint32_t nx;
@@ -725,7 +740,7 @@ __device__ __forceinline__ void chain_loop(const JobDev& jb, bool write, uint32_
             } else {
                 // ---- MCMCMC: K proposals on the uniform-root star ----
                 // (few-chain variant: the next step's sites, interleaved with this step's work)
-                if constexpr (BATCH) {
+                if constexpr (BATCH && AHEAD) {
                     uint32_t j = t + 1u - tb;
                     if (j == SPB) {
                         tb += SPB;
@@ -1070,12 +1085,14 @@ __device__ __forceinline__ void run_item(const WorkItem& wi, const JobDev& jb, u
             // +-J items whose chains all have the uniform root, no traced
             // steps and a weight table that fits the shared copy take the loop
             // compiled for that case; MCMCMC items with K <= 8 or K <= 32 in
-            // the few-chain variant (rows through L1) take their sites in
-            // batches of G/2 or G/8 steps (a choice for the whole CTA: its
-            // groups meet the same record barriers)
+            // the few-chain variant, or in 16-lane and whole-warp chains of the
+            // others (rows through L1), take their sites in batches of G/2 or
+            // G/8 steps (a choice for the whole CTA: its groups meet the same
+            // record barriers)
             const bool fast = sizeof(JT) == 1 && jb.wlen <= kWCache && jb.fcen + jb.fleaf == (2u << 20) &&
                               jb.trace_chains <= wi.chain0;
-            constexpr bool kBatch = RULE == 0 && NB == 1 && STAGE != 1 && UNROLL >= 8;
+            // (throughput variants: 16-lane and whole-warp chains)
+            constexpr bool kBatch = RULE == 0 && NB == 1 && STAGE != 1 && (UNROLL >= 8 || G >= 16);
             constexpr int kSL2 = kBatch && G >= 4 ? 2 : 0;
             constexpr int kSL8 = kBatch && G >= 16 ? 8 : 0;
             auto loop = [&](auto fast_c, auto sl_c) {

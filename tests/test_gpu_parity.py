@@ -488,10 +488,11 @@ def test_inputs_while_compute_is_queued():
     big.close(); run.close(); inst.close()
 
 
-@pytest.mark.parametrize("rule,K,lanes", [(sk.SK_RULE_MCMCMC, 8, 32), (sk.SK_RULE_MCMCMC, 128, 32),
-                                           (sk.SK_RULE_MCMCMC, 128, 16), (sk.SK_RULE_MCMCMC, 200, 16),
-                                           (sk.SK_RULE_MCMCMC, 40, 8), (sk.SK_RULE_METROPOLIS, 1, 32)])
-def test_few_warps_variant_bit_exact(rule, K, lanes):
+@pytest.mark.parametrize("rule,K,lanes,warps", [(sk.SK_RULE_MCMCMC, 8, 32, 8), (sk.SK_RULE_MCMCMC, 128, 32, 8),
+                                                 (sk.SK_RULE_MCMCMC, 128, 16, 8), (sk.SK_RULE_MCMCMC, 200, 16, 8),
+                                                 (sk.SK_RULE_MCMCMC, 40, 8, 8), (sk.SK_RULE_METROPOLIS, 1, 32, 8),
+                                                 (sk.SK_RULE_MCMCMC, 8, 32, 32), (sk.SK_RULE_MCMCMC, 30, 16, 24)])
+def test_few_warps_variant_bit_exact(rule, K, lanes, warps):
     """The 128-register step kernel (at most 16 warps per CTA: the update's
     row loads eight iterations deep, and for MCMCMC with rows through L1 the
     next step's draws and J_ab gathered during the update) follows the
@@ -504,9 +505,9 @@ def test_few_warps_variant_bit_exact(rule, K, lanes):
     inst = sk.Instance(J, stream=st)
     run = sk.Run(inst, chains=chains, K=K, rule=rule, beta=0.8, seed=17, record_every=R,
                  max_records=steps // R, init=init, trace_chains=chains, trace_steps=steps)
-    b = sk.Batch([run], warps_per_cta=8)
+    b = sk.Batch([run], warps_per_cta=warps)
     b.set_layout(lanes, 2)
-    assert b.info()["warps_per_cta"] <= 16
+    assert b.info()["warps_per_cta"] <= max(16, warps)
     b.advance(steps // 3)
     b.advance(steps - steps // 3)
     tr = run.trace()
@@ -521,10 +522,12 @@ def test_few_warps_variant_bit_exact(rule, K, lanes):
     b.close(); run.close(); inst.close()
 
 
-@pytest.mark.parametrize("K,lanes,chains", [(8, 32, 1), (8, 32, 7), (5, 16, 5), (4, 8, 6), (1, 4, 9),
-                                            (3, 32, 2), (9, 32, 3), (32, 16, 4), (17, 16, 2), (24, 32, 3),
-                                            (33, 32, 3), (40, 8, 5)])
-def test_untraced_uniform_root_loop_bit_exact(K, lanes, chains):
+@pytest.mark.parametrize("K,lanes,chains,warps", [
+    (8, 32, 1, 8), (8, 32, 7, 8), (5, 16, 5, 8), (4, 8, 6, 8), (1, 4, 9, 8), (3, 32, 2, 8), (9, 32, 3, 8),
+    (32, 16, 4, 8), (17, 16, 2, 8), (24, 32, 3, 8), (33, 32, 3, 8), (40, 8, 5, 8),
+    # the throughput variants (20, 24, 32 warps: 96, 80, 64 registers) with 16-lane and whole-warp chains
+    (8, 32, 40, 32), (32, 32, 21, 24), (5, 16, 50, 20), (32, 16, 33, 32), (2, 16, 19, 24)])
+def test_untraced_uniform_root_loop_bit_exact(K, lanes, chains, warps):
     """+-J items whose chains have the uniform root, no traced steps and a
     weight table short enough for shared memory run the step loop compiled
     for that case; for K <= 8 (K <= 32) in the 128-register variant it scans
@@ -539,7 +542,7 @@ def test_untraced_uniform_root_loop_bit_exact(K, lanes, chains):
     init = inputs.initial_spins(chains, N, 701 + K)
     inst = sk.Instance(J, stream=st)
     run = sk.Run(inst, chains=chains, K=K, beta=0.9, seed=23, record_every=R, max_records=steps // R, init=init)
-    b = sk.Batch([run], warps_per_cta=8)
+    b = sk.Batch([run], warps_per_cta=warps)
     b.set_layout(lanes, 2)
     for n in (37, 100, steps - 137):
         b.advance(n)
@@ -555,8 +558,9 @@ def test_untraced_uniform_root_loop_bit_exact(K, lanes, chains):
     b.close(); run.close(); inst.close()
 
 
-@pytest.mark.parametrize("K,lanes", [(96, 32), (8, 32), (32, 32), (20, 16), (5, 4)])
-def test_few_warps_variant_gaussian_replay(K, lanes):
+@pytest.mark.parametrize("K,lanes,warps", [(96, 32, 16), (8, 32, 16), (32, 32, 16), (20, 16, 16), (5, 4, 16),
+                                          (8, 32, 32), (32, 32, 24), (20, 16, 32), (32, 16, 20)])
+def test_few_warps_variant_gaussian_replay(K, lanes, warps):
     # the same variant on Gaussian couplings (K <= 32: sites drawn in
     # batches of steps): every chain's recorded trajectory is one the
     # oracle's node rule takes from the same draws
@@ -568,7 +572,7 @@ def test_few_warps_variant_gaussian_replay(K, lanes):
     inst = sk.Instance(J, stream=st)
     run = sk.Run(inst, chains=chains, K=K, beta=1.0, seed=23, init=init, trace_chains=chains,
                  trace_steps=steps)
-    b = sk.Batch([run], warps_per_cta=16)
+    b = sk.Batch([run], warps_per_cta=warps)
     b.set_layout(lanes, 2)
     b.advance(150)
     b.advance(steps - 150)
