@@ -19,7 +19,11 @@
 //       blocks 1..ceil(K/4) give site_d = floor(w N / 2^32), d = 1..K.
 //       Group lane l computes blocks 1 + l + G q for q < NB (NB blocks per
 //       lane), so its slots are d = 4Gq + 4l + 1..4 (slot order is lane order
-//       within a q, then q); block 0 is computed G steps at a time.
+//       within a q, then q); block 0 is computed G steps at a time.  With
+//       K <= 32 and one block per lane (16- and 32-lane groups), the blocks
+//       of G/SL steps are drawn in one pass (draw_site_batch) and handed out
+//       by shuffles, and whole-warp groups then hold one slot per lane,
+//       d = l + 1 (take_site1): the same draws, hence the same choices.
 //   a2  the row of J at a = site_1 of the NEXT step is staged by TMA.
 //   a3  candidate energies: centre root dE_d = 2 s_i h_i (i = site_d);
 //       leaf root dE_1 = 2 s_a h_a, dE_d = 2 s_a h_a + 2 s_b h_b - 4 J_ab s_a s_b
